@@ -1,0 +1,311 @@
+"""Benchmark of the word-count hot path on GB300.
+
+Default workload: the large single-pass count -- 1e9 bytes of Zipf(1.0) text
+over a 1M-word vocabulary (~170M words), one document, 64-bit counts.  A
+step is one whole pass of the path: tokenise + two-level count, compaction
+and the radix sort into (count desc, word asc).  Inputs are resident in HBM
+when the timed region starts; 1 GB is larger than L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line (rank 0).  With --impl reference it times the CPU oracle
+(test infrastructure) on a bounded sample of the same workload instead.
+Under torchrun each rank counts its own replica of the workload (no
+collectives on the data path; timing barrier + max over ranks only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "word-count input GB/s (1 GB Zipf corpus)"
+UNIT = "GB/s"
+WORKLOAD = ("large: 1e9 B synthetic Zipf(s=1.0) text, 1M-word vocabulary (lengths 1-24), mixed case, "
+            "digits and punctuation as separators, ~169M words, one document, uint64 global counts")
+ORACLE_MBPS_GUESS = 13.0  # single-core oracle throughput, MB/s, used only to size its sample
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "50", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("wc_count.cu", "wc_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2206_05269_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kind: str):
+    """DRAM bytes per launch of the counting kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "count_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return d.get(kind)
+
+
+def oracle_sample(text: np.ndarray, nbytes: int) -> np.ndarray:
+    """A prefix of the corpus of about nbytes, cut after a space."""
+    n = min(nbytes, text.size)
+    while n < text.size and text[n - 1] != 0x20:
+        n += 1
+    return text[:n]
+
+
+def run_reference(args, rank, world):
+    """The oracle, as it stands, on the host cores, per step on a bounded
+    sample of the workload."""
+    if rank != 0:
+        return
+    import corpus
+    import oracle
+    oracle.build()
+    c = corpus.generate("large")
+    per_step = int(max(1 << 20, min(200e6, 150.0 * ORACLE_MBPS_GUESS * 1e6 / max(1, args.steps + args.warmup))))
+    sample = oracle_sample(c.text, per_step)
+    for _ in range(args.warmup):
+        oracle.count(sample, keep_docs=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.count(sample, keep_docs=False)
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    val = sample.size / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_bytes_per_step": int(sample.size)},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"first {sample.size} bytes of the workload per step (single-threaded C++ oracle)"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank, world, local):
+    import torch
+    import corpus
+    from paper_2206_05269_gb300 import wc
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    c = corpus.generate("large", seed=corpus.RECIPES["large"].seed + rank, size_a=args.bytes)
+    nbytes = c.nbytes
+    host = torch.from_numpy(c.text).pin_memory()
+    text = host.to(f"cuda:{local}", non_blocking=False)
+    ctr = wc.Counter(local)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return ctr.count(text, stream)
+
+    # warm-up (also settles the pool and checks the result is valid)
+    for _ in range(args.warmup):
+        t = step()
+        if t.status() != wc.WC_OK:
+            raise RuntimeError(f"count failed: {wc.wc_last_error(ctr.ctx)}")
+        nwords, ntok, _ = t.size()
+        t.free()
+
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    wc.wc_profile_enable(ctr.ctx, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tables, done = [], []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        tables.append(step())
+        if len(tables) > 8:  # bound device memory: the oldest step is long finished
+            done.append(tables.pop(0).status())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_count, ms_finish, n_count, launches = wc.wc_profile_read(ctr.ctx)
+    wc.wc_profile_enable(ctr.ctx, False)
+    clocks = sampler.stop()
+    elapsed = ev0.elapsed_time(ev1)
+    done += [t.status() for t in tables]
+    if any(st != wc.WC_OK for st in done):
+        raise RuntimeError("a timed step failed")
+    del tables
+    ms_step = elapsed / args.steps
+    if dist:
+        tt = torch.tensor([ms_step], device=f"cuda:{local}")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_step = float(tt.item())
+    value = nbytes * world / (ms_step * 1e-3) / 1e9
+
+    # end to end through the C ABI: host text -> device, count, table -> host
+    e2e_steps = max(3, min(args.steps, 10))
+    dev2 = torch.empty_like(text)
+    d2h = 0
+    t_e2e = []
+    for i in range(e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dev2.copy_(host, non_blocking=True)
+        tab = ctr.count(dev2, stream)
+        w, o, cnt = tab.export(stream)
+        t_e2e.append(time.perf_counter() - t0)
+        d2h = w.nbytes + o.nbytes + cnt.nbytes
+        tab.free()
+    e2e_s = statistics.mean(t_e2e[1:])
+    e2e_val = nbytes * world / e2e_s / 1e9
+
+    peak, peak_kind = measured_peaks()
+    avg_count_s = ms_count / max(1, n_count) * 1e-3
+    alg_bytes = nbytes + nwords * 24
+    achieved = alg_bytes / avg_count_s / 1e9
+    traffic = profiled_traffic("dram_bytes_per_launch")
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        sample = oracle_sample(c.text, int(args.cpu_sample_mb * 1e6))
+        t0 = time.perf_counter()
+        r = oracle.count(sample, keep_docs=False)
+        dt = time.perf_counter() - t0
+        del r
+        cpu = {"value": sample.size / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {sample.size} bytes of the same corpus, single-threaded C++ oracle, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "bytes": nbytes, "words": ntok, "distinct": nwords,
+                       "l2": "input (1e9 B) larger than L2, no flush", "parallelism": f"replicas x{world}"},
+            "words_per_s": ntok * world / (ms_step * 1e-3),
+            "stages_ms": {"count_kernel": ms_count / max(1, n_count), "compact_sort": ms_finish / max(1, n_count)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_count_global", "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": alg_bytes},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    ctr.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-sample-mb", type=float, default=150.0)
+    ap.add_argument("--bytes", type=float, default=1e9, help="corpus size (smaller only for profiling)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    run_gpu(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,161 @@
+/*
+ * wc.h -- exact word-frequency counting on one GB300 GPU (sm_103a).
+ *
+ * The library implements the map and reduce of the MapReduce word counter of
+ * arXiv 2206.05269 entirely on the GPU:
+ *
+ *   map    (Sec. 2 and Sec. 3.1: strip punctuation, lowercase, split into
+ *           words): a word is a maximal run of ASCII letters [A-Za-z], each
+ *           letter lowercased; every other byte separates words; a document
+ *           edge separates words.
+ *   reduce (Sec. 3.1-3.3: one dictionary per document, then the counts of
+ *           each key summed across documents): exact integer counts per
+ *           document, per document class and overall.
+ *   order  count descending, then word bytes ascending (a proper prefix
+ *           sorts first).
+ *
+ * The paper lists a GPU dictionary as future work (Sec. 5.2); here it is a
+ * two-level open-addressing table (per-block shared memory, then global
+ * memory) keyed by the full word bytes, so two different words never merge.
+ *
+ * Conventions for every call:
+ *  - Pointers named d_* are device pointers, h_* are host pointers.
+ *  - Calls that take a cudaStream_t are stream-ordered and asynchronous: the
+ *    caller's device inputs must stay alive and unmodified until the stream
+ *    reaches the call; results are valid once the stream has reached it.
+ *    wc_table_size, wc_table_status and wc_table_export wait for the table.
+ *  - Every call returns a wc_status; the library never aborts, prints or
+ *    traps.  wc_last_error(ctx) gives a message for the last failure.
+ *  - The library owns wc_table and wc_batch objects until *_free.
+ *  - A context may be used from one host thread at a time.
+ *  - Device-side capacity overflows (table, long-word table, long-word byte
+ *    arena, probe limits) are reported as WC_ERR_CAPACITY by wc_table_status,
+ *    wc_table_size and wc_table_export; such a table holds no partial result.
+ *    Count again with larger capacities (wc_count_opts).
+ */
+#ifndef WC_H_
+#define WC_H_
+
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WC_OK = 0,
+    WC_ERR_INVALID_ARG = 1,  /* bad pointer, size, index or option */
+    WC_ERR_OOM = 2,          /* device allocation failed */
+    WC_ERR_BUDGET = 3,       /* the context's device-memory budget would be exceeded */
+    WC_ERR_CAPACITY = 4,     /* a device table or arena overflowed; retry larger */
+    WC_ERR_CUDA = 5,         /* a CUDA runtime call failed (message in wc_last_error) */
+    WC_ERR_TIMEOUT = 6,      /* a bounded device wait gave up */
+    WC_ERR_INTERNAL = 7,
+    WC_ERR_UNSUPPORTED = 8   /* input outside the documented limits */
+} wc_status;
+
+typedef struct {
+    int device;                 /* CUDA device ordinal */
+    uint64_t mem_budget_bytes;  /* 0 = no budget */
+    int count_bits;             /* width of global/class counts: 32 or 64 (per-document counts are 32) */
+    int autotune;               /* 1 = pick batched-kernel shapes by timing, cached per size class */
+    const char *tune_cache_path;/* JSON cache for the autotuner; NULL = in-memory only */
+} wc_config;
+
+typedef struct wc_ctx wc_ctx;
+typedef struct wc_table wc_table;
+typedef struct wc_batch wc_batch;
+
+/* Optional capacity hints for one count; zero fields pick automatic sizes. */
+typedef struct {
+    uint64_t table_slots;   /* short-word table slots (rounded up to a power of two) */
+    uint64_t long_slots;    /* long-word (> 16 letters) table slots */
+    uint64_t arena_bytes;   /* bytes for the distinct long words' text */
+} wc_count_opts;
+
+enum { WC_TABLE_DOC = 0, WC_TABLE_CLASS = 1, WC_TABLE_GLOBAL = 2 };
+
+/* Creates a context on cfg->device (NULL cfg = defaults: device 0, no
+ * budget, 64-bit counts, no autotune).  *out is set on WC_OK only. */
+wc_status wc_create(const wc_config *cfg, wc_ctx **out);
+void wc_destroy(wc_ctx *ctx);
+
+/* Counts the words of one document d_text[0, nbytes) into a new table with
+ * ctx count width.  Implements Sec. 3 map + reduce for a single document
+ * (the paper's per-document dictionary, built on the GPU).  nbytes may be 0.
+ * d_text may have any alignment. */
+wc_status wc_count(wc_ctx *ctx, const uint8_t *d_text, uint64_t nbytes, cudaStream_t stream,
+                   wc_table **out);
+wc_status wc_count_ex(wc_ctx *ctx, const uint8_t *d_text, uint64_t nbytes,
+                      const wc_count_opts *opts, cudaStream_t stream, wc_table **out);
+
+/* Counts ndocs documents in one pass: document i is d_text[d_offsets[i],
+ * d_offsets[i+1]) (device uint64, non-decreasing, d_offsets[0] may be > 0).
+ * d_class (device uint32, may be NULL) assigns each document a class below
+ * nclasses.  Produces per-document tables (32-bit counts), per-class tables
+ * and the global table (ctx count width): Sec. 3.1's per-document
+ * dictionaries and Sec. 3.3's sum across documents.  ndocs and the offsets
+ * on the host (h_offsets, same layout) are needed to plan the launch. */
+wc_status wc_count_batched(wc_ctx *ctx, const uint8_t *d_text, const uint64_t *d_offsets,
+                           const uint64_t *h_offsets, uint32_t ndocs, const uint32_t *d_class,
+                           uint32_t nclasses, cudaStream_t stream, wc_batch **out);
+
+/* Borrows one table of a batch (owned by the batch). */
+wc_status wc_batch_table(const wc_batch *batch, int kind, uint32_t idx, const wc_table **out);
+
+/* Top-k of class `cls` by the ratio of in-class to out-of-class count
+ * (Sec. 4.3's search for words one class uses more than the others, made
+ * exact): cin/cout descending with cout = global - cin (cout = 0 ranks
+ * first), then cin descending, then word ascending.  Writes up to k rows:
+ * h_idx = index into the class table's sorted order, h_cin, h_cout.
+ * *nout = rows written.  Waits for the batch. */
+wc_status wc_class_ratio_topk(wc_ctx *ctx, const wc_batch *batch, uint32_t cls, uint32_t k,
+                              cudaStream_t stream, uint64_t *h_idx, uint64_t *h_cin,
+                              uint64_t *h_cout, uint32_t *nout);
+
+/* Sums n tables word by word into a new table (Sec. 3.3: counts 10, 4 and 3
+ * of one word reduce to 17).  Count width = ctx count width. */
+wc_status wc_merge(wc_ctx *ctx, const wc_table *const *in, uint32_t n, cudaStream_t stream,
+                   wc_table **out);
+
+/* The first k rows of a table in its sorted order (k >= size: all rows). */
+wc_status wc_topk(wc_ctx *ctx, const wc_table *in, uint32_t k, cudaStream_t stream,
+                  wc_table **out);
+
+/* Waits for the table; reports WC_ERR_CAPACITY / WC_ERR_TIMEOUT from the device. */
+wc_status wc_table_status(const wc_table *t);
+
+/* Waits for the table, then gives its distinct words, total count (tokens)
+ * and the bytes needed for wc_table_export's h_words. */
+wc_status wc_table_size(const wc_table *t, uint64_t *nwords, uint64_t *ntokens,
+                        uint64_t *word_bytes);
+
+/* Copies the sorted table to the host: h_words (word_bytes bytes, words back
+ * to back), h_word_offsets (nwords+1 entries), h_counts (nwords entries of
+ * uint32 or uint64 per wc_table_count_bits).  Any pointer may be NULL to skip
+ * that array.  Waits until the copy is complete. */
+wc_status wc_table_export(const wc_table *t, uint8_t *h_words, uint64_t *h_word_offsets,
+                          void *h_counts, cudaStream_t stream);
+int wc_table_count_bits(const wc_table *t);
+
+void wc_table_free(wc_table *t);
+void wc_batch_free(wc_batch *b);
+
+/* Stage tracing.  While enabled, the context records CUDA events on the
+ * launching stream around each counting kernel and around each compaction +
+ * sort stage of wc_count / wc_count_ex / wc_merge, and counts the kernels
+ * it launches.  wc_profile_read waits for the recorded events and returns
+ * the summed stage times in milliseconds, how many counting kernels were
+ * timed, and how many kernels the library launched since enabling. */
+wc_status wc_profile_enable(wc_ctx *ctx, int enable);
+wc_status wc_profile_read(wc_ctx *ctx, double *ms_count, double *ms_finish, uint64_t *count_launches,
+                          uint64_t *kernel_launches);
+
+const char *wc_status_str(wc_status s);
+const char *wc_last_error(const wc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WC_H_ */

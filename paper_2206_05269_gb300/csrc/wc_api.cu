@@ -1,0 +1,462 @@
+// C-ABI entry points (include/wc.h): contexts, tables, counting, merge,
+// top-k and export.  Device memory comes from a per-context stream-ordered
+// pool and is charged against the context's budget.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/wc.h"
+#include "wc_internal.h"
+#include "wc_host.h"
+
+using namespace wc;
+
+// ---------------------------------------------------------------- context
+const char *wc_status_str(wc_status s) {
+    switch (s) {
+    case WC_OK: return "ok";
+    case WC_ERR_INVALID_ARG: return "invalid argument";
+    case WC_ERR_OOM: return "out of device memory";
+    case WC_ERR_BUDGET: return "device-memory budget exceeded";
+    case WC_ERR_CAPACITY: return "table capacity exceeded";
+    case WC_ERR_CUDA: return "CUDA error";
+    case WC_ERR_TIMEOUT: return "device wait timed out";
+    case WC_ERR_INTERNAL: return "internal error";
+    case WC_ERR_UNSUPPORTED: return "unsupported input";
+    }
+    return "unknown status";
+}
+
+const char *wc_last_error(const wc_ctx *ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+wc_status wc_ctx::fail(wc_status s, const char *what) {
+    last_error = std::string(wc_status_str(s)) + ": " + what;
+    return s;
+}
+wc_status wc_ctx::cuda_fail(cudaError_t e, const char *what) {
+    last_error = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return WC_ERR_OOM;
+    return WC_ERR_CUDA;
+}
+
+wc_status wc_ctx::alloc(void **p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (budget && used.load() + bytes > budget) return fail(WC_ERR_BUDGET, "allocation over the context budget");
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(e, "cudaMallocFromPoolAsync");
+    }
+    used += bytes;
+    return WC_OK;
+}
+void wc_ctx::release(void *p, size_t bytes, cudaStream_t s) {
+    if (!p) return;
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~(size_t)255;
+    cudaFreeAsync(p, s);
+    used -= bytes;
+}
+
+void wc_ctx::prof_mark(std::vector<cudaEvent_t> &v, cudaStream_t s) {
+    if (!profile) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, s);
+    v.push_back(e);
+}
+
+static void prof_clear(wc_ctx *ctx) {
+    for (auto e : ctx->ev_count) cudaEventDestroy(e);
+    for (auto e : ctx->ev_finish) cudaEventDestroy(e);
+    ctx->ev_count.clear();
+    ctx->ev_finish.clear();
+    ctx->launches = 0;
+}
+
+wc_status wc_profile_enable(wc_ctx *ctx, int enable) {
+    if (!ctx) return WC_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    prof_clear(ctx);
+    ctx->profile = enable != 0;
+    return WC_OK;
+}
+
+static double sum_pairs(wc_ctx *ctx, const std::vector<cudaEvent_t> &v, cudaError_t *err) {
+    double tot = 0;
+    for (size_t i = 0; i + 1 < v.size(); i += 2) {
+        float ms = 0;
+        cudaError_t e = cudaEventSynchronize(v[i + 1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, v[i], v[i + 1]);
+        if (e != cudaSuccess) *err = e;
+        tot += ms;
+    }
+    return tot;
+}
+
+wc_status wc_profile_read(wc_ctx *ctx, double *ms_count, double *ms_finish, uint64_t *count_launches,
+                          uint64_t *kernel_launches) {
+    if (!ctx) return WC_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    cudaError_t err = cudaSuccess;
+    double a = sum_pairs(ctx, ctx->ev_count, &err), b = sum_pairs(ctx, ctx->ev_finish, &err);
+    if (err != cudaSuccess) return ctx->cuda_fail(err, "wc_profile_read");
+    if (ms_count) *ms_count = a;
+    if (ms_finish) *ms_finish = b;
+    if (count_launches) *count_launches = ctx->ev_count.size() / 2;
+    if (kernel_launches) *kernel_launches = ctx->launches;
+    return WC_OK;
+}
+
+wc_status wc_create(const wc_config *cfg, wc_ctx **out) {
+    if (!out) return WC_ERR_INVALID_ARG;
+    *out = nullptr;
+    wc_config c{0, 0, 64, 0, nullptr};
+    if (cfg) c = *cfg;
+    if (c.count_bits != 32 && c.count_bits != 64) return WC_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev) {
+        cudaGetLastError();
+        return WC_ERR_INVALID_ARG;
+    }
+    wc_ctx *ctx = new wc_ctx();
+    ctx->device = c.device;
+    ctx->budget = c.mem_budget_bytes;
+    ctx->count_bits = c.count_bits;
+    ctx->autotune = c.autotune;
+    if (c.tune_cache_path) ctx->tune_cache_path = c.tune_cache_path;
+    cudaSetDevice(c.device);
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = c.device;
+    cudaError_t e = cudaMemPoolCreate(&ctx->pool, &props);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return WC_ERR_CUDA;
+    }
+    uint64_t keep = UINT64_MAX;  // keep freed memory cached in the pool
+    cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, c.device);
+    *out = ctx;
+    return WC_OK;
+}
+
+void wc_destroy(wc_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    prof_clear(ctx);
+    cudaMemPoolDestroy(ctx->pool);
+    delete ctx;
+}
+
+// ---------------------------------------------------------------- tables
+static size_t table_bytes(uint64_t cap, uint64_t lcap, uint64_t arena, int bits) {
+    auto r = [](size_t n) { return (n + 255) & ~(size_t)255; };
+    return r(8 * 8) + r(4) + r(cap * 8) * 2 + r(cap * (bits / 8)) + r(cap * 4) + r(lcap * 8) * 2 + r(arena);
+}
+
+wc_status table_create(wc_ctx *ctx, uint64_t cap, uint64_t lcap, uint64_t arena, int bits, cudaStream_t s,
+                       wc_table **out) {
+    wc_table *t = new wc_table();
+    t->ctx = ctx;
+    t->bytes = table_bytes(cap, lcap, arena, bits);
+    wc_status st = ctx->alloc(&t->mem, t->bytes, s);
+    if (st != WC_OK) { delete t; return st; }
+    uint8_t *p = static_cast<uint8_t *>(t->mem);
+    auto take = [&](size_t n) { uint8_t *q = p; p += (n + 255) & ~(size_t)255; return q; };
+    DevTable &d = t->dt;
+    d.cap = cap;
+    d.lcap = lcap;
+    d.arena_cap = arena;
+    d.count_bits = bits;
+    d.d_meta = reinterpret_cast<unsigned long long *>(take(8 * 8));
+    d.d_status = reinterpret_cast<uint32_t *>(take(4));
+    d.khi = reinterpret_cast<unsigned long long *>(take(cap * 8));
+    d.klo = reinterpret_cast<unsigned long long *>(take(cap * 8));
+    d.cnt = take(cap * (bits / 8));
+    d.lref = reinterpret_cast<uint32_t *>(take(cap * 4));
+    d.loff = reinterpret_cast<unsigned long long *>(take(lcap * 8));
+    d.llen = reinterpret_cast<unsigned long long *>(take(lcap * 8));
+    d.arena = take(arena);
+    cudaMemsetAsync(t->mem, 0, 512, s);  // meta + status
+    t->stream = s;
+    cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming);
+    *out = t;
+    return WC_OK;
+}
+
+void table_mark_done(wc_table *t, cudaStream_t s) {
+    t->stream = s;
+    cudaEventRecord(t->done, s);
+}
+
+static wc_status status_from_bits(uint32_t bits) {
+    if (bits & (ST_TABLE_FULL | ST_LONG_FULL | ST_ARENA_FULL | ST_OUT_FULL)) return WC_ERR_CAPACITY;
+    if (bits & ST_TIMEOUT) return WC_ERR_TIMEOUT;
+    if (bits & ST_TOO_LONG) return WC_ERR_UNSUPPORTED;
+    return WC_OK;
+}
+
+wc_status table_sync(const wc_table *ct) {
+    wc_table *t = const_cast<wc_table *>(ct);
+    if (t->synced) return t->sync_status;
+    cudaError_t e = cudaEventSynchronize(t->done);
+    if (e != cudaSuccess) return t->ctx->cuda_fail(e, "cudaEventSynchronize");
+    unsigned long long meta[8];
+    uint32_t status = 0;
+    e = cudaMemcpy(meta, t->dt.d_meta, sizeof(meta), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&status, t->dt.d_status, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return t->ctx->cuda_fail(e, "reading table metadata");
+    t->n = meta[0];
+    t->nlong = meta[1];
+    t->tokens = meta[3];
+    t->word_bytes = meta[4];
+    t->status_bits = status;
+    t->sync_status = status_from_bits(status);
+    if (t->sync_status != WC_OK) {
+        t->n = t->tokens = t->word_bytes = 0;
+        t->ctx->fail(t->sync_status, "device table overflow or wait limit; count again with larger capacities");
+    }
+    t->synced = true;
+    return t->sync_status;
+}
+
+wc_status wc_table_status(const wc_table *t) {
+    if (!t) return WC_ERR_INVALID_ARG;
+    return table_sync(t);
+}
+
+int wc_table_count_bits(const wc_table *t) { return t ? t->dt.count_bits : 0; }
+
+wc_status wc_table_size(const wc_table *t, uint64_t *nwords, uint64_t *ntokens, uint64_t *word_bytes) {
+    if (!t) return WC_ERR_INVALID_ARG;
+    wc_status s = table_sync(t);
+    if (nwords) *nwords = t->n;
+    if (ntokens) *ntokens = t->tokens;
+    if (word_bytes) *word_bytes = t->word_bytes;
+    return s;
+}
+
+wc_status wc_table_export(const wc_table *t, uint8_t *h_words, uint64_t *h_word_offsets, void *h_counts,
+                          cudaStream_t stream) {
+    if (!t) return WC_ERR_INVALID_ARG;
+    wc_ctx *ctx = t->ctx;
+    wc_status s = table_sync(t);
+    if (s != WC_OK) return s;
+    const DevTable &d = t->dt;
+    const uint64_t n = t->n;
+    cudaError_t e = cudaSuccess;
+    if (h_counts && n) {
+        e = cudaMemcpyAsync(h_counts, d.cnt, n * (d.count_bits / 8), cudaMemcpyDeviceToHost, stream);
+        if (e != cudaSuccess) return ctx->cuda_fail(e, "copying counts");
+    }
+    if (h_words || h_word_offsets) {
+        size_t sb = export_scratch_bytes(d.cap);
+        size_t wb = t->word_bytes ? t->word_bytes : 1;
+        void *scratch = nullptr, *dwords = nullptr, *doffs = nullptr;
+        if ((s = ctx->alloc(&scratch, sb, stream)) != WC_OK) return s;
+        if ((s = ctx->alloc(&dwords, wb, stream)) != WC_OK) { ctx->release(scratch, sb, stream); return s; }
+        if ((s = ctx->alloc(&doffs, (d.cap + 1) * 8, stream)) != WC_OK) {
+            ctx->release(scratch, sb, stream);
+            ctx->release(dwords, wb, stream);
+            return s;
+        }
+        e = launch_export(d, scratch, static_cast<uint8_t *>(dwords), static_cast<unsigned long long *>(doffs), stream);
+        if (e == cudaSuccess && h_words && t->word_bytes)
+            e = cudaMemcpyAsync(h_words, dwords, t->word_bytes, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess && h_word_offsets)
+            e = cudaMemcpyAsync(h_word_offsets, doffs, (n + 1) * 8, cudaMemcpyDeviceToHost, stream);
+        ctx->release(scratch, sb, stream);
+        ctx->release(dwords, wb, stream);
+        ctx->release(doffs, (d.cap + 1) * 8, stream);
+        if (e != cudaSuccess) return ctx->cuda_fail(e, "export");
+    }
+    e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaStreamSynchronize (export)");
+    return WC_OK;
+}
+
+void wc_table_free(wc_table *t) {
+    if (!t) return;
+    if (t->owner) return;  // borrowed from a batch
+    cudaSetDevice(t->ctx->device);
+    cudaEventSynchronize(t->done);
+    t->ctx->release(t->mem, t->bytes, t->stream);
+    cudaEventDestroy(t->done);
+    delete t;
+}
+
+// ---------------------------------------------------------------- counting
+static uint64_t pow2_at_least(uint64_t x) {
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// Distinct-word estimate for automatic capacities: a Heaps'-law bound
+// 16 * T^0.6 on the distinct words of T tokens (generous for Zipf text),
+// never above the exact bound ceil(B/2) on tokens.
+void plan_capacity(uint64_t nbytes, const wc_count_opts *o, uint64_t *gcap, uint64_t *glcap, uint64_t *arena) {
+    double tokens = (double)nbytes / 5.0 + 1.0;
+    double est = std::min(tokens, 16.0 * std::pow(tokens, 0.6));
+    uint64_t bound = nbytes / 2 + 1;
+    uint64_t d = std::min<uint64_t>((uint64_t)est + 64, bound);
+    *gcap = pow2_at_least(std::max<uint64_t>(1024, 2 * d));
+    *glcap = pow2_at_least(std::max<uint64_t>(256, 2 * (d / 16 + 16)));
+    *arena = std::max<uint64_t>(4096, std::min<uint64_t>(nbytes + 16, *glcap * 24));
+    if (o) {
+        if (o->table_slots) *gcap = pow2_at_least(std::max<uint64_t>(64, o->table_slots));
+        if (o->long_slots) *glcap = pow2_at_least(std::max<uint64_t>(64, o->long_slots));
+        if (o->arena_bytes) *arena = std::max<uint64_t>(64, o->arena_bytes);
+    }
+}
+
+// Allocates the hash tables + sort scratch for gcap/glcap in one block.
+wc_status scratch_create(wc_ctx *ctx, uint64_t gcap, uint64_t glcap, cudaStream_t s, CountScratch &cs) {
+    cs.gcap = gcap;
+    cs.glcap = glcap;
+    size_t hb = gcap * sizeof(GSlot) + glcap * sizeof(LSlot);
+    cs.bytes = hb + sort_scratch_bytes(gcap + glcap) + 512;
+    wc_status st = ctx->alloc(&cs.mem, cs.bytes, s);
+    if (st != WC_OK) return st;
+    uint8_t *p = static_cast<uint8_t *>(cs.mem);
+    cs.slots = reinterpret_cast<GSlot *>(p);
+    cs.lslots = reinterpret_cast<LSlot *>(p + gcap * sizeof(GSlot));
+    sort_scratch_carve(cs.ss, p + ((hb + 255) & ~(size_t)255), gcap + glcap);
+    cudaMemsetAsync(cs.mem, 0, hb, s);
+    return WC_OK;
+}
+
+wc_status wc_count_ex(wc_ctx *ctx, const uint8_t *d_text, uint64_t nbytes, const wc_count_opts *opts,
+                      cudaStream_t stream, wc_table **out) {
+    if (!ctx || !out) return WC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!d_text && nbytes) return ctx->fail(WC_ERR_INVALID_ARG, "null text");
+    if (nbytes >= (1ull << 40)) return ctx->fail(WC_ERR_UNSUPPORTED, "text of 2^40 bytes or more");
+    if (ctx->count_bits == 32 && nbytes >= (1ull << 33))
+        return ctx->fail(WC_ERR_UNSUPPORTED, "32-bit counts need inputs under 2^33 bytes");
+    cudaSetDevice(ctx->device);
+    uint64_t gcap, glcap, arena;
+    plan_capacity(nbytes, opts, &gcap, &glcap, &arena);
+    CountScratch cs;
+    wc_status st = scratch_create(ctx, gcap, glcap, stream, cs);
+    if (st != WC_OK) return st;
+    wc_table *t = nullptr;
+    st = table_create(ctx, gcap + glcap, glcap, arena, ctx->count_bits, stream, &t);
+    if (st != WC_OK) { ctx->release(cs.mem, cs.bytes, stream); return st; }
+    GTable g{cs.slots, gcap - 1, cs.lslots, glcap - 1, t->dt.d_status};
+    CountLaunch cl{d_text, 0, nbytes, g, 0};
+    ctx->prof_mark(ctx->ev_count, stream);
+    cudaError_t e = launch_count_global(cl, stream);
+    ctx->prof_mark(ctx->ev_count, stream);
+    ctx->launches += nbytes ? 1 : 0;
+    ctx->prof_mark(ctx->ev_finish, stream);
+    if (e == cudaSuccess) e = finish_table(g, gcap, glcap, cs.ss, t->dt, stream);
+    ctx->prof_mark(ctx->ev_finish, stream);
+    ctx->launches += finish_table_launches();
+    ctx->release(cs.mem, cs.bytes, stream);
+    table_mark_done(t, stream);
+    if (e != cudaSuccess) {
+        wc_table_free(t);
+        return ctx->cuda_fail(e, "count launch");
+    }
+    *out = t;
+    return WC_OK;
+}
+
+wc_status wc_count(wc_ctx *ctx, const uint8_t *d_text, uint64_t nbytes, cudaStream_t stream, wc_table **out) {
+    return wc_count_ex(ctx, d_text, nbytes, nullptr, stream, out);
+}
+
+// ---------------------------------------------------------------- merge / top-k
+wc_status wc_merge(wc_ctx *ctx, const wc_table *const *in, uint32_t n, cudaStream_t stream, wc_table **out) {
+    if (!ctx || !out || (n && !in)) return WC_ERR_INVALID_ARG;
+    *out = nullptr;
+    cudaSetDevice(ctx->device);
+    uint64_t sum_cap = 0, sum_lcap = 0, sum_arena = 0, chunks = 0;
+    std::vector<MergeSrc> src(n);
+    std::vector<uint64_t> cstart(n + 1, 0);
+    for (uint32_t i = 0; i < n; i++) {
+        if (!in[i]) return ctx->fail(WC_ERR_INVALID_ARG, "null input table");
+        const DevTable &d = in[i]->dt;
+        src[i] = MergeSrc{d.d_meta, d.khi, d.klo, d.cnt, d.lref, d.loff, d.llen, d.arena, d.count_bits, d.cap};
+        sum_cap += d.cap;
+        sum_lcap += d.lcap;
+        sum_arena += d.arena_cap;
+        cstart[i] = chunks;
+        chunks += (d.cap + kMergeChunk - 1) / kMergeChunk;
+        cudaStreamWaitEvent(stream, in[i]->done, 0);
+    }
+    cstart[n] = chunks;
+    uint64_t gcap = pow2_at_least(std::max<uint64_t>(1024, 2 * sum_cap));
+    uint64_t glcap = pow2_at_least(std::max<uint64_t>(256, 2 * sum_lcap));
+    CountScratch cs;
+    wc_status st = scratch_create(ctx, gcap, glcap, stream, cs);
+    if (st != WC_OK) return st;
+    wc_table *t = nullptr;
+    st = table_create(ctx, gcap + glcap, glcap, std::max<uint64_t>(4096, sum_arena), ctx->count_bits, stream, &t);
+    if (st != WC_OK) { ctx->release(cs.mem, cs.bytes, stream); return st; }
+    void *dsrc = nullptr;
+    size_t sb = sizeof(MergeSrc) * std::max<uint32_t>(n, 1) + 8 * (n + 1);
+    if ((st = ctx->alloc(&dsrc, sb, stream)) != WC_OK) {
+        ctx->release(cs.mem, cs.bytes, stream);
+        wc_table_free(t);
+        return st;
+    }
+    std::vector<uint8_t> host(sb);
+    memcpy(host.data(), src.data(), sizeof(MergeSrc) * n);
+    memcpy(host.data() + sizeof(MergeSrc) * std::max<uint32_t>(n, 1), cstart.data(), 8 * (n + 1));
+    // pageable source: the call returns once the bytes are staged, so `host` may go
+    cudaError_t e = cudaMemcpyAsync(dsrc, host.data(), sb, cudaMemcpyHostToDevice, stream);
+    GTable g{cs.slots, gcap - 1, cs.lslots, glcap - 1, t->dt.d_status};
+    if (e == cudaSuccess)
+        e = launch_merge_insert(static_cast<MergeSrc *>(dsrc),
+                                reinterpret_cast<uint64_t *>(static_cast<uint8_t *>(dsrc) + sizeof(MergeSrc) * std::max<uint32_t>(n, 1)),
+                                n, chunks, g, stream);
+    ctx->launches += chunks ? 1 : 0;
+    ctx->prof_mark(ctx->ev_finish, stream);
+    if (e == cudaSuccess) e = finish_table(g, gcap, glcap, cs.ss, t->dt, stream);
+    ctx->prof_mark(ctx->ev_finish, stream);
+    ctx->launches += finish_table_launches();
+    ctx->release(dsrc, sb, stream);
+    ctx->release(cs.mem, cs.bytes, stream);
+    table_mark_done(t, stream);
+    if (e != cudaSuccess) {
+        wc_table_free(t);
+        return ctx->cuda_fail(e, "merge");
+    }
+    *out = t;
+    return WC_OK;
+}
+
+wc_status wc_topk(wc_ctx *ctx, const wc_table *in, uint32_t k, cudaStream_t stream, wc_table **out) {
+    if (!ctx || !in || !out) return WC_ERR_INVALID_ARG;
+    *out = nullptr;
+    cudaSetDevice(ctx->device);
+    const DevTable &d = in->dt;
+    uint64_t cap = std::max<uint64_t>(1, std::min<uint64_t>(k, d.cap));
+    wc_table *t = nullptr;
+    wc_status st = table_create(ctx, cap, std::max<uint64_t>(1, d.lcap), std::max<uint64_t>(16, d.arena_cap),
+                                d.count_bits, stream, &t);
+    if (st != WC_OK) return st;
+    cudaStreamWaitEvent(stream, in->done, 0);
+    cudaError_t e = launch_topk_copy(d, k, t->dt, stream);
+    ctx->launches += 1;
+    table_mark_done(t, stream);
+    if (e != cudaSuccess) {
+        wc_table_free(t);
+        return ctx->cuda_fail(e, "topk");
+    }
+    *out = t;
+    return WC_OK;
+}

@@ -1,0 +1,277 @@
+// Device primitives shared by the counting, table and sort kernels.
+//
+// Word rule (the paper's normalisation of Sec. 2 / Sec. 3.1 fixed as a byte
+// rule): a word is a maximal run of ASCII letters; letters are lowercased;
+// every other byte and every document edge separates words.
+//
+// Keys: a word of at most 16 letters is keyed by its 16 lowercased bytes,
+// zero padded (4 x u32, little-endian byte order).  Letters are never zero,
+// so the key is unique per word and empty slots are the all-zero key.  Words
+// of 17 or more letters ("long" words) are keyed by (64-bit hash, length) in
+// a separate table whose slots point at one occurrence of the word; an equal
+// (hash, length) pair is always confirmed by comparing the bytes, so a hash
+// collision never merges two words.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace wc {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr int kShortMax = 16;  // letters that fit the in-table key
+
+// status bits written by kernels (OR-ed into one device word)
+enum : uint32_t {
+    ST_TABLE_FULL = 1u,   // short-word table probe limit reached
+    ST_LONG_FULL = 2u,    // long-word table probe limit reached
+    ST_ARENA_FULL = 4u,   // long-word byte arena too small
+    ST_TIMEOUT = 8u,      // a bounded wait gave up
+    ST_TOO_LONG = 16u,    // a word or position beyond the documented limits
+    ST_OUT_FULL = 32u,    // a per-document output region overflowed
+};
+
+// ---------------------------------------------------------------- bytes
+// 0x80 in every byte lane that holds an ASCII letter: fold case with |0x20,
+// then test 0x61 <= y <= 0x7A with two carry-free byte adds; bytes >= 0x80
+// are excluded by the original high bit.
+__device__ __forceinline__ uint32_t letter_bits(uint32_t w) {
+    uint32_t y = (w | 0x20202020u) & 0x7F7F7F7Fu;
+    uint32_t a = y + 0x1F1F1F1Fu;  // bit 7 set iff y >= 0x61
+    uint32_t b = y + 0x05050505u;  // bit 7 set iff y >= 0x7B
+    return a & ~b & ~w & 0x80808080u;
+}
+// Gathers the four lane bits of letter_bits into bits 0..3 (one multiply; the
+// partial products land on distinct bit positions, so nothing carries).
+__device__ __forceinline__ uint32_t letter_mask4(uint32_t w) {
+    return ((letter_bits(w) >> 7) * 0x00204081u) >> 21 & 0xFu;
+}
+__device__ __forceinline__ uint32_t letter_mask16(uint4 v) {
+    return letter_mask4(v.x) | (letter_mask4(v.y) << 4) | (letter_mask4(v.z) << 8) |
+           (letter_mask4(v.w) << 12);
+}
+__device__ __forceinline__ bool is_letter(uint32_t b) {
+    uint32_t y = (b | 0x20u) - 0x61u;
+    return b < 0x80u && y < 26u;
+}
+__device__ __forceinline__ uint32_t lower_byte(uint32_t b) { return b | 0x20u; }
+
+__device__ __forceinline__ uint32_t byte_keep_mask(int r) {  // low r bytes (0..4)
+    return r >= 4 ? 0xFFFFFFFFu : (r <= 0 ? 0u : ((1u << (r * 8)) - 1u));
+}
+
+// 16 lowercased bytes of win[p, p+len), zero padded (len <= 16).  Reads
+// win[p & ~3, (p & ~3) + 20): the window must hold 4 bytes of slack.
+__device__ __forceinline__ uint4 load_key16(const uint8_t *win, uint32_t p, uint32_t len) {
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(win + (p & ~3u));
+    uint32_t sh = (p & 3u) * 8u;
+    uint32_t a0 = w[0], a1 = w[1], a2 = w[2], a3 = w[3], a4 = w[4];
+    uint4 k;
+    int n = (int)len;
+    k.x = (__funnelshift_r(a0, a1, sh) | 0x20202020u) & byte_keep_mask(n);
+    k.y = (__funnelshift_r(a1, a2, sh) | 0x20202020u) & byte_keep_mask(n - 4);
+    k.z = (__funnelshift_r(a2, a3, sh) | 0x20202020u) & byte_keep_mask(n - 8);
+    k.w = (__funnelshift_r(a3, a4, sh) | 0x20202020u) & byte_keep_mask(n - 12);
+    return k;
+}
+
+__device__ __forceinline__ bool key_eq(uint4 a, uint4 b) {
+    return ((a.x ^ b.x) | (a.y ^ b.y) | (a.z ^ b.z) | (a.w ^ b.w)) == 0u;
+}
+__device__ __forceinline__ bool key_zero(uint4 a) { return (a.x | a.y | a.z | a.w) == 0u; }
+
+// 64-bit slot hash of a 16-byte key: MurmurHash3's fmix64 finalizer
+// (Appleby, public domain) over the two halves folded together.  It only picks
+// slots; equality is always decided on the full key.
+__device__ __forceinline__ uint64_t hash_key(uint4 k) {
+    uint64_t lo = ((uint64_t)k.y << 32) | k.x;
+    uint64_t hi = ((uint64_t)k.w << 32) | k.z;
+    uint64_t x = lo ^ (hi * 0x9E3779B97F4A7C15ull);
+    x ^= x >> 33;
+    x *= 0xFF51AFD7ED558CCDull;
+    x ^= x >> 33;
+    x *= 0xC4CEB9FE1A85EC53ull;
+    x ^= x >> 33;
+    return x;
+}
+
+// Byte-wise hash of a lowercased long word (FNV-1a, 64-bit), length mixed in.
+__device__ __forceinline__ uint64_t hash_long_step(uint64_t h, uint32_t b) {
+    return (h ^ (uint64_t)b) * 0x100000001B3ull;
+}
+
+// ---------------------------------------------------------------- atomics
+// 128-bit compare-and-swap (sm_90+): returns the previous value.
+__device__ __forceinline__ uint4 cas128_global(void *addr, uint4 cmp, uint4 val) {
+    uint64_t c0 = ((uint64_t)cmp.y << 32) | cmp.x, c1 = ((uint64_t)cmp.w << 32) | cmp.z;
+    uint64_t v0 = ((uint64_t)val.y << 32) | val.x, v1 = ((uint64_t)val.w << 32) | val.z;
+    uint64_t r0, r1;
+    asm volatile(
+        "{\n\t.reg .b128 c, v, d;\n\t"
+        "mov.b128 c, {%2, %3};\n\t"
+        "mov.b128 v, {%4, %5};\n\t"
+        "atom.relaxed.gpu.global.cas.b128 d, [%6], c, v;\n\t"
+        "mov.b128 {%0, %1}, d;\n\t}"
+        : "=l"(r0), "=l"(r1)
+        : "l"(c0), "l"(c1), "l"(v0), "l"(v1), "l"(addr)
+        : "memory");
+    uint4 r;
+    r.x = (uint32_t)r0; r.y = (uint32_t)(r0 >> 32);
+    r.z = (uint32_t)r1; r.w = (uint32_t)(r1 >> 32);
+    return r;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_shared(const uint32_t *p) {
+    uint32_t v;
+    uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_shared(uint32_t *p, uint32_t v) {
+    uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint4 ld_stream16(const void *p) {  // read-once text
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+// ---------------------------------------------------------------- tables
+// Global short-word slot: one 32-byte sector (key, count, spare).
+struct __align__(32) GSlot {
+    uint4 key;
+    unsigned long long cnt;
+    unsigned long long spare;
+};
+// Global long-word slot: (hash, length) is the CAS target; pos1 = device
+// address of one occurrence of the word, plus one (0 = not yet set).
+struct __align__(32) LSlot {
+    unsigned long long h;
+    unsigned long long len;
+    unsigned long long pos1;
+    unsigned long long cnt;
+};
+
+struct GTable {
+    GSlot *slots;
+    unsigned long long mask;     // capacity - 1 (power of two)
+    LSlot *lslots;
+    unsigned long long lmask;
+    uint32_t *status;
+};
+
+constexpr int kGlobalProbeLimit = 4096;
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+// Adds `add` to word `k` (<= 16 letters) in the global table.
+__device__ __forceinline__ void global_insert(const GTable &g, uint4 k, uint64_t h, unsigned long long add) {
+    unsigned long long s = h & g.mask;
+    const uint4 zero = make_uint4(0, 0, 0, 0);
+    for (int probe = 0; probe < kGlobalProbeLimit; probe++) {
+        GSlot *slot = g.slots + s;
+        uint4 old = cas128_global(&slot->key, zero, k);
+        if (key_zero(old) || key_eq(old, k)) {
+            atomicAdd(&slot->cnt, add);
+            return;
+        }
+        s = (s + 1) & g.mask;
+    }
+    atomicOr(g.status, ST_TABLE_FULL);
+}
+
+// Lowercased byte comparison of two runs of `len` letters.
+__device__ __forceinline__ bool bytes_eq_lower(const uint8_t *a, const uint8_t *b, uint64_t len) {
+    for (uint64_t i = 0; i < len; i++)
+        if ((a[i] | 0x20u) != (b[i] | 0x20u)) return false;
+    return true;
+}
+
+// Adds `add` to the long word w[0, len) (a maximal letter run of len >= 17,
+// in any device buffer that stays alive until the table is compacted).
+__device__ inline void long_insert(const GTable &g, const uint8_t *w, uint64_t len, unsigned long long add) {
+    uint64_t h = 0xCBF29CE484222325ull;
+    for (uint64_t i = 0; i < len; i++) h = hash_long_step(h, w[i] | 0x20u);
+    h ^= len * 0x9E3779B97F4A7C15ull;
+    unsigned long long s = h & g.lmask;
+    uint4 want = make_uint4((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)len, (uint32_t)(len >> 32));
+    const uint4 zero = make_uint4(0, 0, 0, 0);
+    for (int probe = 0; probe < kGlobalProbeLimit; probe++) {
+        LSlot *slot = g.lslots + s;
+        uint4 old = cas128_global(&slot->h, zero, want);
+        if (key_zero(old)) {
+            atomicExch(&slot->pos1, (unsigned long long)reinterpret_cast<uintptr_t>(w) + 1ull);
+            atomicAdd(&slot->cnt, add);
+            return;
+        }
+        if (key_eq(old, want)) {
+            unsigned long long p1 = 0;
+            for (uint32_t spin = 0; spin < kSpinLimit; spin++) {
+                p1 = ld_relaxed_u64(&slot->pos1);
+                if (p1) break;
+            }
+            if (!p1) { atomicOr(g.status, ST_TIMEOUT); return; }
+            if (bytes_eq_lower(reinterpret_cast<const uint8_t *>(p1 - 1ull), w, len)) {
+                atomicAdd(&slot->cnt, add);
+                return;
+            }
+        }
+        s = (s + 1) & g.lmask;
+    }
+    atomicOr(g.status, ST_LONG_FULL);
+}
+
+// ---------------------------------------------------------------- shared table
+// Per-block level-1 table: tag[i] (0 empty, 1 being written, else hash tag
+// with bit 1 set), key[i], cnt[i].  A slot's key and count are written before
+// its tag is published with release order, and read after an acquire load of
+// the tag.  A slot that is being written is skipped, which can only place a
+// second copy of a word in the table: harmless, since every copy is flushed
+// exactly into the global table.
+struct STable {
+    uint32_t *tag;
+    uint4 *key;
+    uint32_t *cnt;
+    uint32_t *nfill;
+    uint32_t mask;
+    uint32_t fill_limit;
+};
+
+__device__ __forceinline__ uint32_t stag_of(uint64_t h) { return ((uint32_t)h & ~1u) | 2u; }
+
+// Returns false when the word must spill to the global table.
+__device__ __forceinline__ bool shared_insert(const STable &t, uint4 k, uint64_t h, uint32_t add, int max_probe) {
+    uint32_t s = (uint32_t)(h >> 40) & t.mask;
+    uint32_t want = stag_of(h);
+    for (int probe = 0; probe < max_probe; probe++) {
+        uint32_t tg = ld_acquire_shared(t.tag + s);
+        if (tg == want) {
+            if (key_eq(t.key[s], k)) { atomicAdd(t.cnt + s, add); return true; }
+        } else if (tg == 0u) {
+            if (*(volatile uint32_t *)t.nfill >= t.fill_limit) return false;
+            uint32_t old = atomicCAS(t.tag + s, 0u, 1u);
+            if (old == 0u) {
+                t.key[s] = k;
+                t.cnt[s] = add;
+                st_release_shared(t.tag + s, want);
+                atomicAdd(t.nfill, 1u);
+                return true;
+            }
+            if (old == want) {
+                __threadfence_block();
+                if (key_eq(t.key[s], k)) { atomicAdd(t.cnt + s, add); return true; }
+            }
+        }
+        s = (s + 1) & t.mask;
+    }
+    return false;
+}
+
+}  // namespace wc

@@ -1,0 +1,65 @@
+// Host-side object layouts behind the opaque C-ABI handles.
+#pragma once
+#include <atomic>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/wc.h"
+#include "wc_internal.h"
+
+struct wc_ctx {
+    int device = 0;
+    int sms = 1;
+    uint64_t budget = 0;
+    std::atomic<uint64_t> used{0};
+    int count_bits = 64;
+    int autotune = 0;
+    std::string tune_cache_path;
+    cudaMemPool_t pool = nullptr;
+    std::string last_error;
+    // stage tracing
+    bool profile = false;
+    std::vector<cudaEvent_t> ev_count, ev_finish;  // (start, stop) pairs
+    uint64_t launches = 0;
+    void prof_mark(std::vector<cudaEvent_t> &v, cudaStream_t s);
+
+    wc_status fail(wc_status s, const char *what);
+    wc_status cuda_fail(cudaError_t e, const char *what);
+    wc_status alloc(void **p, size_t bytes, cudaStream_t s);
+    void release(void *p, size_t bytes, cudaStream_t s);
+};
+
+struct wc_table {
+    wc_ctx *ctx = nullptr;
+    const void *owner = nullptr;   // non-null: a view owned by a batch
+    void *mem = nullptr;
+    size_t bytes = 0;
+    wc::DevTable dt{};
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    // filled by table_sync
+    bool synced = false;
+    wc_status sync_status = WC_OK;
+    uint64_t n = 0, nlong = 0, tokens = 0, word_bytes = 0;
+    uint32_t status_bits = 0;
+};
+
+// Hash tables and sort scratch of one count or merge.
+struct CountScratch {
+    void *mem = nullptr;
+    size_t bytes = 0;
+    uint64_t gcap = 0, glcap = 0;
+    wc::GSlot *slots = nullptr;
+    wc::LSlot *lslots = nullptr;
+    wc::SortScratch ss{};
+};
+
+wc_status table_create(wc_ctx *ctx, uint64_t cap, uint64_t lcap, uint64_t arena, int bits, cudaStream_t s,
+                       wc_table **out);
+void table_mark_done(wc_table *t, cudaStream_t s);
+wc_status table_sync(const wc_table *t);
+void plan_capacity(uint64_t nbytes, const wc_count_opts *o, uint64_t *gcap, uint64_t *glcap, uint64_t *arena);
+wc_status scratch_create(wc_ctx *ctx, uint64_t gcap, uint64_t glcap, cudaStream_t s, CountScratch &cs);

