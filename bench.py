@@ -286,15 +286,170 @@ def run_gpu(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def _dev_docs(c, local):
+    import torch
+    dev = torch.device("cuda", local)
+    host = torch.from_numpy(c.text).pin_memory()
+    text = host.to(dev)
+    offs = torch.from_numpy(c.offsets.view(np.int64)).to(dev)
+    cls = torch.from_numpy(c.classes.view(np.int32)).to(dev) if c.nclasses > 1 else None
+    return host, text, offs, cls
+
+
+def run_docs_workload(args, local):
+    """Batched per-document counting through a replayed plan: 'tiny' (200
+    documents: per-document + global tables), 'classes' (4 x 250 documents:
+    per-document, per-class and global tables + top-50 class-ratio words) or
+    'batched' (100,000 log-normal documents: per-document tables)."""
+    import torch
+    import corpus
+    from paper_2206_05269_gb300 import wc
+    torch.cuda.set_device(local)
+    c = corpus.generate(args.workload)
+    host, text, offs, cls = _dev_docs(c, local)
+    stream = torch.cuda.current_stream()
+    tune = os.path.join(ROOT, "paper_2206_05269_gb300", "_build", "tune_cache.json")
+    ctr = wc.Counter(local, count_bits=32, autotune=True, tune_cache_path=tune)
+    plan = ctr.plan(c.offsets, c.nclasses if c.nclasses > 1 else 0, stream)
+    tables = args.workload in ("tiny", "classes")
+
+    def step():
+        b = plan.run(text, offs, cls, stream)
+        if tables:  # class and global tables (built on the device), ratio ranking
+            g = b.table(wc.WC_TABLE_GLOBAL)
+            for k in range(c.nclasses if c.nclasses > 1 else 0):
+                b.table(wc.WC_TABLE_CLASS, k)
+                wc.wc_class_ratio_topk(ctr.ctx, b.handle, k, 50, int(stream.cuda_stream))
+            g.size()
+        return b
+
+    for _ in range(args.warmup):
+        b = step()
+        if b.status() != wc.WC_OK:
+            raise RuntimeError(wc.wc_last_error(ctr.ctx))
+    nent, _ = wc.wc_batch_size(b.handle)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    wc.wc_profile_enable(ctr.ctx, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        b = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = wc.wc_profile_read(ctr.ctx)[3]
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if tables:
+        ms = max(ms, wall * 1e3 / args.steps)  # host waits inside the step count too
+    docs_s = c.ndocs / (ms * 1e-3)
+    # one wc_count launch per document, on a sample of the same documents
+    nsamp = min(c.ndocs, 2000)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    outs = []
+    for d in range(nsamp):
+        outs.append(ctr.count(text[int(c.offsets[d]):int(c.offsets[d + 1])], stream))
+        if len(outs) > 64:
+            outs.pop(0).status()
+    for t in outs:
+        t.status()
+    per_launch = nsamp / (time.perf_counter() - t1)
+    # end to end: host text -> device, batched count, every table -> host
+    dev2 = torch.empty_like(text)
+    te = []
+    for i in range(4):
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        dev2.copy_(host, non_blocking=True)
+        bb = ctr.count_batched(dev2, offs, c.offsets, cls, c.nclasses if c.nclasses > 1 else 0, stream)
+        ds, dn, w, o, cc = bb.export(stream)
+        te.append(time.perf_counter() - t2)
+        d2h = ds.nbytes + dn.nbytes + w.nbytes + o.nbytes + cc.nbytes
+        del bb
+    e2e = c.ndocs / statistics.mean(te[1:])
+    peak, peak_kind = measured_peaks()
+    alg = c.nbytes + nent * 24
+    line = {
+        "metric": f"{args.workload}: documents/s (per-document tables)", "value": docs_s, "unit": "docs/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": args.workload, "docs": c.ndocs, "bytes": c.nbytes, "words": c.tokens,
+                   "entries": nent,
+                   "autotuned_shapes": json.load(open(tune)) if os.path.exists(tune) else None},
+        "input_GBps": c.nbytes / (ms * 1e-3) / 1e9,
+        "per_launch_docs_s": per_launch, "speedup_vs_per_launch": docs_s / per_launch,
+        "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": alg / (ms * 1e-3) / 1e9 / peak, "traffic": None, "kernel": "whole batched step",
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg},
+        "e2e": {"value": e2e, "unit": "docs/s", "h2d_bytes_per_step": c.nbytes, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    del plan
+    ctr.close()
+
+
+def run_served_workload(args, local):
+    """Served counting: a Poisson stream of requests (2,000/s for
+    --serve-seconds, sizes log-uniform 1 KB - 64 MB) through the
+    continuous-batching loop, then the first --fifo-seconds of the same
+    stream through the plain one-launch-per-request path."""
+    import torch
+    import corpus
+    from paper_2206_05269_gb300 import serve, wc
+    torch.cuda.set_device(local)
+    pool = corpus.generate("served_pool", size_a=args.pool_bytes).text
+    host = torch.from_numpy(pool).pin_memory()
+    trip = corpus.poisson_requests(pool, 2000.0, args.serve_seconds, 1 << 10, 64 << 20, 0x5EED0105)
+    reqs = [serve.Request(i, a, host[s:e]) for i, (a, s, e) in enumerate(trip)]
+    ctr = wc.Counter(local, count_bits=32, budget=40 << 30)
+    # warm-up on a few requests
+    serve.serve_batched(ctr, [serve.Request(i, 0.0, r.data) for i, r in enumerate(reqs[:16])])
+    sampler = ClockSampler(local)
+    sampler.start()
+    ans, st = serve.serve_batched(ctr, reqs, topk=100, max_rounds=4)
+    clocks = sampler.stop()
+    lat = np.array([a.latency for a in ans]) * 1e3
+    nbytes = sum(r.data.numel() for r in reqs)
+    fifo_reqs = [r for r in reqs if r.arrival < args.fifo_seconds]
+    fans, fst = serve.serve_fifo(ctr, fifo_reqs, topk=100)
+    flat = np.array([a.latency for a in fans]) * 1e3
+    bl = np.array([a.latency for a in ans[:len(fans)]]) * 1e3
+    line = {
+        "metric": "served: p99 latency ms (Poisson 2,000 req/s, 1 KB - 64 MB)", "value": float(np.percentile(lat, 99)),
+        "unit": "ms", "n_gpus": 1, "steps": len(reqs), "warmup": 16, "ms_per_step": st["wall_s"] * 1e3 / len(reqs),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "served", "requests": len(reqs), "seconds": args.serve_seconds,
+                   "bytes": nbytes, "rounds": st["rounds"], "budget_GB": 40},
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "req_per_s": len(reqs) / st["wall_s"], "GBps": nbytes / st["wall_s"] / 1e9,
+        "fifo": {"requests": len(fans), "p50_ms": float(np.percentile(flat, 50)) if len(fans) else None,
+                 "p99_ms": float(np.percentile(flat, 99)) if len(fans) else None,
+                 "req_per_s": len(fans) / fst["wall_s"] if len(fans) else None,
+                 "batched_same_requests_p99_ms": float(np.percentile(bl, 99)) if len(fans) else None},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    ctr.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="large", choices=["large", "tiny", "classes", "batched", "served"])
     ap.add_argument("--cpu-sample-mb", type=float, default=150.0)
     ap.add_argument("--bytes", type=float, default=1e9, help="corpus size (smaller only for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--fifo-seconds", type=float, default=2.0)
+    ap.add_argument("--pool-bytes", type=float, default=2e9)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local = dist_env()
@@ -304,7 +459,12 @@ def main():
     import __graft_entry__
     if rank == 0 or world == 1:
         __graft_entry__.build()
-    run_gpu(args, rank, world, local)
+    if args.workload == "large":
+        run_gpu(args, rank, world, local)
+    elif args.workload == "served":
+        run_served_workload(args, local)
+    else:
+        run_docs_workload(args, local)
 
 
 if __name__ == "__main__":

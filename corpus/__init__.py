@@ -242,6 +242,23 @@ def expected_word_len(recipe: Recipe | str, **overrides) -> float:
         lib.gen_destroy(h)
 
 
+def poisson_requests(pool: np.ndarray, rate: float, duration: float, lo: int, hi: int, seed: int):
+    """Serving request stream: Poisson arrivals at `rate` per second for
+    `duration` seconds; sizes log-uniform in [lo, hi] bytes, cut out of the
+    pooled corpus at generator-written spaces.  Returns (arrival s, start, end)."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            break
+        size = int(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+        start = int(rng.integers(0, max(1, pool.size - size)))
+        s, e = slice_at_separators(pool, start, size)
+        out.append((t, s, e))
+    return out
+
+
 def slice_at_separators(text: np.ndarray, start: int, length: int) -> tuple[int, int]:
     """Widens [start, start+length) to the nearest generator-written space or
     newline on each side, so no word is cut.  Used to cut serving requests out

@@ -101,8 +101,46 @@ wc_status wc_count_batched(wc_ctx *ctx, const uint8_t *d_text, const uint64_t *d
                            const uint64_t *h_offsets, uint32_t ndocs, const uint32_t *d_class,
                            uint32_t nclasses, cudaStream_t stream, wc_batch **out);
 
-/* Borrows one table of a batch (owned by the batch). */
+/* Waits for the batch; device-side overflow of its tables or output is
+ * reported as WC_ERR_CAPACITY (count again; nothing partial is kept). */
+wc_status wc_batch_status(const wc_batch *batch);
+
+/* Borrows one table of a batch (owned by the batch, freed with it; calling
+ * wc_table_free on it does nothing).  kind = WC_TABLE_DOC (idx < ndocs, 32-bit
+ * counts), WC_TABLE_CLASS (idx < nclasses, 32-bit counts) or
+ * WC_TABLE_GLOBAL (ctx count width).  Waits for the batch; class and global
+ * tables are built on the first request (Sec. 3.3's sum across documents). */
 wc_status wc_batch_table(const wc_batch *batch, int kind, uint32_t idx, const wc_table **out);
+
+/* Waits for the batch; total per-document entries and their word bytes. */
+wc_status wc_batch_size(const wc_batch *batch, uint64_t *nentries, uint64_t *word_bytes);
+
+/* Copies every per-document table at once.  Entries are stored per document
+ * (each document's entries are contiguous and in (count desc, word asc)
+ * order); document i owns entries [h_doc_start[i], h_doc_start[i] +
+ * h_doc_n[i]).  h_words / h_word_offsets (nentries+1) / h_counts (nentries)
+ * are laid out as in wc_table_export over all entries.  Any pointer may be
+ * NULL.  Waits until the copies are complete. */
+wc_status wc_batch_export(const wc_batch *batch, uint64_t *h_doc_start, uint32_t *h_doc_n, uint8_t *h_words,
+                          uint64_t *h_word_offsets, uint32_t *h_counts, cudaStream_t stream);
+
+/* Plans: resident state for counting the same layout of documents again and
+ * again (serving, repeated batches).  wc_plan_create plans ndocs documents
+ * with the given host offsets (size classes, work items, capacities) and
+ * allocates the output and scratch once.  wc_plan_run counts text laid out
+ * with those offsets: the first run (after autotuning when the context
+ * asks for it: every per-document kernel shape of each size class is timed
+ * on this input and the fastest kept, cached per GPU in tune_cache_path)
+ * captures all device work into a CUDA graph; later runs with the same
+ * pointers and stream replay it.  *out belongs to the plan and is rewritten
+ * by the next run; wait for it (wc_batch_status) before reading it.  Run
+ * the first call outside any stream capture. */
+typedef struct wc_plan wc_plan;
+wc_status wc_plan_create(wc_ctx *ctx, const uint64_t *h_offsets, uint32_t ndocs, uint32_t nclasses,
+                         cudaStream_t stream, wc_plan **out);
+wc_status wc_plan_run(wc_plan *plan, const uint8_t *d_text, const uint64_t *d_offsets, const uint32_t *d_class,
+                      cudaStream_t stream, const wc_batch **out);
+void wc_plan_free(wc_plan *plan);
 
 /* Top-k of class `cls` by the ratio of in-class to out-of-class count
  * (Sec. 4.3's search for words one class uses more than the others, made

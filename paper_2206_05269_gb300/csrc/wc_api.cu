@@ -115,6 +115,40 @@ wc_status wc_profile_read(wc_ctx *ctx, double *ms_count, double *ms_finish, uint
     return WC_OK;
 }
 
+// Autotuner cache: a JSON object keyed by GPU name, e.g.
+//   {"NVIDIA GB300": {"small": 1, "medium": 4}}
+// (shape indices of the per-document kernel per size class).
+void wc_ctx::tune_load() {
+    if (tune_cache_path.empty()) return;
+    FILE *f = fopen(tune_cache_path.c_str(), "rb");
+    if (!f) return;
+    std::string txt;
+    char buf[4096];
+    size_t n;
+    while ((n = fread(buf, 1, sizeof(buf), f)) > 0) txt.append(buf, n);
+    fclose(f);
+    size_t k = txt.find("\"" + gpu_name + "\"");
+    if (k == std::string::npos) return;
+    auto num = [&](const char *field, int *dst) {
+        size_t q = txt.find(std::string("\"") + field + "\"", k);
+        if (q == std::string::npos) return;
+        q = txt.find(':', q);
+        if (q == std::string::npos) return;
+        int v = atoi(txt.c_str() + q + 1);
+        if (v >= 0 && v < 5) *dst = v;
+    };
+    num("small", &tuned_small);
+    num("medium", &tuned_medium);
+}
+
+void wc_ctx::tune_save() const {
+    if (tune_cache_path.empty()) return;
+    FILE *f = fopen(tune_cache_path.c_str(), "wb");
+    if (!f) return;
+    fprintf(f, "{\"%s\": {\"small\": %d, \"medium\": %d}}\n", gpu_name.c_str(), tuned_small, tuned_medium);
+    fclose(f);
+}
+
 wc_status wc_create(const wc_config *cfg, wc_ctx **out) {
     if (!out) return WC_ERR_INVALID_ARG;
     *out = nullptr;
@@ -146,6 +180,9 @@ wc_status wc_create(const wc_config *cfg, wc_ctx **out) {
     uint64_t keep = UINT64_MAX;  // keep freed memory cached in the pool
     cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, c.device);
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, c.device) == cudaSuccess) ctx->gpu_name = prop.name;
+    ctx->tune_load();
     *out = ctx;
     return WC_OK;
 }
@@ -227,6 +264,14 @@ wc_status table_sync(const wc_table *ct) {
         t->n = t->tokens = t->word_bytes = 0;
         t->ctx->fail(t->sync_status, "device table overflow or wait limit; count again with larger capacities");
     }
+    if (t->sync_status == WC_OK && t->src_bytes) {
+        wc_ctx *c = t->ctx;
+        c->hist_bytes = t->src_bytes;
+        c->hist_n8 = meta[5];
+        c->hist_n16 = meta[6] - meta[5];
+        c->hist_nlong = meta[1];
+        c->hist_arena = meta[2];
+    }
     t->synced = true;
     return t->sync_status;
 }
@@ -303,36 +348,59 @@ static uint64_t pow2_at_least(uint64_t x) {
     return p;
 }
 
-// Distinct-word estimate for automatic capacities: a Heaps'-law bound
-// 16 * T^0.6 on the distinct words of T tokens (generous for Zipf text),
-// never above the exact bound ceil(B/2) on tokens.
-void plan_capacity(uint64_t nbytes, const wc_count_opts *o, uint64_t *gcap, uint64_t *glcap, uint64_t *arena) {
+// Automatic capacities.  Distinct words of a text of B bytes are estimated
+// with a Heaps'-law bound 16 * T^0.6 on T = B/5 tokens (generous for Zipf
+// text) and never above the exact bound ceil(B/2).  When the context has
+// counted a text of similar size before, the distinct counts it saw (per key
+// width) are used instead, scaled by size.  Overflow is reported, never
+// silent: callers count again with larger capacities.
+CapPlan plan_capacity(const wc_ctx *ctx, uint64_t nbytes, const wc_count_opts *o) {
     double tokens = (double)nbytes / 5.0 + 1.0;
     double est = std::min(tokens, 16.0 * std::pow(tokens, 0.6));
     uint64_t bound = nbytes / 2 + 1;
     uint64_t d = std::min<uint64_t>((uint64_t)est + 64, bound);
-    *gcap = pow2_at_least(std::max<uint64_t>(1024, 2 * d));
-    *glcap = pow2_at_least(std::max<uint64_t>(256, 2 * (d / 16 + 16)));
-    *arena = std::max<uint64_t>(4096, std::min<uint64_t>(nbytes + 16, *glcap * 24));
-    if (o) {
-        if (o->table_slots) *gcap = pow2_at_least(std::max<uint64_t>(64, o->table_slots));
-        if (o->long_slots) *glcap = pow2_at_least(std::max<uint64_t>(64, o->long_slots));
-        if (o->arena_bytes) *arena = std::max<uint64_t>(64, o->arena_bytes);
+    CapPlan p;
+    p.cap8 = pow2_at_least(std::max<uint64_t>(1024, d + d / 5));
+    p.cap16 = pow2_at_least(std::max<uint64_t>(1024, d * 3 / 5));
+    p.caplong = pow2_at_least(std::max<uint64_t>(256, 2 * (d / 16 + 16)));
+    p.arena = std::max<uint64_t>(4096, std::min<uint64_t>(nbytes + nbytes / 16 + 16, p.caplong * 24));
+    if (ctx && ctx->hist_bytes && nbytes <= 2 * ctx->hist_bytes && 2 * nbytes >= ctx->hist_bytes) {
+        double r = (double)nbytes / (double)ctx->hist_bytes;
+        auto scaled = [&](uint64_t n) { return (uint64_t)((double)n * std::max(1.0, r)) + 64; };
+        p.cap8 = pow2_at_least(std::max<uint64_t>(1024, 2 * scaled(ctx->hist_n8)));
+        p.cap16 = pow2_at_least(std::max<uint64_t>(1024, 2 * scaled(ctx->hist_n16)));
+        p.caplong = pow2_at_least(std::max<uint64_t>(256, 2 * scaled(ctx->hist_nlong)));
+        p.arena = std::max<uint64_t>(4096, 2 * scaled(ctx->hist_arena));
     }
+    if (o) {
+        if (o->table_slots) {
+            p.cap8 = pow2_at_least(std::max<uint64_t>(64, o->table_slots));
+            p.cap16 = pow2_at_least(std::max<uint64_t>(64, o->table_slots));
+        }
+        if (o->long_slots) p.caplong = pow2_at_least(std::max<uint64_t>(64, o->long_slots));
+        if (o->arena_bytes) p.arena = std::max<uint64_t>(64, o->arena_bytes);
+    }
+    return p;
 }
 
-// Allocates the hash tables + sort scratch for gcap/glcap in one block.
-wc_status scratch_create(wc_ctx *ctx, uint64_t gcap, uint64_t glcap, cudaStream_t s, CountScratch &cs) {
-    cs.gcap = gcap;
-    cs.glcap = glcap;
-    size_t hb = gcap * sizeof(GSlot) + glcap * sizeof(LSlot);
-    cs.bytes = hb + sort_scratch_bytes(gcap + glcap) + 512;
+// Allocates the hash tables (+ head-selection scratch) + sort scratch in one block.
+wc_status scratch_create(wc_ctx *ctx, const CapPlan &p, bool head, cudaStream_t s, CountScratch &cs) {
+    cs.gcap8 = p.cap8;
+    cs.gcap = p.cap16;
+    cs.glcap = p.caplong;
+    auto r = [](size_t n) { return (n + 255) & ~(size_t)255; };
+    const size_t b8 = r(p.cap8 * sizeof(G8Slot)), b16 = r(p.cap16 * sizeof(GSlot)), bl = r(p.caplong * sizeof(LSlot));
+    const size_t hb = b8 + b16 + bl;
+    const size_t bh = head ? r(head_scratch_bytes()) : 0;
+    cs.bytes = hb + bh + sort_scratch_bytes(cs.entries()) + 512;
     wc_status st = ctx->alloc(&cs.mem, cs.bytes, s);
     if (st != WC_OK) return st;
-    uint8_t *p = static_cast<uint8_t *>(cs.mem);
-    cs.slots = reinterpret_cast<GSlot *>(p);
-    cs.lslots = reinterpret_cast<LSlot *>(p + gcap * sizeof(GSlot));
-    sort_scratch_carve(cs.ss, p + ((hb + 255) & ~(size_t)255), gcap + glcap);
+    uint8_t *q = static_cast<uint8_t *>(cs.mem);
+    cs.slots8 = reinterpret_cast<G8Slot *>(q);
+    cs.slots = reinterpret_cast<GSlot *>(q + b8);
+    cs.lslots = reinterpret_cast<LSlot *>(q + b8 + b16);
+    cs.head = head ? q + hb : nullptr;
+    sort_scratch_carve(cs.ss, q + hb + bh, cs.entries());
     cudaMemsetAsync(cs.mem, 0, hb, s);
     return WC_OK;
 }
@@ -346,22 +414,22 @@ wc_status wc_count_ex(wc_ctx *ctx, const uint8_t *d_text, uint64_t nbytes, const
     if (ctx->count_bits == 32 && nbytes >= (1ull << 33))
         return ctx->fail(WC_ERR_UNSUPPORTED, "32-bit counts need inputs under 2^33 bytes");
     cudaSetDevice(ctx->device);
-    uint64_t gcap, glcap, arena;
-    plan_capacity(nbytes, opts, &gcap, &glcap, &arena);
+    const CapPlan plan = plan_capacity(ctx, nbytes, opts);
     CountScratch cs;
-    wc_status st = scratch_create(ctx, gcap, glcap, stream, cs);
+    wc_status st = scratch_create(ctx, plan, true, stream, cs);
     if (st != WC_OK) return st;
     wc_table *t = nullptr;
-    st = table_create(ctx, gcap + glcap, glcap, arena, ctx->count_bits, stream, &t);
+    st = table_create(ctx, cs.entries(), plan.caplong, plan.arena, ctx->count_bits, stream, &t);
     if (st != WC_OK) { ctx->release(cs.mem, cs.bytes, stream); return st; }
-    GTable g{cs.slots, gcap - 1, cs.lslots, glcap - 1, t->dt.d_status};
-    CountLaunch cl{d_text, 0, nbytes, g, 0};
+    t->src_bytes = nbytes;
+    const GTable g = cs.gtable(t->dt.d_status);
+    CountLaunch cl{d_text, 0, nbytes, g, 0, cs.head};
     ctx->prof_mark(ctx->ev_count, stream);
     cudaError_t e = launch_count_global(cl, stream);
     ctx->prof_mark(ctx->ev_count, stream);
-    ctx->launches += nbytes ? 1 : 0;
+    ctx->launches += count_global_launches(nbytes, true);
     ctx->prof_mark(ctx->ev_finish, stream);
-    if (e == cudaSuccess) e = finish_table(g, gcap, glcap, cs.ss, t->dt, stream);
+    if (e == cudaSuccess) e = finish_table(g, cs.gcap8, cs.gcap, cs.glcap, cs.ss, t->dt, stream);
     ctx->prof_mark(ctx->ev_finish, stream);
     ctx->launches += finish_table_launches();
     ctx->release(cs.mem, cs.bytes, stream);
@@ -389,7 +457,8 @@ wc_status wc_merge(wc_ctx *ctx, const wc_table *const *in, uint32_t n, cudaStrea
     for (uint32_t i = 0; i < n; i++) {
         if (!in[i]) return ctx->fail(WC_ERR_INVALID_ARG, "null input table");
         const DevTable &d = in[i]->dt;
-        src[i] = MergeSrc{d.d_meta, d.khi, d.klo, d.cnt, d.lref, d.loff, d.llen, d.arena, d.count_bits, d.cap};
+        src[i] = MergeSrc{d.d_meta, d.khi, d.klo, d.cnt, d.lref, d.loff, d.llen, d.arena, d.count_bits, d.cap,
+                          d.arena_cap};
         sum_cap += d.cap;
         sum_lcap += d.lcap;
         sum_arena += d.arena_cap;
@@ -398,13 +467,16 @@ wc_status wc_merge(wc_ctx *ctx, const wc_table *const *in, uint32_t n, cudaStrea
         cudaStreamWaitEvent(stream, in[i]->done, 0);
     }
     cstart[n] = chunks;
-    uint64_t gcap = pow2_at_least(std::max<uint64_t>(1024, 2 * sum_cap));
-    uint64_t glcap = pow2_at_least(std::max<uint64_t>(256, 2 * sum_lcap));
+    CapPlan plan;
+    plan.cap8 = pow2_at_least(std::max<uint64_t>(1024, 2 * sum_cap));
+    plan.cap16 = plan.cap8;
+    plan.caplong = pow2_at_least(std::max<uint64_t>(256, 2 * sum_lcap));
+    plan.arena = std::max<uint64_t>(4096, sum_arena);
     CountScratch cs;
-    wc_status st = scratch_create(ctx, gcap, glcap, stream, cs);
+    wc_status st = scratch_create(ctx, plan, false, stream, cs);
     if (st != WC_OK) return st;
     wc_table *t = nullptr;
-    st = table_create(ctx, gcap + glcap, glcap, std::max<uint64_t>(4096, sum_arena), ctx->count_bits, stream, &t);
+    st = table_create(ctx, cs.entries(), plan.caplong, plan.arena, ctx->count_bits, stream, &t);
     if (st != WC_OK) { ctx->release(cs.mem, cs.bytes, stream); return st; }
     void *dsrc = nullptr;
     size_t sb = sizeof(MergeSrc) * std::max<uint32_t>(n, 1) + 8 * (n + 1);
@@ -418,14 +490,14 @@ wc_status wc_merge(wc_ctx *ctx, const wc_table *const *in, uint32_t n, cudaStrea
     memcpy(host.data() + sizeof(MergeSrc) * std::max<uint32_t>(n, 1), cstart.data(), 8 * (n + 1));
     // pageable source: the call returns once the bytes are staged, so `host` may go
     cudaError_t e = cudaMemcpyAsync(dsrc, host.data(), sb, cudaMemcpyHostToDevice, stream);
-    GTable g{cs.slots, gcap - 1, cs.lslots, glcap - 1, t->dt.d_status};
+    const GTable g = cs.gtable(t->dt.d_status);
     if (e == cudaSuccess)
         e = launch_merge_insert(static_cast<MergeSrc *>(dsrc),
                                 reinterpret_cast<uint64_t *>(static_cast<uint8_t *>(dsrc) + sizeof(MergeSrc) * std::max<uint32_t>(n, 1)),
                                 n, chunks, g, stream);
     ctx->launches += chunks ? 1 : 0;
     ctx->prof_mark(ctx->ev_finish, stream);
-    if (e == cudaSuccess) e = finish_table(g, gcap, glcap, cs.ss, t->dt, stream);
+    if (e == cudaSuccess) e = finish_table(g, cs.gcap8, cs.gcap, cs.glcap, cs.ss, t->dt, stream);
     ctx->prof_mark(ctx->ev_finish, stream);
     ctx->launches += finish_table_launches();
     ctx->release(dsrc, sb, stream);

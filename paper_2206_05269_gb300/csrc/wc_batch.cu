@@ -1,0 +1,609 @@
+// Batched counting: many documents of uneven size in one pass.
+//
+// Sec. 3.1 of the paper builds one dictionary per document and Sec. 3.3 sums
+// them; here every document's table is built on the GPU.  One persistent
+// kernel per size class walks a device work queue of items:
+//  - a whole document (sizes up to the split threshold): one block counts it
+//    into a shared-memory table (dynamic inserts, 16-byte keys) with words of
+//    17+ letters in a small shared list, sorts the entries by (count desc,
+//    word asc) with a bitonic network in shared memory and writes them into
+//    the CSR output at an atomically reserved offset;
+//  - a byte range of a large document: the block counts the range (words
+//    that start in it, read past its end as needed) and adds its table into
+//    global tables keyed by (document, word).
+// A whole document whose shared table fills up spills the rest of its words
+// (and, at the end, its shared table) to the same global tables.  Documents
+// counted there are finished by a segmented pass: compaction, a radix sort
+// with the document as most significant key, and a CSR write.
+#include "wc_batch.h"
+
+namespace wc {
+
+// ---------------------------------------------------------------- (doc, word) keys
+// Letter bytes are 0x61..0x7A: their low 5 bits (1..26) name the letter and
+// bits 5-7 are always 011; padding bytes are 0.  So bits 5-7 of each key byte
+// can carry 3 bits of the document number and be restored afterwards.
+constexpr unsigned long long kCodeMask = 0x1F1F1F1F1F1F1F1Full;
+__device__ __forceinline__ unsigned long long spread_doc(uint32_t d) {  // 24 bits -> bits 5..7 of 8 bytes
+    unsigned long long r = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) r |= (unsigned long long)((d >> (3 * i)) & 7u) << (8 * i + 5);
+    return r;
+}
+__device__ __forceinline__ uint32_t gather_doc(unsigned long long k) {
+    uint32_t d = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) d |= (uint32_t)((k >> (8 * i + 5)) & 7u) << (3 * i);
+    return d;
+}
+__device__ __forceinline__ unsigned long long restore_letters(unsigned long long k) {
+    unsigned long long c = k & kCodeMask;
+    unsigned long long nz = (c + 0x7F7F7F7F7F7F7F7Full) & 0x8080808080808080ull;  // 0x80 where code != 0
+    return c | (nz >> 1) | (nz >> 2);
+}
+__device__ __forceinline__ unsigned long long long_doc_hash(unsigned long long h, uint32_t d) {
+    return h ^ fmix64((unsigned long long)d + 0x632BE59BD9B4E019ull);
+}
+
+// Adds `add` to word k (<= 16 letters) of document d in the global tables.
+__device__ __forceinline__ void doc_insert_key(const GTable &g, uint32_t d, uint4 k, unsigned long long add) {
+    const unsigned long long lo = ((unsigned long long)k.y << 32) | k.x, hi = ((unsigned long long)k.w << 32) | k.z;
+    if (hi == 0ull) {
+        global_insert8(g, (lo & kCodeMask) | spread_doc(d & 0xFFFFFFu), add);
+    } else {
+        const unsigned long long l2 = (lo & kCodeMask) | spread_doc(d & 0xFFFFFFu);
+        const unsigned long long h2 = (hi & kCodeMask) | spread_doc(d >> 24);
+        global_insert16(g, make_uint4((uint32_t)l2, (uint32_t)(l2 >> 32), (uint32_t)h2, (uint32_t)(h2 >> 32)), add);
+    }
+}
+__device__ __forceinline__ void doc_insert_long(const GTable &g, uint32_t d, const uint8_t *w, unsigned long long len,
+                                                unsigned long long add, const uint8_t *begin, const uint8_t *end) {
+    long_insert2(g, w, len, long_doc_hash(long_hash_serial(w, len), d), add, begin, end);
+}
+
+__device__ __forceinline__ unsigned long long be64b(uint32_t x, uint32_t y) {
+    return ((unsigned long long)__byte_perm(x, 0, 0x0123) << 32) | __byte_perm(y, 0, 0x0123);
+}
+__device__ __forceinline__ unsigned long long be_bytes16(const uint8_t *src, int from) {  // lowercased, big endian
+    unsigned long long v = 0;
+    for (int j = from; j < from + 8; j++) v = (v << 8) | (unsigned long long)(src[j] | 0x20u);
+    return v;
+}
+
+// ---------------------------------------------------------------- per-document kernel
+template <int BLOCK, int LOGC1>
+struct DocCfg {
+    static constexpr int W = BLOCK / 32;
+    static constexpr int CH = W * 512;         // one strip per warp
+    static constexpr int WINB = CH + 96;
+    static constexpr int C1 = 1 << LOGC1;
+    static constexpr int TOKCAP = 32 + 256;
+    static constexpr int LCAP = 64;            // distinct long words per document in shared memory
+    static constexpr uint32_t FILL = C1 * 3 / 4;
+    static constexpr size_t SMEM = (size_t)WINB + (size_t)W * TOKCAP * 4 +  // window + queues (sort buffer)
+                                   (size_t)C1 * 16 + (size_t)C1 * 4 + (size_t)C1 * 4 +  // keys, counts, tags
+                                   (size_t)LCAP * (8 + 8 + 4 + 4 + 16) + 64;
+    static_assert((size_t)WINB + (size_t)W * TOKCAP * 4 >= (size_t)C1 * 2, "sort buffer must fit");
+    static_assert(C1 <= 32768, "16-bit sort indices");
+};
+
+struct DocShared {  // per-block scalars
+    uint32_t item;
+    uint32_t lcount;
+    uint32_t nfill;
+    uint32_t spilled;
+    uint32_t nent;
+    uint32_t nlong;
+    unsigned long long base, lbase, abase;
+    uint32_t ok;
+};
+
+template <int BLOCK, int LOGC1>
+__global__ void __launch_bounds__(BLOCK) k_docs(BatchArgs a) {
+    using C = DocCfg<BLOCK, LOGC1>;
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint8_t *win = smem;
+    uint32_t *tokall = reinterpret_cast<uint32_t *>(smem + C::WINB);
+    uint16_t *sidx = reinterpret_cast<uint16_t *>(smem);  // sort buffer, reuses window + queues
+    uint4 *skey = reinterpret_cast<uint4 *>(smem + C::WINB + (size_t)C::W * C::TOKCAP * 4);
+    uint32_t *scnt = reinterpret_cast<uint32_t *>(skey + C::C1);
+    uint32_t *stag = scnt + C::C1;
+    unsigned long long *laddr = reinterpret_cast<unsigned long long *>(stag + C::C1);
+    unsigned long long *llen = laddr + C::LCAP;
+    uint32_t *lcnt = reinterpret_cast<uint32_t *>(llen + C::LCAP);
+    uint32_t *lrank = lcnt + C::LCAP;
+    ulonglong2 *lkey = reinterpret_cast<ulonglong2 *>(lrank + C::LCAP);
+    __shared__ DocShared sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *tok = tokall + warp * C::TOKCAP;
+    STable st{stag, skey, scnt, &sh.nfill, (uint32_t)(C::C1 - 1), C::FILL};
+    const uintptr_t tb = reinterpret_cast<uintptr_t>(a.text);
+
+    for (;;) {
+        if (threadIdx.x == 0) sh.item = atomicAdd(a.next_item, 1u);
+        __syncthreads();
+        const uint32_t item = sh.item;
+        if (item >= a.nitems) break;
+        const DocItem it = a.items[item];
+        const uint32_t d = it.doc;
+        const uintptr_t vb = tb + a.doc_off[d], ve = tb + a.doc_off[d + 1];
+        const uintptr_t own_lo = tb + it.lo, own_hi = tb + it.hi;
+        const uint8_t *dbeg = reinterpret_cast<const uint8_t *>(vb);
+        const uint8_t *dend = reinterpret_cast<const uint8_t *>(ve);
+        for (int i = threadIdx.x; i < C::C1; i += BLOCK) stag[i] = 0u;
+        if (threadIdx.x == 0) {
+            sh.lcount = 0;
+            sh.nfill = 0;
+            sh.spilled = it.kind;  // ranges always go to the global tables
+        }
+        for (int i = threadIdx.x; i < C::LCAP; i += BLOCK) laddr[i] = 0ull;
+        __syncthreads();
+
+        auto process = [&](bool have, uint32_t e) {
+            if (have) {
+                const uint32_t p = e >> 5, len = e & 31u;
+                uint4 k = load_key16(win, p, len);
+                if (!shared_insert(st, k, hash_key(k), 1u, C::C1)) {
+                    doc_insert_key(a.g, d, k, 1ull);
+                    sh.spilled = 1u;
+                }
+            }
+        };
+
+        for (uintptr_t cs = own_lo & ~(uintptr_t)15; cs < own_hi; cs += C::CH) {
+            const uintptr_t w0 = cs - 16;
+            for (int t = threadIdx.x; t < C::WINB / 16; t += BLOCK) {
+                uintptr_t ad = w0 + 16 * (uintptr_t)t;
+                uint4 v = make_uint4(0x20202020u, 0x20202020u, 0x20202020u, 0x20202020u);
+                if (ad < ve && ad + 16 > vb) {
+                    v = ld_stream16(reinterpret_cast<const void *>(ad));
+                    if (ad < vb || ad + 16 > ve) v = mask_outside_doc(v, ad, vb, ve);
+                }
+                *reinterpret_cast<uint4 *>(win + 16 * t) = v;
+            }
+            __syncthreads();
+            // ---- this warp's strip
+            const int sbase = 16 + 512 * warp;
+            const uint32_t prevL = is_letter(win[sbase - 1]) ? 1u : 0u;
+            const uint32_t L = letter_mask16(*reinterpret_cast<const uint4 *>(win + sbase + 16 * lane));
+            const uint32_t Ln = letter_mask16(*reinterpret_cast<const uint4 *>(win + sbase + 512));
+            const uint32_t up = __shfl_up_sync(kFull, L, 1);
+            const uint32_t dn = __shfl_down_sync(kFull, L, 1);
+            const uint32_t pbit = lane == 0 ? prevL : ((up >> 15) & 1u);
+            const uint32_t Wm = L | ((lane == 31 ? Ln : dn) << 16);
+            uint32_t S = L & ~((L << 1) | pbit) & 0xFFFFu;
+            {   // only words that start inside this item's byte range
+                const uintptr_t A = w0 + sbase + 16 * lane;
+                long long lo = (long long)(own_lo - A), hi = (long long)(own_hi - A);
+                int klo = (int)(lo < 0 ? 0 : (lo > 16 ? 16 : lo)), khi = (int)(hi < 0 ? 0 : (hi > 16 ? 16 : hi));
+                uint32_t m = (khi > klo) ? (((1u << khi) - 1u) & ~((1u << klo) - 1u)) : 0u;
+                S &= m;
+            }
+            uint32_t x = Wm;
+            x &= x >> 1; x &= x >> 2; x &= x >> 4; x &= x >> 8; x &= Wm >> 16;
+            uint32_t Ss = S & ~x, Sl = S & x;
+            const uint32_t c1 = __popc(Ss);
+            uint32_t incl = c1;
+#pragma unroll
+            for (int dd = 1; dd < 32; dd <<= 1) {
+                uint32_t t = __shfl_up_sync(kFull, incl, dd);
+                if (lane >= dd) incl += t;
+            }
+            const uint32_t total = __shfl_sync(kFull, incl, 31);
+            uint32_t off = incl - c1;
+            const uint32_t pbase = (uint32_t)(sbase + 16 * lane);
+            while (Ss) {
+                int j = __ffs(Ss) - 1;
+                Ss &= Ss - 1;
+                tok[off++] = ((pbase + (uint32_t)j) << 5) | ((uint32_t)__ffs(~(Wm >> j)) - 1u);
+            }
+            // long words: the whole warp handles each in turn
+            uint32_t pend = __ballot_sync(kFull, Sl != 0);
+            while (pend) {
+                const int who = __ffs(pend) - 1;
+                unsigned long long wa = 0;
+                if (lane == who) {
+                    int j = __ffs(Sl) - 1;
+                    Sl &= Sl - 1;
+                    wa = (unsigned long long)(w0 + pbase + (uint32_t)j);
+                }
+                wa = __shfl_sync(kFull, wa, who);
+                pend = __ballot_sync(kFull, Sl != 0);
+                const uint8_t *w = reinterpret_cast<const uint8_t *>(wa);
+                unsigned long long len = 0;
+                for (unsigned long long o = 0;; o += 32) {
+                    const uint8_t *q = w + o + lane;
+                    uint32_t bb = q < dend ? *q : 0x20u;
+                    uint32_t m = __ballot_sync(kFull, !is_letter(bb));
+                    if (m) { len = o + (unsigned long long)(__ffs(m) - 1); break; }
+                }
+                bool found = false;
+                const uint32_t lc = *(volatile uint32_t *)&sh.lcount;
+                for (uint32_t j = 0; j < lc && j < (uint32_t)C::LCAP && !found; j++) {
+                    const unsigned long long ra = *(volatile unsigned long long *)&laddr[j];
+                    if (!ra || *(volatile unsigned long long *)&llen[j] != len) continue;
+                    const uint8_t *r = reinterpret_cast<const uint8_t *>(ra);
+                    bool ok = true;
+                    for (unsigned long long q = lane; q < len; q += 32) ok &= ((r[q] | 0x20u) == (w[q] | 0x20u));
+                    if (__all_sync(kFull, ok)) {
+                        if (lane == 0) atomicAdd(&lcnt[j], 1u);
+                        found = true;
+                    }
+                }
+                if (!found) {
+                    uint32_t slot = 0;
+                    if (lane == 0) slot = atomicAdd(&sh.lcount, 1u);
+                    slot = __shfl_sync(kFull, slot, 0);
+                    if (slot < (uint32_t)C::LCAP) {
+                        if (lane == 0) {
+                            llen[slot] = len;
+                            lcnt[slot] = 1u;
+                            __threadfence_block();
+                            *(volatile unsigned long long *)&laddr[slot] = wa;
+                        }
+                    } else {
+                        if (lane == 0) {
+                            doc_insert_long(a.g, d, w, len, 1ull, dbeg, dend);
+                            sh.spilled = 1u;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            __syncwarp();
+            uint32_t bq = 0;
+            for (; bq + 32 <= total; bq += 32) process(true, tok[bq + lane]);
+            process((uint32_t)lane < total - bq, (uint32_t)lane < total - bq ? tok[bq + lane] : 0u);
+            __syncthreads();  // the window is about to be overwritten
+        }
+        if (threadIdx.x == 0 && sh.lcount > (uint32_t)C::LCAP) sh.lcount = C::LCAP;
+        __syncthreads();
+
+        if (sh.spilled) {
+            // ---- range or overflowing document: add everything to the global tables
+            for (int i = threadIdx.x; i < C::C1; i += BLOCK)
+                if (stag[i] > 1u) doc_insert_key(a.g, d, skey[i], (unsigned long long)scnt[i]);
+            for (uint32_t j = threadIdx.x; j < sh.lcount; j += BLOCK)
+                doc_insert_long(a.g, d, reinterpret_cast<const uint8_t *>(laddr[j]), llen[j],
+                                (unsigned long long)lcnt[j], dbeg, dend);
+            if (threadIdx.x == 0) atomicOr(&a.doc_flags[d], 1u);
+            __syncthreads();
+            continue;
+        }
+
+        // ---- whole document: merge duplicate entries of the shared table.  A
+        // word may sit in two slots (an insert skips a slot being written);
+        // all its copies share one home slot and probe order, so each copy
+        // walks from home and adds itself to the first slot holding its key,
+        // then marks itself dead (tag 1: probing still passes over it).
+        for (int i = threadIdx.x; i < C::C1; i += BLOCK) {
+            const uint32_t tg = stag[i];
+            if (tg <= 1u) continue;
+            const uint4 k = skey[i];
+            uint32_t s = (uint32_t)(hash_key(k) >> 40) & (uint32_t)(C::C1 - 1);
+            for (int probe = 0; probe < C::C1 && s != (uint32_t)i && stag[s] != 0u; probe++) {
+                if (stag[s] == tg && key_eq(skey[s], k)) {
+                    atomicAdd(&scnt[s], scnt[i]);
+                    stag[i] = 1u;
+                    break;
+                }
+                s = (s + 1) & (uint32_t)(C::C1 - 1);
+            }
+        }
+        __syncthreads();
+        // merge duplicate long entries (warp 0)
+        const uint32_t nl = sh.lcount;
+        if (warp == 0) {
+            for (uint32_t i = 1; i < nl; i++) {
+                for (uint32_t j = 0; j < i; j++) {
+                    if (lcnt[j] == 0u || llen[j] != llen[i]) continue;
+                    const uint8_t *p = reinterpret_cast<const uint8_t *>(laddr[i]);
+                    const uint8_t *q = reinterpret_cast<const uint8_t *>(laddr[j]);
+                    bool ok = true;
+                    for (unsigned long long k = lane; k < llen[i]; k += 32) ok &= ((p[k] | 0x20u) == (q[k] | 0x20u));
+                    if (__all_sync(kFull, ok)) {
+                        if (lane == 0) { lcnt[j] += lcnt[i]; lcnt[i] = 0u; }
+                        __syncwarp();
+                        break;
+                    }
+                }
+            }
+        }
+        // keys to big-endian halves (in place), long prefixes
+        for (int i = threadIdx.x; i < C::C1; i += BLOCK) {
+            if (stag[i] > 1u) {
+                uint4 k = skey[i];
+                reinterpret_cast<ulonglong2 *>(skey)[i] = make_ulonglong2(be64b(k.x, k.y), be64b(k.z, k.w));
+            }
+        }
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < nl; j += BLOCK) {
+            const uint8_t *p = reinterpret_cast<const uint8_t *>(laddr[j]);
+            lkey[j] = make_ulonglong2(be_bytes16(p, 0), be_bytes16(p, 8));
+        }
+        if (threadIdx.x == 0) { sh.nent = 0; sh.nlong = 0; }
+        __syncthreads();
+        // index list of live entries (order is fixed by the sort below)
+        for (int i = threadIdx.x; i < C::C1; i += BLOCK)
+            if (stag[i] > 1u) sidx[atomicAdd(&sh.nent, 1u)] = (uint16_t)i;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t r = 0;
+            for (uint32_t j = 0; j < nl; j++) {
+                if (lcnt[j]) { lrank[j] = r++; sidx[sh.nent++] = (uint16_t)(C::C1 + j); }
+            }
+            sh.nlong = r;
+        }
+        __syncthreads();
+        const uint32_t n = sh.nent;
+        uint32_t N = 1;
+        while (N < n) N <<= 1;
+        for (uint32_t i = n + threadIdx.x; i < N; i += BLOCK) sidx[i] = 0xFFFFu;
+        __syncthreads();
+        auto cnt_of = [&](uint32_t s) -> uint32_t { return s < (uint32_t)C::C1 ? scnt[s] : lcnt[s - C::C1]; };
+        auto key_of = [&](uint32_t s) -> ulonglong2 {
+            return s < (uint32_t)C::C1 ? reinterpret_cast<const ulonglong2 *>(skey)[s] : lkey[s - C::C1];
+        };
+        auto less = [&](uint32_t x, uint32_t y) -> bool {
+            if (x == 0xFFFFu) return false;
+            if (y == 0xFFFFu) return true;
+            const uint32_t cx = cnt_of(x), cy = cnt_of(y);
+            if (cx != cy) return cx > cy;
+            const ulonglong2 kx = key_of(x), ky = key_of(y);
+            if (kx.x != ky.x) return kx.x < ky.x;
+            if (kx.y != ky.y) return kx.y < ky.y;
+            const bool lx = x >= (uint32_t)C::C1, ly = y >= (uint32_t)C::C1;
+            if (!lx) return ly;
+            if (!ly) return false;
+            const uint8_t *px = reinterpret_cast<const uint8_t *>(laddr[x - C::C1]);
+            const uint8_t *py = reinterpret_cast<const uint8_t *>(laddr[y - C::C1]);
+            const unsigned long long nx = llen[x - C::C1], ny = llen[y - C::C1];
+            const unsigned long long m = nx < ny ? nx : ny;
+            for (unsigned long long i = 16; i < m; i++) {
+                uint32_t bx = px[i] | 0x20u, by = py[i] | 0x20u;
+                if (bx != by) return bx < by;
+            }
+            return nx < ny;
+        };
+        for (uint32_t k = 2; k <= N; k <<= 1) {
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                for (uint32_t i = threadIdx.x; i < N; i += BLOCK) {
+                    const uint32_t ixj = i ^ j;
+                    if (ixj > i) {
+                        const uint32_t x = sidx[i], y = sidx[ixj];
+                        const bool up = (i & k) == 0;
+                        if (up ? less(y, x) : less(x, y)) { sidx[i] = (uint16_t)y; sidx[ixj] = (uint16_t)x; }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // reserve output: entries, long words, arena bytes
+        if (threadIdx.x == 0) {
+            unsigned long long ab = 0;
+            for (uint32_t j = 0; j < nl; j++)
+                if (lcnt[j]) ab += llen[j] + 1;
+            sh.base = atomicAdd(&a.meta[0], (unsigned long long)n);
+            sh.lbase = sh.nlong ? atomicAdd(&a.meta[1], (unsigned long long)sh.nlong) : 0ull;
+            sh.abase = ab ? atomicAdd(&a.meta[2], ab) : 0ull;
+            sh.ok = (sh.base + n <= a.out_cap && sh.lbase + sh.nlong <= a.lcap && sh.abase + ab <= a.arena_cap);
+            if (!sh.ok) atomicOr(a.status, ST_OUT_FULL);
+            a.doc_start[d] = sh.base;
+            a.doc_n[d] = sh.ok ? n : 0u;
+        }
+        __syncthreads();
+        if (sh.ok) {
+            const unsigned long long base = sh.base;
+            for (uint32_t i = threadIdx.x; i < n; i += BLOCK) {
+                const uint32_t s = sidx[i];
+                const ulonglong2 k = key_of(s);
+                a.out_khi[base + i] = k.x;
+                a.out_klo[base + i] = k.y;
+                a.out_cnt[base + i] = cnt_of(s);
+                a.out_lref[base + i] = s < (uint32_t)C::C1 ? 0u : (uint32_t)(sh.lbase + lrank[s - C::C1] + 1);
+            }
+            if (warp == 0 && sh.nlong) {
+                unsigned long long ao = sh.abase;
+                for (uint32_t j = 0; j < nl; j++) {
+                    if (!lcnt[j]) continue;
+                    const uint8_t *p = reinterpret_cast<const uint8_t *>(laddr[j]);
+                    const unsigned long long len = llen[j];
+                    for (unsigned long long q = lane; q < len; q += 32) a.arena[ao + q] = (uint8_t)(p[q] | 0x20u);
+                    if (lane == 0) {
+                        a.arena[ao + len] = 0;
+                        a.loff[sh.lbase + lrank[j]] = ao;
+                        a.llen[sh.lbase + lrank[j]] = len;
+                    }
+                    ao += len + 1;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int BLOCK, int LOGC1>
+cudaError_t launch_docs_t(const BatchArgs &a, int grid, cudaStream_t s) {
+    using C = DocCfg<BLOCK, LOGC1>;
+    static bool set = false;
+    if (!set) {
+        cudaError_t e = cudaFuncSetAttribute(k_docs<BLOCK, LOGC1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if (e != cudaSuccess) return e;
+        set = true;
+    }
+    if (grid <= 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_docs<BLOCK, LOGC1>, BLOCK, C::SMEM);
+        grid = sms * (per > 0 ? per : 1);
+    }
+    k_docs<BLOCK, LOGC1><<<grid, BLOCK, C::SMEM, s>>>(a);
+    return cudaGetLastError();
+}
+
+const DocShape kDocShapes[] = {
+    {128, 10}, {256, 11}, {256, 12}, {512, 12}, {512, 13},
+};
+const int kNumDocShapes = sizeof(kDocShapes) / sizeof(kDocShapes[0]);
+
+cudaError_t launch_docs(const BatchArgs &a, int shape, cudaStream_t s) {
+    switch (shape) {
+    case 0: return launch_docs_t<128, 10>(a, 0, s);
+    case 1: return launch_docs_t<256, 11>(a, 0, s);
+    case 2: return launch_docs_t<256, 12>(a, 0, s);
+    case 3: return launch_docs_t<512, 12>(a, 0, s);
+    default: return launch_docs_t<512, 13>(a, 0, s);
+    }
+}
+
+// ---------------------------------------------------------------- segmented finish
+__device__ __forceinline__ uint32_t doc_of_pos(const unsigned long long *off, uint32_t ndocs, unsigned long long pos) {
+    uint32_t lo = 0, hi = ndocs;  // last doc with off[doc] <= pos
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) / 2;
+        if (off[mid] <= pos) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_bcompact8(const G8Slot *slots, unsigned long long cap, SortScratch ss, unsigned long long *meta) {
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long k = slots[i].key;
+        if (!k) continue;
+        const unsigned long long pos = atomicAdd(&meta[0], 1ull);
+        const unsigned long long w = restore_letters(k);
+        ss.khi[pos] = be64b((uint32_t)w, (uint32_t)(w >> 32));
+        ss.klo[pos] = 0ull;
+        ss.cnt[pos] = slots[i].cnt;
+        ss.lref[pos] = 0u;
+        ss.doc[pos] = gather_doc(k);
+    }
+}
+
+__global__ void k_bcompact16(const GSlot *slots, unsigned long long cap, SortScratch ss, unsigned long long *meta) {
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint4 k = slots[i].key;
+        if (key_zero(k)) continue;
+        const unsigned long long lo = ((unsigned long long)k.y << 32) | k.x, hi = ((unsigned long long)k.w << 32) | k.z;
+        const unsigned long long pos = atomicAdd(&meta[0], 1ull);
+        const unsigned long long wl = restore_letters(lo), wh = restore_letters(hi);
+        ss.khi[pos] = be64b((uint32_t)wl, (uint32_t)(wl >> 32));
+        ss.klo[pos] = be64b((uint32_t)wh, (uint32_t)(wh >> 32));
+        ss.cnt[pos] = slots[i].cnt;
+        ss.lref[pos] = 0u;
+        ss.doc[pos] = gather_doc(lo) | (gather_doc(hi) << 24);
+    }
+}
+
+// One warp per long slot: document from the representative's position, bytes
+// copied (lowercased, 0-terminated) into the batch arena.
+__global__ void k_bcompact_long(const LSlot *ls, unsigned long long lcap, SortScratch ss, BatchArgs a,
+                                unsigned long long *meta) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long gw = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    for (unsigned long long w = gw; w < lcap; w += nw) {
+        const unsigned long long h = ls[w].h, addr = ls[w].addr;
+        if (h == 0 && addr == 0) continue;
+        const unsigned long long len = ls[w].len, c = ls[w].cnt;
+        const uint8_t *src = reinterpret_cast<const uint8_t *>(addr);
+        unsigned long long off = 0, lidx = 0, pos = 0;
+        if (lane == 0) {
+            off = atomicAdd(&a.meta[2], len + 1);
+            lidx = atomicAdd(&a.meta[1], 1ull);
+            pos = atomicAdd(&meta[0], 1ull);
+            atomicAdd(&meta[1], 1ull);  // long entries present: the sort orders shared prefixes by full bytes
+        }
+        off = __shfl_sync(kFull, off, 0);
+        lidx = __shfl_sync(kFull, lidx, 0);
+        pos = __shfl_sync(kFull, pos, 0);
+        const bool fits = off + len + 1 <= a.arena_cap && lidx < a.lcap;
+        if (fits)
+            for (unsigned long long j = lane; j < len; j += 32) a.arena[off + j] = (uint8_t)(src[j] | 0x20u);
+        if (lane == 0) {
+            if (!fits) atomicOr(a.status, ST_OUT_FULL);
+            else {
+                a.arena[off + len] = 0;
+                a.loff[lidx] = off;
+                a.llen[lidx] = len;
+            }
+            ss.khi[pos] = be_bytes16(src, 0);
+            ss.klo[pos] = be_bytes16(src, 8);
+            ss.cnt[pos] = c;
+            ss.lref[pos] = fits ? (uint32_t)(lidx + 1) : 0u;
+            ss.doc[pos] = doc_of_pos(a.doc_off, a.ndocs, addr - reinterpret_cast<uintptr_t>(a.text));
+        }
+    }
+}
+
+__global__ void k_seg_base(BatchArgs a, unsigned long long *meta) {
+    const unsigned long long n = meta[0];
+    const unsigned long long base = n ? atomicAdd(&a.meta[0], n) : 0ull;
+    meta[8] = base;
+    if (base + n > a.out_cap) {
+        atomicOr(a.status, ST_OUT_FULL);
+        meta[9] = 0;
+    } else {
+        meta[9] = 1;
+    }
+}
+
+__global__ void k_seg_write(SortScratch ss, BatchArgs a, const unsigned long long *meta, int passes) {
+    const unsigned long long n = meta[0], base = meta[8];
+    if (!meta[9]) return;
+    const uint32_t *perm = ss.perm[ss.cur[passes]];
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t e = perm[i];
+        a.out_khi[base + i] = ss.khi[e];
+        a.out_klo[base + i] = ss.klo[e];
+        a.out_cnt[base + i] = (uint32_t)ss.cnt[e];
+        a.out_lref[base + i] = ss.lref[e];
+        const uint32_t d = ss.doc[e];
+        if (i == 0 || ss.doc[perm[i - 1]] != d) a.doc_start[d] = base + i;
+    }
+}
+
+__global__ void k_seg_ends(SortScratch ss, BatchArgs a, const unsigned long long *meta, int passes) {
+    const unsigned long long n = meta[0], base = meta[8];
+    if (!meta[9]) return;
+    const uint32_t *perm = ss.perm[ss.cur[passes]];
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t d = ss.doc[perm[i]];
+        if (i + 1 == n || ss.doc[perm[i + 1]] != d) a.doc_n[d] = (uint32_t)(base + i + 1 - a.doc_start[d]);
+    }
+}
+
+static int gridn(unsigned long long n, int t, int maxb) {
+    unsigned long long g = (n + t - 1) / t;
+    if (g < 1) g = 1;
+    if (g > (unsigned long long)maxb) g = maxb;
+    return (int)g;
+}
+
+cudaError_t launch_segmented_finish(const BatchArgs &a, const GTable &g, uint64_t cap8, uint64_t cap16,
+                                    uint64_t caplong, SortScratch &ss, unsigned long long *smeta, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaMemsetAsync(smeta, 0, 16 * 8, s);
+    cudaMemsetAsync(ss.hist_all, 0, 4 * 28 * 256, s);
+    cudaMemsetAsync(ss.cur, 0, 4 * 32, s);
+    k_bcompact8<<<gridn(cap8, 256, sms * 8), 256, 0, s>>>(g.slots8, cap8, ss, smeta);
+    k_bcompact16<<<gridn(cap16, 256, sms * 8), 256, 0, s>>>(g.slots, cap16, ss, smeta);
+    k_bcompact_long<<<gridn(caplong * 32, 256, sms * 8), 256, 0, s>>>(g.lslots, caplong, ss, a, smeta);
+    LongView v{ss.lref, a.loff, a.llen, a.arena};
+    cudaError_t e = sort_entries(ss, smeta, v, 28, s);
+    if (e != cudaSuccess) return e;
+    k_seg_base<<<1, 1, 0, s>>>(a, smeta);
+    k_seg_write<<<gridn(ss.cap, 256, sms * 8), 256, 0, s>>>(ss, a, smeta, 28);
+    k_seg_ends<<<gridn(ss.cap, 256, sms * 8), 256, 0, s>>>(ss, a, smeta, 28);
+    return cudaGetLastError();
+}
+int segmented_finish_launches() { return 3 + sort_entries_launches(28) + 3; }
+
+}  // namespace wc

@@ -1,19 +1,818 @@
-// Batched counting entry points (filled in with the batched kernels).
+// Batched counting entry points: planning, capacities, launches, per-document
+// views, class and global tables, the class-ratio ranking and bulk export.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
 #include "../../include/wc.h"
+#include "wc_batch.h"
 #include "wc_host.h"
 
-wc_status wc_count_batched(wc_ctx *ctx, const uint8_t *, const uint64_t *, const uint64_t *, uint32_t,
-                           const uint32_t *, uint32_t, cudaStream_t, wc_batch **out) {
-    if (out) *out = nullptr;
-    return ctx ? ctx->fail(WC_ERR_UNSUPPORTED, "batched counting not built yet") : WC_ERR_INVALID_ARG;
+using namespace wc;
+
+namespace {
+
+constexpr uint64_t kSmallMax = 8 << 10;     // whole documents up to 8 KB: small shape
+constexpr uint64_t kSplitMin = 64 << 10;    // documents above 64 KB are split into ranges
+constexpr uint64_t kRange = 32 << 10;       // byte range per item of a split document
+constexpr uint32_t kMaxDocs = 1u << 24;     // (document, word) keys carry 24 document bits
+
+uint64_t pow2_ge(uint64_t x) {
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
 }
-wc_status wc_batch_table(const wc_batch *, int, uint32_t, const wc_table **out) {
-    if (out) *out = nullptr;
-    return WC_ERR_UNSUPPORTED;
+
+// Distinct-word estimate of one document of s bytes (generous Heaps' law, never
+// above the exact bound ceil(s/2)).
+uint64_t est_distinct(uint64_t s) {
+    if (!s) return 0;
+    double t = (double)s / 5.0 + 1.0;
+    double e = std::min(t, 16.0 * std::pow(t, 0.6));
+    return std::min<uint64_t>((uint64_t)e + 16, s / 2 + 1);
 }
-wc_status wc_class_ratio_topk(wc_ctx *, const wc_batch *, uint32_t, uint32_t, cudaStream_t, uint64_t *,
-                              uint64_t *, uint64_t *, uint32_t *nout) {
-    if (nout) *nout = 0;
-    return WC_ERR_UNSUPPORTED;
+
+}  // namespace
+
+struct BatchScratch {
+    DocItem *items = nullptr;
+    size_t ibytes = 0;
+    uint32_t *next = nullptr;  // [2] queue cursors
+    unsigned long long *smeta = nullptr;
+    CountScratch cs;           // (document, word) tables + sort scratch
+};
+
+struct wc_batch {
+    wc_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    uint32_t ndocs = 0, nclasses = 0;
+    void *mem = nullptr;
+    size_t bytes = 0;
+    BatchArgs args{};
+    uint32_t *d_class = nullptr;  // copy of the classes
+    // planning
+    std::vector<DocItem> items;
+    uint32_t nsmall = 0;
+    int shape_small = 1, shape_medium = 4;
+    uint64_t cap8 = 0, cap16 = 0, caplong = 0;
+    BatchScratch scr;
+    // after sync
+    bool synced = false;
+    wc_status sync_status = WC_OK;
+    uint64_t entries = 0, word_bytes = 0;
+    // lazily built
+    bool tables_built = false;
+    std::vector<wc_table *> class_tables;
+    wc_table *global = nullptr;
+    CountScratch gscratch;        // global hash tables kept for ratio lookups
+    std::vector<wc_table *> views;
+};
+
+static wc_status batch_sync(const wc_batch *cb) {
+    wc_batch *b = const_cast<wc_batch *>(cb);
+    if (b->synced) return b->sync_status;
+    cudaError_t e = cudaEventSynchronize(b->done);
+    if (e != cudaSuccess) return b->ctx->cuda_fail(e, "batch sync");
+    unsigned long long meta[4];
+    uint32_t st = 0;
+    e = cudaMemcpy(meta, b->args.meta, sizeof(meta), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&st, b->args.status, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return b->ctx->cuda_fail(e, "batch metadata");
+    b->entries = meta[0];
+    b->sync_status = WC_OK;
+    if (st & (ST_TABLE_FULL | ST_LONG_FULL | ST_ARENA_FULL | ST_OUT_FULL)) b->sync_status = WC_ERR_CAPACITY;
+    else if (st & ST_TIMEOUT) b->sync_status = WC_ERR_TIMEOUT;
+    if (b->sync_status != WC_OK) {
+        b->entries = 0;
+        b->ctx->fail(b->sync_status, ("batched count overflowed a device table or output (status bits " +
+                                      std::to_string(st) + "); count again").c_str());
+    }
+    b->synced = true;
+    return b->sync_status;
 }
-void wc_batch_free(wc_batch *) {}
+
+// Words bytes and token totals of a view (one block).
+__global__ void k_view_meta(DevTable t, unsigned long long n) {
+    __shared__ unsigned long long sb[32], st[32];
+    unsigned long long bytes = 0, tok = 0;
+    for (unsigned long long i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint32_t r = t.lref[i];
+        unsigned long long hi = t.khi[i], lo = t.klo[i];
+        unsigned long long len;
+        if (r) len = t.llen[r - 1];
+        else if (lo) len = 16 - (__ffsll((long long)lo) - 1) / 8;
+        else len = 8 - (__ffsll((long long)hi) - 1) / 8;
+        bytes += len;
+        tok += static_cast<const uint32_t *>(t.cnt)[i];
+    }
+    for (int d = 16; d; d >>= 1) {
+        bytes += __shfl_xor_sync(0xFFFFFFFFu, bytes, d);
+        tok += __shfl_xor_sync(0xFFFFFFFFu, tok, d);
+    }
+    if ((threadIdx.x & 31) == 0) { sb[threadIdx.x >> 5] = bytes; st[threadIdx.x >> 5] = tok; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long B = 0, T = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) { B += sb[w]; T += st[w]; }
+        t.d_meta[0] = n;
+        t.d_meta[3] = T;
+        t.d_meta[4] = B;
+        *t.d_status = 0;
+    }
+}
+
+// A wc_table that reads entries [start, start+n) of the batch output.
+static wc_status make_view(wc_batch *b, uint64_t start, uint64_t n, wc_table **out) {
+    wc_ctx *ctx = b->ctx;
+    wc_table *t = new wc_table();
+    t->ctx = ctx;
+    t->owner = b;
+    t->bytes = 512;
+    wc_status s = ctx->alloc(&t->mem, t->bytes, b->stream);
+    if (s != WC_OK) { delete t; return s; }
+    cudaMemsetAsync(t->mem, 0, t->bytes, b->stream);
+    DevTable &d = t->dt;
+    d.cap = std::max<uint64_t>(n, 1);
+    d.lcap = b->args.lcap;
+    d.arena_cap = b->args.arena_cap;
+    d.count_bits = 32;
+    d.d_meta = static_cast<unsigned long long *>(t->mem);
+    d.d_status = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(t->mem) + 256);
+    d.khi = b->args.out_khi + start;
+    d.klo = b->args.out_klo + start;
+    d.cnt = b->args.out_cnt + start;
+    d.lref = b->args.out_lref + start;
+    d.loff = b->args.loff;
+    d.llen = b->args.llen;
+    d.arena = b->args.arena;
+    k_view_meta<<<1, 256, 0, b->stream>>>(d, n);
+    t->stream = b->stream;
+    cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming);
+    cudaEventRecord(t->done, b->stream);
+    *out = t;
+    return WC_OK;
+}
+
+static void free_owned_table(wc_table *t) {
+    if (!t) return;
+    cudaEventSynchronize(t->done);
+    t->ctx->release(t->mem, t->bytes, t->stream);
+    cudaEventDestroy(t->done);
+    delete t;
+}
+
+// ---------------------------------------------------------------- batched count
+// Host planning: items per size class (largest first) and capacities.
+static wc_status batch_plan(wc_ctx *ctx, const uint64_t *h_offsets, uint32_t ndocs, uint32_t nclasses, wc_batch **out) {
+    if (ndocs >= kMaxDocs) return ctx->fail(WC_ERR_UNSUPPORTED, "2^24 documents or more in one batch");
+    for (uint32_t i = 0; i < ndocs; i++)
+        if (h_offsets[i + 1] < h_offsets[i]) return ctx->fail(WC_ERR_INVALID_ARG, "offsets decrease");
+    if (ndocs && h_offsets[ndocs] >= (1ull << 40)) return ctx->fail(WC_ERR_UNSUPPORTED, "offsets of 2^40 or more");
+    wc_batch *b = new wc_batch();
+    b->ctx = ctx;
+    b->ndocs = ndocs;
+    b->nclasses = nclasses;
+    std::vector<DocItem> small, medium;
+    uint64_t out_est = 0, glob_est = 0, long_est = 0;
+    for (uint32_t d = 0; d < ndocs; d++) {
+        const uint64_t lo = h_offsets[d], hi = h_offsets[d + 1], s = hi - lo;
+        if (!s) continue;
+        const uint64_t e = est_distinct(s);
+        out_est += e + e / 4;
+        long_est += std::min<uint64_t>(s / 18 + 1, e / 8 + 2);
+        if (s <= kSmallMax) small.push_back({lo, hi, d, 0});
+        else if (s <= kSplitMin) medium.push_back({lo, hi, d, 0});
+        else {
+            glob_est += e;
+            for (uint64_t r = lo; r < hi; r += kRange) medium.push_back({r, std::min(hi, r + kRange), d, 1});
+        }
+    }
+    auto by_size = [](const DocItem &x, const DocItem &y) { return x.hi - x.lo > y.hi - y.lo; };
+    std::stable_sort(small.begin(), small.end(), by_size);
+    std::stable_sort(medium.begin(), medium.end(), by_size);
+    b->nsmall = (uint32_t)small.size();
+    b->items = small;
+    b->items.insert(b->items.end(), medium.begin(), medium.end());
+    b->args.out_cap = out_est + 1024;
+    b->args.lcap = long_est + 1024;
+    b->args.arena_cap = b->args.lcap * 24 + 65536;
+    // planned: split documents; reserve: documents whose shared table fills up
+    b->cap8 = pow2_ge(2 * glob_est + out_est / 32 + (1u << 18));
+    b->cap16 = pow2_ge(glob_est + out_est / 64 + (1u << 17));
+    b->caplong = pow2_ge(glob_est / 8 + (1u << 14));
+    b->shape_small = ctx->tuned_small;
+    b->shape_medium = ctx->tuned_medium;
+    *out = b;
+    return WC_OK;
+}
+
+// Output block (owned by the batch) and, if keep_scratch, the scratch too.
+static wc_status batch_alloc(wc_batch *b, cudaStream_t stream) {
+    wc_ctx *ctx = b->ctx;
+    auto r = [](size_t n) { return (n + 255) & ~(size_t)255; };
+    const size_t nd = std::max<uint32_t>(b->ndocs, 1);
+    const uint64_t out_cap = b->args.out_cap, lcap = b->args.lcap, arena_cap = b->args.arena_cap;
+    b->bytes = r(64) + r(16) + r(out_cap * 8) * 2 + r(out_cap * 4) * 2 + r(nd * 8) + r(nd * 4) * 2 + r(lcap * 8) * 2 +
+               r(arena_cap) + r(nd * 4);
+    wc_status st = ctx->alloc(&b->mem, b->bytes, stream);
+    if (st != WC_OK) return st;
+    uint8_t *p = static_cast<uint8_t *>(b->mem);
+    auto take = [&](size_t n) { uint8_t *q = p; p += r(n); return q; };
+    BatchArgs &a = b->args;
+    a.meta = reinterpret_cast<unsigned long long *>(take(64));
+    a.status = reinterpret_cast<uint32_t *>(take(16));
+    a.out_khi = reinterpret_cast<unsigned long long *>(take(out_cap * 8));
+    a.out_klo = reinterpret_cast<unsigned long long *>(take(out_cap * 8));
+    a.out_cnt = reinterpret_cast<uint32_t *>(take(out_cap * 4));
+    a.out_lref = reinterpret_cast<uint32_t *>(take(out_cap * 4));
+    a.doc_start = reinterpret_cast<unsigned long long *>(take(nd * 8));
+    a.doc_n = reinterpret_cast<uint32_t *>(take(nd * 4));
+    a.doc_flags = reinterpret_cast<uint32_t *>(take(nd * 4));
+    a.loff = reinterpret_cast<unsigned long long *>(take(lcap * 8));
+    a.llen = reinterpret_cast<unsigned long long *>(take(lcap * 8));
+    a.arena = take(arena_cap);
+    b->d_class = reinterpret_cast<uint32_t *>(take(nd * 4));
+    a.ndocs = b->ndocs;
+    // scratch: items + queue cursors, (document, word) tables, sort scratch
+    CapPlan plan{b->cap8, b->cap16, b->caplong, 0};
+    st = scratch_create(ctx, plan, false, stream, b->scr.cs);
+    b->scr.ibytes = sizeof(DocItem) * std::max<size_t>(b->items.size(), 1) + 256 + 16 * 8;
+    void *ib = nullptr;
+    if (st == WC_OK) st = ctx->alloc(&ib, b->scr.ibytes, stream);
+    if (st != WC_OK) return st;
+    b->scr.items = static_cast<DocItem *>(ib);
+    b->scr.next = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(ib) + sizeof(DocItem) * std::max<size_t>(b->items.size(), 1));
+    b->scr.smeta = reinterpret_cast<unsigned long long *>(b->scr.next + 64);
+    cudaError_t e = cudaSuccess;
+    if (!b->items.empty())
+        e = cudaMemcpyAsync(b->scr.items, b->items.data(), sizeof(DocItem) * b->items.size(), cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "batch items");
+    return WC_OK;
+}
+
+static void batch_release_scratch(wc_batch *b, cudaStream_t stream) {
+    wc_ctx *ctx = b->ctx;
+    if (b->scr.items) ctx->release(b->scr.items, b->scr.ibytes, stream);
+    if (b->scr.cs.mem) ctx->release(b->scr.cs.mem, b->scr.cs.bytes, stream);
+    b->scr.items = nullptr;
+    b->scr.cs.mem = nullptr;
+}
+
+// All device work of one batched count, in stream order (capturable: no
+// allocations, no host copies).
+static cudaError_t batch_enqueue(wc_batch *b, const uint8_t *d_text, const uint64_t *d_offsets,
+                                 const uint32_t *d_class, cudaStream_t stream, int shape_small, int shape_medium,
+                                 uint64_t *launches) {
+    BatchArgs &a = b->args;
+    const size_t nd = std::max<uint32_t>(b->ndocs, 1);
+    a.text = d_text;
+    a.doc_off = reinterpret_cast<const unsigned long long *>(d_offsets);
+    cudaMemsetAsync(a.meta, 0, 64 + 256, stream);
+    cudaMemsetAsync(a.doc_start, 0, nd * 8, stream);
+    cudaMemsetAsync(a.doc_n, 0, nd * 4, stream);
+    cudaMemsetAsync(a.doc_flags, 0, nd * 4, stream);
+    if (b->nclasses && d_class) cudaMemcpyAsync(b->d_class, d_class, 4ull * b->ndocs, cudaMemcpyDeviceToDevice, stream);
+    cudaMemsetAsync(b->scr.next, 0, 256, stream);
+    CountScratch &cs = b->scr.cs;
+    const size_t hb = ((cs.gcap8 * sizeof(G8Slot) + 255) & ~(size_t)255) + ((cs.gcap * sizeof(GSlot) + 255) & ~(size_t)255) +
+                      ((cs.glcap * sizeof(LSlot) + 255) & ~(size_t)255);
+    cudaMemsetAsync(cs.mem, 0, hb, stream);
+    a.g = cs.gtable(a.status);
+    cudaError_t e = cudaSuccess;
+    uint64_t n = 0;
+    if (b->nsmall) {
+        BatchArgs s1 = a;
+        s1.items = b->scr.items;
+        s1.nitems = b->nsmall;
+        s1.next_item = b->scr.next;
+        e = launch_docs(s1, shape_small, stream);
+        n++;
+    }
+    if (e == cudaSuccess && b->items.size() > b->nsmall) {
+        BatchArgs s2 = a;
+        s2.items = b->scr.items + b->nsmall;
+        s2.nitems = (uint32_t)(b->items.size() - b->nsmall);
+        s2.next_item = b->scr.next + 1;
+        e = launch_docs(s2, shape_medium, stream);
+        n++;
+    }
+    if (e == cudaSuccess) {
+        e = launch_segmented_finish(a, a.g, cs.gcap8, cs.gcap, cs.glcap, cs.ss, b->scr.smeta, stream);
+        n += segmented_finish_launches();
+    }
+    if (launches) *launches = n;
+    return e;
+}
+
+wc_status wc_count_batched(wc_ctx *ctx, const uint8_t *d_text, const uint64_t *d_offsets, const uint64_t *h_offsets,
+                           uint32_t ndocs, const uint32_t *d_class, uint32_t nclasses, cudaStream_t stream,
+                           wc_batch **out) {
+    if (!ctx || !out) return WC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (ndocs && (!h_offsets || !d_offsets)) return ctx->fail(WC_ERR_INVALID_ARG, "null offsets");
+    if (nclasses && !d_class) return ctx->fail(WC_ERR_INVALID_ARG, "classes without a class array");
+    if (ndocs && h_offsets[ndocs] > h_offsets[0] && !d_text) return ctx->fail(WC_ERR_INVALID_ARG, "null text");
+    cudaSetDevice(ctx->device);
+    wc_batch *b = nullptr;
+    wc_status st = batch_plan(ctx, h_offsets, ndocs, nclasses, &b);
+    if (st != WC_OK) return st;
+    b->stream = stream;
+    if ((st = batch_alloc(b, stream)) != WC_OK) {
+        batch_release_scratch(b, stream);
+        if (b->mem) ctx->release(b->mem, b->bytes, stream);
+        delete b;
+        return st;
+    }
+    uint64_t n = 0;
+    cudaError_t e = batch_enqueue(b, d_text, d_offsets, d_class, stream, b->shape_small, b->shape_medium, &n);
+    ctx->launches += n;
+    batch_release_scratch(b, stream);
+    cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+    cudaEventRecord(b->done, stream);
+    if (e != cudaSuccess) {
+        wc_batch_free(b);
+        return ctx->cuda_fail(e, "batched count launch");
+    }
+    *out = b;
+    return WC_OK;
+}
+
+// ---------------------------------------------------------------- plans: resident state + CUDA graph
+struct wc_plan {
+    wc_batch *b = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const uint8_t *g_text = nullptr;
+    const uint64_t *g_off = nullptr;
+    const uint32_t *g_cls = nullptr;
+    cudaStream_t g_stream = nullptr;
+    uint64_t graph_launches = 0;
+    bool tuned = false;
+};
+
+// Times the per-document kernel shapes on the plan's own input (three runs
+// each, median) and keeps the fastest per size class.
+static wc_status plan_autotune(wc_plan *pl, const uint8_t *d_text, const uint64_t *d_offsets, const uint32_t *d_class,
+                               cudaStream_t stream) {
+    wc_batch *b = pl->b;
+    wc_ctx *ctx = b->ctx;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto time_shapes = [&](int ss, int sm) -> float {
+        float best = 1e30f;
+        for (int rep = 0; rep < 3; rep++) {
+            cudaEventRecord(e0, stream);
+            batch_enqueue(b, d_text, d_offsets, d_class, stream, ss, sm, nullptr);
+            cudaEventRecord(e1, stream);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best = std::min(best, ms);
+        }
+        return best;
+    };
+    int bs = b->shape_small, bm = b->shape_medium;
+    if (b->nsmall) {
+        float t = 1e30f;
+        for (int s = 0; s <= 2; s++) {
+            float ms = time_shapes(s, bm);
+            if (ms < t) { t = ms; bs = s; }
+        }
+    }
+    if (b->items.size() > b->nsmall) {
+        float t = 1e30f;
+        for (int m = 3; m <= 4; m++) {
+            float ms = time_shapes(bs, m);
+            if (ms < t) { t = ms; bm = m; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->shape_small = ctx->tuned_small = bs;
+    b->shape_medium = ctx->tuned_medium = bm;
+    ctx->tune_save();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? WC_OK : ctx->cuda_fail(e, "autotune");
+}
+
+wc_status wc_plan_create(wc_ctx *ctx, const uint64_t *h_offsets, uint32_t ndocs, uint32_t nclasses, cudaStream_t stream,
+                         wc_plan **out) {
+    if (!ctx || !out || (ndocs && !h_offsets)) return WC_ERR_INVALID_ARG;
+    *out = nullptr;
+    cudaSetDevice(ctx->device);
+    wc_plan *pl = new wc_plan();
+    wc_status st = batch_plan(ctx, h_offsets, ndocs, nclasses, &pl->b);
+    if (st == WC_OK) {
+        pl->b->stream = stream;
+        st = batch_alloc(pl->b, stream);
+    }
+    if (st != WC_OK) {
+        wc_plan_free(pl);
+        return st;
+    }
+    cudaEventCreateWithFlags(&pl->b->done, cudaEventDisableTiming);
+    *out = pl;
+    return WC_OK;
+}
+
+wc_status wc_plan_run(wc_plan *pl, const uint8_t *d_text, const uint64_t *d_offsets, const uint32_t *d_class,
+                      cudaStream_t stream, const wc_batch **out) {
+    if (!pl || !out) return WC_ERR_INVALID_ARG;
+    wc_batch *b = pl->b;
+    wc_ctx *ctx = b->ctx;
+    cudaSetDevice(ctx->device);
+    if (ctx->autotune && !pl->tuned) {
+        wc_status st = plan_autotune(pl, d_text, d_offsets, d_class, stream);
+        if (st != WC_OK) return st;
+    }
+    pl->tuned = true;
+    if (!pl->exec || pl->g_text != d_text || pl->g_off != d_offsets || pl->g_cls != d_class || pl->g_stream != stream) {
+        if (pl->exec) { cudaGraphExecDestroy(pl->exec); pl->exec = nullptr; }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+        uint64_t n = 0;
+        if (e == cudaSuccess) {
+            cudaError_t e2 = batch_enqueue(b, d_text, d_offsets, d_class, stream, b->shape_small, b->shape_medium, &n);
+            e = cudaStreamEndCapture(stream, &graph);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&pl->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return ctx->cuda_fail(e, "capturing the batched count");
+        pl->g_text = d_text;
+        pl->g_off = d_offsets;
+        pl->g_cls = d_class;
+        pl->g_stream = stream;
+        pl->graph_launches = n;
+    }
+    // the plan's batch is rewritten: drop tables built from the previous run
+    for (auto *v : b->views) free_owned_table(v);
+    b->views.clear();
+    for (auto *t : b->class_tables) free_owned_table(t);
+    b->class_tables.clear();
+    free_owned_table(b->global);
+    b->global = nullptr;
+    if (b->gscratch.mem) { ctx->release(b->gscratch.mem, b->gscratch.bytes, stream); b->gscratch.mem = nullptr; }
+    b->tables_built = false;
+    b->synced = false;
+    b->word_bytes = 0;
+    b->stream = stream;
+    cudaError_t e = cudaGraphLaunch(pl->exec, stream);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaGraphLaunch");
+    ctx->launches += pl->graph_launches;
+    cudaEventRecord(b->done, stream);
+    *out = b;
+    return WC_OK;
+}
+
+void wc_plan_free(wc_plan *pl) {
+    if (!pl) return;
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->b) {
+        batch_release_scratch(pl->b, pl->b->stream);
+        wc_batch_free(pl->b);
+    }
+    delete pl;
+}
+
+wc_status wc_batch_status(const wc_batch *b) {
+    if (!b) return WC_ERR_INVALID_ARG;
+    return batch_sync(b);
+}
+
+// ---------------------------------------------------------------- class / global tables
+// One block per document: its entries are added to its class table and to
+// the global table (Sec. 3.3: the counts of a key summed across documents).
+__global__ void k_batch_tables(BatchArgs a, const uint32_t *cls, const GTable *gt, uint32_t nclasses, GTable gg) {
+    const uint32_t d = blockIdx.x;
+    const unsigned long long s = a.doc_start[d];
+    const uint32_t n = a.doc_n[d];
+    const GTable *gc = nclasses ? &gt[cls[d]] : nullptr;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const unsigned long long j = s + i;
+        const unsigned long long c = a.out_cnt[j];
+        const uint32_t r = a.out_lref[j];
+        if (r == 0) {
+            const unsigned long long hi8 = a.out_khi[j], lo8 = a.out_klo[j];
+            uint4 k;
+            k.x = __byte_perm((uint32_t)(hi8 >> 32), 0, 0x0123);
+            k.y = __byte_perm((uint32_t)hi8, 0, 0x0123);
+            k.z = __byte_perm((uint32_t)(lo8 >> 32), 0, 0x0123);
+            k.w = __byte_perm((uint32_t)lo8, 0, 0x0123);
+            table_insert_key(gg, k, c);
+            if (gc) table_insert_key(*gc, k, c);
+        } else {
+            const uint8_t *w = a.arena + a.loff[r - 1];
+            long_insert(gg, w, a.llen[r - 1], c, nullptr, nullptr);
+            if (gc) long_insert(*gc, w, a.llen[r - 1], c, nullptr, nullptr);
+        }
+    }
+}
+
+static wc_status build_tables(wc_batch *b) {
+    if (b->tables_built) return WC_OK;
+    wc_status st = batch_sync(b);
+    if (st != WC_OK) return st;
+    wc_ctx *ctx = b->ctx;
+    cudaStream_t s = b->stream;
+    const uint64_t n = std::max<uint64_t>(b->entries, 1);
+    CapPlan plan;
+    plan.cap8 = pow2_ge(std::max<uint64_t>(1024, 2 * n));
+    plan.cap16 = plan.cap8;
+    plan.caplong = pow2_ge(std::max<uint64_t>(256, 2 * std::min<uint64_t>(n, b->args.lcap)));
+    plan.arena = std::max<uint64_t>(4096, b->args.arena_cap);
+    // one scratch (tables + sort) per class and one for the global table
+    std::vector<CountScratch> cls(b->nclasses);
+    for (uint32_t c = 0; c < b->nclasses; c++)
+        if ((st = scratch_create(ctx, plan, false, s, cls[c])) != WC_OK) return st;
+    if ((st = scratch_create(ctx, plan, false, s, b->gscratch)) != WC_OK) return st;
+    std::vector<wc_table *> tabs(b->nclasses + 1, nullptr);
+    for (uint32_t c = 0; c <= b->nclasses; c++) {
+        if ((st = table_create(ctx, b->gscratch.entries(), plan.caplong, plan.arena,
+                               c < b->nclasses ? 32 : ctx->count_bits, s, &tabs[c])) != WC_OK)
+            return st;
+        tabs[c]->owner = b;
+    }
+    std::vector<GTable> g(std::max<uint32_t>(b->nclasses, 1));
+    for (uint32_t c = 0; c < b->nclasses; c++) g[c] = cls[c].gtable(tabs[c]->dt.d_status);
+    void *dg = nullptr;
+    if ((st = ctx->alloc(&dg, sizeof(GTable) * g.size(), s)) != WC_OK) return st;
+    cudaMemcpyAsync(dg, g.data(), sizeof(GTable) * g.size(), cudaMemcpyHostToDevice, s);
+    const GTable gg = b->gscratch.gtable(tabs[b->nclasses]->dt.d_status);
+    if (b->ndocs) k_batch_tables<<<b->ndocs, 128, 0, s>>>(b->args, b->d_class, static_cast<GTable *>(dg), b->nclasses, gg);
+    cudaError_t e = cudaGetLastError();
+    for (uint32_t c = 0; c < b->nclasses && e == cudaSuccess; c++)
+        e = finish_table(g[c], cls[c].gcap8, cls[c].gcap, cls[c].glcap, cls[c].ss, tabs[c]->dt, s);
+    if (e == cudaSuccess)
+        e = finish_table(gg, b->gscratch.gcap8, b->gscratch.gcap, b->gscratch.glcap, b->gscratch.ss,
+                         tabs[b->nclasses]->dt, s);
+    for (uint32_t c = 0; c < b->nclasses; c++) ctx->release(cls[c].mem, cls[c].bytes, s);
+    ctx->release(dg, sizeof(GTable) * g.size(), s);
+    for (auto *t : tabs) table_mark_done(t, s);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "class/global tables");
+    b->class_tables.assign(tabs.begin(), tabs.begin() + b->nclasses);
+    b->global = tabs[b->nclasses];
+    b->tables_built = true;
+    return WC_OK;
+}
+
+wc_status wc_batch_table(const wc_batch *cb, int kind, uint32_t idx, const wc_table **out) {
+    if (!cb || !out) return WC_ERR_INVALID_ARG;
+    *out = nullptr;
+    wc_batch *b = const_cast<wc_batch *>(cb);
+    cudaSetDevice(b->ctx->device);
+    wc_status st = batch_sync(b);
+    if (st != WC_OK) return st;
+    if (kind == WC_TABLE_DOC) {
+        if (idx >= b->ndocs) return WC_ERR_INVALID_ARG;
+        if (b->views.empty()) b->views.assign(b->ndocs, nullptr);
+        if (!b->views[idx]) {
+            unsigned long long start = 0;
+            uint32_t n = 0;
+            cudaMemcpy(&start, b->args.doc_start + idx, 8, cudaMemcpyDeviceToHost);
+            cudaMemcpy(&n, b->args.doc_n + idx, 4, cudaMemcpyDeviceToHost);
+            if ((st = make_view(b, start, n, &b->views[idx])) != WC_OK) return st;
+        }
+        *out = b->views[idx];
+        return WC_OK;
+    }
+    if ((st = build_tables(b)) != WC_OK) return st;
+    if (kind == WC_TABLE_CLASS) {
+        if (idx >= b->nclasses) return WC_ERR_INVALID_ARG;
+        *out = b->class_tables[idx];
+        return WC_OK;
+    }
+    if (kind == WC_TABLE_GLOBAL) {
+        *out = b->global;
+        return WC_OK;
+    }
+    return WC_ERR_INVALID_ARG;
+}
+
+// ---------------------------------------------------------------- class ratio ranking
+// cout of each class entry = global count - cin (global counts looked up in
+// the global hash tables, read only).
+__device__ unsigned long long lookup_count(const GTable &g, uint4 k, const uint8_t *lw, unsigned long long llen) {
+    if (lw) {
+        const unsigned long long h = long_hash_serial(lw, llen);
+        unsigned long long s = h & g.lmask;
+        for (int probe = 0; probe < kGlobalProbeLimit; probe++) {
+            const LSlot &sl = g.lslots[s];
+            if (sl.h == 0 && sl.addr == 0) return 0;
+            if (sl.h == h) {
+                const uint8_t *rep = reinterpret_cast<const uint8_t *>(sl.addr);
+                bool eq = true;
+                for (unsigned long long i = 0; i < llen && eq; i++) eq = (rep[i] | 0x20u) == (lw[i] | 0x20u);
+                if (eq && !is_letter(rep[llen])) return sl.cnt;
+            }
+            s = (s + 1) & g.lmask;
+        }
+        return 0;
+    }
+    if ((k.z | k.w) == 0u) {
+        const unsigned long long key = ((unsigned long long)k.y << 32) | k.x;
+        unsigned long long s = hash8(key) >> __clzll((long long)g.mask8);
+        for (int probe = 0; probe < kGlobalProbeLimit; probe++) {
+            if (g.slots8[s].key == key) return g.slots8[s].cnt;
+            if (g.slots8[s].key == 0) return 0;
+            s = (s + 1) & g.mask8;
+        }
+        return 0;
+    }
+    unsigned long long s = hash_key(k) & g.mask;
+    for (int probe = 0; probe < kGlobalProbeLimit; probe++) {
+        const uint4 c = g.slots[s].key;
+        if (key_eq(c, k)) return g.slots[s].cnt;
+        if (key_zero(c)) return 0;
+        s = (s + 1) & g.mask;
+    }
+    return 0;
+}
+
+struct RatioArgs {
+    DevTable cls;
+    GTable g;
+    unsigned long long *cin, *cout;
+    uint32_t k;
+    unsigned long long *out_idx;
+    unsigned long long *out_n;
+};
+
+__global__ void k_ratio_prepare(RatioArgs r) {
+    const unsigned long long n = r.cls.d_meta[0];
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long c = static_cast<const uint32_t *>(r.cls.cnt)[i];
+        const uint32_t lr = r.cls.lref[i];
+        const unsigned long long hi8 = r.cls.khi[i], lo8 = r.cls.klo[i];
+        uint4 k;
+        k.x = __byte_perm((uint32_t)(hi8 >> 32), 0, 0x0123);
+        k.y = __byte_perm((uint32_t)hi8, 0, 0x0123);
+        k.z = __byte_perm((uint32_t)(lo8 >> 32), 0, 0x0123);
+        k.w = __byte_perm((uint32_t)lo8, 0, 0x0123);
+        const uint8_t *lw = lr ? r.cls.arena + r.cls.loff[lr - 1] : nullptr;
+        const unsigned long long g = lookup_count(r.g, k, lw, lr ? r.cls.llen[lr - 1] : 0);
+        r.cin[i] = c;
+        r.cout[i] = g >= c ? g - c : 0;  // g < c cannot happen for consistent tables
+    }
+}
+
+// true when entry a ranks above entry b: cin/cout descending (cout = 0 is
+// infinite), then cin descending, then word ascending (the table's own
+// order: equal-count entries appear in word order, so a lower index wins).
+__device__ __forceinline__ bool ratio_better(unsigned long long ia, unsigned long long ca, unsigned long long oa,
+                                             unsigned long long ib, unsigned long long cb, unsigned long long ob) {
+    const bool infa = oa == 0, infb = ob == 0;
+    if (infa != infb) return infa;
+    if (!infa) {
+        // ca/oa vs cb/ob by 128-bit cross products
+        const unsigned long long l_lo = ca * ob, l_hi = __umul64hi(ca, ob);
+        const unsigned long long r_lo = cb * oa, r_hi = __umul64hi(cb, oa);
+        if (l_hi != r_hi) return l_hi > r_hi;
+        if (l_lo != r_lo) return l_lo > r_lo;
+    }
+    if (ca != cb) return ca > cb;
+    return ia < ib;
+}
+
+// k rounds of a block-wide arg-best over the class entries (one block).
+__global__ void __launch_bounds__(1024) k_ratio_select(RatioArgs r, unsigned char *taken) {
+    __shared__ unsigned long long bi[32], bc[32], bo[32];
+    const unsigned long long n = r.cls.d_meta[0];
+    const uint32_t k = (uint32_t)(n < r.k ? n : r.k);
+    for (uint32_t round = 0; round < k; round++) {
+        unsigned long long mi = ~0ull, mc = 0, mo = 0;
+        for (unsigned long long i = threadIdx.x; i < n; i += blockDim.x) {
+            if (taken[i]) continue;
+            if (mi == ~0ull || ratio_better(i, r.cin[i], r.cout[i], mi, mc, mo)) { mi = i; mc = r.cin[i]; mo = r.cout[i]; }
+        }
+        for (int d = 16; d; d >>= 1) {
+            unsigned long long oi = __shfl_xor_sync(0xFFFFFFFFu, mi, d), oc = __shfl_xor_sync(0xFFFFFFFFu, mc, d),
+                               oo = __shfl_xor_sync(0xFFFFFFFFu, mo, d);
+            if (oi != ~0ull && (mi == ~0ull || ratio_better(oi, oc, oo, mi, mc, mo))) { mi = oi; mc = oc; mo = oo; }
+        }
+        if ((threadIdx.x & 31) == 0) { bi[threadIdx.x >> 5] = mi; bc[threadIdx.x >> 5] = mc; bo[threadIdx.x >> 5] = mo; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long xi = ~0ull, xc = 0, xo = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++)
+                if (bi[w] != ~0ull && (xi == ~0ull || ratio_better(bi[w], bc[w], bo[w], xi, xc, xo))) {
+                    xi = bi[w]; xc = bc[w]; xo = bo[w];
+                }
+            r.out_idx[round] = xi;
+            taken[xi] = 1;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *r.out_n = k;
+}
+
+wc_status wc_class_ratio_topk(wc_ctx *ctx, const wc_batch *cb, uint32_t cls, uint32_t k, cudaStream_t stream,
+                              uint64_t *h_idx, uint64_t *h_cin, uint64_t *h_cout, uint32_t *nout) {
+    if (!ctx || !cb || !nout) return WC_ERR_INVALID_ARG;
+    *nout = 0;
+    wc_batch *b = const_cast<wc_batch *>(cb);
+    if (cls >= b->nclasses) return ctx->fail(WC_ERR_INVALID_ARG, "class index out of range");
+    cudaSetDevice(ctx->device);
+    wc_status st = build_tables(b);
+    if (st != WC_OK) return st;
+    const wc_table *ct = b->class_tables[cls];
+    if ((st = table_sync(ct)) != WC_OK) return st;
+    if ((st = table_sync(b->global)) != WC_OK) return st;
+    const uint64_t n = ct->n;
+    void *mem = nullptr;
+    const size_t bytes = n * 17 + (size_t)k * 8 + 64 + 256;
+    if ((st = ctx->alloc(&mem, bytes, stream)) != WC_OK) return st;
+    uint8_t *p = static_cast<uint8_t *>(mem);
+    RatioArgs r;
+    r.cls = ct->dt;
+    r.g = b->gscratch.gtable(b->global->dt.d_status);
+    r.cin = reinterpret_cast<unsigned long long *>(p);
+    r.cout = r.cin + n;
+    r.out_idx = r.cout + n;
+    r.out_n = r.out_idx + k;
+    unsigned char *taken = reinterpret_cast<unsigned char *>(r.out_n + 1);
+    r.k = k;
+    cudaMemsetAsync(taken, 0, n + 1, stream);
+    int sms = ctx->sms;
+    if (n) k_ratio_prepare<<<std::max<int>(1, std::min<int>(sms * 4, (int)((n + 255) / 256))), 256, 0, stream>>>(r);
+    k_ratio_select<<<1, 1024, 0, stream>>>(r, taken);
+    std::vector<unsigned long long> idx(k + 1), cin(n), cout(n);
+    unsigned long long m = 0;
+    cudaMemcpyAsync(&m, r.out_n, 8, cudaMemcpyDeviceToHost, stream);
+    if (k) cudaMemcpyAsync(idx.data(), r.out_idx, k * 8, cudaMemcpyDeviceToHost, stream);
+    if (n) cudaMemcpyAsync(cin.data(), r.cin, n * 8, cudaMemcpyDeviceToHost, stream);
+    if (n) cudaMemcpyAsync(cout.data(), r.cout, n * 8, cudaMemcpyDeviceToHost, stream);
+    cudaError_t e = cudaStreamSynchronize(stream);
+    ctx->release(mem, bytes, stream);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "class ratio ranking");
+    for (unsigned long long i = 0; i < m; i++) {
+        if (h_idx) h_idx[i] = idx[i];
+        if (h_cin) h_cin[i] = cin[idx[i]];
+        if (h_cout) h_cout[i] = cout[idx[i]];
+    }
+    *nout = (uint32_t)m;
+    return WC_OK;
+}
+
+// ---------------------------------------------------------------- bulk export
+wc_status wc_batch_size(const wc_batch *b, uint64_t *nentries, uint64_t *word_bytes) {
+    if (!b) return WC_ERR_INVALID_ARG;
+    wc_status st = batch_sync(b);
+    if (st != WC_OK) return st;
+    wc_batch *mb = const_cast<wc_batch *>(b);
+    if (!mb->word_bytes && mb->entries) {
+        wc_table *v = nullptr;
+        if ((st = make_view(mb, 0, mb->entries, &v)) != WC_OK) return st;
+        st = table_sync(v);
+        mb->word_bytes = v->word_bytes;
+        free_owned_table(v);
+        if (st != WC_OK) return st;
+    }
+    if (nentries) *nentries = mb->entries;
+    if (word_bytes) *word_bytes = mb->word_bytes;
+    return WC_OK;
+}
+
+wc_status wc_batch_export(const wc_batch *cb, uint64_t *h_doc_start, uint32_t *h_doc_n, uint8_t *h_words,
+                          uint64_t *h_word_offsets, uint32_t *h_counts, cudaStream_t stream) {
+    if (!cb) return WC_ERR_INVALID_ARG;
+    wc_batch *b = const_cast<wc_batch *>(cb);
+    cudaSetDevice(b->ctx->device);
+    uint64_t n = 0, wb = 0;
+    wc_status st = wc_batch_size(b, &n, &wb);
+    if (st != WC_OK) return st;
+    cudaError_t e = cudaSuccess;
+    if (h_doc_start && b->ndocs)
+        e = cudaMemcpyAsync(h_doc_start, b->args.doc_start, 8ull * b->ndocs, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess && h_doc_n && b->ndocs)
+        e = cudaMemcpyAsync(h_doc_n, b->args.doc_n, 4ull * b->ndocs, cudaMemcpyDeviceToHost, stream);
+    if (e != cudaSuccess) return b->ctx->cuda_fail(e, "batch export");
+    if (!n) {
+        if (h_word_offsets) h_word_offsets[0] = 0;
+        e = cudaStreamSynchronize(stream);
+        return e == cudaSuccess ? WC_OK : b->ctx->cuda_fail(e, "batch export");
+    }
+    wc_table *v = nullptr;
+    if ((st = make_view(b, 0, n, &v)) != WC_OK) return st;
+    st = wc_table_export(v, h_words, h_word_offsets, h_counts, stream);
+    free_owned_table(v);
+    return st;
+}
+
+void wc_batch_free(wc_batch *b) {
+    if (!b) return;
+    wc_ctx *ctx = b->ctx;
+    cudaSetDevice(ctx->device);
+    if (b->done) cudaEventSynchronize(b->done);
+    for (auto *v : b->views) free_owned_table(v);
+    for (auto *t : b->class_tables) free_owned_table(t);
+    free_owned_table(b->global);
+    if (b->gscratch.mem) ctx->release(b->gscratch.mem, b->gscratch.bytes, b->stream);
+    ctx->release(b->mem, b->bytes, b->stream);
+    if (b->done) cudaEventDestroy(b->done);
+    delete b;
+}

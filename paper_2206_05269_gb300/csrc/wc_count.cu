@@ -3,248 +3,592 @@
 // The paper maps on the CPU (Sec. 3.1: remove punctuation, lowercase, split,
 // one dictionary per document) and reduces on the GPU (Sec. 3.3); its
 // conclusion (Sec. 5.2) asks for a GPU dictionary so the whole map and reduce
-// can run on the device.  This kernel is that design for one document:
+// run on the device.  This file is that design for one document:
 //
-//  1. a persistent block stages a chunk of text (plus 16 bytes before and 64
-//     after) into shared memory with 16-byte loads;
-//  2. each warp classifies 512-byte strips: one 16-bit letter mask per lane
-//     (SWAR), word starts = letter & !previous-letter, with the previous
-//     byte carried across lanes, strips and chunk edges; a word belongs to
-//     the chunk that holds its first byte;
-//  3. words of <= 16 letters are queued per warp and processed 32 at a time:
-//     16-byte lowercased key, 64-bit hash, insert into the block's
-//     shared-memory table; a full table or a long probe spills the word to
-//     the global open-addressing table;
-//  4. words of >= 17 letters go to the global long-word table;
-//  5. at the end each block flushes its shared table into the global table.
+//  0. Head selection (texts of 16 MB or more): a sampling pass counts 64
+//     evenly spaced 64 KB pieces into a small table; the most frequent
+//     words of at most 8 letters are placed in a bucketised two-choice hash
+//     image (4 keys per bucket, a key lives in one of two buckets).
+//  1. One persistent 512-thread block per SM copies that image into shared
+//     memory (keys read-only, counts zeroed) and walks its chunks through a
+//     ring of four buffers.  Each chunk window (16 bytes before, 64 after,
+//     16-byte aligned in absolute address space) is staged by a TMA bulk
+//     copy that completes a "full" mbarrier; windows that touch the
+//     document's edges are staged by plain loads with the outside masked to
+//     spaces (a document edge separates words).  Warps never wait for each
+//     other: each warp releases a buffer when its words there are consumed,
+//     and the last warp to release it issues the copy of the chunk four
+//     places ahead.
+//  2. A warp classifies 512-byte strips: one 16-bit letter mask per lane
+//     (SWAR), word starts = letter & !previous letter, the previous byte
+//     carried across lanes, strips and chunks; a word belongs to the chunk
+//     holding its first byte and is read through the window's lookahead.
+//  3. Words of <= 16 letters are queued per warp and processed 32 at a time:
+//     a word of <= 8 letters in the head image adds 1 to its shared count
+//     (two bucket probes); every other word goes to a per-warp tail queue,
+//     flushed 32 at a time into the global 8-byte-key or 16-byte-key table
+//     (plain load of the key, fire-and-forget reduction; CAS only the first
+//     time a word is seen).
+//  4. Words of 17+ letters are queued per warp and inserted 32 at a time,
+//     one per lane, into the global long-word table.
+//  5. At the end each block adds its head counts into the global table.
+#include <algorithm>
+
 #include "wc_internal.h"
 
 namespace wc {
 
-struct CountArgs {
+constexpr int kBlock = 512;           // threads of the main counting kernel
+constexpr int kWarps = kBlock / 32;
+constexpr int kChunk = kWarps * 512;  // bytes per chunk: one 512-byte strip per warp
+constexpr int kStages = 4;            // chunk buffers in flight per block
+constexpr int kLead = 16;             // window bytes before the chunk
+constexpr int kWinB = kChunk + 96;    // lead + chunk + 64 lookahead + 16 slack
+constexpr int kTokCap = 32 + 256;     // per-warp word queue (< 32 left + <= 256 per strip)
+constexpr int kTailCap = 64;          // per-warp tail queue
+constexpr int kLongCap = 48;          // per-warp queue of words of 17+ letters (< 16 left + <= 32 per step)
+constexpr int kHeadBuckets = 3072;    // 12288 head slots
+constexpr int kSamplePieces = 64;
+constexpr int kSamplePieceBytes = 65536;
+constexpr uint64_t kHeadMinBytes = 16ull << 20;
+constexpr unsigned long long kSampleSlots = 1ull << 19;
+
+struct Count2Args {
     const uint8_t *text;
-    unsigned long long lo, hi;
+    unsigned long long lo, hi;        // document bytes text[lo, hi)
+    uintptr_t base_al;                // absolute address of chunk 0 (16-aligned, <= text + lo)
     uint32_t nchunks;
+    uint32_t piece_chunks;            // chunks per piece (sampling) or nchunks
+    unsigned long long piece_stride;  // bytes between pieces (sampling) or 0
     GTable g;
+    const unsigned long long *head;   // head image (nb * 4 keys) or null
+    uint32_t nb;
 };
 
+// ---------------------------------------------------------------- TMA + mbarrier
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ unsigned long long policy_evict_first() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// Arms `bar` for `bytes` and starts the bulk copy global -> shared.
+__device__ __forceinline__ void tma_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
+                                         unsigned long long policy) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+        : "memory");
+}
+// Bounded wait for the phase `parity` of `bar`; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t a = smem_addr(bar);
+    for (uint32_t it = 0; it < (1u << 22); it++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------- staging
 __device__ __forceinline__ uint4 spaces16() { return make_uint4(0x20202020u, 0x20202020u, 0x20202020u, 0x20202020u); }
 
-// Loads the aligned 16-byte block at address a0 if it holds any byte of the
-// valid range [vb, ve) (then it lies inside the caller's allocation pages);
-// otherwise returns spaces.
-__device__ __forceinline__ uint4 load_block(uintptr_t a0, uintptr_t vb, uintptr_t ve) {
-    if (a0 < ve && a0 + 16 > vb) return ld_stream16(reinterpret_cast<const void *>(a0));
-    return spaces16();
-}
-
-// bytes [m, m+16) of the 32-byte concatenation (w0, w1), m in 1..15
-__device__ __forceinline__ uint4 shift_bytes(uint4 w0, uint4 w1, uint32_t m) {
-    uint32_t q = m >> 2, sh = (m & 3u) * 8u;
-    uint32_t s0, s1, s2, s3, s4;
-    if (q == 0) { s0 = w0.x; s1 = w0.y; s2 = w0.z; s3 = w0.w; s4 = w1.x; }
-    else if (q == 1) { s0 = w0.y; s1 = w0.z; s2 = w0.w; s3 = w1.x; s4 = w1.y; }
-    else if (q == 2) { s0 = w0.z; s1 = w0.w; s2 = w1.x; s3 = w1.y; s4 = w1.z; }
-    else { s0 = w0.w; s1 = w1.x; s2 = w1.y; s3 = w1.z; s4 = w1.w; }
-    uint4 r;
-    r.x = __funnelshift_r(s0, s1, sh);
-    r.y = __funnelshift_r(s1, s2, sh);
-    r.z = __funnelshift_r(s2, s3, sh);
-    r.w = __funnelshift_r(s3, s4, sh);
-    return r;
-}
-
-// Replaces the bytes of a 16-byte word (logical positions q0..q0+15) that lie
-// outside [vlo, vhi) by spaces: a document edge is a separator.
-__device__ __forceinline__ uint4 mask_outside(uint4 v, long long q0, long long vlo, long long vhi) {
-    long long a = vlo - q0, b = vhi - q0;
-    int klo = (int)(a < 0 ? 0 : (a > 16 ? 16 : a));
-    int khi = (int)(b < 0 ? 0 : (b > 16 ? 16 : b));
-    uint32_t m0 = byte_keep_mask(khi) & ~byte_keep_mask(klo);
-    uint32_t m1 = byte_keep_mask(khi - 4) & ~byte_keep_mask(klo - 4);
-    uint32_t m2 = byte_keep_mask(khi - 8) & ~byte_keep_mask(klo - 8);
-    uint32_t m3 = byte_keep_mask(khi - 12) & ~byte_keep_mask(klo - 12);
-    v.x = (v.x & m0) | (0x20202020u & ~m0);
-    v.y = (v.y & m1) | (0x20202020u & ~m1);
-    v.z = (v.z & m2) | (0x20202020u & ~m2);
-    v.w = (v.w & m3) | (0x20202020u & ~m3);
-    return v;
-}
-
-// win[j] = text[ws + j] for ws + j in [vlo, vhi), else ' ', for j < nbytes (multiple of 16).
-template <int BLOCK>
-__device__ __forceinline__ void stage_window(uint8_t *win, int nbytes, const uint8_t *text, long long ws,
-                                             unsigned long long vlo, unsigned long long vhi) {
-    const uintptr_t base = reinterpret_cast<uintptr_t>(text);
-    const uintptr_t vb = base + vlo, ve = base + vhi;
-    for (int t = threadIdx.x; t < nbytes / 16; t += BLOCK) {
-        long long q0 = ws + 16LL * t;
-        uintptr_t a = base + (uintptr_t)q0;  // modular arithmetic; only dereferenced when valid
-        uintptr_t a0 = a & ~(uintptr_t)15;
-        uint32_t m = (uint32_t)(a & 15);
-        uint4 w0 = load_block(a0, vb, ve);
-        uint4 out = w0;
-        if (m) out = shift_bytes(w0, load_block(a0 + 16, vb, ve), m);
-        if (q0 < (long long)vlo || q0 + 16 > (long long)vhi) out = mask_outside(out, q0, (long long)vlo, (long long)vhi);
-        *reinterpret_cast<uint4 *>(win + 16 * t) = out;
+// Plain-load staging of the window at absolute (aligned) address w0: bytes
+// outside [vb, ve) become spaces; 16-byte blocks holding no valid byte are
+// not read at all.
+__device__ __forceinline__ void stage_masked(uint8_t *win, uintptr_t w0, uintptr_t vb, uintptr_t ve) {
+    for (int t = threadIdx.x; t < kWinB / 16; t += blockDim.x) {
+        uintptr_t a = w0 + 16 * (uintptr_t)t;
+        uint4 v = spaces16();
+        if (a < ve && a + 16 > vb) {
+            v = ld_stream16(reinterpret_cast<const void *>(a));
+            if (a < vb || a + 16 > ve) v = mask_outside_doc(v, a, vb, ve);
+        }
+        *reinterpret_cast<uint4 *>(win + 16 * t) = v;
     }
 }
 
-// Length of the letter run starting at text[pos] (pos is a letter), capped at hi.
-__device__ __forceinline__ unsigned long long run_length(const uint8_t *text, unsigned long long pos,
-                                                         unsigned long long hi) {
-    unsigned long long e = pos;
-    while (e < hi && is_letter(text[e])) e++;
-    return e - pos;
+// ---------------------------------------------------------------- keys
+// 8 lowercased bytes of win[p, p+len), zero padded (len <= 8), little endian.
+__device__ __forceinline__ unsigned long long load_key8(const uint8_t *win, uint32_t p, uint32_t len) {
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(win + (p & ~3u));
+    const uint32_t sh = (p & 3u) * 8u;
+    const uint32_t a0 = w[0], a1 = w[1], a2 = w[2];
+    const int n = (int)len;
+    uint32_t lo = (__funnelshift_r(a0, a1, sh) | 0x20202020u) & byte_keep_mask(n);
+    uint32_t hi = (__funnelshift_r(a1, a2, sh) | 0x20202020u) & byte_keep_mask(n - 4);
+    return ((unsigned long long)hi << 32) | lo;
 }
 
-template <int BLOCK, int CHUNK, int LOG_C1>
-struct CountCfg {
-    static constexpr int WARPS = BLOCK / 32;
-    static constexpr int STRIPS = CHUNK / 512;
-    static constexpr int SPW = STRIPS / WARPS;
-    static constexpr int LEAD = 16;
-    static constexpr int WIN = LEAD + CHUNK + 64 + 16;
-    static constexpr int TOKCAP = 32 + 256;
-    static constexpr int C1 = 1 << LOG_C1;
-    static constexpr size_t SMEM = (size_t)WIN + (size_t)C1 * 16 + (size_t)C1 * 8 + (size_t)WARPS * TOKCAP * 4 + 16;
-    static_assert(STRIPS % WARPS == 0, "chunk must split evenly into warp strips");
-    static_assert(WIN % 16 == 0, "window must be 16-byte aligned");
+__device__ __forceinline__ uint32_t head_bucket(unsigned long long key, unsigned long long mul, uint32_t nb) {
+    return __umulhi((uint32_t)((key * mul) >> 32), nb);
+}
+constexpr unsigned long long kHeadMulA = 0x9E3779B97F4A7C15ull;
+constexpr unsigned long long kHeadMulB = 0xC2B2AE3D27D4EB4Full;
+
+// Slot of key in the shared head image, or -1 (two buckets of four).
+__device__ __forceinline__ int head_find(const unsigned long long *hkey, unsigned long long key, uint32_t nb,
+                                         uint32_t *slot) {
+    uint32_t bk = head_bucket(key, kHeadMulA, nb);
+    const ulonglong2 *hb = reinterpret_cast<const ulonglong2 *>(hkey + bk * 4);
+    ulonglong2 u0 = hb[0], u1 = hb[1];
+    int q = u0.x == key ? 0 : u0.y == key ? 1 : u1.x == key ? 2 : u1.y == key ? 3 : -1;
+    if (q < 0) {
+        bk = head_bucket(key, kHeadMulB, nb);
+        hb = reinterpret_cast<const ulonglong2 *>(hkey + bk * 4);
+        u0 = hb[0];
+        u1 = hb[1];
+        q = u0.x == key ? 0 : u0.y == key ? 1 : u1.x == key ? 2 : u1.y == key ? 3 : -1;
+    }
+    *slot = bk * 4 + (uint32_t)(q < 0 ? 0 : q);
+    return q;
+}
+
+// Run length of the letters at w (w is a letter), capped at `end`: the warp
+// scans 32 bytes per step.  All lanes call with the same w.
+__device__ __forceinline__ unsigned long long run_length_warp(const uint8_t *w, const uint8_t *end) {
+    const int lane = threadIdx.x & 31;
+    for (unsigned long long off = 0;; off += 32) {
+        const uint8_t *q = w + off + lane;
+        uint32_t b = q < end ? *q : 0x20u;
+        uint32_t m = __ballot_sync(kFull, !is_letter(b));
+        if (m) return off + (unsigned long long)(__ffs(m) - 1);
+    }
+}
+
+// ---------------------------------------------------------------- kernel
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+template <bool SAMPLE>
+struct Counter2 {
+    const Count2Args &a;
+    const unsigned long long *hkey;
+    uint32_t *hcnt;
+    uint4 *tailq;
+    uint32_t nslots;
+    uint32_t tailn;
+    int lane;
+
+    // One queued word per lane (have = lane holds one): a word of <= 8
+    // letters found in the head image adds 1 to its shared count; any other
+    // word is pushed to the tail queue, which is flushed 32 at a time.
+    __device__ __forceinline__ void word(const uint8_t *win, bool have, uint32_t e) {
+        bool tail = false;
+        uint4 tk = make_uint4(0, 0, 0, 0);
+        if (have) {
+            const uint32_t p = e >> 5, len = e & 31u;
+            if (len <= 8) {
+                const unsigned long long key = load_key8(win, p, len);
+                tail = true;
+                if (nslots) {
+                    uint32_t slot;
+                    if (head_find(hkey, key, a.nb, &slot) >= 0) {
+                        atomicAdd(hcnt + slot, 1u);
+                        tail = false;
+                    }
+                }
+                tk = make_uint4((uint32_t)key, (uint32_t)(key >> 32), 0u, 0u);
+            } else if (!SAMPLE) {
+                tail = true;
+                tk = load_key16(win, p, len);
+            }
+        }
+        const uint32_t tb = __ballot_sync(kFull, tail);
+        if (tail) tailq[tailn + __popc(tb & ((1u << lane) - 1u))] = tk;
+        tailn += __popc(tb);
+        __syncwarp();
+        if (tailn >= 32) {
+            tailn -= 32;
+            insert(tailq[tailn + lane]);
+            __syncwarp();
+        }
+    }
+    __device__ __forceinline__ void insert(uint4 k) {
+        if (!SAMPLE) table_insert_key(a.g, k, 1ull);
+        else global_insert8(a.g, ((unsigned long long)k.y << 32) | k.x, 1ull);
+    }
 };
 
-template <int BLOCK, int CHUNK, int LOG_C1, int MINB>
-__global__ void __launch_bounds__(BLOCK, MINB) k_count_global(CountArgs a) {
-    using C = CountCfg<BLOCK, CHUNK, LOG_C1>;
-    extern __shared__ __align__(16) uint8_t smem[];
-    uint8_t *win = smem;
-    uint4 *skey = reinterpret_cast<uint4 *>(smem + C::WIN);
-    uint32_t *stag = reinterpret_cast<uint32_t *>(skey + C::C1);
-    uint32_t *scnt = stag + C::C1;
-    uint32_t *tokall = scnt + C::C1;
-    uint32_t *nfill = tokall + C::WARPS * C::TOKCAP;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *tok = tokall + warp * C::TOKCAP;
-    STable st{stag, skey, scnt, nfill, (uint32_t)(C::C1 - 1), (uint32_t)(C::C1 * 7 / 10)};
+template <bool SAMPLE>
+struct Ring {
+    const Count2Args &a;
+    uint8_t *buf;          // kStages x kWinB
+    uint64_t *full;        // kStages mbarriers
+    uint32_t *done;        // kStages release counters
+    uintptr_t vb, ve;
+    unsigned long long policy;
 
-    for (int i = threadIdx.x; i < C::C1; i += BLOCK) stag[i] = 0u;
-    if (threadIdx.x == 0) *nfill = 0u;
+    __device__ __forceinline__ uintptr_t win_start(uint32_t c) const {
+        uint32_t q = c / a.piece_chunks, r = c % a.piece_chunks;
+        return a.base_al + (uintptr_t)q * a.piece_stride + (uintptr_t)r * kChunk - kLead;
+    }
+    __device__ __forceinline__ bool interior(uintptr_t w0) const { return w0 >= vb && w0 + kWinB <= ve; }
 
-    auto process = [&](uint32_t e) {
-        uint32_t p = e >> 5, len = e & 31u;
-        uint4 k = load_key16(win, p, len);
-        uint64_t h = hash_key(k);
-        if (!shared_insert(st, k, h, 1u, 8)) global_insert(a.g, k, h, 1ull);
-    };
-
-    for (uint32_t c = blockIdx.x; c < a.nchunks; c += gridDim.x) {
-        const unsigned long long lo = a.lo + (unsigned long long)c * CHUNK;
-        const long long ws = (long long)lo - C::LEAD;
-        __syncthreads();  // previous chunk's window reads are done
-        stage_window<BLOCK>(win, C::WIN, a.text, ws, a.lo, a.hi);
-        __syncthreads();
-
-        uint32_t tcount = 0;
-        const int s0 = warp * C::SPW;
-        uint32_t prevL = is_letter(win[C::LEAD + 512 * s0 - 1]) ? 1u : 0u;
-        uint32_t L = letter_mask16(*reinterpret_cast<const uint4 *>(win + C::LEAD + 512 * s0 + 16 * lane));
-#pragma unroll 1
-        for (int k = 0; k < C::SPW; k++) {
-            const int sbase = C::LEAD + 512 * (s0 + k);
-            int nidx = sbase + 512 + 16 * lane;
-            if (nidx > C::LEAD + CHUNK) nidx = C::LEAD + CHUNK;  // past the chunk only lane 0 matters
-            const uint32_t Ln = letter_mask16(*reinterpret_cast<const uint4 *>(win + nidx));
-            const uint32_t up = __shfl_up_sync(kFull, L, 1);
-            const uint32_t dn = __shfl_down_sync(kFull, L, 1);
-            const uint32_t n0 = __shfl_sync(kFull, Ln, 0);
-            const uint32_t pbit = lane == 0 ? prevL : ((up >> 15) & 1u);
-            const uint32_t W = L | ((lane == 31 ? n0 : dn) << 16);
-            const uint32_t S = L & ~((L << 1) | pbit) & 0xFFFFu;
-            prevL = (__shfl_sync(kFull, L, 31) >> 15) & 1u;
-            uint32_t x = W;
-            x &= x >> 1; x &= x >> 2; x &= x >> 4; x &= x >> 8; x &= W >> 16;  // 17-letter runs
-            uint32_t Ss = S & ~x, Sl = S & x;
-
-            const uint32_t c1 = __popc(Ss);
-            uint32_t incl = c1;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                uint32_t t = __shfl_up_sync(kFull, incl, d);
-                if (lane >= d) incl += t;
+    // The calling warp stages this block's i-th chunk into buffer i % kStages.
+    __device__ __forceinline__ void produce(uint32_t i) {
+        const uint32_t c = blockIdx.x + i * gridDim.x;
+        if (c >= a.nchunks) return;
+        const int b = (int)(i % kStages);
+        const uintptr_t w0 = win_start(c);
+        const int lane = threadIdx.x & 31;
+        if (interior(w0)) {
+            if (lane == 0) {
+                fence_proxy_async();
+                tma_load(buf + b * kWinB, reinterpret_cast<const void *>(w0), kWinB, &full[b], policy);
             }
-            const uint32_t total = __shfl_sync(kFull, incl, 31);
-            uint32_t off = tcount + incl - c1;
-            const uint32_t pbase = (uint32_t)(sbase + 16 * lane);
-            while (Ss) {
-                int j = __ffs(Ss) - 1;
-                Ss &= Ss - 1;
-                uint32_t len = (uint32_t)__ffs(~(W >> j)) - 1u;
-                tok[off++] = ((pbase + (uint32_t)j) << 5) | len;
-            }
-            tcount += total;
-            while (Sl) {  // rare: words of 17+ letters
-                int j = __ffs(Sl) - 1;
-                Sl &= Sl - 1;
-                unsigned long long pos = (unsigned long long)(ws + (long long)pbase + j);
-                unsigned long long len = run_length(a.text, pos, a.hi);
-                long_insert(a.g, a.text + pos, len, 1ull);
+        } else {
+            uint8_t *win = buf + b * kWinB;
+            for (int t = lane; t < kWinB / 16; t += 32) {
+                uintptr_t ad = w0 + 16 * (uintptr_t)t;
+                uint4 v = spaces16();
+                if (ad < ve && ad + 16 > vb) {
+                    v = ld_stream16(reinterpret_cast<const void *>(ad));
+                    if (ad < vb || ad + 16 > ve) v = mask_outside_doc(v, ad, vb, ve);
+                }
+                *reinterpret_cast<uint4 *>(win + 16 * t) = v;
             }
             __syncwarp();
-            uint32_t b = 0;
-            for (; b + 32 <= tcount; b += 32) process(tok[b + lane]);
-            const uint32_t rem = tcount - b;
-            if (b) {
-                uint32_t e = lane < rem ? tok[b + lane] : 0u;
-                __syncwarp();
-                if (lane < rem) tok[lane] = e;
-                __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                mbar_arrive(&full[b]);
             }
-            tcount = rem;
-            L = Ln;
         }
-        if ((uint32_t)lane < tcount) process(tok[lane]);
+        __syncwarp();
+    }
+    // The calling warp is done with chunk i; the last warp refills the buffer.
+    __device__ __forceinline__ void release(uint32_t i) {
+        const int b = (int)(i % kStages);
+        const int lane = threadIdx.x & 31;
+        __syncwarp();
+        uint32_t last = 0;
+        if (lane == 0) {
+            __threadfence_block();
+            last = atomicAdd(&done[b], 1u) == kWarps - 1;
+            if (last) done[b] = 0;
+        }
+        if (__shfl_sync(kFull, last, 0)) produce(i + kStages);
+    }
+};
+
+template <bool SAMPLE>
+__global__ void __launch_bounds__(kBlock, 1) k_count2(Count2Args a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    unsigned long long *hkey = reinterpret_cast<unsigned long long *>(smem);        // nb*4
+    uint32_t *hcnt = reinterpret_cast<uint32_t *>(hkey + kHeadBuckets * 4);           // nb*4
+    uint8_t *ring = reinterpret_cast<uint8_t *>(hcnt + kHeadBuckets * 4);             // kStages x kWinB
+    uint32_t *tokall = reinterpret_cast<uint32_t *>(ring + kStages * kWinB);         // warps x kTokCap
+    uint4 *tailall = reinterpret_cast<uint4 *>(tokall + kWarps * kTokCap);           // warps x kTailCap
+    uint4 *longall = tailall + kWarps * kTailCap;                                     // warps x kLongCap
+    uint64_t *full = reinterpret_cast<uint64_t *>(longall + kWarps * kLongCap);     // kStages
+    uint32_t *done = reinterpret_cast<uint32_t *>(full + kStages);                   // kStages
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *tok = tokall + warp * kTokCap;
+    uint4 *longq = longall + warp * kLongCap;
+    const uint32_t nslots = a.head ? a.nb * 4 : 0;
+    Counter2<SAMPLE> ctr{a, hkey, hcnt, tailall + warp * kTailCap, nslots, 0u, lane};
+
+    for (uint32_t i = threadIdx.x; i < nslots; i += kBlock) {
+        hkey[i] = a.head[i];
+        hcnt[i] = 0u;
+    }
+    if (threadIdx.x < kStages) done[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < kStages; b++) mbar_init(&full[b], 1);
+        fence_barrier_init();
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < C::C1; i += BLOCK) {
-        if (stag[i] > 1u) {
-            uint4 k = skey[i];
-            global_insert(a.g, k, hash_key(k), (unsigned long long)scnt[i]);
+
+    Ring<SAMPLE> rg{a, ring, full, done, reinterpret_cast<uintptr_t>(a.text) + a.lo,
+                    reinterpret_cast<uintptr_t>(a.text) + a.hi, policy_evict_first()};
+    const uint8_t *begin = reinterpret_cast<const uint8_t *>(rg.vb);
+    const uint8_t *end = reinterpret_cast<const uint8_t *>(rg.ve);
+    if (warp == 0)
+        for (uint32_t i = 0; i < kStages; i++) rg.produce(i);
+
+    uint32_t tcount = 0;   // queued words (warp-uniform)
+    uint32_t tprev = 0;    // how many of them belong to the previous chunk
+    uint32_t longn = 0;    // queued long words
+    bool timed_out = false;
+    auto flush_long = [&](uint32_t base, uint32_t n) {
+        if ((uint32_t)lane < n) {
+            uint4 e = longq[base + lane];
+            const uint8_t *w = reinterpret_cast<const uint8_t *>(((unsigned long long)e.y << 32) | e.x);
+            unsigned long long len = e.z;
+            if (len == 0) {  // longer than the window showed: scan to the end of the run
+                len = 17;
+                while (w + len < end && is_letter(w[len])) len++;
+            }
+            long_insert(a.g, w, len, 1ull, begin, end);
+        }
+        __syncwarp();
+    };
+
+    uint32_t i = 0;
+    for (uint32_t c = blockIdx.x; c < a.nchunks; c += gridDim.x, i++) {
+        const int b = (int)(i % kStages);
+        if (!mbar_wait(&full[b], (i / kStages) & 1u)) { timed_out = true; break; }
+        const uint8_t *win = ring + b * kWinB;
+        const uintptr_t w0 = rg.win_start(c);
+        // ---- this warp's 512-byte strip
+        const int sbase = kLead + 512 * warp;
+        const uint32_t prevL = is_letter(win[sbase - 1]) ? 1u : 0u;  // the window holds the byte before
+        const uint32_t L = letter_mask16(*reinterpret_cast<const uint4 *>(win + sbase + 16 * lane));
+        const uint32_t Ln = letter_mask16(*reinterpret_cast<const uint4 *>(win + sbase + 512));  // first 16 bytes after
+        const uint32_t up = __shfl_up_sync(kFull, L, 1);
+        const uint32_t dn = __shfl_down_sync(kFull, L, 1);
+        const uint32_t pbit = lane == 0 ? prevL : ((up >> 15) & 1u);
+        const uint32_t W = L | ((lane == 31 ? Ln : dn) << 16);
+        const uint32_t S = L & ~((L << 1) | pbit) & 0xFFFFu;
+        uint32_t x = W;
+        x &= x >> 1; x &= x >> 2; x &= x >> 4; x &= x >> 8; x &= W >> 16;  // starts of 17+ letter runs
+        uint32_t Ss = S & ~x, Sl = S & x;
+
+        const uint32_t c1 = __popc(Ss);
+        uint32_t incl = c1;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t t = __shfl_up_sync(kFull, incl, d);
+            if (lane >= d) incl += t;
+        }
+        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        uint32_t off = tcount + incl - c1;
+        const uint32_t pbase = (uint32_t)(sbase + 16 * lane);
+        const uint32_t btag = (uint32_t)b << 19;
+        while (Ss) {
+            int j = __ffs(Ss) - 1;
+            Ss &= Ss - 1;
+            uint32_t len = (uint32_t)__ffs(~(W >> j)) - 1u;
+            tok[off++] = btag | ((pbase + (uint32_t)j) << 5) | len;
+        }
+        const uint32_t tnew = total;
+        tcount += total;
+        if (!SAMPLE && __any_sync(kFull, Sl != 0)) {
+            while (__any_sync(kFull, Sl != 0)) {
+                const bool act = Sl != 0;
+                uint4 e = make_uint4(0, 0, 0, 0);
+                if (act) {
+                    int j = __ffs(Sl) - 1;
+                    Sl &= Sl - 1;
+                    unsigned long long wa = (unsigned long long)(w0 + pbase + (uint32_t)j);
+                    uint32_t run = (uint32_t)__ffs(~(W >> j)) - 1u;  // letters seen in W (<= 32 - j)
+                    e = make_uint4((uint32_t)wa, (uint32_t)(wa >> 32), run < 32u - (uint32_t)j ? run : 0u, 0u);
+                }
+                const uint32_t lb = __ballot_sync(kFull, act);
+                if (act) longq[longn + __popc(lb & ((1u << lane) - 1u))] = e;
+                longn += __popc(lb);
+                __syncwarp();
+                if (longn >= 16) {  // insert them all, one per lane, 32 at a time
+                    flush_long(0, longn < 32 ? longn : 32);
+                    if (longn > 32) flush_long(32, longn - 32);
+                    longn = 0;
+                }
+            }
+        }
+        __syncwarp();
+        // ---- queued words, 32 at a time
+        uint32_t bq = 0;
+        for (; bq + 32 <= tcount; bq += 32) {
+            const uint32_t e = tok[bq + lane];
+            ctr.word(ring + ((e >> 19) & 3u) * kWinB, true, e & 0x7FFFFu);
+        }
+        uint32_t rem = tcount - bq;
+        const uint32_t old_left = tprev > bq ? tprev - bq : 0u;
+        if (old_left) {  // words of the previous chunk still queued: finish them all now
+            const uint32_t e = (uint32_t)lane < rem ? tok[bq + lane] : 0u;
+            ctr.word(ring + ((e >> 19) & 3u) * kWinB, (uint32_t)lane < rem, e & 0x7FFFFu);
+            rem = 0;
+        } else if (bq) {
+            uint32_t e = (uint32_t)lane < rem ? tok[bq + lane] : 0u;
+            __syncwarp();
+            if ((uint32_t)lane < rem) tok[lane] = e;
+            __syncwarp();
+        }
+        tcount = rem;
+        tprev = rem < tnew ? rem : tnew;
+        if (i > 0) rg.release(i - 1);
+    }
+    // ---- drain: queued words of the last chunk, then the tail and long queues
+    if (!timed_out) {
+        const uint32_t e = (uint32_t)lane < tcount ? tok[lane] : 0u;
+        ctr.word(ring + ((e >> 19) & 3u) * kWinB, (uint32_t)lane < tcount, e & 0x7FFFFu);
+        if (!SAMPLE) {
+            flush_long(0, longn < 32 ? longn : 32);
+            if (longn > 32) flush_long(32, longn - 32);
+        }
+        if ((uint32_t)lane < ctr.tailn) ctr.insert(ctr.tailq[lane]);
+        __syncwarp();
+    }
+    if (__syncthreads_or(timed_out)) {
+        if (threadIdx.x == 0) {
+            atomicOr(a.g.status, ST_TIMEOUT);
+            for (int b = 0; b < kStages; b++) mbar_wait(&full[b], 0u);  // bounded: let copies in flight land
+        }
+        return;
+    }
+    for (uint32_t k = threadIdx.x; k < nslots; k += kBlock)
+        if (hcnt[k]) global_insert8(a.g, hkey[k], (unsigned long long)hcnt[k]);
+}
+
+constexpr size_t kCountSmem = (size_t)kHeadBuckets * 4 * 8 + (size_t)kHeadBuckets * 4 * 4 + kStages * (size_t)kWinB +
+                              (size_t)kWarps * kTokCap * 4 + (size_t)kWarps * kTailCap * 16 +
+                              (size_t)kWarps * kLongCap * 16 + kStages * 8 + kStages * 4;
+static_assert(kCountSmem <= 227 * 1024, "counting kernel shared memory");
+
+// ---------------------------------------------------------------- head selection
+// Histogram of sample counts (clamped to 4095).
+__global__ void k_head_hist(const G8Slot *s, unsigned long long cap, uint32_t *hist) {
+    __shared__ uint32_t h[4096];
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        unsigned long long c = s[i].cnt;
+        if (s[i].key && c >= 2) atomicAdd(&h[c > 4095 ? 4095 : c], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// Smallest count threshold t >= 2 that keeps at most kmax words.
+__global__ void k_head_threshold(const uint32_t *hist, uint32_t kmax, uint32_t *meta) {
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0, t = 4096;
+        for (int c = 4095; c >= 2; c--) {
+            if (acc + hist[c] > kmax) break;
+            acc += hist[c];
+            t = (uint32_t)c;
+        }
+        meta[0] = t;  // threshold
+        meta[1] = 0;  // candidates
+    }
+}
+
+__global__ void k_head_collect(const G8Slot *s, unsigned long long cap, uint32_t *meta, unsigned long long *cand,
+                               uint32_t kmax) {
+    const uint32_t t = meta[0];
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        unsigned long long c = s[i].cnt;
+        if (s[i].key && c >= t) {
+            uint32_t k = atomicAdd(&meta[1], 1u);
+            if (k < kmax) cand[k] = s[i].key;
         }
     }
 }
 
-// Default shape: 256 threads, 8 KB chunks, 2048-slot level-1 table.
-constexpr int kBlock = 256, kChunk = 8192, kLogC1 = 11, kMinBlocks = 3;
+// Two-choice placement of the candidates into nb buckets of 4 (one block).
+__global__ void __launch_bounds__(1024) k_head_build(const unsigned long long *cand, const uint32_t *meta,
+                                                     uint32_t kmax, uint32_t nb, unsigned long long *image) {
+    __shared__ uint32_t fill[kHeadBuckets];
+    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) fill[i] = 0;
+    for (uint32_t i = threadIdx.x; i < nb * 4; i += blockDim.x) image[i] = 0ull;
+    __syncthreads();
+    uint32_t n = meta[1] < kmax ? meta[1] : kmax;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const unsigned long long key = cand[i];
+        uint32_t b1 = head_bucket(key, kHeadMulA, nb), b2 = head_bucket(key, kHeadMulB, nb);
+        uint32_t first = fill[b1] <= fill[b2] ? b1 : b2, second = first == b1 ? b2 : b1;
+        uint32_t slot = atomicAdd(&fill[first], 1u);
+        if (slot < 4) { image[first * 4 + slot] = key; continue; }
+        slot = atomicAdd(&fill[second], 1u);
+        if (slot < 4) image[second * 4 + slot] = key;  // else: not in the head, counted globally
+    }
+}
 
-int count_global_chunk_bytes() { return kChunk; }
+size_t head_scratch_bytes() {
+    return (size_t)kSampleSlots * sizeof(G8Slot) + 4096 * 4 + 64 + (size_t)kHeadBuckets * 4 * 8 * 2 + 1024;
+}
+
+static int sm_count_dev() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+int count_global_launches(uint64_t nbytes, bool head) {
+    return (nbytes >= kHeadMinBytes && head) ? 6 : (nbytes ? 1 : 0);
+}
 
 cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
-    using C = CountCfg<kBlock, kChunk, kLogC1>;
-    auto kern = k_count_global<kBlock, kChunk, kLogC1, kMinBlocks>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(k_count2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCountSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_count2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCountSmem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     if (c.hi <= c.lo) return cudaSuccess;
-    CountArgs a;
+    const int sms = sm_count_dev();
+    const uintptr_t tb = reinterpret_cast<uintptr_t>(c.text);
+    Count2Args a;
     a.text = c.text;
     a.lo = c.lo;
     a.hi = c.hi;
-    unsigned long long n = c.hi - c.lo;
-    a.nchunks = (uint32_t)((n + kChunk - 1) / kChunk);
+    a.base_al = (tb + c.lo) & ~(uintptr_t)15;
+    const unsigned long long span = tb + c.hi - a.base_al;
+    a.nchunks = (uint32_t)((span + kChunk - 1) / kChunk);
+    a.piece_chunks = a.nchunks;
+    a.piece_stride = 0;
     a.g = c.g;
-    int grid = c.grid;
-    if (grid <= 0) {
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kBlock, C::SMEM);
-        grid = sms * (per > 0 ? per : 1);
+    a.head = nullptr;
+    a.nb = kHeadBuckets;
+    const uint64_t n = c.hi - c.lo;
+    if (n >= kHeadMinBytes && c.head_scratch) {
+        // sampling pass into its own small 8-byte-key table
+        uint8_t *p = static_cast<uint8_t *>(c.head_scratch);
+        G8Slot *sample = reinterpret_cast<G8Slot *>(p);
+        uint32_t *hist = reinterpret_cast<uint32_t *>(p + kSampleSlots * sizeof(G8Slot));
+        uint32_t *meta = hist + 4096;
+        unsigned long long *cand = reinterpret_cast<unsigned long long *>(meta + 16);
+        unsigned long long *image = cand + kHeadBuckets * 4;
+        cudaMemsetAsync(p, 0, kSampleSlots * sizeof(G8Slot) + 4096 * 4 + 64, s);
+        Count2Args sa = a;
+        sa.g.slots8 = sample;
+        sa.g.mask8 = kSampleSlots - 1;
+        const uint32_t pc = kSamplePieceBytes / kChunk;
+        sa.piece_chunks = pc;
+        sa.piece_stride = (span / kSamplePieces) & ~(unsigned long long)15;
+        sa.nchunks = pc * kSamplePieces;
+        int g = (int)std::min<uint32_t>(sa.nchunks, (uint32_t)sms);
+        k_count2<true><<<g, kBlock, kCountSmem, s>>>(sa);
+        const uint32_t kmax = kHeadBuckets * 4 * 88 / 100;
+        k_head_hist<<<sms, 256, 0, s>>>(sample, kSampleSlots, hist);
+        k_head_threshold<<<1, 32, 0, s>>>(hist, kmax, meta);
+        k_head_collect<<<sms * 2, 256, 0, s>>>(sample, kSampleSlots, meta, cand, kmax);
+        k_head_build<<<1, 1024, 0, s>>>(cand, meta, kmax, kHeadBuckets, image);
+        a.head = image;
     }
+    int grid = c.grid > 0 ? c.grid : sms;
     if ((uint32_t)grid > a.nchunks) grid = (int)a.nchunks;
-    kern<<<grid, kBlock, C::SMEM, s>>>(a);
+    k_count2<false><<<grid, kBlock, kCountSmem, s>>>(a);
     return cudaGetLastError();
 }
+
+int count_global_chunk_bytes() { return kChunk; }
 
 }  // namespace wc

@@ -94,9 +94,42 @@ __device__ __forceinline__ uint64_t hash_key(uint4 k) {
     return x;
 }
 
-// Byte-wise hash of a lowercased long word (FNV-1a, 64-bit), length mixed in.
-__device__ __forceinline__ uint64_t hash_long_step(uint64_t h, uint32_t b) {
-    return (h ^ (uint64_t)b) * 0x100000001B3ull;
+// Hash of a long word: h = fmix64(sum_i (b_i + 1) * P^i + len * C) over the
+// lowercased bytes b_i, mod 2^64.  A sum of independent terms, so a warp can
+// compute it in parallel (long_hash_warp) and one thread sequentially
+// (long_hash_serial) with the same result.
+constexpr unsigned long long kLongP = 0x100000001B3ull * 2 + 1;
+__device__ __forceinline__ unsigned long long fmix64(unsigned long long x) {
+    x ^= x >> 33;
+    x *= 0xFF51AFD7ED558CCDull;
+    x ^= x >> 33;
+    x *= 0xC4CEB9FE1A85EC53ull;
+    x ^= x >> 33;
+    return x;
+}
+__device__ __forceinline__ unsigned long long powP(unsigned long long e) {
+    unsigned long long r = 1, b = kLongP;
+    while (e) { if (e & 1) r *= b; b *= b; e >>= 1; }
+    return r;
+}
+__device__ inline unsigned long long long_hash_serial(const uint8_t *w, unsigned long long len) {
+    unsigned long long acc = 0, pw = 1;
+    for (unsigned long long i = 0; i < len; i++) {
+        acc += (unsigned long long)((w[i] | 0x20u) + 1u) * pw;
+        pw *= kLongP;
+    }
+    return fmix64(acc + len * 0x9E3779B97F4A7C15ull);
+}
+// Every lane of the warp must call it with the same (w, len).
+__device__ inline unsigned long long long_hash_warp(const uint8_t *w, unsigned long long len) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long pw = powP((unsigned long long)lane), step = powP(32), acc = 0;
+    for (unsigned long long i = lane; i < len; i += 32) {
+        acc += (unsigned long long)((w[i] | 0x20u) + 1u) * pw;
+        pw *= step;
+    }
+    for (int d = 16; d; d >>= 1) acc += __shfl_xor_sync(kFull, acc, d);
+    return fmix64(acc + len * 0x9E3779B97F4A7C15ull);
 }
 
 // ---------------------------------------------------------------- atomics
@@ -118,6 +151,10 @@ __device__ __forceinline__ uint4 cas128_global(void *addr, uint4 cmp, uint4 val)
     r.x = (uint32_t)r0; r.y = (uint32_t)(r0 >> 32);
     r.z = (uint32_t)r1; r.w = (uint32_t)(r1 >> 32);
     return r;
+}
+
+__device__ __forceinline__ void red_add_u64_dev(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ uint32_t ld_acquire_shared(const uint32_t *p) {
@@ -144,6 +181,23 @@ __device__ __forceinline__ uint4 ld_stream16(const void *p) {  // read-once text
     return v;
 }
 
+// Replaces the bytes of 16 aligned bytes at absolute address a that lie
+// outside [vb, ve) by spaces (a document edge separates words).
+__device__ __forceinline__ uint4 mask_outside_doc(uint4 v, uintptr_t a, uintptr_t vb, uintptr_t ve) {
+    long long lo = (long long)(vb - a), hi = (long long)(ve - a);  // keep bytes in [lo, hi)
+    int klo = (int)(lo < 0 ? 0 : (lo > 16 ? 16 : lo));
+    int khi = (int)(hi < 0 ? 0 : (hi > 16 ? 16 : hi));
+    uint32_t m0 = byte_keep_mask(khi) & ~byte_keep_mask(klo);
+    uint32_t m1 = byte_keep_mask(khi - 4) & ~byte_keep_mask(klo - 4);
+    uint32_t m2 = byte_keep_mask(khi - 8) & ~byte_keep_mask(klo - 8);
+    uint32_t m3 = byte_keep_mask(khi - 12) & ~byte_keep_mask(klo - 12);
+    v.x = (v.x & m0) | (0x20202020u & ~m0);
+    v.y = (v.y & m1) | (0x20202020u & ~m1);
+    v.z = (v.z & m2) | (0x20202020u & ~m2);
+    v.w = (v.w & m3) | (0x20202020u & ~m3);
+    return v;
+}
+
 // ---------------------------------------------------------------- tables
 // Global short-word slot: one 32-byte sector (key, count, spare).
 struct __align__(32) GSlot {
@@ -151,25 +205,34 @@ struct __align__(32) GSlot {
     unsigned long long cnt;
     unsigned long long spare;
 };
-// Global long-word slot: (hash, length) is the CAS target; pos1 = device
-// address of one occurrence of the word, plus one (0 = not yet set).
+// Global long-word slot: (hash, address of the first occurrence) is the
+// 128-bit CAS target, so a slot is published whole in one atomic step;
+// len is written by the claimer for compaction only.
 struct __align__(32) LSlot {
     unsigned long long h;
+    unsigned long long addr;
+    unsigned long long cnt;
     unsigned long long len;
-    unsigned long long pos1;
+};
+
+// Global 8-byte-key slot (words of at most 8 letters): key, count.
+struct __align__(16) G8Slot {
+    unsigned long long key;
     unsigned long long cnt;
 };
 
 struct GTable {
-    GSlot *slots;
+    GSlot *slots;                // words of 9..16 letters
     unsigned long long mask;     // capacity - 1 (power of two)
-    LSlot *lslots;
+    LSlot *lslots;               // words of 17+ letters
     unsigned long long lmask;
     uint32_t *status;
+    G8Slot *slots8;              // words of 1..8 letters
+    unsigned long long mask8;
 };
 
 constexpr int kGlobalProbeLimit = 4096;
-constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr uint32_t kSpinLimit = 1u << 20;  // x 64 ns sleeps: about 0.1 s
 
 // Adds `add` to word `k` (<= 16 letters) in the global table.
 __device__ __forceinline__ void global_insert(const GTable &g, uint4 k, uint64_t h, unsigned long long add) {
@@ -193,39 +256,125 @@ __device__ __forceinline__ bool bytes_eq_lower(const uint8_t *a, const uint8_t *
         if ((a[i] | 0x20u) != (b[i] | 0x20u)) return false;
     return true;
 }
+__device__ __forceinline__ bool bytes_eq_lower_warp(const uint8_t *a, const uint8_t *b, uint64_t len) {
+    bool ok = true;
+    for (uint64_t i = threadIdx.x & 31; i < len; i += 32) ok &= ((a[i] | 0x20u) == (b[i] | 0x20u));
+    return __all_sync(kFull, ok);
+}
 
-// Adds `add` to the long word w[0, len) (a maximal letter run of len >= 17,
-// in any device buffer that stays alive until the table is compacted).
-__device__ inline void long_insert(const GTable &g, const uint8_t *w, uint64_t len, unsigned long long add) {
-    uint64_t h = 0xCBF29CE484222325ull;
-    for (uint64_t i = 0; i < len; i++) h = hash_long_step(h, w[i] | 0x20u);
-    h ^= len * 0x9E3779B97F4A7C15ull;
+// Adds `add` to the long word w[0, len) (a maximal letter run, len >= 17),
+// given its hash h (which includes the length, and the document in batched
+// counting).  `end` bounds the buffer holding w: a word ends at its first
+// non-letter or at `end`.  The slot's (hash, address) pair is claimed with one
+// 128-bit CAS; a thread finding the same hash compares the representative's
+// bytes with its own and checks that the representative's run ends after
+// exactly len letters, so a hash collision never merges two words and no
+// thread ever waits for another.  In text, [begin, end) is the document: a
+// representative outside it belongs to another document and never matches.
+// With begin == null the words live in arenas where each word is followed by
+// a 0 byte; the compare stops at the first difference, so it never reads past
+// a representative's terminator.
+__device__ inline void long_insert2(const GTable &g, const uint8_t *w, unsigned long long len,
+                                    unsigned long long h, unsigned long long add, const uint8_t *begin,
+                                    const uint8_t *end) {
     unsigned long long s = h & g.lmask;
-    uint4 want = make_uint4((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)len, (uint32_t)(len >> 32));
+    const unsigned long long wa = (unsigned long long)reinterpret_cast<uintptr_t>(w);
+    const uint4 want = make_uint4((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)wa, (uint32_t)(wa >> 32));
     const uint4 zero = make_uint4(0, 0, 0, 0);
     for (int probe = 0; probe < kGlobalProbeLimit; probe++) {
         LSlot *slot = g.lslots + s;
         uint4 old = cas128_global(&slot->h, zero, want);
         if (key_zero(old)) {
-            atomicExch(&slot->pos1, (unsigned long long)reinterpret_cast<uintptr_t>(w) + 1ull);
-            atomicAdd(&slot->cnt, add);
+            slot->len = len;
+            red_add_u64_dev(&slot->cnt, add);
             return;
         }
-        if (key_eq(old, want)) {
-            unsigned long long p1 = 0;
-            for (uint32_t spin = 0; spin < kSpinLimit; spin++) {
-                p1 = ld_relaxed_u64(&slot->pos1);
-                if (p1) break;
-            }
-            if (!p1) { atomicOr(g.status, ST_TIMEOUT); return; }
-            if (bytes_eq_lower(reinterpret_cast<const uint8_t *>(p1 - 1ull), w, len)) {
-                atomicAdd(&slot->cnt, add);
-                return;
+        if (old.x == want.x && old.y == want.y) {
+            const uint8_t *rep = reinterpret_cast<const uint8_t *>(((unsigned long long)old.w << 32) | old.z);
+            bool cand;
+            if (begin) cand = rep >= begin && rep + len <= end;  // text: same document, in bounds
+            else cand = true;  // arena: 0-terminated words, the early-exit compare stays inside them
+            if (cand) {
+                bool eq = true;
+                for (unsigned long long i = 0; i < len && eq; i++) eq = (rep[i] | 0x20u) == (w[i] | 0x20u);
+                if (eq) eq = begin ? (rep + len == end || !is_letter(rep[len])) : !is_letter(rep[len]);
+                if (eq) {
+                    red_add_u64_dev(&slot->cnt, add);
+                    return;
+                }
             }
         }
         s = (s + 1) & g.lmask;
     }
     atomicOr(g.status, ST_LONG_FULL);
+}
+
+// One thread inserts a long word (computes the hash itself).
+__device__ inline void long_insert(const GTable &g, const uint8_t *w, uint64_t len, unsigned long long add,
+                                   const uint8_t *begin, const uint8_t *end) {
+    long_insert2(g, w, len, long_hash_serial(w, len), add, begin, end);
+}
+
+// ---------------------------------------------------------------- 8-byte keys
+// Words of at most 8 letters: key = the 8 lowercased bytes, zero padded,
+// little-endian (never 0).  Keys are written once (CAS from 0) and never
+// change, so a plain 64-bit load that sees a non-zero key sees the final key.
+__device__ __forceinline__ unsigned long long hash8(unsigned long long key) {
+    return key * 0x9E3779B97F4A7C15ull;  // Fibonacci hashing: use the top bits
+}
+__device__ __forceinline__ void red_add_u64(unsigned long long *p, unsigned long long v) { red_add_u64_dev(p, v); }
+__device__ __forceinline__ unsigned long long ld_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void global_insert8(const GTable &g, unsigned long long key, unsigned long long add) {
+    unsigned long long s = hash8(key) >> __clzll((long long)g.mask8);  // top bits
+    for (int probe = 0; probe < kGlobalProbeLimit; probe++) {
+        G8Slot *slot = g.slots8 + s;
+        unsigned long long cur = ld_u64(&slot->key);
+        if (cur == 0ull) cur = atomicCAS(&slot->key, 0ull, key);
+        if (cur == 0ull || cur == key) {
+            red_add_u64(&slot->cnt, add);
+            return;
+        }
+        s = (s + 1) & g.mask8;
+    }
+    atomicOr(g.status, ST_TABLE_FULL);
+}
+
+// Words of 9..16 letters: both key halves are non-zero, so two 64-bit loads
+// that each see the corresponding half of `k` can only come from a slot that
+// holds exactly `k` (halves are written once, by one 128-bit CAS).  Loads that
+// see a zero half may have caught a claim in flight (possibly of this very
+// word), so that case is settled by the CAS, which returns the whole key.
+__device__ __forceinline__ void global_insert16(const GTable &g, uint4 k, unsigned long long add) {
+    const uint64_t h = hash_key(k);
+    unsigned long long s = h & g.mask;
+    const unsigned long long k0 = ((unsigned long long)k.y << 32) | k.x, k1 = ((unsigned long long)k.w << 32) | k.z;
+    const uint4 zero = make_uint4(0, 0, 0, 0);
+    for (int probe = 0; probe < kGlobalProbeLimit; probe++) {
+        GSlot *slot = g.slots + s;
+        const unsigned long long *kp = reinterpret_cast<const unsigned long long *>(&slot->key);
+        unsigned long long c0 = ld_u64(kp), c1 = ld_u64(kp + 1);
+        bool hit = (c0 == k0 && c1 == k1);
+        if (!hit && (c0 == 0ull || c1 == 0ull)) {  // empty, or a key being written: ask the CAS
+            uint4 old = cas128_global(&slot->key, zero, k);
+            hit = key_zero(old) || key_eq(old, k);
+        }
+        if (hit) {
+            red_add_u64(&slot->cnt, add);
+            return;
+        }
+        s = (s + 1) & g.mask;
+    }
+    atomicOr(g.status, ST_TABLE_FULL);
+}
+
+// Any word of at most 16 letters given as a 16-byte key.
+__device__ __forceinline__ void table_insert_key(const GTable &g, uint4 k, unsigned long long add) {
+    if ((k.z | k.w) == 0u) global_insert8(g, ((unsigned long long)k.y << 32) | k.x, add);
+    else global_insert16(g, k, add);
 }
 
 // ---------------------------------------------------------------- shared table

@@ -25,6 +25,13 @@ struct wc_ctx {
     std::vector<cudaEvent_t> ev_count, ev_finish;  // (start, stop) pairs
     uint64_t launches = 0;
     void prof_mark(std::vector<cudaEvent_t> &v, cudaStream_t s);
+    // per-document kernel shapes picked by the autotuner (indices into kDocShapes)
+    int tuned_small = 1, tuned_medium = 4;
+    std::string gpu_name;
+    void tune_load();
+    void tune_save() const;
+    // distinct words seen by the last synced single-document count (capacity hints)
+    uint64_t hist_bytes = 0, hist_n8 = 0, hist_n16 = 0, hist_nlong = 0, hist_arena = 0;
 
     wc_status fail(wc_status s, const char *what);
     wc_status cuda_fail(cudaError_t e, const char *what);
@@ -45,21 +52,33 @@ struct wc_table {
     wc_status sync_status = WC_OK;
     uint64_t n = 0, nlong = 0, tokens = 0, word_bytes = 0;
     uint32_t status_bits = 0;
+    uint64_t src_bytes = 0;  // input size of a single-document count (capacity hints)
 };
 
 // Hash tables and sort scratch of one count or merge.
 struct CountScratch {
     void *mem = nullptr;
     size_t bytes = 0;
-    uint64_t gcap = 0, glcap = 0;
+    uint64_t gcap8 = 0, gcap = 0, glcap = 0;
+    wc::G8Slot *slots8 = nullptr;
     wc::GSlot *slots = nullptr;
     wc::LSlot *lslots = nullptr;
+    void *head = nullptr;
     wc::SortScratch ss{};
+    wc::GTable gtable(uint32_t *status) const {
+        return wc::GTable{slots, gcap - 1, lslots, glcap - 1, status, slots8, gcap8 - 1};
+    }
+    uint64_t entries() const { return gcap8 + gcap + glcap; }
+};
+
+// Capacities of one count.
+struct CapPlan {
+    uint64_t cap8, cap16, caplong, arena;
 };
 
 wc_status table_create(wc_ctx *ctx, uint64_t cap, uint64_t lcap, uint64_t arena, int bits, cudaStream_t s,
                        wc_table **out);
 void table_mark_done(wc_table *t, cudaStream_t s);
 wc_status table_sync(const wc_table *t);
-void plan_capacity(uint64_t nbytes, const wc_count_opts *o, uint64_t *gcap, uint64_t *glcap, uint64_t *arena);
-wc_status scratch_create(wc_ctx *ctx, uint64_t gcap, uint64_t glcap, cudaStream_t s, CountScratch &cs);
+CapPlan plan_capacity(const wc_ctx *ctx, uint64_t nbytes, const wc_count_opts *o);
+wc_status scratch_create(wc_ctx *ctx, const CapPlan &p, bool head, cudaStream_t s, CountScratch &cs);

@@ -12,11 +12,14 @@ struct CountLaunch {
     const uint8_t *text;     // document bytes are text[lo, hi)
     uint64_t lo, hi;
     GTable g;
-    int grid;                // 0 = one persistent wave
+    int grid;                // 0 = one persistent block per SM
+    void *head_scratch;      // head_scratch_bytes() or null (no shared-memory head)
 };
-// Tokenises and counts text[lo, hi) into g (short and long tables).
+// Tokenises and counts text[lo, hi) into g (8-byte, 16-byte and long tables).
 cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s);
 int count_global_chunk_bytes();
+int count_global_launches(uint64_t nbytes, bool head);
+size_t head_scratch_bytes();
 
 // ---------------------------------------------------------------- tables
 // A compacted, sorted table in device memory.  Entry i: big-endian key
@@ -42,6 +45,7 @@ struct SortScratch {
     unsigned long long *khi, *klo, *cnt;
     uint32_t *lref;
     uint32_t *perm[2];
+    uint32_t *doc;           // document of each entry (segmented sorts)
     uint32_t *hist_all;      // 24 x 256
     uint32_t *tile_hist;     // 256 x ntiles
     uint32_t *cur;           // 25
@@ -49,11 +53,24 @@ struct SortScratch {
 size_t sort_scratch_bytes(uint64_t cap);
 void sort_scratch_carve(SortScratch &s, void *base, uint64_t cap);
 
+// Word bytes of table entries for ordering long words that share a prefix.
+struct LongView {
+    const uint32_t *lref;
+    const unsigned long long *loff, *llen;
+    const uint8_t *arena;
+};
+// Stable LSD radix sort of ss's n = meta[0] entries by (count desc, word asc);
+// with passes == 28 the document is the most significant key.  The result is
+// the permutation ss.perm[ss.cur[passes]] (device value).
+cudaError_t sort_entries(SortScratch &ss, const unsigned long long *meta, const LongView &v, int passes,
+                         cudaStream_t st);
+int sort_entries_launches(int passes);
+
 // Compacts the global hash tables into unsorted scratch arrays and copies
 // the long words into out.arena; then sorts and writes `out`.
 // finish_table_launches() kernels are launched.
 int finish_table_launches();
-cudaError_t finish_table(const GTable &g, uint64_t gcap, uint64_t glcap, SortScratch &ss,
+cudaError_t finish_table(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_t glcap, SortScratch &ss,
                          DevTable &out, cudaStream_t s);
 
 // Entries of finished tables re-inserted into a global hash table (merge).
@@ -66,6 +83,7 @@ struct MergeSrc {
     const uint8_t *arena;
     int count_bits;
     uint64_t cap;
+    uint64_t arena_cap;
 };
 cudaError_t launch_merge_insert(const MergeSrc *d_src, const uint64_t *h_chunk_start, uint32_t nsrc,
                                 uint64_t total_chunks, const GTable &g, cudaStream_t s);

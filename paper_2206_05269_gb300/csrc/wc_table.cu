@@ -17,7 +17,8 @@ namespace wc {
 constexpr int kSortTile = 4096;      // elements per block in a radix pass
 constexpr int kSortThreads = 256;
 constexpr int kItems = kSortTile / kSortThreads;  // 16
-constexpr int kPasses = 24;
+constexpr int kPasses = 24;     // 8 klo + 8 khi + 8 count digits
+constexpr int kPassesSeg = 28;  // + 4 document digits (segmented: per-document order)
 
 __device__ __forceinline__ unsigned long long be64(uint32_t x, uint32_t y) {
     return ((unsigned long long)__byte_perm(x, 0, 0x0123) << 32) | __byte_perm(y, 0, 0x0123);
@@ -30,7 +31,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 
 size_t sort_scratch_bytes(uint64_t cap) {
     uint64_t ntiles = (cap + kSortTile - 1) / kSortTile;
-    return cap * (8 + 8 + 8 + 4 + 4 + 4) + 4 * 24 * 256 + 4 * 256 * ntiles + 4 * 32 + 1024;
+    return cap * (8 + 8 + 8 + 4 + 4 + 4 + 4) + 4 * kPassesSeg * 256 + 4 * 256 * ntiles + 4 * 32 + 2048;
 }
 
 void sort_scratch_carve(SortScratch &s, void *base, uint64_t cap) {
@@ -44,38 +45,62 @@ void sort_scratch_carve(SortScratch &s, void *base, uint64_t cap) {
     s.lref = reinterpret_cast<uint32_t *>(take(cap * 4));
     s.perm[0] = reinterpret_cast<uint32_t *>(take(cap * 4));
     s.perm[1] = reinterpret_cast<uint32_t *>(take(cap * 4));
-    s.hist_all = reinterpret_cast<uint32_t *>(take(4 * 24 * 256));
+    s.doc = reinterpret_cast<uint32_t *>(take(cap * 4));
+    s.hist_all = reinterpret_cast<uint32_t *>(take(4 * kPassesSeg * 256));
     s.tile_hist = reinterpret_cast<uint32_t *>(take(4 * 256 * ntiles));
     s.cur = reinterpret_cast<uint32_t *>(take(4 * 32));
 }
 
 // ---------------------------------------------------------------- compaction
+// Position allocation for a block-wide pass: one atomicAdd per block step.
+// Every thread of the block must call it (the block iterates uniformly).
+struct BlockAlloc {
+    uint32_t wcnt[32];
+    unsigned long long base;
+    unsigned long long tok[32];
+};
+__device__ __forceinline__ unsigned long long block_alloc(BlockAlloc &sh, bool occ, unsigned long long add_tokens,
+                                                          unsigned long long *counter, unsigned long long *tokens) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t m = __ballot_sync(kFull, occ);
+    unsigned long long t = add_tokens;
+    for (int d = 16; d; d >>= 1) t += __shfl_xor_sync(kFull, t, d);
+    if (lane == 0) { sh.wcnt[warp] = __popc(m); sh.tok[warp] = t; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        unsigned long long tt = 0;
+        for (int w = 0; w < nw; w++) {
+            uint32_t v = sh.wcnt[w];
+            sh.wcnt[w] = run;
+            run += v;
+            tt += sh.tok[w];
+        }
+        sh.base = run ? atomicAdd(counter, (unsigned long long)run) : 0ull;
+        if (tt) atomicAdd(tokens, tt);
+    }
+    __syncthreads();
+    unsigned long long pos = sh.base + sh.wcnt[warp] + __popc(m & lanemask_lt());
+    __syncthreads();
+    return pos;
+}
+
+// Occupied 16-byte-key slots -> entries (big-endian key halves).
 __global__ void k_compact_short(const GSlot *slots, unsigned long long cap, SortScratch ss,
                                 unsigned long long *meta) {
-    const int lane = threadIdx.x & 31;
+    __shared__ BlockAlloc sh;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < cap;
-         b += stride) {
-        unsigned long long i = b + lane;
-        bool occ = false;
+    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x; b < cap; b += stride) {
+        const unsigned long long i = b + threadIdx.x;
         uint4 k = make_uint4(0, 0, 0, 0);
         unsigned long long c = 0;
         if (i < cap) {
             k = slots[i].key;
             c = slots[i].cnt;
-            occ = !key_zero(k);
         }
-        uint32_t m = __ballot_sync(kFull, occ);
-        if (!m) continue;
-        int leader = __ffs(m) - 1;
-        unsigned long long base = 0;
-        if (lane == leader) base = atomicAdd(&meta[0], (unsigned long long)__popc(m));
-        base = __shfl_sync(kFull, base, leader);
-        unsigned long long tsum = occ ? c : 0ull;
-        for (int d = 16; d; d >>= 1) tsum += __shfl_xor_sync(kFull, tsum, d);
-        if (lane == leader) atomicAdd(&meta[3], tsum);
+        const bool occ = !key_zero(k);
+        unsigned long long pos = block_alloc(sh, occ, occ ? c : 0ull, &meta[0], &meta[3]);
         if (occ) {
-            unsigned long long pos = base + __popc(m & lanemask_lt());
             ss.khi[pos] = be64(k.x, k.y);
             ss.klo[pos] = be64(k.z, k.w);
             ss.cnt[pos] = c;
@@ -84,20 +109,45 @@ __global__ void k_compact_short(const GSlot *slots, unsigned long long cap, Sort
     }
 }
 
-// One warp per long-word slot: copy the word into the arena and emit an entry.
+// Occupied 8-byte-key slots -> entries.
+__global__ void k_compact8(const G8Slot *slots, unsigned long long cap, SortScratch ss, unsigned long long *meta) {
+    __shared__ BlockAlloc sh;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x; b < cap; b += stride) {
+        const unsigned long long i = b + threadIdx.x;
+        unsigned long long key = 0, c = 0;
+        if (i < cap) {
+            key = slots[i].key;
+            c = slots[i].cnt;
+        }
+        const bool occ = key != 0ull;
+        unsigned long long pos = block_alloc(sh, occ, occ ? c : 0ull, &meta[0], &meta[3]);
+        if (occ) {
+            ss.khi[pos] = be64((uint32_t)key, (uint32_t)(key >> 32));
+            ss.klo[pos] = 0ull;
+            ss.cnt[pos] = c;
+            ss.lref[pos] = 0u;
+        }
+    }
+}
+
+// One warp per long-word slot: copy the word (lowercased, followed by one 0
+// byte so a run in the arena ends where the word ends) into the arena and
+// emit an entry.
 __global__ void k_compact_long(const LSlot *ls, unsigned long long lcap, SortScratch ss, DevTable out) {
     const int lane = threadIdx.x & 31;
     const unsigned long long gw = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
     unsigned long long *meta = out.d_meta;
     for (unsigned long long w = gw; w < lcap; w += nw) {
+        const unsigned long long h = ls[w].h, addr = ls[w].addr;
+        if (h == 0 && addr == 0) continue;
         const unsigned long long len = ls[w].len;
-        if (len == 0) continue;
-        const uint8_t *src = reinterpret_cast<const uint8_t *>(ls[w].pos1 - 1ull);
+        const uint8_t *src = reinterpret_cast<const uint8_t *>(addr);
         const unsigned long long c = ls[w].cnt;
         unsigned long long off = 0, lidx = 0, pos = 0;
         if (lane == 0) {
-            off = atomicAdd(&meta[2], len);
+            off = atomicAdd(&meta[2], len + 1);
             lidx = atomicAdd(&meta[1], 1ull);
             pos = atomicAdd(&meta[0], 1ull);
             atomicAdd(&meta[3], c);
@@ -105,12 +155,13 @@ __global__ void k_compact_long(const LSlot *ls, unsigned long long lcap, SortScr
         off = __shfl_sync(kFull, off, 0);
         lidx = __shfl_sync(kFull, lidx, 0);
         pos = __shfl_sync(kFull, pos, 0);
-        if (off + len > out.arena_cap || lidx >= out.lcap) {
+        if (off + len + 1 > out.arena_cap || lidx >= out.lcap) {
             if (lane == 0) atomicOr(out.d_status, ST_ARENA_FULL);
             continue;
         }
         for (unsigned long long j = lane; j < len; j += 32) out.arena[off + j] = (uint8_t)(src[j] | 0x20u);
         if (lane == 0) {
+            out.arena[off + len] = 0;
             out.loff[lidx] = off;
             out.llen[lidx] = len;
             unsigned long long hi = 0, lo = 0;
@@ -126,15 +177,16 @@ __global__ void k_compact_long(const LSlot *ls, unsigned long long lcap, SortScr
 
 // ---------------------------------------------------------------- radix sort
 __device__ __forceinline__ uint32_t sort_digit(const SortScratch &s, uint32_t idx, int p) {
+    if (p >= 24) return (s.doc[idx] >> (8 * (p - 24))) & 0xFFu;
     unsigned long long v = p < 8 ? s.klo[idx] : (p < 16 ? s.khi[idx] : ~s.cnt[idx]);
     return (uint32_t)(v >> (8 * (p & 7))) & 0xFFu;
 }
 
 // Histograms of all 24 digit positions (for skipping constant digits) and
 // the identity permutation.
-__global__ void k_hist_all(SortScratch s, const unsigned long long *meta) {
-    __shared__ uint32_t h[kPasses * 256];
-    for (int i = threadIdx.x; i < kPasses * 256; i += blockDim.x) h[i] = 0;
+__global__ void k_hist_all(SortScratch s, const unsigned long long *meta, int passes) {
+    __shared__ uint32_t h[kPassesSeg * 256];
+    for (int i = threadIdx.x; i < kPassesSeg * 256; i += blockDim.x) h[i] = 0;
     __syncthreads();
     const unsigned long long n = meta[0];
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -147,9 +199,14 @@ __global__ void k_hist_all(SortScratch s, const unsigned long long *meta) {
             atomicAdd(&h[(8 + b) * 256 + ((hi >> (8 * b)) & 0xFF)], 1u);
             atomicAdd(&h[(16 + b) * 256 + ((c >> (8 * b)) & 0xFF)], 1u);
         }
+        if (passes > kPasses) {
+            const uint32_t d = s.doc[i];
+#pragma unroll
+            for (int b = 0; b < 4; b++) atomicAdd(&h[(24 + b) * 256 + ((d >> (8 * b)) & 0xFF)], 1u);
+        }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kPasses * 256; i += blockDim.x)
+    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x)
         if (h[i]) atomicAdd(&s.hist_all[i], h[i]);
 }
 
@@ -263,13 +320,8 @@ __global__ void __launch_bounds__(kSortThreads) k_pass_scatter(SortScratch s, in
     }
 }
 
-// Word bytes of entry e in a (khi, klo, lref) view: compares two entries whose
-// 16-byte prefixes are equal by the bytes after the prefix.
-struct LongView {
-    const uint32_t *lref;
-    const unsigned long long *loff, *llen;
-    const uint8_t *arena;
-};
+// Compares two entries whose 16-byte prefixes are equal by the bytes after
+// the prefix (a word that fits the prefix is a proper prefix of a longer one).
 __device__ __forceinline__ bool tail_less(const LongView &v, uint32_t a, uint32_t b) {
     uint32_t ra = v.lref[a], rb = v.lref[b];
     if (ra == 0) return rb != 0;   // the 16-letter (or shorter) word is a prefix
@@ -314,7 +366,7 @@ __device__ __forceinline__ unsigned long long short_len(unsigned long long hi, u
 
 __global__ void k_gather_final(SortScratch s, DevTable out) {
     const unsigned long long n = out.d_meta[0];
-    const uint32_t *perm = s.perm[s.cur[kPasses]];
+    const uint32_t *perm = s.perm[s.cur[kPasses]];  // unsegmented: count digits are the last
     unsigned long long bytes = 0;
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
@@ -346,26 +398,43 @@ static int grid_for(unsigned long long n, int threads, int max_blocks) {
     return (int)g;
 }
 
-int finish_table_launches() { return 2 + 1 + 1 + 3 * kPasses + 1; }
+// meta[slot] = meta[0] (entries so far): per-kind counts for capacity hints
+__global__ void k_meta_snapshot(unsigned long long *meta, int slot) { meta[slot] = meta[0]; }
 
-cudaError_t finish_table(const GTable &g, uint64_t gcap, uint64_t glcap, SortScratch &ss, DevTable &out,
+int sort_entries_launches(int passes);
+int finish_table_launches() { return 5 + sort_entries_launches(kPasses) + 1; }
+
+// LSD radix sort of the entries in ss (count n = meta[0]) into ss.perm[ss.cur[passes]].
+cudaError_t sort_entries(SortScratch &ss, const unsigned long long *meta, const LongView &v, int passes,
                          cudaStream_t st) {
     const int sms = sm_count();
     const uint64_t cap = ss.cap;
-    cudaMemsetAsync(ss.hist_all, 0, 4 * kPasses * 256, st);
-    cudaMemsetAsync(ss.cur, 0, 4 * 32, st);
-    k_compact_short<<<grid_for(gcap, 256, sms * 8), 256, 0, st>>>(g.slots, gcap, ss, out.d_meta);
-    k_compact_long<<<grid_for(glcap * 32, 256, sms * 8), 256, 0, st>>>(g.lslots, glcap, ss, out);
-    k_hist_all<<<grid_for(cap, 256, sms * 2), 256, 0, st>>>(ss, out.d_meta);
+    k_hist_all<<<grid_for(cap, 256, sms * 2), 256, 0, st>>>(ss, meta, passes);
     const int ntiles = (int)((cap + kSortTile - 1) / kSortTile);
-    LongView v{ss.lref, out.loff, out.llen, out.arena};
-    for (int p = 0; p < kPasses; p++) {
-        if (p == 16) k_fix_long<<<grid_for(cap, 256, sms * 4), 256, 0, st>>>(ss, v, out.d_meta);
-        k_pass_count<<<ntiles, kSortThreads, 0, st>>>(ss, p, out.d_meta);
-        k_pass_scan<<<1, 1024, 0, st>>>(ss, p, out.d_meta);
-        k_pass_scatter<<<ntiles, kSortThreads, 0, st>>>(ss, p, out.d_meta);
+    for (int p = 0; p < passes; p++) {
+        if (p == 16) k_fix_long<<<grid_for(cap, 256, sms * 4), 256, 0, st>>>(ss, v, meta);
+        k_pass_count<<<ntiles, kSortThreads, 0, st>>>(ss, p, meta);
+        k_pass_scan<<<1, 1024, 0, st>>>(ss, p, meta);
+        k_pass_scatter<<<ntiles, kSortThreads, 0, st>>>(ss, p, meta);
     }
-    k_gather_final<<<grid_for(cap, 256, sms * 8), 256, 0, st>>>(ss, out);
+    return cudaGetLastError();
+}
+int sort_entries_launches(int passes) { return 1 + 1 + 3 * passes; }
+
+cudaError_t finish_table(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_t glcap, SortScratch &ss,
+                         DevTable &out, cudaStream_t st) {
+    const int sms = sm_count();
+    cudaMemsetAsync(ss.hist_all, 0, 4 * kPassesSeg * 256, st);
+    cudaMemsetAsync(ss.cur, 0, 4 * 32, st);
+    k_compact8<<<grid_for(gcap8, 256, sms * 8), 256, 0, st>>>(g.slots8, gcap8, ss, out.d_meta);
+    k_meta_snapshot<<<1, 1, 0, st>>>(out.d_meta, 5);
+    k_compact_short<<<grid_for(gcap, 256, sms * 8), 256, 0, st>>>(g.slots, gcap, ss, out.d_meta);
+    k_meta_snapshot<<<1, 1, 0, st>>>(out.d_meta, 6);
+    k_compact_long<<<grid_for(glcap * 32, 256, sms * 8), 256, 0, st>>>(g.lslots, glcap, ss, out);
+    LongView v{ss.lref, out.loff, out.llen, out.arena};
+    cudaError_t e = sort_entries(ss, out.d_meta, v, kPasses, st);
+    if (e != cudaSuccess) return e;
+    k_gather_final<<<grid_for(ss.cap, 256, sms * 8), 256, 0, st>>>(ss, out);
     return cudaGetLastError();
 }
 
@@ -381,21 +450,27 @@ __global__ void k_merge_insert(const MergeSrc *src, const unsigned long long *ch
     const MergeSrc t = src[lo];
     const unsigned long long n = t.meta[0];
     const unsigned long long i0 = (b - chunk_start[lo]) * kMergeChunk;
-    for (unsigned long long i = i0 + threadIdx.x; i < i0 + kMergeChunk && i < n; i += blockDim.x) {
-        unsigned long long c = t.count_bits == 32 ? static_cast<const uint32_t *>(t.cnt)[i]
-                                                  : static_cast<const unsigned long long *>(t.cnt)[i];
-        uint32_t r = t.lref[i];
-        if (r == 0) {
+    for (unsigned long long ib = i0 + (threadIdx.x & ~31u); ib < i0 + kMergeChunk && ib < n; ib += blockDim.x) {
+        const unsigned long long i = ib + (threadIdx.x & 31);  // whole warps iterate together
+        const bool valid = i < i0 + kMergeChunk && i < n;
+        unsigned long long c = 0;
+        uint32_t r = 0;
+        if (valid) {
+            c = t.count_bits == 32 ? static_cast<const uint32_t *>(t.cnt)[i]
+                                   : static_cast<const unsigned long long *>(t.cnt)[i];
+            r = t.lref[i];
+        }
+        if (valid && r == 0) {
             unsigned long long hi8 = t.khi[i], lo8 = t.klo[i];
             uint4 k;
             k.x = __byte_perm((uint32_t)(hi8 >> 32), 0, 0x0123);
             k.y = __byte_perm((uint32_t)hi8, 0, 0x0123);
             k.z = __byte_perm((uint32_t)(lo8 >> 32), 0, 0x0123);
             k.w = __byte_perm((uint32_t)lo8, 0, 0x0123);
-            global_insert(g, k, hash_key(k), c);
-        } else {
-            long_insert(g, t.arena + t.loff[r - 1], t.llen[r - 1], c);
+            table_insert_key(g, k, c);
         }
+        if (valid && r != 0)
+            long_insert(g, t.arena + t.loff[r - 1], t.llen[r - 1], c, nullptr, nullptr);
     }
 }
 

@@ -32,9 +32,11 @@ WC_TABLE_DOC, WC_TABLE_CLASS, WC_TABLE_GLOBAL = 0, 1, 2
 
 # Every symbol include/wc.h declares (checked by the tests).
 EXPORTS = [
-    "wc_create", "wc_destroy", "wc_count", "wc_count_ex", "wc_count_batched", "wc_batch_table",
+    "wc_create", "wc_destroy", "wc_count", "wc_count_ex", "wc_count_batched", "wc_batch_status",
+    "wc_batch_table", "wc_batch_size", "wc_batch_export",
     "wc_class_ratio_topk", "wc_merge", "wc_topk", "wc_table_status", "wc_table_size",
-    "wc_table_export", "wc_table_count_bits", "wc_table_free", "wc_batch_free", "wc_profile_enable",
+    "wc_table_export", "wc_table_count_bits", "wc_table_free", "wc_batch_free", "wc_plan_create", "wc_plan_run",
+    "wc_plan_free", "wc_profile_enable",
     "wc_profile_read", "wc_status_str", "wc_last_error",
 ]
 
@@ -75,7 +77,10 @@ def load() -> ctypes.CDLL:
         "wc_count": (i32, [vp, vp, u64, vp, pvp]),
         "wc_count_ex": (i32, [vp, vp, u64, ctypes.POINTER(WcCountOpts), vp, pvp]),
         "wc_count_batched": (i32, [vp, vp, vp, vp, u32, vp, u32, vp, pvp]),
+        "wc_batch_status": (i32, [vp]),
         "wc_batch_table": (i32, [vp, i32, u32, pvp]),
+        "wc_batch_size": (i32, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]),
+        "wc_batch_export": (i32, [vp, vp, vp, vp, vp, vp, vp]),
         "wc_class_ratio_topk": (i32, [vp, vp, u32, u32, vp, vp, vp, vp, ctypes.POINTER(u32)]),
         "wc_merge": (i32, [vp, ctypes.POINTER(ctypes.c_void_p), u32, vp, pvp]),
         "wc_topk": (i32, [vp, vp, u32, vp, pvp]),
@@ -85,6 +90,9 @@ def load() -> ctypes.CDLL:
         "wc_table_count_bits": (i32, [vp]),
         "wc_table_free": (None, [vp]),
         "wc_batch_free": (None, [vp]),
+        "wc_plan_create": (i32, [vp, vp, u32, u32, vp, pvp]),
+        "wc_plan_run": (i32, [vp, vp, vp, vp, vp, pvp]),
+        "wc_plan_free": (None, [vp]),
         "wc_profile_enable": (i32, [vp, i32]),
         "wc_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(u64), ctypes.POINTER(u64)]),
@@ -141,6 +149,29 @@ def wc_count_batched(ctx, d_text: int, d_offsets: int, h_offsets: np.ndarray, nd
     _check(load().wc_count_batched(ctx, d_text, d_offsets, h.ctypes.data, ndocs, d_class or None, nclasses,
                                    stream, ctypes.byref(out)), ctx, "wc_count_batched")
     return out
+
+
+def wc_batch_status(batch) -> int:
+    return load().wc_batch_status(batch)
+
+
+def wc_batch_size(batch) -> tuple[int, int]:
+    n, nb = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().wc_batch_size(batch, ctypes.byref(n), ctypes.byref(nb)), None, "wc_batch_size")
+    return n.value, nb.value
+
+
+def wc_batch_export(batch, ndocs: int, stream: int = 0):
+    """Returns (doc_start uint64[ndocs], doc_n uint32[ndocs], words, word offsets, counts uint32)."""
+    n, nb = wc_batch_size(batch)
+    ds = np.zeros(max(1, ndocs), dtype=np.uint64)
+    dn = np.zeros(max(1, ndocs), dtype=np.uint32)
+    words = np.zeros(max(1, nb), dtype=np.uint8)
+    offs = np.zeros(n + 1, dtype=np.uint64)
+    counts = np.zeros(max(1, n), dtype=np.uint32)
+    _check(load().wc_batch_export(batch, ds.ctypes.data, dn.ctypes.data, words.ctypes.data, offs.ctypes.data,
+                                  counts.ctypes.data, stream), None, "wc_batch_export")
+    return ds[:ndocs], dn[:ndocs], words[:nb], offs, counts[:n]
 
 
 def wc_batch_table(batch, kind: int, idx: int):
@@ -209,6 +240,25 @@ def wc_batch_free(batch) -> None:
     load().wc_batch_free(batch)
 
 
+def wc_plan_create(ctx, h_offsets: np.ndarray, nclasses: int, stream: int):
+    h = np.ascontiguousarray(h_offsets, dtype=np.uint64)
+    out = ctypes.c_void_p()
+    _check(load().wc_plan_create(ctx, h.ctypes.data, int(h.size - 1), nclasses, stream, ctypes.byref(out)), ctx,
+           "wc_plan_create")
+    return out
+
+
+def wc_plan_run(ctx, plan, d_text: int, d_offsets: int, d_class: int | None, stream: int):
+    out = ctypes.c_void_p()
+    _check(load().wc_plan_run(plan, d_text, d_offsets, d_class or None, stream, ctypes.byref(out)), ctx,
+           "wc_plan_run")
+    return out
+
+
+def wc_plan_free(plan) -> None:
+    load().wc_plan_free(plan)
+
+
 def wc_profile_enable(ctx, enable: bool) -> None:
     _check(load().wc_profile_enable(ctx, int(enable)), ctx, "wc_profile_enable")
 
@@ -268,13 +318,30 @@ class Table:
 
 
 class Batch:
-    def __init__(self, handle):
+    def __init__(self, handle, ndocs: int = 0, owned: bool = True):
         self.handle = handle
+        self.ndocs = ndocs
+        self.owned = owned
+
+    def status(self) -> int:
+        return wc_batch_status(self.handle)
+
+    def export(self, stream=None):
+        return wc_batch_export(self.handle, self.ndocs, _stream_handle(stream))
+
+    def doc_lists(self):
+        """Per-document [(word, count)] lists from one bulk export."""
+        ds, dn, w, o, c = self.export()
+        out = []
+        for d in range(self.ndocs):
+            s0, n = int(ds[d]), int(dn[d])
+            out.append([(w[o[i]:o[i + 1]].tobytes(), int(c[i])) for i in range(s0, s0 + n)])
+        return out
 
     def __del__(self):
-        if getattr(self, "handle", None):
+        if getattr(self, "handle", None) and self.owned:
             wc_batch_free(self.handle)
-            self.handle = None
+        self.handle = None
 
     def table(self, kind: int, idx: int = 0) -> Table:
         return Table(wc_batch_table(self.handle, kind, idx), owned=False)
@@ -320,10 +387,32 @@ class Counter:
         s = _stream_handle(stream)
         return Batch(wc_count_batched(self.ctx, text.data_ptr(), offsets.data_ptr(), h_offsets,
                                       int(h_offsets.size - 1), classes.data_ptr() if classes is not None else None,
-                                      nclasses, s))
+                                      nclasses, s), int(h_offsets.size - 1))
+
+    def plan(self, h_offsets, nclasses: int = 0, stream=None) -> "Plan":
+        return Plan(self, h_offsets, nclasses, stream)
 
     def merge(self, tables: list[Table], stream=None) -> Table:
         return Table(wc_merge(self.ctx, [t.handle for t in tables], _stream_handle(stream)))
 
     def topk(self, table: Table, k: int, stream=None) -> Table:
         return Table(wc_topk(self.ctx, table.handle, k, _stream_handle(stream)))
+
+
+class Plan:
+    """Resident batched-count state replayed through a CUDA graph (wc_plan_*)."""
+
+    def __init__(self, counter: Counter, h_offsets, nclasses: int = 0, stream=None):
+        self.counter = counter
+        self.ndocs = int(np.asarray(h_offsets).size - 1)
+        self.handle = wc_plan_create(counter.ctx, h_offsets, nclasses, _stream_handle(stream))
+
+    def run(self, text, offsets, classes=None, stream=None) -> Batch:
+        h = wc_plan_run(self.counter.ctx, self.handle, text.data_ptr(), offsets.data_ptr(),
+                        classes.data_ptr() if classes is not None else None, _stream_handle(stream))
+        return Batch(h, self.ndocs, owned=False)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            wc_plan_free(self.handle)
+        self.handle = None

@@ -1,0 +1,139 @@
+"""GPU parity of batched counting (wc_count_batched): per-document, per-class
+and global tables and the class-ratio ranking, bit-exact against the oracle."""
+import numpy as np
+import pytest
+
+import corpus
+import oracle
+from gpu_util import assert_same
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctr():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_05269_gb300 import wc
+    c = wc.Counter(0, count_bits=32)
+    yield c
+    c.close()
+
+
+def run_batched(ctr, text: np.ndarray, offsets: np.ndarray, classes=None, nclasses=0):
+    import torch
+    dev = torch.device("cuda:0")
+    t = torch.from_numpy(np.ascontiguousarray(text, dtype=np.uint8)).to(dev) if text.size else \
+        torch.zeros(16, dtype=torch.uint8, device=dev)
+    o = torch.from_numpy(np.ascontiguousarray(offsets, dtype=np.uint64).view(np.int64)).to(dev)
+    cl = torch.from_numpy(np.ascontiguousarray(classes, dtype=np.uint32).view(np.int32)).to(dev) \
+        if classes is not None else None
+    b = ctr.count_batched(t, o, np.ascontiguousarray(offsets, dtype=np.uint64), cl, nclasses)
+    return b, (t, o, cl)
+
+
+def check_docs(b, r, ndocs, sample=None):
+    from paper_2206_05269_gb300 import wc
+    assert b.status() == wc.WC_OK
+    ds, dn, w, o, c = b.export()
+    docs = range(ndocs) if sample is None else sample
+    for d in docs:
+        want = r.doc(d)
+        s0, n = int(ds[d]), int(dn[d])
+        assert n == len(want), f"doc {d}: {n} words vs oracle {len(want)}"
+        got_w = w[o[s0]:o[s0 + n]] if n else np.zeros(0, np.uint8)
+        assert np.array_equal(got_w, want.words), f"doc {d}: words differ"
+        assert np.array_equal((o[s0:s0 + n + 1] - o[s0]).astype(np.uint64), want.offs), f"doc {d}: offsets"
+        assert np.array_equal(c[s0:s0 + n].astype(np.uint64), want.counts), f"doc {d}: counts differ"
+
+
+def test_tiny_workload_docs_and_global(ctr):
+    from paper_2206_05269_gb300 import wc
+    c = corpus.generate("tiny")
+    r = oracle.count(c.text, c.offsets)
+    b, keep = run_batched(ctr, c.text, c.offsets)
+    check_docs(b, r, c.ndocs)
+    g = b.table(wc.WC_TABLE_GLOBAL)
+    assert_same(g.export(), r.glob(), "global")
+    # a per-document view equals the bulk export
+    v = b.table(wc.WC_TABLE_DOC, 7)
+    assert v.as_list() == r.doc(7).as_list()
+
+
+def test_class_workload_tables_and_ratio(ctr):
+    from paper_2206_05269_gb300 import wc
+    c = corpus.generate("classes")
+    r = oracle.count(c.text, c.offsets, c.classes, c.nclasses)
+    b, keep = run_batched(ctr, c.text, c.offsets, c.classes, c.nclasses)
+    check_docs(b, r, c.ndocs, sample=range(0, c.ndocs, 7))
+    assert_same(b.table(wc.WC_TABLE_GLOBAL).export(), r.glob(), "global")
+    for k in range(c.nclasses):
+        tab = b.table(wc.WC_TABLE_CLASS, k)
+        assert_same(tab.export(), r.cls(k), f"class {k}")
+        idx, cin, cout = wc.wc_class_ratio_topk(ctr.ctx, b.handle, k, 50, 0)
+        want = r.ratio_topk(k, 50)
+        ctab = r.cls(k)
+        got = [(ctab.word(int(i)), int(a), int(o)) for i, a, o in zip(idx, cin, cout)]
+        assert got == want, f"class {k} ratio ranking"
+
+
+def test_edges_long_words_spills_and_splits(ctr):
+    rng = np.random.default_rng(3)
+    docs = [b"", b"   ", b"abc", b"def", b"Abc abc ABC", b"12 34", b"x" * 40 + b" " + b"X" * 40,
+            b"-".join([b"abcdefghijklmnopq%c" % (97 + i % 26) + bytes([97 + i // 26]) for i in range(120)]),
+            # more distinct words than a small document's shared table holds
+            b" ".join(bytes([97 + (i // 676) % 26, 97 + (i // 26) % 26, 97 + i % 26]) for i in range(2000)),
+            ]
+    # a document above the split threshold (counted in ranges across blocks)
+    big = corpus.generate("tiny", ndocs=1, size_a=60000, size_b=60000, len_max=30, len_tail=0.3,
+                          len_tail_mean=8.0)
+    docs.append(big.text.tobytes())
+    # words touching document edges on both sides
+    docs += [b"edge", b"word", b"Edge"]
+    for _ in range(20):
+        n = int(rng.integers(1, 3000))
+        arr = rng.choice(np.frombuffer(b"abcXYZ .,\n1\xc3", np.uint8), n)
+        docs.append(arr.tobytes())
+    text = np.frombuffer(b"".join(docs), np.uint8)
+    offs = np.cumsum([0] + [len(d) for d in docs]).astype(np.uint64)
+    r = oracle.count(text, offs)
+    b, keep = run_batched(ctr, text, offs)
+    check_docs(b, r, len(docs))
+
+
+def test_batched_equals_single_document_counts(ctr):
+    c = corpus.generate("batched", ndocs=300)
+    b, keep = run_batched(ctr, c.text, c.offsets)
+    lists = b.doc_lists()
+    from gpu_util import to_dev
+    for d in range(0, c.ndocs, 37):
+        seg = c.text[c.offsets[d]:c.offsets[d + 1]].tobytes()
+        single = ctr.count_checked(to_dev(seg)).as_list()
+        assert lists[d] == single, f"doc {d}"
+
+
+def test_batched_workload_full_size_sampled(ctr):
+    """The 100k-document workload as the benchmark runs it: every document's
+    table checked for the token invariant, 1,500 sampled documents checked
+    word by word against the oracle, the global table against the generator."""
+    from paper_2206_05269_gb300 import wc
+    c = corpus.generate("batched")
+    b, keep = run_batched(ctr, c.text, c.offsets)
+    ds, dn, w, o, cnt = b.export()
+    rng = np.random.default_rng(1)
+    sample = np.sort(rng.choice(c.ndocs, 1500, replace=False))
+    sub_docs = [c.text[c.offsets[d]:c.offsets[d + 1]] for d in sample]
+    sub_text = np.concatenate(sub_docs)
+    sub_offs = np.cumsum([0] + [x.size for x in sub_docs]).astype(np.uint64)
+    r = oracle.count(sub_text, sub_offs)
+    for j, d in enumerate(sample):
+        want = r.doc(j)
+        s0, n = int(ds[d]), int(dn[d])
+        assert n == len(want)
+        assert np.array_equal(cnt[s0:s0 + n].astype(np.uint64), want.counts)
+        assert np.array_equal(w[o[s0]:o[s0 + n]], want.words)
+    assert int(cnt.astype(np.uint64).sum()) == c.tokens
+    g = b.table(wc.WC_TABLE_GLOBAL)
+    items = sorted(c.truth().items(), key=lambda kv: (-kv[1], kv[0]))
+    assert_same(g.export(), oracle.Table.from_list(items), "global vs generator")

@@ -1,0 +1,56 @@
+"""Served counting: every request's answer in the continuous-batching mix is
+bit-identical to the same request counted alone, and to the oracle."""
+import numpy as np
+import pytest
+
+import corpus
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctr():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_05269_gb300 import wc
+    c = wc.Counter(0, count_bits=32, budget=8 << 30)
+    yield c
+    c.close()
+
+
+def make_requests(n_rate=400.0, dur=0.15, lo=1 << 10, hi=1 << 20, pool_bytes=48e6, seed=9):
+    import torch
+    from paper_2206_05269_gb300.serve import Request
+    pool = corpus.generate("served_pool", size_a=pool_bytes).text
+    host = torch.from_numpy(pool).pin_memory()
+    trip = corpus.poisson_requests(pool, n_rate, dur, lo, hi, seed)
+    reqs = [Request(i, a, host[s:e]) for i, (a, s, e) in enumerate(trip)]
+    return pool, trip, reqs
+
+
+def test_mix_equals_alone_and_oracle(ctr):
+    from paper_2206_05269_gb300 import serve
+    from gpu_util import to_dev
+    pool, trip, reqs = make_requests()
+    assert len(reqs) >= 20
+    answers, stats = serve.serve_batched(ctr, reqs, topk=100, max_rounds=3)
+    assert stats["rounds"] >= 2
+    for (a, s, e), ans in zip(trip, answers):
+        data = pool[s:e].tobytes()
+        alone = ctr.count_checked(to_dev(data)).as_list()
+        assert ans.as_list() == alone, f"request {ans.rid} differs alone vs in the mix"
+        assert ans.latency >= 0
+    for (a, s, e), ans in list(zip(trip, answers))[::5]:
+        assert ans.as_list() == oracle.count(pool[s:e]).glob().as_list()
+
+
+def test_fifo_path_matches(ctr):
+    from paper_2206_05269_gb300 import serve
+    pool, trip, reqs = make_requests(n_rate=200.0, dur=0.05, seed=4)
+    a1, _ = serve.serve_batched(ctr, reqs, topk=100)
+    a2, _ = serve.serve_fifo(ctr, reqs, topk=100)
+    for x, y in zip(a1, a2):
+        assert x.as_list() == y.as_list()
+        assert x.as_list(100) == y.as_list()[:100]
