@@ -356,7 +356,9 @@ static uint64_t pow2_at_least(uint64_t x) {
 // silent: callers count again with larger capacities.
 CapPlan plan_capacity(const wc_ctx *ctx, uint64_t nbytes, const wc_count_opts *o) {
     double tokens = (double)nbytes / 5.0 + 1.0;
-    double est = std::min(tokens, 16.0 * std::pow(tokens, 0.6));
+    // Heaps' term, or T/16 for a large vocabulary in a mid-sized text (capped
+    // at 2M distinct words so huge texts keep L2-sized tables)
+    double est = std::min(tokens, std::max(16.0 * std::pow(tokens, 0.6), std::min(tokens / 16.0, 2097152.0)));
     uint64_t bound = nbytes / 2 + 1;
     uint64_t d = std::min<uint64_t>((uint64_t)est + 64, bound);
     CapPlan p;

@@ -25,14 +25,18 @@ uint64_t pow2_ge(uint64_t x) {
     return p;
 }
 
-// Distinct-word estimate of one document of s bytes (generous Heaps' law, never
-// above the exact bound ceil(s/2)).
+// Distinct-word estimate of one document of s bytes: the larger of a Heaps'-law
+// term 16 * T^0.6 (T = s/5 tokens) and s/16 (a large vocabulary seen in a
+// mid-sized document), never above the exact bound ceil(s/2).
 uint64_t est_distinct(uint64_t s) {
     if (!s) return 0;
     double t = (double)s / 5.0 + 1.0;
-    double e = std::min(t, 16.0 * std::pow(t, 0.6));
-    return std::min<uint64_t>((uint64_t)e + 16, s / 2 + 1);
+    double e = std::max(16.0 * std::pow(t, 0.6), (double)s / 16.0);
+    return std::min<uint64_t>((uint64_t)std::min(e, t) + 16, s / 2 + 1);
 }
+// Output entries reserved for one document: the CSR output is never cleared,
+// so reserve generously (s/8 entries is about two thirds of its tokens).
+uint64_t out_reserve(uint64_t s) { return std::min<uint64_t>(s / 2 + 1, std::max(est_distinct(s), s / 8)) + 4; }
 
 }  // namespace
 
@@ -181,7 +185,7 @@ static wc_status batch_plan(wc_ctx *ctx, const uint64_t *h_offsets, uint32_t ndo
         const uint64_t lo = h_offsets[d], hi = h_offsets[d + 1], s = hi - lo;
         if (!s) continue;
         const uint64_t e = est_distinct(s);
-        out_est += e + e / 4;
+        out_est += out_reserve(s);
         long_est += std::min<uint64_t>(s / 18 + 1, e / 8 + 2);
         if (s <= kSmallMax) small.push_back({lo, hi, d, 0});
         else if (s <= kSplitMin) medium.push_back({lo, hi, d, 0});
