@@ -180,6 +180,37 @@ int wc_table_count_bits(const wc_table *t);
 void wc_table_free(wc_table *t);
 void wc_batch_free(wc_batch *b);
 
+/* Counting for callers that cannot allocate device memory (the paper has no
+ * counterpart: this is a deployment variant of wc_count).  Such callers
+ * include code running while another component owns all device memory
+ * through its own allocator, and services that forbid allocation after
+ * start-up because an allocation can stall or fail at the wrong moment.
+ * No context is needed and nothing is allocated: the hash tables and sort
+ * scratch live in one fixed __device__ array of about 12.5 MB that every GPU
+ * which loads the library holds until the process exits.
+ *   d_text[0, nbytes): one document, nbytes <= 1 MiB (larger: returns
+ *     WC_ERR_UNSUPPORTED; use wc_count).
+ *   Outputs (device, caller-owned), the sorted table in wc_count's layout:
+ *     d_khi, d_klo: big-endian first 16 letters of each word; d_cnt: counts;
+ *     d_lref: 0, or 1 + index into d_loff/d_llen of a word of 17+ letters
+ *     whose lowercased bytes are at d_arena + d_loff[i] (each followed by a
+ *     0 byte).  out_cap >= 204800 entries, long_cap >= 8192, arena_cap >=
+ *     nbytes + nbytes/16 + 16, else WC_ERR_INVALID_ARG.
+ *     d_meta (8 x uint64): [0] distinct words, [1] words of 17+ letters,
+ *     [3] total count, [4] bytes of all words; the low 32 bits of [7] are
+ *     status bits, nonzero when the fixed tables overflowed (then the table
+ *     is not valid).
+ * Stream-ordered and asynchronous like wc_count: results are valid once the
+ * stream has reached the call.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls on a device
+ * share the array and each clears it; calls whose work overlaps on the GPU
+ * race, so keep them on one stream, in order. */
+wc_status wc_count_noalloc(const uint8_t *d_text, uint64_t nbytes, uint64_t *d_khi, uint64_t *d_klo,
+                           uint64_t *d_cnt, uint32_t *d_lref, uint64_t out_cap, uint64_t *d_loff,
+                           uint64_t *d_llen, uint64_t long_cap, uint8_t *d_arena, uint64_t arena_cap,
+                           uint64_t *d_meta, cudaStream_t stream);
+
 /* Stage tracing.  While enabled, the context records CUDA events on the
  * launching stream around each counting kernel and around each compaction +
  * sort stage of wc_count / wc_count_ex / wc_merge, and counts the kernels

@@ -36,7 +36,7 @@ EXPORTS = [
     "wc_batch_table", "wc_batch_size", "wc_batch_export",
     "wc_class_ratio_topk", "wc_merge", "wc_topk", "wc_table_status", "wc_table_size",
     "wc_table_export", "wc_table_count_bits", "wc_table_free", "wc_batch_free", "wc_plan_create", "wc_plan_run",
-    "wc_plan_free", "wc_profile_enable",
+    "wc_plan_free", "wc_count_noalloc", "wc_profile_enable",
     "wc_profile_read", "wc_status_str", "wc_last_error",
 ]
 
@@ -93,6 +93,7 @@ def load() -> ctypes.CDLL:
         "wc_plan_create": (i32, [vp, vp, u32, u32, vp, pvp]),
         "wc_plan_run": (i32, [vp, vp, vp, vp, vp, pvp]),
         "wc_plan_free": (None, [vp]),
+        "wc_count_noalloc": (i32, [vp, u64, vp, vp, vp, vp, u64, vp, vp, u64, vp, u64, vp, vp]),
         "wc_profile_enable": (i32, [vp, i32]),
         "wc_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(u64), ctypes.POINTER(u64)]),
@@ -257,6 +258,20 @@ def wc_plan_run(ctx, plan, d_text: int, d_offsets: int, d_class: int | None, str
 
 def wc_plan_free(plan) -> None:
     load().wc_plan_free(plan)
+
+
+NOALLOC_MAX_BYTES = 1 << 20
+NOALLOC_ENTRIES = (1 << 17) + (1 << 16) + (1 << 13)
+NOALLOC_LONG = 1 << 13
+
+
+def wc_count_noalloc(d_text: int, nbytes: int, d_khi: int, d_klo: int, d_cnt: int, d_lref: int, out_cap: int,
+                     d_loff: int, d_llen: int, long_cap: int, d_arena: int, arena_cap: int, d_meta: int,
+                     stream: int) -> None:
+    """Single-document count that allocates nothing (caller-owned outputs,
+    fixed library scratch); see include/wc.h."""
+    _check(load().wc_count_noalloc(d_text, nbytes, d_khi, d_klo, d_cnt, d_lref, out_cap, d_loff, d_llen, long_cap,
+                                   d_arena, arena_cap, d_meta, stream), None, "wc_count_noalloc")
 
 
 def wc_profile_enable(ctx, enable: bool) -> None:
