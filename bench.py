@@ -411,7 +411,7 @@ def run_served_workload(args, local):
     serve.serve_batched(ctr, [serve.Request(i, 0.0, r.data) for i, r in enumerate(reqs[:16])])
     sampler = ClockSampler(local)
     sampler.start()
-    ans, st = serve.serve_batched(ctr, reqs, topk=100, max_rounds=4)
+    ans, st = serve.serve_batched(ctr, reqs, topk=100)
     clocks = sampler.stop()
     lat = np.array([a.latency for a in ans]) * 1e3
     nbytes = sum(r.data.numel() for r in reqs)
@@ -424,7 +424,8 @@ def run_served_workload(args, local):
         "unit": "ms", "n_gpus": 1, "steps": len(reqs), "warmup": 16, "ms_per_step": st["wall_s"] * 1e3 / len(reqs),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": "served", "requests": len(reqs), "seconds": args.serve_seconds,
-                   "bytes": nbytes, "rounds": st["rounds"], "budget_GB": 40},
+                   "bytes": nbytes, "rounds": st["rounds"], "large_requests": st["large"],
+                   "recounted": st["recounted"], "budget_GB": 40},
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "req_per_s": len(reqs) / st["wall_s"], "GBps": nbytes / st["wall_s"] / 1e9,
         "fifo": {"requests": len(fans), "p50_ms": float(np.percentile(flat, 50)) if len(fans) else None,

@@ -351,7 +351,8 @@ struct wc_plan {
     const uint8_t *g_text = nullptr;
     const uint64_t *g_off = nullptr;
     const uint32_t *g_cls = nullptr;
-    cudaStream_t g_stream = nullptr;
+    cudaStream_t own = nullptr;   // graphs are captured and replayed here
+    cudaEvent_t in_ev = nullptr;
     uint64_t graph_launches = 0;
     bool tuned = false;
 };
@@ -418,6 +419,15 @@ wc_status wc_plan_create(wc_ctx *ctx, const uint64_t *h_offsets, uint32_t ndocs,
         return st;
     }
     cudaEventCreateWithFlags(&pl->b->done, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&pl->in_ev, cudaEventDisableTiming);
+    if (cudaStreamCreateWithFlags(&pl->own, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        wc_plan_free(pl);
+        return ctx->fail(WC_ERR_CUDA, "cudaStreamCreate");
+    }
+    // items and scratch were staged on the caller's stream
+    cudaEventRecord(pl->in_ev, stream);
+    cudaStreamWaitEvent(pl->own, pl->in_ev, 0);
     *out = pl;
     return WC_OK;
 }
@@ -433,14 +443,17 @@ wc_status wc_plan_run(wc_plan *pl, const uint8_t *d_text, const uint64_t *d_offs
         if (st != WC_OK) return st;
     }
     pl->tuned = true;
-    if (!pl->exec || pl->g_text != d_text || pl->g_off != d_offsets || pl->g_cls != d_class || pl->g_stream != stream) {
+    // the graph lives on the plan's own stream, ordered after the caller's
+    cudaEventRecord(pl->in_ev, stream);
+    cudaStreamWaitEvent(pl->own, pl->in_ev, 0);
+    if (!pl->exec || pl->g_text != d_text || pl->g_off != d_offsets || pl->g_cls != d_class) {
         if (pl->exec) { cudaGraphExecDestroy(pl->exec); pl->exec = nullptr; }
         cudaGraph_t graph = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+        cudaError_t e = cudaStreamBeginCapture(pl->own, cudaStreamCaptureModeThreadLocal);
         uint64_t n = 0;
         if (e == cudaSuccess) {
-            cudaError_t e2 = batch_enqueue(b, d_text, d_offsets, d_class, stream, b->shape_small, b->shape_medium, &n);
-            e = cudaStreamEndCapture(stream, &graph);
+            cudaError_t e2 = batch_enqueue(b, d_text, d_offsets, d_class, pl->own, b->shape_small, b->shape_medium, &n);
+            e = cudaStreamEndCapture(pl->own, &graph);
             if (e == cudaSuccess) e = e2;
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&pl->exec, graph, 0);
@@ -449,7 +462,6 @@ wc_status wc_plan_run(wc_plan *pl, const uint8_t *d_text, const uint64_t *d_offs
         pl->g_text = d_text;
         pl->g_off = d_offsets;
         pl->g_cls = d_class;
-        pl->g_stream = stream;
         pl->graph_launches = n;
     }
     // the plan's batch is rewritten: drop tables built from the previous run
@@ -464,17 +476,21 @@ wc_status wc_plan_run(wc_plan *pl, const uint8_t *d_text, const uint64_t *d_offs
     b->synced = false;
     b->word_bytes = 0;
     b->stream = stream;
-    cudaError_t e = cudaGraphLaunch(pl->exec, stream);
+    cudaError_t e = cudaGraphLaunch(pl->exec, pl->own);
     if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaGraphLaunch");
     ctx->launches += pl->graph_launches;
-    cudaEventRecord(b->done, stream);
+    cudaEventRecord(b->done, pl->own);
+    cudaStreamWaitEvent(stream, b->done, 0);
     *out = b;
     return WC_OK;
 }
 
 void wc_plan_free(wc_plan *pl) {
     if (!pl) return;
+    if (pl->own) cudaStreamSynchronize(pl->own);
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->in_ev) cudaEventDestroy(pl->in_ev);
+    if (pl->own) cudaStreamDestroy(pl->own);
     if (pl->b) {
         batch_release_scratch(pl->b, pl->b->stream);
         wc_batch_free(pl->b);

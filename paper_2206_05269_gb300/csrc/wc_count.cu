@@ -11,13 +11,13 @@
 //     image (4 keys per bucket, a key lives in one of two buckets).
 //  1. One persistent 512-thread block per SM copies that image into shared
 //     memory (keys read-only, counts zeroed) and walks its chunks through a
-//     ring of four buffers.  Each chunk window (16 bytes before, 64 after,
+//     ring of eight buffers.  Each chunk window (16 bytes before, 64 after,
 //     16-byte aligned in absolute address space) is staged by a TMA bulk
 //     copy that completes a "full" mbarrier; windows that touch the
 //     document's edges are staged by plain loads with the outside masked to
 //     spaces (a document edge separates words).  Warps never wait for each
 //     other: each warp releases a buffer when its words there are consumed,
-//     and the last warp to release it issues the copy of the chunk four
+//     and the last warp to release it issues the copy of the chunk eight
 //     places ahead.
 //  2. A warp classifies 512-byte strips: one 16-bit letter mask per lane
 //     (SWAR), word starts = letter & !previous letter, the previous byte
@@ -41,13 +41,13 @@ namespace wc {
 constexpr int kBlock = 512;           // threads of the main counting kernel
 constexpr int kWarps = kBlock / 32;
 constexpr int kChunk = kWarps * 512;  // bytes per chunk: one 512-byte strip per warp
-constexpr int kStages = 4;            // chunk buffers in flight per block
+constexpr int kStages = 8;            // chunk buffers in flight per block (64 KB per SM)
 constexpr int kLead = 16;             // window bytes before the chunk
 constexpr int kWinB = kChunk + 96;    // lead + chunk + 64 lookahead + 16 slack
 constexpr int kTokCap = 32 + 256;     // per-warp word queue (< 32 left + <= 256 per strip)
 constexpr int kTailCap = 64;          // per-warp tail queue
 constexpr int kLongCap = 48;          // per-warp queue of words of 17+ letters (< 16 left + <= 32 per step)
-constexpr int kHeadBuckets = 3072;    // 12288 head slots
+constexpr int kHeadBuckets = 2048;    // 8192 head slots
 constexpr int kSamplePieces = 64;
 constexpr int kSamplePieceBytes = 65536;
 constexpr uint64_t kHeadMinBytes = 16ull << 20;
@@ -221,13 +221,54 @@ struct Counter2 {
         __syncwarp();
         if (tailn >= 32) {
             tailn -= 32;
-            insert(tailq[tailn + lane]);
+            const uint4 k = tailq[tailn + lane];
             __syncwarp();
+            complete();  // the previous 32: their slot loads have had time to land
+            issue(k);
         }
     }
     __device__ __forceinline__ void insert(uint4 k) {
         if (!SAMPLE) table_insert_key(a.g, k, 1ull);
         else global_insert8(a.g, ((unsigned long long)k.y << 32) | k.x, 1ull);
+    }
+
+    // Tail inserts in two halves.  issue() computes the home slot of the key
+    // and starts loading the key stored there; complete() (called when the
+    // next 32 words are ready, so the load had time to arrive) finishes the
+    // insert: a matching key gets a fire-and-forget add, an empty or
+    // half-written slot is settled by the CAS, a different key continues the
+    // probe at the next slot.
+    bool pend = false, p16 = false;
+    uint4 pk;
+    unsigned long long pslot = 0, pv0 = 0, pv1 = 0;
+    __device__ __forceinline__ void issue(uint4 k) {
+        pk = k;
+        pend = true;
+        p16 = !SAMPLE && (k.z | k.w) != 0u;
+        if (!p16) {
+            const unsigned long long key = ((unsigned long long)k.y << 32) | k.x;
+            pslot = hash8(key) >> __clzll((long long)a.g.mask8);
+            pv0 = ld_u64(&a.g.slots8[pslot].key);
+        } else {
+            pslot = hash_key(k) & a.g.mask;
+            const unsigned long long *kp = reinterpret_cast<const unsigned long long *>(&a.g.slots[pslot].key);
+            pv0 = ld_u64(kp);
+            pv1 = ld_u64(kp + 1);
+        }
+    }
+    __device__ __forceinline__ void complete() {
+        if (!pend) return;
+        pend = false;
+        if (!p16) {
+            const unsigned long long key = ((unsigned long long)pk.y << 32) | pk.x;
+            if (pv0 == key) { red_add_u64(&a.g.slots8[pslot].cnt, 1ull); return; }
+            global_insert8_from(a.g, key, 1ull, pslot);
+        } else {
+            const unsigned long long k0 = ((unsigned long long)pk.y << 32) | pk.x;
+            const unsigned long long k1 = ((unsigned long long)pk.w << 32) | pk.z;
+            if (pv0 == k0 && pv1 == k1) { red_add_u64(&a.g.slots[pslot].cnt, 1ull); return; }
+            global_insert16_from(a.g, pk, 1ull, pslot);
+        }
     }
 };
 
@@ -375,6 +416,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_count2(Count2Args a) {
         const uint32_t total = __shfl_sync(kFull, incl, 31);
         uint32_t off = tcount + incl - c1;
         const uint32_t pbase = (uint32_t)(sbase + 16 * lane);
+        static_assert(kStages <= 8 && (kStages & (kStages - 1)) == 0, "3-bit buffer tag in queued words");
         const uint32_t btag = (uint32_t)b << 19;
         while (Ss) {
             int j = __ffs(Ss) - 1;
@@ -411,13 +453,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_count2(Count2Args a) {
         uint32_t bq = 0;
         for (; bq + 32 <= tcount; bq += 32) {
             const uint32_t e = tok[bq + lane];
-            ctr.word(ring + ((e >> 19) & 3u) * kWinB, true, e & 0x7FFFFu);
+            ctr.word(ring + ((e >> 19) & (uint32_t)(kStages - 1)) * kWinB, true, e & 0x7FFFFu);
         }
         uint32_t rem = tcount - bq;
         const uint32_t old_left = tprev > bq ? tprev - bq : 0u;
         if (old_left) {  // words of the previous chunk still queued: finish them all now
             const uint32_t e = (uint32_t)lane < rem ? tok[bq + lane] : 0u;
-            ctr.word(ring + ((e >> 19) & 3u) * kWinB, (uint32_t)lane < rem, e & 0x7FFFFu);
+            ctr.word(ring + ((e >> 19) & (uint32_t)(kStages - 1)) * kWinB, (uint32_t)lane < rem, e & 0x7FFFFu);
             rem = 0;
         } else if (bq) {
             uint32_t e = (uint32_t)lane < rem ? tok[bq + lane] : 0u;
@@ -432,11 +474,12 @@ __global__ void __launch_bounds__(kBlock, 1) k_count2(Count2Args a) {
     // ---- drain: queued words of the last chunk, then the tail and long queues
     if (!timed_out) {
         const uint32_t e = (uint32_t)lane < tcount ? tok[lane] : 0u;
-        ctr.word(ring + ((e >> 19) & 3u) * kWinB, (uint32_t)lane < tcount, e & 0x7FFFFu);
+        ctr.word(ring + ((e >> 19) & (uint32_t)(kStages - 1)) * kWinB, (uint32_t)lane < tcount, e & 0x7FFFFu);
         if (!SAMPLE) {
             flush_long(0, longn < 32 ? longn : 32);
             if (longn > 32) flush_long(32, longn - 32);
         }
+        ctr.complete();
         if ((uint32_t)lane < ctr.tailn) ctr.insert(ctr.tailq[lane]);
         __syncwarp();
     }
@@ -472,17 +515,40 @@ __global__ void k_head_hist(const G8Slot *s, unsigned long long cap, uint32_t *h
         if (h[i]) atomicAdd(&hist[i], h[i]);
 }
 
-// Smallest count threshold t >= 2 that keeps at most kmax words.
-__global__ void k_head_threshold(const uint32_t *hist, uint32_t kmax, uint32_t *meta) {
-    if (threadIdx.x == 0) {
-        uint32_t acc = 0, t = 4096;
-        for (int c = 4095; c >= 2; c--) {
-            if (acc + hist[c] > kmax) break;
-            acc += hist[c];
-            t = (uint32_t)c;
-        }
-        meta[0] = t;  // threshold
-        meta[1] = 0;  // candidates
+// Smallest count threshold t >= 2 that keeps at most kmax words: suffix sums
+// of the histogram (one block of 1024 threads, 4 bins each).
+__global__ void __launch_bounds__(1024) k_head_threshold(const uint32_t *hist, uint32_t kmax, uint32_t *meta) {
+    __shared__ uint32_t part[1024];
+    __shared__ uint32_t best;
+    const uint32_t t = threadIdx.x;
+    // bins of thread t, from high counts down: 4095-4t .. 4092-4t
+    uint32_t v[4], s = 0;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const int c = 4095 - 4 * (int)t - j;
+        v[j] = c >= 2 ? hist[c] : 0u;
+        s += v[j];
+    }
+    part[t] = s;
+    if (t == 0) best = 4096;
+    __syncthreads();
+    for (int w = 1; w < 1024; w <<= 1) {  // inclusive prefix over threads = suffix over counts
+        uint32_t x = t >= (uint32_t)w ? part[t - w] : 0u;
+        __syncthreads();
+        part[t] += x;
+        __syncthreads();
+    }
+    uint32_t acc = part[t] - s;  // words with a count above this thread's bins
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const int c = 4095 - 4 * (int)t - j;
+        acc += v[j];
+        if (c >= 2 && acc <= kmax) atomicMin(&best, (uint32_t)c);
+    }
+    __syncthreads();
+    if (t == 0) {
+        meta[0] = best;  // threshold
+        meta[1] = 0;     // candidates
     }
 }
 
@@ -578,7 +644,7 @@ cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
         k_count2<true><<<g, kBlock, kCountSmem, s>>>(sa);
         const uint32_t kmax = kHeadBuckets * 4 * 88 / 100;
         k_head_hist<<<sms, 256, 0, s>>>(sample, kSampleSlots, hist);
-        k_head_threshold<<<1, 32, 0, s>>>(hist, kmax, meta);
+        k_head_threshold<<<1, 1024, 0, s>>>(hist, kmax, meta);
         k_head_collect<<<sms * 2, 256, 0, s>>>(sample, kSampleSlots, meta, cand, kmax);
         k_head_build<<<1, 1024, 0, s>>>(cand, meta, kmax, kHeadBuckets, image);
         a.head = image;

@@ -232,24 +232,6 @@ struct GTable {
 };
 
 constexpr int kGlobalProbeLimit = 4096;
-constexpr uint32_t kSpinLimit = 1u << 20;  // x 64 ns sleeps: about 0.1 s
-
-// Adds `add` to word `k` (<= 16 letters) in the global table.
-__device__ __forceinline__ void global_insert(const GTable &g, uint4 k, uint64_t h, unsigned long long add) {
-    unsigned long long s = h & g.mask;
-    const uint4 zero = make_uint4(0, 0, 0, 0);
-    for (int probe = 0; probe < kGlobalProbeLimit; probe++) {
-        GSlot *slot = g.slots + s;
-        uint4 old = cas128_global(&slot->key, zero, k);
-        if (key_zero(old) || key_eq(old, k)) {
-            atomicAdd(&slot->cnt, add);
-            return;
-        }
-        s = (s + 1) & g.mask;
-    }
-    atomicOr(g.status, ST_TABLE_FULL);
-}
-
 // Lowercased byte comparison of two runs of `len` letters.
 __device__ __forceinline__ bool bytes_eq_lower(const uint8_t *a, const uint8_t *b, uint64_t len) {
     for (uint64_t i = 0; i < len; i++)
@@ -328,8 +310,9 @@ __device__ __forceinline__ unsigned long long ld_u64(const unsigned long long *p
     asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void global_insert8(const GTable &g, unsigned long long key, unsigned long long add) {
-    unsigned long long s = hash8(key) >> __clzll((long long)g.mask8);  // top bits
+// Probes from slot s onwards (s = the home slot, or a later slot of its chain).
+__device__ __forceinline__ void global_insert8_from(const GTable &g, unsigned long long key, unsigned long long add,
+                                                    unsigned long long s) {
     for (int probe = 0; probe < kGlobalProbeLimit; probe++) {
         G8Slot *slot = g.slots8 + s;
         unsigned long long cur = ld_u64(&slot->key);
@@ -342,15 +325,17 @@ __device__ __forceinline__ void global_insert8(const GTable &g, unsigned long lo
     }
     atomicOr(g.status, ST_TABLE_FULL);
 }
+__device__ __forceinline__ void global_insert8(const GTable &g, unsigned long long key, unsigned long long add) {
+    global_insert8_from(g, key, add, hash8(key) >> __clzll((long long)g.mask8));  // top bits
+}
 
 // Words of 9..16 letters: both key halves are non-zero, so two 64-bit loads
 // that each see the corresponding half of `k` can only come from a slot that
 // holds exactly `k` (halves are written once, by one 128-bit CAS).  Loads that
 // see a zero half may have caught a claim in flight (possibly of this very
 // word), so that case is settled by the CAS, which returns the whole key.
-__device__ __forceinline__ void global_insert16(const GTable &g, uint4 k, unsigned long long add) {
-    const uint64_t h = hash_key(k);
-    unsigned long long s = h & g.mask;
+__device__ __forceinline__ void global_insert16_from(const GTable &g, uint4 k, unsigned long long add,
+                                                     unsigned long long s) {
     const unsigned long long k0 = ((unsigned long long)k.y << 32) | k.x, k1 = ((unsigned long long)k.w << 32) | k.z;
     const uint4 zero = make_uint4(0, 0, 0, 0);
     for (int probe = 0; probe < kGlobalProbeLimit; probe++) {
@@ -369,6 +354,9 @@ __device__ __forceinline__ void global_insert16(const GTable &g, uint4 k, unsign
         s = (s + 1) & g.mask;
     }
     atomicOr(g.status, ST_TABLE_FULL);
+}
+__device__ __forceinline__ void global_insert16(const GTable &g, uint4 k, unsigned long long add) {
+    global_insert16_from(g, k, add, hash_key(k) & g.mask);
 }
 
 // Any word of at most 16 letters given as a 16-byte key.

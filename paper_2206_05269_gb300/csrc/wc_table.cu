@@ -235,37 +235,47 @@ __global__ void __launch_bounds__(kSortThreads) k_pass_count(SortScratch s, int 
     s.tile_hist[(unsigned long long)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of the digit-major tile histogram (one block).
-__global__ void __launch_bounds__(1024) k_pass_scan(SortScratch s, int p, const unsigned long long *meta) {
-    __shared__ uint32_t part[1024];
+// Exclusive scan of the digit-major tile histogram: block d scans digit d's
+// row of tile counts, starting from the number of elements with a smaller
+// digit (from the all-pass histogram).  256 blocks of 256 threads.
+__global__ void __launch_bounds__(256) k_pass_scan(SortScratch s, int p, const unsigned long long *meta) {
+    __shared__ uint32_t part[256];
+    __shared__ uint32_t base_s;
     const unsigned long long n = meta[0];
-    if (threadIdx.x == 0 && blockIdx.x == 0) {}
     const bool skip = pass_skipped(s, p, n) || n == 0;
     if (skip) {
-        if (threadIdx.x == 0) s.cur[p + 1] = s.cur[p];
+        if (blockIdx.x == 0 && threadIdx.x == 0) s.cur[p + 1] = s.cur[p];
         return;
     }
-    const unsigned long long ntiles = (n + kSortTile - 1) / kSortTile;
-    const unsigned long long total = 256ull * ntiles;
-    const unsigned long long per = (total + blockDim.x - 1) / blockDim.x;
-    const unsigned long long b = threadIdx.x * per, e = b + per < total ? b + per : total;
-    uint32_t sum = 0;
-    for (unsigned long long i = b; i < e; i++) sum += s.tile_hist[i];
-    part[threadIdx.x] = sum;
+    const uint32_t d = blockIdx.x, t = threadIdx.x;
+    // base = elements whose digit is below d
+    part[t] = t < d ? s.hist_all[p * 256 + t] : 0u;
     __syncthreads();
-    for (int d = 1; d < (int)blockDim.x; d <<= 1) {
-        uint32_t v = threadIdx.x >= (unsigned)d ? part[threadIdx.x - d] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += v;
+    for (int w = 128; w; w >>= 1) {
+        if (t < (uint32_t)w) part[t] += part[t + w];
         __syncthreads();
     }
-    uint32_t run = part[threadIdx.x] - sum;
-    for (unsigned long long i = b; i < e; i++) {
-        uint32_t v = s.tile_hist[i];
-        s.tile_hist[i] = run;
-        run += v;
+    if (t == 0) base_s = part[0];
+    __syncthreads();
+    uint32_t run = base_s;
+    const unsigned long long ntiles = (n + kSortTile - 1) / kSortTile;
+    uint32_t *row = s.tile_hist + (unsigned long long)d * ntiles;
+    for (unsigned long long c0 = 0; c0 < ntiles; c0 += 256) {
+        const unsigned long long i = c0 + t;
+        const uint32_t v = i < ntiles ? row[i] : 0u;
+        __syncthreads();
+        part[t] = v;
+        __syncthreads();
+        for (int w = 1; w < 256; w <<= 1) {
+            uint32_t x = t >= (uint32_t)w ? part[t - w] : 0u;
+            __syncthreads();
+            part[t] += x;
+            __syncthreads();
+        }
+        if (i < ntiles) row[i] = run + part[t] - v;
+        run += part[255];
     }
-    if (threadIdx.x == 0) s.cur[p + 1] = 1u - s.cur[p];
+    if (d == 0 && t == 0) s.cur[p + 1] = 1u - s.cur[p];
 }
 
 // Stable scatter: warp w ranks its 512 consecutive elements in order with
@@ -414,7 +424,7 @@ cudaError_t sort_entries(SortScratch &ss, const unsigned long long *meta, const 
     for (int p = 0; p < passes; p++) {
         if (p == 16) k_fix_long<<<grid_for(cap, 256, sms * 4), 256, 0, st>>>(ss, v, meta);
         k_pass_count<<<ntiles, kSortThreads, 0, st>>>(ss, p, meta);
-        k_pass_scan<<<1, 1024, 0, st>>>(ss, p, meta);
+        k_pass_scan<<<256, 256, 0, st>>>(ss, p, meta);
         k_pass_scatter<<<ntiles, kSortThreads, 0, st>>>(ss, p, meta);
     }
     return cudaGetLastError();

@@ -1,16 +1,21 @@
 """Served counting: a request loop with continuous batching.
 
 Requests (a byte string each, in pinned host memory) arrive over time.  The
-loop keeps up to `max_rounds` rounds on the GPU at once, each on its own CUDA
-stream.  Whenever a stream is free it admits every request that has arrived
-(up to a byte budget per round), copies them host -> device into the round's
-resident text buffer, and counts them all with one wc_count_batched call: each
-request is a document, answered with its own table (32-bit counts, sorted by
-count desc then word asc) and its top-k (the table's first k rows).  Requests
-that arrive while rounds are running are admitted as soon as a stream and
-device memory free up, so their work overlaps on the device.  The context's
-device-memory budget bounds what is admitted; a round the budget cannot hold
-waits for running rounds to finish.
+loop keeps up to `max_inflight` units of work on the GPU at once, each on its
+own CUDA stream:
+  - small requests (up to `big_bytes`) that have arrived are admitted
+    together as one round: copied host -> device into the round's resident
+    text buffer and counted by one wc_count_batched call, each request a
+    document with its own table;
+  - a large request is a unit of its own, counted by wc_count (all SMs,
+    shared-memory head, capacities learned from earlier requests).
+Requests that arrive while work is running are admitted as soon as a stream
+and device memory free up, so their work overlaps on the device.  Each
+request is answered with its table (32-bit counts, count desc then word asc)
+and its top-k (the table's first k rows).  The context's device-memory budget
+bounds admission: work the budget cannot hold waits for running work to
+finish.  A round whose device tables overflow is recounted request by request
+with growing capacities, so answers are always exact.
 
 `serve_fifo` is the plain path for comparison: one request at a time, in
 arrival order, one wc_count launch per request.
@@ -52,15 +57,17 @@ class Answer:
         return [(self.words[self.offs[i]:self.offs[i + 1]].tobytes(), int(self.counts[i])) for i in range(n)]
 
 
-class _Round:
-    def __init__(self, reqs, stream, dev_text, dev_offs, batch, h_offs):
+class _Work:
+    """One unit on the GPU: a round of small requests or one large request."""
+
+    def __init__(self, reqs, stream, keep, batch=None, table=None, h_offs=None):
+        import torch
         self.reqs = reqs
         self.stream = stream
-        self.dev_text = dev_text
-        self.dev_offs = dev_offs
+        self.keep = keep          # device tensors that must outlive the work
         self.batch = batch
+        self.table = table
         self.h_offs = h_offs
-        import torch
         self.event = torch.cuda.Event()
         self.event.record(stream)
 
@@ -73,88 +80,139 @@ def _wait_until(t_target: float, t0: float):
         time.sleep(min(dt, 0.0005) if dt > 0.0002 else 0)
 
 
-def serve_batched(counter: wc.Counter, requests: list[Request], topk: int = 100, max_rounds: int = 4,
-                  round_bytes: int = 512 << 20, keep_tables: bool = True, device: int = 0):
+def _to_device(reqs, dev, stream):
+    import torch
+    h_offs = np.zeros(len(reqs) + 1, dtype=np.uint64)
+    h_offs[1:] = np.cumsum([r.data.numel() for r in reqs])
+    n = int(h_offs[-1])
+    with torch.cuda.stream(stream):
+        text = torch.empty(max(16, n), dtype=torch.uint8, device=dev)
+        for j, r in enumerate(reqs):
+            if r.data.numel():
+                text[int(h_offs[j]):int(h_offs[j + 1])].copy_(r.data, non_blocking=True)
+    return text, h_offs
+
+
+def serve_batched(counter: wc.Counter, requests: list[Request], topk: int = 100, max_inflight: int = 6,
+                  round_bytes: int = 256 << 20, big_bytes: int = 4 << 20, keep_tables: bool = True,
+                  device: int = 0):
     """Runs the request stream through the continuous-batching loop and returns
     one Answer per request (in request order) plus run statistics."""
     import torch
     dev = torch.device("cuda", device)
-    streams = [torch.cuda.Stream(device=dev) for _ in range(max_rounds)]
-    free_streams = deque(streams)
-    pending: deque[Request] = deque()
-    running: deque[_Round] = deque()
+    free_streams = deque(torch.cuda.Stream(device=dev) for _ in range(max_inflight))
+    small: deque[Request] = deque()
+    big: deque[Request] = deque()
+    running: deque[_Work] = deque()
     answers: dict[int, Answer] = {}
     order = sorted(requests, key=lambda r: r.arrival)
     nxt = 0
     t0 = time.perf_counter()
-    rounds = 0
+    stats = {"rounds": 0, "large": 0, "recounted": 0}
 
-    def finish(rd: _Round):
-        rd.event.synchronize()
-        b = rd.batch
-        if b.status() != wc.WC_OK:
-            raise wc.WcError(b.status(), wc.wc_last_error(counter.ctx))
-        ds, dn, w, o, c = b.export(rd.stream)
-        now = time.perf_counter() - t0
-        for j, rq in enumerate(rd.reqs):
-            s0, n = int(ds[j]), int(dn[j])
-            m = n if keep_tables else min(n, topk)
-            ww = w[o[s0]:o[s0 + m]].copy()
-            oo = (o[s0:s0 + m + 1] - o[s0]).astype(np.uint64)
-            answers[rq.rid] = Answer(rq.rid, rq.arrival, now, ww, oo, c[s0:s0 + m].copy(), topk)
-        del rd.batch
-        free_streams.append(rd.stream)
+    def answer(rq, w, o, c, s0, n):
+        m = n if keep_tables else min(n, topk)
+        answers[rq.rid] = Answer(rq.rid, rq.arrival, time.perf_counter() - t0, w[o[s0]:o[s0 + m]].copy(),
+                                 (o[s0:s0 + m + 1] - o[s0]).astype(np.uint64), c[s0:s0 + m].astype(np.uint32), topk)
+
+    def recount(rq, stream):  # exact fallback with growing capacities
+        with torch.cuda.stream(stream):
+            text = torch.empty(max(16, rq.data.numel()), dtype=torch.uint8, device=dev)[:rq.data.numel()]
+            if rq.data.numel():
+                text.copy_(rq.data, non_blocking=True)
+            t = counter.count_checked(text, stream=stream)
+            w, o, c = t.export(stream)
+        answer(rq, w, o, c, 0, c.size)
+        stats["recounted"] += 1
+
+    def finish(wk: _Work):
+        wk.event.synchronize()
+        if wk.table is not None:
+            st = wk.table.status()
+            if st == wc.WC_ERR_CAPACITY:
+                recount(wk.reqs[0], wk.stream)
+            else:
+                w, o, c = wk.table.export(wk.stream)
+                answer(wk.reqs[0], w, o, c, 0, c.size)
+            wk.table.free()
+        else:
+            st = wk.batch.status()
+            if st == wc.WC_ERR_CAPACITY:
+                for rq in wk.reqs:
+                    recount(rq, wk.stream)
+            elif st != wc.WC_OK:
+                raise wc.WcError(st, wc.wc_last_error(counter.ctx))
+            else:
+                ds, dn, w, o, c = wk.batch.export(wk.stream)
+                for j, rq in enumerate(wk.reqs):
+                    answer(rq, w, o, c, int(ds[j]), int(dn[j]))
+            del wk.batch
+        free_streams.append(wk.stream)
+
+    def launch(stream):
+        """Starts the next unit on `stream`; False if the budget refused it."""
+        if big and (not small or big[0].arrival <= small[0].arrival):
+            rq = big.popleft()
+            text, _ = _to_device([rq], dev, stream)
+            try:
+                tab = counter.count(text[:rq.data.numel()], stream=stream)
+            except wc.WcError as e:
+                big.appendleft(rq)
+                if e.status != wc.WC_ERR_BUDGET:
+                    raise
+                return False
+            running.append(_Work([rq], stream, text, table=tab))
+            stats["large"] += 1
+            return True
+        take, nbytes = [], 0
+        while small and (not take or nbytes + small[0].data.numel() <= round_bytes):
+            r = small.popleft()
+            take.append(r)
+            nbytes += r.data.numel()
+        text, h_offs = _to_device(take, dev, stream)
+        try:
+            offs = torch.from_numpy(h_offs.view(np.int64)).to(dev)
+            batch = counter.count_batched(text, offs, h_offs, stream=stream)
+        except wc.WcError as e:
+            for r in reversed(take):
+                small.appendleft(r)
+            if e.status != wc.WC_ERR_BUDGET:
+                raise
+            return False
+        running.append(_Work(take, stream, (text, offs), batch=batch, h_offs=h_offs))
+        stats["rounds"] += 1
+        return True
 
     while len(answers) < len(order):
         now = time.perf_counter() - t0
         while nxt < len(order) and order[nxt].arrival <= now:
-            pending.append(order[nxt])
+            r = order[nxt]
+            (big if r.data.numel() > big_bytes else small).append(r)
             nxt += 1
-        # completed rounds first: they free streams and memory
+        progressed = False
         while running and running[0].event.query():
             finish(running.popleft())
-        if pending and free_streams:
-            take, nbytes = [], 0
-            while pending and (not take or nbytes + pending[0].data.numel() <= round_bytes):
-                r = pending.popleft()
-                take.append(r)
-                nbytes += r.data.numel()
+            progressed = True
+        if (small or big) and free_streams:
             stream = free_streams.popleft()
-            h_offs = np.zeros(len(take) + 1, dtype=np.uint64)
-            h_offs[1:] = np.cumsum([r.data.numel() for r in take])
-            try:
-                with torch.cuda.stream(stream):
-                    text = torch.empty(max(16, nbytes), dtype=torch.uint8, device=dev)
-                    for j, r in enumerate(take):
-                        if r.data.numel():
-                            text[int(h_offs[j]):int(h_offs[j + 1])].copy_(r.data, non_blocking=True)
-                    offs = torch.from_numpy(h_offs.view(np.int64)).to(dev, non_blocking=False)
-                    batch = counter.count_batched(text, offs, h_offs, stream=stream)
-            except wc.WcError as e:
-                if e.status != wc.WC_ERR_BUDGET or not running:
-                    raise
-                for r in reversed(take):  # memory is busy: wait for a round to finish
-                    pending.appendleft(r)
-                free_streams.appendleft(stream)
-                finish(running.popleft())
+            if launch(stream):
                 continue
-            running.append(_Round(take, stream, text, offs, batch, h_offs))
-            rounds += 1
+            free_streams.appendleft(stream)  # budget: wait for running work
+            if running:
+                finish(running.popleft())
             continue
-        if running and (not pending or not free_streams):
-            if nxt < len(order) and not pending:
-                # idle until the next arrival or a completion, whichever comes first
-                if running[0].event.query():
-                    continue
-                time.sleep(0.00005)
+        if progressed:
+            continue
+        if running:
+            if nxt < len(order) and not (small or big):
+                time.sleep(0.00005)  # idle until the next arrival or a completion
                 continue
             finish(running.popleft())
             continue
         if nxt < len(order):
             _wait_until(order[nxt].arrival, t0)
-    wall = time.perf_counter() - t0
-    out = [answers[r.rid] for r in requests]
-    return out, {"rounds": rounds, "wall_s": wall}
+    stats["wall_s"] = time.perf_counter() - t0
+    return [answers[r.rid] for r in requests], stats
 
 
 def serve_fifo(counter: wc.Counter, requests: list[Request], topk: int = 100, keep_tables: bool = True,

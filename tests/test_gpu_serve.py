@@ -35,8 +35,8 @@ def test_mix_equals_alone_and_oracle(ctr):
     from gpu_util import to_dev
     pool, trip, reqs = make_requests()
     assert len(reqs) >= 20
-    answers, stats = serve.serve_batched(ctr, reqs, topk=100, max_rounds=3)
-    assert stats["rounds"] >= 2
+    answers, stats = serve.serve_batched(ctr, reqs, topk=100, max_inflight=3, big_bytes=512 << 10)
+    assert stats["rounds"] >= 2 and stats["large"] >= 1
     for (a, s, e), ans in zip(trip, answers):
         data = pool[s:e].tobytes()
         alone = ctr.count_checked(to_dev(data)).as_list()
