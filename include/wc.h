@@ -212,14 +212,17 @@ wc_status wc_count_noalloc(const uint8_t *d_text, uint64_t nbytes, uint64_t *d_k
                            uint64_t *d_meta, cudaStream_t stream);
 
 /* Stage tracing.  While enabled, the context records CUDA events on the
- * launching stream around each counting kernel and around each compaction +
- * sort stage of wc_count / wc_count_ex / wc_merge, and counts the kernels
- * it launches.  wc_profile_read waits for the recorded events and returns
- * the summed stage times in milliseconds, how many counting kernels were
- * timed, and how many kernels the library launched since enabling. */
+ * launching stream around three stages of wc_count / wc_count_ex (head
+ * selection: the sampling pass and the head kernels; the main counting
+ * kernel alone; compaction + sort) and around the compaction + sort of
+ * wc_merge, and counts the kernels it launches.  wc_profile_read waits for
+ * the recorded events and returns the summed stage times in milliseconds
+ * (any output pointer may be null), how many main counting kernels were
+ * timed, and how many kernels the library launched since enabling.
+ * Enabling (or disabling) discards what was recorded. */
 wc_status wc_profile_enable(wc_ctx *ctx, int enable);
-wc_status wc_profile_read(wc_ctx *ctx, double *ms_count, double *ms_finish, uint64_t *count_launches,
-                          uint64_t *kernel_launches);
+wc_status wc_profile_read(wc_ctx *ctx, double *ms_head, double *ms_count, double *ms_finish,
+                          uint64_t *count_launches, uint64_t *kernel_launches);
 
 const char *wc_status_str(wc_status s);
 const char *wc_last_error(const wc_ctx *ctx);

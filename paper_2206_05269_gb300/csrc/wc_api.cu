@@ -66,16 +66,26 @@ void wc_ctx::release(void *p, size_t bytes, cudaStream_t s) {
 }
 
 void wc_ctx::prof_mark(std::vector<cudaEvent_t> &v, cudaStream_t s) {
-    if (!profile) return;
+    cudaEvent_t e = prof_event(v);
+    if (e) cudaEventRecord(e, s);
+}
+
+cudaEvent_t wc_ctx::prof_event(std::vector<cudaEvent_t> &v) {
+    if (!profile) return nullptr;
     cudaEvent_t e;
-    cudaEventCreate(&e);
-    cudaEventRecord(e, s);
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
     v.push_back(e);
+    return e;
 }
 
 static void prof_clear(wc_ctx *ctx) {
+    for (auto e : ctx->ev_head) cudaEventDestroy(e);
     for (auto e : ctx->ev_count) cudaEventDestroy(e);
     for (auto e : ctx->ev_finish) cudaEventDestroy(e);
+    ctx->ev_head.clear();
     ctx->ev_count.clear();
     ctx->ev_finish.clear();
     ctx->launches = 0;
@@ -101,13 +111,15 @@ static double sum_pairs(wc_ctx *ctx, const std::vector<cudaEvent_t> &v, cudaErro
     return tot;
 }
 
-wc_status wc_profile_read(wc_ctx *ctx, double *ms_count, double *ms_finish, uint64_t *count_launches,
-                          uint64_t *kernel_launches) {
+wc_status wc_profile_read(wc_ctx *ctx, double *ms_head, double *ms_count, double *ms_finish,
+                          uint64_t *count_launches, uint64_t *kernel_launches) {
     if (!ctx) return WC_ERR_INVALID_ARG;
     cudaSetDevice(ctx->device);
     cudaError_t err = cudaSuccess;
+    double h = sum_pairs(ctx, ctx->ev_head, &err);
     double a = sum_pairs(ctx, ctx->ev_count, &err), b = sum_pairs(ctx, ctx->ev_finish, &err);
     if (err != cudaSuccess) return ctx->cuda_fail(err, "wc_profile_read");
+    if (ms_head) *ms_head = h;
     if (ms_count) *ms_count = a;
     if (ms_finish) *ms_finish = b;
     if (count_launches) *count_launches = ctx->ev_count.size() / 2;
@@ -425,8 +437,11 @@ wc_status wc_count_ex(wc_ctx *ctx, const uint8_t *d_text, uint64_t nbytes, const
     if (st != WC_OK) { ctx->release(cs.mem, cs.bytes, stream); return st; }
     t->src_bytes = nbytes;
     const GTable g = cs.gtable(t->dt.d_status);
-    CountLaunch cl{d_text, 0, nbytes, g, 0, cs.head};
-    ctx->prof_mark(ctx->ev_count, stream);
+    CountLaunch cl{d_text, 0, nbytes, g, 0, cs.head, {nullptr, nullptr}};
+    // stages: head selection (sampling pass + head kernels), then the main counting kernel
+    ctx->prof_mark(ctx->ev_head, stream);
+    cl.main_ev[0] = ctx->prof_event(ctx->ev_head);
+    cl.main_ev[1] = ctx->prof_event(ctx->ev_count);
     cudaError_t e = launch_count_global(cl, stream);
     ctx->prof_mark(ctx->ev_count, stream);
     ctx->launches += count_global_launches(nbytes, true);

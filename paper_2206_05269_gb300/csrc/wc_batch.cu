@@ -554,7 +554,7 @@ __global__ void k_seg_base(BatchArgs a, unsigned long long *meta) {
 __global__ void k_seg_write(SortScratch ss, BatchArgs a, const unsigned long long *meta, int passes) {
     const unsigned long long n = meta[0], base = meta[8];
     if (!meta[9]) return;
-    const uint32_t *perm = ss.perm[ss.cur[passes]];
+    const uint32_t *perm = ss.perm_buf(ss.cur[passes]);
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t e = perm[i];
@@ -570,7 +570,7 @@ __global__ void k_seg_write(SortScratch ss, BatchArgs a, const unsigned long lon
 __global__ void k_seg_ends(SortScratch ss, BatchArgs a, const unsigned long long *meta, int passes) {
     const unsigned long long n = meta[0], base = meta[8];
     if (!meta[9]) return;
-    const uint32_t *perm = ss.perm[ss.cur[passes]];
+    const uint32_t *perm = ss.perm_buf(ss.cur[passes]);
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t d = ss.doc[perm[i]];

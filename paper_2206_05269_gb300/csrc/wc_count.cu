@@ -52,6 +52,10 @@ constexpr int kSamplePieces = 64;
 constexpr int kSamplePieceBytes = 65536;
 constexpr uint64_t kHeadMinBytes = 16ull << 20;
 constexpr unsigned long long kSampleSlots = 1ull << 19;
+constexpr uint32_t kHeadSortN = kHeadBuckets * 4;  // >= candidates (a power of two)
+constexpr uint32_t kHeadIdxBits = 13;              // candidate index bits of a sort word
+constexpr uint32_t kHeadCntMax = (1u << (32 - kHeadIdxBits)) - 1u;
+static_assert(kHeadSortN <= (1u << kHeadIdxBits), "candidate index fits the sort word");
 
 struct Count2Args {
     const uint8_t *text;
@@ -129,15 +133,13 @@ __device__ __forceinline__ void stage_masked(uint8_t *win, uintptr_t w0, uintptr
 }
 
 // ---------------------------------------------------------------- keys
-// 8 lowercased bytes of win[p, p+len), zero padded (len <= 8), little endian.
+// 8 lowercased bytes of win[p, p+len), zero padded (1 <= len <= 8), little endian.
 __device__ __forceinline__ unsigned long long load_key8(const uint8_t *win, uint32_t p, uint32_t len) {
     const uint32_t *w = reinterpret_cast<const uint32_t *>(win + (p & ~3u));
     const uint32_t sh = (p & 3u) * 8u;
     const uint32_t a0 = w[0], a1 = w[1], a2 = w[2];
-    const int n = (int)len;
-    uint32_t lo = (__funnelshift_r(a0, a1, sh) | 0x20202020u) & byte_keep_mask(n);
-    uint32_t hi = (__funnelshift_r(a1, a2, sh) | 0x20202020u) & byte_keep_mask(n - 4);
-    return ((unsigned long long)hi << 32) | lo;
+    const unsigned long long v = ((unsigned long long)__funnelshift_r(a1, a2, sh) << 32) | __funnelshift_r(a0, a1, sh);
+    return (v | 0x2020202020202020ull) & (~0ull >> (64u - 8u * len));
 }
 
 __device__ __forceinline__ uint32_t head_bucket(unsigned long long key, unsigned long long mul, uint32_t nb) {
@@ -146,21 +148,25 @@ __device__ __forceinline__ uint32_t head_bucket(unsigned long long key, unsigned
 constexpr unsigned long long kHeadMulA = 0x9E3779B97F4A7C15ull;
 constexpr unsigned long long kHeadMulB = 0xC2B2AE3D27D4EB4Full;
 
-// Slot of key in the shared head image, or -1 (two buckets of four).
+// Slot of key in the shared head image, or -1 (two buckets of four).  Both
+// buckets are read at once (four independent 16-byte loads), so a lookup
+// costs one shared-memory round trip and no branch.
 __device__ __forceinline__ int head_find(const unsigned long long *hkey, unsigned long long key, uint32_t nb,
                                          uint32_t *slot) {
-    uint32_t bk = head_bucket(key, kHeadMulA, nb);
-    const ulonglong2 *hb = reinterpret_cast<const ulonglong2 *>(hkey + bk * 4);
-    ulonglong2 u0 = hb[0], u1 = hb[1];
-    int q = u0.x == key ? 0 : u0.y == key ? 1 : u1.x == key ? 2 : u1.y == key ? 3 : -1;
-    if (q < 0) {
-        bk = head_bucket(key, kHeadMulB, nb);
-        hb = reinterpret_cast<const ulonglong2 *>(hkey + bk * 4);
-        u0 = hb[0];
-        u1 = hb[1];
-        q = u0.x == key ? 0 : u0.y == key ? 1 : u1.x == key ? 2 : u1.y == key ? 3 : -1;
-    }
-    *slot = bk * 4 + (uint32_t)(q < 0 ? 0 : q);
+    const uint32_t b1 = head_bucket(key, kHeadMulA, nb), b2 = head_bucket(key, kHeadMulB, nb);
+    const ulonglong2 *h1 = reinterpret_cast<const ulonglong2 *>(hkey + b1 * 4);
+    const ulonglong2 *h2 = reinterpret_cast<const ulonglong2 *>(hkey + b2 * 4);
+    const ulonglong2 u0 = h1[0], u1 = h1[1], v0 = h2[0], v1 = h2[1];
+    int q = -1;
+    q = u0.x == key ? (int)(b1 * 4) : q;
+    q = u0.y == key ? (int)(b1 * 4 + 1) : q;
+    q = u1.x == key ? (int)(b1 * 4 + 2) : q;
+    q = u1.y == key ? (int)(b1 * 4 + 3) : q;
+    q = v0.x == key ? (int)(b2 * 4) : q;
+    q = v0.y == key ? (int)(b2 * 4 + 1) : q;
+    q = v1.x == key ? (int)(b2 * 4 + 2) : q;
+    q = v1.y == key ? (int)(b2 * 4 + 3) : q;
+    *slot = q < 0 ? 0u : (uint32_t)q;
     return q;
 }
 
@@ -418,11 +424,15 @@ __global__ void __launch_bounds__(kBlock, 1) k_count2(Count2Args a) {
         const uint32_t pbase = (uint32_t)(sbase + 16 * lane);
         static_assert(kStages <= 8 && (kStages & (kStages - 1)) == 0, "3-bit buffer tag in queued words");
         const uint32_t btag = (uint32_t)b << 19;
-        while (Ss) {
-            int j = __ffs(Ss) - 1;
-            Ss &= Ss - 1;
-            uint32_t len = (uint32_t)__ffs(~(W >> j)) - 1u;
-            tok[off++] = btag | ((pbase + (uint32_t)j) << 5) | len;
+        // a warp-uniform trip count: no divergent loop to reconverge
+        const uint32_t nmax = __reduce_max_sync(kFull, c1);
+        for (uint32_t r = 0; r < nmax; r++) {
+            if (Ss) {
+                const int j = __ffs(Ss) - 1;
+                Ss &= Ss - 1;
+                const uint32_t len = (uint32_t)__ffs(~(W >> j)) - 1u;
+                tok[off++] = btag | ((pbase + (uint32_t)j) << 5) | len;
+            }
         }
         const uint32_t tnew = total;
         tcount += total;
@@ -553,39 +563,74 @@ __global__ void __launch_bounds__(1024) k_head_threshold(const uint32_t *hist, u
 }
 
 __global__ void k_head_collect(const G8Slot *s, unsigned long long cap, uint32_t *meta, unsigned long long *cand,
-                               uint32_t kmax) {
+                               uint32_t *ccnt, uint32_t kmax) {
     const uint32_t t = meta[0];
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         unsigned long long c = s[i].cnt;
         if (s[i].key && c >= t) {
             uint32_t k = atomicAdd(&meta[1], 1u);
-            if (k < kmax) cand[k] = s[i].key;
+            if (k < kmax) {
+                cand[k] = s[i].key;
+                ccnt[k] = c < kHeadCntMax ? (uint32_t)c : kHeadCntMax;
+            }
         }
     }
 }
 
-// Two-choice placement of the candidates into nb buckets of 4 (one block).
-__global__ void __launch_bounds__(1024) k_head_build(const unsigned long long *cand, const uint32_t *meta,
-                                                     uint32_t kmax, uint32_t nb, unsigned long long *image) {
+// Two-choice placement of the candidates into nb buckets of 4 (one block),
+// most frequent first.  The candidates are sorted by sample count (bitonic
+// sort of count:index words in shared memory) and placed in rounds of 1024;
+// a key whose two buckets are both full is left out of the head and counted
+// in the global table.  Placing by frequency makes sure that only the
+// rarest candidates can be left out: a frequent word missing from the head
+// would send all its occurrences to one global slot, whose atomics then
+// serialise.
+__global__ void __launch_bounds__(1024) k_head_build(const unsigned long long *cand, const uint32_t *ccnt,
+                                                     const uint32_t *meta, uint32_t kmax, uint32_t nb,
+                                                     unsigned long long *image) {
+    __shared__ uint32_t ord[kHeadSortN];
     __shared__ uint32_t fill[kHeadBuckets];
+    const uint32_t n = meta[1] < kmax ? meta[1] : kmax;
+    for (uint32_t i = threadIdx.x; i < kHeadSortN; i += blockDim.x)
+        ord[i] = i < n ? (ccnt[i] << kHeadIdxBits) | i : 0u;  // counts are >= 2: padding sorts last
     for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) fill[i] = 0;
     for (uint32_t i = threadIdx.x; i < nb * 4; i += blockDim.x) image[i] = 0ull;
     __syncthreads();
-    uint32_t n = meta[1] < kmax ? meta[1] : kmax;
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const unsigned long long key = cand[i];
-        uint32_t b1 = head_bucket(key, kHeadMulA, nb), b2 = head_bucket(key, kHeadMulB, nb);
-        uint32_t first = fill[b1] <= fill[b2] ? b1 : b2, second = first == b1 ? b2 : b1;
-        uint32_t slot = atomicAdd(&fill[first], 1u);
-        if (slot < 4) { image[first * 4 + slot] = key; continue; }
-        slot = atomicAdd(&fill[second], 1u);
-        if (slot < 4) image[second * 4 + slot] = key;  // else: not in the head, counted globally
+    for (uint32_t k = 2; k <= kHeadSortN; k <<= 1)
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = threadIdx.x; i < kHeadSortN; i += blockDim.x) {
+                const uint32_t p = i ^ j;
+                if (p > i) {
+                    const uint32_t x = ord[i], y = ord[p];
+                    if ((i & k) == 0 ? x < y : x > y) {  // descending overall
+                        ord[i] = y;
+                        ord[p] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (uint32_t base = 0; base < n; base += blockDim.x) {
+        const uint32_t r = base + threadIdx.x;
+        if (r < n) {
+            const unsigned long long key = cand[ord[r] & ((1u << kHeadIdxBits) - 1u)];
+            uint32_t b1 = head_bucket(key, kHeadMulA, nb), b2 = head_bucket(key, kHeadMulB, nb);
+            uint32_t first = fill[b1] <= fill[b2] ? b1 : b2, second = first == b1 ? b2 : b1;
+            uint32_t slot = atomicAdd(&fill[first], 1u);
+            if (slot < 4) {
+                image[first * 4 + slot] = key;
+            } else {
+                slot = atomicAdd(&fill[second], 1u);
+                if (slot < 4) image[second * 4 + slot] = key;
+            }
+        }
+        __syncthreads();
     }
 }
 
 size_t head_scratch_bytes() {
-    return (size_t)kSampleSlots * sizeof(G8Slot) + 4096 * 4 + 64 + (size_t)kHeadBuckets * 4 * 8 * 2 + 1024;
+    return (size_t)kSampleSlots * sizeof(G8Slot) + 4096 * 4 + 64 + (size_t)kHeadBuckets * 4 * (8 * 2 + 4) + 1024;
 }
 
 static int sm_count_dev() {
@@ -632,6 +677,7 @@ cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
         uint32_t *meta = hist + 4096;
         unsigned long long *cand = reinterpret_cast<unsigned long long *>(meta + 16);
         unsigned long long *image = cand + kHeadBuckets * 4;
+        uint32_t *ccnt = reinterpret_cast<uint32_t *>(image + kHeadBuckets * 4);
         cudaMemsetAsync(p, 0, kSampleSlots * sizeof(G8Slot) + 4096 * 4 + 64, s);
         Count2Args sa = a;
         sa.g.slots8 = sample;
@@ -645,12 +691,14 @@ cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
         const uint32_t kmax = kHeadBuckets * 4 * 88 / 100;
         k_head_hist<<<sms, 256, 0, s>>>(sample, kSampleSlots, hist);
         k_head_threshold<<<1, 1024, 0, s>>>(hist, kmax, meta);
-        k_head_collect<<<sms * 2, 256, 0, s>>>(sample, kSampleSlots, meta, cand, kmax);
-        k_head_build<<<1, 1024, 0, s>>>(cand, meta, kmax, kHeadBuckets, image);
+        k_head_collect<<<sms * 2, 256, 0, s>>>(sample, kSampleSlots, meta, cand, ccnt, kmax);
+        k_head_build<<<1, 1024, 0, s>>>(cand, ccnt, meta, kmax, kHeadBuckets, image);
         a.head = image;
     }
     int grid = c.grid > 0 ? c.grid : sms;
     if ((uint32_t)grid > a.nchunks) grid = (int)a.nchunks;
+    for (cudaEvent_t e : c.main_ev)
+        if (e) cudaEventRecord(e, s);
     k_count2<false><<<grid, kBlock, kCountSmem, s>>>(a);
     return cudaGetLastError();
 }

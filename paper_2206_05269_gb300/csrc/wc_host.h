@@ -22,9 +22,10 @@ struct wc_ctx {
     std::string last_error;
     // stage tracing
     bool profile = false;
-    std::vector<cudaEvent_t> ev_count, ev_finish;  // (start, stop) pairs
+    std::vector<cudaEvent_t> ev_head, ev_count, ev_finish;  // (start, stop) pairs
     uint64_t launches = 0;
     void prof_mark(std::vector<cudaEvent_t> &v, cudaStream_t s);
+    cudaEvent_t prof_event(std::vector<cudaEvent_t> &v);  // a new event kept in v (not yet recorded), or null
     // per-document kernel shapes picked by the autotuner (indices into kDocShapes)
     int tuned_small = 1, tuned_medium = 4;
     std::string gpu_name;

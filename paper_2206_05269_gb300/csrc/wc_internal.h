@@ -14,6 +14,7 @@ struct CountLaunch {
     GTable g;
     int grid;                // 0 = one persistent block per SM
     void *head_scratch;      // head_scratch_bytes() or null (no shared-memory head)
+    cudaEvent_t main_ev[2];  // recorded (when non-null) right before the main counting kernel
 };
 // Tokenises and counts text[lo, hi) into g (8-byte, 16-byte and long tables).
 cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s);
@@ -49,6 +50,8 @@ struct SortScratch {
     uint32_t *hist_all;      // 24 x 256
     uint32_t *tile_hist;     // 256 x ntiles
     uint32_t *cur;           // 25
+    // permutation buffer c (0 or 1), selected without indexing the parameter array
+    __device__ __forceinline__ uint32_t *perm_buf(uint32_t c) const { return c ? perm[1] : perm[0]; }
 };
 size_t sort_scratch_bytes(uint64_t cap);
 void sort_scratch_carve(SortScratch &s, void *base, uint64_t cap);

@@ -155,22 +155,27 @@ __global__ void k_compact_long(const LSlot *ls, unsigned long long lcap, SortScr
         off = __shfl_sync(kFull, off, 0);
         lidx = __shfl_sync(kFull, lidx, 0);
         pos = __shfl_sync(kFull, pos, 0);
-        if (off + len + 1 > out.arena_cap || lidx >= out.lcap) {
-            if (lane == 0) atomicOr(out.d_status, ST_ARENA_FULL);
-            continue;
-        }
-        for (unsigned long long j = lane; j < len; j += 32) out.arena[off + j] = (uint8_t)(src[j] | 0x20u);
+        // The arena or the long index is full: the table fails (status), but
+        // the entry slot taken above is still filled (prefix key, no long
+        // reference) so that the sort that follows reads only valid entries.
+        const bool full = off + len + 1 > out.arena_cap || lidx >= out.lcap;
+        if (!full)
+            for (unsigned long long j = lane; j < len; j += 32) out.arena[off + j] = (uint8_t)(src[j] | 0x20u);
         if (lane == 0) {
-            out.arena[off + len] = 0;
-            out.loff[lidx] = off;
-            out.llen[lidx] = len;
+            if (full) {
+                atomicOr(out.d_status, ST_ARENA_FULL);
+            } else {
+                out.arena[off + len] = 0;
+                out.loff[lidx] = off;
+                out.llen[lidx] = len;
+            }
             unsigned long long hi = 0, lo = 0;
             for (int j = 0; j < 8; j++) hi = (hi << 8) | (unsigned long long)(src[j] | 0x20u);
             for (int j = 8; j < 16; j++) lo = (lo << 8) | (unsigned long long)(src[j] | 0x20u);
             ss.khi[pos] = hi;
             ss.klo[pos] = lo;
             ss.cnt[pos] = c;
-            ss.lref[pos] = (uint32_t)(lidx + 1);
+            ss.lref[pos] = full ? 0u : (uint32_t)(lidx + 1);
         }
     }
 }
@@ -225,12 +230,21 @@ __global__ void __launch_bounds__(kSortThreads) k_pass_count(SortScratch s, int 
     if (pass_skipped(s, p, n)) return;
     h[threadIdx.x] = 0;
     __syncthreads();
-    const uint32_t *in = s.perm[s.cur[p]];
-    const unsigned long long t0 = (unsigned long long)blockIdx.x * kSortTile;
-    for (int j = threadIdx.x; j < kSortTile; j += kSortThreads) {
-        unsigned long long i = t0 + j;
-        if (i < n) atomicAdd(&h[sort_digit(s, in[i], p)], 1u);
+    const uint32_t *in = s.perm_buf(s.cur[p]);
+    const unsigned long long t0 = (unsigned long long)blockIdx.x * kSortTile + threadIdx.x;
+    // all loads first (16 independent gathers in flight per thread), then the histogram
+    uint32_t dig[kItems];
+#pragma unroll
+    for (int it = 0; it < kItems; it++) {
+        const unsigned long long i = t0 + (unsigned long long)it * kSortThreads;
+        dig[it] = i < n ? in[i] : 0xFFFFFFFFu;
     }
+#pragma unroll
+    for (int it = 0; it < kItems; it++)
+        if (dig[it] != 0xFFFFFFFFu) dig[it] = sort_digit(s, dig[it], p);
+#pragma unroll
+    for (int it = 0; it < kItems; it++)
+        if (dig[it] != 0xFFFFFFFFu) atomicAdd(&h[dig[it]], 1u);
     __syncthreads();
     s.tile_hist[(unsigned long long)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
@@ -291,16 +305,25 @@ __global__ void __launch_bounds__(kSortThreads) k_pass_scatter(SortScratch s, in
     for (int i = threadIdx.x; i < WARPS * 256; i += kSortThreads) (&wcount[0][0])[i] = 0;
     __syncthreads();
     const uint32_t cur = s.cur[p];
-    const uint32_t *in = s.perm[cur];
-    uint32_t *out = s.perm[1 - cur];
+    const uint32_t *in = s.perm_buf(cur);
+    uint32_t *out = s.perm_buf(1 - cur);
     const unsigned long long t0 = (unsigned long long)blockIdx.x * kSortTile + (unsigned long long)warp * (kSortTile / WARPS);
     uint32_t idx[kItems], dig[kItems], rank[kItems];
+    // all loads first (independent gathers in flight), then the in-order ranking
 #pragma unroll
     for (int it = 0; it < kItems; it++) {
-        unsigned long long i = t0 + it * 32 + lane;
-        bool valid = i < n;
-        idx[it] = valid ? in[i] : 0u;
-        dig[it] = valid ? sort_digit(s, idx[it], p) : 256u + lane;  // invalid lanes never match real digits
+        const unsigned long long i = t0 + it * 32 + lane;
+        idx[it] = i < n ? in[i] : 0u;
+    }
+#pragma unroll
+    for (int it = 0; it < kItems; it++) {
+        const unsigned long long i = t0 + it * 32 + lane;
+        dig[it] = i < n ? sort_digit(s, idx[it], p) : 256u + lane;  // invalid lanes never match real digits
+    }
+#pragma unroll
+    for (int it = 0; it < kItems; it++) {
+        const unsigned long long i = t0 + it * 32 + lane;
+        const bool valid = i < n;
         uint32_t peers = __match_any_sync(kFull, dig[it]);
         int leader = __ffs(peers) - 1;
         uint32_t before = 0;
@@ -349,7 +372,7 @@ __device__ __forceinline__ bool tail_less(const LongView &v, uint32_t a, uint32_
 __global__ void k_fix_long(SortScratch s, LongView v, const unsigned long long *meta) {
     const unsigned long long n = meta[0];
     if (meta[1] == 0) return;
-    uint32_t *perm = s.perm[s.cur[16]];
+    uint32_t *perm = s.perm_buf(s.cur[16]);
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         uint32_t e = perm[i];
@@ -376,7 +399,7 @@ __device__ __forceinline__ unsigned long long short_len(unsigned long long hi, u
 
 __global__ void k_gather_final(SortScratch s, DevTable out) {
     const unsigned long long n = out.d_meta[0];
-    const uint32_t *perm = s.perm[s.cur[kPasses]];  // unsegmented: count digits are the last
+    const uint32_t *perm = s.perm_buf(s.cur[kPasses]);  // unsegmented: count digits are the last
     unsigned long long bytes = 0;
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
@@ -414,7 +437,7 @@ __global__ void k_meta_snapshot(unsigned long long *meta, int slot) { meta[slot]
 int sort_entries_launches(int passes);
 int finish_table_launches() { return 5 + sort_entries_launches(kPasses) + 1; }
 
-// LSD radix sort of the entries in ss (count n = meta[0]) into ss.perm[ss.cur[passes]].
+// LSD radix sort of the entries in ss (count n = meta[0]) into ss.perm_buf(ss.cur[passes]).
 cudaError_t sort_entries(SortScratch &ss, const unsigned long long *meta, const LongView &v, int passes,
                          cudaStream_t st) {
     const int sms = sm_count();

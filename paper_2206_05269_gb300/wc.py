@@ -96,7 +96,7 @@ def load() -> ctypes.CDLL:
         "wc_count_noalloc": (i32, [vp, u64, vp, vp, vp, vp, u64, vp, vp, u64, vp, u64, vp, vp]),
         "wc_profile_enable": (i32, [vp, i32]),
         "wc_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
-                                  ctypes.POINTER(u64), ctypes.POINTER(u64)]),
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64), ctypes.POINTER(u64)]),
         "wc_status_str": (ctypes.c_char_p, [i32]),
         "wc_last_error": (ctypes.c_char_p, [vp]),
     }
@@ -278,13 +278,14 @@ def wc_profile_enable(ctx, enable: bool) -> None:
     _check(load().wc_profile_enable(ctx, int(enable)), ctx, "wc_profile_enable")
 
 
-def wc_profile_read(ctx) -> tuple[float, float, int, int]:
-    """(ms in counting kernels, ms in compaction+sort, counting kernels timed, kernels launched)"""
-    a, b = ctypes.c_double(), ctypes.c_double()
+def wc_profile_read(ctx) -> tuple[float, float, float, int, int]:
+    """(ms in head selection, ms in the main counting kernel, ms in compaction+sort,
+    main counting kernels timed, kernels launched)"""
+    h, a, b = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     n, k = ctypes.c_uint64(), ctypes.c_uint64()
-    _check(load().wc_profile_read(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n), ctypes.byref(k)),
-           ctx, "wc_profile_read")
-    return a.value, b.value, n.value, k.value
+    _check(load().wc_profile_read(ctx, ctypes.byref(h), ctypes.byref(a), ctypes.byref(b), ctypes.byref(n),
+                                  ctypes.byref(k)), ctx, "wc_profile_read")
+    return h.value, a.value, b.value, n.value, k.value
 
 
 def wc_status_str(status: int) -> str:
