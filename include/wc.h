@@ -186,7 +186,7 @@ void wc_batch_free(wc_batch *b);
  * through its own allocator, and services that forbid allocation after
  * start-up because an allocation can stall or fail at the wrong moment.
  * No context is needed and nothing is allocated: the hash tables and sort
- * scratch live in one fixed __device__ array of about 12.5 MB that every GPU
+ * scratch live in one fixed __device__ array of about 15.2 MB that every GPU
  * which loads the library holds until the process exits.
  *   d_text[0, nbytes): one document, nbytes <= 1 MiB (larger: returns
  *     WC_ERR_UNSUPPORTED; use wc_count).

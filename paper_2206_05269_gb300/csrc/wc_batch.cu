@@ -58,7 +58,7 @@ __device__ __forceinline__ void doc_insert_key(const GTable &g, uint32_t d, uint
 }
 __device__ __forceinline__ void doc_insert_long(const GTable &g, uint32_t d, const uint8_t *w, unsigned long long len,
                                                 unsigned long long add, const uint8_t *begin, const uint8_t *end) {
-    long_insert2(g, w, len, long_doc_hash(long_hash_serial(w, len), d), add, begin, end);
+    long_insert2(g, w, len, long_doc_hash(long_hash_run(w, len), d), add, begin, end);
 }
 
 __device__ __forceinline__ unsigned long long be64b(uint32_t x, uint32_t y) {
@@ -591,19 +591,19 @@ cudaError_t launch_segmented_finish(const BatchArgs &a, const GTable &g, uint64_
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaMemsetAsync(smeta, 0, 16 * 8, s);
-    cudaMemsetAsync(ss.hist_all, 0, 4 * 28 * 256, s);
+    cudaMemsetAsync(ss.hist_all, 0, 4 * kSortPassesSeg * 256, s);
     cudaMemsetAsync(ss.cur, 0, 4 * 32, s);
     k_bcompact8<<<gridn(cap8, 256, sms * 8), 256, 0, s>>>(g.slots8, cap8, ss, smeta);
     k_bcompact16<<<gridn(cap16, 256, sms * 8), 256, 0, s>>>(g.slots, cap16, ss, smeta);
     k_bcompact_long<<<gridn(caplong * 32, 256, sms * 8), 256, 0, s>>>(g.lslots, caplong, ss, a, smeta);
     LongView v{ss.lref, a.loff, a.llen, a.arena};
-    cudaError_t e = sort_entries(ss, smeta, v, 28, s);
+    cudaError_t e = sort_entries(ss, smeta, v, kSortPassesSeg, s);
     if (e != cudaSuccess) return e;
     k_seg_base<<<1, 1, 0, s>>>(a, smeta);
-    k_seg_write<<<gridn(ss.cap, 256, sms * 8), 256, 0, s>>>(ss, a, smeta, 28);
-    k_seg_ends<<<gridn(ss.cap, 256, sms * 8), 256, 0, s>>>(ss, a, smeta, 28);
+    k_seg_write<<<gridn(ss.cap, 256, sms * 8), 256, 0, s>>>(ss, a, smeta, kSortPassesSeg);
+    k_seg_ends<<<gridn(ss.cap, 256, sms * 8), 256, 0, s>>>(ss, a, smeta, kSortPassesSeg);
     return cudaGetLastError();
 }
-int segmented_finish_launches() { return 3 + sort_entries_launches(28) + 3; }
+int segmented_finish_launches() { return 3 + sort_entries_launches(kSortPassesSeg) + 3; }
 
 }  // namespace wc

@@ -52,10 +52,12 @@ constexpr int kSamplePieces = 64;
 constexpr int kSamplePieceBytes = 65536;
 constexpr uint64_t kHeadMinBytes = 16ull << 20;
 constexpr unsigned long long kSampleSlots = 1ull << 19;
-constexpr uint32_t kHeadSortN = kHeadBuckets * 4;  // >= candidates (a power of two)
-constexpr uint32_t kHeadIdxBits = 13;              // candidate index bits of a sort word
-constexpr uint32_t kHeadCntMax = (1u << (32 - kHeadIdxBits)) - 1u;
-static_assert(kHeadSortN <= (1u << kHeadIdxBits), "candidate index fits the sort word");
+constexpr int kSampleLocalBits = 13;  // per-block table of the sampling pass (the head area)
+static_assert((1u << kSampleLocalBits) <= kHeadBuckets * 4, "sampling table fits the head area");
+constexpr uint32_t kHeadSortN = kHeadBuckets * 4;  // >= candidates, a multiple of 1024
+constexpr uint32_t kHeadIdxBits = 13;
+constexpr uint32_t kHeadCntMax = (1u << (32 - kHeadIdxBits)) - 1u;  // sample counts are clamped here
+static_assert(kHeadSortN % 1024 == 0, "head candidates per build thread");
 
 struct Count2Args {
     const uint8_t *text;
@@ -190,7 +192,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 template <bool SAMPLE>
 struct Counter2 {
     const Count2Args &a;
-    const unsigned long long *hkey;
+    unsigned long long *hkey;  // head image keys (read only) or the sampling table
     uint32_t *hcnt;
     uint4 *tailq;
     uint32_t nslots;
@@ -203,24 +205,43 @@ struct Counter2 {
     __device__ __forceinline__ void word(const uint8_t *win, bool have, uint32_t e) {
         bool tail = false;
         uint4 tk = make_uint4(0, 0, 0, 0);
+        if (SAMPLE) {
+            if (have && (e & 31u) <= 8u) {
+                const unsigned long long key = load_key8(win, e >> 5, e & 31u);
+                tail = !sample_add(key);
+                tk = make_uint4((uint32_t)key, (uint32_t)(key >> 32), 0u, 0u);
+            }
+            push(tail, tk);
+            return;
+        }
+        const int hs = lookup(win, have, e, tail, tk);
+        if (hs >= 0) atomicAdd(hcnt + hs, 1u);
+        push(tail, tk);
+    }
+    // The head slot of a queued word (-1 if none) and, when it is not in the
+    // head, the key it goes to the tail queue with.
+    __device__ __forceinline__ int lookup(const uint8_t *win, bool have, uint32_t e, bool &tail, uint4 &tk) {
+        tail = false;
+        tk = make_uint4(0, 0, 0, 0);
+        int hs = -1;
         if (have) {
             const uint32_t p = e >> 5, len = e & 31u;
+            tail = true;
             if (len <= 8) {
                 const unsigned long long key = load_key8(win, p, len);
-                tail = true;
-                if (nslots) {
-                    uint32_t slot;
-                    if (head_find(hkey, key, a.nb, &slot) >= 0) {
-                        atomicAdd(hcnt + slot, 1u);
-                        tail = false;
-                    }
+                uint32_t slot;
+                if (nslots && head_find(hkey, key, a.nb, &slot) >= 0) {
+                    hs = (int)slot;
+                    tail = false;
                 }
                 tk = make_uint4((uint32_t)key, (uint32_t)(key >> 32), 0u, 0u);
-            } else if (!SAMPLE) {
-                tail = true;
+            } else {
                 tk = load_key16(win, p, len);
             }
         }
+        return hs;
+    }
+    __device__ __forceinline__ void push(bool tail, uint4 tk) {
         const uint32_t tb = __ballot_sync(kFull, tail);
         if (tail) tailq[tailn + __popc(tb & ((1u << lane) - 1u))] = tk;
         tailn += __popc(tb);
@@ -233,20 +254,40 @@ struct Counter2 {
             issue(k);
         }
     }
+    // Sampling pass: the shared head area is a per-block open-addressing table
+    // (keys claimed by CAS), so frequent words cost one shared atomic each
+    // instead of a global atomic on one hot slot; false when the probe limit
+    // is reached (the word then goes to the global sample table).
+    __device__ __forceinline__ bool sample_add(unsigned long long key) {
+        uint32_t s = (uint32_t)(hash8(key) >> (64 - kSampleLocalBits));
+        for (int probe = 0; probe < 16; probe++) {
+            unsigned long long k = hkey[s];
+            if (k == 0ull) k = atomicCAS(&hkey[s], 0ull, key);
+            if (k == 0ull || k == key) {
+                atomicAdd(hcnt + s, 1u);
+                return true;
+            }
+            s = (s + 1u) & ((1u << kSampleLocalBits) - 1u);
+        }
+        return false;
+    }
     __device__ __forceinline__ void insert(uint4 k) {
         if (!SAMPLE) table_insert_key(a.g, k, 1ull);
         else global_insert8(a.g, ((unsigned long long)k.y << 32) | k.x, 1ull);
     }
 
     // Tail inserts in two halves.  issue() computes the home slot of the key
-    // and starts loading the key stored there; complete() (called when the
-    // next 32 words are ready, so the load had time to arrive) finishes the
-    // insert: a matching key gets a fire-and-forget add, an empty or
-    // half-written slot is settled by the CAS, a different key continues the
-    // probe at the next slot.
+    // and starts loading the keys stored there and in the next slot (the
+    // first two probe positions); complete() (called when the next 32 words
+    // are ready, so the loads had time to arrive) finishes the insert.  A
+    // matching key is final wherever it was seen (keys are written once and
+    // never move), so it gets a fire-and-forget add.  Otherwise the probe
+    // resumes with fresh loads at the first position that the early loads did
+    // not show holding another key for good: an empty or half-written slot is
+    // settled there by the CAS.
     bool pend = false, p16 = false;
     uint4 pk;
-    unsigned long long pslot = 0, pv0 = 0, pv1 = 0;
+    unsigned long long pslot = 0, pv0 = 0, pv1 = 0, pv2 = 0, pv3 = 0;
     __device__ __forceinline__ void issue(uint4 k) {
         pk = k;
         pend = true;
@@ -255,25 +296,36 @@ struct Counter2 {
             const unsigned long long key = ((unsigned long long)k.y << 32) | k.x;
             pslot = hash8(key) >> __clzll((long long)a.g.mask8);
             pv0 = ld_u64(&a.g.slots8[pslot].key);
+            pv1 = ld_u64(&a.g.slots8[(pslot + 1) & a.g.mask8].key);
         } else {
             pslot = hash_key(k) & a.g.mask;
             const unsigned long long *kp = reinterpret_cast<const unsigned long long *>(&a.g.slots[pslot].key);
+            const unsigned long long *kq =
+                reinterpret_cast<const unsigned long long *>(&a.g.slots[(pslot + 1) & a.g.mask].key);
             pv0 = ld_u64(kp);
             pv1 = ld_u64(kp + 1);
+            pv2 = ld_u64(kq);
+            pv3 = ld_u64(kq + 1);
         }
     }
     __device__ __forceinline__ void complete() {
         if (!pend) return;
         pend = false;
         if (!p16) {
-            const unsigned long long key = ((unsigned long long)pk.y << 32) | pk.x;
+            const unsigned long long key = ((unsigned long long)pk.y << 32) | pk.x, m = a.g.mask8;
             if (pv0 == key) { red_add_u64(&a.g.slots8[pslot].cnt, 1ull); return; }
-            global_insert8_from(a.g, key, 1ull, pslot);
+            if (pv1 == key) { red_add_u64(&a.g.slots8[(pslot + 1) & m].cnt, 1ull); return; }
+            const unsigned long long from = pv0 == 0ull ? pslot : (pv1 == 0ull ? pslot + 1 : pslot + 2);
+            global_insert8_from(a.g, key, 1ull, from & m);
         } else {
             const unsigned long long k0 = ((unsigned long long)pk.y << 32) | pk.x;
-            const unsigned long long k1 = ((unsigned long long)pk.w << 32) | pk.z;
+            const unsigned long long k1 = ((unsigned long long)pk.w << 32) | pk.z, m = a.g.mask;
             if (pv0 == k0 && pv1 == k1) { red_add_u64(&a.g.slots[pslot].cnt, 1ull); return; }
-            global_insert16_from(a.g, pk, 1ull, pslot);
+            if (pv2 == k0 && pv3 == k1) { red_add_u64(&a.g.slots[(pslot + 1) & m].cnt, 1ull); return; }
+            // both halves non-zero: the slot holds another key for good
+            const bool other0 = pv0 != 0ull && pv1 != 0ull, other1 = pv2 != 0ull && pv3 != 0ull;
+            const unsigned long long from = !other0 ? pslot : (!other1 ? pslot + 1 : pslot + 2);
+            global_insert16_from(a.g, pk, 1ull, from & m);
         }
     }
 };
@@ -353,11 +405,12 @@ __global__ void __launch_bounds__(kBlock, 1) k_count2(Count2Args a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *tok = tokall + warp * kTokCap;
     uint4 *longq = longall + warp * kLongCap;
-    const uint32_t nslots = a.head ? a.nb * 4 : 0;
+    // head image (counting) or an empty local table (sampling)
+    const uint32_t nslots = SAMPLE ? (1u << kSampleLocalBits) : (a.head ? a.nb * 4 : 0);
     Counter2<SAMPLE> ctr{a, hkey, hcnt, tailall + warp * kTailCap, nslots, 0u, lane};
 
     for (uint32_t i = threadIdx.x; i < nslots; i += kBlock) {
-        hkey[i] = a.head[i];
+        hkey[i] = SAMPLE ? 0ull : a.head[i];
         hcnt[i] = 0u;
     }
     if (threadIdx.x < kStages) done[threadIdx.x] = 0u;
@@ -387,7 +440,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_count2(Count2Args a) {
                 len = 17;
                 while (w + len < end && is_letter(w[len])) len++;
             }
-            long_insert(a.g, w, len, 1ull, begin, end);
+            long_insert2(a.g, w, len, long_hash_run(w, len), 1ull, begin, end);
         }
         __syncwarp();
     };
@@ -437,6 +490,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_count2(Count2Args a) {
         const uint32_t tnew = total;
         tcount += total;
         if (!SAMPLE && __any_sync(kFull, Sl != 0)) {
+            // 48 bits of letter mask from this lane on: run lengths up to 32 letters are read here
+            const uint32_t Ln2 = letter_mask16(*reinterpret_cast<const uint4 *>(win + sbase + 528));
+            const uint32_t dn2 = __shfl_down_sync(kFull, L, 2);
+            const unsigned long long W48 =
+                (unsigned long long)W | ((unsigned long long)(lane == 31 ? Ln2 : (lane == 30 ? Ln : dn2)) << 32);
             while (__any_sync(kFull, Sl != 0)) {
                 const bool act = Sl != 0;
                 uint4 e = make_uint4(0, 0, 0, 0);
@@ -444,8 +502,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_count2(Count2Args a) {
                     int j = __ffs(Sl) - 1;
                     Sl &= Sl - 1;
                     unsigned long long wa = (unsigned long long)(w0 + pbase + (uint32_t)j);
-                    uint32_t run = (uint32_t)__ffs(~(W >> j)) - 1u;  // letters seen in W (<= 32 - j)
-                    e = make_uint4((uint32_t)wa, (uint32_t)(wa >> 32), run < 32u - (uint32_t)j ? run : 0u, 0u);
+                    // letters seen in W48 (< 48 - j), else 0: the run continues past it
+                    const uint32_t run = (uint32_t)__ffsll((long long)~(W48 >> j)) - 1u;
+                    e = make_uint4((uint32_t)wa, (uint32_t)(wa >> 32), run < 48u - (uint32_t)j ? run : 0u, 0u);
                 }
                 const uint32_t lb = __ballot_sync(kFull, act);
                 if (act) longq[longn + __popc(lb & ((1u << lane) - 1u))] = e;
@@ -579,50 +638,41 @@ __global__ void k_head_collect(const G8Slot *s, unsigned long long cap, uint32_t
 }
 
 // Two-choice placement of the candidates into nb buckets of 4 (one block),
-// most frequent first.  The candidates are sorted by sample count (bitonic
-// sort of count:index words in shared memory) and placed in rounds of 1024;
-// a key whose two buckets are both full is left out of the head and counted
-// in the global table.  Placing by frequency makes sure that only the
-// rarest candidates can be left out: a frequent word missing from the head
-// would send all its occurrences to one global slot, whose atomics then
-// serialise.
+// most frequent first: candidates are placed in tiers of equal floor(log2
+// sample count), highest tier first, all candidates of a tier in parallel.
+// A key whose two buckets are both full is left out of the head and counted
+// in the global table.  Placing by frequency makes sure that only the rarest
+// candidates can be left out: a frequent word missing from the head would
+// send all its occurrences to one global slot, whose atomics then serialise.
 __global__ void __launch_bounds__(1024) k_head_build(const unsigned long long *cand, const uint32_t *ccnt,
                                                      const uint32_t *meta, uint32_t kmax, uint32_t nb,
                                                      unsigned long long *image) {
-    __shared__ uint32_t ord[kHeadSortN];
+    constexpr int kPer = (int)(kHeadSortN / 1024);  // candidates per thread
     __shared__ uint32_t fill[kHeadBuckets];
     const uint32_t n = meta[1] < kmax ? meta[1] : kmax;
-    for (uint32_t i = threadIdx.x; i < kHeadSortN; i += blockDim.x)
-        ord[i] = i < n ? (ccnt[i] << kHeadIdxBits) | i : 0u;  // counts are >= 2: padding sorts last
     for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) fill[i] = 0;
     for (uint32_t i = threadIdx.x; i < nb * 4; i += blockDim.x) image[i] = 0ull;
+    int tier[kPer];
+    unsigned long long key[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+        const uint32_t i = threadIdx.x + (uint32_t)k * 1024u;
+        tier[k] = i < n ? 31 - __clz((int)ccnt[i]) : -1;  // counts >= 2: tier >= 1
+        key[k] = i < n ? cand[i] : 0ull;
+    }
     __syncthreads();
-    for (uint32_t k = 2; k <= kHeadSortN; k <<= 1)
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = threadIdx.x; i < kHeadSortN; i += blockDim.x) {
-                const uint32_t p = i ^ j;
-                if (p > i) {
-                    const uint32_t x = ord[i], y = ord[p];
-                    if ((i & k) == 0 ? x < y : x > y) {  // descending overall
-                        ord[i] = y;
-                        ord[p] = x;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    for (uint32_t base = 0; base < n; base += blockDim.x) {
-        const uint32_t r = base + threadIdx.x;
-        if (r < n) {
-            const unsigned long long key = cand[ord[r] & ((1u << kHeadIdxBits) - 1u)];
-            uint32_t b1 = head_bucket(key, kHeadMulA, nb), b2 = head_bucket(key, kHeadMulB, nb);
-            uint32_t first = fill[b1] <= fill[b2] ? b1 : b2, second = first == b1 ? b2 : b1;
+    for (int t = 31 - kHeadIdxBits; t >= 1; t--) {
+#pragma unroll
+        for (int k = 0; k < kPer; k++) {
+            if (tier[k] != t) continue;
+            const uint32_t b1 = head_bucket(key[k], kHeadMulA, nb), b2 = head_bucket(key[k], kHeadMulB, nb);
+            const uint32_t first = fill[b1] <= fill[b2] ? b1 : b2, second = first == b1 ? b2 : b1;
             uint32_t slot = atomicAdd(&fill[first], 1u);
             if (slot < 4) {
-                image[first * 4 + slot] = key;
+                image[first * 4 + slot] = key[k];
             } else {
                 slot = atomicAdd(&fill[second], 1u);
-                if (slot < 4) image[second * 4 + slot] = key;
+                if (slot < 4) image[second * 4 + slot] = key[k];
             }
         }
         __syncthreads();

@@ -132,7 +132,71 @@ __device__ inline unsigned long long long_hash_warp(const uint8_t *w, unsigned l
     return fmix64(acc + len * 0x9E3779B97F4A7C15ull);
 }
 
+// 16 lowercased bytes of the letter run at p[0, n), zero padded (n <= 0: all
+// zero).  Reads only the aligned 4-byte words that hold some of those bytes,
+// so it never touches memory past the run's last aligned word; the loads are
+// independent of each other.
+__device__ __forceinline__ uint4 load_run16(const uint8_t *p, long long n) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(a & ~(uintptr_t)3);
+    const uint32_t sh = (uint32_t)(a & 3u) * 8u;
+    const long long need = n > 0 ? n + (long long)(a & 3u) : 0;  // bytes needed from the aligned start
+    uint32_t v0 = 0, v1 = 0, v2 = 0, v3 = 0, v4 = 0;
+    if (need > 0) v0 = __ldg(w);
+    if (need > 4) v1 = __ldg(w + 1);
+    if (need > 8) v2 = __ldg(w + 2);
+    if (need > 12) v3 = __ldg(w + 3);
+    if (need > 16) v4 = __ldg(w + 4);
+    const int m = n < 0 ? 0 : (n > 16 ? 16 : (int)n);
+    uint4 k;
+    k.x = (__funnelshift_r(v0, v1, sh) | 0x20202020u) & byte_keep_mask(m);
+    k.y = (__funnelshift_r(v1, v2, sh) | 0x20202020u) & byte_keep_mask(m - 4);
+    k.z = (__funnelshift_r(v2, v3, sh) | 0x20202020u) & byte_keep_mask(m - 8);
+    k.w = (__funnelshift_r(v3, v4, sh) | 0x20202020u) & byte_keep_mask(m - 12);
+    return k;
+}
+// acc = acc * P + (b + 1) over the first n bytes of k, last byte first (Horner).
+__device__ __forceinline__ unsigned long long horner16(unsigned long long acc, uint4 k, int n) {
+    const uint32_t q[4] = {k.x, k.y, k.z, k.w};
+#pragma unroll
+    for (int j = 15; j >= 0; j--)
+        if (j < n) acc = acc * kLongP + (unsigned long long)(((q[j >> 2] >> (8 * (j & 3))) & 0xFFu) + 1u);
+    return acc;
+}
+// The long-word hash (same value as long_hash_serial) of the letter run
+// w[0, len), len >= 1, from 16-byte pieces read with independent loads.
+__device__ inline unsigned long long long_hash_run(const uint8_t *w, unsigned long long len) {
+    long long off = (long long)((len - 1) / 16) * 16;  // the last piece
+    unsigned long long acc = 0;
+    if (off == 16) {  // 17..32 letters: both pieces loaded together
+        const uint4 k1 = load_run16(w + 16, (long long)len - 16), k0 = load_run16(w, 16);
+        acc = horner16(horner16(0ull, k1, (int)len - 16), k0, 16);
+    } else {
+        for (; off >= 0; off -= 16) {
+            const long long n = (long long)len - off;
+            acc = horner16(acc, load_run16(w + off, n), n > 16 ? 16 : (int)n);
+        }
+    }
+    return fmix64(acc + len * 0x9E3779B97F4A7C15ull);
+}
+// Whether the letter runs a[0, len) and b[0, len) are equal (case folded).
+__device__ inline bool runs_equal(const uint8_t *a, const uint8_t *b, unsigned long long len) {
+    for (unsigned long long off = 0; off < len; off += 32) {
+        const long long n = (long long)(len - off);
+        const uint4 a0 = load_run16(a + off, n), b0 = load_run16(b + off, n);
+        const uint4 a1 = load_run16(a + off + 16, n - 16), b1 = load_run16(b + off + 16, n - 16);
+        if (!key_eq(a0, b0) || !key_eq(a1, b1)) return false;
+    }
+    return true;
+}
+
 // ---------------------------------------------------------------- atomics
+// A 64-bit load that sees other SMs' atomics (not served from a stale L1 line).
+__device__ __forceinline__ unsigned long long ld_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 // 128-bit compare-and-swap (sm_90+): returns the previous value.
 __device__ __forceinline__ uint4 cas128_global(void *addr, uint4 cmp, uint4 val) {
     uint64_t c0 = ((uint64_t)cmp.y << 32) | cmp.x, c1 = ((uint64_t)cmp.w << 32) | cmp.z;
@@ -265,7 +329,11 @@ __device__ inline void long_insert2(const GTable &g, const uint8_t *w, unsigned 
     const uint4 zero = make_uint4(0, 0, 0, 0);
     for (int probe = 0; probe < kGlobalProbeLimit; probe++) {
         LSlot *slot = g.lslots + s;
-        uint4 old = cas128_global(&slot->h, zero, want);
+        // plain loads first: a claimed slot (both words non-zero, written by
+        // one 128-bit CAS) is settled; an empty or half-seen one goes to the CAS
+        const unsigned long long h0 = ld_u64(&slot->h), a0 = ld_u64(&slot->addr);
+        uint4 old = make_uint4((uint32_t)h0, (uint32_t)(h0 >> 32), (uint32_t)a0, (uint32_t)(a0 >> 32));
+        if (h0 == 0ull || a0 == 0ull) old = cas128_global(&slot->h, zero, want);
         if (key_zero(old)) {
             slot->len = len;
             red_add_u64_dev(&slot->cnt, add);
@@ -278,8 +346,13 @@ __device__ inline void long_insert2(const GTable &g, const uint8_t *w, unsigned 
             else cand = true;  // arena: 0-terminated words, the early-exit compare stays inside them
             if (cand) {
                 bool eq = true;
-                for (unsigned long long i = 0; i < len && eq; i++) eq = (rep[i] | 0x20u) == (w[i] | 0x20u);
-                if (eq) eq = begin ? (rep + len == end || !is_letter(rep[len])) : !is_letter(rep[len]);
+                if (begin) {  // text: both runs are readable for len bytes
+                    const bool term = rep + len == end || !is_letter(rep[len]);
+                    eq = term && runs_equal(rep, w, len);
+                } else {
+                    for (unsigned long long i = 0; i < len && eq; i++) eq = (rep[i] | 0x20u) == (w[i] | 0x20u);
+                    if (eq) eq = !is_letter(rep[len]);
+                }
                 if (eq) {
                     red_add_u64_dev(&slot->cnt, add);
                     return;
@@ -305,11 +378,6 @@ __device__ __forceinline__ unsigned long long hash8(unsigned long long key) {
     return key * 0x9E3779B97F4A7C15ull;  // Fibonacci hashing: use the top bits
 }
 __device__ __forceinline__ void red_add_u64(unsigned long long *p, unsigned long long v) { red_add_u64_dev(p, v); }
-__device__ __forceinline__ unsigned long long ld_u64(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
 // Probes from slot s onwards (s = the home slot, or a later slot of its chain).
 __device__ __forceinline__ void global_insert8_from(const GTable &g, unsigned long long key, unsigned long long add,
                                                     unsigned long long s) {

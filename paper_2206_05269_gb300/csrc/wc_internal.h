@@ -41,9 +41,18 @@ struct DevTable {
 };
 
 // Scratch for compaction + sort of up to `cap` entries.
+// Radix passes of the entry sort: 10 byte digits of the packed 16-letter
+// prefix (5 bits a letter, 80 bits), 8 digits of the complemented count, and
+// 4 document digits when a batch is sorted per document.
+constexpr int kSortKeyPasses = 10;
+constexpr int kSortPasses = kSortKeyPasses + 8;
+constexpr int kSortPassesSeg = kSortPasses + 4;
+
 struct SortScratch {
     uint64_t cap;
     unsigned long long *khi, *klo, *cnt;
+    unsigned long long *pk;  // packed prefix, low 64 bits (written by the sort)
+    uint32_t *pk2;           // packed prefix, high 16 bits
     uint32_t *lref;
     uint32_t *perm[2];
     uint32_t *doc;           // document of each entry (segmented sorts)

@@ -35,12 +35,12 @@ constexpr uint64_t round256(uint64_t n) { return (n + kR - 1) / kR * kR; }
 constexpr uint64_t kBytes8 = round256(kNaCap8 * sizeof(wc::G8Slot));
 constexpr uint64_t kBytes16 = round256(kNaCap16 * sizeof(wc::GSlot));
 constexpr uint64_t kBytesLong = round256(kNaCapLong * sizeof(wc::LSlot));
-// Sort scratch for kNaEntries entries (khi, klo, cnt, lref, 2 permutations,
-// doc, 28 digit histograms, tile histograms, pass cursors), each carved at a
-// 256-byte boundary.
-constexpr uint64_t kSortBytes = kNaEntries * (8 + 8 + 8 + 4 + 4 + 4 + 4) + 4 * 28 * 256 +
-                                4 * 256 * ((kNaEntries + 4095) / 4096) + 4 * 32 + 2048 + 16 * kR;
-constexpr uint64_t kScratchBytes = kBytes8 + kBytes16 + kBytesLong + kSortBytes;  // about 12.5 MB
+// Sort scratch for kNaEntries entries (khi, klo, cnt, packed key (8 + 4 bytes),
+// lref, 2 permutations, doc, the digit histograms, tile histograms, pass
+// cursors), each carved at a 256-byte boundary.
+constexpr uint64_t kSortBytes = kNaEntries * (8 + 8 + 8 + 8 + 4 + 4 + 4 + 4 + 4) + 4 * wc::kSortPassesSeg * 256 +
+                                4 * 256 * ((kNaEntries + 4095) / 4096) + 4 * 32 + 4096 + 16 * kR;
+constexpr uint64_t kScratchBytes = kBytes8 + kBytes16 + kBytesLong + kSortBytes;  // about 15.2 MB
 
 }  // namespace
 

@@ -4,12 +4,13 @@
 // once with its exact count (Sec. 3.3's reduced dictionary).  This file turns
 // them into the sorted output: compact the occupied slots, copy long words
 // into the table's own byte arena, then an LSD radix sort over a permutation:
-// 16 byte-digits of the big-endian 16-letter prefix (lexicographic order,
-// zero padding sorts a proper prefix first), a fix-up that orders long words
-// sharing a 16-letter prefix by their remaining bytes, and up to 8 digits of
-// the complemented count (count descending).  Every pass is stable, so the
-// final order is (count desc, word asc).  Digits that are equal for every
-// element are skipped, detected on the device from one histogram pass.
+// 10 byte-digits of the 16-letter prefix packed 5 bits a letter (0 for
+// padding, 1..26 for a..z, so integer order is lexicographic order and a
+// proper prefix sorts first), a fix-up that orders long words sharing a
+// 16-letter prefix by their remaining bytes, and up to 8 digits of the
+// complemented count (count descending).  Every pass is stable, so the final
+// order is (count desc, word asc).  Digits that are equal for every element
+// are skipped, detected on the device from one histogram pass.
 #include "wc_internal.h"
 
 namespace wc {
@@ -17,8 +18,8 @@ namespace wc {
 constexpr int kSortTile = 4096;      // elements per block in a radix pass
 constexpr int kSortThreads = 256;
 constexpr int kItems = kSortTile / kSortThreads;  // 16
-constexpr int kPasses = 24;     // 8 klo + 8 khi + 8 count digits
-constexpr int kPassesSeg = 28;  // + 4 document digits (segmented: per-document order)
+constexpr int kPasses = kSortPasses;
+constexpr int kPassesSeg = kSortPassesSeg;
 
 __device__ __forceinline__ unsigned long long be64(uint32_t x, uint32_t y) {
     return ((unsigned long long)__byte_perm(x, 0, 0x0123) << 32) | __byte_perm(y, 0, 0x0123);
@@ -31,7 +32,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 
 size_t sort_scratch_bytes(uint64_t cap) {
     uint64_t ntiles = (cap + kSortTile - 1) / kSortTile;
-    return cap * (8 + 8 + 8 + 4 + 4 + 4 + 4) + 4 * kPassesSeg * 256 + 4 * 256 * ntiles + 4 * 32 + 2048;
+    return cap * (8 + 8 + 8 + 8 + 4 + 4 + 4 + 4 + 4) + 4 * kPassesSeg * 256 + 4 * 256 * ntiles + 4 * 32 + 4096;
 }
 
 void sort_scratch_carve(SortScratch &s, void *base, uint64_t cap) {
@@ -42,6 +43,8 @@ void sort_scratch_carve(SortScratch &s, void *base, uint64_t cap) {
     s.khi = reinterpret_cast<unsigned long long *>(take(cap * 8));
     s.klo = reinterpret_cast<unsigned long long *>(take(cap * 8));
     s.cnt = reinterpret_cast<unsigned long long *>(take(cap * 8));
+    s.pk = reinterpret_cast<unsigned long long *>(take(cap * 8));
+    s.pk2 = reinterpret_cast<uint32_t *>(take(cap * 4));
     s.lref = reinterpret_cast<uint32_t *>(take(cap * 4));
     s.perm[0] = reinterpret_cast<uint32_t *>(take(cap * 4));
     s.perm[1] = reinterpret_cast<uint32_t *>(take(cap * 4));
@@ -182,13 +185,26 @@ __global__ void k_compact_long(const LSlot *ls, unsigned long long lcap, SortScr
 
 // ---------------------------------------------------------------- radix sort
 __device__ __forceinline__ uint32_t sort_digit(const SortScratch &s, uint32_t idx, int p) {
-    if (p >= 24) return (s.doc[idx] >> (8 * (p - 24))) & 0xFFu;
-    unsigned long long v = p < 8 ? s.klo[idx] : (p < 16 ? s.khi[idx] : ~s.cnt[idx]);
-    return (uint32_t)(v >> (8 * (p & 7))) & 0xFFu;
+    if (p >= kPasses) return (s.doc[idx] >> (8 * (p - kPasses))) & 0xFFu;
+    if (p < 8) return (uint32_t)(s.pk[idx] >> (8 * p)) & 0xFFu;
+    if (p < kSortKeyPasses) return (s.pk2[idx] >> (8 * (p - 8))) & 0xFFu;
+    return (uint32_t)(~s.cnt[idx] >> (8 * (p - kSortKeyPasses))) & 0xFFu;
 }
 
-// Histograms of all 24 digit positions (for skipping constant digits) and
-// the identity permutation.
+// 8 big-endian key bytes (0, or a lowercase letter) -> 8 five-bit codes, the
+// first byte in the highest code (40 bits).
+__device__ __forceinline__ unsigned long long pack5(unsigned long long be) {
+    unsigned long long r = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const uint32_t b = (uint32_t)(be >> (56 - 8 * i)) & 0xFFu;
+        r = (r << 5) | (b ? ((b | 0x20u) - 0x60u) & 31u : 0u);
+    }
+    return r;
+}
+
+// Packs the prefix keys, and takes the histograms of all digit positions
+// (for skipping constant digits) and the identity permutation.
 __global__ void k_hist_all(SortScratch s, const unsigned long long *meta, int passes) {
     __shared__ uint32_t h[kPassesSeg * 256];
     for (int i = threadIdx.x; i < kPassesSeg * 256; i += blockDim.x) h[i] = 0;
@@ -197,17 +213,22 @@ __global__ void k_hist_all(SortScratch s, const unsigned long long *meta, int pa
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         s.perm[0][i] = (uint32_t)i;
-        unsigned long long lo = s.klo[i], hi = s.khi[i], c = ~s.cnt[i];
+        const unsigned long long ph = pack5(s.khi[i]), pl = pack5(s.klo[i]), c = ~s.cnt[i];
+        const unsigned long long lo = (ph << 40) | pl;  // the 80-bit code: ph:pl
+        const uint32_t hi = (uint32_t)(ph >> 24);
+        s.pk[i] = lo;
+        s.pk2[i] = hi;
 #pragma unroll
         for (int b = 0; b < 8; b++) {
             atomicAdd(&h[b * 256 + ((lo >> (8 * b)) & 0xFF)], 1u);
-            atomicAdd(&h[(8 + b) * 256 + ((hi >> (8 * b)) & 0xFF)], 1u);
-            atomicAdd(&h[(16 + b) * 256 + ((c >> (8 * b)) & 0xFF)], 1u);
+            atomicAdd(&h[(kSortKeyPasses + b) * 256 + ((c >> (8 * b)) & 0xFF)], 1u);
         }
+        atomicAdd(&h[8 * 256 + (hi & 0xFF)], 1u);
+        atomicAdd(&h[9 * 256 + ((hi >> 8) & 0xFF)], 1u);
         if (passes > kPasses) {
             const uint32_t d = s.doc[i];
 #pragma unroll
-            for (int b = 0; b < 4; b++) atomicAdd(&h[(24 + b) * 256 + ((d >> (8 * b)) & 0xFF)], 1u);
+            for (int b = 0; b < 4; b++) atomicAdd(&h[(kPasses + b) * 256 + ((d >> (8 * b)) & 0xFF)], 1u);
         }
     }
     __syncthreads();
@@ -372,7 +393,7 @@ __device__ __forceinline__ bool tail_less(const LongView &v, uint32_t a, uint32_
 __global__ void k_fix_long(SortScratch s, LongView v, const unsigned long long *meta) {
     const unsigned long long n = meta[0];
     if (meta[1] == 0) return;
-    uint32_t *perm = s.perm_buf(s.cur[16]);
+    uint32_t *perm = s.perm_buf(s.cur[kSortKeyPasses]);
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         uint32_t e = perm[i];
@@ -445,7 +466,7 @@ cudaError_t sort_entries(SortScratch &ss, const unsigned long long *meta, const 
     k_hist_all<<<grid_for(cap, 256, sms * 2), 256, 0, st>>>(ss, meta, passes);
     const int ntiles = (int)((cap + kSortTile - 1) / kSortTile);
     for (int p = 0; p < passes; p++) {
-        if (p == 16) k_fix_long<<<grid_for(cap, 256, sms * 4), 256, 0, st>>>(ss, v, meta);
+        if (p == kSortKeyPasses) k_fix_long<<<grid_for(cap, 256, sms * 4), 256, 0, st>>>(ss, v, meta);
         k_pass_count<<<ntiles, kSortThreads, 0, st>>>(ss, p, meta);
         k_pass_scan<<<256, 256, 0, st>>>(ss, p, meta);
         k_pass_scatter<<<ntiles, kSortThreads, 0, st>>>(ss, p, meta);
