@@ -11,13 +11,13 @@
 //     image (4 keys per bucket, a key lives in one of two buckets).
 //  1. One persistent 512-thread block per SM copies that image into shared
 //     memory (keys read-only, counts zeroed) and walks its chunks through a
-//     ring of eight buffers.  Each chunk window (16 bytes before, 64 after,
+//     ring of four buffers.  Each chunk window (16 bytes before, 64 after,
 //     16-byte aligned in absolute address space) is staged by a TMA bulk
 //     copy that completes a "full" mbarrier; windows that touch the
 //     document's edges are staged by plain loads with the outside masked to
 //     spaces (a document edge separates words).  Warps never wait for each
 //     other: each warp releases a buffer when its words there are consumed,
-//     and the last warp to release it issues the copy of the chunk eight
+//     and the last warp to release it issues the copy of the chunk four
 //     places ahead.
 //  2. A warp classifies 512-byte strips: one 16-bit letter mask per lane
 //     (SWAR), word starts = letter & !previous letter, the previous byte
@@ -25,7 +25,7 @@
 //     holding its first byte and is read through the window's lookahead.
 //  3. Words of <= 16 letters are queued per warp and processed 32 at a time:
 //     a word of <= 8 letters in the head image adds 1 to its shared count
-//     (two bucket probes); every other word goes to a per-warp tail queue,
+//     (fingerprints of two buckets, then the matching key); every other word goes to a per-warp tail queue,
 //     flushed 32 at a time into the global 8-byte-key or 16-byte-key table
 //     (plain load of the key, fire-and-forget reduction; CAS only the first
 //     time a word is seen).
@@ -41,7 +41,10 @@ namespace wc {
 constexpr int kBlock = 512;           // threads of the main counting kernel
 constexpr int kWarps = kBlock / 32;
 constexpr int kChunk = kWarps * 512;  // bytes per chunk: one 512-byte strip per warp
-constexpr int kStages = 8;            // chunk buffers in flight per block (64 KB per SM)
+// Chunk buffers in flight per block (32 KB per SM).  More stages measured
+// slower: shared memory and L1 share one array per SM, and the L1 left over
+// holds the lines of the tail inserts' scattered loads in flight.
+constexpr int kStages = 4;
 constexpr int kLead = 16;             // window bytes before the chunk
 constexpr int kWinB = kChunk + 96;    // lead + chunk + 64 lookahead + 16 slack
 constexpr int kTokCap = 32 + 256;     // per-warp word queue (< 32 left + <= 256 per strip)
@@ -68,6 +71,7 @@ struct Count2Args {
     unsigned long long piece_stride;  // bytes between pieces (sampling) or 0
     GTable g;
     const unsigned long long *head;   // head image (nb * 4 keys) or null
+    const uint32_t *head_fp;          // its fingerprints (nb words of 4 bytes)
     uint32_t nb;
 };
 
@@ -150,26 +154,33 @@ __device__ __forceinline__ uint32_t head_bucket(unsigned long long key, unsigned
 constexpr unsigned long long kHeadMulA = 0x9E3779B97F4A7C15ull;
 constexpr unsigned long long kHeadMulB = 0xC2B2AE3D27D4EB4Full;
 
-// Slot of key in the shared head image, or -1 (two buckets of four).  Both
-// buckets are read at once (four independent 16-byte loads), so a lookup
-// costs one shared-memory round trip and no branch.
-__device__ __forceinline__ int head_find(const unsigned long long *hkey, unsigned long long key, uint32_t nb,
-                                         uint32_t *slot) {
+// One-byte fingerprint of a head key (never 0: 0 marks an empty slot), from
+// bits of the first bucket hash below the ones that pick the bucket.
+__device__ __forceinline__ uint32_t head_fp(unsigned long long key) {
+    const uint32_t f = (uint32_t)((key * kHeadMulA) >> 40) & 0xFFu;
+    return f ? f : 1u;
+}
+
+// Slot of key in the shared head image, or -1 (two buckets of four).  The
+// two buckets' fingerprint words (one byte a slot) are read first; only a
+// slot whose fingerprint matches has its key read and compared.  Most words
+// outside the head stop at the fingerprints, and a word in the head costs
+// two 4-byte and one 8-byte shared load.
+__device__ __forceinline__ int head_find(const unsigned long long *hkey, const uint32_t *hfp,
+                                         unsigned long long key, uint32_t nb) {
     const uint32_t b1 = head_bucket(key, kHeadMulA, nb), b2 = head_bucket(key, kHeadMulB, nb);
-    const ulonglong2 *h1 = reinterpret_cast<const ulonglong2 *>(hkey + b1 * 4);
-    const ulonglong2 *h2 = reinterpret_cast<const ulonglong2 *>(hkey + b2 * 4);
-    const ulonglong2 u0 = h1[0], u1 = h1[1], v0 = h2[0], v1 = h2[1];
-    int q = -1;
-    q = u0.x == key ? (int)(b1 * 4) : q;
-    q = u0.y == key ? (int)(b1 * 4 + 1) : q;
-    q = u1.x == key ? (int)(b1 * 4 + 2) : q;
-    q = u1.y == key ? (int)(b1 * 4 + 3) : q;
-    q = v0.x == key ? (int)(b2 * 4) : q;
-    q = v0.y == key ? (int)(b2 * 4 + 1) : q;
-    q = v1.x == key ? (int)(b2 * 4 + 2) : q;
-    q = v1.y == key ? (int)(b2 * 4 + 3) : q;
-    *slot = q < 0 ? 0u : (uint32_t)q;
-    return q;
+    const uint32_t f4 = head_fp(key) * 0x01010101u;
+    const uint32_t x1 = hfp[b1] ^ f4, x2 = hfp[b2] ^ f4;  // a zero byte = a matching fingerprint
+    // 0x80 in each zero byte (and possibly in bytes above one: those fail the key compare)
+    unsigned long long mm = ((unsigned long long)((x2 - 0x01010101u) & ~x2 & 0x80808080u) << 32) |
+                            ((x1 - 0x01010101u) & ~x1 & 0x80808080u);
+    while (mm) {
+        const int bit = __ffsll((long long)mm) - 1;  // 8 * byte + 7
+        const uint32_t slot = bit < 32 ? b1 * 4 + (uint32_t)(bit >> 3) : b2 * 4 + (uint32_t)((bit - 32) >> 3);
+        if (hkey[slot] == key) return (int)slot;
+        mm &= mm - 1;
+    }
+    return -1;
 }
 
 // Run length of the letters at w (w is a letter), capped at `end`: the warp
@@ -194,6 +205,7 @@ struct Counter2 {
     const Count2Args &a;
     unsigned long long *hkey;  // head image keys (read only) or the sampling table
     uint32_t *hcnt;
+    const uint32_t *hfp;       // head fingerprints
     uint4 *tailq;
     uint32_t nslots;
     uint32_t tailn;
@@ -229,10 +241,9 @@ struct Counter2 {
             tail = true;
             if (len <= 8) {
                 const unsigned long long key = load_key8(win, p, len);
-                uint32_t slot;
-                if (nslots && head_find(hkey, key, a.nb, &slot) >= 0) {
-                    hs = (int)slot;
-                    tail = false;
+                if (nslots) {
+                    hs = head_find(hkey, hfp, key, a.nb);
+                    tail = hs < 0;
                 }
                 tk = make_uint4((uint32_t)key, (uint32_t)(key >> 32), 0u, 0u);
             } else {
@@ -402,17 +413,20 @@ __global__ void __launch_bounds__(kBlock, 1) k_count2(Count2Args a) {
     uint4 *longall = tailall + kWarps * kTailCap;                                     // warps x kLongCap
     uint64_t *full = reinterpret_cast<uint64_t *>(longall + kWarps * kLongCap);     // kStages
     uint32_t *done = reinterpret_cast<uint32_t *>(full + kStages);                   // kStages
+    uint32_t *hfp = done + kStages;                                                   // nb
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *tok = tokall + warp * kTokCap;
     uint4 *longq = longall + warp * kLongCap;
     // head image (counting) or an empty local table (sampling)
     const uint32_t nslots = SAMPLE ? (1u << kSampleLocalBits) : (a.head ? a.nb * 4 : 0);
-    Counter2<SAMPLE> ctr{a, hkey, hcnt, tailall + warp * kTailCap, nslots, 0u, lane};
+    Counter2<SAMPLE> ctr{a, hkey, hcnt, hfp, tailall + warp * kTailCap, nslots, 0u, lane};
 
     for (uint32_t i = threadIdx.x; i < nslots; i += kBlock) {
         hkey[i] = SAMPLE ? 0ull : a.head[i];
         hcnt[i] = 0u;
     }
+    if (!SAMPLE && nslots)
+        for (uint32_t i = threadIdx.x; i < a.nb; i += kBlock) hfp[i] = a.head_fp[i];
     if (threadIdx.x < kStages) done[threadIdx.x] = 0u;
     if (threadIdx.x == 0) {
         for (int b = 0; b < kStages; b++) mbar_init(&full[b], 1);
@@ -565,7 +579,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_count2(Count2Args a) {
 
 constexpr size_t kCountSmem = (size_t)kHeadBuckets * 4 * 8 + (size_t)kHeadBuckets * 4 * 4 + kStages * (size_t)kWinB +
                               (size_t)kWarps * kTokCap * 4 + (size_t)kWarps * kTailCap * 16 +
-                              (size_t)kWarps * kLongCap * 16 + kStages * 8 + kStages * 4;
+                              (size_t)kWarps * kLongCap * 16 + kStages * 8 + kStages * 4 + (size_t)kHeadBuckets * 4;
 static_assert(kCountSmem <= 227 * 1024, "counting kernel shared memory");
 
 // ---------------------------------------------------------------- head selection
@@ -646,11 +660,15 @@ __global__ void k_head_collect(const G8Slot *s, unsigned long long cap, uint32_t
 // send all its occurrences to one global slot, whose atomics then serialise.
 __global__ void __launch_bounds__(1024) k_head_build(const unsigned long long *cand, const uint32_t *ccnt,
                                                      const uint32_t *meta, uint32_t kmax, uint32_t nb,
-                                                     unsigned long long *image) {
+                                                     unsigned long long *image, uint32_t *image_fp) {
     constexpr int kPer = (int)(kHeadSortN / 1024);  // candidates per thread
     __shared__ uint32_t fill[kHeadBuckets];
+    __shared__ uint32_t fps[kHeadBuckets];
     const uint32_t n = meta[1] < kmax ? meta[1] : kmax;
-    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) fill[i] = 0;
+    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) {
+        fill[i] = 0;
+        fps[i] = 0;
+    }
     for (uint32_t i = threadIdx.x; i < nb * 4; i += blockDim.x) image[i] = 0ull;
     int tier[kPer];
     unsigned long long key[kPer];
@@ -667,20 +685,24 @@ __global__ void __launch_bounds__(1024) k_head_build(const unsigned long long *c
             if (tier[k] != t) continue;
             const uint32_t b1 = head_bucket(key[k], kHeadMulA, nb), b2 = head_bucket(key[k], kHeadMulB, nb);
             const uint32_t first = fill[b1] <= fill[b2] ? b1 : b2, second = first == b1 ? b2 : b1;
-            uint32_t slot = atomicAdd(&fill[first], 1u);
-            if (slot < 4) {
-                image[first * 4 + slot] = key[k];
-            } else {
+            uint32_t slot = atomicAdd(&fill[first], 1u), bk = first;
+            if (slot >= 4) {
                 slot = atomicAdd(&fill[second], 1u);
-                if (slot < 4) image[second * 4 + slot] = key[k];
+                bk = second;
+            }
+            if (slot < 4) {
+                image[bk * 4 + slot] = key[k];
+                atomicOr(&fps[bk], head_fp(key[k]) << (8 * slot));
             }
         }
         __syncthreads();
     }
+    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) image_fp[i] = fps[i];
 }
 
 size_t head_scratch_bytes() {
-    return (size_t)kSampleSlots * sizeof(G8Slot) + 4096 * 4 + 64 + (size_t)kHeadBuckets * 4 * (8 * 2 + 4) + 1024;
+    return (size_t)kSampleSlots * sizeof(G8Slot) + 4096 * 4 + 64 + (size_t)kHeadBuckets * 4 * (8 * 2 + 4) +
+           (size_t)kHeadBuckets * 4 + 1024;
 }
 
 static int sm_count_dev() {
@@ -717,6 +739,7 @@ cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
     a.piece_stride = 0;
     a.g = c.g;
     a.head = nullptr;
+    a.head_fp = nullptr;
     a.nb = kHeadBuckets;
     const uint64_t n = c.hi - c.lo;
     if (n >= kHeadMinBytes && c.head_scratch) {
@@ -728,6 +751,7 @@ cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
         unsigned long long *cand = reinterpret_cast<unsigned long long *>(meta + 16);
         unsigned long long *image = cand + kHeadBuckets * 4;
         uint32_t *ccnt = reinterpret_cast<uint32_t *>(image + kHeadBuckets * 4);
+        uint32_t *image_fp = ccnt + kHeadBuckets * 4;
         cudaMemsetAsync(p, 0, kSampleSlots * sizeof(G8Slot) + 4096 * 4 + 64, s);
         Count2Args sa = a;
         sa.g.slots8 = sample;
@@ -742,8 +766,9 @@ cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
         k_head_hist<<<sms, 256, 0, s>>>(sample, kSampleSlots, hist);
         k_head_threshold<<<1, 1024, 0, s>>>(hist, kmax, meta);
         k_head_collect<<<sms * 2, 256, 0, s>>>(sample, kSampleSlots, meta, cand, ccnt, kmax);
-        k_head_build<<<1, 1024, 0, s>>>(cand, ccnt, meta, kmax, kHeadBuckets, image);
+        k_head_build<<<1, 1024, 0, s>>>(cand, ccnt, meta, kmax, kHeadBuckets, image, image_fp);
         a.head = image;
+        a.head_fp = image_fp;
     }
     int grid = c.grid > 0 ? c.grid : sms;
     if ((uint32_t)grid > a.nchunks) grid = (int)a.nchunks;
