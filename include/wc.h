@@ -112,6 +112,16 @@ wc_status wc_batch_status(const wc_batch *batch);
  * tables are built on the first request (Sec. 3.3's sum across documents). */
 wc_status wc_batch_table(const wc_batch *batch, int kind, uint32_t idx, const wc_table **out);
 
+/* Per-document top-k (Sec. 4.3 reports each speech's most frequent words):
+ * borrows a table (owned by the batch, freed with it or when its plan runs
+ * again; wc_table_free on it does nothing) whose rows are, document after
+ * document, the first min(k, n_i) rows of document i's table, i.e. its top k
+ * in (count desc, word asc) order.  Document i owns rows [h_first[i],
+ * h_first[i] + h_n[i]); h_first and h_n (host, ndocs entries each, either may
+ * be NULL) are filled before the call returns.  Read the rows with
+ * wc_table_size / wc_table_export (32-bit counts).  Waits for the batch. */
+wc_status wc_batch_topk(const wc_batch *batch, uint32_t k, uint64_t *h_first, uint32_t *h_n, const wc_table **out);
+
 /* Waits for the batch; total per-document entries and their word bytes. */
 wc_status wc_batch_size(const wc_batch *batch, uint64_t *nentries, uint64_t *word_bytes);
 

@@ -98,11 +98,13 @@ static wc_status batch_sync(const wc_batch *cb) {
     return b->sync_status;
 }
 
-// Words bytes and token totals of a view (one block).
+// Words bytes and token totals of a view (meta[3], meta[4] zeroed before;
+// any grid).
 __global__ void k_view_meta(DevTable t, unsigned long long n) {
     __shared__ unsigned long long sb[32], st[32];
     unsigned long long bytes = 0, tok = 0;
-    for (unsigned long long i = threadIdx.x; i < n; i += blockDim.x) {
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t r = t.lref[i];
         unsigned long long hi = t.khi[i], lo = t.klo[i];
         unsigned long long len;
@@ -121,11 +123,17 @@ __global__ void k_view_meta(DevTable t, unsigned long long n) {
     if (threadIdx.x == 0) {
         unsigned long long B = 0, T = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) { B += sb[w]; T += st[w]; }
-        t.d_meta[0] = n;
-        t.d_meta[3] = T;
-        t.d_meta[4] = B;
-        *t.d_status = 0;
+        if (T) atomicAdd(&t.d_meta[3], T);
+        if (B) atomicAdd(&t.d_meta[4], B);
+        if (blockIdx.x == 0) {
+            t.d_meta[0] = n;
+            *t.d_status = 0;
+        }
     }
+}
+static int view_meta_grid(unsigned long long n) {
+    const unsigned long long g = (n + 2047) / 2048;
+    return (int)(g < 1 ? 1 : (g > 1024 ? 1024 : g));
 }
 
 // A wc_table that reads entries [start, start+n) of the batch output.
@@ -152,7 +160,7 @@ static wc_status make_view(wc_batch *b, uint64_t start, uint64_t n, wc_table **o
     d.loff = b->args.loff;
     d.llen = b->args.llen;
     d.arena = b->args.arena;
-    k_view_meta<<<1, 256, 0, b->stream>>>(d, n);
+    k_view_meta<<<view_meta_grid(n), 256, 0, b->stream>>>(d, n);
     t->stream = b->stream;
     cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming);
     cudaEventRecord(t->done, b->stream);
@@ -576,6 +584,96 @@ static wc_status build_tables(wc_batch *b) {
     b->class_tables.assign(tabs.begin(), tabs.begin() + b->nclasses);
     b->global = tabs[b->nclasses];
     b->tables_built = true;
+    return WC_OK;
+}
+
+// Rows [first[d], first[d] + min(k, n_d)) of the output are document d's
+// first rows (its top k): one warp per document.
+__global__ void k_batch_topk(BatchArgs a, const unsigned long long *first, uint32_t k, DevTable out) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    for (unsigned long long d = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; d < a.ndocs;
+         d += nw) {
+        const unsigned long long src = a.doc_start[d], dst = first[d];
+        const uint32_t n = a.doc_n[d], m = n < k ? n : k;
+        for (uint32_t j = lane; j < m; j += 32) {
+            out.khi[dst + j] = a.out_khi[src + j];
+            out.klo[dst + j] = a.out_klo[src + j];
+            static_cast<uint32_t *>(out.cnt)[dst + j] = a.out_cnt[src + j];
+            out.lref[dst + j] = a.out_lref[src + j];
+        }
+    }
+}
+
+wc_status wc_batch_topk(const wc_batch *cb, uint32_t k, uint64_t *h_first, uint32_t *h_n, const wc_table **out) {
+    if (!cb || !out) return WC_ERR_INVALID_ARG;
+    *out = nullptr;
+    wc_batch *b = const_cast<wc_batch *>(cb);
+    wc_ctx *ctx = b->ctx;
+    cudaSetDevice(ctx->device);
+    wc_status st = batch_sync(b);
+    if (st != WC_OK) return st;
+    const uint32_t nd = b->ndocs;
+    std::vector<uint32_t> n(nd);
+    std::vector<unsigned long long> first(nd + 1, 0);
+    cudaError_t e = cudaSuccess;
+    if (nd) e = cudaMemcpy(n.data(), b->args.doc_n, 4ull * nd, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "batch top-k");
+    for (uint32_t d = 0; d < nd; d++) first[d + 1] = first[d] + std::min(k, n[d]);
+    const uint64_t rows = first[nd];
+    for (uint32_t d = 0; d < nd; d++) {
+        if (h_first) h_first[d] = first[d];
+        if (h_n) h_n[d] = std::min(k, n[d]);
+    }
+    // one block: metadata, the rows' keys, counts and long references, the offsets
+    auto r = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const uint64_t cap = std::max<uint64_t>(rows, 1);
+    wc_table *t = new wc_table();
+    t->ctx = ctx;
+    t->owner = b;
+    t->bytes = r(512) + r(cap * 8) * 2 + r(cap * 4) * 2 + r(8ull * (nd + 1));
+    st = ctx->alloc(&t->mem, t->bytes, b->stream);
+    if (st != WC_OK) { delete t; return st; }
+    uint8_t *p = static_cast<uint8_t *>(t->mem);
+    e = cudaMemsetAsync(p, 0, 512, b->stream);
+    DevTable &d = t->dt;
+    d.cap = cap;
+    d.lcap = b->args.lcap;
+    d.arena_cap = b->args.arena_cap;
+    d.count_bits = 32;
+    d.d_meta = reinterpret_cast<unsigned long long *>(p);
+    d.d_status = reinterpret_cast<uint32_t *>(p + 256);
+    p += r(512);
+    d.khi = reinterpret_cast<unsigned long long *>(p);
+    p += r(cap * 8);
+    d.klo = reinterpret_cast<unsigned long long *>(p);
+    p += r(cap * 8);
+    d.cnt = p;
+    p += r(cap * 4);
+    d.lref = reinterpret_cast<uint32_t *>(p);
+    p += r(cap * 4);
+    unsigned long long *d_first = reinterpret_cast<unsigned long long *>(p);
+    d.loff = b->args.loff;  // long words stay in the batch's arena
+    d.llen = b->args.llen;
+    d.arena = b->args.arena;
+    // pageable source: the call returns once the bytes are staged
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_first, first.data(), 8ull * (nd + 1), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && nd && rows) {
+        const unsigned long long g = std::min<unsigned long long>((nd + 7) / 8, 4096);
+        k_batch_topk<<<(int)g, 256, 0, b->stream>>>(b->args, d_first, k, d);
+        ctx->launches++;
+    }
+    if (e == cudaSuccess) {
+        k_view_meta<<<view_meta_grid(rows), 256, 0, b->stream>>>(d, rows);
+        ctx->launches++;
+        e = cudaGetLastError();
+    }
+    t->stream = b->stream;
+    cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming);
+    cudaEventRecord(t->done, b->stream);
+    b->views.push_back(t);  // freed with the batch
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "batch top-k");
+    *out = t;
     return WC_OK;
 }
 

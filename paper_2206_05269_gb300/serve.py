@@ -11,11 +11,14 @@ own CUDA stream:
     shared-memory head, capacities learned from earlier requests).
 Requests that arrive while work is running are admitted as soon as a stream
 and device memory free up, so their work overlaps on the device.  Each
-request is answered with its table (32-bit counts, count desc then word asc)
-and its top-k (the table's first k rows).  The context's device-memory budget
-bounds admission: work the budget cannot hold waits for running work to
-finish.  A round whose device tables overflow is recounted request by request
-with growing capacities, so answers are always exact.
+request's table (32-bit counts, count desc then word asc) is built and kept
+on the device; the answer returned to the host is its top-k (the table's
+first k rows, gathered on the device: wc_topk for a single count,
+wc_batch_topk for a round), and the whole table too when keep_tables is set.
+The context's device-memory budget bounds admission: work the budget cannot
+hold waits for running work to finish.  A round whose device tables overflow
+is recounted request by request with growing capacities, so answers are
+always exact.
 
 `serve_fifo` is the plain path for comparison: one request at a time, in
 arrival order, one wc_count launch per request.
@@ -43,16 +46,18 @@ class Answer:
     rid: int
     arrival: float
     done: float
-    words: np.ndarray       # uint8
+    words: np.ndarray       # uint8: the top-k rows, or the whole table when kept
     offs: np.ndarray        # uint64 [n+1]
     counts: np.ndarray      # uint32 [n]
     topk: int
+    full: bool = False      # words/offs/counts hold the whole table
 
     @property
     def latency(self) -> float:
         return self.done - self.arrival
 
     def as_list(self, limit: int | None = None):
+        """The first rows of the answer (all rows held when limit is None)."""
         n = self.counts.size if limit is None else min(limit, self.counts.size)
         return [(self.words[self.offs[i]:self.offs[i + 1]].tobytes(), int(self.counts[i])) for i in range(n)]
 
@@ -94,7 +99,7 @@ def _to_device(reqs, dev, stream):
 
 
 def serve_batched(counter: wc.Counter, requests: list[Request], topk: int = 100, max_inflight: int = 6,
-                  round_bytes: int = 256 << 20, big_bytes: int = 4 << 20, keep_tables: bool = True,
+                  round_bytes: int = 256 << 20, big_bytes: int = 4 << 20, keep_tables: bool = False,
                   device: int = 0):
     """Runs the request stream through the continuous-batching loop and returns
     one Answer per request (in request order) plus run statistics."""
@@ -108,12 +113,23 @@ def serve_batched(counter: wc.Counter, requests: list[Request], topk: int = 100,
     order = sorted(requests, key=lambda r: r.arrival)
     nxt = 0
     t0 = time.perf_counter()
-    stats = {"rounds": 0, "large": 0, "recounted": 0}
+    stats = {"rounds": 0, "large": 0, "recounted": 0, "capacity_errors": []}
 
-    def answer(rq, w, o, c, s0, n):
-        m = n if keep_tables else min(n, topk)
-        answers[rq.rid] = Answer(rq.rid, rq.arrival, time.perf_counter() - t0, w[o[s0]:o[s0 + m]].copy(),
-                                 (o[s0:s0 + m + 1] - o[s0]).astype(np.uint64), c[s0:s0 + m].astype(np.uint32), topk)
+    def answer(rq, w, o, c, s0, n, full):
+        now = time.perf_counter() - t0
+        answers[rq.rid] = Answer(rq.rid, rq.arrival, now, w[o[s0]:o[s0 + n]],
+                                 (o[s0:s0 + n + 1] - o[s0]).astype(np.uint64), c[s0:s0 + n].astype(np.uint32), topk,
+                                 full)
+
+    def answer_table(rq, t, stream):  # one request's device table -> its answer
+        if keep_tables:
+            w, o, c = t.export(stream)
+            answer(rq, w, o, c, 0, c.size, True)
+        else:
+            top = counter.topk(t, topk, stream)
+            w, o, c = top.export(stream)
+            top.free()
+            answer(rq, w, o, c, 0, c.size, False)
 
     def recount(rq, stream):  # exact fallback with growing capacities
         with torch.cuda.stream(stream):
@@ -121,8 +137,8 @@ def serve_batched(counter: wc.Counter, requests: list[Request], topk: int = 100,
             if rq.data.numel():
                 text.copy_(rq.data, non_blocking=True)
             t = counter.count_checked(text, stream=stream)
-            w, o, c = t.export(stream)
-        answer(rq, w, o, c, 0, c.size)
+            answer_table(rq, t, stream)
+            t.free()
         stats["recounted"] += 1
 
     def finish(wk: _Work):
@@ -132,20 +148,26 @@ def serve_batched(counter: wc.Counter, requests: list[Request], topk: int = 100,
             if st == wc.WC_ERR_CAPACITY:
                 recount(wk.reqs[0], wk.stream)
             else:
-                w, o, c = wk.table.export(wk.stream)
-                answer(wk.reqs[0], w, o, c, 0, c.size)
+                answer_table(wk.reqs[0], wk.table, wk.stream)
             wk.table.free()
         else:
             st = wk.batch.status()
             if st == wc.WC_ERR_CAPACITY:
+                if len(stats["capacity_errors"]) < 8:
+                    stats["capacity_errors"].append(wc.wc_last_error(counter.ctx))
                 for rq in wk.reqs:
                     recount(rq, wk.stream)
             elif st != wc.WC_OK:
                 raise wc.WcError(st, wc.wc_last_error(counter.ctx))
-            else:
+            elif keep_tables:
                 ds, dn, w, o, c = wk.batch.export(wk.stream)
                 for j, rq in enumerate(wk.reqs):
-                    answer(rq, w, o, c, int(ds[j]), int(dn[j]))
+                    answer(rq, w, o, c, int(ds[j]), int(dn[j]), True)
+            else:  # every request's top-k gathered on the device, one small copy
+                top, first, n = wk.batch.topk(topk)
+                w, o, c = top.export(wk.stream)
+                for j, rq in enumerate(wk.reqs):
+                    answer(rq, w, o, c, int(first[j]), int(n[j]), False)
             del wk.batch
         free_streams.append(wk.stream)
 
@@ -215,10 +237,11 @@ def serve_batched(counter: wc.Counter, requests: list[Request], topk: int = 100,
     return [answers[r.rid] for r in requests], stats
 
 
-def serve_fifo(counter: wc.Counter, requests: list[Request], topk: int = 100, keep_tables: bool = True,
+def serve_fifo(counter: wc.Counter, requests: list[Request], topk: int = 100, keep_tables: bool = False,
                device: int = 0):
     """The plain path: one request at a time in arrival order, one wc_count
-    launch per request (host -> device copy, count, top-k, table -> host)."""
+    launch per request (host -> device copy, count, top-k on the device,
+    top-k (or the whole table) -> host)."""
     import torch
     dev = torch.device("cuda", device)
     stream = torch.cuda.Stream(device=dev)
@@ -232,11 +255,14 @@ def serve_fifo(counter: wc.Counter, requests: list[Request], topk: int = 100, ke
             if r.data.numel():
                 text.copy_(r.data, non_blocking=True)
             t = counter.count_checked(text, stream=stream)
-            w, o, c = t.export(stream)
+            if keep_tables:
+                w, o, c = t.export(stream)
+            else:
+                top = counter.topk(t, topk, stream)
+                w, o, c = top.export(stream)
+                top.free()
         now = time.perf_counter() - t0
-        m = c.size if keep_tables else min(c.size, topk)
-        answers[r.rid] = Answer(r.rid, r.arrival, now, w[:o[m]].copy(), o[:m + 1].copy(),
-                                c[:m].astype(np.uint32), topk)
+        answers[r.rid] = Answer(r.rid, r.arrival, now, w, o, c.astype(np.uint32), topk, keep_tables)
         t.free()
     wall = time.perf_counter() - t0
     return [answers[r.rid] for r in requests], {"wall_s": wall}

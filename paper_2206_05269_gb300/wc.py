@@ -33,7 +33,7 @@ WC_TABLE_DOC, WC_TABLE_CLASS, WC_TABLE_GLOBAL = 0, 1, 2
 # Every symbol include/wc.h declares (checked by the tests).
 EXPORTS = [
     "wc_create", "wc_destroy", "wc_count", "wc_count_ex", "wc_count_batched", "wc_batch_status",
-    "wc_batch_table", "wc_batch_size", "wc_batch_export",
+    "wc_batch_table", "wc_batch_topk", "wc_batch_size", "wc_batch_export",
     "wc_class_ratio_topk", "wc_merge", "wc_topk", "wc_table_status", "wc_table_size",
     "wc_table_export", "wc_table_count_bits", "wc_table_free", "wc_batch_free", "wc_plan_create", "wc_plan_run",
     "wc_plan_free", "wc_count_noalloc", "wc_profile_enable",
@@ -79,6 +79,7 @@ def load() -> ctypes.CDLL:
         "wc_count_batched": (i32, [vp, vp, vp, vp, u32, vp, u32, vp, pvp]),
         "wc_batch_status": (i32, [vp]),
         "wc_batch_table": (i32, [vp, i32, u32, pvp]),
+        "wc_batch_topk": (i32, [vp, u32, ctypes.POINTER(u64), ctypes.POINTER(u32), pvp]),
         "wc_batch_size": (i32, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]),
         "wc_batch_export": (i32, [vp, vp, vp, vp, vp, vp, vp]),
         "wc_class_ratio_topk": (i32, [vp, vp, u32, u32, vp, vp, vp, vp, ctypes.POINTER(u32)]),
@@ -179,6 +180,18 @@ def wc_batch_table(batch, kind: int, idx: int):
     out = ctypes.c_void_p()
     _check(load().wc_batch_table(batch, kind, idx, ctypes.byref(out)), None, "wc_batch_table")
     return out
+
+
+def wc_batch_topk(batch, ndocs: int, k: int):
+    """Per-document top-k rows: (borrowed table handle, first row per document,
+    rows per document)."""
+    first = np.zeros(max(1, ndocs), dtype=np.uint64)
+    n = np.zeros(max(1, ndocs), dtype=np.uint32)
+    out = ctypes.c_void_p()
+    _check(load().wc_batch_topk(batch, k, first.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                n.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), ctypes.byref(out)),
+           None, "wc_batch_topk")
+    return out, first[:ndocs], n[:ndocs]
 
 
 def wc_class_ratio_topk(ctx, batch, cls: int, k: int, stream: int):
@@ -361,6 +374,12 @@ class Batch:
 
     def table(self, kind: int, idx: int = 0) -> Table:
         return Table(wc_batch_table(self.handle, kind, idx), owned=False)
+
+    def topk(self, k: int):
+        """Every document's top-k rows in one table (borrowed from the batch),
+        with each document's first row and row count."""
+        h, first, n = wc_batch_topk(self.handle, self.ndocs, k)
+        return Table(h, owned=False), first, n
 
 
 class Counter:

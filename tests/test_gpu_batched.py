@@ -137,3 +137,20 @@ def test_batched_workload_full_size_sampled(ctr):
     g = b.table(wc.WC_TABLE_GLOBAL)
     items = sorted(c.truth().items(), key=lambda kv: (-kv[1], kv[0]))
     assert_same(g.export(), oracle.Table.from_list(items), "global vs generator")
+
+
+def test_batch_topk_rows_are_each_documents_first_rows(ctr):
+    """wc_batch_topk: every document's first min(k, n) rows, gathered into one
+    table, equal the oracle's top k of that document (long words included)."""
+    c = corpus.generate("tiny", ndocs=40, len_max=30, len_tail=0.3, len_tail_mean=8.0)
+    r = oracle.count(c.text, c.offsets)
+    b, keep = run_batched(ctr, c.text, c.offsets)
+    for k in (1, 7, 100, 100000):
+        top, first, n = b.topk(k)
+        w, o, cnt = top.export()
+        assert cnt.size == int(n.sum())
+        for d in range(c.ndocs):
+            want = r.doc(d).as_list()[:k]
+            s0, m = int(first[d]), int(n[d])
+            got = [(w[o[i]:o[i + 1]].tobytes(), int(cnt[i])) for i in range(s0, s0 + m)]
+            assert got == want, f"k={k} doc {d}"

@@ -35,22 +35,30 @@ def test_mix_equals_alone_and_oracle(ctr):
     from gpu_util import to_dev
     pool, trip, reqs = make_requests()
     assert len(reqs) >= 20
-    answers, stats = serve.serve_batched(ctr, reqs, topk=100, max_inflight=3, big_bytes=512 << 10)
+    answers, stats = serve.serve_batched(ctr, reqs, topk=100, max_inflight=3, big_bytes=512 << 10,
+                                         keep_tables=True)
     assert stats["rounds"] >= 2 and stats["large"] >= 1
+    alone = []
     for (a, s, e), ans in zip(trip, answers):
         data = pool[s:e].tobytes()
-        alone = ctr.count_checked(to_dev(data)).as_list()
-        assert ans.as_list() == alone, f"request {ans.rid} differs alone vs in the mix"
+        alone.append(ctr.count_checked(to_dev(data)).as_list())
+        assert ans.full and ans.as_list() == alone[-1], f"request {ans.rid} differs alone vs in the mix"
         assert ans.latency >= 0
     for (a, s, e), ans in list(zip(trip, answers))[::5]:
         assert ans.as_list() == oracle.count(pool[s:e]).glob().as_list()
+    # the default answer: the top 100 rows gathered on the device
+    top, _ = serve.serve_batched(ctr, reqs, topk=100, max_inflight=3, big_bytes=512 << 10)
+    for ans, want in zip(top, alone):
+        assert not ans.full and ans.as_list() == want[:100], f"request {ans.rid}: top-100 differs"
 
 
 def test_fifo_path_matches(ctr):
     from paper_2206_05269_gb300 import serve
     pool, trip, reqs = make_requests(n_rate=200.0, dur=0.05, seed=4)
-    a1, _ = serve.serve_batched(ctr, reqs, topk=100)
-    a2, _ = serve.serve_fifo(ctr, reqs, topk=100)
-    for x, y in zip(a1, a2):
+    a1, _ = serve.serve_batched(ctr, reqs, topk=100, keep_tables=True)
+    a2, _ = serve.serve_fifo(ctr, reqs, topk=100, keep_tables=True)
+    t1, _ = serve.serve_batched(ctr, reqs, topk=100)
+    t2, _ = serve.serve_fifo(ctr, reqs, topk=100)
+    for x, y, tx, ty in zip(a1, a2, t1, t2):
         assert x.as_list() == y.as_list()
-        assert x.as_list(100) == y.as_list()[:100]
+        assert tx.as_list() == ty.as_list() == x.as_list()[:100]
