@@ -431,7 +431,8 @@ def run_served_workload(args, local):
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": "served", "requests": len(reqs), "seconds": args.serve_seconds,
                    "bytes": nbytes, "rounds": st["rounds"], "large_requests": st["large"],
-                   "recounted": st["recounted"], "budget_GB": 40},
+                   "recounted": st["recounted"], "budget_GB": 40,
+                   "first_capacity_error": st["capacity_errors"][0] if st["capacity_errors"] else None},
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "req_per_s": len(reqs) / st["wall_s"], "GBps": nbytes / st["wall_s"] / 1e9,
         "fifo": {"requests": len(fans), "p50_ms": float(np.percentile(flat, 50)) if len(fans) else None,
