@@ -311,7 +311,7 @@ def run_docs_workload(args, local):
     import corpus
     from paper_2206_05269_gb300 import wc
     torch.cuda.set_device(local)
-    c = corpus.generate(args.workload)
+    c = corpus.generate(args.workload, **({"ndocs": args.docs} if args.docs else {}))
     host, text, offs, cls = _dev_docs(c, local)
     stream = torch.cuda.current_stream()
     tune = os.path.join(ROOT, "paper_2206_05269_gb300", "_build", "tune_cache.json")
@@ -455,6 +455,7 @@ def main():
     ap.add_argument("--cpu-sample-mb", type=float, default=150.0)
     ap.add_argument("--bytes", type=float, default=1e9, help="corpus size (smaller only for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--docs", type=int, default=0, help="document count of a docs workload (smaller only for profiling)")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--fifo-seconds", type=float, default=2.0)
     ap.add_argument("--pool-bytes", type=float, default=2e9)

@@ -274,7 +274,8 @@ wc_status table_sync(const wc_table *ct) {
     t->sync_status = status_from_bits(status);
     if (t->sync_status != WC_OK) {
         t->n = t->tokens = t->word_bytes = 0;
-        t->ctx->fail(t->sync_status, "device table overflow or wait limit; count again with larger capacities");
+        t->ctx->fail(t->sync_status, ("device table overflow or wait limit (status bits " + std::to_string(status) +
+                                      "); count again with larger capacities").c_str());
     }
     if (t->sync_status == WC_OK && t->src_bytes) {
         wc_ctx *c = t->ctx;
@@ -361,16 +362,18 @@ static uint64_t pow2_at_least(uint64_t x) {
 }
 
 // Automatic capacities.  Distinct words of a text of B bytes are estimated
-// with a Heaps'-law bound 16 * T^0.6 on T = B/5 tokens (generous for Zipf
-// text) and never above the exact bound ceil(B/2).  When the context has
-// counted a text of similar size before, the distinct counts it saw (per key
-// width) are used instead, scaled by size.  Overflow is reported, never
-// silent: callers count again with larger capacities.
+// from T = B/5 tokens as the larger of a Heaps'-law term 16 * T^0.6 (a small
+// vocabulary) and T/4 (a large vocabulary in a mid-sized text, where most
+// tokens of the Zipf tail are still first occurrences), the latter capped at
+// 2M distinct words so huge texts keep L2-sized tables, and never above the
+// exact bound ceil(B/2).  When the context has counted a text within 8x of
+// this size before, the distinct counts it saw (per key width) are used
+// instead, twice over and scaled up (never down) by size: distinct words
+// grow more slowly than the text.  Overflow is reported, never silent:
+// callers count again with larger capacities.
 CapPlan plan_capacity(const wc_ctx *ctx, uint64_t nbytes, const wc_count_opts *o) {
     double tokens = (double)nbytes / 5.0 + 1.0;
-    // Heaps' term, or T/16 for a large vocabulary in a mid-sized text (capped
-    // at 2M distinct words so huge texts keep L2-sized tables)
-    double est = std::min(tokens, std::max(16.0 * std::pow(tokens, 0.6), std::min(tokens / 16.0, 2097152.0)));
+    double est = std::min(tokens, std::max(16.0 * std::pow(tokens, 0.6), std::min(tokens / 4.0, 2097152.0)));
     uint64_t bound = nbytes / 2 + 1;
     uint64_t d = std::min<uint64_t>((uint64_t)est + 64, bound);
     CapPlan p;
@@ -378,7 +381,7 @@ CapPlan plan_capacity(const wc_ctx *ctx, uint64_t nbytes, const wc_count_opts *o
     p.cap16 = pow2_at_least(std::max<uint64_t>(1024, d * 3 / 5));
     p.caplong = pow2_at_least(std::max<uint64_t>(256, 2 * (d / 16 + 16)));
     p.arena = std::max<uint64_t>(4096, std::min<uint64_t>(nbytes + nbytes / 16 + 16, p.caplong * 24));
-    if (ctx && ctx->hist_bytes && nbytes <= 2 * ctx->hist_bytes && 2 * nbytes >= ctx->hist_bytes) {
+    if (ctx && ctx->hist_bytes && nbytes <= 8 * ctx->hist_bytes && 8 * nbytes >= ctx->hist_bytes) {
         double r = (double)nbytes / (double)ctx->hist_bytes;
         auto scaled = [&](uint64_t n) { return (uint64_t)((double)n * std::max(1.0, r)) + 64; };
         p.cap8 = pow2_at_least(std::max<uint64_t>(1024, 2 * scaled(ctx->hist_n8)));

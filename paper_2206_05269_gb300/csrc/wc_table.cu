@@ -388,26 +388,36 @@ __device__ __forceinline__ bool tail_less(const LongView &v, uint32_t a, uint32_
     return la < lb;
 }
 
-// Orders runs of equal 16-byte prefix (only possible with long words) by
-// full bytes; runs are tiny, one thread sorts each by insertion.
+// Orders runs of equal 16-byte prefix that hold a long word by full bytes
+// (only a long word can share its prefix with another word).  The first long
+// entry of such a run sorts it by insertion; runs without a long entry (in a
+// per-document sort: the same short word in many documents) are not touched.
 __global__ void k_fix_long(SortScratch s, LongView v, const unsigned long long *meta) {
     const unsigned long long n = meta[0];
     if (meta[1] == 0) return;
     uint32_t *perm = s.perm_buf(s.cur[kSortKeyPasses]);
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
-        uint32_t e = perm[i];
-        if (i > 0) {
-            uint32_t q = perm[i - 1];
-            if (s.khi[q] == s.khi[e] && s.klo[q] == s.klo[e]) continue;  // not a run start
+        const uint32_t e = perm[i];
+        if (v.lref[e] == 0u) continue;
+        const unsigned long long kh = s.khi[e], kl = s.klo[e];
+        unsigned long long lo = i;
+        bool leader = true;
+        while (lo > 0) {
+            const uint32_t q = perm[lo - 1];
+            if (s.khi[q] != kh || s.klo[q] != kl) break;
+            if (v.lref[q] != 0u) { leader = false; break; }  // an earlier long entry sorts the run
+            lo--;
         }
+        if (!leader) continue;
         unsigned long long j = i + 1;
-        while (j < n && s.khi[perm[j]] == s.khi[e] && s.klo[perm[j]] == s.klo[e]) j++;
-        if (j - i < 2) continue;
-        for (unsigned long long a = i + 1; a < j; a++) {
+        while (j < n && s.khi[perm[j]] == kh && s.klo[perm[j]] == kl) j++;
+        if (j - lo < 2) continue;
+        const unsigned long long i0 = lo;
+        for (unsigned long long a = i0 + 1; a < j; a++) {
             uint32_t x = perm[a];
             unsigned long long b = a;
-            while (b > i && tail_less(v, x, perm[b - 1])) { perm[b] = perm[b - 1]; b--; }
+            while (b > i0 && tail_less(v, x, perm[b - 1])) { perm[b] = perm[b - 1]; b--; }
             perm[b] = x;
         }
     }

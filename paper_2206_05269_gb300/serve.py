@@ -146,6 +146,8 @@ def serve_batched(counter: wc.Counter, requests: list[Request], topk: int = 100,
         if wk.table is not None:
             st = wk.table.status()
             if st == wc.WC_ERR_CAPACITY:
+                if len(stats["capacity_errors"]) < 8:
+                    stats["capacity_errors"].append(wc.wc_last_error(counter.ctx))
                 recount(wk.reqs[0], wk.stream)
             else:
                 answer_table(wk.reqs[0], wk.table, wk.stream)
