@@ -70,6 +70,26 @@ __device__ __forceinline__ unsigned long long be_bytes16(const uint8_t *src, int
     return v;
 }
 
+// 128-bit sort composite of a per-document entry: count (16 bits, stored as
+// 0xFFFF - count so that a larger count sorts first), the 16-letter prefix
+// packed 5 bits a letter (80 bits, pack5 of the big-endian key halves), a
+// long-word flag and the long word's index.  Documents counted in shared
+// memory hold at most 64 KB, so counts stay below 2^16.
+__device__ __forceinline__ ulonglong2 doc_composite(unsigned long long khi, unsigned long long klo, uint32_t cnt,
+                                                   bool is_long, uint32_t idx) {
+    const unsigned long long ph = pack5(khi), pl = pack5(klo);  // 40 bits each
+    const unsigned long long c = 0xFFFFull - (cnt > 0xFFFFu ? 0xFFFFu : cnt);
+    const unsigned long long hi = (c << 48) | (ph << 8) | (pl >> 32);
+    const unsigned long long lo = ((pl & 0xFFFFFFFFull) << 32) | ((unsigned long long)is_long << 31) | (idx & 0x7FFFFFFFu);
+    return make_ulonglong2(hi, lo);
+}
+__device__ __forceinline__ void doc_decompose(ulonglong2 k, unsigned long long *khi, unsigned long long *klo,
+                                              uint32_t *cnt) {
+    *cnt = 0xFFFFu - (uint32_t)(k.x >> 48);
+    *khi = unpack5((k.x >> 8) & 0xFFFFFFFFFFull);
+    *klo = unpack5(((k.x & 0xFFull) << 32) | (k.y >> 32));
+}
+
 // ---------------------------------------------------------------- per-document kernel
 template <int BLOCK, int LOGC1>
 struct DocCfg {
@@ -82,7 +102,7 @@ struct DocCfg {
     static constexpr uint32_t FILL = C1 * 3 / 4;
     static constexpr size_t SMEM = (size_t)WINB + (size_t)W * TOKCAP * 4 +  // window + queues (sort buffer)
                                    (size_t)C1 * 16 + (size_t)C1 * 4 + (size_t)C1 * 4 +  // keys, counts, tags
-                                   (size_t)LCAP * (8 + 8 + 4 + 4 + 16) + 64;
+                                   (size_t)LCAP * (8 + 8 + 4 + 4 + 16) + 16 + 64;
     static_assert((size_t)WINB + (size_t)W * TOKCAP * 4 >= (size_t)C1 * 2, "sort buffer must fit");
     static_assert(C1 <= 32768, "16-bit sort indices");
 };
@@ -309,19 +329,28 @@ __global__ void __launch_bounds__(BLOCK) k_docs(BatchArgs a) {
                 }
             }
         }
-        // keys to big-endian halves (in place), long prefixes
-        for (int i = threadIdx.x; i < C::C1; i += BLOCK) {
+        // Every live entry becomes a 128-bit composite in place (its count,
+        // its 16-letter prefix packed 5 bits a letter, a long-word flag and
+        // index): integer order on composites is the output order (count
+        // desc, word asc) except among long words sharing a prefix, which a
+        // fix-up orders below.  The sort then moves 16-bit indices and
+        // compares composites.
+        for (int i = threadIdx.x; i < C::C1; i += BLOCK)
             if (stag[i] > 1u) {
-                uint4 k = skey[i];
-                reinterpret_cast<ulonglong2 *>(skey)[i] = make_ulonglong2(be64b(k.x, k.y), be64b(k.z, k.w));
+                const uint4 k = skey[i];
+                reinterpret_cast<ulonglong2 *>(skey)[i] =
+                    doc_composite(be64b(k.x, k.y), be64b(k.z, k.w), scnt[i], false, 0u);
             }
-        }
         __syncthreads();
         for (uint32_t j = threadIdx.x; j < nl; j += BLOCK) {
             const uint8_t *p = reinterpret_cast<const uint8_t *>(laddr[j]);
-            lkey[j] = make_ulonglong2(be_bytes16(p, 0), be_bytes16(p, 8));
+            lkey[j] = doc_composite(be_bytes16(p, 0), be_bytes16(p, 8), lcnt[j], true, j);
         }
-        if (threadIdx.x == 0) { sh.nent = 0; sh.nlong = 0; }
+        if (threadIdx.x == 0) {
+            sh.nent = 0;
+            sh.nlong = 0;
+            lkey[C::LCAP] = make_ulonglong2(~0ull, ~0ull);  // the padding entry sorts last
+        }
         __syncthreads();
         // index list of live entries (order is fixed by the sort below)
         for (int i = threadIdx.x; i < C::C1; i += BLOCK)
@@ -338,45 +367,62 @@ __global__ void __launch_bounds__(BLOCK) k_docs(BatchArgs a) {
         const uint32_t n = sh.nent;
         uint32_t N = 1;
         while (N < n) N <<= 1;
-        for (uint32_t i = n + threadIdx.x; i < N; i += BLOCK) sidx[i] = 0xFFFFu;
+        constexpr uint16_t kPad = (uint16_t)(C::C1 + C::LCAP);
+        for (uint32_t i = n + threadIdx.x; i < N; i += BLOCK) sidx[i] = kPad;
         __syncthreads();
-        auto cnt_of = [&](uint32_t s) -> uint32_t { return s < (uint32_t)C::C1 ? scnt[s] : lcnt[s - C::C1]; };
         auto key_of = [&](uint32_t s) -> ulonglong2 {
             return s < (uint32_t)C::C1 ? reinterpret_cast<const ulonglong2 *>(skey)[s] : lkey[s - C::C1];
         };
-        auto less = [&](uint32_t x, uint32_t y) -> bool {
-            if (x == 0xFFFFu) return false;
-            if (y == 0xFFFFu) return true;
-            const uint32_t cx = cnt_of(x), cy = cnt_of(y);
-            if (cx != cy) return cx > cy;
-            const ulonglong2 kx = key_of(x), ky = key_of(y);
-            if (kx.x != ky.x) return kx.x < ky.x;
-            if (kx.y != ky.y) return kx.y < ky.y;
-            const bool lx = x >= (uint32_t)C::C1, ly = y >= (uint32_t)C::C1;
-            if (!lx) return ly;
-            if (!ly) return false;
-            const uint8_t *px = reinterpret_cast<const uint8_t *>(laddr[x - C::C1]);
-            const uint8_t *py = reinterpret_cast<const uint8_t *>(laddr[y - C::C1]);
-            const unsigned long long nx = llen[x - C::C1], ny = llen[y - C::C1];
-            const unsigned long long m = nx < ny ? nx : ny;
-            for (unsigned long long i = 16; i < m; i++) {
-                uint32_t bx = px[i] | 0x20u, by = py[i] | 0x20u;
-                if (bx != by) return bx < by;
-            }
-            return nx < ny;
-        };
+        // bitonic network over N indices: one thread per compared pair
         for (uint32_t k = 2; k <= N; k <<= 1) {
             for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-                for (uint32_t i = threadIdx.x; i < N; i += BLOCK) {
-                    const uint32_t ixj = i ^ j;
-                    if (ixj > i) {
-                        const uint32_t x = sidx[i], y = sidx[ixj];
-                        const bool up = (i & k) == 0;
-                        if (up ? less(y, x) : less(x, y)) { sidx[i] = (uint16_t)y; sidx[ixj] = (uint16_t)x; }
-                    }
+                for (uint32_t t = threadIdx.x; t < N / 2; t += BLOCK) {
+                    const uint32_t i = 2 * t - (t & (j - 1)), ixj = i + j;
+                    const uint32_t x = sidx[i], y = sidx[ixj];
+                    const ulonglong2 kx = key_of(x), ky = key_of(y);
+                    const bool gt = kx.x != ky.x ? kx.x > ky.x : kx.y > ky.y;  // x after y
+                    if (gt == ((i & k) == 0)) { sidx[i] = (uint16_t)y; sidx[ixj] = (uint16_t)x; }
                 }
                 __syncthreads();
             }
+        }
+        // long words with equal count and prefix: order by their remaining
+        // bytes (insertion over each such run; runs are rare and short)
+        if (sh.nlong) {
+            if (threadIdx.x == 0) sh.ok = 0u;
+            __syncthreads();
+            for (uint32_t i = threadIdx.x; i + 1 < n; i += BLOCK) {
+                const ulonglong2 a0 = key_of(sidx[i]), a1 = key_of(sidx[i + 1]);
+                if ((a1.y >> 31) & 1u && a0.x == a1.x && (a0.y >> 32) == (a1.y >> 32)) sh.ok = 2u;
+            }
+            __syncthreads();
+            if (sh.ok == 2u && threadIdx.x == 0) {
+                for (uint32_t a = 1; a < n; a++) {
+                    const uint32_t x = sidx[a];
+                    const ulonglong2 kx = key_of(x);
+                    if (!((kx.y >> 31) & 1u)) continue;  // only long words move
+                    uint32_t b = a;
+                    while (b > 0) {
+                        const uint32_t y = sidx[b - 1];
+                        const ulonglong2 ky = key_of(y);
+                        if (ky.x != kx.x || (ky.y >> 32) != (kx.y >> 32) || !((ky.y >> 31) & 1u)) break;
+                        const uint32_t jx = x - C::C1, jy = y - C::C1;
+                        const uint8_t *px = reinterpret_cast<const uint8_t *>(laddr[jx]);
+                        const uint8_t *py = reinterpret_cast<const uint8_t *>(laddr[jy]);
+                        const unsigned long long nx = llen[jx], ny = llen[jy], m = nx < ny ? nx : ny;
+                        int c = 0;
+                        for (unsigned long long q = 16; q < m && !c; q++) {
+                            const uint32_t bx = px[q] | 0x20u, by = py[q] | 0x20u;
+                            c = bx < by ? -1 : (bx > by ? 1 : 0);
+                        }
+                        if (!(c < 0 || (c == 0 && nx < ny))) break;
+                        sidx[b] = (uint16_t)y;
+                        b--;
+                    }
+                    sidx[b] = (uint16_t)x;
+                }
+            }
+            __syncthreads();
         }
         // reserve output: entries, long words, arena bytes
         if (threadIdx.x == 0) {
@@ -396,10 +442,12 @@ __global__ void __launch_bounds__(BLOCK) k_docs(BatchArgs a) {
             const unsigned long long base = sh.base;
             for (uint32_t i = threadIdx.x; i < n; i += BLOCK) {
                 const uint32_t s = sidx[i];
-                const ulonglong2 k = key_of(s);
-                a.out_khi[base + i] = k.x;
-                a.out_klo[base + i] = k.y;
-                a.out_cnt[base + i] = cnt_of(s);
+                unsigned long long khi, klo;
+                uint32_t cnt;
+                doc_decompose(key_of(s), &khi, &klo, &cnt);
+                a.out_khi[base + i] = khi;
+                a.out_klo[base + i] = klo;
+                a.out_cnt[base + i] = cnt;
                 a.out_lref[base + i] = s < (uint32_t)C::C1 ? 0u : (uint32_t)(sh.lbase + lrank[s - C::C1] + 1);
             }
             if (warp == 0 && sh.nlong) {

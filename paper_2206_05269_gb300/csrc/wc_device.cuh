@@ -74,6 +74,29 @@ __device__ __forceinline__ uint4 load_key16(const uint8_t *win, uint32_t p, uint
     return k;
 }
 
+// 8 big-endian key bytes (0, or a letter) -> 8 five-bit codes (0 for
+// padding, 1..26 for a..z), the first byte in the highest code (40 bits):
+// integer order on codes is byte order on lowercase words.
+__device__ __forceinline__ unsigned long long pack5(unsigned long long be) {
+    unsigned long long r = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const uint32_t b = (uint32_t)(be >> (56 - 8 * i)) & 0xFFu;
+        r = (r << 5) | (b ? ((b | 0x20u) - 0x60u) & 31u : 0u);
+    }
+    return r;
+}
+// The inverse of pack5: 40 bits of codes -> 8 big-endian lowercase bytes.
+__device__ __forceinline__ unsigned long long unpack5(unsigned long long c) {
+    unsigned long long r = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const uint32_t v = (uint32_t)(c >> (35 - 5 * i)) & 31u;
+        r = (r << 8) | (v ? v + 0x60u : 0u);
+    }
+    return r;
+}
+
 __device__ __forceinline__ bool key_eq(uint4 a, uint4 b) {
     return ((a.x ^ b.x) | (a.y ^ b.y) | (a.z ^ b.z) | (a.w ^ b.w)) == 0u;
 }

@@ -191,18 +191,6 @@ __device__ __forceinline__ uint32_t sort_digit(const SortScratch &s, uint32_t id
     return (uint32_t)(~s.cnt[idx] >> (8 * (p - kSortKeyPasses))) & 0xFFu;
 }
 
-// 8 big-endian key bytes (0, or a lowercase letter) -> 8 five-bit codes, the
-// first byte in the highest code (40 bits).
-__device__ __forceinline__ unsigned long long pack5(unsigned long long be) {
-    unsigned long long r = 0;
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-        const uint32_t b = (uint32_t)(be >> (56 - 8 * i)) & 0xFFu;
-        r = (r << 5) | (b ? ((b | 0x20u) - 0x60u) & 31u : 0u);
-    }
-    return r;
-}
-
 // Packs the prefix keys, and takes the histograms of all digit positions
 // (for skipping constant digits) and the identity permutation.
 __global__ void k_hist_all(SortScratch s, const unsigned long long *meta, int passes) {
