@@ -104,6 +104,8 @@ struct DocCfg {
                                    (size_t)C1 * 16 + (size_t)C1 * 4 + (size_t)C1 * 4 +  // keys, counts, tags
                                    (size_t)LCAP * (8 + 8 + 4 + 4 + 16) + 16 + 64;
     static_assert((size_t)WINB + (size_t)W * TOKCAP * 4 >= (size_t)C1 * 2, "sort buffer must fit");
+    // blocks per SM that the shared memory allows: the register budget follows
+    static constexpr int MINB = (int)((227u * 1024u) / SMEM) < 1 ? 1 : ((int)((227u * 1024u) / SMEM) > 8 ? 8 : (int)((227u * 1024u) / SMEM));
     static_assert(C1 <= 32768, "16-bit sort indices");
 };
 
@@ -119,7 +121,7 @@ struct DocShared {  // per-block scalars
 };
 
 template <int BLOCK, int LOGC1>
-__global__ void __launch_bounds__(BLOCK) k_docs(BatchArgs a) {
+__global__ void __launch_bounds__(BLOCK, (DocCfg<BLOCK, LOGC1>::MINB)) k_docs(BatchArgs a) {
     using C = DocCfg<BLOCK, LOGC1>;
     extern __shared__ __align__(16) uint8_t smem[];
     uint8_t *win = smem;
@@ -170,18 +172,34 @@ __global__ void __launch_bounds__(BLOCK) k_docs(BatchArgs a) {
             }
         };
 
+        // The window of the next chunk is loaded one chunk ahead: each thread
+        // keeps its (at most two) 16-byte pieces in registers while the
+        // current chunk is processed, and masks the document's edges when
+        // it stores them.
+        static_assert(C::WINB / 16 <= 2 * BLOCK, "two window pieces per thread");
+        const int t1 = threadIdx.x + BLOCK;
+        auto fetch = [&](uintptr_t w0, uint4 &v0, uint4 &v1) {
+            const uintptr_t a0 = w0 + 16 * (uintptr_t)threadIdx.x, a1 = w0 + 16 * (uintptr_t)t1;
+            v0 = v1 = make_uint4(0x20202020u, 0x20202020u, 0x20202020u, 0x20202020u);
+            if (a0 < ve && a0 + 16 > vb) v0 = ld_stream16(reinterpret_cast<const void *>(a0));
+            if (t1 < C::WINB / 16 && a1 < ve && a1 + 16 > vb) v1 = ld_stream16(reinterpret_cast<const void *>(a1));
+        };
+        auto stage = [&](uintptr_t w0, uint4 v0, uint4 v1) {
+            const uintptr_t a0 = w0 + 16 * (uintptr_t)threadIdx.x, a1 = w0 + 16 * (uintptr_t)t1;
+            if (a0 < ve && a0 + 16 > vb && (a0 < vb || a0 + 16 > ve)) v0 = mask_outside_doc(v0, a0, vb, ve);
+            *reinterpret_cast<uint4 *>(win + 16 * threadIdx.x) = v0;
+            if (t1 < C::WINB / 16) {
+                if (a1 < ve && a1 + 16 > vb && (a1 < vb || a1 + 16 > ve)) v1 = mask_outside_doc(v1, a1, vb, ve);
+                *reinterpret_cast<uint4 *>(win + 16 * t1) = v1;
+            }
+        };
+        uint4 nx0, nx1;
+        fetch((own_lo & ~(uintptr_t)15) - 16, nx0, nx1);
         for (uintptr_t cs = own_lo & ~(uintptr_t)15; cs < own_hi; cs += C::CH) {
             const uintptr_t w0 = cs - 16;
-            for (int t = threadIdx.x; t < C::WINB / 16; t += BLOCK) {
-                uintptr_t ad = w0 + 16 * (uintptr_t)t;
-                uint4 v = make_uint4(0x20202020u, 0x20202020u, 0x20202020u, 0x20202020u);
-                if (ad < ve && ad + 16 > vb) {
-                    v = ld_stream16(reinterpret_cast<const void *>(ad));
-                    if (ad < vb || ad + 16 > ve) v = mask_outside_doc(v, ad, vb, ve);
-                }
-                *reinterpret_cast<uint4 *>(win + 16 * t) = v;
-            }
+            stage(w0, nx0, nx1);
             __syncthreads();
+            if (cs + C::CH < own_hi) fetch(w0 + C::CH, nx0, nx1);
             // ---- this warp's strip
             const int sbase = 16 + 512 * warp;
             const uint32_t prevL = is_letter(win[sbase - 1]) ? 1u : 0u;
@@ -335,26 +353,33 @@ __global__ void __launch_bounds__(BLOCK) k_docs(BatchArgs a) {
         // desc, word asc) except among long words sharing a prefix, which a
         // fix-up orders below.  The sort then moves 16-bit indices and
         // compares composites.
-        for (int i = threadIdx.x; i < C::C1; i += BLOCK)
-            if (stag[i] > 1u) {
-                const uint4 k = skey[i];
-                reinterpret_cast<ulonglong2 *>(skey)[i] =
-                    doc_composite(be64b(k.x, k.y), be64b(k.z, k.w), scnt[i], false, 0u);
-            }
-        __syncthreads();
-        for (uint32_t j = threadIdx.x; j < nl; j += BLOCK) {
-            const uint8_t *p = reinterpret_cast<const uint8_t *>(laddr[j]);
-            lkey[j] = doc_composite(be_bytes16(p, 0), be_bytes16(p, 8), lcnt[j], true, j);
-        }
         if (threadIdx.x == 0) {
             sh.nent = 0;
             sh.nlong = 0;
             lkey[C::LCAP] = make_ulonglong2(~0ull, ~0ull);  // the padding entry sorts last
         }
         __syncthreads();
-        // index list of live entries (order is fixed by the sort below)
-        for (int i = threadIdx.x; i < C::C1; i += BLOCK)
-            if (stag[i] > 1u) sidx[atomicAdd(&sh.nent, 1u)] = (uint16_t)i;
+        // composites in place, and the index list of live entries (its order
+        // is fixed by the sort below): one shared atomic per warp and step
+        static_assert(C::C1 % BLOCK == 0, "whole steps over the shared table");
+        for (int i0 = 0; i0 < C::C1; i0 += BLOCK) {
+            const int i = i0 + threadIdx.x;
+            const bool live = stag[i] > 1u;
+            if (live) {
+                const uint4 k = skey[i];
+                reinterpret_cast<ulonglong2 *>(skey)[i] =
+                    doc_composite(be64b(k.x, k.y), be64b(k.z, k.w), scnt[i], false, 0u);
+            }
+            const uint32_t m = __ballot_sync(kFull, live);
+            uint32_t base = 0;
+            if (lane == 0 && m) base = atomicAdd(&sh.nent, (uint32_t)__popc(m));
+            base = __shfl_sync(kFull, base, 0);
+            if (live) sidx[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)i;
+        }
+        for (uint32_t j = threadIdx.x; j < nl; j += BLOCK) {
+            const uint8_t *p = reinterpret_cast<const uint8_t *>(laddr[j]);
+            lkey[j] = doc_composite(be_bytes16(p, 0), be_bytes16(p, 8), lcnt[j], true, j);
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             uint32_t r = 0;

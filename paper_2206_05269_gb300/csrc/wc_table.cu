@@ -6,11 +6,11 @@
 // into the table's own byte arena, then an LSD radix sort over a permutation:
 // 10 byte-digits of the 16-letter prefix packed 5 bits a letter (0 for
 // padding, 1..26 for a..z, so integer order is lexicographic order and a
-// proper prefix sorts first), a fix-up that orders long words sharing a
-// 16-letter prefix by their remaining bytes, and up to 8 digits of the
-// complemented count (count descending).  Every pass is stable, so the final
-// order is (count desc, word asc).  Digits that are equal for every element
-// are skipped, detected on the device from one histogram pass.
+// proper prefix sorts first) and up to 8 digits of the complemented count
+// (count descending), then a fix-up that orders long words sharing count and
+// 16-letter prefix by their remaining bytes.  Every pass is stable, so the
+// final order is (count desc, word asc).  Digits that are equal for every
+// element are skipped, detected on the device from one histogram pass.
 #include "wc_internal.h"
 
 namespace wc {
@@ -376,30 +376,34 @@ __device__ __forceinline__ bool tail_less(const LongView &v, uint32_t a, uint32_
     return la < lb;
 }
 
-// Orders runs of equal 16-byte prefix that hold a long word by full bytes
-// (only a long word can share its prefix with another word).  The first long
-// entry of such a run sorts it by insertion; runs without a long entry (in a
-// per-document sort: the same short word in many documents) are not touched.
-__global__ void k_fix_long(SortScratch s, LongView v, const unsigned long long *meta) {
+// After the last pass, entries are in (document, count desc, 16-letter prefix
+// asc) order; only a long word can share its prefix with another word, so
+// the runs left to order are the entries of one document with equal count
+// and prefix that hold a long word, ordered here by their full bytes.  The
+// first long entry of such a run sorts it by insertion; the runs are tiny.
+__device__ __forceinline__ bool same_run(const SortScratch &s, uint32_t a, uint32_t b, bool seg) {
+    return s.khi[a] == s.khi[b] && s.klo[a] == s.klo[b] && s.cnt[a] == s.cnt[b] && (!seg || s.doc[a] == s.doc[b]);
+}
+__global__ void k_fix_long(SortScratch s, LongView v, const unsigned long long *meta, int passes) {
     const unsigned long long n = meta[0];
     if (meta[1] == 0) return;
-    uint32_t *perm = s.perm_buf(s.cur[kSortKeyPasses]);
+    const bool seg = passes > kPasses;
+    uint32_t *perm = s.perm_buf(s.cur[passes]);
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t e = perm[i];
         if (v.lref[e] == 0u) continue;
-        const unsigned long long kh = s.khi[e], kl = s.klo[e];
         unsigned long long lo = i;
         bool leader = true;
         while (lo > 0) {
             const uint32_t q = perm[lo - 1];
-            if (s.khi[q] != kh || s.klo[q] != kl) break;
+            if (!same_run(s, q, e, seg)) break;
             if (v.lref[q] != 0u) { leader = false; break; }  // an earlier long entry sorts the run
             lo--;
         }
         if (!leader) continue;
         unsigned long long j = i + 1;
-        while (j < n && s.khi[perm[j]] == kh && s.klo[perm[j]] == kl) j++;
+        while (j < n && same_run(s, perm[j], e, seg)) j++;
         if (j - lo < 2) continue;
         const unsigned long long i0 = lo;
         for (unsigned long long a = i0 + 1; a < j; a++) {
@@ -464,11 +468,11 @@ cudaError_t sort_entries(SortScratch &ss, const unsigned long long *meta, const 
     k_hist_all<<<grid_for(cap, 256, sms * 2), 256, 0, st>>>(ss, meta, passes);
     const int ntiles = (int)((cap + kSortTile - 1) / kSortTile);
     for (int p = 0; p < passes; p++) {
-        if (p == kSortKeyPasses) k_fix_long<<<grid_for(cap, 256, sms * 4), 256, 0, st>>>(ss, v, meta);
         k_pass_count<<<ntiles, kSortThreads, 0, st>>>(ss, p, meta);
         k_pass_scan<<<256, 256, 0, st>>>(ss, p, meta);
         k_pass_scatter<<<ntiles, kSortThreads, 0, st>>>(ss, p, meta);
     }
+    k_fix_long<<<grid_for(cap, 256, sms * 4), 256, 0, st>>>(ss, v, meta, passes);
     return cudaGetLastError();
 }
 int sort_entries_launches(int passes) { return 1 + 1 + 3 * passes; }
