@@ -44,6 +44,28 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks: a job step lasts as long as its slowest
+    rank's.  dist is torch.distributed (initialised) or None for one process."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, ms_step: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's step."""
+    return units_per_rank * world / (ms_step * 1e-3)
+
+
+def replica_seed(rank: int) -> int:
+    """Each replica counts its own corpus (independent problems, no exchange)."""
+    import corpus
+    return corpus.RECIPES["large"].seed + rank
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -185,7 +207,7 @@ def run_gpu(args, rank, world, local):
             dist.barrier()
         torch.cuda.synchronize()
 
-    c = corpus.generate("large", seed=corpus.RECIPES["large"].seed + rank, size_a=args.bytes)
+    c = corpus.generate("large", seed=replica_seed(rank), size_a=args.bytes)
     nbytes = c.nbytes
     host = torch.from_numpy(c.text).pin_memory()
     text = host.to(f"cuda:{local}", non_blocking=False)
@@ -224,12 +246,8 @@ def run_gpu(args, rank, world, local):
     if any(st != wc.WC_OK for st in done):
         raise RuntimeError("a timed step failed")
     del tables
-    ms_step = elapsed / args.steps
-    if dist:
-        tt = torch.tensor([ms_step], device=f"cuda:{local}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_step = float(tt.item())
-    value = nbytes * world / (ms_step * 1e-3) / 1e9
+    ms_step = max_over_ranks(elapsed / args.steps, dist, f"cuda:{local}")
+    value = job_rate(nbytes, world, ms_step) / 1e9
 
     # end to end through the C ABI: host text -> device, count, table -> host
     e2e_steps = max(3, min(args.steps, 10))

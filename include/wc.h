@@ -79,6 +79,9 @@ enum { WC_TABLE_DOC = 0, WC_TABLE_CLASS = 1, WC_TABLE_GLOBAL = 2 };
 /* Creates a context on cfg->device (NULL cfg = defaults: device 0, no
  * budget, 64-bit counts, no autotune).  *out is set on WC_OK only. */
 wc_status wc_create(const wc_config *cfg, wc_ctx **out);
+/* Destroys the context and its memory pool.  Free every table, batch and plan
+ * made with it first: they hold the context, and freeing one after its
+ * context is gone is undefined. */
 void wc_destroy(wc_ctx *ctx);
 
 /* Counts the words of one document d_text[0, nbytes) into a new table with

@@ -253,6 +253,7 @@ static wc_status status_from_bits(uint32_t bits) {
     if (bits & (ST_TABLE_FULL | ST_LONG_FULL | ST_ARENA_FULL | ST_OUT_FULL)) return WC_ERR_CAPACITY;
     if (bits & ST_TIMEOUT) return WC_ERR_TIMEOUT;
     if (bits & ST_TOO_LONG) return WC_ERR_UNSUPPORTED;
+    if (bits & ST_BAD_CLASS) return WC_ERR_INVALID_ARG;
     return WC_OK;
 }
 

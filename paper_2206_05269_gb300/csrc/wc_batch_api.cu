@@ -518,7 +518,12 @@ __global__ void k_batch_tables(BatchArgs a, const uint32_t *cls, const GTable *g
     const uint32_t d = blockIdx.x;
     const unsigned long long s = a.doc_start[d];
     const uint32_t n = a.doc_n[d];
-    const GTable *gc = nclasses ? &gt[cls[d]] : nullptr;
+    const uint32_t c = nclasses ? cls[d] : 0u;
+    const GTable *gc = nclasses && c < nclasses ? &gt[c] : nullptr;
+    if (nclasses && c >= nclasses) {  // reported through the global table's status
+        if (threadIdx.x == 0) atomicOr(gg.status, ST_BAD_CLASS);
+        return;
+    }
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
         const unsigned long long j = s + i;
         const unsigned long long c = a.out_cnt[j];
@@ -540,47 +545,106 @@ __global__ void k_batch_tables(BatchArgs a, const uint32_t *cls, const GTable *g
     }
 }
 
-static wc_status build_tables(wc_batch *b) {
-    if (b->tables_built) return WC_OK;
-    wc_status st = batch_sync(b);
-    if (st != WC_OK) return st;
+// Class and global tables: every document's rows are added (k_batch_tables)
+// into one hash table per class and one for all documents, each then
+// compacted and sorted.  A table's distinct words lie between the largest
+// of its documents' table sizes and their sum (the exact bound); tables are
+// first sized for max(2 x the largest, a quarter of the sum) and, if one
+// overflows, all are built again at the bound.
+static wc_status build_tables_at(wc_batch *b, const std::vector<uint64_t> &est, std::vector<wc_table *> &tabs,
+                                 bool *overflow) {
     wc_ctx *ctx = b->ctx;
     cudaStream_t s = b->stream;
-    const uint64_t n = std::max<uint64_t>(b->entries, 1);
-    CapPlan plan;
-    plan.cap8 = pow2_ge(std::max<uint64_t>(1024, 2 * n));
-    plan.cap16 = plan.cap8;
-    plan.caplong = pow2_ge(std::max<uint64_t>(256, 2 * std::min<uint64_t>(n, b->args.lcap)));
-    plan.arena = std::max<uint64_t>(4096, b->args.arena_cap);
-    // one scratch (tables + sort) per class and one for the global table
-    std::vector<CountScratch> cls(b->nclasses);
-    for (uint32_t c = 0; c < b->nclasses; c++)
-        if ((st = scratch_create(ctx, plan, false, s, cls[c])) != WC_OK) return st;
-    if ((st = scratch_create(ctx, plan, false, s, b->gscratch)) != WC_OK) return st;
-    std::vector<wc_table *> tabs(b->nclasses + 1, nullptr);
-    for (uint32_t c = 0; c <= b->nclasses; c++) {
-        if ((st = table_create(ctx, b->gscratch.entries(), plan.caplong, plan.arena,
-                               c < b->nclasses ? 32 : ctx->count_bits, s, &tabs[c])) != WC_OK)
-            return st;
+    const uint32_t nt = b->nclasses + 1;  // class tables, then the global table
+    wc_status st = WC_OK;
+    std::vector<CountScratch> scr(nt);
+    tabs.assign(nt, nullptr);
+    auto cleanup = [&](uint32_t upto) {
+        for (uint32_t c = 0; c < upto; c++)
+            if (c < b->nclasses && scr[c].mem) ctx->release(scr[c].mem, scr[c].bytes, s);
+    };
+    for (uint32_t c = 0; c < nt && st == WC_OK; c++) {
+        const uint64_t d = std::max<uint64_t>(est[c], 256);
+        CapPlan plan;
+        plan.cap8 = pow2_ge(std::max<uint64_t>(1024, 2 * d));
+        plan.cap16 = pow2_ge(std::max<uint64_t>(1024, d + d / 4));
+        plan.caplong = pow2_ge(std::max<uint64_t>(256, 2 * std::min<uint64_t>(d, b->args.lcap)));
+        plan.arena = std::max<uint64_t>(4096, b->args.arena_cap);
+        CountScratch &cs = c < b->nclasses ? scr[c] : b->gscratch;
+        if ((st = scratch_create(ctx, plan, false, s, cs)) != WC_OK) break;
+        if ((st = table_create(ctx, cs.entries(), plan.caplong, plan.arena, c < b->nclasses ? 32 : ctx->count_bits,
+                               s, &tabs[c])) != WC_OK)
+            break;
         tabs[c]->owner = b;
     }
+    if (st != WC_OK) {
+        cleanup(nt);
+        for (auto *t : tabs) free_owned_table(t);
+        tabs.clear();
+        return st;
+    }
     std::vector<GTable> g(std::max<uint32_t>(b->nclasses, 1));
-    for (uint32_t c = 0; c < b->nclasses; c++) g[c] = cls[c].gtable(tabs[c]->dt.d_status);
+    for (uint32_t c = 0; c < b->nclasses; c++) g[c] = scr[c].gtable(tabs[c]->dt.d_status);
     void *dg = nullptr;
-    if ((st = ctx->alloc(&dg, sizeof(GTable) * g.size(), s)) != WC_OK) return st;
+    if ((st = ctx->alloc(&dg, sizeof(GTable) * g.size(), s)) != WC_OK) {
+        cleanup(nt);
+        for (auto *t : tabs) free_owned_table(t);
+        tabs.clear();
+        return st;
+    }
     cudaMemcpyAsync(dg, g.data(), sizeof(GTable) * g.size(), cudaMemcpyHostToDevice, s);
     const GTable gg = b->gscratch.gtable(tabs[b->nclasses]->dt.d_status);
     if (b->ndocs) k_batch_tables<<<b->ndocs, 128, 0, s>>>(b->args, b->d_class, static_cast<GTable *>(dg), b->nclasses, gg);
     cudaError_t e = cudaGetLastError();
     for (uint32_t c = 0; c < b->nclasses && e == cudaSuccess; c++)
-        e = finish_table(g[c], cls[c].gcap8, cls[c].gcap, cls[c].glcap, cls[c].ss, tabs[c]->dt, s);
+        e = finish_table(g[c], scr[c].gcap8, scr[c].gcap, scr[c].glcap, scr[c].ss, tabs[c]->dt, s);
     if (e == cudaSuccess)
         e = finish_table(gg, b->gscratch.gcap8, b->gscratch.gcap, b->gscratch.glcap, b->gscratch.ss,
                          tabs[b->nclasses]->dt, s);
-    for (uint32_t c = 0; c < b->nclasses; c++) ctx->release(cls[c].mem, cls[c].bytes, s);
+    ctx->launches += 1 + (uint64_t)nt * finish_table_launches();
+    cleanup(nt);
     ctx->release(dg, sizeof(GTable) * g.size(), s);
     for (auto *t : tabs) table_mark_done(t, s);
     if (e != cudaSuccess) return ctx->cuda_fail(e, "class/global tables");
+    *overflow = false;
+    for (auto *t : tabs)
+        if (table_sync(t) == WC_ERR_CAPACITY) *overflow = true;
+    return WC_OK;
+}
+
+static wc_status build_tables(wc_batch *b) {
+    if (b->tables_built) return WC_OK;
+    wc_status st = batch_sync(b);
+    if (st != WC_OK) return st;
+    wc_ctx *ctx = b->ctx;
+    const uint32_t nd = b->ndocs, nt = b->nclasses + 1;
+    // the documents' table sizes (and classes), for the capacities
+    std::vector<uint32_t> dn(nd), dc(nd, 0u);
+    cudaError_t e = cudaSuccess;
+    if (nd) e = cudaMemcpy(dn.data(), b->args.doc_n, 4ull * nd, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && nd && b->nclasses) e = cudaMemcpy(dc.data(), b->d_class, 4ull * nd, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "class/global table sizes");
+    std::vector<uint64_t> sum(nt, 0), mx(nt, 0), est(nt);
+    for (uint32_t d = 0; d < nd; d++) {
+        const uint32_t c = b->nclasses ? dc[d] : 0u;
+        if (b->nclasses && c >= b->nclasses) return ctx->fail(WC_ERR_INVALID_ARG, "a class id is not below nclasses");
+        if (b->nclasses) {
+            sum[c] += dn[d];
+            mx[c] = std::max<uint64_t>(mx[c], dn[d]);
+        }
+        sum[b->nclasses] += dn[d];
+        mx[b->nclasses] = std::max<uint64_t>(mx[b->nclasses], dn[d]);
+    }
+    for (uint32_t t = 0; t < nt; t++) est[t] = std::min(sum[t], std::max(2 * mx[t], sum[t] / 4));
+    std::vector<wc_table *> tabs;
+    bool overflow = false;
+    if ((st = build_tables_at(b, est, tabs, &overflow)) != WC_OK) return st;
+    if (overflow) {  // again at the exact bound: the sum of the documents' sizes
+        for (auto *t : tabs) free_owned_table(t);
+        if (b->gscratch.mem) { ctx->release(b->gscratch.mem, b->gscratch.bytes, b->stream); b->gscratch.mem = nullptr; }
+        if ((st = build_tables_at(b, sum, tabs, &overflow)) != WC_OK) return st;
+        if (overflow) return ctx->fail(WC_ERR_INTERNAL, "class/global tables overflowed at their exact bound");
+    }
     b->class_tables.assign(tabs.begin(), tabs.begin() + b->nclasses);
     b->global = tabs[b->nclasses];
     b->tables_built = true;

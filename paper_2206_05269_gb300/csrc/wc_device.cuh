@@ -28,6 +28,7 @@ enum : uint32_t {
     ST_TIMEOUT = 8u,      // a bounded wait gave up
     ST_TOO_LONG = 16u,    // a word or position beyond the documented limits
     ST_OUT_FULL = 32u,    // a per-document output region overflowed
+    ST_BAD_CLASS = 64u,   // a document's class id is not below the class count
 };
 
 // ---------------------------------------------------------------- bytes

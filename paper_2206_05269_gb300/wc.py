@@ -12,6 +12,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -318,11 +319,18 @@ def _stream_handle(stream) -> int:
 
 
 class Table:
-    """Owns a wc_table handle (or borrows one from a batch)."""
+    """Owns a wc_table handle (or borrows one from a batch, which it keeps
+    alive).  An owned table registers with its Counter, which frees it before
+    destroying the context: a table must not outlive its context, and Python
+    may collect an object (one caught in a reference cycle, say) only after
+    its Counter was closed."""
 
-    def __init__(self, handle, owned: bool = True):
+    def __init__(self, handle, owned: bool = True, counter=None, owner=None):
         self.handle = handle
         self.owned = owned
+        self._owner = owner  # the batch a borrowed table reads from
+        if owned and counter is not None:
+            counter._track(self)
 
     def __del__(self):
         self.free()
@@ -347,10 +355,16 @@ class Table:
 
 
 class Batch:
-    def __init__(self, handle, ndocs: int = 0, owned: bool = True):
+    """Owns a wc_batch handle (or borrows a plan's, keeping the plan alive);
+    an owned batch registers with its Counter like an owned Table."""
+
+    def __init__(self, handle, ndocs: int = 0, owned: bool = True, counter=None, owner=None):
         self.handle = handle
         self.ndocs = ndocs
         self.owned = owned
+        self._owner = owner
+        if owned and counter is not None:
+            counter._track(self)
 
     def status(self) -> int:
         return wc_batch_status(self.handle)
@@ -367,19 +381,22 @@ class Batch:
             out.append([(w[o[i]:o[i + 1]].tobytes(), int(c[i])) for i in range(s0, s0 + n)])
         return out
 
-    def __del__(self):
+    def free(self):
         if getattr(self, "handle", None) and self.owned:
             wc_batch_free(self.handle)
         self.handle = None
 
+    def __del__(self):
+        self.free()
+
     def table(self, kind: int, idx: int = 0) -> Table:
-        return Table(wc_batch_table(self.handle, kind, idx), owned=False)
+        return Table(wc_batch_table(self.handle, kind, idx), owned=False, owner=self)
 
     def topk(self, k: int):
         """Every document's top-k rows in one table (borrowed from the batch),
         with each document's first row and row count."""
         h, first, n = wc_batch_topk(self.handle, self.ndocs, k)
-        return Table(h, owned=False), first, n
+        return Table(h, owned=False, owner=self), first, n
 
 
 class Counter:
@@ -387,9 +404,16 @@ class Counter:
 
     def __init__(self, device: int = 0, budget: int = 0, count_bits: int = 64, autotune: bool = False,
                  tune_cache_path: str | None = None):
+        self._live = weakref.WeakSet()  # owned tables, batches and plans of this context
         self.ctx = wc_create(device, budget, count_bits, int(autotune), tune_cache_path)
 
+    def _track(self, obj) -> None:
+        self._live.add(obj)
+
     def close(self):
+        """Frees every table, batch and plan still alive, then the context."""
+        for obj in list(getattr(self, "_live", ())):
+            obj.free()
         if getattr(self, "ctx", None):
             wc_destroy(self.ctx)
             self.ctx = None
@@ -400,7 +424,7 @@ class Counter:
     def count(self, text, stream=None, opts=None) -> Table:
         """Counts one document held in a uint8 CUDA tensor (asynchronous)."""
         s = _stream_handle(stream)
-        return Table(wc_count_ex(self.ctx, text.data_ptr(), text.numel(), opts, s))
+        return Table(wc_count_ex(self.ctx, text.data_ptr(), text.numel(), opts, s), counter=self)
 
     def count_checked(self, text, stream=None, opts=None, retries: int = 4) -> Table:
         """count() that waits for the result and recounts with 4x capacities on
@@ -422,16 +446,16 @@ class Counter:
         s = _stream_handle(stream)
         return Batch(wc_count_batched(self.ctx, text.data_ptr(), offsets.data_ptr(), h_offsets,
                                       int(h_offsets.size - 1), classes.data_ptr() if classes is not None else None,
-                                      nclasses, s), int(h_offsets.size - 1))
+                                      nclasses, s), int(h_offsets.size - 1), counter=self)
 
     def plan(self, h_offsets, nclasses: int = 0, stream=None) -> "Plan":
         return Plan(self, h_offsets, nclasses, stream)
 
     def merge(self, tables: list[Table], stream=None) -> Table:
-        return Table(wc_merge(self.ctx, [t.handle for t in tables], _stream_handle(stream)))
+        return Table(wc_merge(self.ctx, [t.handle for t in tables], _stream_handle(stream)), counter=self)
 
     def topk(self, table: Table, k: int, stream=None) -> Table:
-        return Table(wc_topk(self.ctx, table.handle, k, _stream_handle(stream)))
+        return Table(wc_topk(self.ctx, table.handle, k, _stream_handle(stream)), counter=self)
 
 
 class Plan:
@@ -441,13 +465,17 @@ class Plan:
         self.counter = counter
         self.ndocs = int(np.asarray(h_offsets).size - 1)
         self.handle = wc_plan_create(counter.ctx, h_offsets, nclasses, _stream_handle(stream))
+        counter._track(self)
 
     def run(self, text, offsets, classes=None, stream=None) -> Batch:
         h = wc_plan_run(self.counter.ctx, self.handle, text.data_ptr(), offsets.data_ptr(),
                         classes.data_ptr() if classes is not None else None, _stream_handle(stream))
-        return Batch(h, self.ndocs, owned=False)
+        return Batch(h, self.ndocs, owned=False, owner=self)
 
-    def __del__(self):
+    def free(self):
         if getattr(self, "handle", None):
             wc_plan_free(self.handle)
         self.handle = None
+
+    def __del__(self):
+        self.free()

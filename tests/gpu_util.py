@@ -10,8 +10,8 @@ def to_dev(data, offset: int = 0):
     buf = torch.empty(arr.size + offset + 16, dtype=torch.uint8, device="cuda:0")
     buf.fill_(ord("x"))  # letters around the slice must not leak into it
     t = buf[offset:offset + arr.size]
-    if arr.size:
-        t.copy_(torch.from_numpy(np.ascontiguousarray(arr)))
+    if arr.size:  # from a writable host copy (the bytes object's buffer is read-only)
+        t.copy_(torch.from_numpy(np.array(arr, dtype=np.uint8, copy=True)))
     return t
 
 

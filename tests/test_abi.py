@@ -39,3 +39,35 @@ def test_product_path_has_no_oracle_or_host_fallback():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "oracle/" not in text, f
+
+
+def test_counter_close_frees_what_is_still_alive():
+    """Objects a context made are freed by Counter.close() even when Python
+    still holds them (a reference cycle keeps an object until the cyclic
+    collector runs, possibly after its Counter was closed); freeing them
+    again later is a no-op.  Pure host logic, checked with stand-in handles."""
+    from paper_2206_05269_gb300 import wc
+
+    freed = []
+
+    class Fake:
+        def __init__(self, name):
+            self.name = name
+            self.handle = object()
+
+        def free(self):
+            if self.handle is not None:
+                freed.append(self.name)
+            self.handle = None
+
+    c = wc.Counter.__new__(wc.Counter)  # no library context here: only the bookkeeping
+    c._live = wc.weakref.WeakSet()
+    c.ctx = None
+    a, b = Fake("table"), Fake("batch")
+    c._track(a)
+    c._track(b)
+    c.close()
+    assert sorted(freed) == ["batch", "table"]
+    a.free()
+    b.free()
+    assert sorted(freed) == ["batch", "table"]

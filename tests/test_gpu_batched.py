@@ -154,3 +154,30 @@ def test_batch_topk_rows_are_each_documents_first_rows(ctr):
             s0, m = int(first[d]), int(n[d])
             got = [(w[o[i]:o[i + 1]].tobytes(), int(cnt[i])) for i in range(s0, s0 + m)]
             assert got == want, f"k={k} doc {d}"
+
+
+def test_class_id_out_of_range_is_an_error(ctr):
+    """A class id not below nclasses is rejected when the class tables are
+    built (WC_ERR_INVALID_ARG), not read past the class-table array."""
+    from paper_2206_05269_gb300 import wc
+    c = corpus.generate("tiny", ndocs=12)
+    classes = np.zeros(c.ndocs, dtype=np.uint32)
+    classes[5] = 3  # nclasses = 2
+    b, keep = run_batched(ctr, c.text, c.offsets, classes, 2)
+    assert b.status() == wc.WC_OK  # per-document tables do not depend on classes
+    with pytest.raises(wc.WcError) as ei:
+        b.table(wc.WC_TABLE_CLASS, 0)
+    assert ei.value.status == wc.WC_ERR_INVALID_ARG
+
+
+def test_class_tables_many_distinct_words(ctr):
+    """Class and global tables of documents with little vocabulary overlap
+    (the first-size estimate is exceeded and the tables are rebuilt at the
+    exact bound) still equal the oracle."""
+    from paper_2206_05269_gb300 import wc
+    c = corpus.generate("classes", ndocs=40, vocab_size=400000, zipf_s=0.6, seed=123)
+    r = oracle.count(c.text, c.offsets, c.classes, c.nclasses)
+    b, keep = run_batched(ctr, c.text, c.offsets, c.classes, c.nclasses)
+    assert_same(b.table(wc.WC_TABLE_GLOBAL).export(), r.glob(), "global")
+    for k in range(c.nclasses):
+        assert_same(b.table(wc.WC_TABLE_CLASS, k).export(), r.cls(k), f"class {k}")
