@@ -239,15 +239,13 @@ struct Counter2 {
         if (have) {
             const uint32_t p = e >> 5, len = e & 31u;
             tail = true;
-            if (len <= 8) {
-                const unsigned long long key = load_key8(win, p, len);
-                if (nslots) {
-                    hs = head_find(hkey, hfp, key, a.nb);
-                    tail = hs < 0;
-                }
-                tk = make_uint4((uint32_t)key, (uint32_t)(key >> 32), 0u, 0u);
-            } else {
-                tk = load_key16(win, p, len);
+            // one key load for every length (no divergent paths): a word of
+            // <= 8 letters has a zero upper half, and its lower half is its
+            // 8-byte key
+            tk = load_key16(win, p, len);
+            if (len <= 8 && nslots) {
+                hs = head_find(hkey, hfp, ((unsigned long long)tk.y << 32) | tk.x, a.nb);
+                tail = hs < 0;
             }
         }
         return hs;
