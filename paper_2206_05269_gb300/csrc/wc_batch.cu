@@ -58,7 +58,7 @@ __device__ __forceinline__ void doc_insert_key(const GTable &g, uint32_t d, uint
 }
 __device__ __forceinline__ void doc_insert_long(const GTable &g, uint32_t d, const uint8_t *w, unsigned long long len,
                                                 unsigned long long add, const uint8_t *begin, const uint8_t *end) {
-    long_insert2(g, w, len, long_doc_hash(long_hash_run(w, len), d), add, begin, end);
+    long_insert2(g, w, len, long_doc_hash(long_hash(w, len), d), add, begin, end);
 }
 
 __device__ __forceinline__ unsigned long long be64b(uint32_t x, uint32_t y) {

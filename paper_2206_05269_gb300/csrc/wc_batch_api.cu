@@ -779,7 +779,7 @@ wc_status wc_batch_table(const wc_batch *cb, int kind, uint32_t idx, const wc_ta
 // the global hash tables, read only).
 __device__ unsigned long long lookup_count(const GTable &g, uint4 k, const uint8_t *lw, unsigned long long llen) {
     if (lw) {
-        const unsigned long long h = long_hash_serial(lw, llen);
+        const unsigned long long h = long_hash(lw, llen);
         unsigned long long s = h & g.lmask;
         for (int probe = 0; probe < kGlobalProbeLimit; probe++) {
             const LSlot &sl = g.lslots[s];

@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_count2(Count2Args a) {
                 len = 17;
                 while (w + len < end && is_letter(w[len])) len++;
             }
-            long_insert2(a.g, w, len, long_hash_run(w, len), 1ull, begin, end);
+            long_insert2(a.g, w, len, long_hash(w, len), 1ull, begin, end);
         }
         __syncwarp();
     };

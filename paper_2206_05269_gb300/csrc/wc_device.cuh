@@ -118,11 +118,6 @@ __device__ __forceinline__ uint64_t hash_key(uint4 k) {
     return x;
 }
 
-// Hash of a long word: h = fmix64(sum_i (b_i + 1) * P^i + len * C) over the
-// lowercased bytes b_i, mod 2^64.  A sum of independent terms, so a warp can
-// compute it in parallel (long_hash_warp) and one thread sequentially
-// (long_hash_serial) with the same result.
-constexpr unsigned long long kLongP = 0x100000001B3ull * 2 + 1;
 __device__ __forceinline__ unsigned long long fmix64(unsigned long long x) {
     x ^= x >> 33;
     x *= 0xFF51AFD7ED558CCDull;
@@ -130,30 +125,6 @@ __device__ __forceinline__ unsigned long long fmix64(unsigned long long x) {
     x *= 0xC4CEB9FE1A85EC53ull;
     x ^= x >> 33;
     return x;
-}
-__device__ __forceinline__ unsigned long long powP(unsigned long long e) {
-    unsigned long long r = 1, b = kLongP;
-    while (e) { if (e & 1) r *= b; b *= b; e >>= 1; }
-    return r;
-}
-__device__ inline unsigned long long long_hash_serial(const uint8_t *w, unsigned long long len) {
-    unsigned long long acc = 0, pw = 1;
-    for (unsigned long long i = 0; i < len; i++) {
-        acc += (unsigned long long)((w[i] | 0x20u) + 1u) * pw;
-        pw *= kLongP;
-    }
-    return fmix64(acc + len * 0x9E3779B97F4A7C15ull);
-}
-// Every lane of the warp must call it with the same (w, len).
-__device__ inline unsigned long long long_hash_warp(const uint8_t *w, unsigned long long len) {
-    const int lane = threadIdx.x & 31;
-    unsigned long long pw = powP((unsigned long long)lane), step = powP(32), acc = 0;
-    for (unsigned long long i = lane; i < len; i += 32) {
-        acc += (unsigned long long)((w[i] | 0x20u) + 1u) * pw;
-        pw *= step;
-    }
-    for (int d = 16; d; d >>= 1) acc += __shfl_xor_sync(kFull, acc, d);
-    return fmix64(acc + len * 0x9E3779B97F4A7C15ull);
 }
 
 // 16 lowercased bytes of the letter run at p[0, n), zero padded (n <= 0: all
@@ -179,29 +150,18 @@ __device__ __forceinline__ uint4 load_run16(const uint8_t *p, long long n) {
     k.w = (__funnelshift_r(v3, v4, sh) | 0x20202020u) & byte_keep_mask(m - 12);
     return k;
 }
-// acc = acc * P + (b + 1) over the first n bytes of k, last byte first (Horner).
-__device__ __forceinline__ unsigned long long horner16(unsigned long long acc, uint4 k, int n) {
-    const uint32_t q[4] = {k.x, k.y, k.z, k.w};
-#pragma unroll
-    for (int j = 15; j >= 0; j--)
-        if (j < n) acc = acc * kLongP + (unsigned long long)(((q[j >> 2] >> (8 * (j & 3))) & 0xFFu) + 1u);
-    return acc;
-}
-// The long-word hash (same value as long_hash_serial) of the letter run
-// w[0, len), len >= 1, from 16-byte pieces read with independent loads.
-__device__ inline unsigned long long long_hash_run(const uint8_t *w, unsigned long long len) {
-    long long off = (long long)((len - 1) / 16) * 16;  // the last piece
-    unsigned long long acc = 0;
-    if (off == 16) {  // 17..32 letters: both pieces loaded together
-        const uint4 k1 = load_run16(w + 16, (long long)len - 16), k0 = load_run16(w, 16);
-        acc = horner16(horner16(0ull, k1, (int)len - 16), k0, 16);
-    } else {
-        for (; off >= 0; off -= 16) {
-            const long long n = (long long)len - off;
-            acc = horner16(acc, load_run16(w + off, n), n > 16 ? 16 : (int)n);
-        }
-    }
-    return fmix64(acc + len * 0x9E3779B97F4A7C15ull);
+// Hash of a long word (17+ letters): its first and last 16 lowercased bytes
+// and its length, mixed by MurmurHash3's fmix64 finalizer (Appleby, public
+// domain).  It only picks slots (equality is always decided on every byte),
+// so the two ends suffice; every table holding long words uses this one
+// function, from the text or from a table's arena alike.
+__device__ __forceinline__ unsigned long long long_hash(const uint8_t *w, unsigned long long len) {
+    const long long m = len < 16 ? (long long)len : 16;
+    const uint4 f = load_run16(w, m), l = load_run16(w + (len - (unsigned long long)m), m);
+    const unsigned long long f0 = ((unsigned long long)f.y << 32) | f.x, f1 = ((unsigned long long)f.w << 32) | f.z;
+    const unsigned long long l0 = ((unsigned long long)l.y << 32) | l.x, l1 = ((unsigned long long)l.w << 32) | l.z;
+    return fmix64(f0 * 0x9E3779B97F4A7C15ull ^ f1 * 0xC2B2AE3D27D4EB4Full ^ l0 * 0x165667B19E3779F9ull ^
+                  l1 * 0xD6E8FEB86659FD93ull ^ len * 0xFF51AFD7ED558CCDull);
 }
 // Whether the letter runs a[0, len) and b[0, len) are equal (case folded).
 __device__ inline bool runs_equal(const uint8_t *a, const uint8_t *b, unsigned long long len) {
@@ -391,7 +351,7 @@ __device__ inline void long_insert2(const GTable &g, const uint8_t *w, unsigned 
 // One thread inserts a long word (computes the hash itself).
 __device__ inline void long_insert(const GTable &g, const uint8_t *w, uint64_t len, unsigned long long add,
                                    const uint8_t *begin, const uint8_t *end) {
-    long_insert2(g, w, len, long_hash_serial(w, len), add, begin, end);
+    long_insert2(g, w, len, long_hash(w, len), add, begin, end);
 }
 
 // ---------------------------------------------------------------- 8-byte keys
