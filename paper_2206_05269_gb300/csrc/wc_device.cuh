@@ -56,8 +56,10 @@ __device__ __forceinline__ bool is_letter(uint32_t b) {
 }
 __device__ __forceinline__ uint32_t lower_byte(uint32_t b) { return b | 0x20u; }
 
-__device__ __forceinline__ uint32_t byte_keep_mask(int r) {  // low r bytes (0..4)
-    return r >= 4 ? 0xFFFFFFFFu : (r <= 0 ? 0u : ((1u << (r * 8)) - 1u));
+// Mask of the low r bytes of a word (none for r <= 0, all for r >= 4): the
+// high word of 0:0xFFFFFFFF shifted left by 8r bits, the shift clamped to 32.
+__device__ __forceinline__ uint32_t byte_keep_mask(int r) {
+    return __funnelshift_lc(0xFFFFFFFFu, 0u, 8u * (uint32_t)(r > 0 ? r : 0));
 }
 
 // 16 lowercased bytes of win[p, p+len), zero padded (len <= 16).  Reads
