@@ -93,6 +93,21 @@ wc_status wc_count(wc_ctx *ctx, const uint8_t *d_text, uint64_t nbytes, cudaStre
 wc_status wc_count_ex(wc_ctx *ctx, const uint8_t *d_text, uint64_t nbytes,
                       const wc_count_opts *opts, cudaStream_t stream, wc_table **out);
 
+/* Counts one document held in host memory h_text[0, nbytes): the same table
+ * as copying the text to the device and calling wc_count (the paper's map +
+ * reduce with its host -> device copy, Sec. 3.3 and Sec. 4.1, made to overlap).
+ * The text is copied into d_buf (device memory of at least nbytes bytes
+ * owned by the caller, or NULL: the library takes it from the context's
+ * pool and releases it after the count) in pieces of about piece_bytes (0:
+ * automatic) cut after a non-letter byte, on a copy stream of the context,
+ * and each piece is counted on `stream` as soon as it has landed, so copying
+ * overlaps counting.  h_text must stay valid until the stream reaches the
+ * end of the call; pinned memory lets the copies run asynchronously, other
+ * memory is copied synchronously.  opts (may be NULL) sets capacities as for
+ * wc_count_ex.  Errors as wc_count_ex. */
+wc_status wc_count_host(wc_ctx *ctx, const uint8_t *h_text, uint64_t nbytes, uint8_t *d_buf, uint64_t piece_bytes,
+                        const wc_count_opts *opts, cudaStream_t stream, wc_table **out);
+
 /* Counts ndocs documents in one pass: document i is d_text[d_offsets[i],
  * d_offsets[i+1]) (device uint64, non-decreasing, d_offsets[0] may be > 0).
  * d_class (device uint32, may be NULL) assigns each document a class below

@@ -204,6 +204,7 @@ void wc_destroy(wc_ctx *ctx) {
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     prof_clear(ctx);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     cudaMemPoolDestroy(ctx->pool);
     delete ctx;
 }
@@ -465,6 +466,87 @@ wc_status wc_count_ex(wc_ctx *ctx, const uint8_t *d_text, uint64_t nbytes, const
 
 wc_status wc_count(wc_ctx *ctx, const uint8_t *d_text, uint64_t nbytes, cudaStream_t stream, wc_table **out) {
     return wc_count_ex(ctx, d_text, nbytes, nullptr, stream, out);
+}
+
+// ---------------------------------------------------------------- counting from host memory
+static bool host_letter(uint8_t b) { return (uint8_t)((b | 0x20) - 0x61) < 26 && b < 0x80; }
+
+wc_status wc_count_host(wc_ctx *ctx, const uint8_t *h_text, uint64_t nbytes, uint8_t *d_buf, uint64_t piece_bytes,
+                        const wc_count_opts *opts, cudaStream_t stream, wc_table **out) {
+    if (!ctx || !out) return WC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!h_text && nbytes) return ctx->fail(WC_ERR_INVALID_ARG, "null text");
+    if (nbytes >= (1ull << 40)) return ctx->fail(WC_ERR_UNSUPPORTED, "text of 2^40 bytes or more");
+    if (ctx->count_bits == 32 && nbytes >= (1ull << 33))
+        return ctx->fail(WC_ERR_UNSUPPORTED, "32-bit counts need inputs under 2^33 bytes");
+    cudaSetDevice(ctx->device);
+    if (!ctx->copy_stream && cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->copy_stream = nullptr;
+        return ctx->fail(WC_ERR_CUDA, "cudaStreamCreate (copy stream)");
+    }
+    // pieces cut where a letter is not followed by a letter: no word spans two
+    if (!piece_bytes) piece_bytes = std::max<uint64_t>(64ull << 20, (nbytes + 31) / 32);
+    std::vector<uint64_t> cut{0};
+    while (cut.back() < nbytes) {
+        uint64_t e = std::min(nbytes, cut.back() + piece_bytes);
+        while (e < nbytes && host_letter(h_text[e - 1]) && host_letter(h_text[e])) e++;
+        cut.push_back(e);
+    }
+    // the device copy of the text, tables for the whole text, the output table
+    void *own = nullptr;
+    uint8_t *dt = d_buf;
+    wc_status st = WC_OK;
+    if (!dt && (st = ctx->alloc(&own, std::max<uint64_t>(nbytes, 16), stream)) != WC_OK) return st;
+    if (!dt) dt = static_cast<uint8_t *>(own);
+    const CapPlan plan = plan_capacity(ctx, nbytes, opts);
+    CountScratch cs;
+    if ((st = scratch_create(ctx, plan, true, stream, cs)) != WC_OK) {
+        if (own) ctx->release(own, std::max<uint64_t>(nbytes, 16), stream);
+        return st;
+    }
+    wc_table *t = nullptr;
+    if ((st = table_create(ctx, cs.entries(), plan.caplong, plan.arena, ctx->count_bits, stream, &t)) != WC_OK) {
+        ctx->release(cs.mem, cs.bytes, stream);
+        if (own) ctx->release(own, std::max<uint64_t>(nbytes, 16), stream);
+        return st;
+    }
+    t->src_bytes = nbytes;
+    const GTable g = cs.gtable(t->dt.d_status);
+    // copies on the copy stream (after the caller's earlier work); each piece
+    // is counted on the caller's stream once it has landed, so later copies
+    // overlap earlier counts
+    const size_t np = cut.size() - 1;
+    std::vector<cudaEvent_t> ev(np + 1, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (auto &x : ev)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[np], stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ev[np], 0);
+    for (size_t i = 0; i < np && e == cudaSuccess; i++) {
+        e = cudaMemcpyAsync(dt + cut[i], h_text + cut[i], cut[i + 1] - cut[i], cudaMemcpyHostToDevice, ctx->copy_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[i], ctx->copy_stream);
+    }
+    const bool head = np && cut[1] - cut[0] >= count_global_head_min();  // the first piece picks the head
+    for (size_t i = 0; i < np && e == cudaSuccess; i++) {
+        e = cudaStreamWaitEvent(stream, ev[i], 0);
+        CountLaunch cl{dt, cut[i], cut[i + 1], g, 0, cs.head, {nullptr, nullptr}, i == 0 ? 0 : (head ? 1 : 2)};
+        if (e == cudaSuccess) e = launch_count_global(cl, stream);
+        ctx->launches += count_global_launches(cut[i + 1] - cut[i], i == 0 && head);
+    }
+    if (e == cudaSuccess) e = finish_table(g, cs.gcap8, cs.gcap, cs.glcap, cs.ss, t->dt, stream);
+    ctx->launches += finish_table_launches();
+    for (auto x : ev)
+        if (x) cudaEventDestroy(x);  // released once their work completes
+    ctx->release(cs.mem, cs.bytes, stream);
+    if (own) ctx->release(own, std::max<uint64_t>(nbytes, 16), stream);
+    table_mark_done(t, stream);
+    if (e != cudaSuccess) {
+        wc_table_free(t);
+        return ctx->cuda_fail(e, "count from host memory");
+    }
+    *out = t;
+    return WC_OK;
 }
 
 // ---------------------------------------------------------------- merge / top-k

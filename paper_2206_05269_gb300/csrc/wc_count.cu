@@ -70,6 +70,7 @@ struct Count2Args {
     uint32_t piece_chunks;            // chunks per piece (sampling) or nchunks
     unsigned long long piece_stride;  // bytes between pieces (sampling) or 0
     GTable g;
+    const uint8_t *lbegin;            // long-word representatives lie in [lbegin, text + hi)
     const unsigned long long *head;   // head image (nb * 4 keys) or null
     const uint32_t *head_fp;          // its fingerprints (nb words of 4 bytes)
     uint32_t nb;
@@ -452,7 +453,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_count2(Count2Args a) {
                 len = 17;
                 while (w + len < end && is_letter(w[len])) len++;
             }
-            long_insert2(a.g, w, len, long_hash(w, len), 1ull, begin, end);
+            long_insert2(a.g, w, len, long_hash(w, len), 1ull, a.lbegin, end);
         }
         __syncwarp();
     };
@@ -736,11 +737,19 @@ cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
     a.piece_chunks = a.nchunks;
     a.piece_stride = 0;
     a.g = c.g;
+    a.lbegin = c.text;
     a.head = nullptr;
     a.head_fp = nullptr;
     a.nb = kHeadBuckets;
     const uint64_t n = c.hi - c.lo;
-    if (n >= kHeadMinBytes && c.head_scratch) {
+    if (c.head_mode == 1 && c.head_scratch) {  // the head an earlier launch built
+        uint8_t *p = static_cast<uint8_t *>(c.head_scratch);
+        unsigned long long *cand =
+            reinterpret_cast<unsigned long long *>(p + kSampleSlots * sizeof(G8Slot) + 4096 * 4 + 64);
+        unsigned long long *image = cand + kHeadBuckets * 4;
+        a.head = image;
+        a.head_fp = reinterpret_cast<uint32_t *>(image + kHeadBuckets * 4) + kHeadBuckets * 4;
+    } else if (c.head_mode == 0 && n >= kHeadMinBytes && c.head_scratch) {
         // sampling pass into its own small 8-byte-key table
         uint8_t *p = static_cast<uint8_t *>(c.head_scratch);
         G8Slot *sample = reinterpret_cast<G8Slot *>(p);
@@ -777,5 +786,6 @@ cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
 }
 
 int count_global_chunk_bytes() { return kChunk; }
+uint64_t count_global_head_min() { return kHeadMinBytes; }
 
 }  // namespace wc

@@ -19,6 +19,7 @@ struct wc_ctx {
     int autotune = 0;
     std::string tune_cache_path;
     cudaMemPool_t pool = nullptr;
+    cudaStream_t copy_stream = nullptr;  // host -> device copies of wc_count_host (created on first use)
     std::string last_error;
     // stage tracing
     bool profile = false;

@@ -9,16 +9,20 @@ namespace wc {
 
 // ---------------------------------------------------------------- counting
 struct CountLaunch {
-    const uint8_t *text;     // document bytes are text[lo, hi)
+    const uint8_t *text;     // document bytes are text[lo, hi); long words may
+                             // match representatives anywhere in text[0, hi)
     uint64_t lo, hi;
     GTable g;
     int grid;                // 0 = one persistent block per SM
     void *head_scratch;      // head_scratch_bytes() or null (no shared-memory head)
     cudaEvent_t main_ev[2];  // recorded (when non-null) right before the main counting kernel
+    int head_mode;           // 0: build a head (texts >= count_global_head_min()); 1: reuse the
+                             // head an earlier launch built in head_scratch; 2: no head
 };
 // Tokenises and counts text[lo, hi) into g (8-byte, 16-byte and long tables).
 cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s);
 int count_global_chunk_bytes();
+uint64_t count_global_head_min();
 int count_global_launches(uint64_t nbytes, bool head);
 size_t head_scratch_bytes();
 

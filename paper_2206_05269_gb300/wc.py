@@ -33,7 +33,7 @@ WC_TABLE_DOC, WC_TABLE_CLASS, WC_TABLE_GLOBAL = 0, 1, 2
 
 # Every symbol include/wc.h declares (checked by the tests).
 EXPORTS = [
-    "wc_create", "wc_destroy", "wc_count", "wc_count_ex", "wc_count_batched", "wc_batch_status",
+    "wc_create", "wc_destroy", "wc_count", "wc_count_ex", "wc_count_host", "wc_count_batched", "wc_batch_status",
     "wc_batch_table", "wc_batch_topk", "wc_batch_size", "wc_batch_export",
     "wc_class_ratio_topk", "wc_merge", "wc_topk", "wc_table_status", "wc_table_size",
     "wc_table_export", "wc_table_count_bits", "wc_table_free", "wc_batch_free", "wc_plan_create", "wc_plan_run",
@@ -77,6 +77,7 @@ def load() -> ctypes.CDLL:
         "wc_destroy": (None, [vp]),
         "wc_count": (i32, [vp, vp, u64, vp, pvp]),
         "wc_count_ex": (i32, [vp, vp, u64, ctypes.POINTER(WcCountOpts), vp, pvp]),
+        "wc_count_host": (i32, [vp, vp, u64, vp, u64, ctypes.POINTER(WcCountOpts), vp, pvp]),
         "wc_count_batched": (i32, [vp, vp, vp, vp, u32, vp, u32, vp, pvp]),
         "wc_batch_status": (i32, [vp]),
         "wc_batch_table": (i32, [vp, i32, u32, pvp]),
@@ -142,6 +143,15 @@ def wc_count_ex(ctx, d_text: int, nbytes: int, opts: tuple[int, int, int] | None
     o = WcCountOpts(*(opts or (0, 0, 0)))
     _check(load().wc_count_ex(ctx, d_text, nbytes, ctypes.byref(o), stream, ctypes.byref(out)), ctx,
            "wc_count_ex")
+    return out
+
+
+def wc_count_host(ctx, h_text: int, nbytes: int, d_buf: int | None, piece_bytes: int,
+                  opts: tuple[int, int, int] | None, stream: int):
+    out = ctypes.c_void_p()
+    o = WcCountOpts(*(opts or (0, 0, 0)))
+    _check(load().wc_count_host(ctx, h_text, nbytes, d_buf, piece_bytes, ctypes.byref(o), stream, ctypes.byref(out)),
+           ctx, "wc_count_host")
     return out
 
 
@@ -425,6 +435,32 @@ class Counter:
         """Counts one document held in a uint8 CUDA tensor (asynchronous)."""
         s = _stream_handle(stream)
         return Table(wc_count_ex(self.ctx, text.data_ptr(), text.numel(), opts, s), counter=self)
+
+    def count_host(self, text, stream=None, out=None, piece_bytes: int = 0, opts=None) -> Table:
+        """Counts one document held in host memory (a uint8 CPU tensor, pinned
+        for the copies to overlap counting): copied to the device piece by
+        piece (into `out`, a uint8 CUDA tensor of at least text.numel()
+        bytes, or library memory) and each piece counted as it lands."""
+        s = _stream_handle(stream)
+        n = int(text.numel())
+        return Table(wc_count_host(self.ctx, text.data_ptr() if n else None, n,
+                                   out.data_ptr() if out is not None else None, piece_bytes, opts, s), counter=self)
+
+    def count_host_checked(self, text, stream=None, out=None, piece_bytes: int = 0, retries: int = 4) -> Table:
+        """count_host() that waits for the result and counts again with 4x
+        capacities on WC_ERR_CAPACITY (as count_checked)."""
+        opts = (0, 0, 0)
+        for _ in range(retries + 1):
+            t = self.count_host(text, stream, out, piece_bytes, opts)
+            st = t.status()
+            if st != WC_ERR_CAPACITY:
+                _check(st, self.ctx, "count_host")
+                return t
+            n = int(text.numel())
+            t.free()
+            base = opts if any(opts) else (max(1024, n // 4), max(256, n // 64), max(4096, n // 8))
+            opts = tuple(max(1, int(v)) * 4 for v in base)
+        raise WcError(WC_ERR_CAPACITY, "capacity retries exhausted")
 
     def count_checked(self, text, stream=None, opts=None, retries: int = 4) -> Table:
         """count() that waits for the result and recounts with 4x capacities on

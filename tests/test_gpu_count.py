@@ -188,3 +188,36 @@ def test_budget_rejects():
         small.count(to_dev(c.text.tobytes()))
     assert e.value.status == wc.WC_ERR_BUDGET
     small.close()
+
+
+@pytest.mark.parametrize("piece", [0, 4096, 65536])
+def test_count_from_host_memory_in_pieces(ctr, piece):
+    """wc_count_host: the text copied and counted piece by piece equals the
+    oracle, with pieces cut mid-text (a 10,000-letter word longer than a
+    piece, long words repeated across pieces, words at the nominal cuts)."""
+    import torch
+    c = corpus.generate("tiny", ndocs=6, len_max=30, len_tail=0.3, len_tail_mean=8.0)
+    arr = np.concatenate([c.text, np.frombuffer(b" " + b"Qx" * 5000 + b" tail", dtype=np.uint8), c.text[:70000]])
+    host = torch.from_numpy(arr.copy()).pin_memory()
+    t = ctr.count_host_checked(host, piece_bytes=piece)
+    assert t.as_list() == oracle.count(arr).glob().as_list()
+
+
+def test_count_from_host_memory_with_head_reuse(ctr):
+    """A 64 MB text counted from host memory in 16 MB pieces (the first piece
+    picks the shared-memory head, the others reuse it) equals the count of
+    the same bytes already on the device."""
+    import torch
+    c = corpus.generate("large", size_a=64e6)
+    host = torch.from_numpy(c.text).pin_memory()
+    a = ctr.count_host_checked(host, piece_bytes=16 << 20)
+    b = ctr.count_checked(host.to("cuda:0"))
+    wa, oa, ca = a.export()
+    wb, ob, cb = b.export()
+    assert np.array_equal(ca, cb) and np.array_equal(oa, ob) and np.array_equal(wa, wb)
+
+
+def test_count_from_host_memory_empty(ctr):
+    import torch
+    t = ctr.count_host_checked(torch.zeros(0, dtype=torch.uint8))
+    assert t.size()[0] == 0
