@@ -860,36 +860,79 @@ __device__ __forceinline__ bool ratio_better(unsigned long long ia, unsigned lon
     return ia < ib;
 }
 
-// k rounds of a block-wide arg-best over the class entries (one block).
-__global__ void __launch_bounds__(1024) k_ratio_select(RatioArgs r, unsigned char *taken) {
+// The top k of a list of entries (src[0, n) holds entry indices, or is the
+// identity when src is null) by k rounds of a block-wide arg-best; the winners
+// go to dst[0, min(k, n)) and *dst_n.  taken[] (n flags, zeroed) marks them.
+__device__ void ratio_topk_block(const RatioArgs &r, const unsigned long long *src, unsigned long long n,
+                                 unsigned char *taken, unsigned long long *dst, unsigned long long *dst_n) {
     __shared__ unsigned long long bi[32], bc[32], bo[32];
-    const unsigned long long n = r.cls.d_meta[0];
     const uint32_t k = (uint32_t)(n < r.k ? n : r.k);
     for (uint32_t round = 0; round < k; round++) {
-        unsigned long long mi = ~0ull, mc = 0, mo = 0;
-        for (unsigned long long i = threadIdx.x; i < n; i += blockDim.x) {
-            if (taken[i]) continue;
-            if (mi == ~0ull || ratio_better(i, r.cin[i], r.cout[i], mi, mc, mo)) { mi = i; mc = r.cin[i]; mo = r.cout[i]; }
+        unsigned long long mi = ~0ull, mc = 0, mo = 0, mj = 0;
+        for (unsigned long long j = threadIdx.x; j < n; j += blockDim.x) {
+            if (taken[j]) continue;
+            const unsigned long long i = src ? src[j] : j;
+            if (mi == ~0ull || ratio_better(i, r.cin[i], r.cout[i], mi, mc, mo)) {
+                mi = i; mc = r.cin[i]; mo = r.cout[i]; mj = j;
+            }
         }
         for (int d = 16; d; d >>= 1) {
-            unsigned long long oi = __shfl_xor_sync(0xFFFFFFFFu, mi, d), oc = __shfl_xor_sync(0xFFFFFFFFu, mc, d),
-                               oo = __shfl_xor_sync(0xFFFFFFFFu, mo, d);
-            if (oi != ~0ull && (mi == ~0ull || ratio_better(oi, oc, oo, mi, mc, mo))) { mi = oi; mc = oc; mo = oo; }
+            const unsigned long long oi = __shfl_xor_sync(0xFFFFFFFFu, mi, d), oc = __shfl_xor_sync(0xFFFFFFFFu, mc, d),
+                                     oo = __shfl_xor_sync(0xFFFFFFFFu, mo, d), oj = __shfl_xor_sync(0xFFFFFFFFu, mj, d);
+            if (oi != ~0ull && (mi == ~0ull || ratio_better(oi, oc, oo, mi, mc, mo))) { mi = oi; mc = oc; mo = oo; mj = oj; }
         }
-        if ((threadIdx.x & 31) == 0) { bi[threadIdx.x >> 5] = mi; bc[threadIdx.x >> 5] = mc; bo[threadIdx.x >> 5] = mo; }
+        __shared__ unsigned long long bj[32];
+        if ((threadIdx.x & 31) == 0) {
+            bi[threadIdx.x >> 5] = mi; bc[threadIdx.x >> 5] = mc; bo[threadIdx.x >> 5] = mo; bj[threadIdx.x >> 5] = mj;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
-            unsigned long long xi = ~0ull, xc = 0, xo = 0;
+            unsigned long long xi = ~0ull, xc = 0, xo = 0, xj = 0;
             for (int w = 0; w < (int)(blockDim.x >> 5); w++)
                 if (bi[w] != ~0ull && (xi == ~0ull || ratio_better(bi[w], bc[w], bo[w], xi, xc, xo))) {
-                    xi = bi[w]; xc = bc[w]; xo = bo[w];
+                    xi = bi[w]; xc = bc[w]; xo = bo[w]; xj = bj[w];
                 }
-            r.out_idx[round] = xi;
-            taken[xi] = 1;
+            dst[round] = xi;
+            taken[xj] = 1;
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) *r.out_n = k;
+    if (threadIdx.x == 0) *dst_n = k;
+}
+
+// Stage 1: block b keeps the top k of its slice of the class entries (the
+// overall top k is among the blocks' winners).  Stage 2 (one block): the top
+// k of the winners.
+constexpr unsigned long long kRatioSlice = 1024;
+__global__ void __launch_bounds__(256) k_ratio_select_slices(RatioArgs r, unsigned char *taken, unsigned long long *cand,
+                                                            unsigned long long *cand_n) {
+    const unsigned long long n = r.cls.d_meta[0];
+    const unsigned long long lo = (unsigned long long)blockIdx.x * kRatioSlice;
+    if (lo >= n) {
+        if (threadIdx.x == 0) cand_n[blockIdx.x] = 0;
+        return;
+    }
+    const unsigned long long m = n - lo < kRatioSlice ? n - lo : kRatioSlice;
+    __shared__ unsigned long long ids[kRatioSlice];
+    for (unsigned long long j = threadIdx.x; j < m; j += blockDim.x) ids[j] = lo + j;
+    __syncthreads();
+    ratio_topk_block(r, ids, m, taken + lo, cand + (unsigned long long)blockIdx.x * r.k, cand_n + blockIdx.x);
+}
+__global__ void __launch_bounds__(1024) k_ratio_select(RatioArgs r, unsigned char *taken, const unsigned long long *cand,
+                                                       const unsigned long long *cand_n, unsigned int nblocks) {
+    // gather the winners densely at the front of cand's slots (in order)
+    __shared__ unsigned long long off[1];
+    unsigned long long *list = const_cast<unsigned long long *>(cand);
+    if (threadIdx.x == 0) {
+        unsigned long long o = 0;
+        for (unsigned int b = 0; b < nblocks; b++) {
+            for (unsigned long long j = 0; j < cand_n[b]; j++) list[o + j] = cand[(unsigned long long)b * r.k + j];
+            o += cand_n[b];
+        }
+        off[0] = o;
+    }
+    __syncthreads();
+    ratio_topk_block(r, list, off[0], taken, r.out_idx, r.out_n);
 }
 
 wc_status wc_class_ratio_topk(wc_ctx *ctx, const wc_batch *cb, uint32_t cls, uint32_t k, cudaStream_t stream,
@@ -905,8 +948,10 @@ wc_status wc_class_ratio_topk(wc_ctx *ctx, const wc_batch *cb, uint32_t cls, uin
     if ((st = table_sync(ct)) != WC_OK) return st;
     if ((st = table_sync(b->global)) != WC_OK) return st;
     const uint64_t n = ct->n;
+    const uint64_t nblk = (n + kRatioSlice - 1) / kRatioSlice;  // stage-1 slices
     void *mem = nullptr;
-    const size_t bytes = n * 17 + (size_t)k * 8 + 64 + 256;
+    // cin, cout, the top k + its length, the slices' winners + lengths, taken flags
+    const size_t bytes = n * 16 + ((size_t)k + 1) * 8 + nblk * ((size_t)k + 1) * 8 + n + nblk * k + 256;
     if ((st = ctx->alloc(&mem, bytes, stream)) != WC_OK) return st;
     uint8_t *p = static_cast<uint8_t *>(mem);
     RatioArgs r;
@@ -916,12 +961,19 @@ wc_status wc_class_ratio_topk(wc_ctx *ctx, const wc_batch *cb, uint32_t cls, uin
     r.cout = r.cin + n;
     r.out_idx = r.cout + n;
     r.out_n = r.out_idx + k;
-    unsigned char *taken = reinterpret_cast<unsigned char *>(r.out_n + 1);
+    unsigned long long *cand = r.out_n + 1, *cand_n = cand + nblk * k;
+    unsigned char *taken = reinterpret_cast<unsigned char *>(cand_n + nblk);
     r.k = k;
-    cudaMemsetAsync(taken, 0, n + 1, stream);
+    cudaMemsetAsync(taken, 0, n + nblk * k + 1, stream);
+    cudaMemsetAsync(r.out_n, 0, 8, stream);
     int sms = ctx->sms;
-    if (n) k_ratio_prepare<<<std::max<int>(1, std::min<int>(sms * 4, (int)((n + 255) / 256))), 256, 0, stream>>>(r);
-    k_ratio_select<<<1, 1024, 0, stream>>>(r, taken);
+    if (n) {
+        k_ratio_prepare<<<std::max<int>(1, std::min<int>(sms * 4, (int)((n + 255) / 256))), 256, 0, stream>>>(r);
+        if (k) {
+            k_ratio_select_slices<<<(unsigned int)nblk, 256, 0, stream>>>(r, taken, cand, cand_n);
+            k_ratio_select<<<1, 1024, 0, stream>>>(r, taken + n, cand, cand_n, (unsigned int)nblk);
+        }
+    }
     std::vector<unsigned long long> idx(k + 1), cin(n), cout(n);
     unsigned long long m = 0;
     cudaMemcpyAsync(&m, r.out_n, 8, cudaMemcpyDeviceToHost, stream);
