@@ -222,7 +222,8 @@ def run_gpu(args, rank, world, local):
         t = step()
         if t.status() != wc.WC_OK:
             raise RuntimeError(f"count failed: {wc.wc_last_error(ctr.ctx)}")
-        nwords, ntok, _ = t.size()
+        nwords, ntok, nbytes_words = t.size()
+        cbits = wc.wc_table_count_bits(t.handle)
         t.free()
 
     barrier()
@@ -255,13 +256,18 @@ def run_gpu(args, rank, world, local):
     dev2 = torch.empty_like(text)
     d2h = 0
     t_e2e = []
+    # pinned host buffers for the result, sized from the device steps' table
+    cnt_t = torch.int64 if cbits == 64 else torch.int32
+    hw = torch.empty(max(1, nbytes_words + 4096), dtype=torch.uint8).pin_memory()
+    ho = torch.empty(nwords + 1, dtype=torch.int64).pin_memory()
+    hc = torch.empty(max(1, nwords), dtype=cnt_t).pin_memory()
     for i in range(e2e_steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         tab = ctr.count_host(host, stream, out=dev2)
-        w, o, cnt = tab.export(stream)
+        n_rows, n_wb = tab.export_into(hw, ho, hc, stream)
         t_e2e.append(time.perf_counter() - t0)
-        d2h = w.nbytes + o.nbytes + cnt.nbytes
+        d2h = n_wb + (n_rows + 1) * 8 + n_rows * hc.element_size()
         tab.free()
     e2e_s = statistics.mean(t_e2e[1:])
     e2e_val = nbytes * world / e2e_s / 1e9
@@ -382,18 +388,23 @@ def run_docs_workload(args, local):
     for t in outs:
         t.status()
     per_launch = nsamp / (time.perf_counter() - t1)
-    # end to end: host text -> device, batched count, every table -> host
-    dev2 = torch.empty_like(text)
+    # end to end: host text -> the plan's device buffer, the step (the plan's
+    # batched count, and for tiny/classes the class/global tables and
+    # rankings), every per-document table -> pinned host buffers
+    nent, nwb = wc.wc_batch_size(b.handle)
+    pin = lambda n, dt: torch.empty(max(1, n), dtype=dt).pin_memory()
+    hds, hdn = pin(c.ndocs, torch.int64), pin(c.ndocs, torch.int32)
+    hw, ho, hc = pin(nwb + 4096, torch.uint8), pin(nent + 1, torch.int64), pin(nent, torch.int32)
     te = []
-    for i in range(4):
+    d2h = 0
+    for i in range(7):
         torch.cuda.synchronize()
         t2 = time.perf_counter()
-        dev2.copy_(host, non_blocking=True)
-        bb = ctr.count_batched(dev2, offs, c.offsets, cls, c.nclasses if c.nclasses > 1 else 0, stream)
-        ds, dn, w, o, cc = bb.export(stream)
+        text.copy_(host, non_blocking=True)
+        bb = step()
+        n_rows, n_wb = bb.export_into(hds, hdn, hw, ho, hc, stream)
         te.append(time.perf_counter() - t2)
-        d2h = ds.nbytes + dn.nbytes + w.nbytes + o.nbytes + cc.nbytes
-        del bb
+        d2h = c.ndocs * 12 + n_wb + (n_rows + 1) * 8 + n_rows * 4
     e2e = c.ndocs / statistics.mean(te[1:])
     peak, peak_kind = measured_peaks()
     alg = c.nbytes + nent * 24

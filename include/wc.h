@@ -119,8 +119,20 @@ wc_status wc_count_batched(wc_ctx *ctx, const uint8_t *d_text, const uint64_t *d
                            const uint64_t *h_offsets, uint32_t ndocs, const uint32_t *d_class,
                            uint32_t nclasses, cudaStream_t stream, wc_batch **out);
 
+/* wc_count_batched with flags.  WC_BATCH_EXACT_BOUNDS sizes the output and
+ * the spill tables from bounds no input can exceed (a document of s bytes
+ * has at most s/2 + 1 distinct words, s/18 + 1 of them 17 letters or
+ * longer) instead of from estimates: far more memory, but it cannot fail
+ * with WC_ERR_CAPACITY, so it is the recount after one.  Other flags:
+ * WC_ERR_INVALID_ARG. */
+enum { WC_BATCH_EXACT_BOUNDS = 1 };
+wc_status wc_count_batched_ex(wc_ctx *ctx, const uint8_t *d_text, const uint64_t *d_offsets,
+                              const uint64_t *h_offsets, uint32_t ndocs, const uint32_t *d_class,
+                              uint32_t nclasses, uint32_t flags, cudaStream_t stream, wc_batch **out);
+
 /* Waits for the batch; device-side overflow of its tables or output is
- * reported as WC_ERR_CAPACITY (count again; nothing partial is kept). */
+ * reported as WC_ERR_CAPACITY (count again with WC_BATCH_EXACT_BOUNDS;
+ * nothing partial is kept). */
 wc_status wc_batch_status(const wc_batch *batch);
 
 /* Borrows one table of a batch (owned by the batch, freed with it; calling

@@ -69,6 +69,7 @@ struct wc_batch {
     uint64_t entries = 0, word_bytes = 0;
     // lazily built
     bool tables_built = false;
+    bool exact = false;  // capacities at the exact bounds
     std::vector<wc_table *> class_tables;
     wc_table *global = nullptr;
     CountScratch gscratch;        // global hash tables kept for ratio lookups
@@ -178,7 +179,12 @@ static void free_owned_table(wc_table *t) {
 
 // ---------------------------------------------------------------- batched count
 // Host planning: items per size class (largest first) and capacities.
-static wc_status batch_plan(wc_ctx *ctx, const uint64_t *h_offsets, uint32_t ndocs, uint32_t nclasses, wc_batch **out) {
+// Capacities from estimates, or (exact) from the bounds no input can exceed:
+// a document of s bytes has at most s/2 + 1 distinct words and s/18 + 1
+// words of 17 or more letters, whose bytes (each followed by a 0) fit in
+// s + its long-word count.
+static wc_status batch_plan(wc_ctx *ctx, const uint64_t *h_offsets, uint32_t ndocs, uint32_t nclasses, bool exact,
+                            wc_batch **out) {
     if (ndocs >= kMaxDocs) return ctx->fail(WC_ERR_UNSUPPORTED, "2^24 documents or more in one batch");
     for (uint32_t i = 0; i < ndocs; i++)
         if (h_offsets[i + 1] < h_offsets[i]) return ctx->fail(WC_ERR_INVALID_ARG, "offsets decrease");
@@ -188,13 +194,14 @@ static wc_status batch_plan(wc_ctx *ctx, const uint64_t *h_offsets, uint32_t ndo
     b->ndocs = ndocs;
     b->nclasses = nclasses;
     std::vector<DocItem> small, medium;
-    uint64_t out_est = 0, glob_est = 0, long_est = 0;
+    uint64_t out_est = 0, glob_est = 0, long_est = 0, total = 0;
     for (uint32_t d = 0; d < ndocs; d++) {
         const uint64_t lo = h_offsets[d], hi = h_offsets[d + 1], s = hi - lo;
         if (!s) continue;
-        const uint64_t e = est_distinct(s);
-        out_est += out_reserve(s);
-        long_est += std::min<uint64_t>(s / 18 + 1, e / 8 + 2);
+        const uint64_t e = exact ? s / 2 + 1 : est_distinct(s);
+        out_est += exact ? s / 2 + 5 : out_reserve(s);
+        long_est += exact ? s / 18 + 1 : std::min<uint64_t>(s / 18 + 1, e / 8 + 2);
+        total += s;
         if (s <= kSmallMax) small.push_back({lo, hi, d, 0});
         else if (s <= kSplitMin) medium.push_back({lo, hi, d, 0});
         else {
@@ -210,11 +217,13 @@ static wc_status batch_plan(wc_ctx *ctx, const uint64_t *h_offsets, uint32_t ndo
     b->items.insert(b->items.end(), medium.begin(), medium.end());
     b->args.out_cap = out_est + 1024;
     b->args.lcap = long_est + 1024;
-    b->args.arena_cap = b->args.lcap * 24 + 65536;
-    // planned: split documents; reserve: documents whose shared table fills up
-    b->cap8 = pow2_ge(2 * glob_est + out_est / 32 + (1u << 18));
-    b->cap16 = pow2_ge(glob_est + out_est / 64 + (1u << 17));
-    b->caplong = pow2_ge(glob_est / 8 + (1u << 14));
+    b->args.arena_cap = exact ? total + b->args.lcap + 65536 : b->args.lcap * 24 + 65536;
+    // planned: split documents; reserve: documents whose shared table fills
+    // up (exact: every (document, word) pair may spill)
+    b->exact = exact;
+    b->cap8 = pow2_ge(exact ? 2 * out_est + (1u << 18) : 2 * glob_est + out_est / 32 + (1u << 18));
+    b->cap16 = pow2_ge(exact ? out_est + out_est / 4 + (1u << 17) : glob_est + out_est / 64 + (1u << 17));
+    b->caplong = pow2_ge(exact ? 2 * long_est + (1u << 14) : glob_est / 8 + (1u << 14));
     b->shape_small = ctx->tuned_small;
     b->shape_medium = ctx->tuned_medium;
     *out = b;
@@ -322,14 +331,21 @@ static cudaError_t batch_enqueue(wc_batch *b, const uint8_t *d_text, const uint6
 wc_status wc_count_batched(wc_ctx *ctx, const uint8_t *d_text, const uint64_t *d_offsets, const uint64_t *h_offsets,
                            uint32_t ndocs, const uint32_t *d_class, uint32_t nclasses, cudaStream_t stream,
                            wc_batch **out) {
+    return wc_count_batched_ex(ctx, d_text, d_offsets, h_offsets, ndocs, d_class, nclasses, 0u, stream, out);
+}
+
+wc_status wc_count_batched_ex(wc_ctx *ctx, const uint8_t *d_text, const uint64_t *d_offsets, const uint64_t *h_offsets,
+                              uint32_t ndocs, const uint32_t *d_class, uint32_t nclasses, uint32_t flags,
+                              cudaStream_t stream, wc_batch **out) {
     if (!ctx || !out) return WC_ERR_INVALID_ARG;
+    if (flags & ~(uint32_t)WC_BATCH_EXACT_BOUNDS) return ctx->fail(WC_ERR_INVALID_ARG, "unknown batch flags");
     *out = nullptr;
     if (ndocs && (!h_offsets || !d_offsets)) return ctx->fail(WC_ERR_INVALID_ARG, "null offsets");
     if (nclasses && !d_class) return ctx->fail(WC_ERR_INVALID_ARG, "classes without a class array");
     if (ndocs && h_offsets[ndocs] > h_offsets[0] && !d_text) return ctx->fail(WC_ERR_INVALID_ARG, "null text");
     cudaSetDevice(ctx->device);
     wc_batch *b = nullptr;
-    wc_status st = batch_plan(ctx, h_offsets, ndocs, nclasses, &b);
+    wc_status st = batch_plan(ctx, h_offsets, ndocs, nclasses, (flags & WC_BATCH_EXACT_BOUNDS) != 0, &b);
     if (st != WC_OK) return st;
     b->stream = stream;
     if ((st = batch_alloc(b, stream)) != WC_OK) {
@@ -417,7 +433,7 @@ wc_status wc_plan_create(wc_ctx *ctx, const uint64_t *h_offsets, uint32_t ndocs,
     *out = nullptr;
     cudaSetDevice(ctx->device);
     wc_plan *pl = new wc_plan();
-    wc_status st = batch_plan(ctx, h_offsets, ndocs, nclasses, &pl->b);
+    wc_status st = batch_plan(ctx, h_offsets, ndocs, nclasses, false, &pl->b);
     if (st == WC_OK) {
         pl->b->stream = stream;
         st = batch_alloc(pl->b, stream);
@@ -900,9 +916,9 @@ __device__ void ratio_topk_block(const RatioArgs &r, const unsigned long long *s
     if (threadIdx.x == 0) *dst_n = k;
 }
 
-// Stage 1: block b keeps the top k of its slice of the class entries (the
-// overall top k is among the blocks' winners).  Stage 2 (one block): the top
-// k of the winners.
+// Large k (above kRatioKeepMax): stage 1, block b keeps the top k of its
+// slice of the class entries by k rounds of arg-best (the overall top k is
+// among the blocks' winners); stage 2 (one block), the top k of the winners.
 constexpr unsigned long long kRatioSlice = 1024;
 __global__ void __launch_bounds__(256) k_ratio_select_slices(RatioArgs r, unsigned char *taken, unsigned long long *cand,
                                                             unsigned long long *cand_n) {
@@ -935,6 +951,61 @@ __global__ void __launch_bounds__(1024) k_ratio_select(RatioArgs r, unsigned cha
     ratio_topk_block(r, list, off[0], taken, r.out_idx, r.out_n);
 }
 
+// k up to kRatioKeepMax: block b sorts the 1024 list entries
+// src[b * 1024, (b + 1) * 1024) by rank (a bitonic network in shared memory;
+// entries past len and the pad index kNoEntry rank last) and keeps its first
+// `keep` in dst[b * keep, (b + 1) * keep).  The list's top k is among the
+// kept entries, and each round shrinks the list by 1024 / keep >= 2 until one
+// block holds it.  src null: the identity list of the class entries.
+constexpr int kRatioSort = 1024;
+constexpr uint32_t kRatioKeepMax = kRatioSort / 2;
+constexpr unsigned long long kNoEntry = ~0ull;
+__device__ __forceinline__ bool ranks_before(unsigned long long ia, unsigned long long ca, unsigned long long oa,
+                                             unsigned long long ib, unsigned long long cb, unsigned long long ob) {
+    if (ib == kNoEntry) return ia != kNoEntry;
+    if (ia == kNoEntry) return false;
+    return ratio_better(ia, ca, oa, ib, cb, ob);
+}
+__global__ void __launch_bounds__(kRatioSort / 2) k_ratio_round(RatioArgs r, const unsigned long long *src,
+                                                                unsigned long long len, unsigned long long *dst,
+                                                                uint32_t keep) {
+    __shared__ unsigned long long si[kRatioSort], sc[kRatioSort], so[kRatioSort];
+    const unsigned long long base = (unsigned long long)blockIdx.x * kRatioSort;
+    for (int j = threadIdx.x; j < kRatioSort; j += blockDim.x) {
+        const unsigned long long p = base + j;
+        const unsigned long long i = p < len ? (src ? src[p] : p) : kNoEntry;
+        si[j] = i;
+        sc[j] = i != kNoEntry ? r.cin[i] : 0ull;
+        so[j] = i != kNoEntry ? r.cout[i] : 0ull;
+    }
+    __syncthreads();
+    const int t = threadIdx.x;  // one compare-exchange pair per thread
+    for (int size = 2; size <= kRatioSort; size <<= 1)
+        for (int stride = size >> 1; stride; stride >>= 1) {
+            const int a = 2 * t - (t & (stride - 1)), b = a + stride;
+            const bool first_run = (a & size) == 0;  // this run ends best-first
+            const bool swap = first_run ? ranks_before(si[b], sc[b], so[b], si[a], sc[a], so[a])
+                                        : ranks_before(si[a], sc[a], so[a], si[b], sc[b], so[b]);
+            if (swap) {
+                unsigned long long x = si[a]; si[a] = si[b]; si[b] = x;
+                x = sc[a]; sc[a] = sc[b]; sc[b] = x;
+                x = so[a]; so[a] = so[b]; so[b] = x;
+            }
+            __syncthreads();
+        }
+    for (uint32_t j = threadIdx.x; j < keep; j += blockDim.x) dst[(unsigned long long)blockIdx.x * keep + j] = si[j];
+}
+
+// Rows j < m of the ranking: (entry index, cin, cout).
+__global__ void k_ratio_rows(RatioArgs r, const unsigned long long *list, unsigned long long m, unsigned long long *rows) {
+    for (unsigned long long j = threadIdx.x; j < m; j += blockDim.x) {
+        const unsigned long long i = list[j];
+        rows[3 * j] = i;
+        rows[3 * j + 1] = r.cin[i];
+        rows[3 * j + 2] = r.cout[i];
+    }
+}
+
 wc_status wc_class_ratio_topk(wc_ctx *ctx, const wc_batch *cb, uint32_t cls, uint32_t k, cudaStream_t stream,
                               uint64_t *h_idx, uint64_t *h_cin, uint64_t *h_cout, uint32_t *nout) {
     if (!ctx || !cb || !nout) return WC_ERR_INVALID_ARG;
@@ -948,10 +1019,16 @@ wc_status wc_class_ratio_topk(wc_ctx *ctx, const wc_batch *cb, uint32_t cls, uin
     if ((st = table_sync(ct)) != WC_OK) return st;
     if ((st = table_sync(b->global)) != WC_OK) return st;
     const uint64_t n = ct->n;
-    const uint64_t nblk = (n + kRatioSlice - 1) / kRatioSlice;  // stage-1 slices
+    const uint64_t m = std::min<uint64_t>(k, n);  // rows of the answer
+    if (m == 0) return WC_OK;
+    const bool rounds = k <= kRatioKeepMax;
+    const uint64_t nblk = (n + kRatioSlice - 1) / kRatioSlice;  // first-round blocks (kRatioSort == kRatioSlice)
+    // cin, cout, the answer rows; then two round lists (bitonic rounds) or
+    // the top k + its length, the slices' winners + lengths and taken flags
+    const size_t list_bytes = nblk * (size_t)m * 8;
+    const size_t bytes = n * 16 + m * 24 +
+                         (rounds ? 2 * list_bytes : ((size_t)k + 1) * 8 + nblk * ((size_t)k + 1) * 8 + n + nblk * k) + 256;
     void *mem = nullptr;
-    // cin, cout, the top k + its length, the slices' winners + lengths, taken flags
-    const size_t bytes = n * 16 + ((size_t)k + 1) * 8 + nblk * ((size_t)k + 1) * 8 + n + nblk * k + 256;
     if ((st = ctx->alloc(&mem, bytes, stream)) != WC_OK) return st;
     uint8_t *p = static_cast<uint8_t *>(mem);
     RatioArgs r;
@@ -959,34 +1036,50 @@ wc_status wc_class_ratio_topk(wc_ctx *ctx, const wc_batch *cb, uint32_t cls, uin
     r.g = b->gscratch.gtable(b->global->dt.d_status);
     r.cin = reinterpret_cast<unsigned long long *>(p);
     r.cout = r.cin + n;
-    r.out_idx = r.cout + n;
-    r.out_n = r.out_idx + k;
-    unsigned long long *cand = r.out_n + 1, *cand_n = cand + nblk * k;
-    unsigned char *taken = reinterpret_cast<unsigned char *>(cand_n + nblk);
+    unsigned long long *rows = r.cout + n;
     r.k = k;
-    cudaMemsetAsync(taken, 0, n + nblk * k + 1, stream);
-    cudaMemsetAsync(r.out_n, 0, 8, stream);
-    int sms = ctx->sms;
-    if (n) {
-        k_ratio_prepare<<<std::max<int>(1, std::min<int>(sms * 4, (int)((n + 255) / 256))), 256, 0, stream>>>(r);
-        if (k) {
-            k_ratio_select_slices<<<(unsigned int)nblk, 256, 0, stream>>>(r, taken, cand, cand_n);
-            k_ratio_select<<<1, 1024, 0, stream>>>(r, taken + n, cand, cand_n, (unsigned int)nblk);
+    r.out_idx = r.out_n = nullptr;
+    const int sms = ctx->sms;
+    uint64_t launches = 2;  // prepare, rows
+    k_ratio_prepare<<<std::max<int>(1, std::min<int>(sms * 4, (int)((n + 255) / 256))), 256, 0, stream>>>(r);
+    const unsigned long long *top = nullptr;
+    if (rounds) {
+        unsigned long long *list[2] = {rows + 3 * m, rows + 3 * m + nblk * m};
+        const unsigned long long *src = nullptr;
+        uint64_t len = n;
+        int w = 0;
+        for (;;) {
+            const uint64_t nb = (len + kRatioSort - 1) / kRatioSort;
+            k_ratio_round<<<(unsigned int)nb, kRatioSort / 2, 0, stream>>>(r, src, len, list[w], (uint32_t)m);
+            launches++;
+            if (nb == 1) break;
+            src = list[w];
+            len = nb * m;
+            w ^= 1;
         }
+        top = list[w];
+    } else {
+        r.out_idx = rows + 3 * m;
+        r.out_n = r.out_idx + k;
+        unsigned long long *cand = r.out_n + 1, *cand_n = cand + nblk * k;
+        unsigned char *taken = reinterpret_cast<unsigned char *>(cand_n + nblk);
+        cudaMemsetAsync(taken, 0, n + nblk * k, stream);
+        k_ratio_select_slices<<<(unsigned int)nblk, 256, 0, stream>>>(r, taken, cand, cand_n);
+        k_ratio_select<<<1, 1024, 0, stream>>>(r, taken + n, cand, cand_n, (unsigned int)nblk);
+        top = r.out_idx;
+        launches += 2;
     }
-    std::vector<unsigned long long> idx(k + 1), cin(n), cout(n);
-    unsigned long long m = 0;
-    cudaMemcpyAsync(&m, r.out_n, 8, cudaMemcpyDeviceToHost, stream);
-    if (k) cudaMemcpyAsync(idx.data(), r.out_idx, k * 8, cudaMemcpyDeviceToHost, stream);
-    if (n) cudaMemcpyAsync(cin.data(), r.cin, n * 8, cudaMemcpyDeviceToHost, stream);
-    if (n) cudaMemcpyAsync(cout.data(), r.cout, n * 8, cudaMemcpyDeviceToHost, stream);
-    cudaError_t e = cudaStreamSynchronize(stream);
+    ctx->launches += launches;
+    k_ratio_rows<<<1, 256, 0, stream>>>(r, top, m, rows);
+    std::vector<unsigned long long> h(3 * m);
+    cudaError_t e = cudaMemcpyAsync(h.data(), rows, m * 24, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     ctx->release(mem, bytes, stream);
     if (e != cudaSuccess) return ctx->cuda_fail(e, "class ratio ranking");
-    for (unsigned long long i = 0; i < m; i++) {
-        if (h_idx) h_idx[i] = idx[i];
-        if (h_cin) h_cin[i] = cin[idx[i]];
-        if (h_cout) h_cout[i] = cout[idx[i]];
+    for (uint64_t j = 0; j < m; j++) {
+        if (h_idx) h_idx[j] = h[3 * j];
+        if (h_cin) h_cin[j] = h[3 * j + 1];
+        if (h_cout) h_cout[j] = h[3 * j + 2];
     }
     *nout = (uint32_t)m;
     return WC_OK;

@@ -134,37 +134,63 @@ __global__ void k_compact8(const G8Slot *slots, unsigned long long cap, SortScra
     }
 }
 
-// One warp per long-word slot: copy the word (lowercased, followed by one 0
-// byte so a run in the arena ends where the word ends) into the arena and
-// emit an entry.
+// One lane per long-word slot: a warp's occupied slots take their entry
+// positions, long-word indices and arena bytes with one atomic each.  Each
+// word is copied (lowercased, followed by one 0 byte so a run in the arena
+// ends where the word ends) into the arena, by its own lane up to 64 bytes
+// and by the whole warp beyond, and emits an entry.
 __global__ void k_compact_long(const LSlot *ls, unsigned long long lcap, SortScratch ss, DevTable out) {
     const int lane = threadIdx.x & 31;
-    const unsigned long long gw = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
     unsigned long long *meta = out.d_meta;
-    for (unsigned long long w = gw; w < lcap; w += nw) {
-        const unsigned long long h = ls[w].h, addr = ls[w].addr;
-        if (h == 0 && addr == 0) continue;
-        const unsigned long long len = ls[w].len;
-        const uint8_t *src = reinterpret_cast<const uint8_t *>(addr);
-        const unsigned long long c = ls[w].cnt;
-        unsigned long long off = 0, lidx = 0, pos = 0;
-        if (lane == 0) {
-            off = atomicAdd(&meta[2], len + 1);
-            lidx = atomicAdd(&meta[1], 1ull);
-            pos = atomicAdd(&meta[0], 1ull);
-            atomicAdd(&meta[3], c);
+    for (unsigned long long w0 = (((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < lcap;
+         w0 += nw * 32) {
+        const unsigned long long w = w0 + lane;
+        unsigned long long h = 0, addr = 0, len = 0, c = 0;
+        if (w < lcap) {
+            h = ls[w].h;
+            addr = ls[w].addr;
+            len = ls[w].len;
+            c = ls[w].cnt;
         }
-        off = __shfl_sync(kFull, off, 0);
-        lidx = __shfl_sync(kFull, lidx, 0);
-        pos = __shfl_sync(kFull, pos, 0);
+        const bool occ = !(h == 0 && addr == 0);
+        const uint32_t m = __ballot_sync(kFull, occ);
+        if (!m) continue;
+        const unsigned long long rank = __popc(m & lanemask_lt()), nocc = __popc(m);
+        const unsigned long long bytes = occ ? len + 1 : 0ull;
+        unsigned long long incl = bytes, tok = occ ? c : 0ull;
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long t = __shfl_up_sync(kFull, incl, d);
+            if (lane >= d) incl += t;
+        }
+        for (int d = 16; d; d >>= 1) tok += __shfl_xor_sync(kFull, tok, d);
+        const unsigned long long total = __shfl_sync(kFull, incl, 31);
+        unsigned long long boff = 0, blidx = 0, bpos = 0;
+        if (lane == 0) {
+            boff = atomicAdd(&meta[2], total);
+            blidx = atomicAdd(&meta[1], nocc);
+            bpos = atomicAdd(&meta[0], nocc);
+            atomicAdd(&meta[3], tok);
+        }
+        const unsigned long long off = __shfl_sync(kFull, boff, 0) + incl - bytes;
+        const unsigned long long lidx = __shfl_sync(kFull, blidx, 0) + rank;
+        const unsigned long long pos = __shfl_sync(kFull, bpos, 0) + rank;
         // The arena or the long index is full: the table fails (status), but
         // the entry slot taken above is still filled (prefix key, no long
         // reference) so that the sort that follows reads only valid entries.
-        const bool full = off + len + 1 > out.arena_cap || lidx >= out.lcap;
-        if (!full)
-            for (unsigned long long j = lane; j < len; j += 32) out.arena[off + j] = (uint8_t)(src[j] | 0x20u);
-        if (lane == 0) {
+        const bool full = occ && (off + len + 1 > out.arena_cap || lidx >= out.lcap);
+        const uint8_t *src = reinterpret_cast<const uint8_t *>(addr);
+        if (occ && !full && len <= 64)
+            for (unsigned long long j = 0; j < len; j++) out.arena[off + j] = (uint8_t)(src[j] | 0x20u);
+        uint32_t big = __ballot_sync(kFull, occ && !full && len > 64);
+        while (big) {
+            const int l = __ffs(big) - 1;
+            big &= big - 1;
+            const uint8_t *bs = reinterpret_cast<const uint8_t *>(__shfl_sync(kFull, addr, l));
+            const unsigned long long bo = __shfl_sync(kFull, off, l), bl = __shfl_sync(kFull, len, l);
+            for (unsigned long long j = lane; j < bl; j += 32) out.arena[bo + j] = (uint8_t)(bs[j] | 0x20u);
+        }
+        if (occ) {
             if (full) {
                 atomicOr(out.d_status, ST_ARENA_FULL);
             } else {
@@ -486,7 +512,7 @@ cudaError_t finish_table(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_
     k_meta_snapshot<<<1, 1, 0, st>>>(out.d_meta, 5);
     k_compact_short<<<grid_for(gcap, 256, sms * 8), 256, 0, st>>>(g.slots, gcap, ss, out.d_meta);
     k_meta_snapshot<<<1, 1, 0, st>>>(out.d_meta, 6);
-    k_compact_long<<<grid_for(glcap * 32, 256, sms * 8), 256, 0, st>>>(g.lslots, glcap, ss, out);
+    k_compact_long<<<grid_for(glcap, 256, sms * 8), 256, 0, st>>>(g.lslots, glcap, ss, out);
     LongView v{ss.lref, out.loff, out.llen, out.arena};
     cudaError_t e = sort_entries(ss, out.d_meta, v, kPasses, st);
     if (e != cudaSuccess) return e;

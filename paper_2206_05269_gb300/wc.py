@@ -30,10 +30,11 @@ WC_ERR_INTERNAL = 7
 WC_ERR_UNSUPPORTED = 8
 
 WC_TABLE_DOC, WC_TABLE_CLASS, WC_TABLE_GLOBAL = 0, 1, 2
+WC_BATCH_EXACT_BOUNDS = 1
 
 # Every symbol include/wc.h declares (checked by the tests).
 EXPORTS = [
-    "wc_create", "wc_destroy", "wc_count", "wc_count_ex", "wc_count_host", "wc_count_batched", "wc_batch_status",
+    "wc_create", "wc_destroy", "wc_count", "wc_count_ex", "wc_count_host", "wc_count_batched", "wc_count_batched_ex", "wc_batch_status",
     "wc_batch_table", "wc_batch_topk", "wc_batch_size", "wc_batch_export",
     "wc_class_ratio_topk", "wc_merge", "wc_topk", "wc_table_status", "wc_table_size",
     "wc_table_export", "wc_table_count_bits", "wc_table_free", "wc_batch_free", "wc_plan_create", "wc_plan_run",
@@ -79,6 +80,7 @@ def load() -> ctypes.CDLL:
         "wc_count_ex": (i32, [vp, vp, u64, ctypes.POINTER(WcCountOpts), vp, pvp]),
         "wc_count_host": (i32, [vp, vp, u64, vp, u64, ctypes.POINTER(WcCountOpts), vp, pvp]),
         "wc_count_batched": (i32, [vp, vp, vp, vp, u32, vp, u32, vp, pvp]),
+        "wc_count_batched_ex": (i32, [vp, vp, vp, vp, u32, vp, u32, u32, vp, pvp]),
         "wc_batch_status": (i32, [vp]),
         "wc_batch_table": (i32, [vp, i32, u32, pvp]),
         "wc_batch_topk": (i32, [vp, u32, ctypes.POINTER(u64), ctypes.POINTER(u32), pvp]),
@@ -156,11 +158,15 @@ def wc_count_host(ctx, h_text: int, nbytes: int, d_buf: int | None, piece_bytes:
 
 
 def wc_count_batched(ctx, d_text: int, d_offsets: int, h_offsets: np.ndarray, ndocs: int, d_class: int | None,
-                     nclasses: int, stream: int):
+                     nclasses: int, stream: int, flags: int = 0):
     h = np.ascontiguousarray(h_offsets, dtype=np.uint64)
     out = ctypes.c_void_p()
-    _check(load().wc_count_batched(ctx, d_text, d_offsets, h.ctypes.data, ndocs, d_class or None, nclasses,
-                                   stream, ctypes.byref(out)), ctx, "wc_count_batched")
+    if flags:
+        _check(load().wc_count_batched_ex(ctx, d_text, d_offsets, h.ctypes.data, ndocs, d_class or None, nclasses,
+                                          flags, stream, ctypes.byref(out)), ctx, "wc_count_batched_ex")
+    else:
+        _check(load().wc_count_batched(ctx, d_text, d_offsets, h.ctypes.data, ndocs, d_class or None, nclasses,
+                                       stream, ctypes.byref(out)), ctx, "wc_count_batched")
     return out
 
 
@@ -359,6 +365,19 @@ class Table:
     def export(self, stream=None):
         return wc_table_export(self.handle, _stream_handle(stream))
 
+    def export_into(self, words, offsets, counts, stream=None) -> tuple[int, int]:
+        """Exports into caller-owned host tensors (uint8 words, int64 offsets
+        of n+1, counts of the table's count width; pinned ones copy fastest),
+        each at least the table's size; returns (rows, word bytes)."""
+        n, _, nb = self.size()
+        if words.numel() < nb or offsets.numel() < n + 1 or counts.numel() < n:
+            raise ValueError("export buffers smaller than the table")
+        if counts.element_size() * 8 != wc_table_count_bits(self.handle):
+            raise ValueError("count buffer width differs from the table's")
+        _check(load().wc_table_export(self.handle, words.data_ptr(), offsets.data_ptr(), counts.data_ptr(),
+                                      _stream_handle(stream)), None, "wc_table_export")
+        return n, nb
+
     def as_list(self) -> list[tuple[bytes, int]]:
         w, o, c = self.export()
         return [(w[o[i]:o[i + 1]].tobytes(), int(c[i])) for i in range(c.size)]
@@ -381,6 +400,19 @@ class Batch:
 
     def export(self, stream=None):
         return wc_batch_export(self.handle, self.ndocs, _stream_handle(stream))
+
+    def export_into(self, doc_start, doc_n, words, offsets, counts, stream=None) -> tuple[int, int]:
+        """Bulk export into caller-owned host tensors (int64 doc_start and
+        int32 doc_n of ndocs, uint8 words, int64 offsets of n+1, int32
+        counts; pinned ones copy fastest); returns (rows, word bytes)."""
+        n, nb = wc_batch_size(self.handle)
+        if (doc_start.numel() < self.ndocs or doc_n.numel() < self.ndocs or words.numel() < nb
+                or offsets.numel() < n + 1 or counts.numel() < n):
+            raise ValueError("export buffers smaller than the batch")
+        _check(load().wc_batch_export(self.handle, doc_start.data_ptr(), doc_n.data_ptr(), words.data_ptr(),
+                                      offsets.data_ptr(), counts.data_ptr(), _stream_handle(stream)),
+               None, "wc_batch_export")
+        return n, nb
 
     def doc_lists(self):
         """Per-document [(word, count)] lists from one bulk export."""
@@ -478,11 +510,27 @@ class Counter:
             opts = tuple(max(1, int(v)) * 4 for v in base)
         raise WcError(WC_ERR_CAPACITY, "capacity retries exhausted")
 
-    def count_batched(self, text, offsets, h_offsets, classes=None, nclasses: int = 0, stream=None) -> Batch:
+    def count_batched(self, text, offsets, h_offsets, classes=None, nclasses: int = 0, stream=None,
+                      exact: bool = False) -> Batch:
         s = _stream_handle(stream)
         return Batch(wc_count_batched(self.ctx, text.data_ptr(), offsets.data_ptr(), h_offsets,
                                       int(h_offsets.size - 1), classes.data_ptr() if classes is not None else None,
-                                      nclasses, s), int(h_offsets.size - 1), counter=self)
+                                      nclasses, s, WC_BATCH_EXACT_BOUNDS if exact else 0),
+                     int(h_offsets.size - 1), counter=self)
+
+    def count_batched_checked(self, text, offsets, h_offsets, classes=None, nclasses: int = 0,
+                              stream=None) -> Batch:
+        """count_batched() that waits for the result and, on WC_ERR_CAPACITY,
+        counts again with capacities at the exact bounds (which cannot
+        overflow)."""
+        b = self.count_batched(text, offsets, h_offsets, classes, nclasses, stream)
+        st = b.status()
+        if st == WC_ERR_CAPACITY:
+            b.free()
+            b = self.count_batched(text, offsets, h_offsets, classes, nclasses, stream, exact=True)
+            st = b.status()
+        _check(st, self.ctx, "count_batched")
+        return b
 
     def plan(self, h_offsets, nclasses: int = 0, stream=None) -> "Plan":
         return Plan(self, h_offsets, nclasses, stream)

@@ -21,7 +21,7 @@ def ctr():
     c.close()
 
 
-def run_batched(ctr, text: np.ndarray, offsets: np.ndarray, classes=None, nclasses=0):
+def run_batched(ctr, text: np.ndarray, offsets: np.ndarray, classes=None, nclasses=0, checked=False):
     import torch
     dev = torch.device("cuda:0")
     t = torch.from_numpy(np.ascontiguousarray(text, dtype=np.uint8)).to(dev) if text.size else \
@@ -29,8 +29,28 @@ def run_batched(ctr, text: np.ndarray, offsets: np.ndarray, classes=None, nclass
     o = torch.from_numpy(np.ascontiguousarray(offsets, dtype=np.uint64).view(np.int64)).to(dev)
     cl = torch.from_numpy(np.ascontiguousarray(classes, dtype=np.uint32).view(np.int32)).to(dev) \
         if classes is not None else None
-    b = ctr.count_batched(t, o, np.ascontiguousarray(offsets, dtype=np.uint64), cl, nclasses)
+    h = np.ascontiguousarray(offsets, dtype=np.uint64)
+    b = ctr.count_batched_checked(t, o, h, cl, nclasses) if checked else ctr.count_batched(t, o, h, cl, nclasses)
     return b, (t, o, cl)
+
+
+def test_dense_documents_recount_at_exact_bounds(ctr):
+    """Documents denser in distinct words than the capacity estimate (a
+    three-byte word per token): the estimated count reports
+    WC_ERR_CAPACITY, the count at the exact bounds is exact."""
+    from paper_2206_05269_gb300 import wc
+    rng = np.random.default_rng(5)
+    vocab = [bytes([97 + i % 26, 97 + (i // 26) % 26]) for i in range(676)]
+    docs = [b" ".join(vocab[w] for w in rng.permutation(676)[:int(rng.integers(300, 676))]) for _ in range(40)]
+    text = np.frombuffer(b"".join(docs), np.uint8)
+    offs = np.cumsum([0] + [len(d) for d in docs]).astype(np.uint64)
+    r = oracle.count(text, offs)
+    b, keep = run_batched(ctr, text, offs)
+    assert b.status() == wc.WC_ERR_CAPACITY
+    b.free()
+    b, keep = run_batched(ctr, text, offs, checked=True)
+    check_docs(b, r, len(docs))
+    assert_same(b.table(wc.WC_TABLE_GLOBAL).export(), r.glob(), "global")
 
 
 def check_docs(b, r, ndocs, sample=None):
@@ -76,6 +96,49 @@ def test_class_workload_tables_and_ratio(ctr):
         ctab = r.cls(k)
         got = [(ctab.word(int(i)), int(a), int(o)) for i, a, o in zip(idx, cin, cout)]
         assert got == want, f"class {k} ratio ranking"
+
+
+def check_ratio(ctr, b, r, cls, k):
+    from paper_2206_05269_gb300 import wc
+    idx, cin, cout = wc.wc_class_ratio_topk(ctr.ctx, b.handle, cls, k, 0)
+    want = r.ratio_topk(cls, k)
+    ctab = r.cls(cls)
+    got = [(ctab.word(int(i)), int(a), int(o)) for i, a, o in zip(idx, cin, cout)]
+    assert got == want, f"class {cls}, k={k}: ratio ranking"
+
+
+def test_ratio_topk_every_k(ctr):
+    """The ranking for k across the selection's regimes: one sorted slice,
+    several rounds of slices, the largest k the rounds take (512), the
+    arg-best path above it, and k at and above the class's size."""
+    c = corpus.generate("classes", ndocs=120)
+    r = oracle.count(c.text, c.offsets, c.classes, c.nclasses)
+    b, keep = run_batched(ctr, c.text, c.offsets, c.classes, c.nclasses)
+    for cls in range(c.nclasses):
+        n = len(r.cls(cls).counts)
+        for k in (1, 7, 50, 511, 512, 513, 700, n, n + 5):
+            check_ratio(ctr, b, r, cls, k)
+
+
+def test_ratio_topk_ties(ctr):
+    """Many equal ratios (every class draws from one small vocabulary): the
+    order falls to cin, then to the word."""
+    rng = np.random.default_rng(11)
+    vocab = [bytes([97 + i % 26, 97 + (i // 26) % 26]) for i in range(1500)]
+    docs, classes = [], []
+    for d in range(60):
+        words = rng.choice(len(vocab), int(rng.integers(50, 400)))
+        docs.append(b" ".join(vocab[w] for w in words))
+        classes.append(d % 3)
+    text = np.frombuffer(b"\n".join(docs) + b"\n", np.uint8)
+    lens = [len(d) + 1 for d in docs]
+    offs = np.cumsum([0] + lens).astype(np.uint64)
+    cl = np.array(classes, np.uint32)
+    r = oracle.count(text, offs, cl, 3)
+    b, keep = run_batched(ctr, text, offs, cl, 3, checked=True)
+    for cls in range(3):
+        for k in (3, 64, 300, 512, 900, 5000):
+            check_ratio(ctr, b, r, cls, k)
 
 
 def test_edges_long_words_spills_and_splits(ctr):
