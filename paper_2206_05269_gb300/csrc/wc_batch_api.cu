@@ -601,8 +601,11 @@ static wc_status build_tables_at(wc_batch *b, const std::vector<uint64_t> &est, 
     }
     std::vector<GTable> g(std::max<uint32_t>(b->nclasses, 1));
     for (uint32_t c = 0; c < b->nclasses; c++) g[c] = scr[c].gtable(tabs[c]->dt.d_status);
+    // device copies: the class hash tables, then the sort jobs of all tables
+    const size_t gbytes = (sizeof(GTable) * g.size() + 255) & ~(size_t)255;
+    const size_t dbytes = gbytes + finish_tables_job_bytes((int)nt);
     void *dg = nullptr;
-    if ((st = ctx->alloc(&dg, sizeof(GTable) * g.size(), s)) != WC_OK) {
+    if ((st = ctx->alloc(&dg, dbytes, s)) != WC_OK) {
         cleanup(nt);
         for (auto *t : tabs) free_owned_table(t);
         tabs.clear();
@@ -612,14 +615,15 @@ static wc_status build_tables_at(wc_batch *b, const std::vector<uint64_t> &est, 
     const GTable gg = b->gscratch.gtable(tabs[b->nclasses]->dt.d_status);
     if (b->ndocs) k_batch_tables<<<b->ndocs, 128, 0, s>>>(b->args, b->d_class, static_cast<GTable *>(dg), b->nclasses, gg);
     cudaError_t e = cudaGetLastError();
-    for (uint32_t c = 0; c < b->nclasses && e == cudaSuccess; c++)
-        e = finish_table(g[c], scr[c].gcap8, scr[c].gcap, scr[c].glcap, scr[c].ss, tabs[c]->dt, s);
-    if (e == cudaSuccess)
-        e = finish_table(gg, b->gscratch.gcap8, b->gscratch.gcap, b->gscratch.glcap, b->gscratch.ss,
-                         tabs[b->nclasses]->dt, s);
-    ctx->launches += 1 + (uint64_t)nt * finish_table_launches();
+    std::vector<FinishSpec> spec(nt);
+    for (uint32_t c = 0; c < nt; c++) {
+        CountScratch &cs = c < b->nclasses ? scr[c] : b->gscratch;
+        spec[c] = FinishSpec{c < b->nclasses ? g[c] : gg, cs.gcap8, cs.gcap, cs.glcap, &cs.ss, &tabs[c]->dt};
+    }
+    if (e == cudaSuccess) e = finish_tables(spec.data(), (int)nt, static_cast<uint8_t *>(dg) + gbytes, s);
+    ctx->launches += 1 + (uint64_t)finish_tables_launches((int)nt);
     cleanup(nt);
-    ctx->release(dg, sizeof(GTable) * g.size(), s);
+    ctx->release(dg, dbytes, s);
     for (auto *t : tabs) table_mark_done(t, s);
     if (e != cudaSuccess) return ctx->cuda_fail(e, "class/global tables");
     *overflow = false;

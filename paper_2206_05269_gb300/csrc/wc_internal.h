@@ -89,6 +89,27 @@ int finish_table_launches();
 cudaError_t finish_table(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_t glcap, SortScratch &ss,
                          DevTable &out, cudaStream_t s);
 
+// One table's sort arguments (device copies of them for finish_tables).
+struct SortJob {
+    SortScratch s;
+    const unsigned long long *meta;
+    LongView v;
+    DevTable out;
+};
+// finish_table for n tables at once: each table's compaction, then every
+// sort pass and the final gather as one launch over all n tables (grid.y).
+// d_jobs: device memory of finish_tables_job_bytes(n), alive until the
+// stream has run the launches.  finish_tables_launches(n) kernels.
+struct FinishSpec {
+    GTable g;
+    uint64_t gcap8, gcap, glcap;
+    SortScratch *ss;
+    DevTable *out;
+};
+size_t finish_tables_job_bytes(int n);
+int finish_tables_launches(int n);
+cudaError_t finish_tables(const FinishSpec *spec, int n, void *d_jobs, cudaStream_t s);
+
 // Entries of finished tables re-inserted into a global hash table (merge).
 struct MergeSrc {
     const unsigned long long *meta;

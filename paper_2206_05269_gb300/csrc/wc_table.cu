@@ -11,6 +11,9 @@
 // 16-letter prefix by their remaining bytes.  Every pass is stable, so the
 // final order is (count desc, word asc).  Digits that are equal for every
 // element are skipped, detected on the device from one histogram pass.
+#include <algorithm>
+#include <vector>
+
 #include "wc_internal.h"
 
 namespace wc {
@@ -210,6 +213,18 @@ __global__ void k_compact_long(const LSlot *ls, unsigned long long lcap, SortScr
 }
 
 // ---------------------------------------------------------------- radix sort
+// The sort kernels take one table's arguments as their parameter (OneJob) or
+// several tables' from a device array, table blockIdx.y (JobList): a batch's
+// class and global tables are sorted by one launch per pass.
+struct OneJob {
+    SortJob j;
+    __device__ __forceinline__ const SortJob &get() const { return j; }
+};
+struct JobList {
+    const SortJob *j;
+    __device__ __forceinline__ const SortJob &get() const { return j[blockIdx.y]; }
+};
+
 __device__ __forceinline__ uint32_t sort_digit(const SortScratch &s, uint32_t idx, int p) {
     if (p >= kPasses) return (s.doc[idx] >> (8 * (p - kPasses))) & 0xFFu;
     if (p < 8) return (uint32_t)(s.pk[idx] >> (8 * p)) & 0xFFu;
@@ -219,7 +234,10 @@ __device__ __forceinline__ uint32_t sort_digit(const SortScratch &s, uint32_t id
 
 // Packs the prefix keys, and takes the histograms of all digit positions
 // (for skipping constant digits) and the identity permutation.
-__global__ void k_hist_all(SortScratch s, const unsigned long long *meta, int passes) {
+template <class J>
+__global__ void k_hist_all(J job, int passes) {
+    const SortScratch &s = job.get().s;
+    const unsigned long long *meta = job.get().meta;
     __shared__ uint32_t h[kPassesSeg * 256];
     for (int i = threadIdx.x; i < kPassesSeg * 256; i += blockDim.x) h[i] = 0;
     __syncthreads();
@@ -257,7 +275,10 @@ __device__ __forceinline__ bool pass_skipped(const SortScratch &s, int p, unsign
     return __syncthreads_or(mine) != 0;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_pass_count(SortScratch s, int p, const unsigned long long *meta) {
+template <class J>
+__global__ void __launch_bounds__(kSortThreads) k_pass_count(J job, int p) {
+    const SortScratch &s = job.get().s;
+    const unsigned long long *meta = job.get().meta;
     __shared__ uint32_t h[256];
     const unsigned long long n = meta[0];
     const unsigned long long ntiles = (n + kSortTile - 1) / kSortTile;
@@ -287,7 +308,10 @@ __global__ void __launch_bounds__(kSortThreads) k_pass_count(SortScratch s, int 
 // Exclusive scan of the digit-major tile histogram: block d scans digit d's
 // row of tile counts, starting from the number of elements with a smaller
 // digit (from the all-pass histogram).  256 blocks of 256 threads.
-__global__ void __launch_bounds__(256) k_pass_scan(SortScratch s, int p, const unsigned long long *meta) {
+template <class J>
+__global__ void __launch_bounds__(256) k_pass_scan(J job, int p) {
+    const SortScratch &s = job.get().s;
+    const unsigned long long *meta = job.get().meta;
     __shared__ uint32_t part[256];
     __shared__ uint32_t base_s;
     const unsigned long long n = meta[0];
@@ -329,7 +353,10 @@ __global__ void __launch_bounds__(256) k_pass_scan(SortScratch s, int p, const u
 
 // Stable scatter: warp w ranks its 512 consecutive elements in order with
 // match_any; warps are combined in order, so equal digits keep their order.
-__global__ void __launch_bounds__(kSortThreads) k_pass_scatter(SortScratch s, int p, const unsigned long long *meta) {
+template <class J>
+__global__ void __launch_bounds__(kSortThreads) k_pass_scatter(J job, int p) {
+    const SortScratch &s = job.get().s;
+    const unsigned long long *meta = job.get().meta;
     constexpr int WARPS = kSortThreads / 32;
     __shared__ uint32_t wcount[WARPS][256];
     const unsigned long long n = meta[0];
@@ -410,7 +437,11 @@ __device__ __forceinline__ bool tail_less(const LongView &v, uint32_t a, uint32_
 __device__ __forceinline__ bool same_run(const SortScratch &s, uint32_t a, uint32_t b, bool seg) {
     return s.khi[a] == s.khi[b] && s.klo[a] == s.klo[b] && s.cnt[a] == s.cnt[b] && (!seg || s.doc[a] == s.doc[b]);
 }
-__global__ void k_fix_long(SortScratch s, LongView v, const unsigned long long *meta, int passes) {
+template <class J>
+__global__ void k_fix_long(J job, int passes) {
+    const SortScratch &s = job.get().s;
+    const LongView &v = job.get().v;
+    const unsigned long long *meta = job.get().meta;
     const unsigned long long n = meta[0];
     if (meta[1] == 0) return;
     const bool seg = passes > kPasses;
@@ -446,7 +477,10 @@ __device__ __forceinline__ unsigned long long short_len(unsigned long long hi, u
     return 8 - (__ffsll((long long)hi) - 1) / 8;
 }
 
-__global__ void k_gather_final(SortScratch s, DevTable out) {
+template <class J>
+__global__ void k_gather_final(J job) {
+    const SortScratch &s = job.get().s;
+    const DevTable &out = job.get().out;
     const unsigned long long n = out.d_meta[0];
     const uint32_t *perm = s.perm_buf(s.cur[kPasses]);  // unsegmented: count digits are the last
     unsigned long long bytes = 0;
@@ -486,25 +520,31 @@ __global__ void k_meta_snapshot(unsigned long long *meta, int slot) { meta[slot]
 int sort_entries_launches(int passes);
 int finish_table_launches() { return 5 + sort_entries_launches(kPasses) + 1; }
 
+// The passes of one sort, for one table (J = OneJob) or a list of them.
+template <class J>
+static void launch_sort(const J &job, uint64_t cap, int ntab, int passes, cudaStream_t st) {
+    const int sms = sm_count();
+    k_hist_all<<<dim3(grid_for(cap, 256, sms * 2), ntab), 256, 0, st>>>(job, passes);
+    const int ntiles = (int)((cap + kSortTile - 1) / kSortTile);
+    for (int p = 0; p < passes; p++) {
+        k_pass_count<<<dim3(ntiles, ntab), kSortThreads, 0, st>>>(job, p);
+        k_pass_scan<<<dim3(256, ntab), 256, 0, st>>>(job, p);
+        k_pass_scatter<<<dim3(ntiles, ntab), kSortThreads, 0, st>>>(job, p);
+    }
+    k_fix_long<<<dim3(grid_for(cap, 256, sms * 4), ntab), 256, 0, st>>>(job, passes);
+}
+
 // LSD radix sort of the entries in ss (count n = meta[0]) into ss.perm_buf(ss.cur[passes]).
 cudaError_t sort_entries(SortScratch &ss, const unsigned long long *meta, const LongView &v, int passes,
                          cudaStream_t st) {
-    const int sms = sm_count();
-    const uint64_t cap = ss.cap;
-    k_hist_all<<<grid_for(cap, 256, sms * 2), 256, 0, st>>>(ss, meta, passes);
-    const int ntiles = (int)((cap + kSortTile - 1) / kSortTile);
-    for (int p = 0; p < passes; p++) {
-        k_pass_count<<<ntiles, kSortThreads, 0, st>>>(ss, p, meta);
-        k_pass_scan<<<256, 256, 0, st>>>(ss, p, meta);
-        k_pass_scatter<<<ntiles, kSortThreads, 0, st>>>(ss, p, meta);
-    }
-    k_fix_long<<<grid_for(cap, 256, sms * 4), 256, 0, st>>>(ss, v, meta, passes);
+    OneJob job{SortJob{ss, meta, v, DevTable{}}};
+    launch_sort(job, ss.cap, 1, passes, st);
     return cudaGetLastError();
 }
 int sort_entries_launches(int passes) { return 1 + 1 + 3 * passes; }
 
-cudaError_t finish_table(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_t glcap, SortScratch &ss,
-                         DevTable &out, cudaStream_t st) {
+static void launch_compaction(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_t glcap, SortScratch &ss,
+                              DevTable &out, cudaStream_t st) {
     const int sms = sm_count();
     cudaMemsetAsync(ss.hist_all, 0, 4 * kPassesSeg * 256, st);
     cudaMemsetAsync(ss.cur, 0, 4 * 32, st);
@@ -513,10 +553,35 @@ cudaError_t finish_table(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_
     k_compact_short<<<grid_for(gcap, 256, sms * 8), 256, 0, st>>>(g.slots, gcap, ss, out.d_meta);
     k_meta_snapshot<<<1, 1, 0, st>>>(out.d_meta, 6);
     k_compact_long<<<grid_for(glcap, 256, sms * 8), 256, 0, st>>>(g.lslots, glcap, ss, out);
-    LongView v{ss.lref, out.loff, out.llen, out.arena};
-    cudaError_t e = sort_entries(ss, out.d_meta, v, kPasses, st);
+}
+
+cudaError_t finish_table(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_t glcap, SortScratch &ss,
+                         DevTable &out, cudaStream_t st) {
+    launch_compaction(g, gcap8, gcap, glcap, ss, out, st);
+    OneJob job{SortJob{ss, out.d_meta, LongView{ss.lref, out.loff, out.llen, out.arena}, out}};
+    launch_sort(job, ss.cap, 1, kPasses, st);
+    k_gather_final<<<grid_for(ss.cap, 256, sm_count() * 8), 256, 0, st>>>(job);
+    return cudaGetLastError();
+}
+
+size_t finish_tables_job_bytes(int n) { return sizeof(SortJob) * (size_t)(n > 0 ? n : 1); }
+int finish_tables_launches(int n) { return 5 * n + sort_entries_launches(kPasses) + 1; }
+
+cudaError_t finish_tables(const FinishSpec *spec, int n, void *d_jobs, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    std::vector<SortJob> jobs((size_t)n);
+    uint64_t cap = 0;
+    for (int t = 0; t < n; t++) {
+        const FinishSpec &f = spec[t];
+        launch_compaction(f.g, f.gcap8, f.gcap, f.glcap, *f.ss, *f.out, st);
+        jobs[t] = SortJob{*f.ss, f.out->d_meta, LongView{f.ss->lref, f.out->loff, f.out->llen, f.out->arena}, *f.out};
+        cap = std::max<uint64_t>(cap, f.ss->cap);
+    }
+    cudaError_t e = cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(SortJob) * jobs.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
-    k_gather_final<<<grid_for(ss.cap, 256, sms * 8), 256, 0, st>>>(ss, out);
+    JobList list{static_cast<const SortJob *>(d_jobs)};
+    launch_sort(list, cap, n, kPasses, st);
+    k_gather_final<<<dim3(grid_for(cap, 256, sm_count() * 8), n), 256, 0, st>>>(list);
     return cudaGetLastError();
 }
 
