@@ -152,7 +152,19 @@ __global__ void __launch_bounds__(BLOCK, (DocCfg<BLOCK, LOGC1>::MINB)) k_docs(Ba
         const uintptr_t own_lo = tb + it.lo, own_hi = tb + it.hi;
         const uint8_t *dbeg = reinterpret_cast<const uint8_t *>(vb);
         const uint8_t *dend = reinterpret_cast<const uint8_t *>(ve);
-        for (int i = threadIdx.x; i < C::C1; i += BLOCK) stag[i] = 0u;
+        // The slots this item uses: a whole document takes a power of two
+        // of about a quarter of its bytes (at least BLOCK; three quarters of
+        // it may fill before words spill), so that the clearing, merging and
+        // composite passes below scale with the document; ranges take all.
+        uint32_t ceff = C::C1;
+        if (!it.kind) {
+            const unsigned long long want = (it.hi - it.lo) / 4;
+            ceff = BLOCK;
+            while (ceff < (uint32_t)C::C1 && ceff < want) ceff <<= 1;
+        }
+        st.mask = ceff - 1u;
+        st.fill_limit = ceff / 4u * 3u;
+        for (int i = threadIdx.x; i < (int)ceff; i += BLOCK) stag[i] = 0u;
         if (threadIdx.x == 0) {
             sh.lcount = 0;
             sh.nfill = 0;
@@ -165,7 +177,7 @@ __global__ void __launch_bounds__(BLOCK, (DocCfg<BLOCK, LOGC1>::MINB)) k_docs(Ba
             if (have) {
                 const uint32_t p = e >> 5, len = e & 31u;
                 uint4 k = load_key16(win, p, len);
-                if (!shared_insert(st, k, hash_key(k), 1u, C::C1)) {
+                if (!shared_insert(st, k, hash_key(k), 1u, (int)ceff)) {
                     doc_insert_key(a.g, d, k, 1ull);
                     sh.spilled = 1u;
                 }
@@ -299,7 +311,7 @@ __global__ void __launch_bounds__(BLOCK, (DocCfg<BLOCK, LOGC1>::MINB)) k_docs(Ba
 
         if (sh.spilled) {
             // ---- range or overflowing document: add everything to the global tables
-            for (int i = threadIdx.x; i < C::C1; i += BLOCK)
+            for (int i = threadIdx.x; i < (int)ceff; i += BLOCK)
                 if (stag[i] > 1u) doc_insert_key(a.g, d, skey[i], (unsigned long long)scnt[i]);
             for (uint32_t j = threadIdx.x; j < sh.lcount; j += BLOCK)
                 doc_insert_long(a.g, d, reinterpret_cast<const uint8_t *>(laddr[j]), llen[j],
@@ -314,18 +326,18 @@ __global__ void __launch_bounds__(BLOCK, (DocCfg<BLOCK, LOGC1>::MINB)) k_docs(Ba
         // all its copies share one home slot and probe order, so each copy
         // walks from home and adds itself to the first slot holding its key,
         // then marks itself dead (tag 1: probing still passes over it).
-        for (int i = threadIdx.x; i < C::C1; i += BLOCK) {
+        for (int i = threadIdx.x; i < (int)ceff; i += BLOCK) {
             const uint32_t tg = stag[i];
             if (tg <= 1u) continue;
             const uint4 k = skey[i];
-            uint32_t s = (uint32_t)(hash_key(k) >> 40) & (uint32_t)(C::C1 - 1);
-            for (int probe = 0; probe < C::C1 && s != (uint32_t)i && stag[s] != 0u; probe++) {
+            uint32_t s = (uint32_t)(hash_key(k) >> 40) & (ceff - 1u);
+            for (int probe = 0; probe < (int)ceff && s != (uint32_t)i && stag[s] != 0u; probe++) {
                 if (stag[s] == tg && key_eq(skey[s], k)) {
                     atomicAdd(&scnt[s], scnt[i]);
                     stag[i] = 1u;
                     break;
                 }
-                s = (s + 1) & (uint32_t)(C::C1 - 1);
+                s = (s + 1) & (ceff - 1u);
             }
         }
         __syncthreads();
@@ -362,7 +374,7 @@ __global__ void __launch_bounds__(BLOCK, (DocCfg<BLOCK, LOGC1>::MINB)) k_docs(Ba
         // composites in place, and the index list of live entries (its order
         // is fixed by the sort below): one shared atomic per warp and step
         static_assert(C::C1 % BLOCK == 0, "whole steps over the shared table");
-        for (int i0 = 0; i0 < C::C1; i0 += BLOCK) {
+        for (int i0 = 0; i0 < (int)ceff; i0 += BLOCK) {
             const int i = i0 + threadIdx.x;
             const bool live = stag[i] > 1u;
             if (live) {
@@ -398,7 +410,11 @@ __global__ void __launch_bounds__(BLOCK, (DocCfg<BLOCK, LOGC1>::MINB)) k_docs(Ba
         auto key_of = [&](uint32_t s) -> ulonglong2 {
             return s < (uint32_t)C::C1 ? reinterpret_cast<const ulonglong2 *>(skey)[s] : lkey[s - C::C1];
         };
-        // bitonic network over N indices: one thread per compared pair
+        // bitonic network over N indices: one thread per compared pair.  The
+        // pairs of thread t lie in the 64 entries from 64 * (t / 32) when the
+        // distance j is at most 32, so a warp owns the same segments through
+        // consecutive such stages and only a change to or from a wider stage
+        // needs a block-wide barrier.
         for (uint32_t k = 2; k <= N; k <<= 1) {
             for (uint32_t j = k >> 1; j > 0; j >>= 1) {
                 for (uint32_t t = threadIdx.x; t < N / 2; t += BLOCK) {
@@ -408,9 +424,12 @@ __global__ void __launch_bounds__(BLOCK, (DocCfg<BLOCK, LOGC1>::MINB)) k_docs(Ba
                     const bool gt = kx.x != ky.x ? kx.x > ky.x : kx.y > ky.y;  // x after y
                     if (gt == ((i & k) == 0)) { sidx[i] = (uint16_t)y; sidx[ixj] = (uint16_t)x; }
                 }
-                __syncthreads();
+                const uint32_t jn = j > 1 ? j >> 1 : k;  // the next stage's distance
+                if (j <= 32 && jn <= 32) __syncwarp();
+                else __syncthreads();
             }
         }
+        __syncthreads();
         // long words with equal count and prefix: order by their remaining
         // bytes (insertion over each such run; runs are rare and short)
         if (sh.nlong) {
@@ -541,62 +560,120 @@ __device__ __forceinline__ uint32_t doc_of_pos(const unsigned long long *off, ui
 }
 
 __global__ void k_bcompact8(const G8Slot *slots, unsigned long long cap, SortScratch ss, unsigned long long *meta) {
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const unsigned long long k = slots[i].key;
-        if (!k) continue;
-        const unsigned long long pos = atomicAdd(&meta[0], 1ull);
-        const unsigned long long w = restore_letters(k);
-        ss.khi[pos] = be64b((uint32_t)w, (uint32_t)(w >> 32));
-        ss.klo[pos] = 0ull;
-        ss.cnt[pos] = slots[i].cnt;
-        ss.lref[pos] = 0u;
-        ss.doc[pos] = gather_doc(k);
+    __shared__ BlockTake sh;
+    const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x * kScanUnroll;
+    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x * kScanUnroll; b < cap; b += step) {
+        ulonglong2 v[kScanUnroll];
+        uint32_t mine = 0;
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; u++) {
+            const unsigned long long i = b + (unsigned long long)u * blockDim.x + threadIdx.x;
+            v[u] = i < cap ? *reinterpret_cast<const ulonglong2 *>(&slots[i]) : make_ulonglong2(0ull, 0ull);
+            mine += v[u].x != 0ull;
+        }
+        unsigned long long pos = block_take(sh, mine, 0ull, &meta[0], nullptr);
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; u++) {
+            const unsigned long long k = v[u].x;
+            if (!k) continue;
+            const unsigned long long w = restore_letters(k);
+            ss.khi[pos] = be64b((uint32_t)w, (uint32_t)(w >> 32));
+            ss.klo[pos] = 0ull;
+            ss.cnt[pos] = v[u].y;
+            ss.lref[pos] = 0u;
+            ss.doc[pos] = gather_doc(k);
+            pos++;
+        }
     }
 }
 
 __global__ void k_bcompact16(const GSlot *slots, unsigned long long cap, SortScratch ss, unsigned long long *meta) {
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint4 k = slots[i].key;
-        if (key_zero(k)) continue;
-        const unsigned long long lo = ((unsigned long long)k.y << 32) | k.x, hi = ((unsigned long long)k.w << 32) | k.z;
-        const unsigned long long pos = atomicAdd(&meta[0], 1ull);
-        const unsigned long long wl = restore_letters(lo), wh = restore_letters(hi);
-        ss.khi[pos] = be64b((uint32_t)wl, (uint32_t)(wl >> 32));
-        ss.klo[pos] = be64b((uint32_t)wh, (uint32_t)(wh >> 32));
-        ss.cnt[pos] = slots[i].cnt;
-        ss.lref[pos] = 0u;
-        ss.doc[pos] = gather_doc(lo) | (gather_doc(hi) << 24);
+    __shared__ BlockTake sh;
+    const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x * kScanUnroll;
+    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x * kScanUnroll; b < cap; b += step) {
+        uint4 k[kScanUnroll];
+        unsigned long long c[kScanUnroll];
+        uint32_t mine = 0;
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; u++) {
+            const unsigned long long i = b + (unsigned long long)u * blockDim.x + threadIdx.x;
+            k[u] = make_uint4(0, 0, 0, 0);
+            c[u] = 0;
+            if (i < cap) {
+                k[u] = slots[i].key;
+                c[u] = slots[i].cnt;
+            }
+            mine += !key_zero(k[u]);
+        }
+        unsigned long long pos = block_take(sh, mine, 0ull, &meta[0], nullptr);
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; u++) {
+            if (key_zero(k[u])) continue;
+            const unsigned long long lo = ((unsigned long long)k[u].y << 32) | k[u].x;
+            const unsigned long long hi = ((unsigned long long)k[u].w << 32) | k[u].z;
+            const unsigned long long wl = restore_letters(lo), wh = restore_letters(hi);
+            ss.khi[pos] = be64b((uint32_t)wl, (uint32_t)(wl >> 32));
+            ss.klo[pos] = be64b((uint32_t)wh, (uint32_t)(wh >> 32));
+            ss.cnt[pos] = c[u];
+            ss.lref[pos] = 0u;
+            ss.doc[pos] = gather_doc(lo) | (gather_doc(hi) << 24);
+            pos++;
+        }
     }
 }
 
-// One warp per long slot: document from the representative's position, bytes
-// copied (lowercased, 0-terminated) into the batch arena.
+// One lane per long slot, a warp's slots reserving entries, long indices
+// and arena bytes with one atomic each: document from the representative's
+// position, bytes copied (lowercased, 0-terminated) into the batch arena by
+// the slot's lane up to 64 bytes and by the whole warp beyond.
 __global__ void k_bcompact_long(const LSlot *ls, unsigned long long lcap, SortScratch ss, BatchArgs a,
                                 unsigned long long *meta) {
     const int lane = threadIdx.x & 31;
-    const unsigned long long gw = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-    for (unsigned long long w = gw; w < lcap; w += nw) {
-        const unsigned long long h = ls[w].h, addr = ls[w].addr;
-        if (h == 0 && addr == 0) continue;
-        const unsigned long long len = ls[w].len, c = ls[w].cnt;
-        const uint8_t *src = reinterpret_cast<const uint8_t *>(addr);
-        unsigned long long off = 0, lidx = 0, pos = 0;
-        if (lane == 0) {
-            off = atomicAdd(&a.meta[2], len + 1);
-            lidx = atomicAdd(&a.meta[1], 1ull);
-            pos = atomicAdd(&meta[0], 1ull);
-            atomicAdd(&meta[1], 1ull);  // long entries present: the sort orders shared prefixes by full bytes
+    for (unsigned long long w0 = (((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < lcap;
+         w0 += nw * 32) {
+        const unsigned long long w = w0 + lane;
+        unsigned long long h = 0, addr = 0, len = 0, c = 0;
+        if (w < lcap) {
+            h = ls[w].h;
+            addr = ls[w].addr;
+            len = ls[w].len;
+            c = ls[w].cnt;
         }
-        off = __shfl_sync(kFull, off, 0);
-        lidx = __shfl_sync(kFull, lidx, 0);
-        pos = __shfl_sync(kFull, pos, 0);
-        const bool fits = off + len + 1 <= a.arena_cap && lidx < a.lcap;
-        if (fits)
-            for (unsigned long long j = lane; j < len; j += 32) a.arena[off + j] = (uint8_t)(src[j] | 0x20u);
+        const bool occ = !(h == 0 && addr == 0);
+        const uint32_t m = __ballot_sync(kFull, occ);
+        if (!m) continue;
+        const unsigned long long rank = __popc(m & ((1u << lane) - 1u)), nocc = __popc(m);
+        const unsigned long long bytes = occ ? len + 1 : 0ull;
+        unsigned long long incl = bytes;
+        for (int dd = 1; dd < 32; dd <<= 1) {
+            const unsigned long long t = __shfl_up_sync(kFull, incl, dd);
+            if (lane >= dd) incl += t;
+        }
+        const unsigned long long total = __shfl_sync(kFull, incl, 31);
+        unsigned long long boff = 0, blidx = 0, bpos = 0;
         if (lane == 0) {
+            boff = atomicAdd(&a.meta[2], total);
+            blidx = atomicAdd(&a.meta[1], nocc);
+            bpos = atomicAdd(&meta[0], nocc);
+            atomicAdd(&meta[1], nocc);  // long entries present: the sort orders shared prefixes by full bytes
+        }
+        const unsigned long long off = __shfl_sync(kFull, boff, 0) + incl - bytes;
+        const unsigned long long lidx = __shfl_sync(kFull, blidx, 0) + rank;
+        const unsigned long long pos = __shfl_sync(kFull, bpos, 0) + rank;
+        const bool fits = off + len + 1 <= a.arena_cap && lidx < a.lcap;
+        const uint8_t *src = reinterpret_cast<const uint8_t *>(addr);
+        if (occ && fits && len <= 64)
+            for (unsigned long long j = 0; j < len; j++) a.arena[off + j] = (uint8_t)(src[j] | 0x20u);
+        uint32_t big = __ballot_sync(kFull, occ && fits && len > 64);
+        while (big) {
+            const int l = __ffs(big) - 1;
+            big &= big - 1;
+            const uint8_t *bs = reinterpret_cast<const uint8_t *>(__shfl_sync(kFull, addr, l));
+            const unsigned long long bo = __shfl_sync(kFull, off, l), bl = __shfl_sync(kFull, len, l);
+            for (unsigned long long j = lane; j < bl; j += 32) a.arena[bo + j] = (uint8_t)(bs[j] | 0x20u);
+        }
+        if (occ) {
             if (!fits) atomicOr(a.status, ST_OUT_FULL);
             else {
                 a.arena[off + len] = 0;
@@ -666,9 +743,9 @@ cudaError_t launch_segmented_finish(const BatchArgs &a, const GTable &g, uint64_
     cudaMemsetAsync(smeta, 0, 16 * 8, s);
     cudaMemsetAsync(ss.hist_all, 0, 4 * kSortPassesSeg * 256, s);
     cudaMemsetAsync(ss.cur, 0, 4 * 32, s);
-    k_bcompact8<<<gridn(cap8, 256, sms * 8), 256, 0, s>>>(g.slots8, cap8, ss, smeta);
-    k_bcompact16<<<gridn(cap16, 256, sms * 8), 256, 0, s>>>(g.slots, cap16, ss, smeta);
-    k_bcompact_long<<<gridn(caplong * 32, 256, sms * 8), 256, 0, s>>>(g.lslots, caplong, ss, a, smeta);
+    k_bcompact8<<<gridn(cap8, 256 * kScanUnroll, sms * 8), 256, 0, s>>>(g.slots8, cap8, ss, smeta);
+    k_bcompact16<<<gridn(cap16, 256 * kScanUnroll, sms * 8), 256, 0, s>>>(g.slots, cap16, ss, smeta);
+    k_bcompact_long<<<gridn(caplong, 256, sms * 8), 256, 0, s>>>(g.lslots, caplong, ss, a, smeta);
     LongView v{ss.lref, a.loff, a.llen, a.arena};
     cudaError_t e = sort_entries(ss, smeta, v, kSortPassesSeg, s);
     if (e != cudaSuccess) return e;

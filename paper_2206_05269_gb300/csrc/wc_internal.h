@@ -89,6 +89,49 @@ int finish_table_launches();
 cudaError_t finish_table(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_t glcap, SortScratch &ss,
                          DevTable &out, cudaStream_t s);
 
+// Compaction scans read kScanUnroll slots a thread per step (independent
+// loads in flight) and reserve output positions with one atomic per block
+// and step: block_take returns the first of `mine` positions reserved for
+// the calling thread and adds the block's `tok` to *tokens (may be null).
+// Every thread of the block must call it (the loops step block-uniformly).
+constexpr int kScanUnroll = 4;
+struct BlockTake {
+    uint32_t wsum[32];
+    unsigned long long tok[32];
+    unsigned long long base;
+};
+__device__ __forceinline__ unsigned long long block_take(BlockTake &sh, uint32_t mine, unsigned long long tok,
+                                                         unsigned long long *counter, unsigned long long *tokens) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    uint32_t incl = mine;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += t;
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) tok += __shfl_xor_sync(0xFFFFFFFFu, tok, d);
+    if (lane == 31) sh.wsum[warp] = incl;
+    if (lane == 0) sh.tok[warp] = tok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        unsigned long long tt = 0;
+        for (int w = 0; w < nw; w++) {
+            const uint32_t v = sh.wsum[w];
+            sh.wsum[w] = run;
+            run += v;
+            tt += sh.tok[w];
+        }
+        sh.base = run ? atomicAdd(counter, (unsigned long long)run) : 0ull;
+        if (tokens && tt) atomicAdd(tokens, tt);
+    }
+    __syncthreads();
+    const unsigned long long pos = sh.base + sh.wsum[warp] + incl - mine;
+    __syncthreads();
+    return pos;
+}
+
 // One table's sort arguments (device copies of them for finish_tables).
 struct SortJob {
     SortScratch s;

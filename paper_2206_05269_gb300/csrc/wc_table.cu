@@ -58,81 +58,69 @@ void sort_scratch_carve(SortScratch &s, void *base, uint64_t cap) {
 }
 
 // ---------------------------------------------------------------- compaction
-// Position allocation for a block-wide pass: one atomicAdd per block step.
-// Every thread of the block must call it (the block iterates uniformly).
-struct BlockAlloc {
-    uint32_t wcnt[32];
-    unsigned long long base;
-    unsigned long long tok[32];
-};
-__device__ __forceinline__ unsigned long long block_alloc(BlockAlloc &sh, bool occ, unsigned long long add_tokens,
-                                                          unsigned long long *counter, unsigned long long *tokens) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const uint32_t m = __ballot_sync(kFull, occ);
-    unsigned long long t = add_tokens;
-    for (int d = 16; d; d >>= 1) t += __shfl_xor_sync(kFull, t, d);
-    if (lane == 0) { sh.wcnt[warp] = __popc(m); sh.tok[warp] = t; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;
-        unsigned long long tt = 0;
-        for (int w = 0; w < nw; w++) {
-            uint32_t v = sh.wcnt[w];
-            sh.wcnt[w] = run;
-            run += v;
-            tt += sh.tok[w];
-        }
-        sh.base = run ? atomicAdd(counter, (unsigned long long)run) : 0ull;
-        if (tt) atomicAdd(tokens, tt);
-    }
-    __syncthreads();
-    unsigned long long pos = sh.base + sh.wcnt[warp] + __popc(m & lanemask_lt());
-    __syncthreads();
-    return pos;
-}
-
 // Occupied 16-byte-key slots -> entries (big-endian key halves).
 __global__ void k_compact_short(const GSlot *slots, unsigned long long cap, SortScratch ss,
                                 unsigned long long *meta) {
-    __shared__ BlockAlloc sh;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x; b < cap; b += stride) {
-        const unsigned long long i = b + threadIdx.x;
-        uint4 k = make_uint4(0, 0, 0, 0);
-        unsigned long long c = 0;
-        if (i < cap) {
-            k = slots[i].key;
-            c = slots[i].cnt;
+    __shared__ BlockTake sh;
+    const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x * kScanUnroll;
+    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x * kScanUnroll; b < cap; b += step) {
+        uint4 k[kScanUnroll];
+        unsigned long long c[kScanUnroll], tok = 0;
+        uint32_t mine = 0;
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; u++) {
+            const unsigned long long i = b + (unsigned long long)u * blockDim.x + threadIdx.x;
+            k[u] = make_uint4(0, 0, 0, 0);
+            c[u] = 0;
+            if (i < cap) {
+                k[u] = slots[i].key;
+                c[u] = slots[i].cnt;
+            }
+            if (!key_zero(k[u])) {
+                mine++;
+                tok += c[u];
+            }
         }
-        const bool occ = !key_zero(k);
-        unsigned long long pos = block_alloc(sh, occ, occ ? c : 0ull, &meta[0], &meta[3]);
-        if (occ) {
-            ss.khi[pos] = be64(k.x, k.y);
-            ss.klo[pos] = be64(k.z, k.w);
-            ss.cnt[pos] = c;
+        unsigned long long pos = block_take(sh, mine, tok, &meta[0], &meta[3]);
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; u++) {
+            if (key_zero(k[u])) continue;
+            ss.khi[pos] = be64(k[u].x, k[u].y);
+            ss.klo[pos] = be64(k[u].z, k[u].w);
+            ss.cnt[pos] = c[u];
             ss.lref[pos] = 0u;
+            pos++;
         }
     }
 }
 
 // Occupied 8-byte-key slots -> entries.
 __global__ void k_compact8(const G8Slot *slots, unsigned long long cap, SortScratch ss, unsigned long long *meta) {
-    __shared__ BlockAlloc sh;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x; b < cap; b += stride) {
-        const unsigned long long i = b + threadIdx.x;
-        unsigned long long key = 0, c = 0;
-        if (i < cap) {
-            key = slots[i].key;
-            c = slots[i].cnt;
+    __shared__ BlockTake sh;
+    const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x * kScanUnroll;
+    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x * kScanUnroll; b < cap; b += step) {
+        ulonglong2 v[kScanUnroll];
+        unsigned long long tok = 0;
+        uint32_t mine = 0;
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; u++) {
+            const unsigned long long i = b + (unsigned long long)u * blockDim.x + threadIdx.x;
+            v[u] = i < cap ? *reinterpret_cast<const ulonglong2 *>(&slots[i]) : make_ulonglong2(0ull, 0ull);
+            if (v[u].x) {
+                mine++;
+                tok += v[u].y;
+            }
         }
-        const bool occ = key != 0ull;
-        unsigned long long pos = block_alloc(sh, occ, occ ? c : 0ull, &meta[0], &meta[3]);
-        if (occ) {
+        unsigned long long pos = block_take(sh, mine, tok, &meta[0], &meta[3]);
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; u++) {
+            const unsigned long long key = v[u].x;
+            if (!key) continue;
             ss.khi[pos] = be64((uint32_t)key, (uint32_t)(key >> 32));
             ss.klo[pos] = 0ull;
-            ss.cnt[pos] = c;
+            ss.cnt[pos] = v[u].y;
             ss.lref[pos] = 0u;
+            pos++;
         }
     }
 }
@@ -548,9 +536,9 @@ static void launch_compaction(const GTable &g, uint64_t gcap8, uint64_t gcap, ui
     const int sms = sm_count();
     cudaMemsetAsync(ss.hist_all, 0, 4 * kPassesSeg * 256, st);
     cudaMemsetAsync(ss.cur, 0, 4 * 32, st);
-    k_compact8<<<grid_for(gcap8, 256, sms * 8), 256, 0, st>>>(g.slots8, gcap8, ss, out.d_meta);
+    k_compact8<<<grid_for(gcap8, 256 * kScanUnroll, sms * 8), 256, 0, st>>>(g.slots8, gcap8, ss, out.d_meta);
     k_meta_snapshot<<<1, 1, 0, st>>>(out.d_meta, 5);
-    k_compact_short<<<grid_for(gcap, 256, sms * 8), 256, 0, st>>>(g.slots, gcap, ss, out.d_meta);
+    k_compact_short<<<grid_for(gcap, 256 * kScanUnroll, sms * 8), 256, 0, st>>>(g.slots, gcap, ss, out.d_meta);
     k_meta_snapshot<<<1, 1, 0, st>>>(out.d_meta, 6);
     k_compact_long<<<grid_for(glcap, 256, sms * 8), 256, 0, st>>>(g.lslots, glcap, ss, out);
 }
