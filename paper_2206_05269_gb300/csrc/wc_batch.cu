@@ -90,6 +90,68 @@ __device__ __forceinline__ void doc_decompose(ulonglong2 k, unsigned long long *
     *klo = unpack5(((k.x & 0xFFull) << 32) | (k.y >> 32));
 }
 
+// ---------------------------------------------------------------- per-document shared table
+// A document's shared table holds 16-byte keys claimed whole by a 128-bit
+// CAS, so a word can never occupy two slots.  A word of at most 8 letters is
+// stored with byte 8 set to 1 (never a letter), so neither half of a stored
+// key is ever zero: a 16-byte load that shows a zero half is empty or a
+// claim in flight (possibly of this very word), settled by the CAS, which
+// returns the whole key; a load that shows two non-zero halves equal to the
+// word's can only come from that word's slot.
+__device__ __forceinline__ uint4 mark_key(uint4 k) {
+    if ((k.z | k.w) == 0u) k.z = 1u;
+    return k;
+}
+__device__ __forceinline__ uint4 unmark_key(uint4 k) {
+    if (k.z == 1u && k.w == 0u) k.z = 0u;
+    return k;
+}
+__device__ __forceinline__ ulonglong2 lds128(const uint4 *p) {
+    ulonglong2 v;
+    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "r"((uint32_t)__cvta_generic_to_shared(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint4 cas128_shared(uint4 *p, uint4 val) {  // compare with zero
+    const uint64_t v0 = ((uint64_t)val.y << 32) | val.x, v1 = ((uint64_t)val.w << 32) | val.z;
+    uint64_t r0, r1;
+    asm volatile(
+        "{\n\t.reg .b128 c, v, d;\n\t"
+        "mov.b128 c, {%2, %2};\n\t"
+        "mov.b128 v, {%3, %4};\n\t"
+        "atom.relaxed.cta.shared::cta.cas.b128 d, [%5], c, v;\n\t"
+        "mov.b128 {%0, %1}, d;\n\t}"
+        : "=l"(r0), "=l"(r1)
+        : "l"(0ull), "l"(v0), "l"(v1), "r"((uint32_t)__cvta_generic_to_shared(p))
+        : "memory");
+    return make_uint4((uint32_t)r0, (uint32_t)(r0 >> 32), (uint32_t)r1, (uint32_t)(r1 >> 32));
+}
+// Adds 1 to marked key km from home slot s; false when the word must spill
+// (the probe limit, or an empty slot found with the table filled to its limit).
+__device__ __forceinline__ bool doc_table_add(uint4 *skey, uint32_t *scnt, uint32_t *nfill, uint32_t mask,
+                                              uint32_t fill_limit, uint4 km, uint32_t s, int max_probe) {
+    const unsigned long long k0 = ((unsigned long long)km.y << 32) | km.x, k1 = ((unsigned long long)km.w << 32) | km.z;
+    for (int probe = 0; probe < max_probe; probe++) {
+        const ulonglong2 c = lds128(skey + s);
+        bool hit = c.x == k0 && c.y == k1;
+        if (!hit && (c.x == 0ull || c.y == 0ull)) {
+            if (c.x == 0ull && c.y == 0ull && *(volatile uint32_t *)nfill >= fill_limit) return false;
+            const uint4 old = cas128_shared(skey + s, km);
+            if (key_zero(old)) {
+                atomicAdd(nfill, 1u);
+                hit = true;
+            } else {
+                hit = key_eq(old, km);
+            }
+        }
+        if (hit) {
+            atomicAdd(scnt + s, 1u);
+            return true;
+        }
+        s = (s + 1u) & mask;
+    }
+    return false;
+}
+
 // ---------------------------------------------------------------- per-document kernel
 template <int BLOCK, int LOGC1>
 struct DocCfg {
@@ -101,7 +163,7 @@ struct DocCfg {
     static constexpr int LCAP = 64;            // distinct long words per document in shared memory
     static constexpr uint32_t FILL = C1 * 3 / 4;
     static constexpr size_t SMEM = (size_t)WINB + (size_t)W * TOKCAP * 4 +  // window + queues (sort buffer)
-                                   (size_t)C1 * 16 + (size_t)C1 * 4 + (size_t)C1 * 4 +  // keys, counts, tags
+                                   (size_t)C1 * 16 + (size_t)C1 * 4 +  // keys, counts
                                    (size_t)LCAP * (8 + 8 + 4 + 4 + 16) + 16 + 64;
     static_assert((size_t)WINB + (size_t)W * TOKCAP * 4 >= (size_t)C1 * 2, "sort buffer must fit");
     // blocks per SM that the shared memory allows: the register budget follows
@@ -129,8 +191,7 @@ __global__ void __launch_bounds__(BLOCK, (DocCfg<BLOCK, LOGC1>::MINB)) k_docs(Ba
     uint16_t *sidx = reinterpret_cast<uint16_t *>(smem);  // sort buffer, reuses window + queues
     uint4 *skey = reinterpret_cast<uint4 *>(smem + C::WINB + (size_t)C::W * C::TOKCAP * 4);
     uint32_t *scnt = reinterpret_cast<uint32_t *>(skey + C::C1);
-    uint32_t *stag = scnt + C::C1;
-    unsigned long long *laddr = reinterpret_cast<unsigned long long *>(stag + C::C1);
+    unsigned long long *laddr = reinterpret_cast<unsigned long long *>(scnt + C::C1);
     unsigned long long *llen = laddr + C::LCAP;
     uint32_t *lcnt = reinterpret_cast<uint32_t *>(llen + C::LCAP);
     uint32_t *lrank = lcnt + C::LCAP;
@@ -138,7 +199,6 @@ __global__ void __launch_bounds__(BLOCK, (DocCfg<BLOCK, LOGC1>::MINB)) k_docs(Ba
     __shared__ DocShared sh;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *tok = tokall + warp * C::TOKCAP;
-    STable st{stag, skey, scnt, &sh.nfill, (uint32_t)(C::C1 - 1), C::FILL};
     const uintptr_t tb = reinterpret_cast<uintptr_t>(a.text);
 
     for (;;) {
@@ -162,9 +222,11 @@ __global__ void __launch_bounds__(BLOCK, (DocCfg<BLOCK, LOGC1>::MINB)) k_docs(Ba
             ceff = BLOCK;
             while (ceff < (uint32_t)C::C1 && ceff < want) ceff <<= 1;
         }
-        st.mask = ceff - 1u;
-        st.fill_limit = ceff / 4u * 3u;
-        for (int i = threadIdx.x; i < (int)ceff; i += BLOCK) stag[i] = 0u;
+        const uint32_t fill_limit = ceff / 4u * 3u;
+        for (int i = threadIdx.x; i < (int)ceff; i += BLOCK) {
+            skey[i] = make_uint4(0u, 0u, 0u, 0u);
+            scnt[i] = 0u;
+        }
         if (threadIdx.x == 0) {
             sh.lcount = 0;
             sh.nfill = 0;
@@ -177,7 +239,8 @@ __global__ void __launch_bounds__(BLOCK, (DocCfg<BLOCK, LOGC1>::MINB)) k_docs(Ba
             if (have) {
                 const uint32_t p = e >> 5, len = e & 31u;
                 uint4 k = load_key16(win, p, len);
-                if (!shared_insert(st, k, hash_key(k), 1u, (int)ceff)) {
+                if (!doc_table_add(skey, scnt, &sh.nfill, ceff - 1u, fill_limit, mark_key(k),
+                                   (uint32_t)(hash_key(k) >> 40) & (ceff - 1u), (int)ceff)) {
                     doc_insert_key(a.g, d, k, 1ull);
                     sh.spilled = 1u;
                 }
@@ -312,7 +375,7 @@ __global__ void __launch_bounds__(BLOCK, (DocCfg<BLOCK, LOGC1>::MINB)) k_docs(Ba
         if (sh.spilled) {
             // ---- range or overflowing document: add everything to the global tables
             for (int i = threadIdx.x; i < (int)ceff; i += BLOCK)
-                if (stag[i] > 1u) doc_insert_key(a.g, d, skey[i], (unsigned long long)scnt[i]);
+                if (!key_zero(skey[i])) doc_insert_key(a.g, d, unmark_key(skey[i]), (unsigned long long)scnt[i]);
             for (uint32_t j = threadIdx.x; j < sh.lcount; j += BLOCK)
                 doc_insert_long(a.g, d, reinterpret_cast<const uint8_t *>(laddr[j]), llen[j],
                                 (unsigned long long)lcnt[j], dbeg, dend);
@@ -321,26 +384,6 @@ __global__ void __launch_bounds__(BLOCK, (DocCfg<BLOCK, LOGC1>::MINB)) k_docs(Ba
             continue;
         }
 
-        // ---- whole document: merge duplicate entries of the shared table.  A
-        // word may sit in two slots (an insert skips a slot being written);
-        // all its copies share one home slot and probe order, so each copy
-        // walks from home and adds itself to the first slot holding its key,
-        // then marks itself dead (tag 1: probing still passes over it).
-        for (int i = threadIdx.x; i < (int)ceff; i += BLOCK) {
-            const uint32_t tg = stag[i];
-            if (tg <= 1u) continue;
-            const uint4 k = skey[i];
-            uint32_t s = (uint32_t)(hash_key(k) >> 40) & (ceff - 1u);
-            for (int probe = 0; probe < (int)ceff && s != (uint32_t)i && stag[s] != 0u; probe++) {
-                if (stag[s] == tg && key_eq(skey[s], k)) {
-                    atomicAdd(&scnt[s], scnt[i]);
-                    stag[i] = 1u;
-                    break;
-                }
-                s = (s + 1) & (ceff - 1u);
-            }
-        }
-        __syncthreads();
         // merge duplicate long entries (warp 0)
         const uint32_t nl = sh.lcount;
         if (warp == 0) {
@@ -376,9 +419,10 @@ __global__ void __launch_bounds__(BLOCK, (DocCfg<BLOCK, LOGC1>::MINB)) k_docs(Ba
         static_assert(C::C1 % BLOCK == 0, "whole steps over the shared table");
         for (int i0 = 0; i0 < (int)ceff; i0 += BLOCK) {
             const int i = i0 + threadIdx.x;
-            const bool live = stag[i] > 1u;
+            const uint4 km = skey[i];
+            const bool live = !key_zero(km);
             if (live) {
-                const uint4 k = skey[i];
+                const uint4 k = unmark_key(km);
                 reinterpret_cast<ulonglong2 *>(skey)[i] =
                     doc_composite(be64b(k.x, k.y), be64b(k.z, k.w), scnt[i], false, 0u);
             }
