@@ -411,7 +411,6 @@ __global__ void __launch_bounds__(BLOCK, (DocCfg<BLOCK, LOGC1>::MINB)) k_docs(Ba
         if (threadIdx.x == 0) {
             sh.nent = 0;
             sh.nlong = 0;
-            lkey[C::LCAP] = make_ulonglong2(~0ull, ~0ull);  // the padding entry sorts last
         }
         __syncthreads();
         // composites in place, and the index list of live entries (its order
@@ -448,28 +447,32 @@ __global__ void __launch_bounds__(BLOCK, (DocCfg<BLOCK, LOGC1>::MINB)) k_docs(Ba
         const uint32_t n = sh.nent;
         uint32_t N = 1;
         while (N < n) N <<= 1;
-        constexpr uint16_t kPad = (uint16_t)(C::C1 + C::LCAP);
-        for (uint32_t i = n + threadIdx.x; i < N; i += BLOCK) sidx[i] = kPad;
         __syncthreads();
         auto key_of = [&](uint32_t s) -> ulonglong2 {
             return s < (uint32_t)C::C1 ? reinterpret_cast<const ulonglong2 *>(skey)[s] : lkey[s - C::C1];
         };
-        // bitonic network over N indices: one thread per compared pair.  The
-        // pairs of thread t lie in the 64 entries from 64 * (t / 32) when the
-        // distance j is at most 32, so a warp owns the same segments through
-        // consecutive such stages and only a change to or from a wider stage
-        // needs a block-wide barrier.
+        // Bitonic network over N = 2^m >= n positions, every merge ascending:
+        // its first stage compares each position of a block's lower half with
+        // its mirror in the upper half, the later stages with the position j
+        // above.  Positions from n on stand for entries above every real
+        // one, so a pair that reaches one never swaps and is skipped: the
+        // padding is never touched.  The pairs of thread t lie in the 64
+        // positions from 64 * (t / 32) while a stage works within blocks of
+        // at most 64, so a warp owns the same positions through consecutive
+        // such stages and only a change to or from a wider stage needs a
+        // block-wide barrier.
         for (uint32_t k = 2; k <= N; k <<= 1) {
             for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                const bool mirror = j == (k >> 1);
                 for (uint32_t t = threadIdx.x; t < N / 2; t += BLOCK) {
-                    const uint32_t i = 2 * t - (t & (j - 1)), ixj = i + j;
-                    const uint32_t x = sidx[i], y = sidx[ixj];
+                    const uint32_t i = 2 * t - (t & (j - 1)), q = mirror ? (i ^ (k - 1)) : i + j;
+                    if (q >= n) continue;
+                    const uint32_t x = sidx[i], y = sidx[q];
                     const ulonglong2 kx = key_of(x), ky = key_of(y);
-                    const bool gt = kx.x != ky.x ? kx.x > ky.x : kx.y > ky.y;  // x after y
-                    if (gt == ((i & k) == 0)) { sidx[i] = (uint16_t)y; sidx[ixj] = (uint16_t)x; }
+                    if (ky.x != kx.x ? ky.x < kx.x : ky.y < kx.y) { sidx[i] = (uint16_t)y; sidx[q] = (uint16_t)x; }
                 }
-                const uint32_t jn = j > 1 ? j >> 1 : k;  // the next stage's distance
-                if (j <= 32 && jn <= 32) __syncwarp();
+                const uint32_t span = 2 * j, span_next = j > 1 ? j : 2 * k;  // block sizes of this and the next stage
+                if (span <= 64 && span_next <= 64) __syncwarp();
                 else __syncthreads();
             }
         }
