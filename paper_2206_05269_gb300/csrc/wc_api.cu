@@ -151,13 +151,15 @@ void wc_ctx::tune_load() {
     };
     num("small", &tuned_small);
     num("medium", &tuned_medium);
+    num("large", &tuned_large);
 }
 
 void wc_ctx::tune_save() const {
     if (tune_cache_path.empty()) return;
     FILE *f = fopen(tune_cache_path.c_str(), "wb");
     if (!f) return;
-    fprintf(f, "{\"%s\": {\"small\": %d, \"medium\": %d}}\n", gpu_name.c_str(), tuned_small, tuned_medium);
+    fprintf(f, "{\"%s\": {\"small\": %d, \"medium\": %d, \"large\": %d}}\n", gpu_name.c_str(), tuned_small,
+            tuned_medium, tuned_large);
     fclose(f);
 }
 

@@ -748,19 +748,43 @@ __global__ void k_seg_base(BatchArgs a, unsigned long long *meta) {
     }
 }
 
+// The sorted (document, word) entries -> the CSR output, and each
+// document's first row; kScanUnroll entries a thread per step, all loads
+// issued before the stores.
 __global__ void k_seg_write(SortScratch ss, BatchArgs a, const unsigned long long *meta, int passes) {
     const unsigned long long n = meta[0], base = meta[8];
     if (!meta[9]) return;
     const uint32_t *perm = ss.perm_buf(ss.cur[passes]);
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint32_t e = perm[i];
-        a.out_khi[base + i] = ss.khi[e];
-        a.out_klo[base + i] = ss.klo[e];
-        a.out_cnt[base + i] = (uint32_t)ss.cnt[e];
-        a.out_lref[base + i] = ss.lref[e];
-        const uint32_t d = ss.doc[e];
-        if (i == 0 || ss.doc[perm[i - 1]] != d) a.doc_start[d] = base + i;
+    const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x * kScanUnroll;
+    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x * kScanUnroll; b < n; b += step) {
+        uint32_t e[kScanUnroll], ep[kScanUnroll];
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; u++) {
+            const unsigned long long i = b + (unsigned long long)u * blockDim.x + threadIdx.x;
+            e[u] = i < n ? perm[i] : 0u;
+            ep[u] = i < n && i > 0 ? perm[i - 1] : 0u;
+        }
+        unsigned long long kh[kScanUnroll], kl[kScanUnroll], c[kScanUnroll];
+        uint32_t lr[kScanUnroll], d[kScanUnroll], dp[kScanUnroll];
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; u++) {
+            kh[u] = ss.khi[e[u]];
+            kl[u] = ss.klo[e[u]];
+            c[u] = ss.cnt[e[u]];
+            lr[u] = ss.lref[e[u]];
+            d[u] = ss.doc[e[u]];
+            dp[u] = ss.doc[ep[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; u++) {
+            const unsigned long long i = b + (unsigned long long)u * blockDim.x + threadIdx.x;
+            if (i >= n) continue;
+            a.out_khi[base + i] = kh[u];
+            a.out_klo[base + i] = kl[u];
+            a.out_cnt[base + i] = (uint32_t)c[u];
+            a.out_lref[base + i] = lr[u];
+            if (i == 0 || dp[u] != d[u]) a.doc_start[d[u]] = base + i;
+        }
     }
 }
 
@@ -768,10 +792,20 @@ __global__ void k_seg_ends(SortScratch ss, BatchArgs a, const unsigned long long
     const unsigned long long n = meta[0], base = meta[8];
     if (!meta[9]) return;
     const uint32_t *perm = ss.perm_buf(ss.cur[passes]);
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint32_t d = ss.doc[perm[i]];
-        if (i + 1 == n || ss.doc[perm[i + 1]] != d) a.doc_n[d] = (uint32_t)(base + i + 1 - a.doc_start[d]);
+    const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x * kScanUnroll;
+    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x * kScanUnroll; b < n; b += step) {
+        uint32_t d[kScanUnroll], dn[kScanUnroll];
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; u++) {
+            const unsigned long long i = b + (unsigned long long)u * blockDim.x + threadIdx.x;
+            d[u] = i < n ? ss.doc[perm[i]] : 0u;
+            dn[u] = i + 1 < n ? ss.doc[perm[i + 1]] : ~0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; u++) {
+            const unsigned long long i = b + (unsigned long long)u * blockDim.x + threadIdx.x;
+            if (i < n && dn[u] != d[u]) a.doc_n[d[u]] = (uint32_t)(base + i + 1 - a.doc_start[d[u]]);
+        }
     }
 }
 
@@ -797,8 +831,8 @@ cudaError_t launch_segmented_finish(const BatchArgs &a, const GTable &g, uint64_
     cudaError_t e = sort_entries(ss, smeta, v, kSortPassesSeg, s);
     if (e != cudaSuccess) return e;
     k_seg_base<<<1, 1, 0, s>>>(a, smeta);
-    k_seg_write<<<gridn(ss.cap, 256, sms * 8), 256, 0, s>>>(ss, a, smeta, kSortPassesSeg);
-    k_seg_ends<<<gridn(ss.cap, 256, sms * 8), 256, 0, s>>>(ss, a, smeta, kSortPassesSeg);
+    k_seg_write<<<gridn(ss.cap, 256 * kScanUnroll, sms * 8), 256, 0, s>>>(ss, a, smeta, kSortPassesSeg);
+    k_seg_ends<<<gridn(ss.cap, 256 * kScanUnroll, sms * 8), 256, 0, s>>>(ss, a, smeta, kSortPassesSeg);
     return cudaGetLastError();
 }
 int segmented_finish_launches() { return 3 + sort_entries_launches(kSortPassesSeg) + 3; }

@@ -15,6 +15,7 @@ using namespace wc;
 namespace {
 
 constexpr uint64_t kSmallMax = 8 << 10;     // whole documents up to 8 KB: small shape
+constexpr uint64_t kMediumMax = 32 << 10;   // whole documents up to 32 KB: medium shape; larger: large shape
 constexpr uint64_t kSplitMin = 64 << 10;    // documents above 64 KB are split into ranges
 constexpr uint64_t kRange = 32 << 10;       // byte range per item of a split document
 constexpr uint32_t kMaxDocs = 1u << 24;     // (document, word) keys carry 24 document bits
@@ -59,8 +60,8 @@ struct wc_batch {
     uint32_t *d_class = nullptr;  // copy of the classes
     // planning
     std::vector<DocItem> items;
-    uint32_t nsmall = 0;
-    int shape_small = 1, shape_medium = 4;
+    uint32_t nsmall = 0, nmedium = 0;  // items: small, then medium, then large
+    int shape_small = 1, shape_medium = 3, shape_large = 4;
     uint64_t cap8 = 0, cap16 = 0, caplong = 0;
     BatchScratch scr;
     // after sync
@@ -193,7 +194,7 @@ static wc_status batch_plan(wc_ctx *ctx, const uint64_t *h_offsets, uint32_t ndo
     b->ctx = ctx;
     b->ndocs = ndocs;
     b->nclasses = nclasses;
-    std::vector<DocItem> small, medium;
+    std::vector<DocItem> small, medium, large;
     uint64_t out_est = 0, glob_est = 0, long_est = 0, total = 0;
     for (uint32_t d = 0; d < ndocs; d++) {
         const uint64_t lo = h_offsets[d], hi = h_offsets[d + 1], s = hi - lo;
@@ -203,18 +204,22 @@ static wc_status batch_plan(wc_ctx *ctx, const uint64_t *h_offsets, uint32_t ndo
         long_est += exact ? s / 18 + 1 : std::min<uint64_t>(s / 18 + 1, e / 8 + 2);
         total += s;
         if (s <= kSmallMax) small.push_back({lo, hi, d, 0});
-        else if (s <= kSplitMin) medium.push_back({lo, hi, d, 0});
+        else if (s <= kMediumMax) medium.push_back({lo, hi, d, 0});
+        else if (s <= kSplitMin) large.push_back({lo, hi, d, 0});
         else {
             glob_est += e;
-            for (uint64_t r = lo; r < hi; r += kRange) medium.push_back({r, std::min(hi, r + kRange), d, 1});
+            for (uint64_t r = lo; r < hi; r += kRange) large.push_back({r, std::min(hi, r + kRange), d, 1});
         }
     }
     auto by_size = [](const DocItem &x, const DocItem &y) { return x.hi - x.lo > y.hi - y.lo; };
     std::stable_sort(small.begin(), small.end(), by_size);
     std::stable_sort(medium.begin(), medium.end(), by_size);
+    std::stable_sort(large.begin(), large.end(), by_size);
     b->nsmall = (uint32_t)small.size();
+    b->nmedium = (uint32_t)medium.size();
     b->items = small;
     b->items.insert(b->items.end(), medium.begin(), medium.end());
+    b->items.insert(b->items.end(), large.begin(), large.end());
     b->args.out_cap = out_est + 1024;
     b->args.lcap = long_est + 1024;
     b->args.arena_cap = exact ? total + b->args.lcap + 65536 : b->args.lcap * 24 + 65536;
@@ -226,6 +231,7 @@ static wc_status batch_plan(wc_ctx *ctx, const uint64_t *h_offsets, uint32_t ndo
     b->caplong = pow2_ge(exact ? 2 * long_est + (1u << 14) : glob_est / 8 + (1u << 14));
     b->shape_small = ctx->tuned_small;
     b->shape_medium = ctx->tuned_medium;
+    b->shape_large = ctx->tuned_large;
     *out = b;
     return WC_OK;
 }
@@ -286,6 +292,7 @@ static void batch_release_scratch(wc_batch *b, cudaStream_t stream) {
 // allocations, no host copies).
 static cudaError_t batch_enqueue(wc_batch *b, const uint8_t *d_text, const uint64_t *d_offsets,
                                  const uint32_t *d_class, cudaStream_t stream, int shape_small, int shape_medium,
+                                 int shape_large,
                                  uint64_t *launches) {
     BatchArgs &a = b->args;
     const size_t nd = std::max<uint32_t>(b->ndocs, 1);
@@ -312,12 +319,21 @@ static cudaError_t batch_enqueue(wc_batch *b, const uint8_t *d_text, const uint6
         e = launch_docs(s1, shape_small, stream);
         n++;
     }
-    if (e == cudaSuccess && b->items.size() > b->nsmall) {
+    if (e == cudaSuccess && b->nmedium) {
         BatchArgs s2 = a;
         s2.items = b->scr.items + b->nsmall;
-        s2.nitems = (uint32_t)(b->items.size() - b->nsmall);
+        s2.nitems = b->nmedium;
         s2.next_item = b->scr.next + 1;
         e = launch_docs(s2, shape_medium, stream);
+        n++;
+    }
+    const size_t nbig = b->items.size() - b->nsmall - b->nmedium;
+    if (e == cudaSuccess && nbig) {
+        BatchArgs s3 = a;
+        s3.items = b->scr.items + b->nsmall + b->nmedium;
+        s3.nitems = (uint32_t)nbig;
+        s3.next_item = b->scr.next + 2;
+        e = launch_docs(s3, shape_large, stream);
         n++;
     }
     if (e == cudaSuccess) {
@@ -355,7 +371,8 @@ wc_status wc_count_batched_ex(wc_ctx *ctx, const uint8_t *d_text, const uint64_t
         return st;
     }
     uint64_t n = 0;
-    cudaError_t e = batch_enqueue(b, d_text, d_offsets, d_class, stream, b->shape_small, b->shape_medium, &n);
+    cudaError_t e = batch_enqueue(b, d_text, d_offsets, d_class, stream, b->shape_small, b->shape_medium,
+                                  b->shape_large, &n);
     ctx->launches += n;
     batch_release_scratch(b, stream);
     cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
@@ -390,11 +407,11 @@ static wc_status plan_autotune(wc_plan *pl, const uint8_t *d_text, const uint64_
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    auto time_shapes = [&](int ss, int sm) -> float {
+    auto time_shapes = [&](int ss, int sm, int sl) -> float {
         float best = 1e30f;
         for (int rep = 0; rep < 3; rep++) {
             cudaEventRecord(e0, stream);
-            batch_enqueue(b, d_text, d_offsets, d_class, stream, ss, sm, nullptr);
+            batch_enqueue(b, d_text, d_offsets, d_class, stream, ss, sm, sl, nullptr);
             cudaEventRecord(e1, stream);
             cudaEventSynchronize(e1);
             float ms = 0;
@@ -403,25 +420,33 @@ static wc_status plan_autotune(wc_plan *pl, const uint8_t *d_text, const uint64_
         }
         return best;
     };
-    int bs = b->shape_small, bm = b->shape_medium;
+    int bs = b->shape_small, bm = b->shape_medium, bl = b->shape_large;
     if (b->nsmall) {
         float t = 1e30f;
         for (int s = 0; s <= 2; s++) {
-            float ms = time_shapes(s, bm);
+            float ms = time_shapes(s, bm, bl);
             if (ms < t) { t = ms; bs = s; }
         }
     }
-    if (b->items.size() > b->nsmall) {
+    if (b->nmedium) {
         float t = 1e30f;
-        for (int m = 3; m <= 4; m++) {
-            float ms = time_shapes(bs, m);
+        for (int m = 2; m <= 4; m++) {
+            float ms = time_shapes(bs, m, bl);
             if (ms < t) { t = ms; bm = m; }
+        }
+    }
+    if (b->items.size() > b->nsmall + b->nmedium) {
+        float t = 1e30f;
+        for (int l = 3; l <= 4; l++) {
+            float ms = time_shapes(bs, bm, l);
+            if (ms < t) { t = ms; bl = l; }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->shape_small = ctx->tuned_small = bs;
     b->shape_medium = ctx->tuned_medium = bm;
+    b->shape_large = ctx->tuned_large = bl;
     ctx->tune_save();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? WC_OK : ctx->cuda_fail(e, "autotune");
@@ -476,7 +501,8 @@ wc_status wc_plan_run(wc_plan *pl, const uint8_t *d_text, const uint64_t *d_offs
         cudaError_t e = cudaStreamBeginCapture(pl->own, cudaStreamCaptureModeThreadLocal);
         uint64_t n = 0;
         if (e == cudaSuccess) {
-            cudaError_t e2 = batch_enqueue(b, d_text, d_offsets, d_class, pl->own, b->shape_small, b->shape_medium, &n);
+            cudaError_t e2 = batch_enqueue(b, d_text, d_offsets, d_class, pl->own, b->shape_small, b->shape_medium,
+                                           b->shape_large, &n);
             e = cudaStreamEndCapture(pl->own, &graph);
             if (e == cudaSuccess) e = e2;
         }

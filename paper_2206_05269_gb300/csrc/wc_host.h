@@ -28,7 +28,7 @@ struct wc_ctx {
     void prof_mark(std::vector<cudaEvent_t> &v, cudaStream_t s);
     cudaEvent_t prof_event(std::vector<cudaEvent_t> &v);  // a new event kept in v (not yet recorded), or null
     // per-document kernel shapes picked by the autotuner (indices into kDocShapes)
-    int tuned_small = 1, tuned_medium = 4;
+    int tuned_small = 1, tuned_medium = 3, tuned_large = 4;
     std::string gpu_name;
     void tune_load();
     void tune_save() const;

@@ -472,17 +472,35 @@ __global__ void k_gather_final(J job) {
     const unsigned long long n = out.d_meta[0];
     const uint32_t *perm = s.perm_buf(s.cur[kPasses]);  // unsegmented: count digits are the last
     unsigned long long bytes = 0;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        uint32_t e = perm[i];
-        unsigned long long hi = s.khi[e], lo = s.klo[e];
-        uint32_t r = s.lref[e];
-        out.khi[i] = hi;
-        out.klo[i] = lo;
-        out.lref[i] = r;
-        if (out.count_bits == 32) static_cast<uint32_t *>(out.cnt)[i] = (uint32_t)s.cnt[e];
-        else static_cast<unsigned long long *>(out.cnt)[i] = s.cnt[e];
-        bytes += r ? out.llen[r - 1] : short_len(hi, lo);
+    // kScanUnroll entries a thread per step, all gathers issued before the stores
+    const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x * kScanUnroll;
+    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x * kScanUnroll; b < n; b += step) {
+        uint32_t e[kScanUnroll];
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; u++) {
+            const unsigned long long i = b + (unsigned long long)u * blockDim.x + threadIdx.x;
+            e[u] = i < n ? perm[i] : 0u;
+        }
+        unsigned long long hi[kScanUnroll], lo[kScanUnroll], c[kScanUnroll];
+        uint32_t r[kScanUnroll];
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; u++) {
+            hi[u] = s.khi[e[u]];
+            lo[u] = s.klo[e[u]];
+            c[u] = s.cnt[e[u]];
+            r[u] = s.lref[e[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; u++) {
+            const unsigned long long i = b + (unsigned long long)u * blockDim.x + threadIdx.x;
+            if (i >= n) continue;
+            out.khi[i] = hi[u];
+            out.klo[i] = lo[u];
+            out.lref[i] = r[u];
+            if (out.count_bits == 32) static_cast<uint32_t *>(out.cnt)[i] = (uint32_t)c[u];
+            else static_cast<unsigned long long *>(out.cnt)[i] = c[u];
+            bytes += r[u] ? out.llen[r[u] - 1] : short_len(hi[u], lo[u]);
+        }
     }
     for (int d = 16; d; d >>= 1) bytes += __shfl_xor_sync(kFull, bytes, d);
     if ((threadIdx.x & 31) == 0 && bytes) atomicAdd(&out.d_meta[4], bytes);
@@ -548,7 +566,7 @@ cudaError_t finish_table(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_
     launch_compaction(g, gcap8, gcap, glcap, ss, out, st);
     OneJob job{SortJob{ss, out.d_meta, LongView{ss.lref, out.loff, out.llen, out.arena}, out}};
     launch_sort(job, ss.cap, 1, kPasses, st);
-    k_gather_final<<<grid_for(ss.cap, 256, sm_count() * 8), 256, 0, st>>>(job);
+    k_gather_final<<<grid_for(ss.cap, 256 * kScanUnroll, sm_count() * 8), 256, 0, st>>>(job);
     return cudaGetLastError();
 }
 
@@ -569,7 +587,7 @@ cudaError_t finish_tables(const FinishSpec *spec, int n, void *d_jobs, cudaStrea
     if (e != cudaSuccess) return e;
     JobList list{static_cast<const SortJob *>(d_jobs)};
     launch_sort(list, cap, n, kPasses, st);
-    k_gather_final<<<dim3(grid_for(cap, 256, sm_count() * 8), n), 256, 0, st>>>(list);
+    k_gather_final<<<dim3(grid_for(cap, 256 * kScanUnroll, sm_count() * 8), n), 256, 0, st>>>(list);
     return cudaGetLastError();
 }
 
