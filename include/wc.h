@@ -169,8 +169,10 @@ wc_status wc_batch_export(const wc_batch *batch, uint64_t *h_doc_start, uint32_t
  * with the given host offsets (size classes, work items, capacities) and
  * allocates the output and scratch once.  wc_plan_run counts text laid out
  * with those offsets: the first run (after autotuning when the context
- * asks for it: every per-document kernel shape of each size class is timed
- * on this input and the fastest kept, cached per GPU in tune_cache_path)
+ * asks for it and knows no shapes yet: every per-document kernel shape of
+ * each size class is timed on this input and the fastest kept, saved per
+ * GPU in tune_cache_path; a context whose cache holds an entry for its GPU,
+ * or one of whose plans was tuned already, uses those shapes untimed)
  * captures all device work into a CUDA graph; later runs with the same
  * pointers and stream replay it.  *out belongs to the plan and is rewritten
  * by the next run; wait for it (wc_batch_status) before reading it.  Run

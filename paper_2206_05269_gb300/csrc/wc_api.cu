@@ -128,8 +128,9 @@ wc_status wc_profile_read(wc_ctx *ctx, double *ms_head, double *ms_count, double
 }
 
 // Autotuner cache: a JSON object keyed by GPU name, e.g.
-//   {"NVIDIA GB300": {"small": 1, "medium": 4}}
-// (shape indices of the per-document kernel per size class).
+//   {"NVIDIA GB300": {"small": 0, "medium": 3, "large": 4}}
+// (shape indices of the per-document kernel per size class).  An entry for
+// this GPU is used as it is: plans then skip the timing.
 void wc_ctx::tune_load() {
     if (tune_cache_path.empty()) return;
     FILE *f = fopen(tune_cache_path.c_str(), "rb");
@@ -152,6 +153,7 @@ void wc_ctx::tune_load() {
     num("small", &tuned_small);
     num("medium", &tuned_medium);
     num("large", &tuned_large);
+    tuned = true;
 }
 
 void wc_ctx::tune_save() const {
@@ -207,6 +209,7 @@ void wc_destroy(wc_ctx *ctx) {
     cudaDeviceSynchronize();
     prof_clear(ctx);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->meta_host) cudaFreeHost(ctx->meta_host);
     cudaMemPoolDestroy(ctx->pool);
     delete ctx;
 }
@@ -247,8 +250,40 @@ wc_status table_create(wc_ctx *ctx, uint64_t cap, uint64_t lcap, uint64_t arena,
     return WC_OK;
 }
 
+int wc_ctx::meta_take() {
+    std::lock_guard<std::mutex> g(meta_mu);
+    if (!meta_host) {
+        void *p = nullptr;
+        if (cudaHostAlloc(&p, (size_t)kMetaSlots * kMetaSlotBytes, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return -1;
+        }
+        meta_host = static_cast<uint8_t *>(p);
+        meta_free.reserve(kMetaSlots);
+        for (int i = kMetaSlots - 1; i >= 0; i--) meta_free.push_back(i);
+    }
+    if (meta_free.empty()) return -1;
+    const int slot = meta_free.back();
+    meta_free.pop_back();
+    return slot;
+}
+
+void wc_ctx::meta_give(int slot) {
+    if (slot < 0) return;
+    std::lock_guard<std::mutex> g(meta_mu);
+    meta_free.push_back(slot);
+}
+
+// The table's work is all enqueued on s: its metadata and status follow it
+// into a pinned slot, then the done event.
 void table_mark_done(wc_table *t, cudaStream_t s) {
     t->stream = s;
+    if (t->meta_slot < 0) t->meta_slot = t->ctx->meta_take();
+    if (t->meta_slot >= 0) {
+        uint8_t *h = t->ctx->meta_host + (size_t)t->meta_slot * wc_ctx::kMetaSlotBytes;
+        cudaMemcpyAsync(h, t->dt.d_meta, 64, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(h + 64, t->dt.d_status, 4, cudaMemcpyDeviceToHost, s);
+    }
     cudaEventRecord(t->done, s);
 }
 
@@ -267,9 +302,15 @@ wc_status table_sync(const wc_table *ct) {
     if (e != cudaSuccess) return t->ctx->cuda_fail(e, "cudaEventSynchronize");
     unsigned long long meta[8];
     uint32_t status = 0;
-    e = cudaMemcpy(meta, t->dt.d_meta, sizeof(meta), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(&status, t->dt.d_status, 4, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return t->ctx->cuda_fail(e, "reading table metadata");
+    if (t->meta_slot >= 0) {  // landed with the table's work
+        const uint8_t *h = t->ctx->meta_host + (size_t)t->meta_slot * wc_ctx::kMetaSlotBytes;
+        memcpy(meta, h, sizeof(meta));
+        memcpy(&status, h + 64, 4);
+    } else {
+        e = cudaMemcpy(meta, t->dt.d_meta, sizeof(meta), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(&status, t->dt.d_status, 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return t->ctx->cuda_fail(e, "reading table metadata");
+    }
     t->n = meta[0];
     t->nlong = meta[1];
     t->tokens = meta[3];
@@ -354,6 +395,7 @@ void wc_table_free(wc_table *t) {
     cudaSetDevice(t->ctx->device);
     cudaEventSynchronize(t->done);
     t->ctx->release(t->mem, t->bytes, t->stream);
+    t->ctx->meta_give(t->meta_slot);
     cudaEventDestroy(t->done);
     delete t;
 }

@@ -165,7 +165,7 @@ static wc_status make_view(wc_batch *b, uint64_t start, uint64_t n, wc_table **o
     k_view_meta<<<view_meta_grid(n), 256, 0, b->stream>>>(d, n);
     t->stream = b->stream;
     cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming);
-    cudaEventRecord(t->done, b->stream);
+    table_mark_done(t, b->stream);
     *out = t;
     return WC_OK;
 }
@@ -174,6 +174,7 @@ static void free_owned_table(wc_table *t) {
     if (!t) return;
     cudaEventSynchronize(t->done);
     t->ctx->release(t->mem, t->bytes, t->stream);
+    t->ctx->meta_give(t->meta_slot);
     cudaEventDestroy(t->done);
     delete t;
 }
@@ -447,6 +448,7 @@ static wc_status plan_autotune(wc_plan *pl, const uint8_t *d_text, const uint64_
     b->shape_small = ctx->tuned_small = bs;
     b->shape_medium = ctx->tuned_medium = bm;
     b->shape_large = ctx->tuned_large = bl;
+    ctx->tuned = true;
     ctx->tune_save();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? WC_OK : ctx->cuda_fail(e, "autotune");
@@ -487,7 +489,7 @@ wc_status wc_plan_run(wc_plan *pl, const uint8_t *d_text, const uint64_t *d_offs
     wc_batch *b = pl->b;
     wc_ctx *ctx = b->ctx;
     cudaSetDevice(ctx->device);
-    if (ctx->autotune && !pl->tuned) {
+    if (ctx->autotune && !ctx->tuned && !pl->tuned) {
         wc_status st = plan_autotune(pl, d_text, d_offsets, d_class, stream);
         if (st != WC_OK) return st;
     }
@@ -778,9 +780,8 @@ wc_status wc_batch_topk(const wc_batch *cb, uint32_t k, uint64_t *h_first, uint3
         ctx->launches++;
         e = cudaGetLastError();
     }
-    t->stream = b->stream;
     cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming);
-    cudaEventRecord(t->done, b->stream);
+    table_mark_done(t, b->stream);
     b->views.push_back(t);  // freed with the batch
     if (e != cudaSuccess) return ctx->cuda_fail(e, "batch top-k");
     *out = t;

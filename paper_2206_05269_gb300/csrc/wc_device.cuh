@@ -207,16 +207,6 @@ __device__ __forceinline__ void red_add_u64_dev(unsigned long long *p, unsigned 
     asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__device__ __forceinline__ uint32_t ld_acquire_shared(const uint32_t *p) {
-    uint32_t v;
-    uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-    asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release_shared(uint32_t *p, uint32_t v) {
-    uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-    asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
-}
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
     unsigned long long v;
     asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -417,52 +407,6 @@ __device__ __forceinline__ void global_insert16(const GTable &g, uint4 k, unsign
 __device__ __forceinline__ void table_insert_key(const GTable &g, uint4 k, unsigned long long add) {
     if ((k.z | k.w) == 0u) global_insert8(g, ((unsigned long long)k.y << 32) | k.x, add);
     else global_insert16(g, k, add);
-}
-
-// ---------------------------------------------------------------- shared table
-// Per-block level-1 table: tag[i] (0 empty, 1 being written, else hash tag
-// with bit 1 set), key[i], cnt[i].  A slot's key and count are written before
-// its tag is published with release order, and read after an acquire load of
-// the tag.  A slot that is being written is skipped, which can only place a
-// second copy of a word in the table: harmless, since every copy is flushed
-// exactly into the global table.
-struct STable {
-    uint32_t *tag;
-    uint4 *key;
-    uint32_t *cnt;
-    uint32_t *nfill;
-    uint32_t mask;
-    uint32_t fill_limit;
-};
-
-__device__ __forceinline__ uint32_t stag_of(uint64_t h) { return ((uint32_t)h & ~1u) | 2u; }
-
-// Returns false when the word must spill to the global table.
-__device__ __forceinline__ bool shared_insert(const STable &t, uint4 k, uint64_t h, uint32_t add, int max_probe) {
-    uint32_t s = (uint32_t)(h >> 40) & t.mask;
-    uint32_t want = stag_of(h);
-    for (int probe = 0; probe < max_probe; probe++) {
-        uint32_t tg = ld_acquire_shared(t.tag + s);
-        if (tg == want) {
-            if (key_eq(t.key[s], k)) { atomicAdd(t.cnt + s, add); return true; }
-        } else if (tg == 0u) {
-            if (*(volatile uint32_t *)t.nfill >= t.fill_limit) return false;
-            uint32_t old = atomicCAS(t.tag + s, 0u, 1u);
-            if (old == 0u) {
-                t.key[s] = k;
-                t.cnt[s] = add;
-                st_release_shared(t.tag + s, want);
-                atomicAdd(t.nfill, 1u);
-                return true;
-            }
-            if (old == want) {
-                __threadfence_block();
-                if (key_eq(t.key[s], k)) { atomicAdd(t.cnt + s, add); return true; }
-            }
-        }
-        s = (s + 1) & t.mask;
-    }
-    return false;
 }
 
 }  // namespace wc

@@ -2,6 +2,7 @@
 #pragma once
 #include <atomic>
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -29,11 +30,22 @@ struct wc_ctx {
     cudaEvent_t prof_event(std::vector<cudaEvent_t> &v);  // a new event kept in v (not yet recorded), or null
     // per-document kernel shapes picked by the autotuner (indices into kDocShapes)
     int tuned_small = 1, tuned_medium = 3, tuned_large = 4;
+    bool tuned = false;  // shapes known (from the cache, or timed by a plan of this context)
     std::string gpu_name;
     void tune_load();
     void tune_save() const;
     // distinct words seen by the last synced single-document count (capacity hints)
     uint64_t hist_bytes = 0, hist_n8 = 0, hist_n16 = 0, hist_nlong = 0, hist_arena = 0;
+
+    // pinned host slots that receive each table's metadata and status by an
+    // asynchronous copy when its work completes, so that reading them waits
+    // for that table only, not for work enqueued after it
+    static constexpr int kMetaSlots = 4096, kMetaSlotBytes = 128;
+    uint8_t *meta_host = nullptr;
+    std::vector<int> meta_free;
+    std::mutex meta_mu;
+    int meta_take();          // a free slot, or -1 (then tables read their metadata synchronously)
+    void meta_give(int slot);
 
     wc_status fail(wc_status s, const char *what);
     wc_status cuda_fail(cudaError_t e, const char *what);
@@ -55,6 +67,7 @@ struct wc_table {
     uint64_t n = 0, nlong = 0, tokens = 0, word_bytes = 0;
     uint32_t status_bits = 0;
     uint64_t src_bytes = 0;  // input size of a single-document count (capacity hints)
+    int meta_slot = -1;      // pinned slot of wc_ctx::meta_host, or -1
 };
 
 // Hash tables and sort scratch of one count or merge.
