@@ -1010,20 +1010,26 @@ __global__ void __launch_bounds__(kRatioSort / 2) k_ratio_round(RatioArgs r, con
         so[j] = i != kNoEntry ? r.cout[i] : 0ull;
     }
     __syncthreads();
+    // ascending merges whose first stage compares mirrored positions: pairs
+    // reaching past the block's valid entries meet padding (ranked last)
+    // and never swap; stages within 64 positions stay inside one warp's
+    // positions and need only a warp barrier (as in the per-document sort)
+    const unsigned long long nv = len > base ? (len - base < (unsigned long long)kRatioSort ? len - base : kRatioSort) : 0ull;
     const int t = threadIdx.x;  // one compare-exchange pair per thread
     for (int size = 2; size <= kRatioSort; size <<= 1)
         for (int stride = size >> 1; stride; stride >>= 1) {
-            const int a = 2 * t - (t & (stride - 1)), b = a + stride;
-            const bool first_run = (a & size) == 0;  // this run ends best-first
-            const bool swap = first_run ? ranks_before(si[b], sc[b], so[b], si[a], sc[a], so[a])
-                                        : ranks_before(si[a], sc[a], so[a], si[b], sc[b], so[b]);
-            if (swap) {
+            const int a = 2 * t - (t & (stride - 1));
+            const int b = stride == (size >> 1) ? (a ^ (size - 1)) : a + stride;
+            if ((unsigned long long)b < nv && ranks_before(si[b], sc[b], so[b], si[a], sc[a], so[a])) {
                 unsigned long long x = si[a]; si[a] = si[b]; si[b] = x;
                 x = sc[a]; sc[a] = sc[b]; sc[b] = x;
                 x = so[a]; so[a] = so[b]; so[b] = x;
             }
-            __syncthreads();
+            const int span = 2 * stride, span_next = stride > 1 ? stride : 2 * size;
+            if (span <= 64 && span_next <= 64) __syncwarp();
+            else __syncthreads();
         }
+    __syncthreads();
     for (uint32_t j = threadIdx.x; j < keep; j += blockDim.x) dst[(unsigned long long)blockIdx.x * keep + j] = si[j];
 }
 
