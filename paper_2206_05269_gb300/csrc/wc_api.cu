@@ -12,6 +12,7 @@
 
 #include "../../include/wc.h"
 #include "wc_internal.h"
+#include "wc_batch.h"
 #include "wc_host.h"
 
 using namespace wc;
@@ -148,7 +149,7 @@ void wc_ctx::tune_load() {
         q = txt.find(':', q);
         if (q == std::string::npos) return;
         int v = atoi(txt.c_str() + q + 1);
-        if (v >= 0 && v < 5) *dst = v;
+        if (v >= 0 && v < kNumDocShapes) *dst = v;
     };
     num("small", &tuned_small);
     num("medium", &tuned_medium);

@@ -438,7 +438,7 @@ static wc_status plan_autotune(wc_plan *pl, const uint8_t *d_text, const uint64_
     }
     if (b->items.size() > b->nsmall + b->nmedium) {
         float t = 1e30f;
-        for (int l = 3; l <= 4; l++) {
+        for (int l = 3; l <= 5; l++) {
             float ms = time_shapes(bs, bm, l);
             if (ms < t) { t = ms; bl = l; }
         }
