@@ -266,6 +266,17 @@ wc_status wc_profile_enable(wc_ctx *ctx, int enable);
 wc_status wc_profile_read(wc_ctx *ctx, double *ms_head, double *ms_count, double *ms_finish,
                           uint64_t *count_launches, uint64_t *kernel_launches);
 
+/* Self-test of the device-side failure path (no part of the paper's method:
+ * every device wait of the library is bounded and reports WC_ERR_TIMEOUT
+ * instead of hanging).  Runs the counting kernel's bounded barrier wait in
+ * one block on `stream`, on a barrier that expects one arrival: with
+ * arrive != 0 the block makes that arrival first and the call returns
+ * WC_OK; with arrive == 0 nothing arrives, the wait gives up after `polls`
+ * polls (1 .. 2^22) and the call returns WC_ERR_TIMEOUT, the context staying
+ * usable.  Waits for the stream.  polls outside that range:
+ * WC_ERR_INVALID_ARG. */
+wc_status wc_selftest_wait(wc_ctx *ctx, uint32_t polls, int arrive, cudaStream_t stream);
+
 const char *wc_status_str(wc_status s);
 const char *wc_last_error(const wc_ctx *ctx);
 

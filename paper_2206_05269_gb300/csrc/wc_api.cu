@@ -215,6 +215,30 @@ void wc_destroy(wc_ctx *ctx) {
     delete ctx;
 }
 
+// ---------------------------------------------------------------- wait self-test
+static wc_status status_from_bits(uint32_t bits);
+
+wc_status wc_selftest_wait(wc_ctx *ctx, uint32_t polls, int arrive, cudaStream_t stream) {
+    if (!ctx) return WC_ERR_INVALID_ARG;
+    if (polls < 1 || polls > (1u << 22)) return ctx->fail(WC_ERR_INVALID_ARG, "polls outside 1 .. 2^22");
+    cudaSetDevice(ctx->device);
+    void *d = nullptr;
+    wc_status st = ctx->alloc(&d, 256, stream);
+    if (st != WC_OK) return st;
+    uint32_t *d_status = static_cast<uint32_t *>(d);
+    uint32_t h = 0;
+    cudaError_t e = cudaMemsetAsync(d_status, 0, 4, stream);
+    if (e == cudaSuccess) e = launch_wait_selftest(d_status, polls, arrive, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_status, 4, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    ctx->release(d, 256, stream);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "wait self-test");
+    ctx->launches++;
+    st = status_from_bits(h);
+    if (st != WC_OK) return ctx->fail(st, "bounded device wait gave up (self-test)");
+    return WC_OK;
+}
+
 // ---------------------------------------------------------------- tables
 static size_t table_bytes(uint64_t cap, uint64_t lcap, uint64_t arena, int bits) {
     auto r = [](size_t n) { return (n + 255) & ~(size_t)255; };

@@ -104,10 +104,11 @@ __device__ __forceinline__ void tma_load(void *dst, const void *src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
         : "memory");
 }
-// Bounded wait for the phase `parity` of `bar`; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Bounded wait for the phase `parity` of `bar` (at most `polls` polls);
+// false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t polls = 1u << 22) {
     const uint32_t a = smem_addr(bar);
-    for (uint32_t it = 0; it < (1u << 22); it++) {
+    for (uint32_t it = 0; it < polls; it++) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -787,5 +788,29 @@ cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
 
 int count_global_chunk_bytes() { return kChunk; }
 uint64_t count_global_head_min() { return kHeadMinBytes; }
+
+// ---------------------------------------------------------------- wait self-test
+// The counting kernel's bounded wait, on a barrier expecting one arrival:
+// with `arrive` thread 0 makes it first and the wait succeeds; without, no
+// one does, the wait gives up after `polls` polls and the timeout is recorded
+// in *status as the counting kernel records it.  Nothing else waits, so the
+// block always finishes.
+__global__ void k_wait_selftest(uint32_t *status, uint32_t polls, int arrive) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (arrive) mbar_arrive(&bar);
+        if (!mbar_wait(&bar, 0u, polls)) atomicOr(status, ST_TIMEOUT);
+    }
+}
+
+cudaError_t launch_wait_selftest(uint32_t *d_status, uint32_t polls, int arrive, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(d_status, polls, arrive);
+    return cudaGetLastError();
+}
 
 }  // namespace wc

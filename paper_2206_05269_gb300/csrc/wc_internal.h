@@ -23,6 +23,8 @@ struct CountLaunch {
 cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s);
 int count_global_chunk_bytes();
 uint64_t count_global_head_min();
+// One block runs the counting kernel's bounded barrier wait (see wc_selftest_wait).
+cudaError_t launch_wait_selftest(uint32_t *d_status, uint32_t polls, int arrive, cudaStream_t s);
 int count_global_launches(uint64_t nbytes, bool head);
 size_t head_scratch_bytes();
 

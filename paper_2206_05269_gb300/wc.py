@@ -39,7 +39,7 @@ EXPORTS = [
     "wc_class_ratio_topk", "wc_merge", "wc_topk", "wc_table_status", "wc_table_size",
     "wc_table_export", "wc_table_count_bits", "wc_table_free", "wc_batch_free", "wc_plan_create", "wc_plan_run",
     "wc_plan_free", "wc_count_noalloc", "wc_profile_enable",
-    "wc_profile_read", "wc_status_str", "wc_last_error",
+    "wc_profile_read", "wc_selftest_wait", "wc_status_str", "wc_last_error",
 ]
 
 
@@ -102,6 +102,7 @@ def load() -> ctypes.CDLL:
         "wc_profile_enable": (i32, [vp, i32]),
         "wc_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64), ctypes.POINTER(u64)]),
+        "wc_selftest_wait": (i32, [vp, u32, i32, vp]),
         "wc_status_str": (ctypes.c_char_p, [i32]),
         "wc_last_error": (ctypes.c_char_p, [vp]),
     }
@@ -316,6 +317,12 @@ def wc_profile_read(ctx) -> tuple[float, float, float, int, int]:
     _check(load().wc_profile_read(ctx, ctypes.byref(h), ctypes.byref(a), ctypes.byref(b), ctypes.byref(n),
                                   ctypes.byref(k)), ctx, "wc_profile_read")
     return h.value, a.value, b.value, n.value, k.value
+
+
+def wc_selftest_wait(ctx, polls: int, arrive: bool, stream: int = 0) -> int:
+    """Runs the bounded device wait on a barrier that is (arrive) or is not
+    arrived at; returns the status (WC_OK, or WC_ERR_TIMEOUT)."""
+    return load().wc_selftest_wait(ctx, polls, int(arrive), stream)
 
 
 def wc_status_str(status: int) -> str:
