@@ -278,6 +278,18 @@ def run_gpu(args, rank, world, local):
     achieved = alg_bytes / avg_count_s / 1e9
     traffic = profiled_traffic("dram_bytes_per_launch")
 
+    # the practical ceiling of one pass over this text: a kernel that only reads it
+    sink = torch.zeros(4096, dtype=torch.int64, device=f"cuda:{local}")
+    ev2, ev3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        wc.wc_read_ceiling(text.data_ptr(), nbytes, sink.data_ptr(), 4096, stream.cuda_stream)
+    ev2.record(stream)
+    for _ in range(20):
+        wc.wc_read_ceiling(text.data_ptr(), nbytes, sink.data_ptr(), 4096, stream.cuda_stream)
+    ev3.record(stream)
+    torch.cuda.synchronize()
+    read_ceiling = nbytes / (ev2.elapsed_time(ev3) / 20 * 1e-3) / 1e9
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -303,7 +315,8 @@ def run_gpu(args, rank, world, local):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_count2<false>", "peak_kind": peak_kind,
-                         "algorithmic_bytes_per_launch": alg_bytes},
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "read_ceiling_GBps": read_ceiling, "frac_of_read_ceiling": achieved / read_ceiling},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clocks,

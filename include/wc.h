@@ -266,6 +266,16 @@ wc_status wc_profile_enable(wc_ctx *ctx, int enable);
 wc_status wc_profile_read(wc_ctx *ctx, double *ms_head, double *ms_count, double *ms_finish,
                           uint64_t *count_launches, uint64_t *kernel_launches);
 
+/* Read ceiling (measurement, not the paper's method): reads d_text[0,
+ * nbytes) once with 16-byte streaming loads (any alignment; byte loads for
+ * the ragged ends) and folds every byte into d_sink (device, sink_words
+ * uint64 words, overwritten; at least one).  A pass that reads the text
+ * once cannot beat this kernel's time, so it is the practical HBM limit for
+ * the counting kernel.  Asynchronous on `stream`; null pointers or
+ * sink_words == 0: WC_ERR_INVALID_ARG. */
+wc_status wc_read_ceiling(const uint8_t *d_text, uint64_t nbytes, uint64_t *d_sink, uint32_t sink_words,
+                          cudaStream_t stream);
+
 /* Self-test of the device-side failure path (no part of the paper's method:
  * every device wait of the library is bounded and reports WC_ERR_TIMEOUT
  * instead of hanging).  Runs the counting kernel's bounded barrier wait in

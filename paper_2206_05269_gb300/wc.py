@@ -39,7 +39,7 @@ EXPORTS = [
     "wc_class_ratio_topk", "wc_merge", "wc_topk", "wc_table_status", "wc_table_size",
     "wc_table_export", "wc_table_count_bits", "wc_table_free", "wc_batch_free", "wc_plan_create", "wc_plan_run",
     "wc_plan_free", "wc_count_noalloc", "wc_profile_enable",
-    "wc_profile_read", "wc_selftest_wait", "wc_status_str", "wc_last_error",
+    "wc_profile_read", "wc_read_ceiling", "wc_selftest_wait", "wc_status_str", "wc_last_error",
 ]
 
 
@@ -103,6 +103,7 @@ def load() -> ctypes.CDLL:
         "wc_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64), ctypes.POINTER(u64)]),
         "wc_selftest_wait": (i32, [vp, u32, i32, vp]),
+        "wc_read_ceiling": (i32, [vp, u64, vp, u32, vp]),
         "wc_status_str": (ctypes.c_char_p, [i32]),
         "wc_last_error": (ctypes.c_char_p, [vp]),
     }
@@ -317,6 +318,12 @@ def wc_profile_read(ctx) -> tuple[float, float, float, int, int]:
     _check(load().wc_profile_read(ctx, ctypes.byref(h), ctypes.byref(a), ctypes.byref(b), ctypes.byref(n),
                                   ctypes.byref(k)), ctx, "wc_profile_read")
     return h.value, a.value, b.value, n.value, k.value
+
+
+def wc_read_ceiling(d_text: int, nbytes: int, d_sink: int, sink_words: int, stream: int = 0) -> int:
+    """One read-only pass over a device text (the practical HBM limit of any
+    single pass); asynchronous, returns the launch status."""
+    return load().wc_read_ceiling(d_text, nbytes, d_sink, sink_words, stream)
 
 
 def wc_selftest_wait(ctx, polls: int, arrive: bool, stream: int = 0) -> int:
