@@ -298,9 +298,18 @@ def run_gpu(args, rank, world, local):
         t0 = time.perf_counter()
         r = oracle.count(sample, keep_docs=False)
         dt = time.perf_counter() - t0
+        r_tokens = int(r.glob().counts.sum())
         del r
         cpu = {"value": sample.size / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"first {sample.size} bytes of the same corpus, single-threaded C++ oracle, {dt:.1f} s"}
+        # the paper's multicore map + reduce on every host core, same sample
+        import cpu_parallel
+        cp = cpu_parallel.count(sample)
+        if cp["tokens"] != r_tokens:
+            raise RuntimeError("parallel CPU baseline disagrees with the oracle on the token count")
+        cpu_par = {"value": sample.size / cp["seconds"] / 1e9, "unit": UNIT, "cores": cp["threads"],
+                   "cpu_model": cpu_parallel.cpu_model(), "kind": "paper-style parallel (per-thread maps + merge)",
+                   "sample": f"first {sample.size} bytes of the same corpus, {cp['seconds']:.2f} s"}
 
     if rank == 0:
         line = {
@@ -323,6 +332,7 @@ def run_gpu(args, rank, world, local):
         }
         if cpu:
             line["cpu_baseline"] = cpu
+            line["cpu_parallel_baseline"] = cpu_par
         print(json.dumps(line), flush=True)
     ctr.close()
     if dist:
