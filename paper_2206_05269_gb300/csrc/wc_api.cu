@@ -522,7 +522,7 @@ wc_status wc_count_ex(wc_ctx *ctx, const uint8_t *d_text, uint64_t nbytes, const
     ctx->prof_mark(ctx->ev_finish, stream);
     if (e == cudaSuccess) e = finish_table(g, cs.gcap8, cs.gcap, cs.glcap, cs.ss, t->dt, stream);
     ctx->prof_mark(ctx->ev_finish, stream);
-    ctx->launches += finish_table_launches();
+    ctx->launches += finish_table_launches(cs.ss.cap);
     ctx->release(cs.mem, cs.bytes, stream);
     table_mark_done(t, stream);
     if (e != cudaSuccess) {
@@ -604,7 +604,7 @@ wc_status wc_count_host(wc_ctx *ctx, const uint8_t *h_text, uint64_t nbytes, uin
         ctx->launches += count_global_launches(cut[i + 1] - cut[i], i == 0 && head);
     }
     if (e == cudaSuccess) e = finish_table(g, cs.gcap8, cs.gcap, cs.glcap, cs.ss, t->dt, stream);
-    ctx->launches += finish_table_launches();
+    ctx->launches += finish_table_launches(cs.ss.cap);
     for (auto x : ev)
         if (x) cudaEventDestroy(x);  // released once their work completes
     ctx->release(cs.mem, cs.bytes, stream);
@@ -671,7 +671,7 @@ wc_status wc_merge(wc_ctx *ctx, const wc_table *const *in, uint32_t n, cudaStrea
     ctx->prof_mark(ctx->ev_finish, stream);
     if (e == cudaSuccess) e = finish_table(g, cs.gcap8, cs.gcap, cs.glcap, cs.ss, t->dt, stream);
     ctx->prof_mark(ctx->ev_finish, stream);
-    ctx->launches += finish_table_launches();
+    ctx->launches += finish_table_launches(cs.ss.cap);
     ctx->release(dsrc, sb, stream);
     ctx->release(cs.mem, cs.bytes, stream);
     table_mark_done(t, stream);

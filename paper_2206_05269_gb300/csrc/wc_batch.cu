@@ -825,6 +825,7 @@ cudaError_t launch_segmented_finish(const BatchArgs &a, const GTable &g, uint64_
     cudaMemsetAsync(smeta, 0, 16 * 8, s);
     cudaMemsetAsync(ss.hist_all, 0, 4 * kSortPassesSeg * 256, s);
     cudaMemsetAsync(ss.cur, 0, 4 * 32, s);
+    cudaMemsetAsync(ss.group_hist[0], 0, 2 * 4 * 256 * (size_t)ss.group_stride, s);
     k_bcompact8<<<gridn(cap8, 256 * kScanUnroll, sms * 8), 256, 0, s>>>(g.slots8, cap8, ss, smeta);
     k_bcompact16<<<gridn(cap16, 256 * kScanUnroll, sms * 8), 256, 0, s>>>(g.slots, cap16, ss, smeta);
     k_bcompact_long<<<gridn(caplong, 256, sms * 8), 256, 0, s>>>(g.lslots, caplong, ss, a, smeta);
@@ -836,6 +837,6 @@ cudaError_t launch_segmented_finish(const BatchArgs &a, const GTable &g, uint64_
     k_seg_ends<<<gridn(ss.cap, 256 * kScanUnroll, sms * 8), 256, 0, s>>>(ss, a, smeta, kSortPassesSeg);
     return cudaGetLastError();
 }
-int segmented_finish_launches() { return 3 + sort_entries_launches(kSortPassesSeg) + 3; }
+int segmented_finish_launches(uint64_t cap) { return 3 + sort_entries_launches(kSortPassesSeg, cap) + 3; }
 
 }  // namespace wc

@@ -339,7 +339,7 @@ static cudaError_t batch_enqueue(wc_batch *b, const uint8_t *d_text, const uint6
     }
     if (e == cudaSuccess) {
         e = launch_segmented_finish(a, a.g, cs.gcap8, cs.gcap, cs.glcap, cs.ss, b->scr.smeta, stream);
-        n += segmented_finish_launches();
+        n += segmented_finish_launches(cs.ss.cap);
     }
     if (launches) *launches = n;
     return e;
@@ -649,7 +649,9 @@ static wc_status build_tables_at(wc_batch *b, const std::vector<uint64_t> &est, 
         spec[c] = FinishSpec{c < b->nclasses ? g[c] : gg, cs.gcap8, cs.gcap, cs.glcap, &cs.ss, &tabs[c]->dt};
     }
     if (e == cudaSuccess) e = finish_tables(spec.data(), (int)nt, static_cast<uint8_t *>(dg) + gbytes, s);
-    ctx->launches += 1 + (uint64_t)finish_tables_launches((int)nt);
+    uint64_t capmax = 0;
+    for (uint32_t c = 0; c < nt; c++) capmax = std::max<uint64_t>(capmax, spec[c].ss->cap);
+    ctx->launches += 1 + (uint64_t)finish_tables_launches((int)nt, capmax);
     cleanup(nt);
     ctx->release(dg, dbytes, s);
     for (auto *t : tabs) table_mark_done(t, s);

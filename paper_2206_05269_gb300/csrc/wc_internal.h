@@ -54,6 +54,26 @@ constexpr int kSortKeyPasses = 10;
 constexpr int kSortPasses = kSortKeyPasses + 8;
 constexpr int kSortPassesSeg = kSortPasses + 4;
 
+// A radix pass sorts tiles of kSortTileElems entries.  A small sort (at most
+// kSortFusedMaxTiles tiles by capacity) needs no scan pass: each tile finds
+// its digit offsets from the counts of the tile groups before its own group
+// and of the tiles before it in its group, in groups of sort_group_tiles(t)
+// tiles for t tiles (a power of two of at least sqrt(t)), so at most
+// sort_group_stride(capacity tiles) groups.  Larger sorts scan the tile
+// counts in a pass of their own.
+constexpr uint64_t kSortTileElems = 4096;
+constexpr uint64_t kSortFusedMaxTiles = 1024;
+__host__ __device__ constexpr uint64_t sort_group_tiles(uint64_t ntiles) {
+    uint64_t g = 1;
+    while (g * g < ntiles) g <<= 1;
+    return g;
+}
+constexpr uint64_t sort_group_stride(uint64_t ntiles_cap) {
+    uint64_t r = 1;
+    while (r * r < ntiles_cap) r++;
+    return r + 1;
+}
+
 struct SortScratch {
     uint64_t cap;
     unsigned long long *khi, *klo, *cnt;
@@ -65,8 +85,11 @@ struct SortScratch {
     uint32_t *hist_all;      // 24 x 256
     uint32_t *tile_hist;     // 256 x ntiles
     uint32_t *cur;           // 25
+    uint32_t *group_hist[2]; // 256 x group_stride each: digit counts per tile group, by pass parity
+    uint32_t group_stride;
     // permutation buffer c (0 or 1), selected without indexing the parameter array
     __device__ __forceinline__ uint32_t *perm_buf(uint32_t c) const { return c ? perm[1] : perm[0]; }
+    __device__ __forceinline__ uint32_t *group_buf(uint32_t c) const { return c ? group_hist[1] : group_hist[0]; }
 };
 size_t sort_scratch_bytes(uint64_t cap);
 void sort_scratch_carve(SortScratch &s, void *base, uint64_t cap);
@@ -82,12 +105,12 @@ struct LongView {
 // the permutation ss.perm[ss.cur[passes]] (device value).
 cudaError_t sort_entries(SortScratch &ss, const unsigned long long *meta, const LongView &v, int passes,
                          cudaStream_t st);
-int sort_entries_launches(int passes);
+int sort_entries_launches(int passes, uint64_t cap);
 
 // Compacts the global hash tables into unsorted scratch arrays and copies
 // the long words into out.arena; then sorts and writes `out`.
-// finish_table_launches() kernels are launched.
-int finish_table_launches();
+// finish_table_launches(ss.cap) kernels are launched.
+int finish_table_launches(uint64_t cap);
 cudaError_t finish_table(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_t glcap, SortScratch &ss,
                          DevTable &out, cudaStream_t s);
 
@@ -144,7 +167,7 @@ struct SortJob {
 // finish_table for n tables at once: each table's compaction, then every
 // sort pass and the final gather as one launch over all n tables (grid.y).
 // d_jobs: device memory of finish_tables_job_bytes(n), alive until the
-// stream has run the launches.  finish_tables_launches(n) kernels.
+// stream has run the launches.  finish_tables_launches(n, largest cap) kernels.
 struct FinishSpec {
     GTable g;
     uint64_t gcap8, gcap, glcap;
@@ -152,7 +175,7 @@ struct FinishSpec {
     DevTable *out;
 };
 size_t finish_tables_job_bytes(int n);
-int finish_tables_launches(int n);
+int finish_tables_launches(int n, uint64_t cap);
 cudaError_t finish_tables(const FinishSpec *spec, int n, void *d_jobs, cudaStream_t s);
 
 // Entries of finished tables re-inserted into a global hash table (merge).

@@ -39,7 +39,8 @@ constexpr uint64_t kBytesLong = round256(kNaCapLong * sizeof(wc::LSlot));
 // lref, 2 permutations, doc, the digit histograms, tile histograms, pass
 // cursors), each carved at a 256-byte boundary.
 constexpr uint64_t kSortBytes = kNaEntries * (8 + 8 + 8 + 8 + 4 + 4 + 4 + 4 + 4) + 4 * wc::kSortPassesSeg * 256 +
-                                4 * 256 * ((kNaEntries + 4095) / 4096) + 4 * 32 + 4096 + 16 * kR;
+                                4 * 256 * ((kNaEntries + 4095) / 4096) + 4 * 32 +
+                                2 * 4 * 256 * wc::sort_group_stride((kNaEntries + 4095) / 4096) + 4096 + 16 * kR;
 constexpr uint64_t kScratchBytes = kBytes8 + kBytes16 + kBytesLong + kSortBytes;  // about 15.2 MB
 
 }  // namespace

@@ -18,7 +18,7 @@
 
 namespace wc {
 
-constexpr int kSortTile = 4096;      // elements per block in a radix pass
+constexpr int kSortTile = (int)kSortTileElems;  // elements per block in a radix pass
 constexpr int kSortThreads = 256;
 constexpr int kItems = kSortTile / kSortThreads;  // 16
 constexpr int kPasses = kSortPasses;
@@ -35,7 +35,8 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 
 size_t sort_scratch_bytes(uint64_t cap) {
     uint64_t ntiles = (cap + kSortTile - 1) / kSortTile;
-    return cap * (8 + 8 + 8 + 8 + 4 + 4 + 4 + 4 + 4) + 4 * kPassesSeg * 256 + 4 * 256 * ntiles + 4 * 32 + 4096;
+    return cap * (8 + 8 + 8 + 8 + 4 + 4 + 4 + 4 + 4) + 4 * kPassesSeg * 256 + 4 * 256 * ntiles + 4 * 32 +
+           2 * 4 * 256 * (ntiles <= kSortFusedMaxTiles ? sort_group_stride(ntiles) : 1) + 4096;
 }
 
 void sort_scratch_carve(SortScratch &s, void *base, uint64_t cap) {
@@ -55,6 +56,9 @@ void sort_scratch_carve(SortScratch &s, void *base, uint64_t cap) {
     s.hist_all = reinterpret_cast<uint32_t *>(take(4 * kPassesSeg * 256));
     s.tile_hist = reinterpret_cast<uint32_t *>(take(4 * 256 * ntiles));
     s.cur = reinterpret_cast<uint32_t *>(take(4 * 32));
+    s.group_stride = (uint32_t)(ntiles <= kSortFusedMaxTiles ? sort_group_stride(ntiles) : 1);
+    s.group_hist[0] = reinterpret_cast<uint32_t *>(take(2 * 4 * 256 * (size_t)s.group_stride));  // both, adjacent
+    s.group_hist[1] = s.group_hist[0] + 256 * (size_t)s.group_stride;
 }
 
 // ---------------------------------------------------------------- compaction
@@ -264,7 +268,7 @@ __device__ __forceinline__ bool pass_skipped(const SortScratch &s, int p, unsign
 }
 
 template <class J>
-__global__ void __launch_bounds__(kSortThreads) k_pass_count(J job, int p) {
+__global__ void __launch_bounds__(kSortThreads) k_pass_count(J job, int p, int fused) {
     const SortScratch &s = job.get().s;
     const unsigned long long *meta = job.get().meta;
     __shared__ uint32_t h[256];
@@ -290,10 +294,16 @@ __global__ void __launch_bounds__(kSortThreads) k_pass_count(J job, int p) {
     for (int it = 0; it < kItems; it++)
         if (dig[it] != 0xFFFFFFFFu) atomicAdd(&h[dig[it]], 1u);
     __syncthreads();
-    s.tile_hist[(unsigned long long)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+    const uint32_t c = h[threadIdx.x];
+    s.tile_hist[(unsigned long long)threadIdx.x * ntiles + blockIdx.x] = c;
+    if (fused && c)
+        atomicAdd(&s.group_buf((uint32_t)p & 1u)[(unsigned long long)threadIdx.x * s.group_stride +
+                                                 blockIdx.x / sort_group_tiles(ntiles)],
+                  c);
 }
 
-// Exclusive scan of the digit-major tile histogram: block d scans digit d's
+// Sorts of more than kSortFusedMaxTiles tiles: exclusive scan of the
+// digit-major tile histogram: block d scans digit d's
 // row of tile counts, starting from the number of elements with a smaller
 // digit (from the all-pass histogram).  256 blocks of 256 threads.
 template <class J>
@@ -342,18 +352,56 @@ __global__ void __launch_bounds__(256) k_pass_scan(J job, int p) {
 // Stable scatter: warp w ranks its 512 consecutive elements in order with
 // match_any; warps are combined in order, so equal digits keep their order.
 template <class J>
-__global__ void __launch_bounds__(kSortThreads) k_pass_scatter(J job, int p) {
+__global__ void __launch_bounds__(kSortThreads) k_pass_scatter(J job, int p, int fused) {
     const SortScratch &s = job.get().s;
     const unsigned long long *meta = job.get().meta;
     constexpr int WARPS = kSortThreads / 32;
+    static_assert(kSortThreads == 256, "one thread per digit");
     __shared__ uint32_t wcount[WARPS][256];
+    __shared__ uint32_t wtot[WARPS];
     const unsigned long long n = meta[0];
     const unsigned long long ntiles = (n + kSortTile - 1) / kSortTile;
-    if (blockIdx.x >= ntiles) return;
-    if (pass_skipped(s, p, n)) return;
+    const bool skip = pass_skipped(s, p, n);
+    if (fused) {  // (the scan pass does both otherwise)
+        if (blockIdx.x == 0 && threadIdx.x == 0) s.cur[p + 1] = skip ? s.cur[p] : 1u - s.cur[p];
+        // the next pass's group counts start from zero (this pass's are in the other buffer)
+        uint32_t *gn = s.group_buf(((uint32_t)p + 1u) & 1u);
+        for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+             i < 256ull * s.group_stride; i += (unsigned long long)gridDim.x * blockDim.x)
+            gn[i] = 0u;
+    }
+    if (skip || blockIdx.x >= ntiles) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < WARPS * 256; i += kSortThreads) (&wcount[0][0])[i] = 0;
+    // This tile's first position for digit d = threadIdx.x: scanned by the
+    // scan pass, or (fused) the entries with a smaller digit, then digit d's
+    // entries in the earlier tile groups and in the earlier tiles of this
+    // tile's group.
+    const int d = threadIdx.x;
+    uint32_t run;
+    if (fused) {
+        const uint32_t own = s.hist_all[p * 256 + d];
+        uint32_t incl = own;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += x;
+        }
+        if (lane == 31) wtot[warp] = incl;
+        run = incl - own;
+        const uint32_t G = (uint32_t)sort_group_tiles(ntiles), g = blockIdx.x / G;
+        const uint32_t *gb = s.group_buf((uint32_t)p & 1u) + (unsigned long long)d * s.group_stride;
+#pragma unroll 4
+        for (uint32_t q = 0; q < g; q++) run += gb[q];
+        const uint32_t *tb = s.tile_hist + (unsigned long long)d * ntiles;
+#pragma unroll 4
+        for (uint32_t t2 = g * G; t2 < blockIdx.x; t2++) run += tb[t2];
+    } else {
+        run = s.tile_hist[(unsigned long long)d * ntiles + blockIdx.x];
+    }
     __syncthreads();
+    if (fused)
+        for (int w = 0; w < warp; w++) run += wtot[w];
     const uint32_t cur = s.cur[p];
     const uint32_t *in = s.perm_buf(cur);
     uint32_t *out = s.perm_buf(1 - cur);
@@ -387,8 +435,6 @@ __global__ void __launch_bounds__(kSortThreads) k_pass_scatter(J job, int p) {
     __syncthreads();
     // exclusive prefix over warps, per digit (thread d handles digit d)
     {
-        const int d = threadIdx.x;
-        uint32_t run = s.tile_hist[(unsigned long long)d * ntiles + blockIdx.x];
         for (int w = 0; w < WARPS; w++) {
             uint32_t v = wcount[w][d];
             wcount[w][d] = run;
@@ -523,8 +569,7 @@ static int grid_for(unsigned long long n, int threads, int max_blocks) {
 // meta[slot] = meta[0] (entries so far): per-kind counts for capacity hints
 __global__ void k_meta_snapshot(unsigned long long *meta, int slot) { meta[slot] = meta[0]; }
 
-int sort_entries_launches(int passes);
-int finish_table_launches() { return 5 + sort_entries_launches(kPasses) + 1; }
+int finish_table_launches(uint64_t cap) { return 5 + sort_entries_launches(kPasses, cap) + 1; }
 
 // The passes of one sort, for one table (J = OneJob) or a list of them.
 template <class J>
@@ -532,10 +577,11 @@ static void launch_sort(const J &job, uint64_t cap, int ntab, int passes, cudaSt
     const int sms = sm_count();
     k_hist_all<<<dim3(grid_for(cap, 256, sms * 2), ntab), 256, 0, st>>>(job, passes);
     const int ntiles = (int)((cap + kSortTile - 1) / kSortTile);
+    const int fused = (uint64_t)ntiles <= kSortFusedMaxTiles;
     for (int p = 0; p < passes; p++) {
-        k_pass_count<<<dim3(ntiles, ntab), kSortThreads, 0, st>>>(job, p);
-        k_pass_scan<<<dim3(256, ntab), 256, 0, st>>>(job, p);
-        k_pass_scatter<<<dim3(ntiles, ntab), kSortThreads, 0, st>>>(job, p);
+        k_pass_count<<<dim3(ntiles, ntab), kSortThreads, 0, st>>>(job, p, fused);
+        if (!fused) k_pass_scan<<<dim3(256, ntab), 256, 0, st>>>(job, p);
+        k_pass_scatter<<<dim3(ntiles, ntab), kSortThreads, 0, st>>>(job, p, fused);
     }
     k_fix_long<<<dim3(grid_for(cap, 256, sms * 4), ntab), 256, 0, st>>>(job, passes);
 }
@@ -547,13 +593,17 @@ cudaError_t sort_entries(SortScratch &ss, const unsigned long long *meta, const 
     launch_sort(job, ss.cap, 1, passes, st);
     return cudaGetLastError();
 }
-int sort_entries_launches(int passes) { return 1 + 1 + 3 * passes; }
+int sort_entries_launches(int passes, uint64_t cap) {
+    const bool fused = (cap + kSortTile - 1) / kSortTile <= kSortFusedMaxTiles;
+    return 1 + 1 + (fused ? 2 : 3) * passes;
+}
 
 static void launch_compaction(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_t glcap, SortScratch &ss,
                               DevTable &out, cudaStream_t st) {
     const int sms = sm_count();
     cudaMemsetAsync(ss.hist_all, 0, 4 * kPassesSeg * 256, st);
     cudaMemsetAsync(ss.cur, 0, 4 * 32, st);
+    cudaMemsetAsync(ss.group_hist[0], 0, 2 * 4 * 256 * (size_t)ss.group_stride, st);
     k_compact8<<<grid_for(gcap8, 256 * kScanUnroll, sms * 8), 256, 0, st>>>(g.slots8, gcap8, ss, out.d_meta);
     k_meta_snapshot<<<1, 1, 0, st>>>(out.d_meta, 5);
     k_compact_short<<<grid_for(gcap, 256 * kScanUnroll, sms * 8), 256, 0, st>>>(g.slots, gcap, ss, out.d_meta);
@@ -571,7 +621,7 @@ cudaError_t finish_table(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_
 }
 
 size_t finish_tables_job_bytes(int n) { return sizeof(SortJob) * (size_t)(n > 0 ? n : 1); }
-int finish_tables_launches(int n) { return 5 * n + sort_entries_launches(kPasses) + 1; }
+int finish_tables_launches(int n, uint64_t cap) { return 5 * n + sort_entries_launches(kPasses, cap) + 1; }
 
 cudaError_t finish_tables(const FinishSpec *spec, int n, void *d_jobs, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
