@@ -512,7 +512,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="large", choices=["large", "tiny", "classes", "batched", "served"])
-    ap.add_argument("--cpu-sample-mb", type=float, default=150.0)
+    ap.add_argument("--cpu-sample-mb", type=float, default=400.0)
     ap.add_argument("--bytes", type=float, default=1e9, help="corpus size (smaller only for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--docs", type=int, default=0, help="document count of a docs workload (smaller only for profiling)")
