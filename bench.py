@@ -387,16 +387,33 @@ def run_docs_workload(args, local):
     sampler.start()
     wc.wc_profile_enable(ctr.ctx, True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0 = time.perf_counter()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        b = step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
+    # inputs smaller than L2 (129 MB): L2 flushed before every timed step by
+    # writing a 256 MB buffer, each step timed on its own
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}") if c.nbytes < (256 << 20) else None
+    ms_sum, wall = 0.0, 0.0
+    if flush is None:
+        t0 = time.perf_counter()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            b = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ms_sum = ev0.elapsed_time(ev1)
+    else:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ev0.record(stream)
+            b = step()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            wall += time.perf_counter() - t0
+            ms_sum += ev0.elapsed_time(ev1)
     launches = wc.wc_profile_read(ctr.ctx)[4]
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = ms_sum / args.steps
     if tables:
         ms = max(ms, wall * 1e3 / args.steps)  # host waits inside the step count too
     docs_s = c.ndocs / (ms * 1e-3)
@@ -438,6 +455,8 @@ def run_docs_workload(args, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": args.workload, "docs": c.ndocs, "bytes": c.nbytes, "words": c.tokens,
                    "entries": nent,
+                   "l2": "input smaller than L2: flushed (256 MB write) before each timed step" if flush is not None
+                         else "input larger than L2, no flush",
                    "autotuned_shapes": json.load(open(tune)) if os.path.exists(tune) else None},
         "input_GBps": c.nbytes / (ms * 1e-3) / 1e9,
         "per_launch_docs_s": per_launch, "speedup_vs_per_launch": docs_s / per_launch,
