@@ -582,7 +582,7 @@ cudaError_t launch_docs_t(const BatchArgs &a, int grid, cudaStream_t s) {
 }
 
 const DocShape kDocShapes[] = {
-    {128, 10}, {256, 11}, {256, 12}, {512, 12}, {512, 13}, {1024, 13},
+    {128, 10}, {256, 11}, {256, 12}, {512, 12}, {512, 13}, {1024, 13}, {64, 10}, {32, 9},
 };
 const int kNumDocShapes = sizeof(kDocShapes) / sizeof(kDocShapes[0]);
 
@@ -593,7 +593,9 @@ cudaError_t launch_docs(const BatchArgs &a, int shape, cudaStream_t s) {
     case 2: return launch_docs_t<256, 12>(a, 0, s);
     case 3: return launch_docs_t<512, 12>(a, 0, s);
     case 4: return launch_docs_t<512, 13>(a, 0, s);
-    default: return launch_docs_t<1024, 13>(a, 0, s);
+    case 5: return launch_docs_t<1024, 13>(a, 0, s);
+    case 6: return launch_docs_t<64, 10>(a, 0, s);
+    default: return launch_docs_t<32, 9>(a, 0, s);
     }
 }
 

@@ -424,7 +424,7 @@ static wc_status plan_autotune(wc_plan *pl, const uint8_t *d_text, const uint64_
     int bs = b->shape_small, bm = b->shape_medium, bl = b->shape_large;
     if (b->nsmall) {
         float t = 1e30f;
-        for (int s = 0; s <= 2; s++) {
+        for (int s : {0, 1, 2, 6, 7}) {
             float ms = time_shapes(s, bm, bl);
             if (ms < t) { t = ms; bs = s; }
         }

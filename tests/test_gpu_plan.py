@@ -44,7 +44,7 @@ def check(b, c, r):
         assert np.array_equal(w[o[s0]:o[s0 + n]], want.words), f"doc {d}: words"
 
 
-@pytest.mark.parametrize("shapes", [(0, 2, 3), (1, 3, 4), (2, 4, 5), (0, 3, 5)])
+@pytest.mark.parametrize("shapes", [(0, 2, 3), (1, 3, 4), (2, 4, 5), (6, 3, 5), (7, 2, 4)])
 def test_plan_replay_every_shape(docs, shapes, tmp_path):
     import torch
     from paper_2206_05269_gb300 import wc
@@ -78,4 +78,4 @@ def test_plan_autotune_then_replay(docs, tmp_path):
     finally:
         ctr.close()
     tuned = json.loads(cache.read_text())[torch.cuda.get_device_name(0)]
-    assert tuned["small"] in (0, 1, 2) and tuned["medium"] in (2, 3, 4) and tuned["large"] in (3, 4, 5)
+    assert tuned["small"] in (0, 1, 2, 6, 7) and tuned["medium"] in (2, 3, 4) and tuned["large"] in (3, 4, 5)
