@@ -520,9 +520,10 @@ wc_status wc_count_ex(wc_ctx *ctx, const uint8_t *d_text, uint64_t nbytes, const
     ctx->prof_mark(ctx->ev_count, stream);
     ctx->launches += count_global_launches(nbytes, true);
     ctx->prof_mark(ctx->ev_finish, stream);
-    if (e == cudaSuccess) e = finish_table(g, cs.gcap8, cs.gcap, cs.glcap, cs.ss, t->dt, stream);
+    const uint32_t skip = sort_skip_mask(nbytes / 2 + 1, 0);  // no count exceeds the token bound
+    if (e == cudaSuccess) e = finish_table(g, cs.gcap8, cs.gcap, cs.glcap, cs.ss, t->dt, stream, skip);
     ctx->prof_mark(ctx->ev_finish, stream);
-    ctx->launches += finish_table_launches(cs.ss.cap);
+    ctx->launches += finish_table_launches(cs.ss.cap, skip);
     ctx->release(cs.mem, cs.bytes, stream);
     table_mark_done(t, stream);
     if (e != cudaSuccess) {
@@ -603,8 +604,9 @@ wc_status wc_count_host(wc_ctx *ctx, const uint8_t *h_text, uint64_t nbytes, uin
         if (e == cudaSuccess) e = launch_count_global(cl, stream);
         ctx->launches += count_global_launches(cut[i + 1] - cut[i], i == 0 && head);
     }
-    if (e == cudaSuccess) e = finish_table(g, cs.gcap8, cs.gcap, cs.glcap, cs.ss, t->dt, stream);
-    ctx->launches += finish_table_launches(cs.ss.cap);
+    const uint32_t skip = sort_skip_mask(nbytes / 2 + 1, 0);  // no count exceeds the token bound
+    if (e == cudaSuccess) e = finish_table(g, cs.gcap8, cs.gcap, cs.glcap, cs.ss, t->dt, stream, skip);
+    ctx->launches += finish_table_launches(cs.ss.cap, skip);
     for (auto x : ev)
         if (x) cudaEventDestroy(x);  // released once their work completes
     ctx->release(cs.mem, cs.bytes, stream);

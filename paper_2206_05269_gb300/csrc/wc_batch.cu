@@ -757,7 +757,7 @@ __global__ void k_seg_base(BatchArgs a, unsigned long long *meta) {
 __global__ void k_seg_write(SortScratch ss, BatchArgs a, const unsigned long long *meta, int passes) {
     const unsigned long long n = meta[0], base = meta[8];
     if (!meta[9]) return;
-    const uint32_t *perm = ss.perm_buf(ss.cur[passes]);
+    const uint32_t *perm = ss.perm_buf(ss.cur[kCurFinal]);
     const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x * kScanUnroll;
     for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x * kScanUnroll; b < n; b += step) {
         uint32_t e[kScanUnroll], ep[kScanUnroll];
@@ -794,7 +794,7 @@ __global__ void k_seg_write(SortScratch ss, BatchArgs a, const unsigned long lon
 __global__ void k_seg_ends(SortScratch ss, BatchArgs a, const unsigned long long *meta, int passes) {
     const unsigned long long n = meta[0], base = meta[8];
     if (!meta[9]) return;
-    const uint32_t *perm = ss.perm_buf(ss.cur[passes]);
+    const uint32_t *perm = ss.perm_buf(ss.cur[kCurFinal]);
     const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x * kScanUnroll;
     for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x * kScanUnroll; b < n; b += step) {
         uint32_t d[kScanUnroll], dn[kScanUnroll];
@@ -820,7 +820,8 @@ static int gridn(unsigned long long n, int t, int maxb) {
 }
 
 cudaError_t launch_segmented_finish(const BatchArgs &a, const GTable &g, uint64_t cap8, uint64_t cap16,
-                                    uint64_t caplong, SortScratch &ss, unsigned long long *smeta, cudaStream_t s) {
+                                    uint64_t caplong, SortScratch &ss, unsigned long long *smeta, cudaStream_t s,
+                                    uint32_t skip) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -832,13 +833,15 @@ cudaError_t launch_segmented_finish(const BatchArgs &a, const GTable &g, uint64_
     k_bcompact16<<<gridn(cap16, 256 * kScanUnroll, sms * 8), 256, 0, s>>>(g.slots, cap16, ss, smeta);
     k_bcompact_long<<<gridn(caplong, 256, sms * 8), 256, 0, s>>>(g.lslots, caplong, ss, a, smeta);
     LongView v{ss.lref, a.loff, a.llen, a.arena};
-    cudaError_t e = sort_entries(ss, smeta, v, kSortPassesSeg, s);
+    cudaError_t e = sort_entries(ss, smeta, v, kSortPassesSeg, s, skip);
     if (e != cudaSuccess) return e;
     k_seg_base<<<1, 1, 0, s>>>(a, smeta);
     k_seg_write<<<gridn(ss.cap, 256 * kScanUnroll, sms * 8), 256, 0, s>>>(ss, a, smeta, kSortPassesSeg);
     k_seg_ends<<<gridn(ss.cap, 256 * kScanUnroll, sms * 8), 256, 0, s>>>(ss, a, smeta, kSortPassesSeg);
     return cudaGetLastError();
 }
-int segmented_finish_launches(uint64_t cap) { return 3 + sort_entries_launches(kSortPassesSeg, cap) + 3; }
+int segmented_finish_launches(uint64_t cap, uint32_t skip) {
+    return 3 + sort_entries_launches(kSortPassesSeg, cap, skip) + 3;
+}
 
 }  // namespace wc

@@ -43,7 +43,8 @@ extern const int kNumDocShapes;
 
 cudaError_t launch_docs(const BatchArgs &a, int shape, cudaStream_t s);
 cudaError_t launch_segmented_finish(const BatchArgs &a, const GTable &g, uint64_t cap8, uint64_t cap16,
-                                    uint64_t caplong, SortScratch &ss, unsigned long long *smeta, cudaStream_t s);
-int segmented_finish_launches(uint64_t cap);
+                                    uint64_t caplong, SortScratch &ss, unsigned long long *smeta, cudaStream_t s,
+                                    uint32_t skip = 0);
+int segmented_finish_launches(uint64_t cap, uint32_t skip = 0);
 
 }  // namespace wc

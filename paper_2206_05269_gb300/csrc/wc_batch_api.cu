@@ -71,6 +71,7 @@ struct wc_batch {
     // lazily built
     bool tables_built = false;
     bool exact = false;  // capacities at the exact bounds
+    uint64_t max_doc_bytes = 0, total_bytes = 0;  // bounds on counts: no count exceeds half of these
     std::vector<wc_table *> class_tables;
     wc_table *global = nullptr;
     CountScratch gscratch;        // global hash tables kept for ratio lookups
@@ -204,6 +205,7 @@ static wc_status batch_plan(wc_ctx *ctx, const uint64_t *h_offsets, uint32_t ndo
         out_est += exact ? s / 2 + 5 : out_reserve(s);
         long_est += exact ? s / 18 + 1 : std::min<uint64_t>(s / 18 + 1, e / 8 + 2);
         total += s;
+        b->max_doc_bytes = std::max(b->max_doc_bytes, s);
         if (s <= kSmallMax) small.push_back({lo, hi, d, 0});
         else if (s <= kMediumMax) medium.push_back({lo, hi, d, 0});
         else if (s <= kSplitMin) large.push_back({lo, hi, d, 0});
@@ -221,6 +223,7 @@ static wc_status batch_plan(wc_ctx *ctx, const uint64_t *h_offsets, uint32_t ndo
     b->items = small;
     b->items.insert(b->items.end(), medium.begin(), medium.end());
     b->items.insert(b->items.end(), large.begin(), large.end());
+    b->total_bytes = total;
     b->args.out_cap = out_est + 1024;
     b->args.lcap = long_est + 1024;
     b->args.arena_cap = exact ? total + b->args.lcap + 65536 : b->args.lcap * 24 + 65536;
@@ -338,8 +341,9 @@ static cudaError_t batch_enqueue(wc_batch *b, const uint8_t *d_text, const uint6
         n++;
     }
     if (e == cudaSuccess) {
-        e = launch_segmented_finish(a, a.g, cs.gcap8, cs.gcap, cs.glcap, cs.ss, b->scr.smeta, stream);
-        n += segmented_finish_launches(cs.ss.cap);
+        const uint32_t skip = sort_skip_mask(b->max_doc_bytes / 2 + 1, b->ndocs);
+        e = launch_segmented_finish(a, a.g, cs.gcap8, cs.gcap, cs.glcap, cs.ss, b->scr.smeta, stream, skip);
+        n += segmented_finish_launches(cs.ss.cap, skip);
     }
     if (launches) *launches = n;
     return e;
@@ -648,10 +652,11 @@ static wc_status build_tables_at(wc_batch *b, const std::vector<uint64_t> &est, 
         CountScratch &cs = c < b->nclasses ? scr[c] : b->gscratch;
         spec[c] = FinishSpec{c < b->nclasses ? g[c] : gg, cs.gcap8, cs.gcap, cs.glcap, &cs.ss, &tabs[c]->dt};
     }
-    if (e == cudaSuccess) e = finish_tables(spec.data(), (int)nt, static_cast<uint8_t *>(dg) + gbytes, s);
+    const uint32_t skip = sort_skip_mask(b->total_bytes / 2 + 1, 0);
+    if (e == cudaSuccess) e = finish_tables(spec.data(), (int)nt, static_cast<uint8_t *>(dg) + gbytes, s, skip);
     uint64_t capmax = 0;
     for (uint32_t c = 0; c < nt; c++) capmax = std::max<uint64_t>(capmax, spec[c].ss->cap);
-    ctx->launches += 1 + (uint64_t)finish_tables_launches((int)nt, capmax);
+    ctx->launches += 1 + (uint64_t)finish_tables_launches((int)nt, capmax, skip);
     cleanup(nt);
     ctx->release(dg, dbytes, s);
     for (auto *t : tabs) table_mark_done(t, s);

@@ -100,19 +100,26 @@ struct LongView {
     const unsigned long long *loff, *llen;
     const uint8_t *arena;
 };
+// Slot of SortScratch::cur naming the permutation buffer that holds a
+// finished sort's order.
+constexpr int kCurFinal = 31;
+// Radix passes the host knows to be constant, not launched at all: the count
+// digits above the bytes of `max_count` (a bound on every count) and the
+// document digits above those of `ndocs - 1` (bit p: pass p skipped).
+uint32_t sort_skip_mask(uint64_t max_count, uint64_t ndocs);
 // Stable LSD radix sort of ss's n = meta[0] entries by (count desc, word asc);
-// with passes == 28 the document is the most significant key.  The result is
-// the permutation ss.perm[ss.cur[passes]] (device value).
+// with passes == kSortPassesSeg the document is the most significant key.
+// The result is the permutation ss.perm_buf(ss.cur[kCurFinal]) (device value).
 cudaError_t sort_entries(SortScratch &ss, const unsigned long long *meta, const LongView &v, int passes,
-                         cudaStream_t st);
-int sort_entries_launches(int passes, uint64_t cap);
+                         cudaStream_t st, uint32_t skip = 0);
+int sort_entries_launches(int passes, uint64_t cap, uint32_t skip = 0);
 
 // Compacts the global hash tables into unsorted scratch arrays and copies
 // the long words into out.arena; then sorts and writes `out`.
 // finish_table_launches(ss.cap) kernels are launched.
-int finish_table_launches(uint64_t cap);
+int finish_table_launches(uint64_t cap, uint32_t skip = 0);
 cudaError_t finish_table(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_t glcap, SortScratch &ss,
-                         DevTable &out, cudaStream_t s);
+                         DevTable &out, cudaStream_t s, uint32_t skip = 0);
 
 // Compaction scans read kScanUnroll slots a thread per step (independent
 // loads in flight) and reserve output positions with one atomic per block
@@ -175,8 +182,8 @@ struct FinishSpec {
     DevTable *out;
 };
 size_t finish_tables_job_bytes(int n);
-int finish_tables_launches(int n, uint64_t cap);
-cudaError_t finish_tables(const FinishSpec *spec, int n, void *d_jobs, cudaStream_t s);
+int finish_tables_launches(int n, uint64_t cap, uint32_t skip = 0);
+cudaError_t finish_tables(const FinishSpec *spec, int n, void *d_jobs, cudaStream_t s, uint32_t skip = 0);
 
 // Entries of finished tables re-inserted into a global hash table (merge).
 struct MergeSrc {

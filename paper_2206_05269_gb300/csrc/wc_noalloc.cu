@@ -117,7 +117,8 @@ extern "C" wc_status wc_count_noalloc(const uint8_t *d_text, uint64_t nbytes, ui
     if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, kBytes8 + kBytes16 + kBytesLong, stream);
     wc::CountLaunch cl{d_text, 0, nbytes, g, 0, nullptr, {nullptr, nullptr}};
     if (e == cudaSuccess) e = wc::launch_count_global(cl, stream);
-    if (e == cudaSuccess) e = wc::finish_table(g, kNaCap8, kNaCap16, kNaCapLong, ss, out, stream);
+    if (e == cudaSuccess)
+        e = wc::finish_table(g, kNaCap8, kNaCap16, kNaCapLong, ss, out, stream, wc::sort_skip_mask(nbytes / 2 + 1, 0));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return WC_ERR_CUDA;

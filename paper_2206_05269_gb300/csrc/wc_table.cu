@@ -268,7 +268,7 @@ __device__ __forceinline__ bool pass_skipped(const SortScratch &s, int p, unsign
 }
 
 template <class J>
-__global__ void __launch_bounds__(kSortThreads) k_pass_count(J job, int p, int fused) {
+__global__ void __launch_bounds__(kSortThreads) k_pass_count(J job, int p, int e, int fused) {
     const SortScratch &s = job.get().s;
     const unsigned long long *meta = job.get().meta;
     __shared__ uint32_t h[256];
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kSortThreads) k_pass_count(J job, int p, int f
     if (pass_skipped(s, p, n)) return;
     h[threadIdx.x] = 0;
     __syncthreads();
-    const uint32_t *in = s.perm_buf(s.cur[p]);
+    const uint32_t *in = s.perm_buf(s.cur[e]);
     const unsigned long long t0 = (unsigned long long)blockIdx.x * kSortTile + threadIdx.x;
     // all loads first (16 independent gathers in flight per thread), then the histogram
     uint32_t dig[kItems];
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(kSortThreads) k_pass_count(J job, int p, int f
     const uint32_t c = h[threadIdx.x];
     s.tile_hist[(unsigned long long)threadIdx.x * ntiles + blockIdx.x] = c;
     if (fused && c)
-        atomicAdd(&s.group_buf((uint32_t)p & 1u)[(unsigned long long)threadIdx.x * s.group_stride +
+        atomicAdd(&s.group_buf((uint32_t)e & 1u)[(unsigned long long)threadIdx.x * s.group_stride +
                                                  blockIdx.x / sort_group_tiles(ntiles)],
                   c);
 }
@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(kSortThreads) k_pass_count(J job, int p, int f
 // row of tile counts, starting from the number of elements with a smaller
 // digit (from the all-pass histogram).  256 blocks of 256 threads.
 template <class J>
-__global__ void __launch_bounds__(256) k_pass_scan(J job, int p) {
+__global__ void __launch_bounds__(256) k_pass_scan(J job, int p, int e, int last) {
     const SortScratch &s = job.get().s;
     const unsigned long long *meta = job.get().meta;
     __shared__ uint32_t part[256];
@@ -315,7 +315,10 @@ __global__ void __launch_bounds__(256) k_pass_scan(J job, int p) {
     const unsigned long long n = meta[0];
     const bool skip = pass_skipped(s, p, n) || n == 0;
     if (skip) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) s.cur[p + 1] = s.cur[p];
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            s.cur[e + 1] = s.cur[e];
+            if (last) s.cur[kCurFinal] = s.cur[e];
+        }
         return;
     }
     const uint32_t d = blockIdx.x, t = threadIdx.x;
@@ -346,13 +349,16 @@ __global__ void __launch_bounds__(256) k_pass_scan(J job, int p) {
         if (i < ntiles) row[i] = run + part[t] - v;
         run += part[255];
     }
-    if (d == 0 && t == 0) s.cur[p + 1] = 1u - s.cur[p];
+    if (d == 0 && t == 0) {
+        s.cur[e + 1] = 1u - s.cur[e];
+        if (last) s.cur[kCurFinal] = 1u - s.cur[e];
+    }
 }
 
 // Stable scatter: warp w ranks its 512 consecutive elements in order with
 // match_any; warps are combined in order, so equal digits keep their order.
 template <class J>
-__global__ void __launch_bounds__(kSortThreads) k_pass_scatter(J job, int p, int fused) {
+__global__ void __launch_bounds__(kSortThreads) k_pass_scatter(J job, int p, int e, int fused, int last) {
     const SortScratch &s = job.get().s;
     const unsigned long long *meta = job.get().meta;
     constexpr int WARPS = kSortThreads / 32;
@@ -363,9 +369,13 @@ __global__ void __launch_bounds__(kSortThreads) k_pass_scatter(J job, int p, int
     const unsigned long long ntiles = (n + kSortTile - 1) / kSortTile;
     const bool skip = pass_skipped(s, p, n);
     if (fused) {  // (the scan pass does both otherwise)
-        if (blockIdx.x == 0 && threadIdx.x == 0) s.cur[p + 1] = skip ? s.cur[p] : 1u - s.cur[p];
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const uint32_t c = skip ? s.cur[e] : 1u - s.cur[e];
+            s.cur[e + 1] = c;
+            if (last) s.cur[kCurFinal] = c;
+        }
         // the next pass's group counts start from zero (this pass's are in the other buffer)
-        uint32_t *gn = s.group_buf(((uint32_t)p + 1u) & 1u);
+        uint32_t *gn = s.group_buf(((uint32_t)e + 1u) & 1u);
         for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
              i < 256ull * s.group_stride; i += (unsigned long long)gridDim.x * blockDim.x)
             gn[i] = 0u;
@@ -390,7 +400,7 @@ __global__ void __launch_bounds__(kSortThreads) k_pass_scatter(J job, int p, int
         if (lane == 31) wtot[warp] = incl;
         run = incl - own;
         const uint32_t G = (uint32_t)sort_group_tiles(ntiles), g = blockIdx.x / G;
-        const uint32_t *gb = s.group_buf((uint32_t)p & 1u) + (unsigned long long)d * s.group_stride;
+        const uint32_t *gb = s.group_buf((uint32_t)e & 1u) + (unsigned long long)d * s.group_stride;
 #pragma unroll 4
         for (uint32_t q = 0; q < g; q++) run += gb[q];
         const uint32_t *tb = s.tile_hist + (unsigned long long)d * ntiles;
@@ -402,7 +412,7 @@ __global__ void __launch_bounds__(kSortThreads) k_pass_scatter(J job, int p, int
     __syncthreads();
     if (fused)
         for (int w = 0; w < warp; w++) run += wtot[w];
-    const uint32_t cur = s.cur[p];
+    const uint32_t cur = s.cur[e];
     const uint32_t *in = s.perm_buf(cur);
     uint32_t *out = s.perm_buf(1 - cur);
     const unsigned long long t0 = (unsigned long long)blockIdx.x * kSortTile + (unsigned long long)warp * (kSortTile / WARPS);
@@ -479,7 +489,7 @@ __global__ void k_fix_long(J job, int passes) {
     const unsigned long long n = meta[0];
     if (meta[1] == 0) return;
     const bool seg = passes > kPasses;
-    uint32_t *perm = s.perm_buf(s.cur[passes]);
+    uint32_t *perm = s.perm_buf(s.cur[kCurFinal]);
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t e = perm[i];
@@ -516,7 +526,7 @@ __global__ void k_gather_final(J job) {
     const SortScratch &s = job.get().s;
     const DevTable &out = job.get().out;
     const unsigned long long n = out.d_meta[0];
-    const uint32_t *perm = s.perm_buf(s.cur[kPasses]);  // unsegmented: count digits are the last
+    const uint32_t *perm = s.perm_buf(s.cur[kCurFinal]);
     unsigned long long bytes = 0;
     // kScanUnroll entries a thread per step, all gathers issued before the stores
     const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x * kScanUnroll;
@@ -569,33 +579,54 @@ static int grid_for(unsigned long long n, int threads, int max_blocks) {
 // meta[slot] = meta[0] (entries so far): per-kind counts for capacity hints
 __global__ void k_meta_snapshot(unsigned long long *meta, int slot) { meta[slot] = meta[0]; }
 
-int finish_table_launches(uint64_t cap) { return 5 + sort_entries_launches(kPasses, cap) + 1; }
+int finish_table_launches(uint64_t cap, uint32_t skip) { return 5 + sort_entries_launches(kPasses, cap, skip) + 1; }
 
 // The passes of one sort, for one table (J = OneJob) or a list of them.
 template <class J>
-static void launch_sort(const J &job, uint64_t cap, int ntab, int passes, cudaStream_t st) {
+static void launch_sort(const J &job, uint64_t cap, int ntab, int passes, uint32_t skip, cudaStream_t st) {
     const int sms = sm_count();
     k_hist_all<<<dim3(grid_for(cap, 256, sms * 2), ntab), 256, 0, st>>>(job, passes);
     const int ntiles = (int)((cap + kSortTile - 1) / kSortTile);
     const int fused = (uint64_t)ntiles <= kSortFusedMaxTiles;
-    for (int p = 0; p < passes; p++) {
-        k_pass_count<<<dim3(ntiles, ntab), kSortThreads, 0, st>>>(job, p, fused);
-        if (!fused) k_pass_scan<<<dim3(256, ntab), 256, 0, st>>>(job, p);
-        k_pass_scatter<<<dim3(ntiles, ntab), kSortThreads, 0, st>>>(job, p, fused);
+    int lastp = -1;
+    for (int p = 0; p < passes; p++)
+        if (!((skip >> p) & 1u)) lastp = p;
+    // e counts the launched passes: pass e reads its order from cur[e]
+    for (int p = 0, e = 0; p < passes; p++) {
+        if ((skip >> p) & 1u) continue;
+        const int last = p == lastp;
+        k_pass_count<<<dim3(ntiles, ntab), kSortThreads, 0, st>>>(job, p, e, fused);
+        if (!fused) k_pass_scan<<<dim3(256, ntab), 256, 0, st>>>(job, p, e, last);
+        k_pass_scatter<<<dim3(ntiles, ntab), kSortThreads, 0, st>>>(job, p, e, fused, last);
+        e++;
     }
     k_fix_long<<<dim3(grid_for(cap, 256, sms * 4), ntab), 256, 0, st>>>(job, passes);
 }
 
 // LSD radix sort of the entries in ss (count n = meta[0]) into ss.perm_buf(ss.cur[passes]).
 cudaError_t sort_entries(SortScratch &ss, const unsigned long long *meta, const LongView &v, int passes,
-                         cudaStream_t st) {
+                         cudaStream_t st, uint32_t skip) {
     OneJob job{SortJob{ss, meta, v, DevTable{}}};
-    launch_sort(job, ss.cap, 1, passes, st);
+    launch_sort(job, ss.cap, 1, passes, skip, st);
     return cudaGetLastError();
 }
-int sort_entries_launches(int passes, uint64_t cap) {
+int sort_entries_launches(int passes, uint64_t cap, uint32_t skip) {
     const bool fused = (cap + kSortTile - 1) / kSortTile <= kSortFusedMaxTiles;
-    return 1 + 1 + (fused ? 2 : 3) * passes;
+    const uint32_t mask = passes >= 32 ? ~0u : ((1u << passes) - 1u);
+    return 1 + 1 + (fused ? 2 : 3) * (passes - __builtin_popcount(skip & mask));
+}
+
+uint32_t sort_skip_mask(uint64_t max_count, uint64_t ndocs) {
+    auto bytes_of = [](uint64_t x) {
+        int b = 0;
+        while (x) { b++; x >>= 8; }
+        return b;
+    };
+    uint32_t m = 0;
+    for (int b = bytes_of(max_count); b < 8; b++) m |= 1u << (kSortKeyPasses + b);
+    const int db = std::max(1, bytes_of(ndocs ? ndocs - 1 : 0));
+    for (int b = db; b < 4; b++) m |= 1u << (kPasses + b);
+    return m;
 }
 
 static void launch_compaction(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_t glcap, SortScratch &ss,
@@ -612,18 +643,20 @@ static void launch_compaction(const GTable &g, uint64_t gcap8, uint64_t gcap, ui
 }
 
 cudaError_t finish_table(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_t glcap, SortScratch &ss,
-                         DevTable &out, cudaStream_t st) {
+                         DevTable &out, cudaStream_t st, uint32_t skip) {
     launch_compaction(g, gcap8, gcap, glcap, ss, out, st);
     OneJob job{SortJob{ss, out.d_meta, LongView{ss.lref, out.loff, out.llen, out.arena}, out}};
-    launch_sort(job, ss.cap, 1, kPasses, st);
+    launch_sort(job, ss.cap, 1, kPasses, skip, st);
     k_gather_final<<<grid_for(ss.cap, 256 * kScanUnroll, sm_count() * 8), 256, 0, st>>>(job);
     return cudaGetLastError();
 }
 
 size_t finish_tables_job_bytes(int n) { return sizeof(SortJob) * (size_t)(n > 0 ? n : 1); }
-int finish_tables_launches(int n, uint64_t cap) { return 5 * n + sort_entries_launches(kPasses, cap) + 1; }
+int finish_tables_launches(int n, uint64_t cap, uint32_t skip) {
+    return 5 * n + sort_entries_launches(kPasses, cap, skip) + 1;
+}
 
-cudaError_t finish_tables(const FinishSpec *spec, int n, void *d_jobs, cudaStream_t st) {
+cudaError_t finish_tables(const FinishSpec *spec, int n, void *d_jobs, cudaStream_t st, uint32_t skip) {
     if (n <= 0) return cudaSuccess;
     std::vector<SortJob> jobs((size_t)n);
     uint64_t cap = 0;
@@ -636,7 +669,7 @@ cudaError_t finish_tables(const FinishSpec *spec, int n, void *d_jobs, cudaStrea
     cudaError_t e = cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(SortJob) * jobs.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
     JobList list{static_cast<const SortJob *>(d_jobs)};
-    launch_sort(list, cap, n, kPasses, st);
+    launch_sort(list, cap, n, kPasses, skip, st);
     k_gather_final<<<dim3(grid_for(cap, 256 * kScanUnroll, sm_count() * 8), n), 256, 0, st>>>(list);
     return cudaGetLastError();
 }
