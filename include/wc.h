@@ -108,6 +108,19 @@ wc_status wc_count_ex(wc_ctx *ctx, const uint8_t *d_text, uint64_t nbytes,
 wc_status wc_count_host(wc_ctx *ctx, const uint8_t *h_text, uint64_t nbytes, uint8_t *d_buf, uint64_t piece_bytes,
                         const wc_count_opts *opts, cudaStream_t stream, wc_table **out);
 
+/* Counts one document held in host memory that need not fit on the device
+ * (Sec. 3.3's reduce applied across chunks): h_text[0, nbytes) is cut into
+ * chunks of about chunk_bytes (0: 512 MB; at least 1 MB) after a non-letter
+ * byte, each chunk is counted with wc_count_host through one reused device
+ * buffer of the chunk size (its long words are copied into its table, so the
+ * buffer can take the next chunk), a chunk whose table overflows is counted
+ * again with four times the capacities (at most four times), and each
+ * chunk's table is merged into the running total (wc_merge).  Device memory:
+ * the buffer, one chunk's tables and two totals.  Waits for each chunk's
+ * status; *out is the total.  Errors as wc_count_host and wc_merge. */
+wc_status wc_count_stream(wc_ctx *ctx, const uint8_t *h_text, uint64_t nbytes, uint64_t chunk_bytes,
+                          cudaStream_t stream, wc_table **out);
+
 /* Counts ndocs documents in one pass: document i is d_text[d_offsets[i],
  * d_offsets[i+1]) (device uint64, non-decreasing, d_offsets[0] may be > 0).
  * d_class (device uint32, may be NULL) assigns each document a class below

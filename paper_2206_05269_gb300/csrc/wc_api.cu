@@ -633,9 +633,11 @@ wc_status wc_merge(wc_ctx *ctx, const wc_table *const *in, uint32_t n, cudaStrea
         const DevTable &d = in[i]->dt;
         src[i] = MergeSrc{d.d_meta, d.khi, d.klo, d.cnt, d.lref, d.loff, d.llen, d.arena, d.count_bits, d.cap,
                           d.arena_cap};
-        sum_cap += d.cap;
-        sum_lcap += d.lcap;
-        sum_arena += d.arena_cap;
+        // a table already waited for gives its sizes, any other its capacities
+        const bool known = in[i]->synced && in[i]->sync_status == WC_OK;
+        sum_cap += known ? in[i]->n : d.cap;
+        sum_lcap += known ? in[i]->nlong : d.lcap;
+        sum_arena += known ? in[i]->word_bytes + in[i]->nlong : d.arena_cap;
         cstart[i] = chunks;
         chunks += (d.cap + kMergeChunk - 1) / kMergeChunk;
         cudaStreamWaitEvent(stream, in[i]->done, 0);
@@ -682,6 +684,77 @@ wc_status wc_merge(wc_ctx *ctx, const wc_table *const *in, uint32_t n, cudaStrea
         return ctx->cuda_fail(e, "merge");
     }
     *out = t;
+    return WC_OK;
+}
+
+// ---------------------------------------------------------------- streaming count
+wc_status wc_count_stream(wc_ctx *ctx, const uint8_t *h_text, uint64_t nbytes, uint64_t chunk_bytes,
+                          cudaStream_t stream, wc_table **out) {
+    if (!ctx || !out) return WC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!h_text && nbytes) return ctx->fail(WC_ERR_INVALID_ARG, "null text");
+    if (!chunk_bytes) chunk_bytes = 512ull << 20;
+    if (chunk_bytes < (1ull << 20)) return ctx->fail(WC_ERR_INVALID_ARG, "chunk_bytes below 1 MB");
+    cudaSetDevice(ctx->device);
+    void *buf = nullptr;
+    uint64_t bufb = 0;
+    wc_table *acc = nullptr;
+    wc_status st = WC_OK;
+    for (uint64_t lo = 0; st == WC_OK && (lo < nbytes || !acc);) {
+        // a chunk ends after a non-letter byte (a word running past it extends it)
+        uint64_t hi = std::min(nbytes, lo + chunk_bytes);
+        while (hi < nbytes && host_letter(h_text[hi - 1]) && host_letter(h_text[hi])) hi++;
+        const uint64_t n = hi - lo;
+        if (n + 16 > bufb) {
+            if (buf) ctx->release(buf, bufb, stream);
+            buf = nullptr;
+            bufb = std::max<uint64_t>(n, chunk_bytes) + 16;
+            if ((st = ctx->alloc(&buf, bufb, stream)) != WC_OK) {
+                bufb = 0;
+                break;
+            }
+        }
+        // the chunk's table, counted again with larger capacities on overflow
+        wc_count_opts o{0, 0, 0};
+        wc_table *t = nullptr;
+        for (int attempt = 0;; attempt++) {
+            st = wc_count_host(ctx, n ? h_text + lo : nullptr, n, static_cast<uint8_t *>(buf), 0,
+                               attempt ? &o : nullptr, stream, &t);
+            if (st == WC_OK) st = wc_table_status(t);
+            if (st != WC_ERR_CAPACITY || attempt == 4) break;
+            wc_table_free(t);
+            t = nullptr;
+            if (!attempt) o = wc_count_opts{std::max<uint64_t>(1024, n / 4), std::max<uint64_t>(256, n / 64),
+                                            std::max<uint64_t>(4096, n / 8)};
+            o.table_slots *= 4;
+            o.long_slots *= 4;
+            o.arena_bytes *= 4;
+        }
+        if (st != WC_OK) {
+            if (t) wc_table_free(t);
+            break;
+        }
+        if (!acc) {
+            acc = t;
+        } else {  // the running total plus this chunk (both freed once the merge has read them)
+            const wc_table *pair[2] = {acc, t};
+            wc_table *m = nullptr;
+            st = wc_merge(ctx, pair, 2, stream, &m);
+            if (st == WC_OK) st = wc_table_status(m);
+            wc_table_free(acc);
+            wc_table_free(t);
+            acc = st == WC_OK ? m : nullptr;
+            if (st != WC_OK && m) wc_table_free(m);
+        }
+        lo = hi;
+        if (!nbytes) break;
+    }
+    if (buf) ctx->release(buf, bufb, stream);
+    if (st != WC_OK) {
+        if (acc) wc_table_free(acc);
+        return st;
+    }
+    *out = acc;
     return WC_OK;
 }
 

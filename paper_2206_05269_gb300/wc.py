@@ -34,7 +34,8 @@ WC_BATCH_EXACT_BOUNDS = 1
 
 # Every symbol include/wc.h declares (checked by the tests).
 EXPORTS = [
-    "wc_create", "wc_destroy", "wc_count", "wc_count_ex", "wc_count_host", "wc_count_batched", "wc_count_batched_ex", "wc_batch_status",
+    "wc_create", "wc_destroy", "wc_count", "wc_count_ex", "wc_count_host", "wc_count_stream", "wc_count_batched",
+    "wc_count_batched_ex", "wc_batch_status",
     "wc_batch_table", "wc_batch_topk", "wc_batch_size", "wc_batch_export",
     "wc_class_ratio_topk", "wc_merge", "wc_topk", "wc_table_status", "wc_table_size",
     "wc_table_export", "wc_table_count_bits", "wc_table_free", "wc_batch_free", "wc_plan_create", "wc_plan_run",
@@ -79,6 +80,7 @@ def load() -> ctypes.CDLL:
         "wc_count": (i32, [vp, vp, u64, vp, pvp]),
         "wc_count_ex": (i32, [vp, vp, u64, ctypes.POINTER(WcCountOpts), vp, pvp]),
         "wc_count_host": (i32, [vp, vp, u64, vp, u64, ctypes.POINTER(WcCountOpts), vp, pvp]),
+        "wc_count_stream": (i32, [vp, vp, u64, u64, vp, pvp]),
         "wc_count_batched": (i32, [vp, vp, vp, vp, u32, vp, u32, vp, pvp]),
         "wc_count_batched_ex": (i32, [vp, vp, vp, vp, u32, vp, u32, u32, vp, pvp]),
         "wc_batch_status": (i32, [vp]),
@@ -156,6 +158,12 @@ def wc_count_host(ctx, h_text: int, nbytes: int, d_buf: int | None, piece_bytes:
     o = WcCountOpts(*(opts or (0, 0, 0)))
     _check(load().wc_count_host(ctx, h_text, nbytes, d_buf, piece_bytes, ctypes.byref(o), stream, ctypes.byref(out)),
            ctx, "wc_count_host")
+    return out
+
+
+def wc_count_stream(ctx, h_text: int, nbytes: int, chunk_bytes: int, stream: int):
+    out = ctypes.c_void_p()
+    _check(load().wc_count_stream(ctx, h_text, nbytes, chunk_bytes, stream, ctypes.byref(out)), ctx, "wc_count_stream")
     return out
 
 
@@ -491,6 +499,14 @@ class Counter:
         n = int(text.numel())
         return Table(wc_count_host(self.ctx, text.data_ptr() if n else None, n,
                                    out.data_ptr() if out is not None else None, piece_bytes, opts, s), counter=self)
+
+    def count_stream(self, text, chunk_bytes: int = 0, stream=None) -> Table:
+        """Counts a host text (a uint8 CPU tensor, pinned for overlap) that
+        need not fit on the device: chunk by chunk through one device buffer,
+        each chunk's table merged into the total (wc_count_stream)."""
+        n = int(text.numel())
+        return Table(wc_count_stream(self.ctx, text.data_ptr() if n else None, n, chunk_bytes,
+                                     _stream_handle(stream)), counter=self)
 
     def count_host_checked(self, text, stream=None, out=None, piece_bytes: int = 0, retries: int = 4) -> Table:
         """count_host() that waits for the result and counts again with 4x

@@ -221,3 +221,26 @@ def test_count_from_host_memory_empty(ctr):
     import torch
     t = ctr.count_host_checked(torch.zeros(0, dtype=torch.uint8))
     assert t.size()[0] == 0
+
+
+@pytest.mark.parametrize("chunk_mb", [1, 3])
+def test_count_stream_chunks_equal_one_count(ctr, chunk_mb):
+    """A host text counted chunk by chunk through one device buffer and
+    merged equals the oracle: chunks cut between words, a word longer than a
+    chunk extending its chunk, long words kept by their tables."""
+    import torch
+    text = corpus.generate("large", size_a=9e6).text
+    longword = np.frombuffer(b" " + b"Qz" * (700 << 10) + b" ", np.uint8)  # 1.4 MB word
+    full = np.concatenate([text[:4_000_000], longword, text[4_000_000:]])
+    host = torch.from_numpy(full).pin_memory()
+    t = ctr.count_stream(host, chunk_bytes=chunk_mb << 20)
+    assert_same(t.export(), oracle.count(full).glob(), f"stream, {chunk_mb} MB chunks")
+
+
+def test_count_stream_empty_and_small(ctr):
+    import torch
+    for data in (b"", b"a", b"The cat; the CAT's hat."):
+        arr = np.frombuffer(data, np.uint8) if data else np.zeros(0, np.uint8)
+        host = torch.from_numpy(np.array(arr, copy=True))
+        t = ctr.count_stream(host)
+        assert_same(t.export(), oracle.count(arr).glob(), f"stream {data!r}")
