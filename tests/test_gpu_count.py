@@ -159,6 +159,20 @@ def test_merge_equals_concatenation(ctr):
     assert_same(m.export(), want, "merge")
 
 
+def test_merge_unsynced_and_chained(ctr):
+    """Tables not yet waited for (the merge sizes from their capacities),
+    then a chain of merges of merges (sized from the known sizes)."""
+    c = corpus.generate("tiny", ndocs=8, len_max=30, len_tail=0.3, len_tail_mean=8.0)
+    docs = [c.text[c.offsets[i]:c.offsets[i + 1]].tobytes() for i in range(c.ndocs)]
+    devs = [to_dev(d) for d in docs]
+    tabs = [ctr.count(t) for t in devs]
+    acc = ctr.merge(tabs[:4])
+    for t in tabs[4:]:
+        acc = ctr.merge([acc, t])
+        assert acc.status() == 0
+    assert_same(acc.export(), oracle.count(b" ".join(docs)).glob(), "chained merge")
+
+
 def test_topk(ctr):
     c = corpus.generate("tiny", ndocs=10)
     t = ctr.count_checked(to_dev(c.text.tobytes()))
