@@ -182,7 +182,7 @@ def test_topk(ctr):
         assert top.as_list() == want.as_list()[:k]
 
 
-def test_count_bits_32():
+def test_count_bits_32(ctr):
     from paper_2206_05269_gb300 import wc
     c32 = wc.Counter(0, count_bits=32)
     c = corpus.generate("tiny", ndocs=5)
@@ -194,7 +194,7 @@ def test_count_bits_32():
     c32.close()
 
 
-def test_budget_rejects():
+def test_budget_rejects(ctr):
     from paper_2206_05269_gb300 import wc
     small = wc.Counter(0, budget=1 << 20)
     c = corpus.generate("large", size_a=8e6)
