@@ -10,7 +10,9 @@
 // (count descending), then a fix-up that orders long words sharing count and
 // 16-letter prefix by their remaining bytes.  Every pass is stable, so the
 // final order is (count desc, word asc).  Digits that are equal for every
-// element are skipped, detected on the device from one histogram pass.
+// element are skipped, detected on the device from one histogram pass; those
+// the host's bounds already show constant (count bytes above the token bound,
+// document bytes above the document count) are not launched at all.
 #include <algorithm>
 #include <vector>
 
