@@ -325,7 +325,8 @@ def run_gpu(args, rank, world, local):
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_count2<false>", "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": alg_bytes,
-                         "read_ceiling_GBps": read_ceiling, "frac_of_read_ceiling": achieved / read_ceiling},
+                         "read_ceiling_GBps": read_ceiling, "frac_of_read_ceiling": achieved / read_ceiling,
+                         "nominal_peak_GBps": 7900.0, "frac_of_nominal": achieved / 7900.0},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clocks,
