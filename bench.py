@@ -235,7 +235,7 @@ def run_gpu(args, rank, world, local):
     ev0.record(stream)
     for _ in range(args.steps):
         tables.append(step())
-        if len(tables) > 8:  # bound device memory: the oldest step is long finished
+        if len(tables) > 32:  # bound device memory (about 1 GB of tables): the oldest step is long finished
             done.append(tables.pop(0).status())
     ev1.record(stream)
     torch.cuda.synchronize()
