@@ -258,3 +258,13 @@ def test_count_stream_empty_and_small(ctr):
         host = torch.from_numpy(np.array(arr, copy=True))
         t = ctr.count_stream(host)
         assert_same(t.export(), oracle.count(arr).glob(), f"stream {data!r}")
+
+
+def test_counts_across_digit_boundaries(ctr):
+    """Counts just above and below 2^8, 2^16 and 2^24: every count digit the
+    token bound leaves in the sort is ordered (count desc, word asc)."""
+    parts = [(b"a", (1 << 24) + 1), (b"b", (1 << 24) - 1), (b"c", (1 << 16) + 1), (b"dd", 1 << 16),
+             (b"e", (1 << 16) - 1), (b"f", 257), (b"g", 256), (b"h", 255), (b"i", 1)]
+    text = b"".join((w + b" ") * n for w, n in parts)
+    t = ctr.count_checked(to_dev(text))
+    assert t.as_list() == [(w, n) for w, n in parts]
