@@ -384,20 +384,47 @@ wc_status wc_table_export(const wc_table *t, uint8_t *h_words, uint64_t *h_word_
     const DevTable &d = t->dt;
     const uint64_t n = t->n;
     cudaError_t e = cudaSuccess;
+    // the counts go to the host on the context's copy stream while the word
+    // bytes and offsets are built on `stream` (overlapped when h_counts is pinned)
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    const bool side = h_counts && n && (h_words || h_word_offsets) &&
+                      (ctx->copy_stream || cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) ==
+                                               cudaSuccess) &&
+                      cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) == cudaSuccess &&
+                      cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) == cudaSuccess;
     if (h_counts && n) {
-        e = cudaMemcpyAsync(h_counts, d.cnt, n * (d.count_bits / 8), cudaMemcpyDeviceToHost, stream);
-        if (e != cudaSuccess) return ctx->cuda_fail(e, "copying counts");
+        if (side) {
+            cudaEventRecord(ev[0], stream);
+            cudaStreamWaitEvent(ctx->copy_stream, ev[0], 0);
+        }
+        e = cudaMemcpyAsync(h_counts, d.cnt, n * (d.count_bits / 8), cudaMemcpyDeviceToHost,
+                            side ? ctx->copy_stream : stream);
+        if (side) cudaEventRecord(ev[1], ctx->copy_stream);
+        if (e != cudaSuccess) {
+            for (auto x : ev)
+                if (x) cudaEventDestroy(x);
+            return ctx->cuda_fail(e, "copying counts");
+        }
     }
+    auto abandon = [&](wc_status st) {  // an allocation failed: let the counts copy land first
+        if (side) cudaStreamSynchronize(ctx->copy_stream);
+        for (auto x : ev)
+            if (x) cudaEventDestroy(x);
+        return st;
+    };
     if (h_words || h_word_offsets) {
         size_t sb = export_scratch_bytes(d.cap);
         size_t wb = t->word_bytes ? t->word_bytes : 1;
         void *scratch = nullptr, *dwords = nullptr, *doffs = nullptr;
-        if ((s = ctx->alloc(&scratch, sb, stream)) != WC_OK) return s;
-        if ((s = ctx->alloc(&dwords, wb, stream)) != WC_OK) { ctx->release(scratch, sb, stream); return s; }
+        if ((s = ctx->alloc(&scratch, sb, stream)) != WC_OK) return abandon(s);
+        if ((s = ctx->alloc(&dwords, wb, stream)) != WC_OK) {
+            ctx->release(scratch, sb, stream);
+            return abandon(s);
+        }
         if ((s = ctx->alloc(&doffs, (d.cap + 1) * 8, stream)) != WC_OK) {
             ctx->release(scratch, sb, stream);
             ctx->release(dwords, wb, stream);
-            return s;
+            return abandon(s);
         }
         e = launch_export(d, scratch, static_cast<uint8_t *>(dwords), static_cast<unsigned long long *>(doffs), stream);
         if (e == cudaSuccess && h_words && t->word_bytes)
@@ -407,10 +434,13 @@ wc_status wc_table_export(const wc_table *t, uint8_t *h_words, uint64_t *h_word_
         ctx->release(scratch, sb, stream);
         ctx->release(dwords, wb, stream);
         ctx->release(doffs, (d.cap + 1) * 8, stream);
-        if (e != cudaSuccess) return ctx->cuda_fail(e, "export");
     }
-    e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaStreamSynchronize (export)");
+    if (side) cudaStreamWaitEvent(stream, ev[1], 0);
+    const cudaError_t es = cudaStreamSynchronize(stream);
+    for (auto x : ev)
+        if (x) cudaEventDestroy(x);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "export");
+    if (es != cudaSuccess) return ctx->cuda_fail(es, "cudaStreamSynchronize (export)");
     return WC_OK;
 }
 
