@@ -810,18 +810,34 @@ __global__ void k_export_lens(DevTable t, unsigned long long *offs, unsigned lon
     if (threadIdx.x == 255) blocksum[blockIdx.x] = part[255];
 }
 
-__global__ void k_export_blocksums(const DevTable t, unsigned long long *blocksum, unsigned long long *offs) {
+// Exclusive scan of the scan blocks' byte counts, in one block: each thread
+// sums a contiguous run of them, the run totals are scanned in shared
+// memory, and each thread writes its run's prefixes.
+constexpr int kBlockSumThreads = 1024;
+__global__ void __launch_bounds__(kBlockSumThreads) k_export_blocksums(const DevTable t, unsigned long long *blocksum,
+                                                                       unsigned long long *offs) {
+    __shared__ unsigned long long part[kBlockSumThreads];
     const unsigned long long n = t.d_meta[0];
     const unsigned long long nb = (n + kScanBlock - 1) / kScanBlock;
-    if (threadIdx.x == 0) {
-        unsigned long long run = 0;
-        for (unsigned long long b = 0; b < nb; b++) {
-            unsigned long long v = blocksum[b];
-            blocksum[b] = run;
-            run += v;
-        }
-        offs[n] = run;
+    const unsigned long long per = (nb + kBlockSumThreads - 1) / kBlockSumThreads;
+    const unsigned long long lo = threadIdx.x * per, hi = lo + per < nb ? lo + per : nb;
+    unsigned long long own = 0;
+    for (unsigned long long b = lo; b < hi; b++) own += blocksum[b];
+    part[threadIdx.x] = own;
+    __syncthreads();
+    for (int o = 1; o < kBlockSumThreads; o <<= 1) {
+        const unsigned long long x = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0ull;
+        __syncthreads();
+        part[threadIdx.x] += x;
+        __syncthreads();
     }
+    unsigned long long run = part[threadIdx.x] - own;
+    for (unsigned long long b = lo; b < hi; b++) {
+        const unsigned long long v = blocksum[b];
+        blocksum[b] = run;
+        run += v;
+    }
+    if (threadIdx.x == kBlockSumThreads - 1) offs[n] = part[kBlockSumThreads - 1];
 }
 
 __global__ void k_export_write(DevTable t, unsigned long long *offs, const unsigned long long *blocksum, uint8_t *words) {
@@ -849,7 +865,7 @@ cudaError_t launch_export(const DevTable &t, void *scratch, uint8_t *d_words, un
     unsigned long long *blocksum = static_cast<unsigned long long *>(scratch);
     const int nb = (int)((t.cap + kScanBlock - 1) / kScanBlock);
     k_export_lens<<<nb > 0 ? nb : 1, 256, 0, s>>>(t, d_offs, blocksum);
-    k_export_blocksums<<<1, 32, 0, s>>>(t, blocksum, d_offs);
+    k_export_blocksums<<<1, kBlockSumThreads, 0, s>>>(t, blocksum, d_offs);
     k_export_write<<<grid_for(t.cap, 256, sm_count() * 8), 256, 0, s>>>(t, d_offs, blocksum, d_words);
     return cudaGetLastError();
 }
