@@ -77,7 +77,12 @@ typedef struct {
 enum { WC_TABLE_DOC = 0, WC_TABLE_CLASS = 1, WC_TABLE_GLOBAL = 2 };
 
 /* Creates a context on cfg->device (NULL cfg = defaults: device 0, no
- * budget, 64-bit counts, no autotune).  *out is set on WC_OK only. */
+ * budget, 64-bit counts, no autotune).  *out is set on WC_OK only.  The
+ * context is the resident state of the paper's GPU reduce (Sec. 3.3: the
+ * device that sums the per-document counts), extended to the map (Sec. 5.2's
+ * GPU dictionary): a stream-ordered memory pool charged against the budget,
+ * capacity history, pinned metadata slots.  Errors: WC_ERR_INVALID_ARG (bad
+ * device or count width), WC_ERR_CUDA. */
 wc_status wc_create(const wc_config *cfg, wc_ctx **out);
 /* Destroys the context and its memory pool.  Free every table, batch and plan
  * made with it first: they hold the context, and freeing one after its
@@ -212,21 +217,28 @@ wc_status wc_class_ratio_topk(wc_ctx *ctx, const wc_batch *batch, uint32_t cls, 
 wc_status wc_merge(wc_ctx *ctx, const wc_table *const *in, uint32_t n, cudaStream_t stream,
                    wc_table **out);
 
-/* The first k rows of a table in its sorted order (k >= size: all rows). */
+/* The first k rows of a table in its sorted order (k >= size: all rows):
+ * the most frequent words, as Sec. 4.3 reports per speech.  Asynchronous;
+ * *out is a new table owned by the caller (wc_table_free).  Errors:
+ * WC_ERR_INVALID_ARG, WC_ERR_OOM / WC_ERR_BUDGET. */
 wc_status wc_topk(wc_ctx *ctx, const wc_table *in, uint32_t k, cudaStream_t stream,
                   wc_table **out);
 
 /* Waits for the table; reports WC_ERR_CAPACITY / WC_ERR_TIMEOUT from the device. */
 wc_status wc_table_status(const wc_table *t);
 
-/* Waits for the table, then gives its distinct words, total count (tokens)
- * and the bytes needed for wc_table_export's h_words. */
+/* Waits for the table, then gives its distinct words (the keys of the
+ * paper's dictionary, Sec. 3.1), total count (tokens) and the bytes needed
+ * for wc_table_export's h_words.  Any output pointer may be NULL.  A table
+ * whose device work overflowed reports WC_ERR_CAPACITY and sizes 0. */
 wc_status wc_table_size(const wc_table *t, uint64_t *nwords, uint64_t *ntokens,
                         uint64_t *word_bytes);
 
-/* Copies the sorted table to the host: h_words (word_bytes bytes, words back
- * to back), h_word_offsets (nwords+1 entries), h_counts (nwords entries of
- * uint32 or uint64 per wc_table_count_bits).  Any pointer may be NULL to skip
+/* Copies the sorted table to the host (the word -> count dictionary of
+ * Sec. 3.1, in count-descending, word-ascending order): h_words (word_bytes
+ * bytes, words back to back), h_word_offsets (nwords+1 entries), h_counts
+ * (nwords entries of uint32 or uint64 per wc_table_count_bits).  Buffers are
+ * caller-owned, sized from wc_table_size.  Any pointer may be NULL to skip
  * that array.  Waits until the copy is complete. */
 wc_status wc_table_export(const wc_table *t, uint8_t *h_words, uint64_t *h_word_offsets,
                           void *h_counts, cudaStream_t stream);
@@ -258,9 +270,11 @@ void wc_batch_free(wc_batch *b);
  * Stream-ordered and asynchronous like wc_count: results are valid once the
  * stream has reached the call.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  All calls on a device
- * share the array and each clears it; calls whose work overlaps on the GPU
- * race, so keep them on one stream, in order. */
+ * make that first call before any stream capture.  The address is kept per
+ * device ordinal for the life of the process: calling after cudaDeviceReset,
+ * or with a non-primary context current, is not supported.  All calls on a
+ * device share the array and each clears it; calls whose work overlaps on the
+ * GPU race, so keep them on one stream, in order. */
 wc_status wc_count_noalloc(const uint8_t *d_text, uint64_t nbytes, uint64_t *d_khi, uint64_t *d_klo,
                            uint64_t *d_cnt, uint32_t *d_lref, uint64_t out_cap, uint64_t *d_loff,
                            uint64_t *d_llen, uint64_t long_cap, uint8_t *d_arena, uint64_t arena_cap,

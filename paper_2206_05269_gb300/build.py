@@ -2,6 +2,11 @@
 
 Each translation unit is compiled by nvcc in parallel, then linked into
 paper_2206_05269_gb300/_build/libwc.so with the static CUDA runtime.
+
+build(variant="oneslot") builds a test-only copy into _build/oneslot/ with
+-DWC_TEST_ONE_SLOT: every hash is a constant, so every key of a table starts
+at one home slot (the parity tests' forced-collision build).  Nothing but
+those tests loads it.
 """
 from __future__ import annotations
 
@@ -40,18 +45,28 @@ def _stale(target: str, inputs: list[str]) -> bool:
     return any(os.path.getmtime(i) > t for i in inputs)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OUT, exist_ok=True)
+VARIANTS = {None: [], "oneslot": ["-DWC_TEST_ONE_SLOT"]}
+
+
+def lib_path(variant: str | None = None) -> str:
+    return LIB if variant is None else os.path.join(OUT, variant, "libwc.so")
+
+
+def build(force: bool = False, verbose: bool = False, variant: str | None = None) -> str:
+    if variant not in VARIANTS:
+        raise ValueError(f"unknown build variant {variant!r}")
+    out = OUT if variant is None else os.path.join(OUT, variant)
+    os.makedirs(out, exist_ok=True)
     import fcntl
-    with open(os.path.join(OUT, ".lock"), "w") as lk:
+    with open(os.path.join(out, ".lock"), "w") as lk:
         fcntl.flock(lk, fcntl.LOCK_EX)
         try:
-            return _build(force, verbose)
+            return _build(force, verbose, out, VARIANTS[variant], lib_path(variant))
         finally:
             fcntl.flock(lk, fcntl.LOCK_UN)
 
 
-def _build(force: bool, verbose: bool) -> str:
+def _build(force: bool, verbose: bool, out: str, extra: list[str], lib: str) -> str:
     nvcc = _nvcc()
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
     deps = _deps()
@@ -59,10 +74,10 @@ def _build(force: bool, verbose: bool) -> str:
     jobs = []
     for s in srcs:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(OUT, s.replace(".cu", ".o"))
+        obj = os.path.join(out, s.replace(".cu", ".o"))
         objs.append(obj)
         if force or _stale(obj, [src] + deps):
-            jobs.append([nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj])
+            jobs.append([nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -74,11 +89,11 @@ def _build(force: bool, verbose: bool) -> str:
     if jobs:
         with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
             list(ex.map(run, jobs))
-    if force or _stale(LIB, objs):
-        tmp = LIB + f".{os.getpid()}.tmp"
+    if force or _stale(lib, objs):
+        tmp = lib + f".{os.getpid()}.tmp"
         run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

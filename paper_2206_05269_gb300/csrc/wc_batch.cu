@@ -42,6 +42,7 @@ __device__ __forceinline__ unsigned long long restore_letters(unsigned long long
     return c | (nz >> 1) | (nz >> 2);
 }
 __device__ __forceinline__ unsigned long long long_doc_hash(unsigned long long h, uint32_t d) {
+    if (kOneSlot) return h;  // test build: one home slot for every document's long words
     return h ^ fmix64((unsigned long long)d + 0x632BE59BD9B4E019ull);
 }
 
@@ -564,12 +565,8 @@ __global__ void __launch_bounds__(BLOCK, (DocCfg<BLOCK, LOGC1>::MINB)) k_docs(Ba
 template <int BLOCK, int LOGC1>
 cudaError_t launch_docs_t(const BatchArgs &a, int grid, cudaStream_t s) {
     using C = DocCfg<BLOCK, LOGC1>;
-    static bool set = false;
-    if (!set) {
-        cudaError_t e = cudaFuncSetAttribute(k_docs<BLOCK, LOGC1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        if (e != cudaSuccess) return e;
-        set = true;
-    }
+    const cudaError_t ea = ensure_smem_limit((const void *)k_docs<BLOCK, LOGC1>, (int)C::SMEM);
+    if (ea != cudaSuccess) return ea;
     if (grid <= 0) {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);

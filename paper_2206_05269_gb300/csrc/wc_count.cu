@@ -33,6 +33,9 @@
 //     one per lane, into the global long-word table.
 //  5. At the end each block adds its head counts into the global table.
 #include <algorithm>
+#include <mutex>
+#include <set>
+#include <tuple>
 
 #include "wc_internal.h"
 
@@ -151,6 +154,7 @@ __device__ __forceinline__ unsigned long long load_key8(const uint8_t *win, uint
 }
 
 __device__ __forceinline__ uint32_t head_bucket(unsigned long long key, unsigned long long mul, uint32_t nb) {
+    if (kOneSlot) return 0u;  // test build: one bucket for every head word
     return __umulhi((uint32_t)((key * mul) >> 32), nb);
 }
 constexpr unsigned long long kHeadMulA = 0x9E3779B97F4A7C15ull;
@@ -716,15 +720,24 @@ int count_global_launches(uint64_t nbytes, bool head) {
     return (nbytes >= kHeadMinBytes && head) ? 6 : (nbytes ? 1 : 0);
 }
 
+cudaError_t ensure_smem_limit(const void *func, int bytes) {
+    static std::mutex mu;
+    static std::set<std::tuple<const void *, int, int>> done;  // (kernel, device, bytes)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_tuple(func, dev, bytes);
+    if (done.count(key)) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.insert(key);
+    return e;
+}
+
 cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_count2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCountSmem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_count2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCountSmem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    cudaError_t ea = ensure_smem_limit((const void *)k_count2<false>, (int)kCountSmem);
+    if (ea == cudaSuccess) ea = ensure_smem_limit((const void *)k_count2<true>, (int)kCountSmem);
+    if (ea != cudaSuccess) return ea;
     if (c.hi <= c.lo) return cudaSuccess;
     const int sms = sm_count_dev();
     const uintptr_t tb = reinterpret_cast<uintptr_t>(c.text);

@@ -7,6 +7,13 @@
 
 namespace wc {
 
+// Raises kernel `func`'s dynamic shared-memory limit to `bytes` on the
+// calling thread's current device.  The attribute belongs to that device's
+// context, so it is set once per (kernel, device, size): a process that
+// counts on several devices sets it on each.  Safe to call from several host
+// threads at once.
+cudaError_t ensure_smem_limit(const void *func, int bytes);
+
 // ---------------------------------------------------------------- counting
 struct CountLaunch {
     const uint8_t *text;     // document bytes are text[lo, hi); long words may

@@ -17,7 +17,9 @@ import weakref
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_build", "libwc.so")
+# WC_LIB_PATH selects another build of the same library (the tests' one-slot
+# build); there is no host implementation to fall back to either way.
+LIB_PATH = os.environ.get("WC_LIB_PATH") or os.path.join(_PKG, "_build", "libwc.so")
 
 WC_OK = 0
 WC_ERR_INVALID_ARG = 1
