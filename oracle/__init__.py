@@ -29,14 +29,14 @@ DOC, CLASS, GLOBAL = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
-    """Compiles oracle.cpp with the host C++ compiler (portable flags)."""
-    src = os.path.join(_HERE, "oracle.cpp")
+    """Compiles oracle.cpp and series.cpp with the host C++ compiler (portable flags)."""
+    srcs = [os.path.join(_HERE, f) for f in ("oracle.cpp", "series.cpp")]
     with _lock:
-        if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
+        if not force and os.path.exists(_SO) and all(os.path.getmtime(_SO) >= os.path.getmtime(s) for s in srcs):
             return _SO
         os.makedirs(os.path.dirname(_SO), exist_ok=True)
         tmp = _SO + f".{os.getpid()}.tmp"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", src, "-o", tmp])
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", *srcs, "-o", tmp])
         os.replace(tmp, _SO)
     return _SO
 
@@ -57,6 +57,8 @@ def _load():
         lib.oracle_ratio_topk.restype = ctypes.c_int64
         lib.oracle_ratio_topk.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, vp, vp, vp]
         lib.oracle_free.argtypes = [vp]
+        lib.oracle_series_sum.restype = ctypes.c_double
+        lib.oracle_series_sum.argtypes = [ctypes.c_int, ctypes.c_uint64]
         _lib = lib
     return _lib
 
@@ -191,3 +193,15 @@ def merge(tables: list[Table]) -> Table:
                          ctypes.cast(C, ctypes.c_void_p), sizes.ctypes.data)
     r = Result(h, 0, 0)
     return r.glob()
+
+
+SERIES_SQRT, SERIES_ALT_HARMONIC = 0, 1
+
+
+def series_sum(series: int, n: int) -> float:
+    """Sec. 4.2's numeric MapReduce: sum_{i=1}^n sqrt(i) (SERIES_SQRT) or
+    sum_{i=1}^n (-1)^(i+1)/i (SERIES_ALT_HARMONIC), double-precision terms,
+    Neumaier-compensated left-to-right sum (see series.cpp)."""
+    if series not in (SERIES_SQRT, SERIES_ALT_HARMONIC) or n < 0:
+        raise ValueError("unknown series or negative n")
+    return float(_load().oracle_series_sum(series, n))

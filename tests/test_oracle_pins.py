@@ -190,3 +190,55 @@ def test_ratio_ranking_against_fractions():
         assert [w for w, _, _ in got] == want
         for w, cin, cout in got:
             assert cin == r.cls(k).as_dict()[w] and cin + cout == g[w]
+
+
+# ---------------------------------------------------------------- numeric MapReduce (Sec. 4.2)
+def _ulps(a: float, b: float) -> float:
+    import math
+    return abs(a - b) / math.ulp(max(abs(a), abs(b), 1e-300))
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 10, 99, 100, 1000, 4097])
+def test_series_alternating_harmonic_exact_rationals(n):
+    """A(n) = sum (-1)^(i+1)/i as an exact fraction, rounded once."""
+    from fractions import Fraction
+    exact = sum((Fraction(1, i) if i % 2 else Fraction(-1, i)) for i in range(1, n + 1))
+    got = oracle.series_sum(oracle.SERIES_ALT_HARMONIC, n)
+    assert (n == 0 and got == 0.0) or _ulps(got, float(exact)) <= 2.0, (n, got, float(exact))
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 10, 1000, 100_000, 1_000_000])
+def test_series_sqrt_against_an_exactly_rounded_sum(n):
+    """S(n) = sum sqrt(i): math.fsum rounds the exact sum of the double terms once."""
+    import math
+    want = math.fsum(math.sqrt(i) for i in range(1, n + 1))
+    got = oracle.series_sum(oracle.SERIES_SQRT, n)
+    assert (n == 0 and got == 0.0) or _ulps(got, want) <= 2.0, (n, got, want)
+
+
+@pytest.mark.parametrize("n", [10_000, 1_000_000, 10_000_000])
+def test_series_sqrt_euler_maclaurin(n):
+    """S(n) = 2/3 n^(3/2) + 1/2 n^(1/2) + zeta(-1/2) + n^(-1/2)/24 - n^(-5/2)/1920
+    + O(n^(-9/2)), evaluated with 40 significant digits."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    x = mpmath.mpf(n)
+    em = (mpmath.mpf(2) / 3 * x ** 1.5 + x ** 0.5 / 2 + mpmath.zeta(-0.5) + x ** -0.5 / 24 - x ** -2.5 / 1920)
+    got = oracle.series_sum(oracle.SERIES_SQRT, n)
+    assert abs(got - float(em)) <= 1e-14 * float(em), (n, got, float(em))
+
+
+@pytest.mark.parametrize("n", [1, 2, 1001, 100_000, 10_000_000])
+def test_series_alternating_harmonic_closed_form_and_limit(n):
+    """A(n) = ln 2 + (-1)^(n+1)/2 * (psi((n+2)/2) - psi((n+1)/2)), and the
+    alternating-series bound |A(n) - ln 2| < 1/(n+1) with the sign of the
+    first omitted term's opposite."""
+    import math
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    sign = 1 if n % 2 else -1
+    closed = mpmath.log(2) + sign * (mpmath.digamma(mpmath.mpf(n + 2) / 2) - mpmath.digamma(mpmath.mpf(n + 1) / 2)) / 2
+    got = oracle.series_sum(oracle.SERIES_ALT_HARMONIC, n)
+    assert abs(got - float(closed)) <= 4e-16 * max(1.0, abs(float(closed))), (n, got, float(closed))
+    d = got - math.log(2)
+    assert abs(d) < 1.0 / (n + 1) and (d > 0) == (n % 2 == 1)
