@@ -129,18 +129,23 @@ class ClockSampler:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("wc_count.cu", "wc_device.cuh"):
+    for f in ("wc_count.cu", "wc_device.cuh", "wc_internal.h"):
         with open(os.path.join(ROOT, "paper_2206_05269_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
+TRAFFIC_FILE = os.path.join("profiles", "count_kernel_large_1GB_traffic.txt")
+
+
 def profiled_traffic(kind: str):
     """DRAM bytes per launch of the counting kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "count_kernel_large_1GB_traffic.txt")
+    summary (a profiler cannot run inside the timed benchmark), and a note
+    saying where the figure comes from or why there is none: the summary
+    must have been taken on the current kernel source."""
+    p = os.path.join(ROOT, TRAFFIC_FILE)
     if not os.path.exists(p):
-        return None
+        return None, f"no traffic capture ({TRAFFIC_FILE} missing)"
     d = {}
     with open(p) as f:
         for ln in f:
@@ -148,9 +153,10 @@ def profiled_traffic(kind: str):
             if sep and not ln.startswith((" ", "#", "|")):
                 d[k.strip()] = v.strip()
     if d.get("kernel_source_hash") != kernel_source_hash():
-        return None
+        return None, (f"{TRAFFIC_FILE} was captured on kernel source {d.get('kernel_source_hash')}, "
+                      f"not the current {kernel_source_hash()}: traffic unmeasured for this build")
     v = d.get(kind)
-    return float(v) if v else None
+    return (float(v) if v else None), f"ncu capture in {TRAFFIC_FILE} (kernel source {kernel_source_hash()})"
 
 
 def oracle_sample(text: np.ndarray, nbytes: int) -> np.ndarray:
@@ -191,7 +197,7 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_gpu(args, rank, world, local):
+def run_gpu(args, rank, world, local, subs=None):
     import torch
     import corpus
     from paper_2206_05269_gb300 import wc
@@ -276,7 +282,7 @@ def run_gpu(args, rank, world, local):
     avg_count_s = ms_count / max(1, n_count) * 1e-3
     alg_bytes = nbytes + nwords * 24
     achieved = alg_bytes / avg_count_s / 1e9
-    traffic = profiled_traffic("dram_bytes_per_launch")
+    traffic, traffic_note = profiled_traffic("dram_bytes_per_launch")
 
     # the practical ceiling of one pass over this text: a kernel that only reads it
     sink = torch.zeros(4096, dtype=torch.int64, device=f"cuda:{local}")
@@ -322,8 +328,8 @@ def run_gpu(args, rank, world, local):
             "stages_ms": {"head_selection": ms_head / max(1, n_count), "count_kernel": ms_count / max(1, n_count),
                           "compact_sort": ms_finish / max(1, n_count)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_count2<false>", "peak_kind": peak_kind,
+                         "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_note,
+                         "kernel": "k_count3<HEAD> (main counting kernel)", "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": alg_bytes,
                          "read_ceiling_GBps": read_ceiling, "frac_of_read_ceiling": achieved / read_ceiling,
                          "nominal_peak_GBps": 7900.0, "frac_of_nominal": achieved / 7900.0},
@@ -334,6 +340,7 @@ def run_gpu(args, rank, world, local):
         if cpu:
             line["cpu_baseline"] = cpu
             line["cpu_parallel_baseline"] = cpu_par
+        line.update(subs or {})
         print(json.dumps(line), flush=True)
     ctr.close()
     if dist:
@@ -350,11 +357,30 @@ def _dev_docs(c, local):
     return host, text, offs, cls
 
 
-def run_docs_workload(args, local):
+def docs_oracle_baseline(c, seconds: float = 8.0) -> dict:
+    """The oracle (single-threaded C++) on the first documents of the same
+    corpus, as many as about `seconds` of CPU work: documents per second with
+    per-document tables (and class/global sums where the corpus has them)."""
+    import oracle
+    oracle.build()
+    per_doc = max(1, c.nbytes // max(1, c.ndocs))
+    nd = int(max(1, min(c.ndocs, seconds * ORACLE_MBPS_GUESS * 1e6 / per_doc)))
+    offs = c.offsets[:nd + 1].copy()
+    text = c.text[:int(offs[-1])]
+    cls = c.classes[:nd] if c.nclasses > 1 else None
+    t0 = time.perf_counter()
+    oracle.count(text, offs, cls, c.nclasses if c.nclasses > 1 else 0)
+    dt = time.perf_counter() - t0
+    return {"value": nd / dt, "unit": "docs/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {nd} of {c.ndocs} documents ({text.size} bytes), single-threaded C++ oracle, {dt:.1f} s"}
+
+
+def run_docs_workload(args, local, print_line: bool = True):
     """Batched per-document counting through a replayed plan: 'tiny' (200
     documents: per-document + global tables), 'classes' (4 x 250 documents:
     per-document, per-class and global tables + top-50 class-ratio words) or
-    'batched' (100,000 log-normal documents: per-document tables)."""
+    'batched' (100,000 log-normal documents: per-document tables).  Returns
+    the result line (printed unless print_line is false)."""
     import torch
     import corpus
     from paper_2206_05269_gb300 import wc
@@ -448,6 +474,23 @@ def run_docs_workload(args, local):
         te.append(time.perf_counter() - t2)
         d2h = c.ndocs * 12 + n_wb + (n_rows + 1) * 8 + n_rows * 4
     e2e = c.ndocs / statistics.mean(te[1:])
+    # the same end to end with the vocabulary-id export: every document's
+    # (id, count) rows plus the vocabulary (words, offsets, global counts) once
+    hi, hcn = pin(nent, torch.int32), pin(nent, torch.int32)
+    te_ids, d2h_ids = [], 0
+    for i in range(7):
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        text.copy_(host, non_blocking=True)
+        bb = step()
+        n_rows = bb.export_ids_into(hds, hdn, hi, hcn, stream)
+        voc = bb.vocab()
+        nv, _, nvb = voc.size()
+        vw, vo, vc = pin(nvb + 16, torch.uint8), pin(nv + 1, torch.int64), pin(nv, torch.int64)
+        voc.export_into(vw, vo, vc, stream)
+        te_ids.append(time.perf_counter() - t2)
+        d2h_ids = c.ndocs * 12 + n_rows * 8 + nvb + (nv + 1) * 8 + nv * 8
+    e2e_ids = c.ndocs / statistics.mean(te_ids[1:])
     peak, peak_kind = measured_peaks()
     alg = c.nbytes + nent * 24
     line = {
@@ -465,18 +508,26 @@ def run_docs_workload(args, local):
                      "frac": alg / (ms * 1e-3) / 1e9 / peak, "traffic": None, "kernel": "whole batched step",
                      "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg},
         "e2e": {"value": e2e, "unit": "docs/s", "h2d_bytes_per_step": c.nbytes, "d2h_bytes_per_step": d2h},
+        "e2e_vocab_ids": {"value": e2e_ids, "unit": "docs/s", "h2d_bytes_per_step": c.nbytes,
+                          "d2h_bytes_per_step": d2h_ids,
+                          "note": "per-document (vocabulary id, count) rows + the vocabulary once"},
         "gpu_launches": launches, "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
     del plan
     ctr.close()
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = docs_oracle_baseline(c)
+    if print_line:
+        print(json.dumps(line), flush=True)
+    return line
 
 
-def run_served_workload(args, local):
+def run_served_workload(args, local, print_line: bool = True):
     """Served counting: a Poisson stream of requests (2,000/s for
     --serve-seconds, sizes log-uniform 1 KB - 64 MB) through the
     continuous-batching loop, then the first --fifo-seconds of the same
-    stream through the plain one-launch-per-request path."""
+    stream through the plain one-launch-per-request path.  Returns the
+    result line (printed unless print_line is false)."""
     import torch
     import corpus
     from paper_2206_05269_gb300 import serve, wc
@@ -520,9 +571,140 @@ def run_served_workload(args, local):
                 "d2h_bytes_per_step": sum(a.words.nbytes + a.offs.nbytes + a.counts.nbytes for a in ans) / len(ans)},
         "gpu_launches": launches,
         "clocks": clocks,
+        "budget_waits": st.get("budget_waits", 0),
     }
-    print(json.dumps(line), flush=True)
     ctr.close()
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        # the oracle on the first requests of the same stream, about 8 s of CPU work
+        t0, done_b, k = time.perf_counter(), 0, 0
+        while k < len(trip) and time.perf_counter() - t0 < 8.0:
+            a, s0, e0 = trip[k]
+            oracle.count(pool[s0:e0], keep_docs=False)
+            done_b += e0 - s0
+            k += 1
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": k / dt, "unit": "req/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first {k} requests of the stream ({done_b} bytes) counted one after "
+                                          f"another, single-threaded C++ oracle, {dt:.1f} s"}
+    if print_line:
+        print(json.dumps(line), flush=True)
+    return line
+
+
+def run_numeric(args, local) -> dict:
+    """The paper's numeric MapReduce (Sec. 4.2) at n = 1e8: sum of sqrt(i)
+    and the alternating harmonic sum, each term a correctly rounded double,
+    compensated sums (wc_series_sum).  ALU-bound: reported against the
+    nominal FP64 rate of the part (no measured FP64 peak is available)."""
+    import torch
+    import oracle
+    from paper_2206_05269_gb300 import wc
+    torch.cuda.set_device(local)
+    ctr = wc.Counter(local)
+    stream = torch.cuda.current_stream()
+    out = torch.zeros(1, dtype=torch.float64, device=f"cuda:{local}")
+    n = 100_000_000
+    res = {}
+    for series, name in ((wc.WC_SERIES_SQRT, "sum_sqrt"), (wc.WC_SERIES_ALT_HARMONIC, "alt_harmonic")):
+        for _ in range(3):
+            wc.wc_series_sum(ctr.ctx, series, n, out.data_ptr(), stream.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(20):
+            wc.wc_series_sum(ctr.ctx, series, n, out.data_ptr(), stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        got = float(out.cpu()[0])
+        t0 = time.perf_counter()
+        m = 10_000_000  # the oracle on a tenth of the terms (about a second of CPU work)
+        oracle.series_sum(series, m)
+        cpu_s = time.perf_counter() - t0
+        # two floating-point operations a term (the map: sqrt or 1/i; the reduce: +)
+        gflops = 2.0 * n / (ms * 1e-3) / 1e9
+        res[name] = {"n": n, "value": got, "oracle": oracle.series_sum(series, n), "ms": ms,
+                     "terms_per_s": n / (ms * 1e-3),
+                     "roofline": {"bound": "alu", "achieved": gflops, "peak": 1250.0, "unit": "GFLOP/s (FP64)",
+                                  "frac": gflops / 1250.0, "peak_kind": "nominal FP64 rate of the part",
+                                  "flops_per_term": 2},
+                     "cpu_baseline": {"value": m / cpu_s, "unit": "terms/s", "cores": 1, "kind": "oracle",
+                                      "sample": f"first {m} terms, single-threaded compensated sum, {cpu_s:.2f} s"},
+                     "paper_v100_ms": 73.372 if series == wc.WC_SERIES_SQRT else 65.323}
+    ctr.close()
+    return res
+
+
+def run_hybrid(args, local) -> dict:
+    """The paper's hybrid pipeline (Sec. 3.3, Sec. 4.1) on the class-split
+    workload's 1,000 documents: CPU map into per-document dictionaries on
+    every host core, grouped into a zero-padded count matrix, copied to the
+    device, summed by rows on the GPU (wc_row_sums) -- beside the on-device
+    path (text copied in, wc_count_batched, global table out) on the same
+    documents.  Context for the host -> device cost the paper reports."""
+    import torch
+    import corpus
+    import cpu_parallel
+    from paper_2206_05269_gb300 import wc
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    c = corpus.generate("classes")
+    stream = torch.cuda.current_stream()
+    runs = []
+    for _ in range(4):
+        t0 = time.perf_counter()
+        hy = cpu_parallel.HybridMap(c.text, c.offsets)
+        m = torch.empty((hy.rows, hy.cols), dtype=torch.int32).pin_memory()
+        hy.fill(m)
+        t1 = time.perf_counter()
+        dm = m.to(dev, non_blocking=True)
+        sums = torch.empty(max(1, hy.rows), dtype=torch.int64, device=dev)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        wc.wc_row_sums(dm.data_ptr(), hy.rows, hy.cols, sums.data_ptr(), stream.cuda_stream)
+        e1.record(stream)
+        h_sums = sums.cpu()
+        t3 = time.perf_counter()
+        runs.append({"map_and_group_ms": hy.seconds["map_and_group"] * 1e3, "matrix_ms": hy.seconds["matrix"] * 1e3,
+                     "h2d_ms": (t2 - t1) * 1e3, "kernel_ms": e0.elapsed_time(e1), "total_ms": (t3 - t0) * 1e3,
+                     "rows": hy.rows, "cols": hy.cols, "matrix_bytes": hy.rows * hy.cols * 4})
+        del dm, m, hy
+    best = min(runs[1:], key=lambda r: r["total_ms"])
+    kb = best["matrix_bytes"] / (best["kernel_ms"] * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    best["row_sum_roofline"] = {"bound": "hbm", "achieved": kb, "peak": peak, "unit": "GB/s", "frac": kb / peak,
+                                "peak_kind": peak_kind}
+    # the on-device path on the same documents: text in, batched count, global table out
+    host = torch.from_numpy(c.text).pin_memory()
+    offs = torch.from_numpy(c.offsets.view(np.int64)).to(dev)
+    ctr = wc.Counter(local, count_bits=32)
+    tms = []
+    for _ in range(4):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        text = host.to(dev, non_blocking=True)
+        b = ctr.count_batched(text, offs, c.offsets)
+        g = b.table(wc.WC_TABLE_GLOBAL)
+        g.export()
+        tms.append((time.perf_counter() - t0) * 1e3)
+        b.free()
+    ctr.close()
+    best["on_device_total_ms"] = min(tms[1:])
+    best["workload"] = "classes: 1,000 documents, 29.6 MB (the paper ran 4n speeches, n <= 500)"
+    best["cpu_threads"] = os.cpu_count()
+    return best
+
+
+def _sub(line: dict) -> dict:
+    """The parts of a workload's own result line that the default line carries."""
+    keep = ("metric", "value", "unit", "ms_per_step", "higher_is_better", "config", "input_GBps", "per_launch_docs_s",
+            "speedup_vs_per_launch", "roofline", "e2e", "e2e_vocab_ids", "gpu_launches", "clocks", "cpu_baseline",
+            "p50_ms", "p99_ms",
+            "req_per_s", "GBps", "fifo", "budget_waits")
+    return {k: line[k] for k in keep if k in line}
 
 
 def main():
@@ -539,6 +721,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--fifo-seconds", type=float, default=2.0)
     ap.add_argument("--pool-bytes", type=float, default=2e9)
+    ap.add_argument("--no-sub", action="store_true",
+                    help="large workload only (no batched / served sub-objects in the default line)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local = dist_env()
@@ -549,7 +733,19 @@ def main():
     if rank == 0 or world == 1:
         __graft_entry__.build()
     if args.workload == "large":
-        run_gpu(args, rank, world, local)
+        subs = {}
+        if world == 1 and not args.no_sub and args.bytes == 1e9:
+            # the batched (100,000 documents) and served (Poisson requests)
+            # workloads, measured first and carried in the default line
+            import copy
+            for name in ("batched", "served"):
+                a2 = copy.copy(args)
+                a2.workload, a2.steps, a2.warmup, a2.docs = name, 10, 3, 0
+                subs[name] = _sub(run_docs_workload(a2, local, False) if name == "batched"
+                                  else run_served_workload(a2, local, False))
+            subs["numeric"] = run_numeric(args, local)
+            subs["hybrid"] = run_hybrid(args, local)
+        run_gpu(args, rank, world, local, subs)
     elif args.workload == "served":
         run_served_workload(args, local)
     else:

@@ -182,6 +182,25 @@ wc_status wc_batch_size(const wc_batch *batch, uint64_t *nentries, uint64_t *wor
 wc_status wc_batch_export(const wc_batch *batch, uint64_t *h_doc_start, uint32_t *h_doc_n, uint8_t *h_words,
                           uint64_t *h_word_offsets, uint32_t *h_counts, cudaStream_t stream);
 
+/* Vocabulary-id form of a batch (Sec. 3.3 sums every document's counts per
+ * key; here the batch's global table, ordered by word, is that one shared
+ * dictionary).  wc_batch_vocab borrows a table (owned by the batch, freed
+ * with it or when its plan runs again; wc_table_free on it does nothing)
+ * holding the batch's distinct words in word order, each with its global
+ * count (64-bit, wc_table_export); a word's id is its row, so ids order as
+ * their words.  wc_batch_export_ids copies every per-document entry as
+ * (id, count): h_ids and h_counts (uint32, wc_batch_size entries, in the
+ * order of wc_batch_export's rows: each document's entries contiguous, count
+ * desc then word asc) and h_doc_start / h_doc_n as in wc_batch_export; any
+ * pointer may be NULL.  An id decoded through the vocabulary is the word
+ * wc_batch_export gives for that row.  Both wait for the batch and build the
+ * class/global tables and the vocabulary on first use (device memory from
+ * the context's pool).  Export size: 8 bytes a row plus the vocabulary once,
+ * where wc_batch_export needs the word bytes plus 12 bytes a row. */
+wc_status wc_batch_vocab(const wc_batch *batch, const wc_table **vocab);
+wc_status wc_batch_export_ids(const wc_batch *batch, uint64_t *h_doc_start, uint32_t *h_doc_n, uint32_t *h_ids,
+                              uint32_t *h_counts, cudaStream_t stream);
+
 /* Plans: resident state for counting the same layout of documents again and
  * again (serving, repeated batches).  wc_plan_create plans ndocs documents
  * with the given host offsets (size classes, work items, capacities) and
@@ -253,7 +272,7 @@ void wc_batch_free(wc_batch *b);
  * through its own allocator, and services that forbid allocation after
  * start-up because an allocation can stall or fail at the wrong moment.
  * No context is needed and nothing is allocated: the hash tables and sort
- * scratch live in one fixed __device__ array of about 15.2 MB that every GPU
+ * scratch live in one fixed __device__ array of about 15.5 MB that every GPU
  * which loads the library holds until the process exits.
  *   d_text[0, nbytes): one document, nbytes <= 1 MiB (larger: returns
  *     WC_ERR_UNSUPPORTED; use wc_count).
@@ -279,6 +298,52 @@ wc_status wc_count_noalloc(const uint8_t *d_text, uint64_t nbytes, uint64_t *d_k
                            uint64_t *d_cnt, uint32_t *d_lref, uint64_t out_cap, uint64_t *d_loff,
                            uint64_t *d_llen, uint64_t long_cap, uint8_t *d_arena, uint64_t arena_cap,
                            uint64_t *d_meta, cudaStream_t stream);
+
+/* The paper's numeric MapReduce (Sec. 4.2): *d_out (one device double) =
+ * sum_{i=1}^{n} term(i) with term(i) = sqrt(i) (WC_SERIES_SQRT) or
+ * (-1)^(i+1) / i (WC_SERIES_ALT_HARMONIC, whose limit is ln 2).  Each term is
+ * an IEEE double (correctly rounded sqrt and division); the terms are summed
+ * with Neumaier-compensated additions, per thread over a strided share of one
+ * block's contiguous range, then over warps and blocks in a fixed order, so a
+ * given GPU always returns the same value (no atomics).  n = 0 gives 0.
+ * Asynchronous on `stream`; scratch (16 bytes a block) comes from the
+ * context's pool.  Errors: WC_ERR_INVALID_ARG (unknown series, null
+ * pointer), WC_ERR_UNSUPPORTED (n >= 2^53: indices no longer exact in
+ * double), WC_ERR_BUDGET / WC_ERR_OOM. */
+enum { WC_SERIES_SQRT = 0, WC_SERIES_ALT_HARMONIC = 1 };
+wc_status wc_series_sum(wc_ctx *ctx, int series, uint64_t n, double *d_out, cudaStream_t stream);
+
+/* The reduce of the paper's hybrid pipeline (Sec. 3.3 "Reduce on GPU",
+ * measured in Sec. 4.1): the host maps every document to a dictionary and
+ * lays the per-document counts of each word out as one row of a zero-padded
+ * row-major matrix d_matrix[rows][cols] (device, uint32, caller-owned); this
+ * call writes each row's sum to d_sums[rows] (device, uint64, caller-owned).
+ * Kept to measure that design beside wc_count on the same GPU.  Asynchronous
+ * on `stream`; rows = 0 does nothing.  Null pointers with rows > 0, or a
+ * matrix of 2^64 bytes or more: WC_ERR_INVALID_ARG; launch failure:
+ * WC_ERR_CUDA. */
+wc_status wc_row_sums(const uint32_t *d_matrix, uint64_t rows, uint64_t cols, uint64_t *d_sums, cudaStream_t stream);
+
+/* Device buffers charged against the context's budget.  The library's own
+ * tables and scratch come from the context's stream-ordered pool and count
+ * against mem_budget_bytes; these calls let a caller hold its input there
+ * too (a serving loop's request text), so that one budget covers everything
+ * resident for the context.  The paper's GPU reduce copies its count matrix
+ * to the device for each call (Sec. 3.3); nothing there is budgeted.
+ *   wc_buffer_alloc: `bytes` of device memory (256-byte aligned), allocated
+ *     in stream order on `stream`; *out is set on WC_OK only.  WC_ERR_BUDGET
+ *     when the budget cannot hold `bytes` more (nothing is allocated: wait
+ *     for the context's other work to be freed and try again); WC_ERR_OOM.
+ *   wc_buffer_free: returns a buffer (same context, pointer and byte count)
+ *     in stream order on `stream`: work enqueued on `stream` before the call
+ *     may still read it; a NULL pointer is a no-op.
+ *   wc_mem_usage: the bytes the context holds now (tables, scratch and these
+ *     buffers not yet freed) and the largest such figure since creation or
+ *     the last reset; reset != 0 restarts the peak from the current use.
+ *     Any output pointer may be NULL. */
+wc_status wc_buffer_alloc(wc_ctx *ctx, uint64_t bytes, cudaStream_t stream, void **out);
+wc_status wc_buffer_free(wc_ctx *ctx, void *p, uint64_t bytes, cudaStream_t stream);
+wc_status wc_mem_usage(wc_ctx *ctx, uint64_t *used, uint64_t *peak, int reset);
 
 /* Stage tracing.  While enabled, the context records CUDA events on the
  * launching stream around three stages of wc_count / wc_count_ex (head

@@ -20,7 +20,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libwc.so")
-SOURCES = ["wc_count.cu", "wc_table.cu", "wc_batch.cu", "wc_api.cu", "wc_batch_api.cu", "wc_noalloc.cu", "wc_ceiling.cu"]
+SOURCES = ["wc_count.cu", "wc_table.cu", "wc_batch.cu", "wc_api.cu", "wc_batch_api.cu", "wc_noalloc.cu", "wc_ceiling.cu",
+           "wc_numeric.cu", "wc_hybrid.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -49,13 +49,22 @@ wc_status wc_ctx::alloc(void **p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
     if (bytes == 0) bytes = 256;
     bytes = (bytes + 255) & ~(size_t)255;
-    if (budget && used.load() + bytes > budget) return fail(WC_ERR_BUDGET, "allocation over the context budget");
+    // reserve the bytes against the budget first (compare-and-swap: two
+    // callers can never both pass a budget that holds only one of them)
+    uint64_t cur = used.load();
+    do {
+        if (budget && cur + bytes > budget) return fail(WC_ERR_BUDGET, "allocation over the context budget");
+    } while (!used.compare_exchange_weak(cur, cur + bytes));
     cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        used -= bytes;
+        *p = nullptr;
         return cuda_fail(e, "cudaMallocFromPoolAsync");
     }
-    used += bytes;
+    uint64_t pk = peak.load();
+    while (cur + bytes > pk && !peak.compare_exchange_weak(pk, cur + bytes)) {
+    }
     return WC_OK;
 }
 void wc_ctx::release(void *p, size_t bytes, cudaStream_t s) {
@@ -213,6 +222,61 @@ void wc_destroy(wc_ctx *ctx) {
     if (ctx->meta_host) cudaFreeHost(ctx->meta_host);
     cudaMemPoolDestroy(ctx->pool);
     delete ctx;
+}
+
+// ---------------------------------------------------------------- numeric MapReduce
+wc_status wc_series_sum(wc_ctx *ctx, int series, uint64_t n, double *d_out, cudaStream_t stream) {
+    if (!ctx || !d_out) return WC_ERR_INVALID_ARG;
+    if (series != WC_SERIES_SQRT && series != WC_SERIES_ALT_HARMONIC)
+        return ctx->fail(WC_ERR_INVALID_ARG, "unknown series");
+    if (n >= (1ull << 53)) return ctx->fail(WC_ERR_UNSUPPORTED, "n of 2^53 or more (indices not exact in double)");
+    cudaSetDevice(ctx->device);
+    const int nb = series_blocks(n);
+    void *part = nullptr;
+    wc_status st = ctx->alloc(&part, sizeof(double2) * (size_t)nb, stream);
+    if (st != WC_OK) return st;
+    const cudaError_t e = launch_series(series, n, static_cast<double2 *>(part), nb, d_out, stream);
+    ctx->release(part, sizeof(double2) * (size_t)nb, stream);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "series sum");
+    ctx->launches += 2;
+    return WC_OK;
+}
+
+// ---------------------------------------------------------------- hybrid pipeline reduce
+wc_status wc_row_sums(const uint32_t *d_matrix, uint64_t rows, uint64_t cols, uint64_t *d_sums, cudaStream_t stream) {
+    if (rows && (!d_sums || (cols && !d_matrix))) return WC_ERR_INVALID_ARG;
+    if (rows && cols > UINT64_MAX / 4 / rows) return WC_ERR_INVALID_ARG;
+    const cudaError_t e = launch_row_sums(d_matrix, rows, cols, reinterpret_cast<unsigned long long *>(d_sums), stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return WC_ERR_CUDA;
+    }
+    return WC_OK;
+}
+
+// ---------------------------------------------------------------- budgeted buffers
+wc_status wc_buffer_alloc(wc_ctx *ctx, uint64_t bytes, cudaStream_t stream, void **out) {
+    if (!ctx || !out) return WC_ERR_INVALID_ARG;
+    *out = nullptr;
+    cudaSetDevice(ctx->device);
+    return ctx->alloc(out, bytes, stream);
+}
+
+wc_status wc_buffer_free(wc_ctx *ctx, void *p, uint64_t bytes, cudaStream_t stream) {
+    if (!ctx) return WC_ERR_INVALID_ARG;
+    if (!p) return WC_OK;
+    cudaSetDevice(ctx->device);
+    ctx->release(p, bytes, stream);
+    return WC_OK;
+}
+
+wc_status wc_mem_usage(wc_ctx *ctx, uint64_t *used, uint64_t *peak, int reset) {
+    if (!ctx) return WC_ERR_INVALID_ARG;
+    const uint64_t u = ctx->used.load();
+    if (used) *used = u;
+    if (peak) *peak = ctx->peak.load();
+    if (reset) ctx->peak.store(u);
+    return WC_OK;
 }
 
 // ---------------------------------------------------------------- wait self-test
@@ -534,7 +598,8 @@ wc_status wc_count_ex(wc_ctx *ctx, const uint8_t *d_text, uint64_t nbytes, const
     cudaSetDevice(ctx->device);
     const CapPlan plan = plan_capacity(ctx, nbytes, opts);
     CountScratch cs;
-    wc_status st = scratch_create(ctx, plan, true, stream, cs);
+    // head scratch only for texts long enough to sample a head from
+    wc_status st = scratch_create(ctx, plan, nbytes >= count_global_head_min(), stream, cs);
     if (st != WC_OK) return st;
     wc_table *t = nullptr;
     st = table_create(ctx, cs.entries(), plan.caplong, plan.arena, ctx->count_bits, stream, &t);

@@ -684,7 +684,7 @@ __global__ void k_bcompact_long(const LSlot *ls, unsigned long long lcap, SortSc
         if (w < lcap) {
             h = ls[w].h;
             addr = ls[w].addr;
-            len = ls[w].len;
+            len = long_len(ls[w].len);
             c = ls[w].cnt;
         }
         const bool occ = !(h == 0 && addr == 0);

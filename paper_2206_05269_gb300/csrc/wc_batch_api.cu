@@ -76,7 +76,13 @@ struct wc_batch {
     wc_table *global = nullptr;
     CountScratch gscratch;        // global hash tables kept for ratio lookups
     std::vector<wc_table *> views;
+    // vocabulary ids (built on request, dropped when a plan runs again)
+    wc_table *vocab = nullptr;    // the distinct words in word order, global counts
+    uint32_t *d_ids = nullptr;    // per-document entry -> row of vocab
+    size_t ids_bytes = 0;
 };
+
+static void drop_vocab(wc_batch *b, cudaStream_t s);
 
 static wc_status batch_sync(const wc_batch *cb) {
     wc_batch *b = const_cast<wc_batch *>(cb);
@@ -528,6 +534,7 @@ wc_status wc_plan_run(wc_plan *pl, const uint8_t *d_text, const uint64_t *d_offs
     free_owned_table(b->global);
     b->global = nullptr;
     if (b->gscratch.mem) { ctx->release(b->gscratch.mem, b->gscratch.bytes, stream); b->gscratch.mem = nullptr; }
+    drop_vocab(b, stream);
     b->tables_built = false;
     b->synced = false;
     b->word_bytes = 0;
@@ -1183,7 +1190,190 @@ void wc_batch_free(wc_batch *b) {
     for (auto *t : b->class_tables) free_owned_table(t);
     free_owned_table(b->global);
     if (b->gscratch.mem) ctx->release(b->gscratch.mem, b->gscratch.bytes, b->stream);
+    drop_vocab(b, b->stream);
     ctx->release(b->mem, b->bytes, b->stream);
     if (b->done) cudaEventDestroy(b->done);
     delete b;
+}
+
+// ---------------------------------------------------------------- vocabulary ids
+// The reduce of Sec. 3.3 keys every count by a word; here the batch's global
+// table, ordered by word, is the one dictionary, and each per-document entry
+// is stored as (row of that dictionary, count): words sort the same way as
+// their ids, and a document's table needs 8 bytes a row.
+static void drop_vocab(wc_batch *b, cudaStream_t s) {
+    if (b->vocab) free_owned_table(b->vocab);
+    b->vocab = nullptr;
+    if (b->d_ids) b->ctx->release(b->d_ids, b->ids_bytes, s);
+    b->d_ids = nullptr;
+    b->ids_bytes = 0;
+}
+
+// The 16-byte table key of entry (khi, klo) (big-endian halves of the first
+// 16 letters), as the count kernels build it.
+__device__ __forceinline__ uint4 entry_key(unsigned long long hi8, unsigned long long lo8) {
+    uint4 k;
+    k.x = __byte_perm((uint32_t)(hi8 >> 32), 0, 0x0123);
+    k.y = __byte_perm((uint32_t)hi8, 0, 0x0123);
+    k.z = __byte_perm((uint32_t)(lo8 >> 32), 0, 0x0123);
+    k.w = __byte_perm((uint32_t)lo8, 0, 0x0123);
+    return k;
+}
+
+// Sort input: the global table's entries with every count zero, so that the
+// stable (count desc, word asc) sort orders them by word alone.
+__global__ void k_vocab_prep(DevTable G, SortScratch ss, unsigned long long *meta) {
+    const unsigned long long n = G.d_meta[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0) meta[0] = n;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        ss.khi[i] = G.khi[i];
+        ss.klo[i] = G.klo[i];
+        ss.cnt[i] = 0ull;
+        ss.lref[i] = G.lref[i];
+    }
+}
+
+// Row i of the vocabulary = the i-th word in word order (with its global
+// count and the global table's long-word bytes); the id table maps each
+// word to i + 1.
+__global__ void k_vocab_place(DevTable G, SortScratch ss, DevTable V, GTable vg) {
+    const unsigned long long n = G.d_meta[0];
+    const uint32_t *perm = ss.perm_buf(ss.cur[kCurFinal]);
+    if (blockIdx.x == 0 && threadIdx.x < 8) V.d_meta[threadIdx.x] = G.d_meta[threadIdx.x];
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t src = perm[i];
+        const unsigned long long hi8 = G.khi[src], lo8 = G.klo[src];
+        const uint32_t r = G.lref[src];
+        V.khi[i] = hi8;
+        V.klo[i] = lo8;
+        V.lref[i] = r;
+        static_cast<unsigned long long *>(V.cnt)[i] = G.count_bits == 64
+                                                          ? static_cast<const unsigned long long *>(G.cnt)[src]
+                                                          : static_cast<const uint32_t *>(G.cnt)[src];
+        if (r == 0) table_insert_key(vg, entry_key(hi8, lo8), i + 1);
+        else long_insert(vg, G.arena + G.loff[r - 1], G.llen[r - 1], i + 1, nullptr, nullptr);
+    }
+}
+
+// The vocabulary row of every per-document entry.
+__global__ void k_vocab_ids(BatchArgs a, GTable vg, uint32_t *ids, unsigned long long n) {
+    for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t r = a.out_lref[j];
+        const unsigned long long v =
+            r ? lookup_count(vg, make_uint4(0u, 0u, 0u, 0u), a.arena + a.loff[r - 1], a.llen[r - 1])
+              : lookup_count(vg, entry_key(a.out_khi[j], a.out_klo[j]), nullptr, 0ull);
+        ids[j] = (uint32_t)(v - 1ull);  // every document word is in the vocabulary
+    }
+}
+
+static wc_status build_vocab(wc_batch *b) {
+    if (b->vocab) return WC_OK;
+    wc_status st = build_tables(b);
+    if (st != WC_OK) return st;
+    wc_ctx *ctx = b->ctx;
+    cudaStream_t s = b->stream;
+    wc_table *G = b->global;
+    if ((st = table_sync(G)) != WC_OK) return st;
+    const uint64_t n = G->n, nlong = G->nlong;
+    // sort scratch + the id hash tables (sized from the known word counts)
+    CapPlan plan;
+    plan.cap8 = pow2_ge(std::max<uint64_t>(1024, 2 * n));
+    plan.cap16 = pow2_ge(std::max<uint64_t>(1024, n + n / 4));
+    plan.caplong = pow2_ge(std::max<uint64_t>(256, 2 * nlong));
+    plan.arena = 4096;
+    CountScratch cs;
+    if ((st = scratch_create(ctx, plan, false, s, cs)) != WC_OK) return st;
+    wc_table *V = nullptr;
+    if ((st = table_create(ctx, std::max<uint64_t>(1, n), 1, 16, 64, s, &V)) != WC_OK) {
+        ctx->release(cs.mem, cs.bytes, s);
+        return st;
+    }
+    V->owner = b;
+    V->dt.loff = G->dt.loff;  // long words: the global table's bytes
+    V->dt.llen = G->dt.llen;
+    V->dt.arena = G->dt.arena;
+    V->dt.lcap = G->dt.lcap;
+    V->dt.arena_cap = G->dt.arena_cap;
+    void *ids = nullptr;
+    const size_t ib = 4 * std::max<uint64_t>(1, b->entries);
+    if ((st = ctx->alloc(&ids, ib, s)) != WC_OK) {
+        free_owned_table(V);
+        ctx->release(cs.mem, cs.bytes, s);
+        return st;
+    }
+    void *dmeta = nullptr;
+    if ((st = ctx->alloc(&dmeta, 64, s)) != WC_OK) {
+        ctx->release(ids, ib, s);
+        free_owned_table(V);
+        ctx->release(cs.mem, cs.bytes, s);
+        return st;
+    }
+    unsigned long long *smeta = static_cast<unsigned long long *>(dmeta);
+    cudaMemsetAsync(smeta, 0, 64, s);
+    const GTable vg = cs.gtable(V->dt.d_status);
+    const int grid = std::max(1, std::min(ctx->sms * 8, (int)((std::max<uint64_t>(n, b->entries) + 255) / 256)));
+    cudaStreamWaitEvent(s, G->done, 0);
+    k_vocab_prep<<<grid, 256, 0, s>>>(G->dt, cs.ss, smeta);
+    const LongView lv{G->dt.lref, G->dt.loff, G->dt.llen, G->dt.arena};
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = sort_entries(cs.ss, smeta, lv, kSortPasses, s, sort_skip_mask(0, 0));
+    if (e == cudaSuccess) {
+        k_vocab_place<<<grid, 256, 0, s>>>(G->dt, cs.ss, V->dt, vg);
+        k_vocab_ids<<<grid, 256, 0, s>>>(b->args, vg, static_cast<uint32_t *>(ids), b->entries);
+        e = cudaGetLastError();
+    }
+    ctx->launches += 3 + (uint64_t)sort_entries_launches(kSortPasses, cs.ss.cap, sort_skip_mask(0, 0));
+    ctx->release(dmeta, 64, s);
+    ctx->release(cs.mem, cs.bytes, s);
+    table_mark_done(V, s);
+    if (e != cudaSuccess) {
+        ctx->release(ids, ib, s);
+        free_owned_table(V);
+        return ctx->cuda_fail(e, "vocabulary ids");
+    }
+    if ((st = table_sync(V)) != WC_OK) {  // an overflowing id table is reported, never used
+        ctx->release(ids, ib, s);
+        free_owned_table(V);
+        return st;
+    }
+    b->vocab = V;
+    b->d_ids = static_cast<uint32_t *>(ids);
+    b->ids_bytes = ib;
+    return WC_OK;
+}
+
+wc_status wc_batch_vocab(const wc_batch *cb, const wc_table **out) {
+    if (!cb || !out) return WC_ERR_INVALID_ARG;
+    *out = nullptr;
+    wc_batch *b = const_cast<wc_batch *>(cb);
+    cudaSetDevice(b->ctx->device);
+    const wc_status st = build_vocab(b);
+    if (st != WC_OK) return st;
+    *out = b->vocab;
+    return WC_OK;
+}
+
+wc_status wc_batch_export_ids(const wc_batch *cb, uint64_t *h_doc_start, uint32_t *h_doc_n, uint32_t *h_ids,
+                              uint32_t *h_counts, cudaStream_t stream) {
+    if (!cb) return WC_ERR_INVALID_ARG;
+    wc_batch *b = const_cast<wc_batch *>(cb);
+    cudaSetDevice(b->ctx->device);
+    wc_status st = build_vocab(b);
+    if (st != WC_OK) return st;
+    cudaStreamWaitEvent(stream, b->vocab->done, 0);
+    cudaError_t e = cudaSuccess;
+    if (h_doc_start && b->ndocs)
+        e = cudaMemcpyAsync(h_doc_start, b->args.doc_start, 8ull * b->ndocs, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess && h_doc_n && b->ndocs)
+        e = cudaMemcpyAsync(h_doc_n, b->args.doc_n, 4ull * b->ndocs, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess && h_ids && b->entries)
+        e = cudaMemcpyAsync(h_ids, b->d_ids, 4ull * b->entries, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess && h_counts && b->entries)
+        e = cudaMemcpyAsync(h_counts, b->args.out_cnt, 4ull * b->entries, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return b->ctx->cuda_fail(e, "id export");
+    return WC_OK;
 }

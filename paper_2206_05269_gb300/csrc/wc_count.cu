@@ -3,35 +3,40 @@
 // The paper maps on the CPU (Sec. 3.1: remove punctuation, lowercase, split,
 // one dictionary per document) and reduces on the GPU (Sec. 3.3); its
 // conclusion (Sec. 5.2) asks for a GPU dictionary so the whole map and reduce
-// run on the device.  This file is that design for one document:
+// run on the device.  This file is that design for one document.
 //
-//  0. Head selection (texts of 16 MB or more): a sampling pass counts 64
-//     evenly spaced 64 KB pieces into a small table; the most frequent
-//     words of at most 8 letters are placed in a bucketised two-choice hash
-//     image (4 keys per bucket, a key lives in one of two buckets).
-//  1. One persistent 512-thread block per SM copies that image into shared
-//     memory (keys read-only, counts zeroed) and walks its chunks through a
-//     ring of four buffers.  Each chunk window (16 bytes before, 64 after,
-//     16-byte aligned in absolute address space) is staged by a TMA bulk
-//     copy that completes a "full" mbarrier; windows that touch the
-//     document's edges are staged by plain loads with the outside masked to
-//     spaces (a document edge separates words).  Warps never wait for each
-//     other: each warp releases a buffer when its words there are consumed,
-//     and the last warp to release it issues the copy of the chunk four
-//     places ahead.
-//  2. A warp classifies 512-byte strips: one 16-bit letter mask per lane
-//     (SWAR), word starts = letter & !previous letter, the previous byte
-//     carried across lanes, strips and chunks; a word belongs to the chunk
-//     holding its first byte and is read through the window's lookahead.
-//  3. Words of <= 16 letters are queued per warp and processed 32 at a time:
-//     a word of <= 8 letters in the head image adds 1 to its shared count
-//     (fingerprints of two buckets, then the matching key); every other word goes to a per-warp tail queue,
-//     flushed 32 at a time into the global 8-byte-key or 16-byte-key table
-//     (plain load of the key, fire-and-forget reduction; CAS only the first
-//     time a word is seen).
-//  4. Words of 17+ letters are queued per warp and inserted 32 at a time,
-//     one per lane, into the global long-word table.
-//  5. At the end each block adds its head counts into the global table.
+// Work split.  The document is cut into 512-byte strips (16-byte aligned in
+// absolute address space).  Every warp of the grid owns every
+// (grid x warps)-th strip and stages its strips through a private ring of
+// four buffers: a strip's window (16 bytes before it, the strip, 32 bytes
+// after it) arrives by one TMA bulk copy that completes an mbarrier of that
+// warp; windows touching the document's edges are loaded by the warp with
+// plain loads and the outside masked to spaces (a document edge separates
+// words).  No warp ever waits for another.
+//
+// Per strip a lane classifies 16 bytes (SWAR letter mask); word starts are
+// letters whose previous byte is not one (carried across lanes, and from the
+// window's lead byte across strips); a word belongs to the strip holding its
+// first byte and is read through the window's lookahead.  Starts of words of
+// at most 16 letters go to a per-warp queue (window position and length) and
+// are processed 32 at a time, one per lane:
+//   * level 1 (shared memory): a word of at most 8 letters is looked up in
+//     the block's table of 8,192 keys and, if there, its shared count is
+//     incremented.  Two table kinds:
+//       HEAD  (texts of 16 MB or more): a read-only image of the words a
+//             sampling pass found most frequent, placed by hash-and-displace
+//             (one displacement byte per bucket of keys), so a lookup is one
+//             displacement load and one key compare;
+//       LOCAL (smaller texts, and the sampling pass itself): an empty table
+//             whose slots words claim by 64-bit CAS as they come (linear
+//             probing, at most four probes).
+//   * level 2 (global memory): every other word goes to a per-warp tail
+//     queue of 16-byte keys, flushed 32 at a time into the global 8-byte-key
+//     or 16-byte-key open-addressing table (slot loads issued one flush
+//     ahead, fire-and-forget reductions, CAS only for a word's first claim).
+// Words of 17+ letters are queued by address and inserted 32 at a time into
+// the global long-word table (bytes compared, never only hashes).  At the end
+// each block adds its nonzero level-1 counts into the global table.
 #include <algorithm>
 #include <mutex>
 #include <set>
@@ -41,42 +46,42 @@
 
 namespace wc {
 
-constexpr int kBlock = 512;           // threads of the main counting kernel
-constexpr int kWarps = kBlock / 32;
-constexpr int kChunk = kWarps * 512;  // bytes per chunk: one 512-byte strip per warp
-// Chunk buffers in flight per block (32 KB per SM).  More stages measured
-// slower: shared memory and L1 share one array per SM, and the L1 left over
-// holds the lines of the tail inserts' scattered loads in flight.
-constexpr int kStages = 4;
-constexpr int kLead = 16;             // window bytes before the chunk
-constexpr int kWinB = kChunk + 96;    // lead + chunk + 64 lookahead + 16 slack
-constexpr int kTokCap = 32 + 256;     // per-warp word queue (< 32 left + <= 256 per strip)
-constexpr int kTailCap = 64;          // per-warp tail queue
-constexpr int kLongCap = 48;          // per-warp queue of words of 17+ letters (< 16 left + <= 32 per step)
-constexpr int kHeadBuckets = 2048;    // 8192 head slots
+constexpr int kWarps = 20;                // warps of the counting kernel, each with its own ring
+constexpr int kBlock = kWarps * 32;
+constexpr int kStrip = 512;               // bytes a warp classifies per step (16 per lane)
+constexpr int kLead = 16;                 // window bytes before the strip (the previous byte, aligned)
+constexpr int kWinB = kLead + kStrip + 32;  // + 32 lookahead: 560 bytes, a multiple of 16
+constexpr int kStages = 4;                // ring buffers per warp
+constexpr int kTokCap = 32 + 256;         // queued words: < 32 left over + at most 256 starts a strip
+constexpr int kTailCap = 64;
+constexpr int kLongCap = 48;              // < 16 left over + at most 32 starts a step
+constexpr int kHeadSlots = 8192;          // level-1 table keys
+constexpr int kHeadBuckets = 2048;        // hash-and-displace buckets of the HEAD image
+constexpr int kLocalProbes = 4;
 constexpr int kSamplePieces = 64;
 constexpr int kSamplePieceBytes = 65536;
 constexpr uint64_t kHeadMinBytes = 16ull << 20;
 constexpr unsigned long long kSampleSlots = 1ull << 19;
-constexpr int kSampleLocalBits = 13;  // per-block table of the sampling pass (the head area)
-static_assert((1u << kSampleLocalBits) <= kHeadBuckets * 4, "sampling table fits the head area");
-constexpr uint32_t kHeadSortN = kHeadBuckets * 4;  // >= candidates, a multiple of 1024
-constexpr uint32_t kHeadIdxBits = 13;
-constexpr uint32_t kHeadCntMax = (1u << (32 - kHeadIdxBits)) - 1u;  // sample counts are clamped here
-static_assert(kHeadSortN % 1024 == 0, "head candidates per build thread");
+constexpr int kHeadRegions = 16;          // the image is placed region by region, one warp each
+constexpr int kRegionSlots = kHeadSlots / kHeadRegions;
+constexpr uint32_t kHeadMax = kHeadSlots * 80 / 100;  // head candidates (load factor of the image)
+constexpr uint32_t kHotMax = 512;                     // candidates placed first (the sample's most frequent)
+static_assert(kWinB % 16 == 0, "TMA bulk copies move multiples of 16 bytes");
+static_assert(kStages == 4, "2-bit stage tag in queued words");
+
+enum : int { MODE_HEAD = 0, MODE_LOCAL = 1, MODE_SAMPLE = 2 };
 
 struct Count2Args {
     const uint8_t *text;
     unsigned long long lo, hi;        // document bytes text[lo, hi)
-    uintptr_t base_al;                // absolute address of chunk 0 (16-aligned, <= text + lo)
-    uint32_t nchunks;
-    uint32_t piece_chunks;            // chunks per piece (sampling) or nchunks
-    unsigned long long piece_stride;  // bytes between pieces (sampling) or 0
+    uintptr_t base_al;                // absolute address of strip 0 (16-aligned, <= text + lo)
+    unsigned long long nstrips;
+    uint32_t piece_strips;            // strips per piece (sampling) or 0 (contiguous)
+    unsigned long long piece_stride;  // bytes between pieces (sampling)
     GTable g;
     const uint8_t *lbegin;            // long-word representatives lie in [lbegin, text + hi)
-    const unsigned long long *head;   // head image (nb * 4 keys) or null
-    const uint32_t *head_fp;          // its fingerprints (nb words of 4 bytes)
-    uint32_t nb;
+    const unsigned long long *head;   // HEAD image: kHeadSlots keys
+    const uint8_t *head_disp;         // HEAD image: kHeadBuckets displacements
 };
 
 // ---------------------------------------------------------------- TMA + mbarrier
@@ -96,7 +101,8 @@ __device__ __forceinline__ unsigned long long policy_evict_first() {
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
-// Arms `bar` for `bytes` and starts the bulk copy global -> shared.
+// Arms `bar` for `bytes` and starts the bulk copy global -> shared.  Both
+// addresses are 16-byte aligned and bytes is a multiple of 16.
 __device__ __forceinline__ void tma_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
                                          unsigned long long policy) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
@@ -106,6 +112,9 @@ __device__ __forceinline__ void tma_load(void *dst, const void *src, uint32_t by
             smem_addr(dst)),
         "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
         : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 // Bounded wait for the phase `parity` of `bar` (at most `polls` polls);
 // false on timeout.
@@ -125,257 +134,260 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
     return false;
 }
 
-// ---------------------------------------------------------------- staging
 __device__ __forceinline__ uint4 spaces16() { return make_uint4(0x20202020u, 0x20202020u, 0x20202020u, 0x20202020u); }
 
-// Plain-load staging of the window at absolute (aligned) address w0: bytes
-// outside [vb, ve) become spaces; 16-byte blocks holding no valid byte are
-// not read at all.
-__device__ __forceinline__ void stage_masked(uint8_t *win, uintptr_t w0, uintptr_t vb, uintptr_t ve) {
-    for (int t = threadIdx.x; t < kWinB / 16; t += blockDim.x) {
-        uintptr_t a = w0 + 16 * (uintptr_t)t;
-        uint4 v = spaces16();
-        if (a < ve && a + 16 > vb) {
-            v = ld_stream16(reinterpret_cast<const void *>(a));
-            if (a < vb || a + 16 > ve) v = mask_outside_doc(v, a, vb, ve);
-        }
-        *reinterpret_cast<uint4 *>(win + 16 * t) = v;
-    }
+// ---------------------------------------------------------------- level-1 tables
+// Both table kinds hold kHeadSlots 8-byte keys (words of at most 8 letters,
+// lowercased, zero padded; never 0) and 32-bit counts.  One block's counts
+// stay below 2^32: a block reads at most 2^40 / 128 bytes (texts are under
+// 2^40 bytes and grids have at least 128 blocks), so it sees fewer than 2^32
+// words.
+//
+// Level-1 hash of an 8-byte key: the high letters folded onto the low bits,
+// times an odd constant, so that every bit of the product depends on every
+// letter.
+__device__ __forceinline__ unsigned long long l1_mix(unsigned long long key) {
+    if (kOneSlot) return 0ull;  // test build: one home slot, one bucket
+    return (key ^ (key >> 29)) * 0xBF58476D1CE4E5B9ull;
 }
-
-// ---------------------------------------------------------------- keys
-// 8 lowercased bytes of win[p, p+len), zero padded (1 <= len <= 8), little endian.
-__device__ __forceinline__ unsigned long long load_key8(const uint8_t *win, uint32_t p, uint32_t len) {
-    const uint32_t *w = reinterpret_cast<const uint32_t *>(win + (p & ~3u));
-    const uint32_t sh = (p & 3u) * 8u;
-    const uint32_t a0 = w[0], a1 = w[1], a2 = w[2];
-    const unsigned long long v = ((unsigned long long)__funnelshift_r(a1, a2, sh) << 32) | __funnelshift_r(a0, a1, sh);
-    return (v | 0x2020202020202020ull) & (~0ull >> (64u - 8u * len));
+// HEAD image (hash and displace): a key's bucket is the top 11 bits of its
+// hash and its region the bucket's low 4 bits; every key of a bucket is
+// placed in its region at base + d * step (mod 512) for the bucket's one
+// displacement d, with base and odd step taken from other bits of the hash,
+// so the slots of one key for d = 0, 1, ... are all distinct.
+static_assert(kHeadSlots == 8192 && kHeadBuckets == 2048 && kRegionSlots == 512, "hash bit fields below");
+__device__ __forceinline__ uint32_t head_bucket(unsigned long long h) { return (uint32_t)(h >> 53); }
+__device__ __forceinline__ uint32_t head_slot(unsigned long long h, uint32_t d) {
+    const uint32_t base = (uint32_t)(h >> 32), step = ((uint32_t)h >> 12) | 1u;
+    return ((head_bucket(h) & (uint32_t)(kHeadRegions - 1)) << 9) | ((base + d * step) & (uint32_t)(kRegionSlots - 1));
 }
+// LOCAL table: home slot = the top 13 bits of the hash.
+__device__ __forceinline__ uint32_t local_home(unsigned long long h) { return (uint32_t)(h >> 51); }
 
-__device__ __forceinline__ uint32_t head_bucket(unsigned long long key, unsigned long long mul, uint32_t nb) {
-    if (kOneSlot) return 0u;  // test build: one bucket for every head word
-    return __umulhi((uint32_t)((key * mul) >> 32), nb);
-}
-constexpr unsigned long long kHeadMulA = 0x9E3779B97F4A7C15ull;
-constexpr unsigned long long kHeadMulB = 0xC2B2AE3D27D4EB4Full;
-
-// One-byte fingerprint of a head key (never 0: 0 marks an empty slot), from
-// bits of the first bucket hash below the ones that pick the bucket.
-__device__ __forceinline__ uint32_t head_fp(unsigned long long key) {
-    const uint32_t f = (uint32_t)((key * kHeadMulA) >> 40) & 0xFFu;
-    return f ? f : 1u;
-}
-
-// Slot of key in the shared head image, or -1 (two buckets of four).  The
-// two buckets' fingerprint words (one byte a slot) are read first; only a
-// slot whose fingerprint matches has its key read and compared.  Most words
-// outside the head stop at the fingerprints, and a word in the head costs
-// two 4-byte and one 8-byte shared load.
-__device__ __forceinline__ int head_find(const unsigned long long *hkey, const uint32_t *hfp,
-                                         unsigned long long key, uint32_t nb) {
-    const uint32_t b1 = head_bucket(key, kHeadMulA, nb), b2 = head_bucket(key, kHeadMulB, nb);
-    const uint32_t f4 = head_fp(key) * 0x01010101u;
-    const uint32_t x1 = hfp[b1] ^ f4, x2 = hfp[b2] ^ f4;  // a zero byte = a matching fingerprint
-    // 0x80 in each zero byte (and possibly in bytes above one: those fail the key compare)
-    unsigned long long mm = ((unsigned long long)((x2 - 0x01010101u) & ~x2 & 0x80808080u) << 32) |
-                            ((x1 - 0x01010101u) & ~x1 & 0x80808080u);
-    while (mm) {
-        const int bit = __ffsll((long long)mm) - 1;  // 8 * byte + 7
-        const uint32_t slot = bit < 32 ? b1 * 4 + (uint32_t)(bit >> 3) : b2 * 4 + (uint32_t)((bit - 32) >> 3);
-        if (hkey[slot] == key) return (int)slot;
-        mm &= mm - 1;
+// The LOCAL slot holding `key`, claiming the first empty slot on its probe
+// path by 64-bit CAS; -1 after kLocalProbes occupied slots of other keys.
+// Keys are written once (CAS from 0) and never move, so a load that sees a
+// non-zero key sees that slot's final key.
+__device__ __forceinline__ int local_slot(unsigned long long *skey, unsigned long long key) {
+    uint32_t s = local_home(l1_mix(key));
+#pragma unroll 1
+    for (int p = 0; p < kLocalProbes; p++) {
+        unsigned long long k = *reinterpret_cast<volatile unsigned long long *>(&skey[s]);
+        if (k == 0ull) k = atomicCAS(&skey[s], 0ull, key);
+        if (k == 0ull || k == key) return (int)s;
+        s = (s + 1u) & (uint32_t)(kHeadSlots - 1);
     }
     return -1;
 }
 
-// Run length of the letters at w (w is a letter), capped at `end`: the warp
-// scans 32 bytes per step.  All lanes call with the same w.
-__device__ __forceinline__ unsigned long long run_length_warp(const uint8_t *w, const uint8_t *end) {
-    const int lane = threadIdx.x & 31;
-    for (unsigned long long off = 0;; off += 32) {
-        const uint8_t *q = w + off + lane;
-        uint32_t b = q < end ? *q : 0x20u;
-        uint32_t m = __ballot_sync(kFull, !is_letter(b));
-        if (m) return off + (unsigned long long)(__ffs(m) - 1);
+// ---------------------------------------------------------------- keys
+__device__ __forceinline__ unsigned long long key_lo(uint4 k) { return ((unsigned long long)k.y << 32) | k.x; }
+// 16 lowercased bytes of the word win[p, p + len) (len <= 16), zero padded:
+// a word of at most 8 letters has a zero upper half, and its lower half is
+// its 8-byte key.  mask[len] keeps the low len bytes; lowercasing and masking
+// take one three-input logic operation per word.  Reads win[p & ~3, +20).
+__device__ __forceinline__ uint4 window_key16(const uint8_t *win, uint32_t p, uint32_t len, const uint4 *mask) {
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(win + (p & ~3u));
+    const uint32_t sh = (p & 3u) * 8u;
+    const uint32_t a0 = w[0], a1 = w[1], a2 = w[2], a3 = w[3], a4 = w[4];
+    const uint4 m = mask[len];
+    return make_uint4((__funnelshift_r(a0, a1, sh) | 0x20202020u) & m.x, (__funnelshift_r(a1, a2, sh) | 0x20202020u) & m.y,
+                      (__funnelshift_r(a2, a3, sh) | 0x20202020u) & m.z, (__funnelshift_r(a3, a4, sh) | 0x20202020u) & m.w);
+}
+
+// ---------------------------------------------------------------- level 2
+// Per-warp tail inserts, 32 words at a time (one per lane), as a state
+// machine that never waits for a dependent round trip inside a flush.  A
+// lane takes a word from the tail queue, computes its home slot and starts
+// loading the keys stored there and in the next slot; at the next flush
+// (when the next 32 tail words are ready, so the loads had time to land) it
+// advances one step:
+//   * the key is in one of the two slots: a fire-and-forget add, done;
+//   * the first slot not holding another key for good is empty (or, for
+//     16-byte keys, half written): a CAS claims it, and its result is
+//     checked at the following flush (the word is done if the CAS won or
+//     found the same key, else probing resumes after that slot);
+//   * both slots hold other keys: loads of the next two slots are started.
+// Keys are written once and never move, so a key seen in a slot is final.
+// Lanes still busy keep their word across flushes; free lanes take new words.
+template <int MODE>
+struct Tail {
+    const GTable &g;
+    uint32_t st = 0;  // 0 free, 1 loads in flight, 2 CAS in flight
+    bool p16 = false;
+    uint32_t probes = 0;
+    uint4 pk;
+    unsigned long long pslot = 0, v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+
+    __device__ __forceinline__ explicit Tail(const GTable &gt) : g(gt) {}
+
+    __device__ __forceinline__ void load() {
+        if (!p16) {
+            v0 = ld_u64(&g.slots8[pslot].key);
+            v1 = ld_u64(&g.slots8[(pslot + 1) & g.mask8].key);
+        } else {
+            const unsigned long long *kp = reinterpret_cast<const unsigned long long *>(&g.slots[pslot].key);
+            const unsigned long long *kq =
+                reinterpret_cast<const unsigned long long *>(&g.slots[(pslot + 1) & g.mask].key);
+            v0 = ld_u64(kp);
+            v1 = ld_u64(kp + 1);
+            v2 = ld_u64(kq);
+            v3 = ld_u64(kq + 1);
+        }
+        st = 1;
     }
-}
-
-// ---------------------------------------------------------------- kernel
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-template <bool SAMPLE>
-struct Counter2 {
-    const Count2Args &a;
-    unsigned long long *hkey;  // head image keys (read only) or the sampling table
-    uint32_t *hcnt;
-    const uint32_t *hfp;       // head fingerprints
-    uint4 *tailq;
-    uint32_t nslots;
-    uint32_t tailn;
-    int lane;
-
-    // One queued word per lane (have = lane holds one): a word of <= 8
-    // letters found in the head image adds 1 to its shared count; any other
-    // word is pushed to the tail queue, which is flushed 32 at a time.
-    __device__ __forceinline__ void word(const uint8_t *win, bool have, uint32_t e) {
-        bool tail = false;
-        uint4 tk = make_uint4(0, 0, 0, 0);
-        if (SAMPLE) {
-            if (have && (e & 31u) <= 8u) {
-                const unsigned long long key = load_key8(win, e >> 5, e & 31u);
-                tail = !sample_add(key);
-                tk = make_uint4((uint32_t)key, (uint32_t)(key >> 32), 0u, 0u);
-            }
-            push(tail, tk);
+    __device__ __forceinline__ void take(uint4 k) {
+        pk = k;
+        p16 = MODE != MODE_SAMPLE && (k.z | k.w) != 0u;
+        pslot = p16 ? (hash_key(k) & g.mask) : (hash8(key_lo(k)) >> __clzll((long long)g.mask8));
+        probes = 0;
+        load();
+    }
+    __device__ __forceinline__ void add_at(unsigned long long s) {
+        if (!p16) red_add_u64(&g.slots8[s].cnt, 1ull);
+        else red_add_u64(&g.slots[s].cnt, 1ull);
+        st = 0;
+    }
+    __device__ __forceinline__ void claim(unsigned long long s) {
+        pslot = s;
+        if (!p16) {
+            v0 = atomicCAS(&g.slots8[s].key, 0ull, key_lo(pk));
+        } else {
+            const uint4 old = cas128_global(&g.slots[s].key, make_uint4(0u, 0u, 0u, 0u), pk);
+            v0 = ((unsigned long long)old.y << 32) | old.x;
+            v1 = ((unsigned long long)old.w << 32) | old.z;
+        }
+        st = 2;
+    }
+    __device__ __forceinline__ void next(unsigned long long from) {
+        probes += 2;
+        if (probes >= (uint32_t)kGlobalProbeLimit) {  // the table is full: reported, the word dropped
+            atomicOr(g.status, ST_TABLE_FULL);
+            st = 0;
             return;
         }
-        const int hs = lookup(win, have, e, tail, tk);
-        if (hs >= 0) atomicAdd(hcnt + hs, 1u);
-        push(tail, tk);
+        pslot = from & (p16 ? g.mask : g.mask8);
+        load();
     }
-    // The head slot of a queued word (-1 if none) and, when it is not in the
-    // head, the key it goes to the tail queue with.
-    __device__ __forceinline__ int lookup(const uint8_t *win, bool have, uint32_t e, bool &tail, uint4 &tk) {
-        tail = false;
-        tk = make_uint4(0, 0, 0, 0);
-        int hs = -1;
-        if (have) {
-            const uint32_t p = e >> 5, len = e & 31u;
-            tail = true;
-            // one key load for every length (no divergent paths): a word of
-            // <= 8 letters has a zero upper half, and its lower half is its
-            // 8-byte key
-            tk = load_key16(win, p, len);
-            if (len <= 8 && nslots) {
-                hs = head_find(hkey, hfp, ((unsigned long long)tk.y << 32) | tk.x, a.nb);
-                tail = hs < 0;
-            }
+    // One step of a busy lane with what its last step fetched.
+    __device__ __forceinline__ void step() {
+        const unsigned long long m = p16 ? g.mask : g.mask8;
+        const unsigned long long k0 = key_lo(pk), k1 = ((unsigned long long)pk.w << 32) | pk.z;
+        if (st == 2) {  // the CAS result
+            const bool mine = p16 ? ((v0 == 0ull && v1 == 0ull) || (v0 == k0 && v1 == k1)) : (v0 == 0ull || v0 == k0);
+            if (mine) add_at(pslot);
+            else next(pslot + 1);
+            return;
         }
-        return hs;
-    }
-    __device__ __forceinline__ void push(bool tail, uint4 tk) {
-        const uint32_t tb = __ballot_sync(kFull, tail);
-        if (tail) tailq[tailn + __popc(tb & ((1u << lane) - 1u))] = tk;
-        tailn += __popc(tb);
-        __syncwarp();
-        if (tailn >= 32) {
-            tailn -= 32;
-            const uint4 k = tailq[tailn + lane];
-            __syncwarp();
-            complete();  // the previous 32: their slot loads have had time to land
-            issue(k);
-        }
-    }
-    // Sampling pass: the shared head area is a per-block open-addressing table
-    // (keys claimed by CAS), so frequent words cost one shared atomic each
-    // instead of a global atomic on one hot slot; false when the probe limit
-    // is reached (the word then goes to the global sample table).
-    __device__ __forceinline__ bool sample_add(unsigned long long key) {
-        uint32_t s = (uint32_t)(hash8(key) >> (64 - kSampleLocalBits));
-        for (int probe = 0; probe < 16; probe++) {
-            unsigned long long k = hkey[s];
-            if (k == 0ull) k = atomicCAS(&hkey[s], 0ull, key);
-            if (k == 0ull || k == key) {
-                atomicAdd(hcnt + s, 1u);
-                return true;
-            }
-            s = (s + 1u) & ((1u << kSampleLocalBits) - 1u);
-        }
-        return false;
-    }
-    __device__ __forceinline__ void insert(uint4 k) {
-        if (!SAMPLE) table_insert_key(a.g, k, 1ull);
-        else global_insert8(a.g, ((unsigned long long)k.y << 32) | k.x, 1ull);
-    }
-
-    // Tail inserts in two halves.  issue() computes the home slot of the key
-    // and starts loading the keys stored there and in the next slot (the
-    // first two probe positions); complete() (called when the next 32 words
-    // are ready, so the loads had time to arrive) finishes the insert.  A
-    // matching key is final wherever it was seen (keys are written once and
-    // never move), so it gets a fire-and-forget add.  Otherwise the probe
-    // resumes with fresh loads at the first position that the early loads did
-    // not show holding another key for good: an empty or half-written slot is
-    // settled there by the CAS.
-    bool pend = false, p16 = false;
-    uint4 pk;
-    unsigned long long pslot = 0, pv0 = 0, pv1 = 0, pv2 = 0, pv3 = 0;
-    __device__ __forceinline__ void issue(uint4 k) {
-        pk = k;
-        pend = true;
-        p16 = !SAMPLE && (k.z | k.w) != 0u;
         if (!p16) {
-            const unsigned long long key = ((unsigned long long)k.y << 32) | k.x;
-            pslot = hash8(key) >> __clzll((long long)a.g.mask8);
-            pv0 = ld_u64(&a.g.slots8[pslot].key);
-            pv1 = ld_u64(&a.g.slots8[(pslot + 1) & a.g.mask8].key);
+            if (v0 == k0) { add_at(pslot); return; }
+            if (v1 == k0) { add_at((pslot + 1) & m); return; }
+            if (v0 == 0ull) { claim(pslot); return; }
+            if (v1 == 0ull) { claim((pslot + 1) & m); return; }
         } else {
-            pslot = hash_key(k) & a.g.mask;
-            const unsigned long long *kp = reinterpret_cast<const unsigned long long *>(&a.g.slots[pslot].key);
-            const unsigned long long *kq =
-                reinterpret_cast<const unsigned long long *>(&a.g.slots[(pslot + 1) & a.g.mask].key);
-            pv0 = ld_u64(kp);
-            pv1 = ld_u64(kp + 1);
-            pv2 = ld_u64(kq);
-            pv3 = ld_u64(kq + 1);
-        }
-    }
-    __device__ __forceinline__ void complete() {
-        if (!pend) return;
-        pend = false;
-        if (!p16) {
-            const unsigned long long key = ((unsigned long long)pk.y << 32) | pk.x, m = a.g.mask8;
-            if (pv0 == key) { red_add_u64(&a.g.slots8[pslot].cnt, 1ull); return; }
-            if (pv1 == key) { red_add_u64(&a.g.slots8[(pslot + 1) & m].cnt, 1ull); return; }
-            const unsigned long long from = pv0 == 0ull ? pslot : (pv1 == 0ull ? pslot + 1 : pslot + 2);
-            global_insert8_from(a.g, key, 1ull, from & m);
-        } else {
-            const unsigned long long k0 = ((unsigned long long)pk.y << 32) | pk.x;
-            const unsigned long long k1 = ((unsigned long long)pk.w << 32) | pk.z, m = a.g.mask;
-            if (pv0 == k0 && pv1 == k1) { red_add_u64(&a.g.slots[pslot].cnt, 1ull); return; }
-            if (pv2 == k0 && pv3 == k1) { red_add_u64(&a.g.slots[(pslot + 1) & m].cnt, 1ull); return; }
+            if (v0 == k0 && v1 == k1) { add_at(pslot); return; }
+            if (v2 == k0 && v3 == k1) { add_at((pslot + 1) & m); return; }
             // both halves non-zero: the slot holds another key for good
-            const bool other0 = pv0 != 0ull && pv1 != 0ull, other1 = pv2 != 0ull && pv3 != 0ull;
-            const unsigned long long from = !other0 ? pslot : (!other1 ? pslot + 1 : pslot + 2);
-            global_insert16_from(a.g, pk, 1ull, from & m);
+            if (v0 == 0ull || v1 == 0ull) { claim(pslot); return; }
+            if (v2 == 0ull || v3 == 0ull) { claim((pslot + 1) & m); return; }
         }
+        next(pslot + 2);
+    }
+    // One flush round: busy lanes step, free lanes take words from the end of
+    // the queue (tailn, warp-uniform, is updated).
+    __device__ __forceinline__ void round(const uint4 *tailq, uint32_t &tailn, int lane) {
+        if (st) step();
+        const uint32_t freem = __ballot_sync(kFull, st == 0u);
+        const uint32_t nf = __popc(freem);
+        const uint32_t tk = nf < tailn ? nf : tailn;
+        const uint32_t r = __popc(freem & ((1u << lane) - 1u));
+        if (st == 0u && r < tk) take(tailq[tailn - tk + r]);
+        tailn -= tk;
+        __syncwarp();
     }
 };
 
-template <bool SAMPLE>
-struct Ring {
-    const Count2Args &a;
-    uint8_t *buf;          // kStages x kWinB
-    uint64_t *full;        // kStages mbarriers
-    uint32_t *done;        // kStages release counters
-    uintptr_t vb, ve;
-    unsigned long long policy;
+// ---------------------------------------------------------------- kernel
+constexpr size_t kSmemKeys = (size_t)kHeadSlots * 8;
+constexpr size_t kSmemCnts = (size_t)kHeadSlots * 4;
+constexpr size_t kSmemDisp = (size_t)kHeadBuckets;
+constexpr size_t kSmemRing = (size_t)kWarps * kStages * kWinB;
+constexpr size_t kSmemTok = (size_t)kWarps * kTokCap * 4;
+constexpr size_t kSmemTail = (size_t)kWarps * kTailCap * 16;
+constexpr size_t kSmemLong = (size_t)kWarps * kLongCap * 8;
+constexpr size_t kSmemBars = (size_t)kWarps * kStages * 8;
+constexpr size_t kCountSmem = kSmemKeys + kSmemCnts + kSmemDisp + kSmemRing + kSmemTok + kSmemTail + kSmemLong + kSmemBars;
+static_assert((kSmemKeys + kSmemCnts + kSmemDisp) % 16 == 0 && kSmemRing % 16 == 0 && kSmemTok % 16 == 0,
+              "16-byte aligned ring buffers and queues");
+static_assert(kCountSmem <= 227 * 1024, "counting kernel shared memory");
 
-    __device__ __forceinline__ uintptr_t win_start(uint32_t c) const {
-        uint32_t q = c / a.piece_chunks, r = c % a.piece_chunks;
-        return a.base_al + (uintptr_t)q * a.piece_stride + (uintptr_t)r * kChunk - kLead;
+template <int MODE>
+__global__ void __launch_bounds__(kBlock, 1) k_count3(Count2Args a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    unsigned long long *skey = reinterpret_cast<unsigned long long *>(smem);
+    uint32_t *scnt = reinterpret_cast<uint32_t *>(smem + kSmemKeys);
+    uint8_t *sdisp = smem + kSmemKeys + kSmemCnts;
+    uint8_t *ring_all = sdisp + kSmemDisp;
+    uint32_t *tok_all = reinterpret_cast<uint32_t *>(ring_all + kSmemRing);
+    uint4 *tail_all = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(tok_all) + kSmemTok);
+    unsigned long long *long_all = reinterpret_cast<unsigned long long *>(reinterpret_cast<uint8_t *>(tail_all) + kSmemTail);
+    uint64_t *bar_all = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(long_all) + kSmemLong);
+
+    __shared__ uint4 kmask[17];  // kmask[n]: the low n bytes of 16 kept
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint8_t *ring = ring_all + (size_t)warp * kStages * kWinB;
+    uint64_t *full = bar_all + warp * kStages;
+    uint32_t *tok = tok_all + warp * kTokCap;
+    uint4 *tailq = tail_all + warp * kTailCap;
+    unsigned long long *longq = long_all + warp * kLongCap;
+
+    for (int i = threadIdx.x; i < kHeadSlots; i += kBlock) {
+        skey[i] = MODE == MODE_HEAD ? a.head[i] : 0ull;
+        scnt[i] = 0u;
     }
-    __device__ __forceinline__ bool interior(uintptr_t w0) const { return w0 >= vb && w0 + kWinB <= ve; }
+    if (MODE == MODE_HEAD)
+        for (int i = threadIdx.x; i < kHeadBuckets; i += kBlock) sdisp[i] = a.head_disp[i];
+    if (threadIdx.x <= 16) {
+        const int n = threadIdx.x;
+        kmask[n] = make_uint4(byte_keep_mask(n), byte_keep_mask(n - 4), byte_keep_mask(n - 8), byte_keep_mask(n - 12));
+    }
+    if (lane == 0) {
+        for (int b = 0; b < kStages; b++) mbar_init(&full[b], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
 
-    // The calling warp stages this block's i-th chunk into buffer i % kStages.
-    __device__ __forceinline__ void produce(uint32_t i) {
-        const uint32_t c = blockIdx.x + i * gridDim.x;
-        if (c >= a.nchunks) return;
-        const int b = (int)(i % kStages);
-        const uintptr_t w0 = win_start(c);
-        const int lane = threadIdx.x & 31;
-        if (interior(w0)) {
+    const uintptr_t vb = reinterpret_cast<uintptr_t>(a.text) + a.lo, ve = reinterpret_cast<uintptr_t>(a.text) + a.hi;
+    const uint8_t *end = reinterpret_cast<const uint8_t *>(ve);
+    const unsigned long long policy = policy_evict_first();
+    // this warp's strips: s0, s0 + stride, ...
+    const unsigned long long stride = (unsigned long long)gridDim.x * kWarps;
+    const unsigned long long s0 = (unsigned long long)blockIdx.x * kWarps + (unsigned long long)warp;
+    const unsigned long long nk = s0 < a.nstrips ? (a.nstrips - s0 + stride - 1) / stride : 0ull;
+
+    auto win_start = [&](unsigned long long k) -> uintptr_t {
+        const unsigned long long s = s0 + k * stride;
+        if (a.piece_strips == 0u) return a.base_al + (uintptr_t)(s * kStrip) - kLead;
+        const unsigned long long q = s / a.piece_strips, r = s % a.piece_strips;
+        return a.base_al + (uintptr_t)(q * a.piece_stride + r * kStrip) - kLead;
+    };
+    // Stages this warp's k-th strip into ring buffer k % kStages (strips are
+    // produced in order; `issued` is one past the last one).
+    unsigned long long issued = 0;
+    auto produce = [&](unsigned long long k) {
+        if (k >= nk) return;
+        issued = k + 1;
+        const int b = (int)(k % kStages);
+        uint8_t *win = ring + b * kWinB;
+        const uintptr_t w0 = win_start(k);
+        if (w0 >= vb && w0 + kWinB <= ve) {
             if (lane == 0) {
                 fence_proxy_async();
-                tma_load(buf + b * kWinB, reinterpret_cast<const void *>(w0), kWinB, &full[b], policy);
+                tma_load(win, reinterpret_cast<const void *>(w0), kWinB, &full[b], policy);
             }
-        } else {
-            uint8_t *win = buf + b * kWinB;
+        } else {  // a document edge: plain loads, the outside read as spaces
             for (int t = lane; t < kWinB / 16; t += 32) {
-                uintptr_t ad = w0 + 16 * (uintptr_t)t;
+                const uintptr_t ad = w0 + 16 * (uintptr_t)t;
                 uint4 v = spaces16();
                 if (ad < ve && ad + 16 > vb) {
                     v = ld_stream16(reinterpret_cast<const void *>(ad));
@@ -384,145 +396,128 @@ struct Ring {
                 *reinterpret_cast<uint4 *>(win + 16 * t) = v;
             }
             __syncwarp();
-            if (lane == 0) {
-                __threadfence_block();
-                mbar_arrive(&full[b]);
-            }
-        }
-        __syncwarp();
-    }
-    // The calling warp is done with chunk i; the last warp refills the buffer.
-    __device__ __forceinline__ void release(uint32_t i) {
-        const int b = (int)(i % kStages);
-        const int lane = threadIdx.x & 31;
-        __syncwarp();
-        uint32_t last = 0;
-        if (lane == 0) {
-            __threadfence_block();
-            last = atomicAdd(&done[b], 1u) == kWarps - 1;
-            if (last) done[b] = 0;
-        }
-        if (__shfl_sync(kFull, last, 0)) produce(i + kStages);
-    }
-};
-
-template <bool SAMPLE>
-__global__ void __launch_bounds__(kBlock, 1) k_count2(Count2Args a) {
-    extern __shared__ __align__(128) uint8_t smem[];
-    unsigned long long *hkey = reinterpret_cast<unsigned long long *>(smem);        // nb*4
-    uint32_t *hcnt = reinterpret_cast<uint32_t *>(hkey + kHeadBuckets * 4);           // nb*4
-    uint8_t *ring = reinterpret_cast<uint8_t *>(hcnt + kHeadBuckets * 4);             // kStages x kWinB
-    uint32_t *tokall = reinterpret_cast<uint32_t *>(ring + kStages * kWinB);         // warps x kTokCap
-    uint4 *tailall = reinterpret_cast<uint4 *>(tokall + kWarps * kTokCap);           // warps x kTailCap
-    uint4 *longall = tailall + kWarps * kTailCap;                                     // warps x kLongCap
-    uint64_t *full = reinterpret_cast<uint64_t *>(longall + kWarps * kLongCap);     // kStages
-    uint32_t *done = reinterpret_cast<uint32_t *>(full + kStages);                   // kStages
-    uint32_t *hfp = done + kStages;                                                   // nb
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *tok = tokall + warp * kTokCap;
-    uint4 *longq = longall + warp * kLongCap;
-    // head image (counting) or an empty local table (sampling)
-    const uint32_t nslots = SAMPLE ? (1u << kSampleLocalBits) : (a.head ? a.nb * 4 : 0);
-    Counter2<SAMPLE> ctr{a, hkey, hcnt, hfp, tailall + warp * kTailCap, nslots, 0u, lane};
-
-    for (uint32_t i = threadIdx.x; i < nslots; i += kBlock) {
-        hkey[i] = SAMPLE ? 0ull : a.head[i];
-        hcnt[i] = 0u;
-    }
-    if (!SAMPLE && nslots)
-        for (uint32_t i = threadIdx.x; i < a.nb; i += kBlock) hfp[i] = a.head_fp[i];
-    if (threadIdx.x < kStages) done[threadIdx.x] = 0u;
-    if (threadIdx.x == 0) {
-        for (int b = 0; b < kStages; b++) mbar_init(&full[b], 1);
-        fence_barrier_init();
-    }
-    __syncthreads();
-
-    Ring<SAMPLE> rg{a, ring, full, done, reinterpret_cast<uintptr_t>(a.text) + a.lo,
-                    reinterpret_cast<uintptr_t>(a.text) + a.hi, policy_evict_first()};
-    const uint8_t *begin = reinterpret_cast<const uint8_t *>(rg.vb);
-    const uint8_t *end = reinterpret_cast<const uint8_t *>(rg.ve);
-    if (warp == 0)
-        for (uint32_t i = 0; i < kStages; i++) rg.produce(i);
-
-    uint32_t tcount = 0;   // queued words (warp-uniform)
-    uint32_t tprev = 0;    // how many of them belong to the previous chunk
-    uint32_t longn = 0;    // queued long words
-    bool timed_out = false;
-    auto flush_long = [&](uint32_t base, uint32_t n) {
-        if ((uint32_t)lane < n) {
-            uint4 e = longq[base + lane];
-            const uint8_t *w = reinterpret_cast<const uint8_t *>(((unsigned long long)e.y << 32) | e.x);
-            unsigned long long len = e.z;
-            if (len == 0) {  // longer than the window showed: scan to the end of the run
-                len = 17;
-                while (w + len < end && is_letter(w[len])) len++;
-            }
-            long_insert2(a.g, w, len, long_hash(w, len), 1ull, a.lbegin, end);
+            if (lane == 0) mbar_arrive(&full[b]);
         }
         __syncwarp();
     };
 
-    uint32_t i = 0;
-    for (uint32_t c = blockIdx.x; c < a.nchunks; c += gridDim.x, i++) {
-        const int b = (int)(i % kStages);
-        if (!mbar_wait(&full[b], (i / kStages) & 1u)) { timed_out = true; break; }
+    Tail<MODE> tl(a.g);
+    uint32_t tailn = 0;
+    // One queued word per lane (have: this lane holds one).
+    auto process = [&](uint32_t e, bool have) {
+        bool tail = false;
+        uint4 tk = make_uint4(0u, 0u, 0u, 0u);
+        if (have) {
+            const uint32_t len = e & 31u, p = (e >> 5) & 0x3FFu;
+            const uint8_t *w = ring + (e >> 27) * kWinB;
+            // one key load for every length (no divergent paths)
+            tk = window_key16(w, p, len, kmask);
+            tail = true;
+            if (len <= 8u) {
+                const unsigned long long key = key_lo(tk);
+                int s;
+                if (MODE == MODE_HEAD) {
+                    const unsigned long long h = l1_mix(key);
+                    const uint32_t hs = head_slot(h, sdisp[head_bucket(h)]);
+                    s = skey[hs] == key ? (int)hs : -1;
+                } else {
+                    s = local_slot(skey, key);
+                }
+                if (s >= 0) {
+                    atomicAdd(&scnt[s], 1u);
+                    tail = false;
+                }
+            } else if (MODE == MODE_SAMPLE) {
+                tail = false;  // the sampling pass looks for frequent words of <= 8 letters only
+            }
+        }
+        const uint32_t tb = __ballot_sync(kFull, tail);
+        if (tail) tailq[tailn + __popc(tb & ((1u << lane) - 1u))] = tk;
+        tailn += __popc(tb);
+        __syncwarp();
+        // flush: the lanes' previous words advance (their loads have had time
+        // to land), free lanes take new ones; the queue ends below 32 words
+        while (tailn >= 32) tl.round(tailq, tailn, lane);
+    };
+
+    // Words of 17+ letters: (address << 16 | run length, or 0 when the window
+    // did not show the run's end), inserted one per lane.
+    uint32_t longn = 0;
+    auto flush_long = [&](uint32_t base, uint32_t n) {
+        if ((uint32_t)lane < n) {
+            const unsigned long long e = longq[base + lane];
+            const uint8_t *w = reinterpret_cast<const uint8_t *>(e >> 16);
+            unsigned long long len = e & 0xFFFFull;
+            if (len == 0) {  // longer than the window showed: scan to the end of the run
+                len = 17;
+                while (w + len < end && is_letter(w[len])) len++;
+            }
+            uint4 fl[2];
+            long_ends(w, len, fl[0], fl[1]);
+            long_insert2(a.g, w, len, long_hash_mix(fl[0], fl[1], len), 1ull, a.lbegin, end, fl);
+        }
+        __syncwarp();
+    };
+
+    for (unsigned long long k = 0; k < kStages; k++) produce(k);
+
+    uint32_t tcount = 0;  // queued words (warp-uniform)
+    uint32_t tprev = 0;   // how many of them belong to the previous strip
+    unsigned long long k = 0;
+    bool timed_out = false;
+    for (; k < nk; k++) {
+        const int b = (int)(k % kStages);
+        if (!mbar_wait(&full[b], (uint32_t)(k / kStages) & 1u)) { timed_out = true; break; }
         const uint8_t *win = ring + b * kWinB;
-        const uintptr_t w0 = rg.win_start(c);
-        // ---- this warp's 512-byte strip
-        const int sbase = kLead + 512 * warp;
-        const uint32_t prevL = is_letter(win[sbase - 1]) ? 1u : 0u;  // the window holds the byte before
-        const uint32_t L = letter_mask16(*reinterpret_cast<const uint4 *>(win + sbase + 16 * lane));
-        const uint32_t Ln = letter_mask16(*reinterpret_cast<const uint4 *>(win + sbase + 512));  // first 16 bytes after
+        // ---- classify this lane's 16 bytes
+        const uint32_t L = letter_mask16(*reinterpret_cast<const uint4 *>(win + kLead + 16 * lane));
+        // the 32 lookahead bytes after the strip, one per lane, as one mask
+        const uint32_t A = __ballot_sync(kFull, is_letter(win[kLead + kStrip + lane]));
+        const uint32_t prevL = is_letter(win[kLead - 1]) ? 1u : 0u;
         const uint32_t up = __shfl_up_sync(kFull, L, 1);
         const uint32_t dn = __shfl_down_sync(kFull, L, 1);
         const uint32_t pbit = lane == 0 ? prevL : ((up >> 15) & 1u);
-        const uint32_t W = L | ((lane == 31 ? Ln : dn) << 16);
-        const uint32_t S = L & ~((L << 1) | pbit) & 0xFFFFu;
+        const uint32_t W = L | ((lane == 31 ? (A & 0xFFFFu) : dn) << 16);  // this lane's and the next 16 bytes
+        const uint32_t S = L & ~((L << 1) | pbit) & 0xFFFFu;                // word starts
         uint32_t x = W;
         x &= x >> 1; x &= x >> 2; x &= x >> 4; x &= x >> 8; x &= W >> 16;  // starts of 17+ letter runs
         uint32_t Ss = S & ~x, Sl = S & x;
+        const uint32_t E = W & ~(W >> 1);  // last letters of runs (bits 0..30 are exact)
 
         const uint32_t c1 = __popc(Ss);
         uint32_t incl = c1;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            uint32_t t = __shfl_up_sync(kFull, incl, d);
+            const uint32_t t = __shfl_up_sync(kFull, incl, d);
             if (lane >= d) incl += t;
         }
         const uint32_t total = __shfl_sync(kFull, incl, 31);
         uint32_t off = tcount + incl - c1;
-        const uint32_t pbase = (uint32_t)(sbase + 16 * lane);
-        static_assert(kStages <= 8 && (kStages & (kStages - 1)) == 0, "3-bit buffer tag in queued words");
-        const uint32_t btag = (uint32_t)b << 19;
-        // a warp-uniform trip count: no divergent loop to reconverge
-        const uint32_t nmax = __reduce_max_sync(kFull, c1);
+        const uint32_t tag = ((uint32_t)b << 27) | ((uint32_t)(kLead + 16 * lane) << 5);
+        const uint32_t nmax = __reduce_max_sync(kFull, c1);  // a warp-uniform trip count
         for (uint32_t r = 0; r < nmax; r++) {
-            if (Ss) {
-                const int j = __ffs(Ss) - 1;
-                Ss &= Ss - 1;
-                const uint32_t len = (uint32_t)__ffs(~(W >> j)) - 1u;
-                tok[off++] = btag | ((pbase + (uint32_t)j) << 5) | len;
+            if (Ss) {  // this lane's starts from the highest down (queue order does not matter)
+                const uint32_t j = 31u - (uint32_t)__clz(Ss);
+                Ss ^= 1u << j;
+                const uint32_t len = (uint32_t)__ffs(E >> j);  // a short word ends within the 32 bits
+                tok[off++] = tag + (j << 5) + len;
             }
         }
-        const uint32_t tnew = total;
         tcount += total;
-        if (!SAMPLE && __any_sync(kFull, Sl != 0)) {
-            // 48 bits of letter mask from this lane on: run lengths up to 32 letters are read here
-            const uint32_t Ln2 = letter_mask16(*reinterpret_cast<const uint4 *>(win + sbase + 528));
+        if (MODE != MODE_SAMPLE && __any_sync(kFull, Sl != 0)) {
+            // 48 bits of letter mask from this lane on: runs shorter than 48 - j are measured here
             const uint32_t dn2 = __shfl_down_sync(kFull, L, 2);
-            const unsigned long long W48 =
-                (unsigned long long)W | ((unsigned long long)(lane == 31 ? Ln2 : (lane == 30 ? Ln : dn2)) << 32);
+            const uint32_t third = lane == 31 ? (A >> 16) : (lane == 30 ? (A & 0xFFFFu) : dn2);
+            const unsigned long long W48 = (unsigned long long)W | ((unsigned long long)third << 32);
+            const uintptr_t lbase = win_start(k) + kLead + 16 * (uintptr_t)lane;
             while (__any_sync(kFull, Sl != 0)) {
                 const bool act = Sl != 0;
-                uint4 e = make_uint4(0, 0, 0, 0);
+                unsigned long long e = 0;
                 if (act) {
-                    int j = __ffs(Sl) - 1;
+                    const int j = __ffs(Sl) - 1;
                     Sl &= Sl - 1;
-                    unsigned long long wa = (unsigned long long)(w0 + pbase + (uint32_t)j);
-                    // letters seen in W48 (< 48 - j), else 0: the run continues past it
                     const uint32_t run = (uint32_t)__ffsll((long long)~(W48 >> j)) - 1u;
-                    e = make_uint4((uint32_t)wa, (uint32_t)(wa >> 32), run < 48u - (uint32_t)j ? run : 0u, 0u);
+                    e = ((unsigned long long)(lbase + (uintptr_t)j) << 16) | (run < 48u - (uint32_t)j ? run : 0u);
                 }
                 const uint32_t lb = __ballot_sync(kFull, act);
                 if (act) longq[longn + __popc(lb & ((1u << lane) - 1u))] = e;
@@ -538,53 +533,46 @@ __global__ void __launch_bounds__(kBlock, 1) k_count2(Count2Args a) {
         __syncwarp();
         // ---- queued words, 32 at a time
         uint32_t bq = 0;
-        for (; bq + 32 <= tcount; bq += 32) {
-            const uint32_t e = tok[bq + lane];
-            ctr.word(ring + ((e >> 19) & (uint32_t)(kStages - 1)) * kWinB, true, e & 0x7FFFFu);
-        }
+        for (; bq + 32 <= tcount; bq += 32) process(tok[bq + lane], true);
         uint32_t rem = tcount - bq;
-        const uint32_t old_left = tprev > bq ? tprev - bq : 0u;
-        if (old_left) {  // words of the previous chunk still queued: finish them all now
+        if (tprev > bq) {  // words of the previous strip still queued: finish them all now
             const uint32_t e = (uint32_t)lane < rem ? tok[bq + lane] : 0u;
-            ctr.word(ring + ((e >> 19) & (uint32_t)(kStages - 1)) * kWinB, (uint32_t)lane < rem, e & 0x7FFFFu);
+            process(e, (uint32_t)lane < rem);
             rem = 0;
         } else if (bq) {
-            uint32_t e = (uint32_t)lane < rem ? tok[bq + lane] : 0u;
+            const uint32_t e = (uint32_t)lane < rem ? tok[bq + lane] : 0u;
             __syncwarp();
             if ((uint32_t)lane < rem) tok[lane] = e;
             __syncwarp();
         }
         tcount = rem;
-        tprev = rem < tnew ? rem : tnew;
-        if (i > 0) rg.release(i - 1);
+        tprev = rem;
+        // the previous strip's buffer holds no queued word any more: refill it
+        if (k > 0) produce(k - 1 + kStages);
     }
-    // ---- drain: queued words of the last chunk, then the tail and long queues
+    // ---- drain: the last strip's queued words, then the long and tail queues
     if (!timed_out) {
         const uint32_t e = (uint32_t)lane < tcount ? tok[lane] : 0u;
-        ctr.word(ring + ((e >> 19) & (uint32_t)(kStages - 1)) * kWinB, (uint32_t)lane < tcount, e & 0x7FFFFu);
-        if (!SAMPLE) {
+        process(e, (uint32_t)lane < tcount);
+        if (MODE != MODE_SAMPLE) {
             flush_long(0, longn < 32 ? longn : 32);
             if (longn > 32) flush_long(32, longn - 32);
         }
-        ctr.complete();
-        if ((uint32_t)lane < ctr.tailn) ctr.insert(ctr.tailq[lane]);
-        __syncwarp();
+        while (tailn > 0 || __any_sync(kFull, tl.st != 0u)) tl.round(tailq, tailn, lane);
     }
     if (__syncthreads_or(timed_out)) {
-        if (threadIdx.x == 0) {
-            atomicOr(a.g.status, ST_TIMEOUT);
-            for (int b = 0; b < kStages; b++) mbar_wait(&full[b], 0u);  // bounded: let copies in flight land
+        if (lane == 0) {
+            if (timed_out) atomicOr(a.g.status, ST_TIMEOUT);
+            // let this warp's copies in flight land before the block exits
+            // (bounded): strips k .. issued - 1 were staged but not waited for
+            for (unsigned long long j = k; j < issued; j++)
+                mbar_wait(&full[j % kStages], (uint32_t)(j / kStages) & 1u);
         }
         return;
     }
-    for (uint32_t k = threadIdx.x; k < nslots; k += kBlock)
-        if (hcnt[k]) global_insert8(a.g, hkey[k], (unsigned long long)hcnt[k]);
+    for (int i = threadIdx.x; i < kHeadSlots; i += kBlock)
+        if (scnt[i]) global_insert8(a.g, skey[i], (unsigned long long)scnt[i]);
 }
-
-constexpr size_t kCountSmem = (size_t)kHeadBuckets * 4 * 8 + (size_t)kHeadBuckets * 4 * 4 + kStages * (size_t)kWinB +
-                              (size_t)kWarps * kTokCap * 4 + (size_t)kWarps * kTailCap * 16 +
-                              (size_t)kWarps * kLongCap * 16 + kStages * 8 + kStages * 4 + (size_t)kHeadBuckets * 4;
-static_assert(kCountSmem <= 227 * 1024, "counting kernel shared memory");
 
 // ---------------------------------------------------------------- head selection
 // Histogram of sample counts (clamped to 4095).
@@ -606,7 +594,7 @@ __global__ void k_head_hist(const G8Slot *s, unsigned long long cap, uint32_t *h
 // of the histogram (one block of 1024 threads, 4 bins each).
 __global__ void __launch_bounds__(1024) k_head_threshold(const uint32_t *hist, uint32_t kmax, uint32_t *meta) {
     __shared__ uint32_t part[1024];
-    __shared__ uint32_t best;
+    __shared__ uint32_t best, hot;
     const uint32_t t = threadIdx.x;
     // bins of thread t, from high counts down: 4095-4t .. 4092-4t
     uint32_t v[4], s = 0;
@@ -617,7 +605,10 @@ __global__ void __launch_bounds__(1024) k_head_threshold(const uint32_t *hist, u
         s += v[j];
     }
     part[t] = s;
-    if (t == 0) best = 4096;
+    if (t == 0) {
+        best = 4096;
+        hot = 4096;
+    }
     __syncthreads();
     for (int w = 1; w < 1024; w <<= 1) {  // inclusive prefix over threads = suffix over counts
         uint32_t x = t >= (uint32_t)w ? part[t - w] : 0u;
@@ -631,11 +622,13 @@ __global__ void __launch_bounds__(1024) k_head_threshold(const uint32_t *hist, u
         const int c = 4095 - 4 * (int)t - j;
         acc += v[j];
         if (c >= 2 && acc <= kmax) atomicMin(&best, (uint32_t)c);
+        if (c >= 2 && acc <= kHotMax) atomicMin(&hot, (uint32_t)c);
     }
     __syncthreads();
     if (t == 0) {
         meta[0] = best;  // threshold
         meta[1] = 0;     // candidates
+        meta[2] = hot;   // the sample count from which a candidate is placed first
     }
 }
 
@@ -649,65 +642,174 @@ __global__ void k_head_collect(const G8Slot *s, unsigned long long cap, uint32_t
             uint32_t k = atomicAdd(&meta[1], 1u);
             if (k < kmax) {
                 cand[k] = s[i].key;
-                ccnt[k] = c < kHeadCntMax ? (uint32_t)c : kHeadCntMax;
+                ccnt[k] = c < 0xFFFFFFFFull ? (uint32_t)c : 0xFFFFFFFFu;
             }
         }
     }
 }
 
-// Two-choice placement of the candidates into nb buckets of 4 (one block),
-// most frequent first: candidates are placed in tiers of equal floor(log2
-// sample count), highest tier first, all candidates of a tier in parallel.
-// A key whose two buckets are both full is left out of the head and counted
-// in the global table.  Placing by frequency makes sure that only the rarest
-// candidates can be left out: a frequent word missing from the head would
-// send all its occurrences to one global slot, whose atomics then serialise.
-__global__ void __launch_bounds__(1024) k_head_build(const unsigned long long *cand, const uint32_t *ccnt,
-                                                     const uint32_t *meta, uint32_t kmax, uint32_t nb,
-                                                     unsigned long long *image, uint32_t *image_fp) {
-    constexpr int kPer = (int)(kHeadSortN / 1024);  // candidates per thread
-    __shared__ uint32_t fill[kHeadBuckets];
-    __shared__ uint32_t fps[kHeadBuckets];
-    const uint32_t n = meta[1] < kmax ? meta[1] : kmax;
-    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) {
-        fill[i] = 0;
-        fps[i] = 0;
+// Places the head candidates into the HEAD image by hash and displace (one
+// block, one warp per region of 512 slots; a region's buckets are placed by
+// its warp alone, so no two warps touch the same slots and no claim ever
+// has to be undone).  The candidates are copied into shared memory grouped
+// by bucket.  Each warp places its region's buckets in two passes, first
+// the buckets that hold one of the sample's kHotMax most frequent words (the
+// region is then nearly empty, so they always find room), then the rest,
+// each pass largest bucket first.  A bucket of at most 8 keys tries 32
+// displacements at once, one per lane: a lane's displacement qualifies when
+// its keys land on distinct slots that the region's occupancy bitmap shows
+// free, and the lowest qualifying lane takes it.  Larger buckets try one
+// displacement at a time, one key per lane.  A bucket with no displacement in
+// 0..255, or with more than 32 keys, is left out: its words are then counted
+// in the global table, never wrongly, because a lookup always compares the
+// whole key.  Empty slots keep key 0, which no word has.
+constexpr int kChdSmall = 8;
+constexpr int kChdThreads = kHeadRegions * 32;
+constexpr size_t kChdSmem = (size_t)kHeadMax * 8 + (size_t)kHeadBuckets * 4 * 3 + kHeadSlots / 8 + kHeadBuckets +
+                            (size_t)kChdThreads * 4 + 16;
+__device__ __forceinline__ bool slot_used(const uint32_t *used, uint32_t s) { return (used[s >> 5] >> (s & 31u)) & 1u; }
+
+__global__ void __launch_bounds__(kChdThreads) k_head_chd(const unsigned long long *cand, const uint32_t *ccnt,
+                                                          const uint32_t *meta, unsigned long long *image,
+                                                          uint8_t *disp) {
+    extern __shared__ __align__(16) uint8_t chd_smem[];
+    unsigned long long *skey = reinterpret_cast<unsigned long long *>(chd_smem);  // kHeadMax, by bucket
+    uint32_t *bsize = reinterpret_cast<uint32_t *>(skey + kHeadMax);            // low 16 bits size, bit 31 hot
+    uint32_t *bstart = bsize + kHeadBuckets;
+    uint32_t *bfill = bstart + kHeadBuckets;
+    uint32_t *used = bfill + kHeadBuckets;                          // kHeadSlots bits
+    uint32_t *scan = used + kHeadSlots / 32;                        // kChdThreads
+    uint8_t *sdisp = reinterpret_cast<uint8_t *>(scan + kChdThreads);  // kHeadBuckets
+    constexpr uint32_t kHot = 1u << 31, kPer = kHeadBuckets / kChdThreads;
+    const uint32_t t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint32_t n = meta[1] < kHeadMax ? meta[1] : kHeadMax, hot_min = meta[2];
+    for (uint32_t i = t; i < kHeadBuckets; i += kChdThreads) {
+        bsize[i] = 0;
+        bfill[i] = 0;
+        sdisp[i] = 0;
     }
-    for (uint32_t i = threadIdx.x; i < nb * 4; i += blockDim.x) image[i] = 0ull;
-    int tier[kPer];
-    unsigned long long key[kPer];
-#pragma unroll
-    for (int k = 0; k < kPer; k++) {
-        const uint32_t i = threadIdx.x + (uint32_t)k * 1024u;
-        tier[k] = i < n ? 31 - __clz((int)ccnt[i]) : -1;  // counts >= 2: tier >= 1
-        key[k] = i < n ? cand[i] : 0ull;
+    for (uint32_t i = t; i < kHeadSlots / 32; i += kChdThreads) used[i] = 0;
+    __syncthreads();
+    for (uint32_t i = t; i < n; i += kChdThreads) {
+        const uint32_t g = head_bucket(l1_mix(cand[i]));
+        atomicAdd(&bsize[g], 1u);
+        if (ccnt[i] >= hot_min) atomicOr(&bsize[g], kHot);
     }
     __syncthreads();
-    for (int t = 31 - kHeadIdxBits; t >= 1; t--) {
-#pragma unroll
-        for (int k = 0; k < kPer; k++) {
-            if (tier[k] != t) continue;
-            const uint32_t b1 = head_bucket(key[k], kHeadMulA, nb), b2 = head_bucket(key[k], kHeadMulB, nb);
-            const uint32_t first = fill[b1] <= fill[b2] ? b1 : b2, second = first == b1 ? b2 : b1;
-            uint32_t slot = atomicAdd(&fill[first], 1u), bk = first;
-            if (slot >= 4) {
-                slot = atomicAdd(&fill[second], 1u);
-                bk = second;
-            }
-            if (slot < 4) {
-                image[bk * 4 + slot] = key[k];
-                atomicOr(&fps[bk], head_fp(key[k]) << (8 * slot));
-            }
-        }
+    // exclusive prefix of the bucket sizes (kPer buckets a thread)
+    uint32_t own = 0;
+    for (uint32_t j = 0; j < kPer; j++) own += bsize[t * kPer + j] & 0xFFFFu;
+    scan[t] = own;
+    __syncthreads();
+    for (uint32_t w = 1; w < kChdThreads; w <<= 1) {
+        const uint32_t x = t >= w ? scan[t - w] : 0u;
+        __syncthreads();
+        scan[t] += x;
         __syncthreads();
     }
-    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) image_fp[i] = fps[i];
+    uint32_t run = scan[t] - own;
+    for (uint32_t j = 0; j < kPer; j++) {
+        bstart[t * kPer + j] = run;
+        run += bsize[t * kPer + j] & 0xFFFFu;
+    }
+    __syncthreads();
+    for (uint32_t i = t; i < n; i += kChdThreads) {
+        const unsigned long long key = cand[i];
+        const uint32_t g = head_bucket(l1_mix(key));
+        skey[bstart[g] + atomicAdd(&bfill[g], 1u)] = key;
+    }
+    __syncthreads();
+    // ---- warp `warp` places the buckets of region `warp`: g = warp + 16 i
+    uint32_t maxsize = 0;
+    for (uint32_t i = lane; i < kHeadBuckets / kHeadRegions; i += 32)
+        maxsize = max(maxsize, bsize[warp + kHeadRegions * i] & 0xFFFFu);
+    maxsize = __reduce_max_sync(kFull, maxsize);
+    for (int pass = 0; pass < 2; pass++) {
+        for (uint32_t size = maxsize < 32u ? maxsize : 32u; size >= 1; size--) {
+            for (uint32_t i0 = 0; i0 < kHeadBuckets / kHeadRegions; i0 += 32) {
+                const uint32_t gl = warp + kHeadRegions * (i0 + lane);
+                const uint32_t bs = bsize[gl];
+                uint32_t todo = __ballot_sync(kFull, (bs & 0xFFFFu) == size && ((bs & kHot) != 0) == (pass == 0));
+                while (todo) {
+                    const uint32_t g = warp + kHeadRegions * (i0 + (uint32_t)(__ffs(todo) - 1));
+                    todo &= todo - 1;
+                    const unsigned long long *bk = skey + bstart[g];
+                    if (size <= (uint32_t)kChdSmall) {
+                        // every lane holds the bucket's keys and tries displacement dbase + lane
+                        unsigned long long key[kChdSmall], h[kChdSmall];
+#pragma unroll
+                        for (int k = 0; k < kChdSmall; k++) {
+                            key[k] = k < (int)size ? bk[k] : 0ull;
+                            h[k] = l1_mix(key[k]);
+                        }
+                        for (uint32_t dbase = 0; dbase < 256; dbase += 32) {
+                            const uint32_t d = dbase + lane;
+                            uint32_t slot[kChdSmall];
+                            bool ok = true;
+#pragma unroll
+                            for (int k = 0; k < kChdSmall; k++) {
+                                slot[k] = head_slot(h[k], d);
+                                if (k < (int)size) {
+                                    ok = ok && !slot_used(used, slot[k]);
+#pragma unroll
+                                    for (int j = 0; j < k; j++) ok = ok && slot[j] != slot[k];
+                                }
+                            }
+                            const uint32_t win = __ballot_sync(kFull, ok);
+                            if (win) {
+                                if ((int)lane == __ffs(win) - 1) {  // the region is this warp's alone
+#pragma unroll
+                                    for (int k = 0; k < kChdSmall; k++) {
+                                        if (k < (int)size) {
+                                            used[slot[k] >> 5] |= 1u << (slot[k] & 31u);
+                                            image[slot[k]] = key[k];
+                                        }
+                                    }
+                                    sdisp[g] = (uint8_t)d;
+                                }
+                                __syncwarp();
+                                break;
+                            }
+                        }
+                        continue;
+                    }
+                    const bool mine = lane < size;
+                    const unsigned long long key = mine ? bk[lane] : 0ull;
+                    const unsigned long long h = l1_mix(key);
+                    for (uint32_t d = 0; d < 256; d++) {
+                        const uint32_t slot = mine ? head_slot(h, d) : (uint32_t)kHeadSlots + lane;  // dummies never clash
+                        // every lane takes part in the match (never behind a short-circuit)
+                        const uint32_t peers = __match_any_sync(kFull, slot);
+                        const bool ok = (!mine || !slot_used(used, slot)) && peers == (1u << lane);
+                        if (!__all_sync(kFull, ok)) continue;
+                        if (mine) {
+                            atomicOr(&used[slot >> 5], 1u << (slot & 31u));  // lanes may share a bitmap word
+                            image[slot] = key;
+                        }
+                        if (lane == 0) sdisp[g] = (uint8_t)d;
+                        __syncwarp();
+                        break;
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (uint32_t s = t; s < kHeadSlots; s += kChdThreads)
+        if (!slot_used(used, s)) image[s] = 0ull;
+    for (uint32_t i = t; i < kHeadBuckets; i += kChdThreads) disp[i] = sdisp[i];
 }
 
-size_t head_scratch_bytes() {
-    return (size_t)kSampleSlots * sizeof(G8Slot) + 4096 * 4 + 64 + (size_t)kHeadBuckets * 4 * (8 * 2 + 4) +
-           (size_t)kHeadBuckets * 4 + 1024;
-}
+// ---------------------------------------------------------------- launch
+// Head scratch: the sample table, its histogram and metadata, the candidates
+// and the HEAD image (keys, then displacements).
+constexpr size_t kHsSample = (size_t)kSampleSlots * sizeof(G8Slot);
+constexpr size_t kHsHist = 4096 * 4;
+constexpr size_t kHsMeta = 64;
+constexpr size_t kHsCand = (size_t)kHeadSlots * 8;
+constexpr size_t kHsCcnt = (size_t)kHeadSlots * 4;
+constexpr size_t kHsImage = (size_t)kHeadSlots * 8;
+size_t head_scratch_bytes() { return kHsSample + kHsHist + kHsMeta + kHsCand + kHsCcnt + kHsImage + kHeadBuckets + 256; }
 
 static int sm_count_dev() {
     int dev = 0, sms = 0;
@@ -735,9 +837,11 @@ cudaError_t ensure_smem_limit(const void *func, int bytes) {
 }
 
 cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
-    cudaError_t ea = ensure_smem_limit((const void *)k_count2<false>, (int)kCountSmem);
-    if (ea == cudaSuccess) ea = ensure_smem_limit((const void *)k_count2<true>, (int)kCountSmem);
-    if (ea != cudaSuccess) return ea;
+    cudaError_t e = ensure_smem_limit((const void *)k_count3<MODE_HEAD>, (int)kCountSmem);
+    if (e == cudaSuccess) e = ensure_smem_limit((const void *)k_head_chd, (int)kChdSmem);
+    if (e == cudaSuccess) e = ensure_smem_limit((const void *)k_count3<MODE_LOCAL>, (int)kCountSmem);
+    if (e == cudaSuccess) e = ensure_smem_limit((const void *)k_count3<MODE_SAMPLE>, (int)kCountSmem);
+    if (e != cudaSuccess) return e;
     if (c.hi <= c.lo) return cudaSuccess;
     const int sms = sm_count_dev();
     const uintptr_t tb = reinterpret_cast<uintptr_t>(c.text);
@@ -747,59 +851,61 @@ cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
     a.hi = c.hi;
     a.base_al = (tb + c.lo) & ~(uintptr_t)15;
     const unsigned long long span = tb + c.hi - a.base_al;
-    a.nchunks = (uint32_t)((span + kChunk - 1) / kChunk);
-    a.piece_chunks = a.nchunks;
+    a.nstrips = (span + kStrip - 1) / kStrip;
+    a.piece_strips = 0;
     a.piece_stride = 0;
     a.g = c.g;
     a.lbegin = c.text;
     a.head = nullptr;
-    a.head_fp = nullptr;
-    a.nb = kHeadBuckets;
+    a.head_disp = nullptr;
     const uint64_t n = c.hi - c.lo;
-    if (c.head_mode == 1 && c.head_scratch) {  // the head an earlier launch built
-        uint8_t *p = static_cast<uint8_t *>(c.head_scratch);
-        unsigned long long *cand =
-            reinterpret_cast<unsigned long long *>(p + kSampleSlots * sizeof(G8Slot) + 4096 * 4 + 64);
-        unsigned long long *image = cand + kHeadBuckets * 4;
-        a.head = image;
-        a.head_fp = reinterpret_cast<uint32_t *>(image + kHeadBuckets * 4) + kHeadBuckets * 4;
-    } else if (c.head_mode == 0 && n >= kHeadMinBytes && c.head_scratch) {
-        // sampling pass into its own small 8-byte-key table
-        uint8_t *p = static_cast<uint8_t *>(c.head_scratch);
-        G8Slot *sample = reinterpret_cast<G8Slot *>(p);
-        uint32_t *hist = reinterpret_cast<uint32_t *>(p + kSampleSlots * sizeof(G8Slot));
-        uint32_t *meta = hist + 4096;
-        unsigned long long *cand = reinterpret_cast<unsigned long long *>(meta + 16);
-        unsigned long long *image = cand + kHeadBuckets * 4;
-        uint32_t *ccnt = reinterpret_cast<uint32_t *>(image + kHeadBuckets * 4);
-        uint32_t *image_fp = ccnt + kHeadBuckets * 4;
-        cudaMemsetAsync(p, 0, kSampleSlots * sizeof(G8Slot) + 4096 * 4 + 64, s);
+    uint8_t *hs = static_cast<uint8_t *>(c.head_scratch);
+    unsigned long long *image =
+        hs ? reinterpret_cast<unsigned long long *>(hs + kHsSample + kHsHist + kHsMeta + kHsCand + kHsCcnt) : nullptr;
+    uint8_t *image_disp = hs ? reinterpret_cast<uint8_t *>(image + kHeadSlots) : nullptr;
+    bool head = false;
+    if (c.head_mode == 1 && hs) {  // the head an earlier launch built
+        head = true;
+    } else if (c.head_mode == 0 && n >= kHeadMinBytes && hs) {
+        // sampling pass (LOCAL tables per block, spills into the sample table)
+        G8Slot *sample = reinterpret_cast<G8Slot *>(hs);
+        uint32_t *hist = reinterpret_cast<uint32_t *>(hs + kHsSample);
+        uint32_t *meta = reinterpret_cast<uint32_t *>(hs + kHsSample + kHsHist);
+        unsigned long long *cand = reinterpret_cast<unsigned long long *>(hs + kHsSample + kHsHist + kHsMeta);
+        uint32_t *ccnt = reinterpret_cast<uint32_t *>(hs + kHsSample + kHsHist + kHsMeta + kHsCand);
+        e = cudaMemsetAsync(hs, 0, kHsSample + kHsHist + kHsMeta, s);
+        if (e != cudaSuccess) return e;
         Count2Args sa = a;
         sa.g.slots8 = sample;
         sa.g.mask8 = kSampleSlots - 1;
-        const uint32_t pc = kSamplePieceBytes / kChunk;
-        sa.piece_chunks = pc;
+        sa.piece_strips = kSamplePieceBytes / kStrip;
         sa.piece_stride = (span / kSamplePieces) & ~(unsigned long long)15;
-        sa.nchunks = pc * kSamplePieces;
-        int g = (int)std::min<uint32_t>(sa.nchunks, (uint32_t)sms);
-        k_count2<true><<<g, kBlock, kCountSmem, s>>>(sa);
-        const uint32_t kmax = kHeadBuckets * 4 * 88 / 100;
+        sa.nstrips = (unsigned long long)sa.piece_strips * kSamplePieces;
+        k_count3<MODE_SAMPLE><<<sms, kBlock, kCountSmem, s>>>(sa);
         k_head_hist<<<sms, 256, 0, s>>>(sample, kSampleSlots, hist);
-        k_head_threshold<<<1, 1024, 0, s>>>(hist, kmax, meta);
-        k_head_collect<<<sms * 2, 256, 0, s>>>(sample, kSampleSlots, meta, cand, ccnt, kmax);
-        k_head_build<<<1, 1024, 0, s>>>(cand, ccnt, meta, kmax, kHeadBuckets, image, image_fp);
-        a.head = image;
-        a.head_fp = image_fp;
+        k_head_threshold<<<1, 1024, 0, s>>>(hist, kHeadMax, meta);
+        k_head_collect<<<sms * 2, 256, 0, s>>>(sample, kSampleSlots, meta, cand, ccnt, kHeadMax);
+        k_head_chd<<<1, kChdThreads, kChdSmem, s>>>(cand, ccnt, meta, image, image_disp);
+        head = true;
     }
-    int grid = c.grid > 0 ? c.grid : sms;
-    if ((uint32_t)grid > a.nchunks) grid = (int)a.nchunks;
-    for (cudaEvent_t e : c.main_ev)
-        if (e) cudaEventRecord(e, s);
-    k_count2<false><<<grid, kBlock, kCountSmem, s>>>(a);
+    if (head) {
+        a.head = image;
+        a.head_disp = image_disp;
+    }
+    // one persistent block per SM (fewer for short texts); each block's
+    // level-1 counts stay below 2^32 because a block reads under 2^33 bytes
+    unsigned long long grid = c.grid > 0 ? (unsigned long long)c.grid : (unsigned long long)sms;
+    const unsigned long long need = (a.nstrips + kWarps - 1) / kWarps;
+    if (grid > need) grid = need;
+    while ((a.nstrips + grid * kWarps - 1) / (grid * kWarps) * kWarps * kStrip >= (1ull << 33)) grid *= 2;
+    for (cudaEvent_t ev : c.main_ev)
+        if (ev) cudaEventRecord(ev, s);
+    if (head) k_count3<MODE_HEAD><<<(unsigned)grid, kBlock, kCountSmem, s>>>(a);
+    else k_count3<MODE_LOCAL><<<(unsigned)grid, kBlock, kCountSmem, s>>>(a);
     return cudaGetLastError();
 }
 
-int count_global_chunk_bytes() { return kChunk; }
+int count_global_chunk_bytes() { return kStrip; }
 uint64_t count_global_head_min() { return kHeadMinBytes; }
 
 // ---------------------------------------------------------------- wait self-test

@@ -170,14 +170,21 @@ __device__ __forceinline__ uint4 load_run16(const uint8_t *p, long long n) {
 // domain).  It only picks slots (equality is always decided on every byte),
 // so the two ends suffice; every table holding long words uses this one
 // function, from the text or from a table's arena alike.
-__device__ __forceinline__ unsigned long long long_hash(const uint8_t *w, unsigned long long len) {
+__device__ __forceinline__ unsigned long long long_hash_mix(uint4 f, uint4 l, unsigned long long len) {
     if (kOneSlot) return 1ull;  // a claimed slot keeps a non-zero hash word
-    const long long m = len < 16 ? (long long)len : 16;
-    const uint4 f = load_run16(w, m), l = load_run16(w + (len - (unsigned long long)m), m);
     const unsigned long long f0 = ((unsigned long long)f.y << 32) | f.x, f1 = ((unsigned long long)f.w << 32) | f.z;
     const unsigned long long l0 = ((unsigned long long)l.y << 32) | l.x, l1 = ((unsigned long long)l.w << 32) | l.z;
     return fmix64(f0 * 0x9E3779B97F4A7C15ull ^ f1 * 0xC2B2AE3D27D4EB4Full ^ l0 * 0x165667B19E3779F9ull ^
                   l1 * 0xD6E8FEB86659FD93ull ^ len * 0xFF51AFD7ED558CCDull);
+}
+// The first and last 16 lowercased letters of the run w[0, len) (len >= 16).
+__device__ __forceinline__ void long_ends(const uint8_t *w, unsigned long long len, uint4 &f, uint4 &l) {
+    f = load_run16(w, 16);
+    l = load_run16(w + (len - 16ull), 16);
+}
+__device__ __forceinline__ unsigned long long long_hash(const uint8_t *w, unsigned long long len) {
+    const long long m = len < 16 ? (long long)len : 16;
+    return long_hash_mix(load_run16(w, m), load_run16(w + (len - (unsigned long long)m), m), len);
 }
 // Whether the letter runs a[0, len) and b[0, len) are equal (case folded).
 __device__ inline bool runs_equal(const uint8_t *a, const uint8_t *b, unsigned long long len) {
@@ -260,14 +267,35 @@ struct __align__(32) GSlot {
     unsigned long long spare;
 };
 // Global long-word slot: (hash, address of the first occurrence) is the
-// 128-bit CAS target, so a slot is published whole in one atomic step;
-// len is written by the claimer for compaction only.
-struct __align__(32) LSlot {
+// 128-bit CAS target, so a slot is published whole in one atomic step.  The
+// claimer then writes the length and, when it knows them, the word's first
+// and last 16 lowercased letters (f, l) followed by kLongReady in len with a
+// release store: for a word of at most 32 letters (f, l, length) is the
+// whole word, so later inserts that read kLongReady (acquire) compare
+// against the slot instead of reading the first occurrence's bytes.  Length
+// readers mask kLongReady off (long_len).
+constexpr unsigned long long kLongReady = 1ull << 63;
+struct __align__(64) LSlot {
     unsigned long long h;
     unsigned long long addr;
     unsigned long long cnt;
     unsigned long long len;
+    uint4 f, l;
 };
+__device__ __forceinline__ unsigned long long long_len(unsigned long long len_field) { return len_field & ~kLongReady; }
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint4 ld_relaxed_u128(const uint4 *p) {
+    const unsigned long long *q = reinterpret_cast<const unsigned long long *>(p);
+    const unsigned long long a = ld_u64(q), b = ld_u64(q + 1);
+    return make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
+}
 
 // Global 8-byte-key slot (words of at most 8 letters): key, count.
 struct __align__(16) G8Slot {
@@ -300,7 +328,9 @@ __device__ __forceinline__ bool bytes_eq_lower_warp(const uint8_t *a, const uint
 
 // Adds `add` to the long word w[0, len) (a maximal letter run, len >= 17),
 // given its hash h (which includes the length, and the document in batched
-// counting).  `end` bounds the buffer holding w: a word ends at its first
+// counting).  fl (may be null) holds the word's first and last 16 lowercased
+// letters: a claimer publishes them in the slot, and a word of at most 32
+// letters is then matched against a ready slot without reading text.  `end` bounds the buffer holding w: a word ends at its first
 // non-letter or at `end`.  The slot's (hash, address) pair is claimed with one
 // 128-bit CAS; a thread finding the same hash compares the representative's
 // bytes with its own and checks that the representative's run ends after
@@ -312,7 +342,7 @@ __device__ __forceinline__ bool bytes_eq_lower_warp(const uint8_t *a, const uint
 // a representative's terminator.
 __device__ inline void long_insert2(const GTable &g, const uint8_t *w, unsigned long long len,
                                     unsigned long long h, unsigned long long add, const uint8_t *begin,
-                                    const uint8_t *end) {
+                                    const uint8_t *end, const uint4 *fl = nullptr) {
     unsigned long long s = h & g.lmask;
     const unsigned long long wa = (unsigned long long)reinterpret_cast<uintptr_t>(w);
     const uint4 want = make_uint4((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)wa, (uint32_t)(wa >> 32));
@@ -325,9 +355,30 @@ __device__ inline void long_insert2(const GTable &g, const uint8_t *w, unsigned 
         uint4 old = make_uint4((uint32_t)h0, (uint32_t)(h0 >> 32), (uint32_t)a0, (uint32_t)(a0 >> 32));
         if (h0 == 0ull || a0 == 0ull) old = cas128_global(&slot->h, zero, want);
         if (key_zero(old)) {
-            slot->len = len;
+            if (fl) {
+                slot->f = fl[0];
+                slot->l = fl[1];
+                st_release_u64(&slot->len, len | kLongReady);
+            } else {
+                slot->len = len;
+            }
             red_add_u64_dev(&slot->cnt, add);
             return;
+        }
+        if (fl && old.x == want.x && old.y == want.y) {
+            const unsigned long long lr = ld_acquire_u64(&slot->len);
+            if (lr & kLongReady) {
+                const bool ends = long_len(lr) == len && key_eq(ld_relaxed_u128(&slot->f), fl[0]) &&
+                                  key_eq(ld_relaxed_u128(&slot->l), fl[1]);
+                if (ends && len <= 32) {  // the ends and the length are the whole word
+                    red_add_u64_dev(&slot->cnt, add);
+                    return;
+                }
+                if (!ends) {  // another word with the same hash
+                    s = (s + 1) & g.lmask;
+                    continue;
+                }
+            }
         }
         if (old.x == want.x && old.y == want.y) {
             const uint8_t *rep = reinterpret_cast<const uint8_t *>(((unsigned long long)old.w << 32) | old.z);

@@ -15,7 +15,8 @@ struct wc_ctx {
     int device = 0;
     int sms = 1;
     uint64_t budget = 0;
-    std::atomic<uint64_t> used{0};
+    std::atomic<uint64_t> used{0};   // device bytes the context holds (pool allocations not yet released)
+    std::atomic<uint64_t> peak{0};   // the largest `used` since creation or the last wc_mem_usage reset
     int count_bits = 64;
     int autotune = 0;
     std::string tune_cache_path;

@@ -35,6 +35,16 @@ cudaError_t launch_wait_selftest(uint32_t *d_status, uint32_t polls, int arrive,
 int count_global_launches(uint64_t nbytes, bool head);
 size_t head_scratch_bytes();
 
+// ---------------------------------------------------------------- numeric MapReduce
+// Blocks of the series sum for n terms, and its two launches (per-block
+// compensated partial sums into part[nb], then their fixed-order sum).
+int series_blocks(unsigned long long n);
+cudaError_t launch_series(int series, unsigned long long n, double2 *part, int nb, double *d_out, cudaStream_t s);
+
+// Row sums of a row-major uint32 matrix (the hybrid pipeline's reduce).
+cudaError_t launch_row_sums(const uint32_t *m, unsigned long long rows, unsigned long long cols,
+                            unsigned long long *out, cudaStream_t s);
+
 // ---------------------------------------------------------------- tables
 // A compacted, sorted table in device memory.  Entry i: big-endian key
 // halves (first 16 letters), count, and lref (0 = word fits the key, else

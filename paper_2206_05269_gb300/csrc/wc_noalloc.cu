@@ -41,7 +41,7 @@ constexpr uint64_t kBytesLong = round256(kNaCapLong * sizeof(wc::LSlot));
 constexpr uint64_t kSortBytes = kNaEntries * (8 + 8 + 8 + 8 + 4 + 4 + 4 + 4 + 4) + 4 * wc::kSortPassesSeg * 256 +
                                 4 * 256 * ((kNaEntries + 4095) / 4096) + 4 * 32 +
                                 2 * 4 * 256 * wc::sort_group_stride((kNaEntries + 4095) / 4096) + 4096 + 16 * kR;
-constexpr uint64_t kScratchBytes = kBytes8 + kBytes16 + kBytesLong + kSortBytes;  // about 15.2 MB
+constexpr uint64_t kScratchBytes = kBytes8 + kBytes16 + kBytesLong + kSortBytes;  // about 15.5 MB
 
 }  // namespace
 

@@ -131,11 +131,19 @@ __global__ void k_compact8(const G8Slot *slots, unsigned long long cap, SortScra
     }
 }
 
+// Byte i (0..15) of 16 bytes held as a uint4 (little-endian words).
+__device__ __forceinline__ uint32_t byte16(uint4 v, uint32_t i) {
+    const uint32_t w = i < 8u ? (i < 4u ? v.x : v.y) : (i < 12u ? v.z : v.w);
+    return (w >> (8u * (i & 3u))) & 0xFFu;
+}
+
 // One lane per long-word slot: a warp's occupied slots take their entry
 // positions, long-word indices and arena bytes with one atomic each.  Each
 // word is copied (lowercased, followed by one 0 byte so a run in the arena
 // ends where the word ends) into the arena, by its own lane up to 64 bytes
-// and by the whole warp beyond, and emits an entry.
+// and by the whole warp beyond, and emits an entry.  A word of at most 32
+// letters whose slot holds its first and last 16 letters (kLongReady) is
+// written from the slot, without reading its occurrence in the text.
 __global__ void k_compact_long(const LSlot *ls, unsigned long long lcap, SortScratch ss, DevTable out) {
     const int lane = threadIdx.x & 31;
     const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
@@ -143,16 +151,23 @@ __global__ void k_compact_long(const LSlot *ls, unsigned long long lcap, SortScr
     for (unsigned long long w0 = (((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < lcap;
          w0 += nw * 32) {
         const unsigned long long w = w0 + lane;
-        unsigned long long h = 0, addr = 0, len = 0, c = 0;
+        unsigned long long h = 0, addr = 0, len = 0, c = 0, lr = 0;
+        uint4 f = make_uint4(0u, 0u, 0u, 0u), l = f;
         if (w < lcap) {
             h = ls[w].h;
             addr = ls[w].addr;
-            len = ls[w].len;
+            lr = ls[w].len;
+            len = long_len(lr);
             c = ls[w].cnt;
         }
         const bool occ = !(h == 0 && addr == 0);
         const uint32_t m = __ballot_sync(kFull, occ);
         if (!m) continue;
+        const bool from_slot = occ && (lr & kLongReady) && len <= 32;
+        if (from_slot) {
+            f = ls[w].f;
+            l = ls[w].l;
+        }
         const unsigned long long rank = __popc(m & lanemask_lt()), nocc = __popc(m);
         const unsigned long long bytes = occ ? len + 1 : 0ull;
         unsigned long long incl = bytes, tok = occ ? c : 0ull;
@@ -177,7 +192,10 @@ __global__ void k_compact_long(const LSlot *ls, unsigned long long lcap, SortScr
         // reference) so that the sort that follows reads only valid entries.
         const bool full = occ && (off + len + 1 > out.arena_cap || lidx >= out.lcap);
         const uint8_t *src = reinterpret_cast<const uint8_t *>(addr);
-        if (occ && !full && len <= 64)
+        if (from_slot && !full)  // word byte j: f[j] below 16, else l[j - (len - 16)]
+            for (uint32_t j = 0; j < (uint32_t)len; j++)
+                out.arena[off + j] = (uint8_t)(j < 16u ? byte16(f, j) : byte16(l, j + 16u - (uint32_t)len));
+        else if (occ && !full && len <= 64)
             for (unsigned long long j = 0; j < len; j++) out.arena[off + j] = (uint8_t)(src[j] | 0x20u);
         uint32_t big = __ballot_sync(kFull, occ && !full && len > 64);
         while (big) {
@@ -196,8 +214,13 @@ __global__ void k_compact_long(const LSlot *ls, unsigned long long lcap, SortScr
                 out.llen[lidx] = len;
             }
             unsigned long long hi = 0, lo = 0;
-            for (int j = 0; j < 8; j++) hi = (hi << 8) | (unsigned long long)(src[j] | 0x20u);
-            for (int j = 8; j < 16; j++) lo = (lo << 8) | (unsigned long long)(src[j] | 0x20u);
+            if (from_slot) {  // f holds the first 16 letters, lowercased, little-endian words
+                hi = ((unsigned long long)__byte_perm(f.x, 0, 0x0123) << 32) | __byte_perm(f.y, 0, 0x0123);
+                lo = ((unsigned long long)__byte_perm(f.z, 0, 0x0123) << 32) | __byte_perm(f.w, 0, 0x0123);
+            } else {
+                for (int j = 0; j < 8; j++) hi = (hi << 8) | (unsigned long long)(src[j] | 0x20u);
+                for (int j = 8; j < 16; j++) lo = (lo << 8) | (unsigned long long)(src[j] | 0x20u);
+            }
             ss.khi[pos] = hi;
             ss.klo[pos] = lo;
             ss.cnt[pos] = c;

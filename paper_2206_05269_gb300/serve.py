@@ -15,10 +15,14 @@ request's table (32-bit counts, count desc then word asc) is built and kept
 on the device; the answer returned to the host is its top-k (the table's
 first k rows, gathered on the device: wc_topk for a single count,
 wc_batch_topk for a round), and the whole table too when keep_tables is set.
-The context's device-memory budget bounds admission: work the budget cannot
-hold waits for running work to finish.  A round whose device tables overflow
-is recounted request by request with growing capacities, so answers are
-always exact.
+The context's device-memory budget bounds admission: each unit's request text
+is allocated from the context's budgeted pool (wc_buffer_alloc) like the
+library's own tables and scratch, so a unit whose text or tables the budget
+cannot hold waits for running work to finish and free its memory (a round
+refused with nothing running is cut to fewer requests; a single request
+larger than the whole budget is an error).  A round whose device tables
+overflow is recounted request by request with growing capacities, so answers
+are always exact.
 
 `serve_fifo` is the plain path for comparison: one request at a time, in
 arrival order, one wc_count launch per request.
@@ -65,10 +69,11 @@ class Answer:
 class _Work:
     """One unit on the GPU: a round of small requests or one large request."""
 
-    def __init__(self, reqs, stream, keep, batch=None, table=None, h_offs=None):
+    def __init__(self, reqs, stream, buf, keep=None, batch=None, table=None, h_offs=None):
         import torch
         self.reqs = reqs
         self.stream = stream
+        self.buf = buf            # the unit's request text (budgeted device buffer)
         self.keep = keep          # device tensors that must outlive the work
         self.batch = batch
         self.table = table
@@ -85,17 +90,19 @@ def _wait_until(t_target: float, t0: float):
         time.sleep(min(dt, 0.0005) if dt > 0.0002 else 0)
 
 
-def _to_device(reqs, dev, stream):
+def _to_device(counter, reqs, stream):
+    """The requests' text copied into one budgeted device buffer (raises
+    WcError with WC_ERR_BUDGET, allocating nothing, when it does not fit)."""
     import torch
     h_offs = np.zeros(len(reqs) + 1, dtype=np.uint64)
     h_offs[1:] = np.cumsum([r.data.numel() for r in reqs])
     n = int(h_offs[-1])
+    buf = counter.buffer(max(16, n), stream)
     with torch.cuda.stream(stream):
-        text = torch.empty(max(16, n), dtype=torch.uint8, device=dev)
         for j, r in enumerate(reqs):
             if r.data.numel():
-                text[int(h_offs[j]):int(h_offs[j + 1])].copy_(r.data, non_blocking=True)
-    return text, h_offs
+                buf.tensor[int(h_offs[j]):int(h_offs[j + 1])].copy_(r.data, non_blocking=True)
+    return buf, h_offs
 
 
 def serve_batched(counter: wc.Counter, requests: list[Request], topk: int = 100, max_inflight: int = 6,
@@ -113,7 +120,7 @@ def serve_batched(counter: wc.Counter, requests: list[Request], topk: int = 100,
     order = sorted(requests, key=lambda r: r.arrival)
     nxt = 0
     t0 = time.perf_counter()
-    stats = {"rounds": 0, "large": 0, "recounted": 0, "capacity_errors": []}
+    stats = {"rounds": 0, "large": 0, "recounted": 0, "capacity_errors": [], "budget_waits": 0}
 
     def answer(rq, w, o, c, s0, n, full):
         now = time.perf_counter() - t0
@@ -123,26 +130,47 @@ def serve_batched(counter: wc.Counter, requests: list[Request], topk: int = 100,
 
     def answer_table(rq, t, stream):  # one request's device table -> its answer
         if keep_tables:
-            w, o, c = t.export(stream)
+            w, o, c = with_budget(lambda: t.export(stream))
             answer(rq, w, o, c, 0, c.size, True)
         else:
-            top = counter.topk(t, topk, stream)
-            w, o, c = top.export(stream)
+            top = with_budget(lambda: counter.topk(t, topk, stream))
+            w, o, c = with_budget(lambda: top.export(stream))
             top.free()
             answer(rq, w, o, c, 0, c.size, False)
 
     def recount(rq, stream):  # exact fallback with growing capacities
+        while True:
+            try:
+                buf, _ = _to_device(counter, [rq], stream)
+                break
+            except wc.WcError as e:
+                if e.status != wc.WC_ERR_BUDGET or not running:
+                    raise
+                finish(running.popleft())  # free budget held by older work
         with torch.cuda.stream(stream):
-            text = torch.empty(max(16, rq.data.numel()), dtype=torch.uint8, device=dev)[:rq.data.numel()]
-            if rq.data.numel():
-                text.copy_(rq.data, non_blocking=True)
-            t = counter.count_checked(text, stream=stream)
+            t = counter.count_checked(buf.tensor[:rq.data.numel()], stream=stream)
             answer_table(rq, t, stream)
             t.free()
+        buf.free(stream)
         stats["recounted"] += 1
+
+    def with_budget(fn):
+        """Runs fn(); when the budget refuses one of its allocations (a
+        finished unit's top-k table or export scratch), the other running
+        units are finished first to free their memory, then fn runs again."""
+        while True:
+            try:
+                return fn()
+            except wc.WcError as e:
+                if e.status != wc.WC_ERR_BUDGET or not running:
+                    raise
+                finish(running.popleft())
 
     def finish(wk: _Work):
         wk.event.synchronize()
+        if wk.buf is not None:  # the counts have read the text: its budget is free again
+            wk.buf.free(wk.stream)
+            wk.buf = None
         if wk.table is not None:
             st = wk.table.status()
             if st == wc.WC_ERR_CAPACITY:
@@ -162,48 +190,57 @@ def serve_batched(counter: wc.Counter, requests: list[Request], topk: int = 100,
             elif st != wc.WC_OK:
                 raise wc.WcError(st, wc.wc_last_error(counter.ctx))
             elif keep_tables:
-                ds, dn, w, o, c = wk.batch.export(wk.stream)
+                ds, dn, w, o, c = with_budget(lambda: wk.batch.export(wk.stream))
                 for j, rq in enumerate(wk.reqs):
                     answer(rq, w, o, c, int(ds[j]), int(dn[j]), True)
             else:  # every request's top-k gathered on the device, one small copy
-                top, first, n = wk.batch.topk(topk)
-                w, o, c = top.export(wk.stream)
+                top, first, n = with_budget(lambda: wk.batch.topk(topk))
+                w, o, c = with_budget(lambda: top.export(wk.stream))
                 for j, rq in enumerate(wk.reqs):
                     answer(rq, w, o, c, int(first[j]), int(n[j]), False)
             del wk.batch
         free_streams.append(wk.stream)
 
+    round_limit = [round_bytes]  # cut while a round is refused with nothing running
+
     def launch(stream):
         """Starts the next unit on `stream`; False if the budget refused it."""
         if big and (not small or big[0].arrival <= small[0].arrival):
             rq = big.popleft()
-            text, _ = _to_device([rq], dev, stream)
+            buf = None
             try:
-                tab = counter.count(text[:rq.data.numel()], stream=stream)
+                buf, _ = _to_device(counter, [rq], stream)
+                tab = counter.count(buf.tensor[:rq.data.numel()], stream=stream)
             except wc.WcError as e:
+                if buf is not None:
+                    buf.free(stream)
                 big.appendleft(rq)
                 if e.status != wc.WC_ERR_BUDGET:
                     raise
                 return False
-            running.append(_Work([rq], stream, text, table=tab))
+            running.append(_Work([rq], stream, buf, table=tab))
             stats["large"] += 1
             return True
         take, nbytes = [], 0
-        while small and (not take or nbytes + small[0].data.numel() <= round_bytes):
+        while small and (not take or nbytes + small[0].data.numel() <= round_limit[0]):
             r = small.popleft()
             take.append(r)
             nbytes += r.data.numel()
-        text, h_offs = _to_device(take, dev, stream)
+        buf = None
         try:
-            offs = torch.from_numpy(h_offs.view(np.int64)).to(dev)
-            batch = counter.count_batched(text, offs, h_offs, stream=stream)
+            buf, h_offs = _to_device(counter, take, stream)
+            with torch.cuda.stream(stream):
+                offs = torch.from_numpy(h_offs.view(np.int64)).to(dev, non_blocking=True)
+            batch = counter.count_batched(buf.tensor[:max(16, nbytes)], offs, h_offs, stream=stream)
         except wc.WcError as e:
+            if buf is not None:
+                buf.free(stream)
             for r in reversed(take):
                 small.appendleft(r)
             if e.status != wc.WC_ERR_BUDGET:
                 raise
             return False
-        running.append(_Work(take, stream, (text, offs), batch=batch, h_offs=h_offs))
+        running.append(_Work(take, stream, buf, keep=offs, batch=batch, h_offs=h_offs))
         stats["rounds"] += 1
         return True
 
@@ -221,9 +258,14 @@ def serve_batched(counter: wc.Counter, requests: list[Request], topk: int = 100,
             stream = free_streams.popleft()
             if launch(stream):
                 continue
+            stats["budget_waits"] += 1
             free_streams.appendleft(stream)  # budget: wait for running work
             if running:
                 finish(running.popleft())
+            elif small and round_limit[0] > 1:
+                round_limit[0] //= 2  # nothing else holds memory: admit a smaller round
+            else:
+                raise wc.WcError(wc.WC_ERR_BUDGET, "a request larger than the whole device-memory budget")
             continue
         if progressed:
             continue

@@ -41,7 +41,8 @@ EXPORTS = [
     "wc_batch_table", "wc_batch_topk", "wc_batch_size", "wc_batch_export",
     "wc_class_ratio_topk", "wc_merge", "wc_topk", "wc_table_status", "wc_table_size",
     "wc_table_export", "wc_table_count_bits", "wc_table_free", "wc_batch_free", "wc_plan_create", "wc_plan_run",
-    "wc_plan_free", "wc_count_noalloc", "wc_profile_enable",
+    "wc_plan_free", "wc_count_noalloc", "wc_buffer_alloc", "wc_buffer_free", "wc_mem_usage",
+    "wc_series_sum", "wc_batch_vocab", "wc_batch_export_ids", "wc_row_sums", "wc_profile_enable",
     "wc_profile_read", "wc_read_ceiling", "wc_selftest_wait", "wc_status_str", "wc_last_error",
 ]
 
@@ -103,6 +104,13 @@ def load() -> ctypes.CDLL:
         "wc_plan_run": (i32, [vp, vp, vp, vp, vp, pvp]),
         "wc_plan_free": (None, [vp]),
         "wc_count_noalloc": (i32, [vp, u64, vp, vp, vp, vp, u64, vp, vp, u64, vp, u64, vp, vp]),
+        "wc_series_sum": (i32, [vp, i32, u64, vp, vp]),
+        "wc_batch_vocab": (i32, [vp, pvp]),
+        "wc_row_sums": (i32, [vp, u64, u64, vp, vp]),
+        "wc_batch_export_ids": (i32, [vp, vp, vp, vp, vp, vp]),
+        "wc_buffer_alloc": (i32, [vp, u64, vp, pvp]),
+        "wc_buffer_free": (i32, [vp, vp, u64, vp]),
+        "wc_mem_usage": (i32, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), i32]),
         "wc_profile_enable": (i32, [vp, i32]),
         "wc_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64), ctypes.POINTER(u64)]),
@@ -316,6 +324,38 @@ def wc_count_noalloc(d_text: int, nbytes: int, d_khi: int, d_klo: int, d_cnt: in
                                    d_arena, arena_cap, d_meta, stream), None, "wc_count_noalloc")
 
 
+WC_SERIES_SQRT, WC_SERIES_ALT_HARMONIC = 0, 1
+
+
+def wc_series_sum(ctx, series: int, n: int, d_out: int, stream: int) -> None:
+    """Sec. 4.2's numeric MapReduce into one device double (asynchronous)."""
+    _check(load().wc_series_sum(ctx, series, n, d_out, stream), ctx, "wc_series_sum")
+
+
+def wc_row_sums(d_matrix: int, rows: int, cols: int, d_sums: int, stream: int) -> None:
+    """Row sums of a device uint32 matrix into device uint64 (the hybrid pipeline's reduce)."""
+    _check(load().wc_row_sums(d_matrix, rows, cols, d_sums, stream), None, "wc_row_sums")
+
+
+def wc_buffer_alloc(ctx, nbytes: int, stream: int) -> int:
+    """Device buffer from the context's budgeted pool (raises WcError with
+    WC_ERR_BUDGET when the budget cannot hold it); returns the pointer."""
+    out = ctypes.c_void_p()
+    _check(load().wc_buffer_alloc(ctx, nbytes, stream, ctypes.byref(out)), ctx, "wc_buffer_alloc")
+    return int(out.value)
+
+
+def wc_buffer_free(ctx, ptr: int, nbytes: int, stream: int) -> None:
+    _check(load().wc_buffer_free(ctx, ptr, nbytes, stream), ctx, "wc_buffer_free")
+
+
+def wc_mem_usage(ctx, reset: bool = False) -> tuple[int, int]:
+    """(bytes the context holds now, peak since creation or the last reset)"""
+    u, p = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().wc_mem_usage(ctx, ctypes.byref(u), ctypes.byref(p), int(reset)), ctx, "wc_mem_usage")
+    return u.value, p.value
+
+
 def wc_profile_enable(ctx, enable: bool) -> None:
     _check(load().wc_profile_enable(ctx, int(enable)), ctx, "wc_profile_enable")
 
@@ -438,6 +478,34 @@ class Batch:
                None, "wc_batch_export")
         return n, nb
 
+    def vocab(self) -> Table:
+        """The batch's distinct words in word order with global counts
+        (borrowed from the batch); a word's id is its row."""
+        out = ctypes.c_void_p()
+        _check(load().wc_batch_vocab(self.handle, ctypes.byref(out)), None, "wc_batch_vocab")
+        return Table(out, owned=False, owner=self)
+
+    def export_ids(self, stream=None):
+        """(doc_start uint64[ndocs], doc_n uint32[ndocs], ids uint32[n], counts uint32[n])."""
+        n, _ = wc_batch_size(self.handle)
+        ds = np.zeros(max(1, self.ndocs), dtype=np.uint64)
+        dn = np.zeros(max(1, self.ndocs), dtype=np.uint32)
+        ids = np.zeros(max(1, n), dtype=np.uint32)
+        counts = np.zeros(max(1, n), dtype=np.uint32)
+        _check(load().wc_batch_export_ids(self.handle, ds.ctypes.data, dn.ctypes.data, ids.ctypes.data,
+                                          counts.ctypes.data, _stream_handle(stream)), None, "wc_batch_export_ids")
+        return ds[:self.ndocs], dn[:self.ndocs], ids[:n], counts[:n]
+
+    def export_ids_into(self, doc_start, doc_n, ids, counts, stream=None) -> int:
+        """export_ids into caller-owned host tensors (int64 doc_start, int32
+        doc_n, ids and counts; pinned ones copy fastest); returns the rows."""
+        n, _ = wc_batch_size(self.handle)
+        if doc_start.numel() < self.ndocs or doc_n.numel() < self.ndocs or ids.numel() < n or counts.numel() < n:
+            raise ValueError("export buffers smaller than the batch")
+        _check(load().wc_batch_export_ids(self.handle, doc_start.data_ptr(), doc_n.data_ptr(), ids.data_ptr(),
+                                          counts.data_ptr(), _stream_handle(stream)), None, "wc_batch_export_ids")
+        return n
+
     def doc_lists(self):
         """Per-document [(word, count)] lists from one bulk export."""
         ds, dn, w, o, c = self.export()
@@ -463,6 +531,28 @@ class Batch:
         with each document's first row and row count."""
         h, first, n = wc_batch_topk(self.handle, self.ndocs, k)
         return Table(h, owned=False, owner=self), first, n
+
+
+class DeviceBuffer:
+    """A device buffer from a context's budgeted pool (wc_buffer_alloc), seen
+    from torch as a uint8 tensor without a copy; free() returns it in stream
+    order."""
+
+    def __init__(self, counter, nbytes: int, stream=None):
+        import torch
+        self.counter = counter
+        self.nbytes = max(1, int(nbytes))
+        self.ptr = wc_buffer_alloc(counter.ctx, self.nbytes, _stream_handle(stream))
+        self.__cuda_array_interface__ = {"shape": (self.nbytes,), "typestr": "|u1", "data": (self.ptr, False),
+                                         "version": 3}
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.tensor = torch.as_tensor(self, device=dev)
+
+    def free(self, stream=None):
+        if getattr(self, "ptr", None) and self.counter.ctx:
+            wc_buffer_free(self.counter.ctx, self.ptr, self.nbytes, _stream_handle(stream))
+        self.ptr = None
+        self.tensor = None
 
 
 class Counter:
@@ -563,6 +653,13 @@ class Counter:
             st = b.status()
         _check(st, self.ctx, "count_batched")
         return b
+
+    def buffer(self, nbytes: int, stream=None) -> DeviceBuffer:
+        """Device memory charged against this context's budget."""
+        return DeviceBuffer(self, nbytes, stream)
+
+    def mem_usage(self, reset: bool = False) -> tuple[int, int]:
+        return wc_mem_usage(self.ctx, reset)
 
     def plan(self, h_offsets, nclasses: int = 0, stream=None) -> "Plan":
         return Plan(self, h_offsets, nclasses, stream)

@@ -244,3 +244,36 @@ def test_class_tables_many_distinct_words(ctr):
     assert_same(b.table(wc.WC_TABLE_GLOBAL).export(), r.glob(), "global")
     for k in range(c.nclasses):
         assert_same(b.table(wc.WC_TABLE_CLASS, k).export(), r.cls(k), f"class {k}")
+
+
+def test_vocabulary_ids_decode_to_the_oracle():
+    """Vocabulary-id export: the vocabulary is the global word set in word
+    order with global counts, and every document's (id, count) rows decode to
+    the oracle's table of that document, row for row."""
+    import torch
+    from paper_2206_05269_gb300 import wc
+    ctr = wc.Counter(0, count_bits=32)
+    c = corpus.generate("batched", ndocs=600)
+    docs_extra = [b"", b"x" * 40 + b" Y" * 3, b"-".join([b"abcdefghijklmnopq%c" % (97 + i % 26) for i in range(60)])]
+    text = np.concatenate([c.text, np.frombuffer(b"".join(docs_extra), np.uint8)])
+    offs = np.concatenate([c.offsets, c.offsets[-1] + np.cumsum([len(d) for d in docs_extra])]).astype(np.uint64)
+    b, keep = run_batched(ctr, text, offs, checked=True)
+    r = oracle.count(text, offs)
+    v = b.vocab()
+    vw, vo, vc = v.export()
+    vocab = [vw[vo[i]:vo[i + 1]].tobytes() for i in range(vc.size)]
+    gd = r.glob().as_dict()
+    assert vocab == sorted(gd), "vocabulary: the global words in word order"
+    assert [int(x) for x in vc] == [gd[w] for w in vocab], "vocabulary counts"
+    ds, dn, ids, counts = b.export_ids()
+    ndocs = offs.size - 1
+    for d in range(ndocs):
+        s0, n = int(ds[d]), int(dn[d])
+        got = [(vocab[int(i)], int(k)) for i, k in zip(ids[s0:s0 + n], counts[s0:s0 + n])]
+        assert got == r.doc(d).as_list(), f"doc {d}"
+    # the same rows as the word export, in the same order
+    _, _, w, o, cw = b.export()
+    assert np.array_equal(cw, counts)
+    assert all(vocab[int(ids[j])] == w[o[j]:o[j + 1]].tobytes() for j in range(0, ids.size, 97))
+    b.free()
+    ctr.close()

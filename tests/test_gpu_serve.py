@@ -62,3 +62,35 @@ def test_fifo_path_matches(ctr):
     for x, y, tx, ty in zip(a1, a2, t1, t2):
         assert x.as_list() == y.as_list()
         assert tx.as_list() == ty.as_list() == x.as_list()[:100]
+
+
+def test_admission_waits_under_a_tight_budget():
+    """Request text is charged to the context's budget with the tables: with
+    requests of about 250 KB arriving together, each counted as a unit of its
+    own on one of six streams, and a budget of two and a half units, units
+    wait for admission instead of failing, the context never holds more than
+    its budget, and every answer is still the oracle's."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_05269_gb300 import serve, wc
+    pool, trip, reqs = make_requests(n_rate=4000.0, dur=0.015, lo=200 << 10, hi=300 << 10, seed=21)
+    assert len(reqs) >= 30
+    reqs = [serve.Request(r.rid, 0.0, r.data) for r in reqs]  # all waiting at the start
+    kw = dict(topk=100, big_bytes=128 << 10, keep_tables=True)
+    # one unit's footprint: the largest, counting one unit at a time
+    solo = wc.Counter(0, count_bits=32, budget=8 << 30)
+    solo.mem_usage(reset=True)
+    serve.serve_batched(solo, reqs, max_inflight=1, **kw)
+    unit = solo.mem_usage()[1]
+    solo.close()
+    budget = int(unit * 2.5)
+    tight = wc.Counter(0, count_bits=32, budget=budget)
+    answers, stats = serve.serve_batched(tight, reqs, max_inflight=6, **kw)
+    used, peak = tight.mem_usage()
+    tight.close()
+    assert stats["large"] == len(reqs)
+    assert stats["budget_waits"] > 0, "six streams under a budget of two and a half units must wait"
+    assert peak <= budget, f"peak {peak} over the budget {budget}"
+    for (a, s, e), ans in zip(trip, answers):
+        assert ans.full and ans.as_list() == oracle.count(pool[s:e]).glob().as_list(), f"request {ans.rid}"
