@@ -57,7 +57,9 @@ typedef enum {
 
 typedef struct {
     int device;                 /* CUDA device ordinal */
-    uint64_t mem_budget_bytes;  /* 0 = no budget */
+    uint64_t mem_budget_bytes;  /* 0 = no budget; device memory the context may hold at once: its
+                                   tables, scratch and wc_buffer_alloc buffers, each charged from
+                                   its allocation until its stream-ordered free has executed */
     int count_bits;             /* width of global/class counts: 32 or 64 (per-document counts are 32) */
     int autotune;               /* 1 = pick batched-kernel shapes by timing, cached per size class */
     const char *tune_cache_path;/* JSON cache for the autotuner; NULL = in-memory only */
@@ -336,7 +338,8 @@ wc_status wc_row_sums(const uint32_t *d_matrix, uint64_t rows, uint64_t cols, ui
  *     for the context's other work to be freed and try again); WC_ERR_OOM.
  *   wc_buffer_free: returns a buffer (same context, pointer and byte count)
  *     in stream order on `stream`: work enqueued on `stream` before the call
- *     may still read it; a NULL pointer is a no-op.
+ *     may still read it, so its bytes stay charged to the budget until the
+ *     stream has passed the free; a NULL pointer is a no-op.
  *   wc_mem_usage: the bytes the context holds now (tables, scratch and these
  *     buffers not yet freed) and the largest such figure since creation or
  *     the last reset; reset != 0 restarts the peak from the current use.

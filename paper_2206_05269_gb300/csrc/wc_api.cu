@@ -67,11 +67,39 @@ wc_status wc_ctx::alloc(void **p, size_t bytes, cudaStream_t s) {
     }
     return WC_OK;
 }
+namespace {
+struct ReleaseArg {
+    wc_ctx *ctx;
+    size_t bytes;
+};
+void CUDART_CB release_done(void *a) {  // runs once the stream has passed the free
+    ReleaseArg *r = static_cast<ReleaseArg *>(a);
+    r->ctx->used -= r->bytes;
+    delete r;
+}
+}  // namespace
+
+// Stream-ordered free: the bytes stay charged to the budget until the stream
+// has passed the free (a host callback after it), because work enqueued
+// before it may still use them.  While the stream is being captured into a
+// graph the charge is dropped at once (the graph's own allocation and free
+// nodes balance on every replay).
 void wc_ctx::release(void *p, size_t bytes, cudaStream_t s) {
     if (!p) return;
     if (bytes == 0) bytes = 256;
     bytes = (bytes + 255) & ~(size_t)255;
     cudaFreeAsync(p, s);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        cap = cudaStreamCaptureStatusActive;  // unknown: do not defer
+    }
+    if (cap == cudaStreamCaptureStatusNone) {
+        ReleaseArg *r = new ReleaseArg{this, bytes};
+        if (cudaLaunchHostFunc(s, release_done, r) == cudaSuccess) return;
+        cudaGetLastError();
+        delete r;
+    }
     used -= bytes;
 }
 

@@ -823,9 +823,7 @@ cudaError_t launch_segmented_finish(const BatchArgs &a, const GTable &g, uint64_
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaMemsetAsync(smeta, 0, 16 * 8, s);
-    cudaMemsetAsync(ss.hist_all, 0, 4 * kSortPassesSeg * 256, s);
-    cudaMemsetAsync(ss.cur, 0, 4 * 32, s);
-    cudaMemsetAsync(ss.group_hist[0], 0, 2 * 4 * 256 * (size_t)ss.group_stride, s);
+    sort_state_reset(ss, s);
     k_bcompact8<<<gridn(cap8, 256 * kScanUnroll, sms * 8), 256, 0, s>>>(g.slots8, cap8, ss, smeta);
     k_bcompact16<<<gridn(cap16, 256 * kScanUnroll, sms * 8), 256, 0, s>>>(g.slots, cap16, ss, smeta);
     k_bcompact_long<<<gridn(caplong, 256, sms * 8), 256, 0, s>>>(g.lslots, caplong, ss, a, smeta);

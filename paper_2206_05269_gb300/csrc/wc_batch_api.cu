@@ -1316,6 +1316,7 @@ static wc_status build_vocab(wc_batch *b) {
     const GTable vg = cs.gtable(V->dt.d_status);
     const int grid = std::max(1, std::min(ctx->sms * 8, (int)((std::max<uint64_t>(n, b->entries) + 255) / 256)));
     cudaStreamWaitEvent(s, G->done, 0);
+    sort_state_reset(cs.ss, s);
     k_vocab_prep<<<grid, 256, 0, s>>>(G->dt, cs.ss, smeta);
     const LongView lv{G->dt.lref, G->dt.loff, G->dt.llen, G->dt.arena};
     cudaError_t e = cudaGetLastError();

@@ -648,145 +648,165 @@ __global__ void k_head_collect(const G8Slot *s, unsigned long long cap, uint32_t
     }
 }
 
-// Places the head candidates into the HEAD image by hash and displace (one
-// block, one warp per region of 512 slots; a region's buckets are placed by
-// its warp alone, so no two warps touch the same slots and no claim ever
-// has to be undone).  The candidates are copied into shared memory grouped
-// by bucket.  Each warp places its region's buckets in two passes, first
-// the buckets that hold one of the sample's kHotMax most frequent words (the
-// region is then nearly empty, so they always find room), then the rest,
-// each pass largest bucket first.  A bucket of at most 8 keys tries 32
-// displacements at once, one per lane: a lane's displacement qualifies when
-// its keys land on distinct slots that the region's occupancy bitmap shows
-// free, and the lowest qualifying lane takes it.  Larger buckets try one
-// displacement at a time, one key per lane.  A bucket with no displacement in
-// 0..255, or with more than 32 keys, is left out: its words are then counted
-// in the global table, never wrongly, because a lookup always compares the
-// whole key.  Empty slots keep key 0, which no word has.
-constexpr int kChdSmall = 8;
-constexpr int kChdThreads = kHeadRegions * 32;
-constexpr size_t kChdSmem = (size_t)kHeadMax * 8 + (size_t)kHeadBuckets * 4 * 3 + kHeadSlots / 8 + kHeadBuckets +
-                            (size_t)kChdThreads * 4 + 16;
-__device__ __forceinline__ bool slot_used(const uint32_t *used, uint32_t s) { return (used[s >> 5] >> (s & 31u)) & 1u; }
+// Places the head candidates into the HEAD image by hash and displace.  The
+// image's regions of 512 slots are independent (a key's region is fixed by
+// its bucket), so block r builds region r alone: its eight warps pick out
+// the candidates whose bucket lies in the region and group them by bucket,
+// and its first warp places the buckets in two passes, first those holding one of the sample's
+// kHotMax most frequent words (the region is then nearly empty, so they
+// always find room), then the rest, each pass largest bucket first.  A bucket
+// of at most 8 keys tries 32 displacements at once, one per lane: a lane's
+// displacement qualifies when its keys land on distinct slots that the
+// region's occupancy bitmap shows free, and the lowest qualifying lane takes
+// it.  Larger buckets try one displacement at a time, one key per lane.  A
+// bucket with no displacement in 0..255, or with more than 32 keys, is left
+// out (as are candidates beyond the region's 512 slots): their words are then
+// counted in the global table, never wrongly, because a lookup always
+// compares the whole key.  Empty slots keep key 0, which no word has.
+constexpr int kRegionBuckets = kHeadBuckets / kHeadRegions;  // 128
+static_assert(kRegionBuckets == 128, "four buckets a lane");
 
+template <int S>
+__device__ __forceinline__ bool chd_place_small(const unsigned long long *bk, uint32_t *used, unsigned long long *rimage,
+                                                uint8_t *disp, uint32_t lane) {
+    unsigned long long key[S], h[S];
+#pragma unroll
+    for (int i = 0; i < S; i++) {
+        key[i] = bk[i];
+        h[i] = l1_mix(key[i]);
+    }
+    for (uint32_t dbase = 0; dbase < 256; dbase += 32) {
+        const uint32_t d = dbase + lane;
+        uint32_t slot[S];
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < S; i++) {
+            slot[i] = head_slot(h[i], d) & (uint32_t)(kRegionSlots - 1);
+            ok = ok && !((used[slot[i] >> 5] >> (slot[i] & 31u)) & 1u);
+#pragma unroll
+            for (int j = 0; j < i; j++) ok = ok && slot[j] != slot[i];
+        }
+        const uint32_t win = __ballot_sync(kFull, ok);
+        if (win) {
+            if ((int)lane == __ffs(win) - 1) {  // the region is this warp's alone
+#pragma unroll
+                for (int i = 0; i < S; i++) {
+                    used[slot[i] >> 5] |= 1u << (slot[i] & 31u);
+                    rimage[slot[i]] = key[i];
+                }
+                *disp = (uint8_t)d;
+            }
+            __syncwarp();
+            return true;
+        }
+    }
+    return false;
+}
+
+constexpr int kChdThreads = 256;
 __global__ void __launch_bounds__(kChdThreads) k_head_chd(const unsigned long long *cand, const uint32_t *ccnt,
                                                           const uint32_t *meta, unsigned long long *image,
                                                           uint8_t *disp) {
-    extern __shared__ __align__(16) uint8_t chd_smem[];
-    unsigned long long *skey = reinterpret_cast<unsigned long long *>(chd_smem);  // kHeadMax, by bucket
-    uint32_t *bsize = reinterpret_cast<uint32_t *>(skey + kHeadMax);            // low 16 bits size, bit 31 hot
-    uint32_t *bstart = bsize + kHeadBuckets;
-    uint32_t *bfill = bstart + kHeadBuckets;
-    uint32_t *used = bfill + kHeadBuckets;                          // kHeadSlots bits
-    uint32_t *scan = used + kHeadSlots / 32;                        // kChdThreads
-    uint8_t *sdisp = reinterpret_cast<uint8_t *>(scan + kChdThreads);  // kHeadBuckets
-    constexpr uint32_t kHot = 1u << 31, kPer = kHeadBuckets / kChdThreads;
-    const uint32_t t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    __shared__ unsigned long long sel[kRegionSlots], rkey[kRegionSlots], rimage[kRegionSlots];
+    __shared__ uint32_t selb[kRegionSlots];  // local bucket, bit 31: hot
+    __shared__ uint32_t bsize[kRegionBuckets], bstart[kRegionBuckets], bfill[kRegionBuckets];
+    __shared__ uint32_t used[kRegionSlots / 32];
+    __shared__ uint8_t sdisp[kRegionBuckets];
+    __shared__ uint32_t nsel_sh;
+    constexpr uint32_t kHot = 1u << 31;
+    const uint32_t r = blockIdx.x, t = threadIdx.x, lane = t & 31;
     const uint32_t n = meta[1] < kHeadMax ? meta[1] : kHeadMax, hot_min = meta[2];
-    for (uint32_t i = t; i < kHeadBuckets; i += kChdThreads) {
+    for (uint32_t i = t; i < kRegionBuckets; i += kChdThreads) {
         bsize[i] = 0;
         bfill[i] = 0;
         sdisp[i] = 0;
     }
-    for (uint32_t i = t; i < kHeadSlots / 32; i += kChdThreads) used[i] = 0;
+    for (uint32_t i = t; i < kRegionSlots; i += kChdThreads) rimage[i] = 0ull;
+    if (t < kRegionSlots / 32) used[t] = 0;
+    if (t == 0) nsel_sh = 0;
     __syncthreads();
-    for (uint32_t i = t; i < n; i += kChdThreads) {
-        const uint32_t g = head_bucket(l1_mix(cand[i]));
-        atomicAdd(&bsize[g], 1u);
-        if (ccnt[i] >= hot_min) atomicOr(&bsize[g], kHot);
-    }
-    __syncthreads();
-    // exclusive prefix of the bucket sizes (kPer buckets a thread)
-    uint32_t own = 0;
-    for (uint32_t j = 0; j < kPer; j++) own += bsize[t * kPer + j] & 0xFFFFu;
-    scan[t] = own;
-    __syncthreads();
-    for (uint32_t w = 1; w < kChdThreads; w <<= 1) {
-        const uint32_t x = t >= w ? scan[t - w] : 0u;
-        __syncthreads();
-        scan[t] += x;
-        __syncthreads();
-    }
-    uint32_t run = scan[t] - own;
-    for (uint32_t j = 0; j < kPer; j++) {
-        bstart[t * kPer + j] = run;
-        run += bsize[t * kPer + j] & 0xFFFFu;
-    }
-    __syncthreads();
+    // ---- this region's candidates (in any order), every thread a share
     for (uint32_t i = t; i < n; i += kChdThreads) {
         const unsigned long long key = cand[i];
         const uint32_t g = head_bucket(l1_mix(key));
-        skey[bstart[g] + atomicAdd(&bfill[g], 1u)] = key;
+        if ((g & (uint32_t)(kHeadRegions - 1)) == r) {
+            const uint32_t pos = atomicAdd(&nsel_sh, 1u);
+            if (pos < (uint32_t)kRegionSlots) {
+                sel[pos] = key;
+                selb[pos] = (g / kHeadRegions) | (ccnt[i] >= hot_min ? kHot : 0u);
+            }
+        }
     }
     __syncthreads();
-    // ---- warp `warp` places the buckets of region `warp`: g = warp + 16 i
+    const uint32_t nsel = nsel_sh < (uint32_t)kRegionSlots ? nsel_sh : (uint32_t)kRegionSlots;
+    for (uint32_t j = t; j < nsel; j += kChdThreads) {
+        const uint32_t lb = selb[j] & ~kHot;
+        atomicAdd(&bsize[lb], 1u);
+        if (selb[j] & kHot) atomicOr(&bsize[lb], kHot);
+    }
+    __syncthreads();
+    if (t >= 32) return;  // grouping and placement: the first warp alone (warp barriers only)
+    // bucket starts: four buckets a lane, then a shuffle scan
+    uint32_t own = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) own += bsize[lane * 4 + q] & 0xFFFFu;
+    uint32_t incl = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(kFull, incl, o);
+        if (lane >= (uint32_t)o) incl += x;
+    }
+    uint32_t run = incl - own;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        bstart[lane * 4 + q] = run;
+        run += bsize[lane * 4 + q] & 0xFFFFu;
+    }
+    __syncwarp();
+    for (uint32_t j = lane; j < nsel; j += 32) {
+        const uint32_t lb = selb[j] & ~kHot;
+        rkey[bstart[lb] + atomicAdd(&bfill[lb], 1u)] = sel[j];
+    }
+    __syncwarp();
     uint32_t maxsize = 0;
-    for (uint32_t i = lane; i < kHeadBuckets / kHeadRegions; i += 32)
-        maxsize = max(maxsize, bsize[warp + kHeadRegions * i] & 0xFFFFu);
+#pragma unroll
+    for (int q = 0; q < 4; q++) maxsize = max(maxsize, bsize[lane * 4 + q] & 0xFFFFu);
     maxsize = __reduce_max_sync(kFull, maxsize);
+    // ---- placement
     for (int pass = 0; pass < 2; pass++) {
         for (uint32_t size = maxsize < 32u ? maxsize : 32u; size >= 1; size--) {
-            for (uint32_t i0 = 0; i0 < kHeadBuckets / kHeadRegions; i0 += 32) {
-                const uint32_t gl = warp + kHeadRegions * (i0 + lane);
-                const uint32_t bs = bsize[gl];
+            for (uint32_t i0 = 0; i0 < (uint32_t)kRegionBuckets; i0 += 32) {
+                const uint32_t bs = bsize[i0 + lane];
                 uint32_t todo = __ballot_sync(kFull, (bs & 0xFFFFu) == size && ((bs & kHot) != 0) == (pass == 0));
                 while (todo) {
-                    const uint32_t g = warp + kHeadRegions * (i0 + (uint32_t)(__ffs(todo) - 1));
+                    const uint32_t lb = i0 + (uint32_t)(__ffs(todo) - 1);
                     todo &= todo - 1;
-                    const unsigned long long *bk = skey + bstart[g];
-                    if (size <= (uint32_t)kChdSmall) {
-                        // every lane holds the bucket's keys and tries displacement dbase + lane
-                        unsigned long long key[kChdSmall], h[kChdSmall];
-#pragma unroll
-                        for (int k = 0; k < kChdSmall; k++) {
-                            key[k] = k < (int)size ? bk[k] : 0ull;
-                            h[k] = l1_mix(key[k]);
-                        }
-                        for (uint32_t dbase = 0; dbase < 256; dbase += 32) {
-                            const uint32_t d = dbase + lane;
-                            uint32_t slot[kChdSmall];
-                            bool ok = true;
-#pragma unroll
-                            for (int k = 0; k < kChdSmall; k++) {
-                                slot[k] = head_slot(h[k], d);
-                                if (k < (int)size) {
-                                    ok = ok && !slot_used(used, slot[k]);
-#pragma unroll
-                                    for (int j = 0; j < k; j++) ok = ok && slot[j] != slot[k];
-                                }
-                            }
-                            const uint32_t win = __ballot_sync(kFull, ok);
-                            if (win) {
-                                if ((int)lane == __ffs(win) - 1) {  // the region is this warp's alone
-#pragma unroll
-                                    for (int k = 0; k < kChdSmall; k++) {
-                                        if (k < (int)size) {
-                                            used[slot[k] >> 5] |= 1u << (slot[k] & 31u);
-                                            image[slot[k]] = key[k];
-                                        }
-                                    }
-                                    sdisp[g] = (uint8_t)d;
-                                }
-                                __syncwarp();
-                                break;
-                            }
-                        }
-                        continue;
+                    const unsigned long long *bk = rkey + bstart[lb];
+                    switch (size) {  // warp-uniform
+                    case 1: chd_place_small<1>(bk, used, rimage, &sdisp[lb], lane); continue;
+                    case 2: chd_place_small<2>(bk, used, rimage, &sdisp[lb], lane); continue;
+                    case 3: chd_place_small<3>(bk, used, rimage, &sdisp[lb], lane); continue;
+                    case 4: chd_place_small<4>(bk, used, rimage, &sdisp[lb], lane); continue;
+                    case 5: chd_place_small<5>(bk, used, rimage, &sdisp[lb], lane); continue;
+                    case 6: chd_place_small<6>(bk, used, rimage, &sdisp[lb], lane); continue;
+                    case 7: chd_place_small<7>(bk, used, rimage, &sdisp[lb], lane); continue;
+                    case 8: chd_place_small<8>(bk, used, rimage, &sdisp[lb], lane); continue;
+                    default: break;
                     }
                     const bool mine = lane < size;
                     const unsigned long long key = mine ? bk[lane] : 0ull;
                     const unsigned long long h = l1_mix(key);
                     for (uint32_t d = 0; d < 256; d++) {
-                        const uint32_t slot = mine ? head_slot(h, d) : (uint32_t)kHeadSlots + lane;  // dummies never clash
-                        // every lane takes part in the match (never behind a short-circuit)
+                        // dummy slots of idle lanes never clash; every lane takes part in the match
+                        const uint32_t slot = mine ? (head_slot(h, d) & (uint32_t)(kRegionSlots - 1)) : 1024u + lane;
                         const uint32_t peers = __match_any_sync(kFull, slot);
-                        const bool ok = (!mine || !slot_used(used, slot)) && peers == (1u << lane);
+                        const bool ok = (!mine || !((used[slot >> 5] >> (slot & 31u)) & 1u)) && peers == (1u << lane);
                         if (!__all_sync(kFull, ok)) continue;
                         if (mine) {
                             atomicOr(&used[slot >> 5], 1u << (slot & 31u));  // lanes may share a bitmap word
-                            image[slot] = key;
+                            rimage[slot] = key;
                         }
-                        if (lane == 0) sdisp[g] = (uint8_t)d;
+                        if (lane == 0) sdisp[lb] = (uint8_t)d;
                         __syncwarp();
                         break;
                     }
@@ -794,10 +814,9 @@ __global__ void __launch_bounds__(kChdThreads) k_head_chd(const unsigned long lo
             }
         }
     }
-    __syncthreads();
-    for (uint32_t s = t; s < kHeadSlots; s += kChdThreads)
-        if (!slot_used(used, s)) image[s] = 0ull;
-    for (uint32_t i = t; i < kHeadBuckets; i += kChdThreads) disp[i] = sdisp[i];
+    __syncwarp();
+    for (uint32_t i = lane; i < kRegionSlots; i += 32) image[r * kRegionSlots + i] = rimage[i];
+    for (uint32_t i = lane; i < (uint32_t)kRegionBuckets; i += 32) disp[r + kHeadRegions * i] = sdisp[i];
 }
 
 // ---------------------------------------------------------------- launch
@@ -838,7 +857,6 @@ cudaError_t ensure_smem_limit(const void *func, int bytes) {
 
 cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
     cudaError_t e = ensure_smem_limit((const void *)k_count3<MODE_HEAD>, (int)kCountSmem);
-    if (e == cudaSuccess) e = ensure_smem_limit((const void *)k_head_chd, (int)kChdSmem);
     if (e == cudaSuccess) e = ensure_smem_limit((const void *)k_count3<MODE_LOCAL>, (int)kCountSmem);
     if (e == cudaSuccess) e = ensure_smem_limit((const void *)k_count3<MODE_SAMPLE>, (int)kCountSmem);
     if (e != cudaSuccess) return e;
@@ -885,7 +903,7 @@ cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
         k_head_hist<<<sms, 256, 0, s>>>(sample, kSampleSlots, hist);
         k_head_threshold<<<1, 1024, 0, s>>>(hist, kHeadMax, meta);
         k_head_collect<<<sms * 2, 256, 0, s>>>(sample, kSampleSlots, meta, cand, ccnt, kHeadMax);
-        k_head_chd<<<1, kChdThreads, kChdSmem, s>>>(cand, ccnt, meta, image, image_disp);
+        k_head_chd<<<kHeadRegions, kChdThreads, 0, s>>>(cand, ccnt, meta, image, image_disp);
         head = true;
     }
     if (head) {

@@ -104,12 +104,22 @@ struct SortScratch {
     uint32_t *cur;           // 25
     uint32_t *group_hist[2]; // 256 x group_stride each: digit counts per tile group, by pass parity
     uint32_t group_stride;
+    uint32_t *look[2];       // 256 x ntiles each: per-tile digit counts published for the look-back, by pass parity
+    uint32_t *tile_ctr;      // [2]: tiles taken in launch order, by pass parity
     // permutation buffer c (0 or 1), selected without indexing the parameter array
     __device__ __forceinline__ uint32_t *perm_buf(uint32_t c) const { return c ? perm[1] : perm[0]; }
     __device__ __forceinline__ uint32_t *group_buf(uint32_t c) const { return c ? group_hist[1] : group_hist[0]; }
+    __device__ __forceinline__ uint32_t *look_buf(uint32_t c) const { return c ? look[1] : look[0]; }
 };
+// Slot of SortScratch::cur where a radix pass records a look-back that gave
+// up waiting (the finish then reports WC_ERR_TIMEOUT).
+constexpr int kCurSortError = 30;
 size_t sort_scratch_bytes(uint64_t cap);
 void sort_scratch_carve(SortScratch &s, void *base, uint64_t cap);
+// Zeroes what a sort accumulates into (digit histograms, pass cursors, group
+// counts, the first pass's look-back buffer and the tile counters): every
+// sort of a scratch starts with this (stream-ordered memsets).
+void sort_state_reset(SortScratch &ss, cudaStream_t st);
 
 // Word bytes of table entries for ordering long words that share a prefix.
 struct LongView {

@@ -37,10 +37,12 @@ constexpr uint64_t kBytes16 = round256(kNaCap16 * sizeof(wc::GSlot));
 constexpr uint64_t kBytesLong = round256(kNaCapLong * sizeof(wc::LSlot));
 // Sort scratch for kNaEntries entries (khi, klo, cnt, packed key (8 + 4 bytes),
 // lref, 2 permutations, doc, the digit histograms, tile histograms, pass
-// cursors), each carved at a 256-byte boundary.
+// cursors, group counts, the look-back buffers and tile counters), each
+// carved at a 256-byte boundary.
+constexpr uint64_t kNaTiles = (kNaEntries + 4095) / 4096;
 constexpr uint64_t kSortBytes = kNaEntries * (8 + 8 + 8 + 8 + 4 + 4 + 4 + 4 + 4) + 4 * wc::kSortPassesSeg * 256 +
-                                4 * 256 * ((kNaEntries + 4095) / 4096) + 4 * 32 +
-                                2 * 4 * 256 * wc::sort_group_stride((kNaEntries + 4095) / 4096) + 4096 + 16 * kR;
+                                4 * 256 * kNaTiles + 4 * 32 + 2 * 4 * 256 * wc::sort_group_stride(kNaTiles) + 4096 +
+                                2 * (4 * 256 * kNaTiles + 256) + 256 + 20 * kR;
 constexpr uint64_t kScratchBytes = kBytes8 + kBytes16 + kBytesLong + kSortBytes;  // about 15.5 MB
 
 }  // namespace

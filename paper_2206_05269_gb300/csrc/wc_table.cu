@@ -38,7 +38,8 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 size_t sort_scratch_bytes(uint64_t cap) {
     uint64_t ntiles = (cap + kSortTile - 1) / kSortTile;
     return cap * (8 + 8 + 8 + 8 + 4 + 4 + 4 + 4 + 4) + 4 * kPassesSeg * 256 + 4 * 256 * ntiles + 4 * 32 +
-           2 * 4 * 256 * (ntiles <= kSortFusedMaxTiles ? sort_group_stride(ntiles) : 1) + 4096;
+           2 * 4 * 256 * (ntiles <= kSortFusedMaxTiles ? sort_group_stride(ntiles) : 1) + 4096 +
+           2 * (4 * 256 * ntiles + 256) + 256;
 }
 
 void sort_scratch_carve(SortScratch &s, void *base, uint64_t cap) {
@@ -61,6 +62,9 @@ void sort_scratch_carve(SortScratch &s, void *base, uint64_t cap) {
     s.group_stride = (uint32_t)(ntiles <= kSortFusedMaxTiles ? sort_group_stride(ntiles) : 1);
     s.group_hist[0] = reinterpret_cast<uint32_t *>(take(2 * 4 * 256 * (size_t)s.group_stride));  // both, adjacent
     s.group_hist[1] = s.group_hist[0] + 256 * (size_t)s.group_stride;
+    s.look[0] = reinterpret_cast<uint32_t *>(take(4 * 256 * ntiles));
+    s.look[1] = reinterpret_cast<uint32_t *>(take(4 * 256 * ntiles));
+    s.tile_ctr = reinterpret_cast<uint32_t *>(take(4 * 2));
 }
 
 // ---------------------------------------------------------------- compaction
@@ -484,6 +488,133 @@ __global__ void __launch_bounds__(kSortThreads) k_pass_scatter(J job, int p, int
     }
 }
 
+// One radix pass in one launch, with a decoupled look-back for the tile
+// offsets.  Blocks take tiles in launch order from a counter (so every tile
+// a block waits for belongs to a block that is already running), rank their
+// entries per digit as k_pass_scatter does, publish their per-digit counts
+// (flag "aggregate"), and learn the counts of all earlier tiles by walking
+// back over the published values until one carries a complete prefix (flag
+// "inclusive"), which they then publish for their own tile.  Each wait is
+// bounded: a look-back that gives up records kCurSortError (reported as a
+// timeout by the finish) instead of hanging.  The block also zeroes its row
+// of the other parity's look-back buffer and block 0 the other tile counter,
+// for the next pass.
+constexpr uint32_t kLookAgg = 1u << 30, kLookInc = 2u << 30, kLookVal = kLookAgg - 1u;
+constexpr uint32_t kLookSpins = 1u << 24;
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+template <class J>
+__global__ void __launch_bounds__(kSortThreads) k_pass_one(J job, int p, int e, int last) {
+    const SortScratch &s = job.get().s;
+    const unsigned long long *meta = job.get().meta;
+    constexpr int WARPS = kSortThreads / 32;
+    __shared__ uint32_t wcount[WARPS][256];
+    __shared__ uint32_t wtot[WARPS];
+    __shared__ uint32_t tile_sh;
+    const unsigned long long n = meta[0];
+    const unsigned long long ntiles = (n + kSortTile - 1) / kSortTile;
+    const uint32_t par = (uint32_t)e & 1u;
+    if (blockIdx.x < ntiles) s.look_buf(par ^ 1u)[(unsigned long long)blockIdx.x * 256 + threadIdx.x] = 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) s.tile_ctr[par ^ 1u] = 0u;
+    const bool skip = pass_skipped(s, p, n);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const uint32_t c = skip ? s.cur[e] : 1u - s.cur[e];
+        s.cur[e + 1] = c;
+        if (last) s.cur[kCurFinal] = c;
+    }
+    if (skip || blockIdx.x >= ntiles) return;
+    if (threadIdx.x == 0) tile_sh = atomicAdd(&s.tile_ctr[par], 1u);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < WARPS * 256; i += kSortThreads) (&wcount[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t tile = tile_sh;
+    const uint32_t cur = s.cur[e];
+    const uint32_t *in = s.perm_buf(cur);
+    uint32_t *out = s.perm_buf(1 - cur);
+    const unsigned long long t0 = (unsigned long long)tile * kSortTile + (unsigned long long)warp * (kSortTile / WARPS);
+    uint32_t idx[kItems], dig[kItems], rank[kItems];
+#pragma unroll
+    for (int it = 0; it < kItems; it++) {
+        const unsigned long long i = t0 + it * 32 + lane;
+        idx[it] = i < n ? in[i] : 0u;
+    }
+#pragma unroll
+    for (int it = 0; it < kItems; it++) {
+        const unsigned long long i = t0 + it * 32 + lane;
+        dig[it] = i < n ? sort_digit(s, idx[it], p) : 256u + lane;  // invalid lanes never match real digits
+    }
+#pragma unroll
+    for (int it = 0; it < kItems; it++) {
+        const unsigned long long i = t0 + it * 32 + lane;
+        const bool valid = i < n;
+        const uint32_t peers = __match_any_sync(kFull, dig[it]);
+        const int leader = __ffs(peers) - 1;
+        uint32_t before = 0;
+        if (lane == leader && valid) {
+            before = wcount[warp][dig[it]];
+            wcount[warp][dig[it]] = before + __popc(peers);
+        }
+        before = __shfl_sync(kFull, before, leader);
+        rank[it] = before + __popc(peers & lanemask_lt());
+    }
+    __syncthreads();
+    // thread d: this tile's count of digit d, published, then the look-back
+    const int d = threadIdx.x;
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; w++) cnt += wcount[w][d];
+    uint32_t *look = s.look_buf(par);
+    uint32_t excl = 0;
+    if (tile == 0) {
+        st_release_u32(&look[d], kLookInc | cnt);
+    } else {
+        st_release_u32(&look[(unsigned long long)tile * 256 + d], kLookAgg | cnt);
+        for (long long t = (long long)tile - 1; t >= 0; t--) {
+            uint32_t v = 0, spins = 0;
+            do {
+                v = ld_acquire_u32(&look[(unsigned long long)t * 256 + d]);
+            } while (!(v & (kLookAgg | kLookInc)) && ++spins < kLookSpins);
+            if (!(v & (kLookAgg | kLookInc))) {  // gave up: recorded, the order is not used
+                atomicOr(&s.cur[kCurSortError], 1u);
+                break;
+            }
+            excl += v & kLookVal;
+            if (v & kLookInc) break;
+        }
+        st_release_u32(&look[(unsigned long long)tile * 256 + d], kLookInc | (excl + cnt));
+    }
+    // this tile's first position for digit d: the entries with a smaller
+    // digit (the all-pass histogram) plus digit d's entries in earlier tiles
+    const uint32_t own = s.hist_all[p * 256 + d];
+    uint32_t incl = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += x;
+    }
+    if (lane == 31) wtot[warp] = incl;
+    __syncthreads();
+    uint32_t run = incl - own + excl;
+    for (int w = 0; w < warp; w++) run += wtot[w];
+    for (int w = 0; w < WARPS; w++) {
+        const uint32_t v = wcount[w][d];
+        wcount[w][d] = run;
+        run += v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kItems; it++) {
+        const unsigned long long i = t0 + it * 32 + lane;
+        if (i < n) out[wcount[warp][dig[it]] + rank[it]] = idx[it];
+    }
+}
+
 // Compares two entries whose 16-byte prefixes are equal by the bytes after
 // the prefix (a word that fits the prefix is a proper prefix of a longer one).
 __device__ __forceinline__ bool tail_less(const LongView &v, uint32_t a, uint32_t b) {
@@ -551,6 +682,7 @@ __global__ void k_gather_final(J job) {
     const SortScratch &s = job.get().s;
     const DevTable &out = job.get().out;
     const unsigned long long n = out.d_meta[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && s.cur[kCurSortError]) atomicOr(out.d_status, ST_TIMEOUT);
     const uint32_t *perm = s.perm_buf(s.cur[kCurFinal]);
     unsigned long long bytes = 0;
     // kScanUnroll entries a thread per step, all gathers issued before the stores
@@ -616,13 +748,20 @@ static void launch_sort(const J &job, uint64_t cap, int ntab, int passes, uint32
     int lastp = -1;
     for (int p = 0; p < passes; p++)
         if (!((skip >> p) & 1u)) lastp = p;
-    // e counts the launched passes: pass e reads its order from cur[e]
+    // e counts the launched passes: pass e reads its order from cur[e].
+    // Counts below 2^30 fit the look-back words: one launch a pass; larger
+    // sorts count, (scan) and scatter in separate launches.
+    const bool onesweep = cap < (1ull << 30);
     for (int p = 0, e = 0; p < passes; p++) {
         if ((skip >> p) & 1u) continue;
         const int last = p == lastp;
-        k_pass_count<<<dim3(ntiles, ntab), kSortThreads, 0, st>>>(job, p, e, fused);
-        if (!fused) k_pass_scan<<<dim3(256, ntab), 256, 0, st>>>(job, p, e, last);
-        k_pass_scatter<<<dim3(ntiles, ntab), kSortThreads, 0, st>>>(job, p, e, fused, last);
+        if (onesweep) {
+            k_pass_one<<<dim3(ntiles, ntab), kSortThreads, 0, st>>>(job, p, e, last);
+        } else {
+            k_pass_count<<<dim3(ntiles, ntab), kSortThreads, 0, st>>>(job, p, e, fused);
+            if (!fused) k_pass_scan<<<dim3(256, ntab), 256, 0, st>>>(job, p, e, last);
+            k_pass_scatter<<<dim3(ntiles, ntab), kSortThreads, 0, st>>>(job, p, e, fused, last);
+        }
         e++;
     }
     k_fix_long<<<dim3(grid_for(cap, 256, sms * 4), ntab), 256, 0, st>>>(job, passes);
@@ -638,7 +777,8 @@ cudaError_t sort_entries(SortScratch &ss, const unsigned long long *meta, const 
 int sort_entries_launches(int passes, uint64_t cap, uint32_t skip) {
     const bool fused = (cap + kSortTile - 1) / kSortTile <= kSortFusedMaxTiles;
     const uint32_t mask = passes >= 32 ? ~0u : ((1u << passes) - 1u);
-    return 1 + 1 + (fused ? 2 : 3) * (passes - __builtin_popcount(skip & mask));
+    const int per = cap < (1ull << 30) ? 1 : (fused ? 2 : 3);
+    return 1 + 1 + per * (passes - __builtin_popcount(skip & mask));
 }
 
 uint32_t sort_skip_mask(uint64_t max_count, uint64_t ndocs) {
@@ -654,12 +794,19 @@ uint32_t sort_skip_mask(uint64_t max_count, uint64_t ndocs) {
     return m;
 }
 
-static void launch_compaction(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_t glcap, SortScratch &ss,
-                              DevTable &out, cudaStream_t st) {
-    const int sms = sm_count();
+void sort_state_reset(SortScratch &ss, cudaStream_t st) {
+    const uint64_t ntiles = (ss.cap + kSortTile - 1) / kSortTile;
     cudaMemsetAsync(ss.hist_all, 0, 4 * kPassesSeg * 256, st);
     cudaMemsetAsync(ss.cur, 0, 4 * 32, st);
     cudaMemsetAsync(ss.group_hist[0], 0, 2 * 4 * 256 * (size_t)ss.group_stride, st);
+    cudaMemsetAsync(ss.look[0], 0, 4 * 256 * (size_t)ntiles, st);
+    cudaMemsetAsync(ss.tile_ctr, 0, 4 * 2, st);
+}
+
+static void launch_compaction(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_t glcap, SortScratch &ss,
+                              DevTable &out, cudaStream_t st) {
+    const int sms = sm_count();
+    sort_state_reset(ss, st);
     k_compact8<<<grid_for(gcap8, 256 * kScanUnroll, sms * 8), 256, 0, st>>>(g.slots8, gcap8, ss, out.d_meta);
     k_meta_snapshot<<<1, 1, 0, st>>>(out.d_meta, 5);
     k_compact_short<<<grid_for(gcap, 256 * kScanUnroll, sms * 8), 256, 0, st>>>(g.slots, gcap, ss, out.d_meta);

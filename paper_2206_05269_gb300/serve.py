@@ -18,9 +18,10 @@ wc_batch_topk for a round), and the whole table too when keep_tables is set.
 The context's device-memory budget bounds admission: each unit's request text
 is allocated from the context's budgeted pool (wc_buffer_alloc) like the
 library's own tables and scratch, so a unit whose text or tables the budget
-cannot hold waits for running work to finish and free its memory (a round
-refused with nothing running is cut to fewer requests; a single request
-larger than the whole budget is an error).  A round whose device tables
+cannot hold waits for running work to finish and free its memory (memory freed in stream order is charged until its stream has passed the
+free, so with nothing running the loop first waits for the device; a round
+still refused then is cut to fewer requests, and a single request larger than
+the whole budget is an error).  A round whose device tables
 overflow is recounted request by request with growing capacities, so answers
 are always exact.
 
@@ -120,7 +121,8 @@ def serve_batched(counter: wc.Counter, requests: list[Request], topk: int = 100,
     order = sorted(requests, key=lambda r: r.arrival)
     nxt = 0
     t0 = time.perf_counter()
-    stats = {"rounds": 0, "large": 0, "recounted": 0, "capacity_errors": [], "budget_waits": 0}
+    stats = {"rounds": 0, "large": 0, "recounted": 0, "capacity_errors": [], "budget_waits": 0,
+             "max_running": 0}
 
     def answer(rq, w, o, c, s0, n, full):
         now = time.perf_counter() - t0
@@ -144,9 +146,8 @@ def serve_batched(counter: wc.Counter, requests: list[Request], topk: int = 100,
                 buf, _ = _to_device(counter, [rq], stream)
                 break
             except wc.WcError as e:
-                if e.status != wc.WC_ERR_BUDGET or not running:
+                if e.status != wc.WC_ERR_BUDGET or not make_room():
                     raise
-                finish(running.popleft())  # free budget held by older work
         with torch.cuda.stream(stream):
             t = counter.count_checked(buf.tensor[:rq.data.numel()], stream=stream)
             answer_table(rq, t, stream)
@@ -162,9 +163,22 @@ def serve_batched(counter: wc.Counter, requests: list[Request], topk: int = 100,
             try:
                 return fn()
             except wc.WcError as e:
-                if e.status != wc.WC_ERR_BUDGET or not running:
+                if e.status != wc.WC_ERR_BUDGET or not make_room():
                     raise
-                finish(running.popleft())
+
+    def make_room():
+        """Frees budget for a refused allocation: finishes the oldest running
+        unit; with nothing running, waits for the device, since memory freed
+        in stream order is charged until its stream has passed the free.
+        False when neither frees anything."""
+        if running:
+            finish(running.popleft())
+            return True
+        used = counter.mem_usage()[0]
+        if used:
+            torch.cuda.synchronize(dev)
+            return counter.mem_usage()[0] < used
+        return False
 
     def finish(wk: _Work):
         wk.event.synchronize()
@@ -257,11 +271,12 @@ def serve_batched(counter: wc.Counter, requests: list[Request], topk: int = 100,
         if (small or big) and free_streams:
             stream = free_streams.popleft()
             if launch(stream):
+                stats["max_running"] = max(stats["max_running"], len(running))
                 continue
             stats["budget_waits"] += 1
             free_streams.appendleft(stream)  # budget: wait for running work
-            if running:
-                finish(running.popleft())
+            if make_room():
+                pass
             elif small and round_limit[0] > 1:
                 round_limit[0] //= 2  # nothing else holds memory: admit a smaller round
             else:

@@ -64,33 +64,65 @@ def test_fifo_path_matches(ctr):
         assert tx.as_list() == ty.as_list() == x.as_list()[:100]
 
 
+def test_budget_charges_buffers_until_their_free_has_run():
+    """wc_buffer_alloc refuses what the budget cannot hold; a buffer freed in
+    stream order stays charged until the stream has passed the free."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_05269_gb300 import wc
+    c = wc.Counter(0, count_bits=32, budget=64 << 20)
+    s = torch.cuda.Stream()
+    a = c.buffer(40 << 20, s)
+    with pytest.raises(wc.WcError) as e:
+        c.buffer(40 << 20, s)
+    assert e.value.status == wc.WC_ERR_BUDGET
+    # keep the stream busy (a bounded spin of about 0.2 s), then free in stream order
+    with torch.cuda.stream(s):
+        torch.cuda._sleep(400_000_000)
+    a.free(s)
+    assert c.mem_usage()[0] >= 40 << 20, "freed bytes must stay charged until the stream passes the free"
+    with pytest.raises(wc.WcError) as e:
+        c.buffer(40 << 20, s)
+    assert e.value.status == wc.WC_ERR_BUDGET
+    s.synchronize()
+    assert c.mem_usage()[0] == 0
+    b = c.buffer(40 << 20, s)
+    assert c.mem_usage()[0] >= 40 << 20
+    b.free(s)
+    s.synchronize()
+    assert c.mem_usage() == (0, c.mem_usage()[1]) and c.mem_usage()[1] <= 64 << 20
+    c.close()
+
+
 def test_admission_waits_under_a_tight_budget():
     """Request text is charged to the context's budget with the tables: with
-    requests of about 250 KB arriving together, each counted as a unit of its
-    own on one of six streams, and a budget of two and a half units, units
-    wait for admission instead of failing, the context never holds more than
-    its budget, and every answer is still the oracle's."""
+    requests of about 12 MB arriving together (each a unit of its own, longer
+    on the GPU than the loop takes to launch the next), six streams and a
+    budget of 1.6 units, units wait for admission instead of failing, the
+    context never holds more than its budget, and every answer is still the
+    oracle's."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2206_05269_gb300 import serve, wc
-    pool, trip, reqs = make_requests(n_rate=4000.0, dur=0.015, lo=200 << 10, hi=300 << 10, seed=21)
-    assert len(reqs) >= 30
+    pool, trip, reqs = make_requests(n_rate=2000.0, dur=0.006, lo=10 << 20, hi=14 << 20, pool_bytes=96e6, seed=21)
+    assert len(reqs) >= 6
     reqs = [serve.Request(r.rid, 0.0, r.data) for r in reqs]  # all waiting at the start
-    kw = dict(topk=100, big_bytes=128 << 10, keep_tables=True)
+    kw = dict(topk=100, big_bytes=4 << 20)
     # one unit's footprint: the largest, counting one unit at a time
     solo = wc.Counter(0, count_bits=32, budget=8 << 30)
     solo.mem_usage(reset=True)
     serve.serve_batched(solo, reqs, max_inflight=1, **kw)
     unit = solo.mem_usage()[1]
     solo.close()
-    budget = int(unit * 2.5)
+    budget = int(unit * 1.6)
     tight = wc.Counter(0, count_bits=32, budget=budget)
     answers, stats = serve.serve_batched(tight, reqs, max_inflight=6, **kw)
     used, peak = tight.mem_usage()
     tight.close()
     assert stats["large"] == len(reqs)
-    assert stats["budget_waits"] > 0, "six streams under a budget of two and a half units must wait"
+    assert stats["budget_waits"] > 0, f"six streams under a budget of 1.6 units must wait: unit {unit}, {stats}"
     assert peak <= budget, f"peak {peak} over the budget {budget}"
     for (a, s, e), ans in zip(trip, answers):
-        assert ans.full and ans.as_list() == oracle.count(pool[s:e]).glob().as_list(), f"request {ans.rid}"
+        assert ans.as_list() == oracle.count(pool[s:e]).glob().as_list()[:100], f"request {ans.rid}"
