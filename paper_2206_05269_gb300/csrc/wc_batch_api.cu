@@ -865,7 +865,7 @@ __device__ unsigned long long lookup_count(const GTable &g, uint4 k, const uint8
         }
         return 0;
     }
-    unsigned long long s = hash_key(k) & g.mask;
+    unsigned long long s = home16(k, g.mask);
     for (int probe = 0; probe < kGlobalProbeLimit; probe++) {
         const uint4 c = g.slots[s].key;
         if (key_eq(c, k)) return g.slots[s].cnt;

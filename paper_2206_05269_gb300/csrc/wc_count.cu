@@ -38,6 +38,7 @@
 // the global long-word table (bytes compared, never only hashes).  At the end
 // each block adds its nonzero level-1 counts into the global table.
 #include <algorithm>
+#include <cstddef>
 #include <mutex>
 #include <set>
 #include <tuple>
@@ -66,6 +67,7 @@ constexpr int kHeadRegions = 16;          // the image is placed region by regio
 constexpr int kRegionSlots = kHeadSlots / kHeadRegions;
 constexpr uint32_t kHeadMax = kHeadSlots * 80 / 100;  // head candidates (load factor of the image)
 constexpr uint32_t kHotMax = 512;                     // candidates placed first (the sample's most frequent)
+constexpr unsigned long long kLongQCap = 1ull << 21;  // deferred long words per launch
 static_assert(kWinB % 16 == 0, "TMA bulk copies move multiples of 16 bytes");
 static_assert(kStages == 4, "2-bit stage tag in queued words");
 
@@ -82,6 +84,8 @@ struct Count2Args {
     const uint8_t *lbegin;            // long-word representatives lie in [lbegin, text + hi)
     const unsigned long long *head;   // HEAD image: kHeadSlots keys
     const uint8_t *head_disp;         // HEAD image: kHeadBuckets displacements
+    unsigned long long *lq;           // deferred long words (kLongQCap entries), or null: inserted in place
+    unsigned long long *lqn;          // entries appended to lq (may pass kLongQCap: the rest were inserted in place)
 };
 
 // ---------------------------------------------------------------- TMA + mbarrier
@@ -199,63 +203,68 @@ __device__ __forceinline__ uint4 window_key16(const uint8_t *win, uint32_t p, ui
 // Per-warp tail inserts, 32 words at a time (one per lane), as a state
 // machine that never waits for a dependent round trip inside a flush.  A
 // lane takes a word from the tail queue, computes its home slot and starts
-// loading the keys stored there and in the next slot; at the next flush
-// (when the next 32 tail words are ready, so the loads had time to land) it
-// advances one step:
+// loading the first 16 bytes of that slot and of the next one; at the next
+// flush (when the next 32 tail words are ready, so the loads had time to
+// land) it advances one step:
 //   * the key is in one of the two slots: a fire-and-forget add, done;
-//   * the first slot not holding another key for good is empty (or, for
-//     16-byte keys, half written): a CAS claims it, and its result is
+//   * else the first of them not holding another key for good is empty (or,
+//     for 16-byte keys, half written): a CAS claims it, and its result is
 //     checked at the following flush (the word is done if the CAS won or
 //     found the same key, else probing resumes after that slot);
 //   * both slots hold other keys: loads of the next two slots are started.
 // Keys are written once and never move, so a key seen in a slot is final.
-// Lanes still busy keep their word across flushes; free lanes take new words.
+// Both key sizes take the same path: the table (8-byte slots of 16 bytes,
+// 16-byte slots of 32 bytes) is chosen by address arithmetic, the slot hash
+// is shared, and a 16-byte load covers either slot's key (for an 8-byte slot,
+// key and count; the count is ignored).  Only the claim differs (64- or
+// 128-bit CAS); claims are rare.  Lanes still busy keep their word across
+// flushes; free lanes take new words.
+static_assert(sizeof(G8Slot) == 16 && offsetof(G8Slot, cnt) == 8, "8-byte slot layout");
+static_assert(sizeof(GSlot) == 32 && offsetof(GSlot, cnt) == 16, "16-byte slot layout");
 template <int MODE>
 struct Tail {
     const GTable &g;
     uint32_t st = 0;  // 0 free, 1 loads in flight, 2 CAS in flight
     bool p16 = false;
     uint32_t probes = 0;
-    uint4 pk;
-    unsigned long long pslot = 0, v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+    unsigned long long k0 = 0, k1 = 0;  // key halves (k1 = 0 for 8-byte keys)
+    unsigned long long pslot = 0;
+    uint4 v0, v1;  // slots pslot and pslot + 1 (first 16 bytes), or the CAS result in v0
 
     __device__ __forceinline__ explicit Tail(const GTable &gt) : g(gt) {}
 
+    __device__ __forceinline__ uint8_t *tab() const {
+        return p16 ? reinterpret_cast<uint8_t *>(g.slots) : reinterpret_cast<uint8_t *>(g.slots8);
+    }
+    __device__ __forceinline__ unsigned long long msk() const { return p16 ? g.mask : g.mask8; }
+    __device__ __forceinline__ uint32_t shf() const { return p16 ? 5u : 4u; }
+
     __device__ __forceinline__ void load() {
-        if (!p16) {
-            v0 = ld_u64(&g.slots8[pslot].key);
-            v1 = ld_u64(&g.slots8[(pslot + 1) & g.mask8].key);
-        } else {
-            const unsigned long long *kp = reinterpret_cast<const unsigned long long *>(&g.slots[pslot].key);
-            const unsigned long long *kq =
-                reinterpret_cast<const unsigned long long *>(&g.slots[(pslot + 1) & g.mask].key);
-            v0 = ld_u64(kp);
-            v1 = ld_u64(kp + 1);
-            v2 = ld_u64(kq);
-            v3 = ld_u64(kq + 1);
-        }
+        uint8_t *t = tab();
+        v0 = ld_relaxed_v2(t + (pslot << shf()));
+        v1 = ld_relaxed_v2(t + (((pslot + 1) & msk()) << shf()));
         st = 1;
     }
     __device__ __forceinline__ void take(uint4 k) {
-        pk = k;
-        p16 = MODE != MODE_SAMPLE && (k.z | k.w) != 0u;
-        pslot = p16 ? (hash_key(k) & g.mask) : (hash8(key_lo(k)) >> __clzll((long long)g.mask8));
+        k0 = key_lo(k);
+        k1 = ((unsigned long long)k.w << 32) | k.z;
+        p16 = MODE != MODE_SAMPLE && k1 != 0ull;
+        pslot = hash_slot(k0, k1) >> __clzll((long long)msk());
         probes = 0;
         load();
     }
     __device__ __forceinline__ void add_at(unsigned long long s) {
-        if (!p16) red_add_u64(&g.slots8[s].cnt, 1ull);
-        else red_add_u64(&g.slots[s].cnt, 1ull);
+        red_add_u64(reinterpret_cast<unsigned long long *>(tab() + (s << shf()) + (p16 ? 16u : 8u)), 1ull);
         st = 0;
     }
     __device__ __forceinline__ void claim(unsigned long long s) {
         pslot = s;
         if (!p16) {
-            v0 = atomicCAS(&g.slots8[s].key, 0ull, key_lo(pk));
+            const unsigned long long old = atomicCAS(&g.slots8[s].key, 0ull, k0);
+            v0 = make_uint4((uint32_t)old, (uint32_t)(old >> 32), 0u, 0u);
         } else {
-            const uint4 old = cas128_global(&g.slots[s].key, make_uint4(0u, 0u, 0u, 0u), pk);
-            v0 = ((unsigned long long)old.y << 32) | old.x;
-            v1 = ((unsigned long long)old.w << 32) | old.z;
+            const uint4 want = make_uint4((uint32_t)k0, (uint32_t)(k0 >> 32), (uint32_t)k1, (uint32_t)(k1 >> 32));
+            v0 = cas128_global(&g.slots[s].key, make_uint4(0u, 0u, 0u, 0u), want);
         }
         st = 2;
     }
@@ -266,31 +275,26 @@ struct Tail {
             st = 0;
             return;
         }
-        pslot = from & (p16 ? g.mask : g.mask8);
+        pslot = from & msk();
         load();
     }
     // One step of a busy lane with what its last step fetched.
     __device__ __forceinline__ void step() {
-        const unsigned long long m = p16 ? g.mask : g.mask8;
-        const unsigned long long k0 = key_lo(pk), k1 = ((unsigned long long)pk.w << 32) | pk.z;
-        if (st == 2) {  // the CAS result
-            const bool mine = p16 ? ((v0 == 0ull && v1 == 0ull) || (v0 == k0 && v1 == k1)) : (v0 == 0ull || v0 == k0);
+        const unsigned long long m = msk();
+        const unsigned long long a0 = key_lo(v0), a1 = ((unsigned long long)v0.w << 32) | v0.z;
+        if (st == 2) {  // the CAS result (an 8-byte claim left a1 = 0 = k1)
+            const bool mine = (a0 == 0ull && a1 == 0ull) || (a0 == k0 && a1 == k1);
             if (mine) add_at(pslot);
             else next(pslot + 1);
             return;
         }
-        if (!p16) {
-            if (v0 == k0) { add_at(pslot); return; }
-            if (v1 == k0) { add_at((pslot + 1) & m); return; }
-            if (v0 == 0ull) { claim(pslot); return; }
-            if (v1 == 0ull) { claim((pslot + 1) & m); return; }
-        } else {
-            if (v0 == k0 && v1 == k1) { add_at(pslot); return; }
-            if (v2 == k0 && v3 == k1) { add_at((pslot + 1) & m); return; }
-            // both halves non-zero: the slot holds another key for good
-            if (v0 == 0ull || v1 == 0ull) { claim(pslot); return; }
-            if (v2 == 0ull || v3 == 0ull) { claim((pslot + 1) & m); return; }
-        }
+        const unsigned long long b0 = key_lo(v1), b1 = ((unsigned long long)v1.w << 32) | v1.z;
+        // an 8-byte slot's second word is its count: only 16-byte keys compare it
+        const bool m0 = a0 == k0 && (!p16 || a1 == k1), m1 = b0 == k0 && (!p16 || b1 == k1);
+        if (m0 || m1) { add_at(m0 ? pslot : ((pslot + 1) & m)); return; }
+        // a 16-byte slot with both halves non-zero holds another key for good
+        const bool e0 = a0 == 0ull || (p16 && a1 == 0ull), e1 = b0 == 0ull || (p16 && b1 == 0ull);
+        if (e0 || e1) { claim(e0 ? pslot : ((pslot + 1) & m)); return; }
         next(pslot + 2);
     }
     // One flush round: busy lanes step, free lanes take words from the end of
@@ -441,10 +445,21 @@ __global__ void __launch_bounds__(kBlock, 1) k_count3(Count2Args a) {
     };
 
     // Words of 17+ letters: (address << 16 | run length, or 0 when the window
-    // did not show the run's end), inserted one per lane.
+    // did not show the run's end).  With a deferred queue they are appended to
+    // it (one atomic a flush) and inserted by k_long_deferred after this
+    // kernel, so the warp never waits on their table round trips; entries the
+    // queue cannot hold, or all of them without a queue, are inserted here,
+    // one per lane.
     uint32_t longn = 0;
     auto flush_long = [&](uint32_t base, uint32_t n) {
-        if ((uint32_t)lane < n) {
+        unsigned long long qb = kLongQCap;
+        if (a.lq) {
+            if (lane == 0) qb = atomicAdd(a.lqn, (unsigned long long)n);
+            qb = __shfl_sync(kFull, qb, 0);
+        }
+        if ((uint32_t)lane < n && qb + (unsigned long long)lane < kLongQCap) {
+            a.lq[qb + lane] = longq[base + lane];
+        } else if ((uint32_t)lane < n) {
             const unsigned long long e = longq[base + lane];
             const uint8_t *w = reinterpret_cast<const uint8_t *>(e >> 16);
             unsigned long long len = e & 0xFFFFull;
@@ -572,6 +587,27 @@ __global__ void __launch_bounds__(kBlock, 1) k_count3(Count2Args a) {
     }
     for (int i = threadIdx.x; i < kHeadSlots; i += kBlock)
         if (scnt[i]) global_insert8(a.g, skey[i], (unsigned long long)scnt[i]);
+}
+
+// Inserts the long words k_count3 queued (Count2Args::lq), one a thread: the
+// same insertion the counting kernel makes in place, run with enough threads
+// in flight to hide the table round trips.
+__global__ void __launch_bounds__(256) k_long_deferred(const unsigned long long *lq, const unsigned long long *lqn,
+                                                       GTable g, const uint8_t *lbegin, const uint8_t *end) {
+    const unsigned long long n = *lqn < kLongQCap ? *lqn : kLongQCap;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long e = lq[i];
+        const uint8_t *w = reinterpret_cast<const uint8_t *>(e >> 16);
+        unsigned long long len = e & 0xFFFFull;
+        if (len == 0) {  // longer than the window showed: scan to the end of the run
+            len = 17;
+            while (w + len < end && is_letter(w[len])) len++;
+        }
+        uint4 fl[2];
+        long_ends(w, len, fl[0], fl[1]);
+        long_insert2(g, w, len, long_hash_mix(fl[0], fl[1], len), 1ull, lbegin, end, fl);
+    }
 }
 
 // ---------------------------------------------------------------- head selection
@@ -820,15 +856,18 @@ __global__ void __launch_bounds__(kChdThreads) k_head_chd(const unsigned long lo
 }
 
 // ---------------------------------------------------------------- launch
-// Head scratch: the sample table, its histogram and metadata, the candidates
-// and the HEAD image (keys, then displacements).
+// Head scratch: the sample table, its histogram and metadata (the deferred
+// long-word count at byte 32), the candidates and the HEAD image (keys, then
+// displacements), then the deferred long-word queue.
 constexpr size_t kHsSample = (size_t)kSampleSlots * sizeof(G8Slot);
 constexpr size_t kHsHist = 4096 * 4;
 constexpr size_t kHsMeta = 64;
 constexpr size_t kHsCand = (size_t)kHeadSlots * 8;
 constexpr size_t kHsCcnt = (size_t)kHeadSlots * 4;
 constexpr size_t kHsImage = (size_t)kHeadSlots * 8;
-size_t head_scratch_bytes() { return kHsSample + kHsHist + kHsMeta + kHsCand + kHsCcnt + kHsImage + kHeadBuckets + 256; }
+constexpr size_t kHsLongQ =
+    (kHsSample + kHsHist + kHsMeta + kHsCand + kHsCcnt + kHsImage + kHeadBuckets + 255) & ~(size_t)255;
+size_t head_scratch_bytes() { return kHsLongQ + (size_t)kLongQCap * 8; }
 
 static int sm_count_dev() {
     int dev = 0, sms = 0;
@@ -837,8 +876,9 @@ static int sm_count_dev() {
     return sms > 0 ? sms : 1;
 }
 
-int count_global_launches(uint64_t nbytes, bool head) {
-    return (nbytes >= kHeadMinBytes && head) ? 6 : (nbytes ? 1 : 0);
+int count_global_launches(uint64_t nbytes, bool head, bool scratch) {
+    if (!nbytes) return 0;
+    return ((nbytes >= kHeadMinBytes && head) ? 6 : 1) + (scratch ? 1 : 0);
 }
 
 cudaError_t ensure_smem_limit(const void *func, int bytes) {
@@ -876,12 +916,14 @@ cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
     a.lbegin = c.text;
     a.head = nullptr;
     a.head_disp = nullptr;
+    a.lq = nullptr;
+    a.lqn = nullptr;
     const uint64_t n = c.hi - c.lo;
     uint8_t *hs = static_cast<uint8_t *>(c.head_scratch);
     unsigned long long *image =
         hs ? reinterpret_cast<unsigned long long *>(hs + kHsSample + kHsHist + kHsMeta + kHsCand + kHsCcnt) : nullptr;
     uint8_t *image_disp = hs ? reinterpret_cast<uint8_t *>(image + kHeadSlots) : nullptr;
-    bool head = false;
+    bool head = false, sampled = false;
     if (c.head_mode == 1 && hs) {  // the head an earlier launch built
         head = true;
     } else if (c.head_mode == 0 && n >= kHeadMinBytes && hs) {
@@ -905,6 +947,15 @@ cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
         k_head_collect<<<sms * 2, 256, 0, s>>>(sample, kSampleSlots, meta, cand, ccnt, kHeadMax);
         k_head_chd<<<kHeadRegions, kChdThreads, 0, s>>>(cand, ccnt, meta, image, image_disp);
         head = true;
+        sampled = true;
+    }
+    if (hs && !sampled) {  // the deferred long-word count (the sampling memset zeroes it otherwise)
+        e = cudaMemsetAsync(hs + kHsSample + kHsHist + 32, 0, 8, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (hs) {
+        a.lq = reinterpret_cast<unsigned long long *>(hs + kHsLongQ);
+        a.lqn = reinterpret_cast<unsigned long long *>(hs + kHsSample + kHsHist + 32);
     }
     if (head) {
         a.head = image;
@@ -920,6 +971,9 @@ cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
         if (ev) cudaEventRecord(ev, s);
     if (head) k_count3<MODE_HEAD><<<(unsigned)grid, kBlock, kCountSmem, s>>>(a);
     else k_count3<MODE_LOCAL><<<(unsigned)grid, kBlock, kCountSmem, s>>>(a);
+    if (a.lq)
+        k_long_deferred<<<sms * 8, 256, 0, s>>>(a.lq, a.lqn, a.g, a.lbegin,
+                                                reinterpret_cast<const uint8_t *>(tb + c.hi));
     return cudaGetLastError();
 }
 

@@ -291,6 +291,13 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 __device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
     asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+// 16 bytes at a 16-byte aligned address as one vector load of two relaxed
+// 64-bit elements (each half single-copy atomic, as two separate loads).
+__device__ __forceinline__ uint4 ld_relaxed_v2(const void *p) {
+    unsigned long long a, b;
+    asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+    return make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
+}
 __device__ __forceinline__ uint4 ld_relaxed_u128(const uint4 *p) {
     const unsigned long long *q = reinterpret_cast<const unsigned long long *>(p);
     const unsigned long long a = ld_u64(q), b = ld_u64(q + 1);
@@ -415,9 +422,20 @@ __device__ inline void long_insert(const GTable &g, const uint8_t *w, uint64_t l
 // Words of at most 8 letters: key = the 8 lowercased bytes, zero padded,
 // little-endian (never 0).  Keys are written once (CAS from 0) and never
 // change, so a plain 64-bit load that sees a non-zero key sees the final key.
-__device__ __forceinline__ unsigned long long hash8(unsigned long long key) {
+// Slot hash of a word of at most 16 letters, given as its key halves k0 (the
+// first 8 letters) and k1 (the next 8, or 0): multiplicative (Fibonacci)
+// hashing of k0 ^ (k1 * c); a table of 2^b slots takes the top b bits.  With
+// k1 = 0 it is k0 times the golden-ratio constant.  Both global key tables
+// use it, so one probe sequence serves either key size.
+__device__ __forceinline__ unsigned long long hash_slot(unsigned long long k0, unsigned long long k1) {
     if (kOneSlot) return 0ull;
-    return key * 0x9E3779B97F4A7C15ull;  // Fibonacci hashing: use the top bits
+    return (k0 ^ (k1 * 0xC2B2AE3D27D4EB4Full)) * 0x9E3779B97F4A7C15ull;
+}
+__device__ __forceinline__ unsigned long long hash8(unsigned long long key) { return hash_slot(key, 0ull); }
+// The home slot of a 16-byte key in a table of mask + 1 (a power of two, at least 2) slots.
+__device__ __forceinline__ unsigned long long home16(uint4 k, unsigned long long mask) {
+    return hash_slot(((unsigned long long)k.y << 32) | k.x, ((unsigned long long)k.w << 32) | k.z) >>
+           __clzll((long long)mask);
 }
 __device__ __forceinline__ void red_add_u64(unsigned long long *p, unsigned long long v) { red_add_u64_dev(p, v); }
 // Probes from slot s onwards (s = the home slot, or a later slot of its chain).
@@ -466,7 +484,7 @@ __device__ __forceinline__ void global_insert16_from(const GTable &g, uint4 k, u
     atomicOr(g.status, ST_TABLE_FULL);
 }
 __device__ __forceinline__ void global_insert16(const GTable &g, uint4 k, unsigned long long add) {
-    global_insert16_from(g, k, add, hash_key(k) & g.mask);
+    global_insert16_from(g, k, add, home16(k, g.mask));
 }
 
 // Any word of at most 16 letters given as a 16-byte key.

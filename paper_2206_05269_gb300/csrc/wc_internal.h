@@ -32,7 +32,10 @@ int count_global_chunk_bytes();
 uint64_t count_global_head_min();
 // One block runs the counting kernel's bounded barrier wait (see wc_selftest_wait).
 cudaError_t launch_wait_selftest(uint32_t *d_status, uint32_t polls, int arrive, cudaStream_t s);
-int count_global_launches(uint64_t nbytes, bool head);
+// Kernel launches of one launch_count_global: head selection when `head` and
+// the text is long enough, the counting kernel, and the deferred long-word
+// inserts when head scratch is given (`scratch`).
+int count_global_launches(uint64_t nbytes, bool head, bool scratch);
 size_t head_scratch_bytes();
 
 // ---------------------------------------------------------------- numeric MapReduce
