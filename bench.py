@@ -698,6 +698,49 @@ def run_hybrid(args, local) -> dict:
     return best
 
 
+def run_mid(args, local) -> dict:
+    """Single documents of 1, 4 and 15 MB (prefixes of the 1 GB corpus),
+    counted whole by wc_count with the claim-as-you-go shared-memory table
+    these sizes use, and with it switched off (every word to the global
+    tables).  L2 is flushed before each timed count; the time is the whole
+    count (tables, kernel, compaction, sort) on the launching stream."""
+    import torch
+    import corpus
+    from paper_2206_05269_gb300 import wc
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ctr = wc.Counter(local)
+    out = {}
+    for size in (1e6, 4e6, 15e6):
+        c = corpus.generate("large", size_a=size)
+        text = torch.from_numpy(c.text).to(dev)
+        row = {"bytes": int(c.text.size)}
+        for name, nl in (("level1", 0), ("all_global", 1)):
+            ms = []
+            for rep in range(23):
+                flush.fill_(rep & 0xFF)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                t = ctr.count(text, stream, (0, 0, 0, nl))
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if t.status() != wc.WC_OK:
+                    raise RuntimeError(f"mid-size count failed: {t.status()}")
+                t.free()
+                if rep >= 3:
+                    ms.append(e0.elapsed_time(e1))
+            ms.sort()
+            med = ms[len(ms) // 2]
+            row[name] = {"ms": med, "GBps": c.text.size / (med * 1e-3) / 1e9}
+        row["speedup"] = row["all_global"]["ms"] / row["level1"]["ms"]
+        out[f"{size / 1e6:.0f}MB"] = row
+    ctr.close()
+    out["l2"] = "flushed (256 MB written) before each timed count"
+    return out
+
+
 def _sub(line: dict) -> dict:
     """The parts of a workload's own result line that the default line carries."""
     keep = ("metric", "value", "unit", "ms_per_step", "higher_is_better", "config", "input_GBps", "per_launch_docs_s",
@@ -713,7 +756,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "tiny", "classes", "batched", "served"])
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "tiny", "classes", "batched", "served", "numeric", "hybrid", "mid"])
     ap.add_argument("--cpu-sample-mb", type=float, default=400.0)
     ap.add_argument("--bytes", type=float, default=1e9, help="corpus size (smaller only for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -745,9 +789,13 @@ def main():
                                   else run_served_workload(a2, local, False))
             subs["numeric"] = run_numeric(args, local)
             subs["hybrid"] = run_hybrid(args, local)
+            subs["mid_sizes"] = run_mid(args, local)
         run_gpu(args, rank, world, local, subs)
     elif args.workload == "served":
         run_served_workload(args, local)
+    elif args.workload in ("numeric", "hybrid", "mid"):  # one sub-measurement alone (profiling)
+        fn = {"numeric": run_numeric, "hybrid": run_hybrid, "mid": run_mid}[args.workload]
+        print(json.dumps({"workload": args.workload, "result": fn(args, local)}), flush=True)
     else:
         run_docs_workload(args, local)
 

@@ -74,6 +74,9 @@ typedef struct {
     uint64_t table_slots;   /* short-word table slots (rounded up to a power of two) */
     uint64_t long_slots;    /* long-word (> 16 letters) table slots */
     uint64_t arena_bytes;   /* bytes for the distinct long words' text */
+    int no_level1;          /* 1 = no shared-memory level-1 table (every word goes to the global
+                               tables): the same result, for measuring what the level-1 table
+                               saves; 0 = default */
 } wc_count_opts;
 
 enum { WC_TABLE_DOC = 0, WC_TABLE_CLASS = 1, WC_TABLE_GLOBAL = 2 };

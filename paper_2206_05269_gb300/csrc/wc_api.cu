@@ -635,13 +635,14 @@ wc_status wc_count_ex(wc_ctx *ctx, const uint8_t *d_text, uint64_t nbytes, const
     t->src_bytes = nbytes;
     const GTable g = cs.gtable(t->dt.d_status);
     CountLaunch cl{d_text, 0, nbytes, g, 0, cs.head, {nullptr, nullptr}};
+    cl.no_level1 = opts && opts->no_level1 ? 1 : 0;
     // stages: head selection (sampling pass + head kernels), then the main counting kernel
     ctx->prof_mark(ctx->ev_head, stream);
     cl.main_ev[0] = ctx->prof_event(ctx->ev_head);
     cl.main_ev[1] = ctx->prof_event(ctx->ev_count);
     cudaError_t e = launch_count_global(cl, stream);
     ctx->prof_mark(ctx->ev_count, stream);
-    ctx->launches += count_global_launches(nbytes, true, cs.head != nullptr);
+    ctx->launches += count_global_launches(nbytes, !cl.no_level1, cs.head != nullptr);
     ctx->prof_mark(ctx->ev_finish, stream);
     const uint32_t skip = sort_skip_mask(nbytes / 2 + 1, 0);  // no count exceeds the token bound
     if (e == cudaSuccess) e = finish_table(g, cs.gcap8, cs.gcap, cs.glcap, cs.ss, t->dt, stream, skip);
@@ -724,8 +725,9 @@ wc_status wc_count_host(wc_ctx *ctx, const uint8_t *h_text, uint64_t nbytes, uin
     for (size_t i = 0; i < np && e == cudaSuccess; i++) {
         e = cudaStreamWaitEvent(stream, ev[i], 0);
         CountLaunch cl{dt, cut[i], cut[i + 1], g, 0, cs.head, {nullptr, nullptr}, i == 0 ? 0 : (head ? 1 : 2)};
+        cl.no_level1 = opts && opts->no_level1 ? 1 : 0;
         if (e == cudaSuccess) e = launch_count_global(cl, stream);
-        ctx->launches += count_global_launches(cut[i + 1] - cut[i], i == 0 && head, cs.head != nullptr);
+        ctx->launches += count_global_launches(cut[i + 1] - cut[i], i == 0 && head && !cl.no_level1, cs.head != nullptr);
     }
     const uint32_t skip = sort_skip_mask(nbytes / 2 + 1, 0);  // no count exceeds the token bound
     if (e == cudaSuccess) e = finish_table(g, cs.gcap8, cs.gcap, cs.glcap, cs.ss, t->dt, stream, skip);

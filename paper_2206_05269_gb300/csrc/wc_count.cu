@@ -86,6 +86,7 @@ struct Count2Args {
     const uint8_t *head_disp;         // HEAD image: kHeadBuckets displacements
     unsigned long long *lq;           // deferred long words (kLongQCap entries), or null: inserted in place
     unsigned long long *lqn;          // entries appended to lq (may pass kLongQCap: the rest were inserted in place)
+    int l1_off;                       // LOCAL: no level-1 table (every word to the global tables)
 };
 
 // ---------------------------------------------------------------- TMA + mbarrier
@@ -417,7 +418,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_count3(Count2Args a) {
             // one key load for every length (no divergent paths)
             tk = window_key16(w, p, len, kmask);
             tail = true;
-            if (len <= 8u) {
+            if (len <= 8u && (MODE != MODE_LOCAL || !a.l1_off)) {
                 const unsigned long long key = key_lo(tk);
                 int s;
                 if (MODE == MODE_HEAD) {
@@ -589,24 +590,84 @@ __global__ void __launch_bounds__(kBlock, 1) k_count3(Count2Args a) {
         if (scnt[i]) global_insert8(a.g, skey[i], (unsigned long long)scnt[i]);
 }
 
-// Inserts the long words k_count3 queued (Count2Args::lq), one a thread: the
-// same insertion the counting kernel makes in place, run with enough threads
-// in flight to hide the table round trips.
-__global__ void __launch_bounds__(256) k_long_deferred(const unsigned long long *lq, const unsigned long long *lqn,
-                                                       GTable g, const uint8_t *lbegin, const uint8_t *end) {
+// Inserts the long words k_count3 queued (Count2Args::lq).  A block takes
+// chunks of kDefChunk queued words, one a thread: each thread computes its
+// word's ends and hash, and the chunk's words of at most 32 letters are
+// counted in a shared table first.  Two queued words are the same word
+// exactly when hash, length and first and last 16 letters agree, since those
+// cover every letter.  The thread that claimed a word's shared slot then makes
+// its one global insert, carrying the chunk count, so a frequent long word
+// costs one table update per chunk instead of one per occurrence.  Words of
+// more than 32 letters are inserted one by one (the insert compares bytes).
+constexpr int kDefChunk = 512;  // = threads per block (two blocks per SM)
+constexpr int kDefSlots = 2 * kDefChunk;
+constexpr size_t kDefSmem = (size_t)kDefChunk * (16 + 16 + 8 + 8 + 4) + (size_t)kDefSlots * 8;
+__global__ void __launch_bounds__(kDefChunk) k_long_deferred(const unsigned long long *lq,
+                                                             const unsigned long long *lqn, GTable g,
+                                                             const uint8_t *lbegin, const uint8_t *end) {
+    extern __shared__ __align__(16) uint8_t dsm[];
+    uint4 *ef = reinterpret_cast<uint4 *>(dsm);
+    uint4 *el = ef + kDefChunk;
+    unsigned long long *eh = reinterpret_cast<unsigned long long *>(el + kDefChunk);
+    unsigned long long *ea = eh + kDefChunk;
+    uint32_t *elen = reinterpret_cast<uint32_t *>(ea + kDefChunk);
+    uint32_t *tidx = elen + kDefChunk;  // 1 + entry index, 0 = empty
+    uint32_t *tcnt = tidx + kDefSlots;
     const unsigned long long n = *lqn < kLongQCap ? *lqn : kLongQCap;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const unsigned long long e = lq[i];
-        const uint8_t *w = reinterpret_cast<const uint8_t *>(e >> 16);
-        unsigned long long len = e & 0xFFFFull;
-        if (len == 0) {  // longer than the window showed: scan to the end of the run
-            len = 17;
-            while (w + len < end && is_letter(w[len])) len++;
+    const int i = threadIdx.x;
+    for (unsigned long long c0 = (unsigned long long)blockIdx.x * kDefChunk; c0 < n;
+         c0 += (unsigned long long)gridDim.x * kDefChunk) {
+        tidx[i] = 0u;
+        tidx[i + kDefChunk] = 0u;
+        tcnt[i] = 0u;
+        tcnt[i + kDefChunk] = 0u;
+        uint32_t mylen = 0;
+        if (c0 + i < n) {
+            const unsigned long long e = lq[c0 + i];
+            const uint8_t *w = reinterpret_cast<const uint8_t *>(e >> 16);
+            unsigned long long len = e & 0xFFFFull;
+            if (len == 0) {  // longer than the window showed: scan to the end of the run
+                len = 17;
+                while (w + len < end && is_letter(w[len])) len++;
+            }
+            uint4 fl[2];
+            long_ends(w, len, fl[0], fl[1]);
+            const unsigned long long h = long_hash_mix(fl[0], fl[1], len);
+            if (len > 32) {
+                long_insert2(g, w, len, h, 1ull, lbegin, end, fl);
+            } else {
+                ef[i] = fl[0];
+                el[i] = fl[1];
+                eh[i] = h;
+                ea[i] = (unsigned long long)reinterpret_cast<uintptr_t>(w);
+                mylen = (uint32_t)len;
+            }
         }
-        uint4 fl[2];
-        long_ends(w, len, fl[0], fl[1]);
-        long_insert2(g, w, len, long_hash_mix(fl[0], fl[1], len), 1ull, lbegin, end, fl);
+        elen[i] = mylen;
+        __syncthreads();
+        // count the chunk's words in the shared table (at most half full)
+        int mine = -1;  // the slot this thread claimed
+        if (mylen) {
+            uint32_t sl = (uint32_t)(eh[i] >> 40) & (uint32_t)(kDefSlots - 1);
+            for (int probe = 0; probe < kDefSlots; probe++) {
+                uint32_t cur = tidx[sl];
+                if (cur == 0u) cur = atomicCAS(&tidx[sl], 0u, (uint32_t)i + 1u);
+                const uint32_t j = cur ? cur - 1u : (uint32_t)i;
+                if (j == (uint32_t)i || (eh[j] == eh[i] && elen[j] == mylen && key_eq(ef[j], ef[i]) &&
+                                         key_eq(el[j], el[i]))) {
+                    if (j == (uint32_t)i) mine = (int)sl;
+                    atomicAdd(&tcnt[sl], 1u);
+                    break;
+                }
+                sl = (sl + 1u) & (uint32_t)(kDefSlots - 1);
+            }
+        }
+        __syncthreads();
+        if (mine >= 0) {  // the word's one global insert, with its count in the chunk
+            const uint4 fl[2] = {ef[i], el[i]};
+            long_insert2(g, reinterpret_cast<const uint8_t *>(ea[i]), mylen, eh[i], tcnt[mine], lbegin, end, fl);
+        }
+        __syncthreads();
     }
 }
 
@@ -899,6 +960,7 @@ cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
     cudaError_t e = ensure_smem_limit((const void *)k_count3<MODE_HEAD>, (int)kCountSmem);
     if (e == cudaSuccess) e = ensure_smem_limit((const void *)k_count3<MODE_LOCAL>, (int)kCountSmem);
     if (e == cudaSuccess) e = ensure_smem_limit((const void *)k_count3<MODE_SAMPLE>, (int)kCountSmem);
+    if (e == cudaSuccess) e = ensure_smem_limit((const void *)k_long_deferred, (int)kDefSmem);
     if (e != cudaSuccess) return e;
     if (c.hi <= c.lo) return cudaSuccess;
     const int sms = sm_count_dev();
@@ -918,13 +980,15 @@ cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
     a.head_disp = nullptr;
     a.lq = nullptr;
     a.lqn = nullptr;
+    a.l1_off = c.no_level1 ? 1 : 0;
     const uint64_t n = c.hi - c.lo;
     uint8_t *hs = static_cast<uint8_t *>(c.head_scratch);
     unsigned long long *image =
         hs ? reinterpret_cast<unsigned long long *>(hs + kHsSample + kHsHist + kHsMeta + kHsCand + kHsCcnt) : nullptr;
     uint8_t *image_disp = hs ? reinterpret_cast<uint8_t *>(image + kHeadSlots) : nullptr;
     bool head = false, sampled = false;
-    if (c.head_mode == 1 && hs) {  // the head an earlier launch built
+    if (c.no_level1) {  // LOCAL kernel with its table switched off
+    } else if (c.head_mode == 1 && hs) {  // the head an earlier launch built
         head = true;
     } else if (c.head_mode == 0 && n >= kHeadMinBytes && hs) {
         // sampling pass (LOCAL tables per block, spills into the sample table)
@@ -972,8 +1036,8 @@ cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
     if (head) k_count3<MODE_HEAD><<<(unsigned)grid, kBlock, kCountSmem, s>>>(a);
     else k_count3<MODE_LOCAL><<<(unsigned)grid, kBlock, kCountSmem, s>>>(a);
     if (a.lq)
-        k_long_deferred<<<sms * 8, 256, 0, s>>>(a.lq, a.lqn, a.g, a.lbegin,
-                                                reinterpret_cast<const uint8_t *>(tb + c.hi));
+        k_long_deferred<<<sms * 2, kDefChunk, kDefSmem, s>>>(a.lq, a.lqn, a.g, a.lbegin,
+                                                            reinterpret_cast<const uint8_t *>(tb + c.hi));
     return cudaGetLastError();
 }
 

@@ -25,6 +25,7 @@ struct CountLaunch {
     cudaEvent_t main_ev[2];  // recorded (when non-null) right before the main counting kernel
     int head_mode;           // 0: build a head (texts >= count_global_head_min()); 1: reuse the
                              // head an earlier launch built in head_scratch; 2: no head
+    int no_level1;           // 1: no shared-memory level-1 table at all (measurement)
 };
 // Tokenises and counts text[lo, hi) into g (8-byte, 16-byte and long tables).
 cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s);

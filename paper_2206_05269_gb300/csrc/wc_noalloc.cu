@@ -39,7 +39,7 @@ constexpr uint64_t kBytesLong = round256(kNaCapLong * sizeof(wc::LSlot));
 // lref, 2 permutations, doc, the digit histograms, tile histograms, pass
 // cursors, group counts, the look-back buffers and tile counters), each
 // carved at a 256-byte boundary.
-constexpr uint64_t kNaTiles = (kNaEntries + 4095) / 4096;
+constexpr uint64_t kNaTiles = (kNaEntries + wc::kSortTileElems - 1) / wc::kSortTileElems;
 constexpr uint64_t kSortBytes = kNaEntries * (8 + 8 + 8 + 8 + 4 + 4 + 4 + 4 + 4) + 4 * wc::kSortPassesSeg * 256 +
                                 4 * 256 * kNaTiles + 4 * 32 + 2 * 4 * 256 * wc::sort_group_stride(kNaTiles) + 4096 +
                                 2 * (4 * 256 * kNaTiles + 256) + 256 + 20 * kR;

@@ -500,13 +500,17 @@ __global__ void __launch_bounds__(kSortThreads) k_pass_scatter(J job, int p, int
 // of the other parity's look-back buffer and block 0 the other tile counter,
 // for the next pass.
 constexpr uint32_t kLookAgg = 1u << 30, kLookInc = 2u << 30, kLookVal = kLookAgg - 1u;
-constexpr uint32_t kLookSpins = 1u << 24;
-__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+constexpr uint32_t kLookSpins = 1u << 22;  // look-back rounds before giving up
+constexpr int kLookWin = 8;                // earlier tiles read per round
+// A published word carries its flag and value together, and nothing else is
+// read on its account (the next pass is ordered by the kernel boundary), so
+// relaxed GPU-scope accesses suffice.
+__device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
     uint32_t v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 template <class J>
@@ -572,22 +576,35 @@ __global__ void __launch_bounds__(kSortThreads) k_pass_one(J job, int p, int e, 
     uint32_t *look = s.look_buf(par);
     uint32_t excl = 0;
     if (tile == 0) {
-        st_release_u32(&look[d], kLookInc | cnt);
+        st_relaxed_u32(&look[d], kLookInc | cnt);
     } else {
-        st_release_u32(&look[(unsigned long long)tile * 256 + d], kLookAgg | cnt);
-        for (long long t = (long long)tile - 1; t >= 0; t--) {
-            uint32_t v = 0, spins = 0;
-            do {
-                v = ld_acquire_u32(&look[(unsigned long long)t * 256 + d]);
-            } while (!(v & (kLookAgg | kLookInc)) && ++spins < kLookSpins);
-            if (!(v & (kLookAgg | kLookInc))) {  // gave up: recorded, the order is not used
+        st_relaxed_u32(&look[(unsigned long long)tile * 256 + d], kLookAgg | cnt);
+        // look back kLookWin tiles per round trip: add published counts from
+        // the nearest tile down until one carries a complete prefix; a tile not
+        // yet published ends the round, and the next round starts from it
+        long long t = (long long)tile - 1;
+        uint32_t rounds = 0;
+        bool done = false;
+        while (!done) {
+            uint32_t v[kLookWin];
+#pragma unroll
+            for (int j = 0; j < kLookWin; j++)
+                v[j] = t - j >= 0 ? ld_relaxed_u32(&look[(unsigned long long)(t - j) * 256 + d]) : 0u;
+            int j = 0;
+#pragma unroll
+            for (; j < kLookWin; j++) {
+                if (!(v[j] & (kLookAgg | kLookInc))) break;
+                excl += v[j] & kLookVal;
+                if (v[j] & kLookInc) { done = true; break; }
+            }
+            if (done) break;
+            t -= j;
+            if (++rounds >= kLookSpins) {  // gave up: recorded, the order is not used
                 atomicOr(&s.cur[kCurSortError], 1u);
                 break;
             }
-            excl += v & kLookVal;
-            if (v & kLookInc) break;
         }
-        st_release_u32(&look[(unsigned long long)tile * 256 + d], kLookInc | (excl + cnt));
+        st_relaxed_u32(&look[(unsigned long long)tile * 256 + d], kLookInc | (excl + cnt));
     }
     // this tile's first position for digit d: the entries with a smaller
     // digit (the all-pass histogram) plus digit d's entries in earlier tiles

@@ -61,7 +61,7 @@ class WcConfig(ctypes.Structure):
 
 class WcCountOpts(ctypes.Structure):
     _fields_ = [("table_slots", ctypes.c_uint64), ("long_slots", ctypes.c_uint64),
-                ("arena_bytes", ctypes.c_uint64)]
+                ("arena_bytes", ctypes.c_uint64), ("no_level1", ctypes.c_int)]
 
 
 _lib = None
@@ -620,16 +620,17 @@ class Counter:
         """count() that waits for the result and recounts with 4x capacities on
         WC_ERR_CAPACITY (the input is still alive, so a recount is exact)."""
         opts = tuple(opts) if opts else (0, 0, 0)
+        caps, rest = opts[:3], opts[3:]  # capacity hints; the no_level1 flag is kept as given
         for _ in range(retries + 1):
-            t = self.count(text, stream, opts)
+            t = self.count(text, stream, caps + rest)
             st = t.status()
             if st != WC_ERR_CAPACITY:
                 _check(st, self.ctx, "count")
                 return t
             n = text.numel()
             t.free()
-            base = opts if any(opts) else (max(1024, n // 4), max(256, n // 64), max(4096, n // 8))
-            opts = tuple(max(1, int(v)) * 4 for v in base)
+            base = caps if any(caps) else (max(1024, n // 4), max(256, n // 64), max(4096, n // 8))
+            caps = tuple(max(1, int(v)) * 4 for v in base)
         raise WcError(WC_ERR_CAPACITY, "capacity retries exhausted")
 
     def count_batched(self, text, offsets, h_offsets, classes=None, nclasses: int = 0, stream=None,

@@ -109,6 +109,52 @@ def test_large_recipe_64mb(ctr):
     check(ctr, c.text.tobytes(), what="large recipe, 64 MB")
 
 
+_MID = {}
+
+
+@pytest.mark.parametrize("no_level1", [0, 1])
+@pytest.mark.parametrize("size", [1e6, 4e6, 15e6])
+def test_mid_sizes_with_and_without_level1(ctr, size, no_level1):
+    """Single documents under 16 MB are counted with the claim-as-you-go
+    shared-memory table (no sampling pass); at 1, 4 and 15 MB the table, and
+    the all-global path with it switched off, equal the oracle."""
+    if size not in _MID:
+        c = corpus.generate("large", size_a=size)
+        _MID[size] = (c.text.tobytes(), oracle.count(c.text).glob())
+    data, want = _MID[size]
+    t = ctr.count_checked(to_dev(data), opts=(0, 0, 0, no_level1))
+    assert_same(t.export(), want, f"{size / 1e6:.0f} MB, no_level1={no_level1}")
+
+
+def test_two_contexts_from_two_host_threads():
+    """Two contexts, created and used from two host threads at once (kernel
+    attributes are set per device under a lock), both count exactly."""
+    import threading
+    from paper_2206_05269_gb300 import wc
+    texts = [corpus.generate("large", size_a=s).text.tobytes() for s in (20e6, 6e6)]
+    results, errors = [None, None], []
+
+    def work(i):
+        try:
+            c = wc.Counter(0)
+            for _ in range(3):
+                t = c.count_checked(to_dev(texts[i]))
+                results[i] = t.export()
+                t.free()
+            c.close()
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    th = [threading.Thread(target=work, args=(i,)) for i in range(2)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    assert not errors, errors
+    for i in range(2):
+        assert_same(results[i], oracle.count(texts[i]).glob(), f"thread {i}")
+
+
 def test_large_full_size_against_generator_truth(ctr):
     """The 1e9-byte workload as the benchmark runs it, checked in full against
     the generator's tally (which the oracle is pinned to) and the token count."""
