@@ -443,7 +443,7 @@ wc_status table_sync(const wc_table *ct) {
         wc_ctx *c = t->ctx;
         c->hist_bytes = t->src_bytes;
         c->hist_n8 = meta[5];
-        c->hist_n16 = meta[6] - meta[5];
+        c->hist_n16 = meta[6];
         c->hist_nlong = meta[1];
         c->hist_arena = meta[2];
     }

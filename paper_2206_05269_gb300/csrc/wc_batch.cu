@@ -836,7 +836,7 @@ cudaError_t launch_segmented_finish(const BatchArgs &a, const GTable &g, uint64_
     return cudaGetLastError();
 }
 int segmented_finish_launches(uint64_t cap, uint32_t skip) {
-    return 3 + sort_entries_launches(kSortPassesSeg, cap, skip) + 3;
+    return 4 + sort_entries_launches(kSortPassesSeg, cap, skip) + 3;
 }
 
 }  // namespace wc

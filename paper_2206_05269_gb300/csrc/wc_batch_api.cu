@@ -1326,7 +1326,7 @@ static wc_status build_vocab(wc_batch *b) {
         k_vocab_ids<<<grid, 256, 0, s>>>(b->args, vg, static_cast<uint32_t *>(ids), b->entries);
         e = cudaGetLastError();
     }
-    ctx->launches += 3 + (uint64_t)sort_entries_launches(kSortPasses, cs.ss.cap, sort_skip_mask(0, 0));
+    ctx->launches += 4 + (uint64_t)sort_entries_launches(kSortPasses, cs.ss.cap, sort_skip_mask(0, 0));
     ctx->release(dmeta, 64, s);
     ctx->release(cs.mem, cs.bytes, s);
     table_mark_done(V, s);

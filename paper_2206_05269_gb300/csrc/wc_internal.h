@@ -155,7 +155,8 @@ cudaError_t finish_table(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_
 // Compaction scans read kScanUnroll slots a thread per step (independent
 // loads in flight) and reserve output positions with one atomic per block
 // and step: block_take returns the first of `mine` positions reserved for
-// the calling thread and adds the block's `tok` to *tokens (may be null).
+// the calling thread and adds the block's `tok` to *tokens and its count of
+// positions to *kind (either may be null).
 // Every thread of the block must call it (the loops step block-uniformly).
 constexpr int kScanUnroll = 4;
 struct BlockTake {
@@ -164,7 +165,8 @@ struct BlockTake {
     unsigned long long base;
 };
 __device__ __forceinline__ unsigned long long block_take(BlockTake &sh, uint32_t mine, unsigned long long tok,
-                                                         unsigned long long *counter, unsigned long long *tokens) {
+                                                         unsigned long long *counter, unsigned long long *tokens,
+                                                         unsigned long long *kind = nullptr) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
     uint32_t incl = mine;
 #pragma unroll
@@ -188,6 +190,7 @@ __device__ __forceinline__ unsigned long long block_take(BlockTake &sh, uint32_t
         }
         sh.base = run ? atomicAdd(counter, (unsigned long long)run) : 0ull;
         if (tokens && tt) atomicAdd(tokens, tt);
+        if (kind && run) atomicAdd(kind, (unsigned long long)run);
     }
     __syncthreads();
     const unsigned long long pos = sh.base + sh.wsum[warp] + incl - mine;

@@ -68,12 +68,44 @@ void sort_scratch_carve(SortScratch &s, void *base, uint64_t cap) {
 }
 
 // ---------------------------------------------------------------- compaction
-// Occupied 16-byte-key slots -> entries (big-endian key halves).
-__global__ void k_compact_short(const GSlot *slots, unsigned long long cap, SortScratch ss,
-                                unsigned long long *meta) {
+// The sort's key for an entry: the 16-letter prefix packed 5 bits a letter
+// (80 bits: pk low 64, pk2 high 16) and the count inverted (descending), and
+// the counts of each of their digits in a block's histogram h (one row of 256
+// per pass), from which a pass with a single digit value is skipped.
+__device__ __forceinline__ void sort_key_prep(const SortScratch &s, unsigned long long i, unsigned long long khi,
+                                              unsigned long long klo, unsigned long long cnt, uint32_t *h) {
+    const unsigned long long ph = pack5(khi), pl = pack5(klo), c = ~cnt;
+    const unsigned long long lo = (ph << 40) | pl;  // the 80-bit code: ph:pl
+    const uint32_t hi = (uint32_t)(ph >> 24);
+    s.perm[0][i] = (uint32_t)i;
+    s.pk[i] = lo;
+    s.pk2[i] = hi;
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+        atomicAdd(&h[b * 256 + ((lo >> (8 * b)) & 0xFF)], 1u);
+        atomicAdd(&h[(kSortKeyPasses + b) * 256 + ((c >> (8 * b)) & 0xFF)], 1u);
+    }
+    atomicAdd(&h[8 * 256 + (hi & 0xFF)], 1u);
+    atomicAdd(&h[9 * 256 + ((hi >> 8) & 0xFF)], 1u);
+}
+
+// One entry of a compaction; with h (the fused compaction of a single
+// table's finish) also its sort key and digit counts.
+__device__ __forceinline__ void emit_entry(const SortScratch &ss, unsigned long long pos, unsigned long long khi,
+                                           unsigned long long klo, unsigned long long cnt, uint32_t lref, uint32_t *h) {
+    ss.khi[pos] = khi;
+    ss.klo[pos] = klo;
+    ss.cnt[pos] = cnt;
+    ss.lref[pos] = lref;
+    if (h) sort_key_prep(ss, pos, khi, klo, cnt, h);
+}
+
+// Occupied 16-byte-key slots -> entries (big-endian key halves); block bid of nb.
+__device__ __forceinline__ void compact_short_body(const GSlot *slots, unsigned long long cap, const SortScratch &ss,
+                                                   unsigned long long *meta, unsigned bid, unsigned nb, uint32_t *h) {
     __shared__ BlockTake sh;
-    const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x * kScanUnroll;
-    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x * kScanUnroll; b < cap; b += step) {
+    const unsigned long long step = (unsigned long long)nb * blockDim.x * kScanUnroll;
+    for (unsigned long long b = (unsigned long long)bid * blockDim.x * kScanUnroll; b < cap; b += step) {
         uint4 k[kScanUnroll];
         unsigned long long c[kScanUnroll], tok = 0;
         uint32_t mine = 0;
@@ -91,24 +123,22 @@ __global__ void k_compact_short(const GSlot *slots, unsigned long long cap, Sort
                 tok += c[u];
             }
         }
-        unsigned long long pos = block_take(sh, mine, tok, &meta[0], &meta[3]);
+        unsigned long long pos = block_take(sh, mine, tok, &meta[0], &meta[3], &meta[6]);
 #pragma unroll
         for (int u = 0; u < kScanUnroll; u++) {
             if (key_zero(k[u])) continue;
-            ss.khi[pos] = be64(k[u].x, k[u].y);
-            ss.klo[pos] = be64(k[u].z, k[u].w);
-            ss.cnt[pos] = c[u];
-            ss.lref[pos] = 0u;
+            emit_entry(ss, pos, be64(k[u].x, k[u].y), be64(k[u].z, k[u].w), c[u], 0u, h);
             pos++;
         }
     }
 }
 
-// Occupied 8-byte-key slots -> entries.
-__global__ void k_compact8(const G8Slot *slots, unsigned long long cap, SortScratch ss, unsigned long long *meta) {
+// Occupied 8-byte-key slots -> entries; block bid of nb.
+__device__ __forceinline__ void compact8_body(const G8Slot *slots, unsigned long long cap, const SortScratch &ss,
+                                              unsigned long long *meta, unsigned bid, unsigned nb, uint32_t *h) {
     __shared__ BlockTake sh;
-    const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x * kScanUnroll;
-    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x * kScanUnroll; b < cap; b += step) {
+    const unsigned long long step = (unsigned long long)nb * blockDim.x * kScanUnroll;
+    for (unsigned long long b = (unsigned long long)bid * blockDim.x * kScanUnroll; b < cap; b += step) {
         ulonglong2 v[kScanUnroll];
         unsigned long long tok = 0;
         uint32_t mine = 0;
@@ -121,15 +151,12 @@ __global__ void k_compact8(const G8Slot *slots, unsigned long long cap, SortScra
                 tok += v[u].y;
             }
         }
-        unsigned long long pos = block_take(sh, mine, tok, &meta[0], &meta[3]);
+        unsigned long long pos = block_take(sh, mine, tok, &meta[0], &meta[3], &meta[5]);
 #pragma unroll
         for (int u = 0; u < kScanUnroll; u++) {
             const unsigned long long key = v[u].x;
             if (!key) continue;
-            ss.khi[pos] = be64((uint32_t)key, (uint32_t)(key >> 32));
-            ss.klo[pos] = 0ull;
-            ss.cnt[pos] = v[u].y;
-            ss.lref[pos] = 0u;
+            emit_entry(ss, pos, be64((uint32_t)key, (uint32_t)(key >> 32)), 0ull, v[u].y, 0u, h);
             pos++;
         }
     }
@@ -148,11 +175,12 @@ __device__ __forceinline__ uint32_t byte16(uint4 v, uint32_t i) {
 // and by the whole warp beyond, and emits an entry.  A word of at most 32
 // letters whose slot holds its first and last 16 letters (kLongReady) is
 // written from the slot, without reading its occurrence in the text.
-__global__ void k_compact_long(const LSlot *ls, unsigned long long lcap, SortScratch ss, DevTable out) {
+__device__ __forceinline__ void compact_long_body(const LSlot *ls, unsigned long long lcap, const SortScratch &ss,
+                                                  const DevTable &out, unsigned bid, unsigned nb, uint32_t *hist) {
     const int lane = threadIdx.x & 31;
-    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    const unsigned long long nw = ((unsigned long long)nb * blockDim.x) >> 5;
     unsigned long long *meta = out.d_meta;
-    for (unsigned long long w0 = (((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < lcap;
+    for (unsigned long long w0 = (((unsigned long long)bid * blockDim.x + threadIdx.x) >> 5) * 32; w0 < lcap;
          w0 += nw * 32) {
         const unsigned long long w = w0 + lane;
         unsigned long long h = 0, addr = 0, len = 0, c = 0, lr = 0;
@@ -225,11 +253,33 @@ __global__ void k_compact_long(const LSlot *ls, unsigned long long lcap, SortScr
                 for (int j = 0; j < 8; j++) hi = (hi << 8) | (unsigned long long)(src[j] | 0x20u);
                 for (int j = 8; j < 16; j++) lo = (lo << 8) | (unsigned long long)(src[j] | 0x20u);
             }
-            ss.khi[pos] = hi;
-            ss.klo[pos] = lo;
-            ss.cnt[pos] = c;
-            ss.lref[pos] = full ? 0u : (uint32_t)(lidx + 1);
+            emit_entry(ss, pos, hi, lo, c, full ? 0u : (uint32_t)(lidx + 1), hist);
         }
+    }
+}
+
+// All three tables' occupied slots -> entries in one launch: blocks
+// [0, nb8) scan the 8-byte table, the next nb16 the 16-byte table and the
+// rest the long-word table.  The per-kind entry counts go to meta[5] (8-byte)
+// and meta[6] (16-byte).  With `hist` (a single table's finish) the entries'
+// sort keys and digit histograms are taken here as well, for the sort's passes.
+__global__ void __launch_bounds__(256) k_compact_all(GTable g, unsigned long long cap8, unsigned long long cap16,
+                                                     unsigned long long lcap, SortScratch ss, DevTable out,
+                                                     unsigned nb8, unsigned nb16, int hist) {
+    __shared__ uint32_t h[kPasses * 256];
+    if (hist) {
+        for (int i = threadIdx.x; i < kPasses * 256; i += blockDim.x) h[i] = 0u;
+        __syncthreads();
+    }
+    uint32_t *hp = hist ? h : nullptr;
+    const unsigned b = blockIdx.x;
+    if (b < nb8) compact8_body(g.slots8, cap8, ss, out.d_meta, b, nb8, hp);
+    else if (b < nb8 + nb16) compact_short_body(g.slots, cap16, ss, out.d_meta, b - nb8, nb16, hp);
+    else compact_long_body(g.lslots, lcap, ss, out, b - nb8 - nb16, gridDim.x - nb8 - nb16, hp);
+    if (hist) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < kPasses * 256; i += blockDim.x)
+            if (h[i]) atomicAdd(&ss.hist_all[i], h[i]);
     }
 }
 
@@ -265,19 +315,7 @@ __global__ void k_hist_all(J job, int passes) {
     const unsigned long long n = meta[0];
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
-        s.perm[0][i] = (uint32_t)i;
-        const unsigned long long ph = pack5(s.khi[i]), pl = pack5(s.klo[i]), c = ~s.cnt[i];
-        const unsigned long long lo = (ph << 40) | pl;  // the 80-bit code: ph:pl
-        const uint32_t hi = (uint32_t)(ph >> 24);
-        s.pk[i] = lo;
-        s.pk2[i] = hi;
-#pragma unroll
-        for (int b = 0; b < 8; b++) {
-            atomicAdd(&h[b * 256 + ((lo >> (8 * b)) & 0xFF)], 1u);
-            atomicAdd(&h[(kSortKeyPasses + b) * 256 + ((c >> (8 * b)) & 0xFF)], 1u);
-        }
-        atomicAdd(&h[8 * 256 + (hi & 0xFF)], 1u);
-        atomicAdd(&h[9 * 256 + ((hi >> 8) & 0xFF)], 1u);
+        sort_key_prep(s, i, s.khi[i], s.klo[i], s.cnt[i], h);
         if (passes > kPasses) {
             const uint32_t d = s.doc[i];
 #pragma unroll
@@ -750,16 +788,16 @@ static int grid_for(unsigned long long n, int threads, int max_blocks) {
     return (int)g;
 }
 
-// meta[slot] = meta[0] (entries so far): per-kind counts for capacity hints
-__global__ void k_meta_snapshot(unsigned long long *meta, int slot) { meta[slot] = meta[0]; }
+// reset + fused compaction + the sort without its key pass + gather
+int finish_table_launches(uint64_t cap, uint32_t skip) { return 2 + sort_entries_launches(kPasses, cap, skip) - 1 + 1; }
 
-int finish_table_launches(uint64_t cap, uint32_t skip) { return 5 + sort_entries_launches(kPasses, cap, skip) + 1; }
-
-// The passes of one sort, for one table (J = OneJob) or a list of them.
+// The passes of one sort, for one table (J = OneJob) or a list of them;
+// keyed: the compaction has prepared the sort keys and histograms already.
 template <class J>
-static void launch_sort(const J &job, uint64_t cap, int ntab, int passes, uint32_t skip, cudaStream_t st) {
+static void launch_sort(const J &job, uint64_t cap, int ntab, int passes, uint32_t skip, cudaStream_t st,
+                        bool keyed = false) {
     const int sms = sm_count();
-    k_hist_all<<<dim3(grid_for(cap, 256, sms * 2), ntab), 256, 0, st>>>(job, passes);
+    if (!keyed) k_hist_all<<<dim3(grid_for(cap, 256, sms * 2), ntab), 256, 0, st>>>(job, passes);
     const int ntiles = (int)((cap + kSortTile - 1) / kSortTile);
     const int fused = (uint64_t)ntiles <= kSortFusedMaxTiles;
     int lastp = -1;
@@ -811,38 +849,51 @@ uint32_t sort_skip_mask(uint64_t max_count, uint64_t ndocs) {
     return m;
 }
 
-void sort_state_reset(SortScratch &ss, cudaStream_t st) {
-    const uint64_t ntiles = (ss.cap + kSortTile - 1) / kSortTile;
-    cudaMemsetAsync(ss.hist_all, 0, 4 * kPassesSeg * 256, st);
-    cudaMemsetAsync(ss.cur, 0, 4 * 32, st);
-    cudaMemsetAsync(ss.group_hist[0], 0, 2 * 4 * 256 * (size_t)ss.group_stride, st);
-    cudaMemsetAsync(ss.look[0], 0, 4 * 256 * (size_t)ntiles, st);
-    cudaMemsetAsync(ss.tile_ctr, 0, 4 * 2, st);
+// Zeroes a sort's state in one launch: the digit histograms, the pass
+// order words, the group histograms, the first look-back buffer and the tile
+// counters (the second look-back buffer is zeroed by the first pass).
+__global__ void k_sort_reset(SortScratch ss, uint64_t nlook) {
+    const uint64_t n0 = (uint64_t)kPassesSeg * 256, n1 = n0 + 32, n2 = n1 + 2ull * 256 * ss.group_stride,
+                   n3 = n2 + nlook, n4 = n3 + 2;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (uint64_t)gridDim.x * blockDim.x) {
+        if (i < n0) ss.hist_all[i] = 0u;
+        else if (i < n1) ss.cur[i - n0] = 0u;
+        else if (i < n2) ss.group_hist[0][i - n1] = 0u;
+        else if (i < n3) ss.look[0][i - n2] = 0u;
+        else ss.tile_ctr[i - n3] = 0u;
+    }
 }
 
+void sort_state_reset(SortScratch &ss, cudaStream_t st) {
+    const uint64_t ntiles = (ss.cap + kSortTile - 1) / kSortTile;
+    const uint64_t n = (uint64_t)kPassesSeg * 256 + 32 + 2ull * 256 * ss.group_stride + 256 * ntiles + 2;
+    k_sort_reset<<<grid_for(n, 256, sm_count() * 2), 256, 0, st>>>(ss, 256 * ntiles);
+}
+
+// Resets the sort state and compacts the three tables in one launch (with
+// `keyed`, also preparing the sort keys and histograms).
 static void launch_compaction(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_t glcap, SortScratch &ss,
-                              DevTable &out, cudaStream_t st) {
+                              DevTable &out, cudaStream_t st, bool keyed) {
     const int sms = sm_count();
     sort_state_reset(ss, st);
-    k_compact8<<<grid_for(gcap8, 256 * kScanUnroll, sms * 8), 256, 0, st>>>(g.slots8, gcap8, ss, out.d_meta);
-    k_meta_snapshot<<<1, 1, 0, st>>>(out.d_meta, 5);
-    k_compact_short<<<grid_for(gcap, 256 * kScanUnroll, sms * 8), 256, 0, st>>>(g.slots, gcap, ss, out.d_meta);
-    k_meta_snapshot<<<1, 1, 0, st>>>(out.d_meta, 6);
-    k_compact_long<<<grid_for(glcap, 256, sms * 8), 256, 0, st>>>(g.lslots, glcap, ss, out);
+    const int nb8 = grid_for(gcap8, 256 * kScanUnroll, sms * 8), nb16 = grid_for(gcap, 256 * kScanUnroll, sms * 8),
+              nbl = grid_for(glcap, 256, sms * 8);
+    k_compact_all<<<nb8 + nb16 + nbl, 256, 0, st>>>(g, gcap8, gcap, glcap, ss, out, (unsigned)nb8, (unsigned)nb16,
+                                                    keyed ? 1 : 0);
 }
 
 cudaError_t finish_table(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_t glcap, SortScratch &ss,
                          DevTable &out, cudaStream_t st, uint32_t skip) {
-    launch_compaction(g, gcap8, gcap, glcap, ss, out, st);
+    launch_compaction(g, gcap8, gcap, glcap, ss, out, st, true);
     OneJob job{SortJob{ss, out.d_meta, LongView{ss.lref, out.loff, out.llen, out.arena}, out}};
-    launch_sort(job, ss.cap, 1, kPasses, skip, st);
+    launch_sort(job, ss.cap, 1, kPasses, skip, st, true);
     k_gather_final<<<grid_for(ss.cap, 256 * kScanUnroll, sm_count() * 8), 256, 0, st>>>(job);
     return cudaGetLastError();
 }
 
 size_t finish_tables_job_bytes(int n) { return sizeof(SortJob) * (size_t)(n > 0 ? n : 1); }
 int finish_tables_launches(int n, uint64_t cap, uint32_t skip) {
-    return 5 * n + sort_entries_launches(kPasses, cap, skip) + 1;
+    return 2 * n + sort_entries_launches(kPasses, cap, skip) + 1;
 }
 
 cudaError_t finish_tables(const FinishSpec *spec, int n, void *d_jobs, cudaStream_t st, uint32_t skip) {
@@ -851,7 +902,7 @@ cudaError_t finish_tables(const FinishSpec *spec, int n, void *d_jobs, cudaStrea
     uint64_t cap = 0;
     for (int t = 0; t < n; t++) {
         const FinishSpec &f = spec[t];
-        launch_compaction(f.g, f.gcap8, f.gcap, f.glcap, *f.ss, *f.out, st);
+        launch_compaction(f.g, f.gcap8, f.gcap, f.glcap, *f.ss, *f.out, st, false);
         jobs[t] = SortJob{*f.ss, f.out->d_meta, LongView{f.ss->lref, f.out->loff, f.out->llen, f.out->arena}, *f.out};
         cap = std::max<uint64_t>(cap, f.ss->cap);
     }
