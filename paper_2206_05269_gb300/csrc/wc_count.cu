@@ -329,6 +329,10 @@ static_assert(kCountSmem <= 227 * 1024, "counting kernel shared memory");
 template <int MODE>
 __global__ void __launch_bounds__(kBlock, 1) k_count3(Count2Args a) {
     extern __shared__ __align__(128) uint8_t smem[];
+    // an ordinary launch (measured: as a dependent of the head kernels, with
+    // its blocks scheduled early, the kernel ran about 1 % slower); no early
+    // trigger, so the deferred long-word kernel launches as its blocks exit
+    grid_dependency_wait();
     unsigned long long *skey = reinterpret_cast<unsigned long long *>(smem);
     uint32_t *scnt = reinterpret_cast<uint32_t *>(smem + kSmemKeys);
     uint8_t *sdisp = smem + kSmemKeys + kSmemCnts;
@@ -606,6 +610,8 @@ __global__ void __launch_bounds__(kDefChunk) k_long_deferred(const unsigned long
                                                              const unsigned long long *lqn, GTable g,
                                                              const uint8_t *lbegin, const uint8_t *end) {
     extern __shared__ __align__(16) uint8_t dsm[];
+    grid_dependency_wait();  // the counting kernel's queue
+    grid_dependency_trigger();
     uint4 *ef = reinterpret_cast<uint4 *>(dsm);
     uint4 *el = ef + kDefChunk;
     unsigned long long *eh = reinterpret_cast<unsigned long long *>(el + kDefChunk);
@@ -675,6 +681,8 @@ __global__ void __launch_bounds__(kDefChunk) k_long_deferred(const unsigned long
 // Histogram of sample counts (clamped to 4095).
 __global__ void k_head_hist(const G8Slot *s, unsigned long long cap, uint32_t *hist) {
     __shared__ uint32_t h[4096];
+    grid_dependency_wait();
+    grid_dependency_trigger();
     for (int i = threadIdx.x; i < 4096; i += blockDim.x) h[i] = 0;
     __syncthreads();
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
@@ -692,6 +700,8 @@ __global__ void k_head_hist(const G8Slot *s, unsigned long long cap, uint32_t *h
 __global__ void __launch_bounds__(1024) k_head_threshold(const uint32_t *hist, uint32_t kmax, uint32_t *meta) {
     __shared__ uint32_t part[1024];
     __shared__ uint32_t best, hot;
+    grid_dependency_wait();
+    grid_dependency_trigger();
     const uint32_t t = threadIdx.x;
     // bins of thread t, from high counts down: 4095-4t .. 4092-4t
     uint32_t v[4], s = 0;
@@ -731,6 +741,8 @@ __global__ void __launch_bounds__(1024) k_head_threshold(const uint32_t *hist, u
 
 __global__ void k_head_collect(const G8Slot *s, unsigned long long cap, uint32_t *meta, unsigned long long *cand,
                                uint32_t *ccnt, uint32_t kmax) {
+    grid_dependency_wait();
+    grid_dependency_trigger();
     const uint32_t t = meta[0];
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
          i += (unsigned long long)gridDim.x * blockDim.x) {
@@ -805,6 +817,8 @@ __global__ void __launch_bounds__(kChdThreads) k_head_chd(const unsigned long lo
                                                           const uint32_t *meta, unsigned long long *image,
                                                           uint8_t *disp) {
     __shared__ unsigned long long sel[kRegionSlots], rkey[kRegionSlots], rimage[kRegionSlots];
+    grid_dependency_wait();
+    grid_dependency_trigger();
     __shared__ uint32_t selb[kRegionSlots];  // local bucket, bit 31: hot
     __shared__ uint32_t bsize[kRegionBuckets], bstart[kRegionBuckets], bfill[kRegionBuckets];
     __shared__ uint32_t used[kRegionSlots / 32];
@@ -1006,10 +1020,13 @@ cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
         sa.piece_stride = (span / kSamplePieces) & ~(unsigned long long)15;
         sa.nstrips = (unsigned long long)sa.piece_strips * kSamplePieces;
         k_count3<MODE_SAMPLE><<<sms, kBlock, kCountSmem, s>>>(sa);
-        k_head_hist<<<sms, 256, 0, s>>>(sample, kSampleSlots, hist);
-        k_head_threshold<<<1, 1024, 0, s>>>(hist, kHeadMax, meta);
-        k_head_collect<<<sms * 2, 256, 0, s>>>(sample, kSampleSlots, meta, cand, ccnt, kHeadMax);
-        k_head_chd<<<kHeadRegions, kChdThreads, 0, s>>>(cand, ccnt, meta, image, image_disp);
+        // each head kernel overlaps its launch with the tail of the one before
+        launch_dependent(k_head_hist, dim3(sms), dim3(256), 0, s, (const G8Slot *)sample, kSampleSlots, hist);
+        launch_dependent(k_head_threshold, dim3(1), dim3(1024), 0, s, (const uint32_t *)hist, kHeadMax, meta);
+        launch_dependent(k_head_collect, dim3(sms * 2), dim3(256), 0, s, (const G8Slot *)sample, kSampleSlots, meta,
+                         cand, ccnt, kHeadMax);
+        launch_dependent(k_head_chd, dim3(kHeadRegions), dim3(kChdThreads), 0, s, (const unsigned long long *)cand,
+                         (const uint32_t *)ccnt, (const uint32_t *)meta, image, image_disp);
         head = true;
         sampled = true;
     }
@@ -1036,8 +1053,8 @@ cudaError_t launch_count_global(const CountLaunch &c, cudaStream_t s) {
     if (head) k_count3<MODE_HEAD><<<(unsigned)grid, kBlock, kCountSmem, s>>>(a);
     else k_count3<MODE_LOCAL><<<(unsigned)grid, kBlock, kCountSmem, s>>>(a);
     if (a.lq)
-        k_long_deferred<<<sms * 2, kDefChunk, kDefSmem, s>>>(a.lq, a.lqn, a.g, a.lbegin,
-                                                            reinterpret_cast<const uint8_t *>(tb + c.hi));
+        launch_dependent(k_long_deferred, dim3(sms * 2), dim3(kDefChunk), kDefSmem, s, (const unsigned long long *)a.lq,
+                         (const unsigned long long *)a.lqn, a.g, a.lbegin, reinterpret_cast<const uint8_t *>(tb + c.hi));
     return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 // Host-side declarations shared by the library's translation units.
 #pragma once
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "wc_device.cuh"
@@ -38,6 +39,33 @@ cudaError_t launch_wait_selftest(uint32_t *d_status, uint32_t polls, int arrive,
 // inserts when head scratch is given (`scratch`).
 int count_global_launches(uint64_t nbytes, bool head, bool scratch);
 size_t head_scratch_bytes();
+
+// ---------------------------------------------------------------- dependent launches
+// A kernel launched with launch_dependent may have its blocks scheduled
+// before the previous kernel in the stream has finished; it must call
+// grid_dependency_wait() before touching anything that kernel (or earlier
+// work) reads or writes.  grid_dependency_trigger() lets the next dependent
+// launch start once every block of the calling kernel has called it.  Both
+// are no-ops for ordinary launches.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependency_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                             Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // ---------------------------------------------------------------- numeric MapReduce
 // Blocks of the series sum for n terms, and its two launches (per-block

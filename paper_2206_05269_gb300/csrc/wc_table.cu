@@ -267,6 +267,8 @@ __global__ void __launch_bounds__(256) k_compact_all(GTable g, unsigned long lon
                                                      unsigned long long lcap, SortScratch ss, DevTable out,
                                                      unsigned nb8, unsigned nb16, int hist) {
     __shared__ uint32_t h[kPasses * 256];
+    grid_dependency_wait();
+    grid_dependency_trigger();
     if (hist) {
         for (int i = threadIdx.x; i < kPasses * 256; i += blockDim.x) h[i] = 0u;
         __syncthreads();
@@ -553,6 +555,8 @@ __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
 }
 template <class J>
 __global__ void __launch_bounds__(kSortThreads) k_pass_one(J job, int p, int e, int last) {
+    grid_dependency_wait();
+    grid_dependency_trigger();
     const SortScratch &s = job.get().s;
     const unsigned long long *meta = job.get().meta;
     constexpr int WARPS = kSortThreads / 32;
@@ -694,6 +698,8 @@ __device__ __forceinline__ bool same_run(const SortScratch &s, uint32_t a, uint3
 }
 template <class J>
 __global__ void k_fix_long(J job, int passes) {
+    grid_dependency_wait();
+    grid_dependency_trigger();
     const SortScratch &s = job.get().s;
     const LongView &v = job.get().v;
     const unsigned long long *meta = job.get().meta;
@@ -734,6 +740,8 @@ __device__ __forceinline__ unsigned long long short_len(unsigned long long hi, u
 
 template <class J>
 __global__ void k_gather_final(J job) {
+    grid_dependency_wait();
+    grid_dependency_trigger();
     const SortScratch &s = job.get().s;
     const DevTable &out = job.get().out;
     const unsigned long long n = out.d_meta[0];
@@ -810,8 +818,8 @@ static void launch_sort(const J &job, uint64_t cap, int ntab, int passes, uint32
     for (int p = 0, e = 0; p < passes; p++) {
         if ((skip >> p) & 1u) continue;
         const int last = p == lastp;
-        if (onesweep) {
-            k_pass_one<<<dim3(ntiles, ntab), kSortThreads, 0, st>>>(job, p, e, last);
+        if (onesweep) {  // overlaps its launch with the tail of the kernel before
+            launch_dependent(k_pass_one<J>, dim3(ntiles, ntab), dim3(kSortThreads), 0, st, job, p, e, last);
         } else {
             k_pass_count<<<dim3(ntiles, ntab), kSortThreads, 0, st>>>(job, p, e, fused);
             if (!fused) k_pass_scan<<<dim3(256, ntab), 256, 0, st>>>(job, p, e, last);
@@ -819,7 +827,7 @@ static void launch_sort(const J &job, uint64_t cap, int ntab, int passes, uint32
         }
         e++;
     }
-    k_fix_long<<<dim3(grid_for(cap, 256, sms * 4), ntab), 256, 0, st>>>(job, passes);
+    launch_dependent(k_fix_long<J>, dim3(grid_for(cap, 256, sms * 4), ntab), dim3(256), 0, st, job, passes);
 }
 
 // LSD radix sort of the entries in ss (count n = meta[0]) into ss.perm_buf(ss.cur[passes]).
@@ -878,8 +886,9 @@ static void launch_compaction(const GTable &g, uint64_t gcap8, uint64_t gcap, ui
     sort_state_reset(ss, st);
     const int nb8 = grid_for(gcap8, 256 * kScanUnroll, sms * 8), nb16 = grid_for(gcap, 256 * kScanUnroll, sms * 8),
               nbl = grid_for(glcap, 256, sms * 8);
-    k_compact_all<<<nb8 + nb16 + nbl, 256, 0, st>>>(g, gcap8, gcap, glcap, ss, out, (unsigned)nb8, (unsigned)nb16,
-                                                    keyed ? 1 : 0);
+    launch_dependent(k_compact_all, dim3(nb8 + nb16 + nbl), dim3(256), 0, st, g, (unsigned long long)gcap8,
+                     (unsigned long long)gcap, (unsigned long long)glcap, ss, out, (unsigned)nb8, (unsigned)nb16,
+                     keyed ? 1 : 0);
 }
 
 cudaError_t finish_table(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_t glcap, SortScratch &ss,
@@ -887,7 +896,8 @@ cudaError_t finish_table(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_
     launch_compaction(g, gcap8, gcap, glcap, ss, out, st, true);
     OneJob job{SortJob{ss, out.d_meta, LongView{ss.lref, out.loff, out.llen, out.arena}, out}};
     launch_sort(job, ss.cap, 1, kPasses, skip, st, true);
-    k_gather_final<<<grid_for(ss.cap, 256 * kScanUnroll, sm_count() * 8), 256, 0, st>>>(job);
+    launch_dependent(k_gather_final<OneJob>, dim3(grid_for(ss.cap, 256 * kScanUnroll, sm_count() * 8)), dim3(256), 0,
+                     st, job);
     return cudaGetLastError();
 }
 
@@ -910,7 +920,8 @@ cudaError_t finish_tables(const FinishSpec *spec, int n, void *d_jobs, cudaStrea
     if (e != cudaSuccess) return e;
     JobList list{static_cast<const SortJob *>(d_jobs)};
     launch_sort(list, cap, n, kPasses, skip, st);
-    k_gather_final<<<dim3(grid_for(cap, 256 * kScanUnroll, sm_count() * 8), n), 256, 0, st>>>(list);
+    launch_dependent(k_gather_final<JobList>, dim3(grid_for(cap, 256 * kScanUnroll, sm_count() * 8), n), dim3(256), 0,
+                     st, list);
     return cudaGetLastError();
 }
 
