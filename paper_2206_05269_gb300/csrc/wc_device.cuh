@@ -356,10 +356,18 @@ __device__ inline void long_insert2(const GTable &g, const uint8_t *w, unsigned 
     const uint4 zero = make_uint4(0, 0, 0, 0);
     for (int probe = 0; probe < kGlobalProbeLimit; probe++) {
         LSlot *slot = g.lslots + s;
-        // plain loads first: a claimed slot (both words non-zero, written by
-        // one 128-bit CAS) is settled; an empty or half-seen one goes to the CAS
-        const unsigned long long h0 = ld_u64(&slot->h), a0 = ld_u64(&slot->addr);
-        uint4 old = make_uint4((uint32_t)h0, (uint32_t)(h0 >> 32), (uint32_t)a0, (uint32_t)(a0 >> 32));
+        // relaxed loads first, the whole slot in one round trip: a claimed slot
+        // (both key words non-zero, written by one 128-bit CAS) is settled; an
+        // empty or half-seen one goes to the CAS
+        uint4 old = ld_relaxed_v2(&slot->h);
+        const uint4 clen = ld_relaxed_v2(&slot->cnt);
+        uint4 sf = make_uint4(0u, 0u, 0u, 0u), sl = sf;
+        if (fl) {
+            sf = ld_relaxed_v2(&slot->f);
+            sl = ld_relaxed_v2(&slot->l);
+        }
+        const unsigned long long h0 = ((unsigned long long)old.y << 32) | old.x,
+                                 a0 = ((unsigned long long)old.w << 32) | old.z;
         if (h0 == 0ull || a0 == 0ull) old = cas128_global(&slot->h, zero, want);
         if (key_zero(old)) {
             if (fl) {
@@ -373,10 +381,18 @@ __device__ inline void long_insert2(const GTable &g, const uint8_t *w, unsigned 
             return;
         }
         if (fl && old.x == want.x && old.y == want.y) {
-            const unsigned long long lr = ld_acquire_u64(&slot->len);
+            // the length word seen with the slot: when ready, the ends read
+            // with it are the published ones or (if read before publication)
+            // still zero, which no word's ends are; a mismatch is confirmed
+            // by reading the ends again after an acquire of the length word
+            unsigned long long lr = ((unsigned long long)clen.w << 32) | clen.z;
+            bool ends = (lr & kLongReady) && long_len(lr) == len && key_eq(sf, fl[0]) && key_eq(sl, fl[1]);
+            if (!ends) {
+                lr = ld_acquire_u64(&slot->len);
+                ends = (lr & kLongReady) && long_len(lr) == len && key_eq(ld_relaxed_u128(&slot->f), fl[0]) &&
+                       key_eq(ld_relaxed_u128(&slot->l), fl[1]);
+            }
             if (lr & kLongReady) {
-                const bool ends = long_len(lr) == len && key_eq(ld_relaxed_u128(&slot->f), fl[0]) &&
-                                  key_eq(ld_relaxed_u128(&slot->l), fl[1]);
                 if (ends && len <= 32) {  // the ends and the length are the whole word
                     red_add_u64_dev(&slot->cnt, add);
                     return;
