@@ -277,6 +277,18 @@ def run_gpu(args, rank, world, local, subs=None):
         tab.free()
     e2e_s = statistics.mean(t_e2e[1:])
     e2e_val = nbytes * world / e2e_s / 1e9
+    # the host link measured in the same run: one plain pinned host -> device
+    # copy of the whole text (the end-to-end figure cannot pass it)
+    t_copy = []
+    for _ in range(3):
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        with torch.cuda.stream(stream):
+            dev2.copy_(host, non_blocking=True)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        t_copy.append(c0.elapsed_time(c1))
+    h2d_gbps = nbytes / (min(t_copy) * 1e-3) / 1e9
 
     peak, peak_kind = measured_peaks()
     avg_count_s = ms_count / max(1, n_count) * 1e-3
@@ -333,7 +345,8 @@ def run_gpu(args, rank, world, local, subs=None):
                          "algorithmic_bytes_per_launch": alg_bytes,
                          "read_ceiling_GBps": read_ceiling, "frac_of_read_ceiling": achieved / read_ceiling,
                          "nominal_peak_GBps": 7900.0, "frac_of_nominal": achieved / 7900.0},
-            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": d2h,
+                    "h2d_copy_GBps": h2d_gbps},
             "gpu_launches": launches,
             "clocks": clocks,
         }
@@ -593,10 +606,15 @@ def run_served_workload(args, local, print_line: bool = True):
     return line
 
 
+# fp64 thread instructions per term of k_series_part<0> and <1>
+# (sm__inst_executed_pipe_fp64 x 32 / n, n = 1e8)
+FP64_INSTR_PER_TERM = {0: 16.15, 1: 14.15}
+
+
 def run_numeric(args, local) -> dict:
     """The paper's numeric MapReduce (Sec. 4.2) at n = 1e8: sum of sqrt(i)
     and the alternating harmonic sum, each term a correctly rounded double,
-    compensated sums (wc_series_sum).  ALU-bound: reported against the
+    compensated sums (wc_series_sum).  FP64-pipe bound: reported against the
     nominal FP64 rate of the part (no measured FP64 peak is available)."""
     import torch
     import oracle
@@ -622,13 +640,18 @@ def run_numeric(args, local) -> dict:
         m = 10_000_000  # the oracle on a tenth of the terms (about a second of CPU work)
         oracle.series_sum(series, m)
         cpu_s = time.perf_counter() - t0
-        # two floating-point operations a term (the map: sqrt or 1/i; the reduce: +)
-        gflops = 2.0 * n / (ms * 1e-3) / 1e9
+        # FP64-pipe bound: fp64 instructions per term from the ncu count of
+        # this kernel (sm__inst_executed_pipe_fp64), against the part's
+        # nominal FP64 rate, 1.25 TFLOP/s with an FMA counted twice
+        per_term = FP64_INSTR_PER_TERM[series]
+        ginstr = per_term * n / (ms * 1e-3) / 1e9
         res[name] = {"n": n, "value": got, "oracle": oracle.series_sum(series, n), "ms": ms,
                      "terms_per_s": n / (ms * 1e-3),
-                     "roofline": {"bound": "alu", "achieved": gflops, "peak": 1250.0, "unit": "GFLOP/s (FP64)",
-                                  "frac": gflops / 1250.0, "peak_kind": "nominal FP64 rate of the part",
-                                  "flops_per_term": 2},
+                     "roofline": {"bound": "fp64", "achieved": ginstr, "peak": 625.0,
+                                  "unit": "G fp64 instructions/s", "frac": ginstr / 625.0,
+                                  "peak_kind": "nominal FP64 rate of the part (1.25 TFLOP/s, FMA = 2)",
+                                  "instr_per_term": per_term,
+                                  "instr_source": "ncu sm__inst_executed_pipe_fp64 (profiles/numeric_series_fp64.md)"},
                      "cpu_baseline": {"value": m / cpu_s, "unit": "terms/s", "cores": 1, "kind": "oracle",
                                       "sample": f"first {m} terms, single-threaded compensated sum, {cpu_s:.2f} s"},
                      "paper_v100_ms": 73.372 if series == wc.WC_SERIES_SQRT else 65.323}
