@@ -59,7 +59,7 @@ constexpr int kLongCap = 48;              // < 16 left over + at most 32 starts 
 constexpr int kHeadSlots = 8192;          // level-1 table keys
 constexpr int kHeadBuckets = 2048;        // hash-and-displace buckets of the HEAD image
 constexpr int kLocalProbes = 4;
-constexpr int kSamplePieces = 64;
+constexpr int kSamplePieces = 32;
 constexpr int kSamplePieceBytes = 65536;
 constexpr uint64_t kHeadMinBytes = 16ull << 20;
 constexpr unsigned long long kSampleSlots = 1ull << 19;
