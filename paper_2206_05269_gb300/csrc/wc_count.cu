@@ -512,15 +512,19 @@ __global__ void __launch_bounds__(kBlock, 1) k_count3(Count2Args a) {
             if (lane >= d) incl += t;
         }
         const uint32_t total = __shfl_sync(kFull, incl, 31);
-        uint32_t off = tcount + incl - c1;
+        // this lane's c1 queue slots are [lo, hi): each step takes its highest
+        // start into the top and its lowest into the bottom (two independent
+        // chains; queue order does not matter)
+        uint32_t lo = tcount + incl - c1, hi = tcount + incl;
         const uint32_t tag = ((uint32_t)b << 27) | ((uint32_t)(kLead + 16 * lane) << 5);
-        const uint32_t nmax = __reduce_max_sync(kFull, c1);  // a warp-uniform trip count
+        const uint32_t nmax = (__reduce_max_sync(kFull, c1) + 1u) >> 1;  // a warp-uniform trip count
         for (uint32_t r = 0; r < nmax; r++) {
-            if (Ss) {  // this lane's starts from the highest down (queue order does not matter)
-                const uint32_t j = 31u - (uint32_t)__clz(Ss);
-                Ss ^= 1u << j;
-                const uint32_t len = (uint32_t)__ffs(E >> j);  // a short word ends within the 32 bits
-                tok[off++] = tag + (j << 5) + len;
+            if (Ss) {
+                const uint32_t j = 31u - (uint32_t)__clz(Ss), i = (uint32_t)__ffs(Ss) - 1u;
+                Ss &= ~((1u << j) | (1u << i));
+                // a short word ends within the 32 bits
+                tok[--hi] = tag + (j << 5) + (uint32_t)__ffs(E >> j);
+                if (i != j) tok[lo++] = tag + (i << 5) + (uint32_t)__ffs(E >> i);
             }
         }
         tcount += total;
