@@ -448,6 +448,31 @@ __global__ void __launch_bounds__(kBlock, 1) k_count3(Count2Args a) {
         // to land), free lanes take new ones; the queue ends below 32 words
         while (tailn >= 32) tl.round(tailq, tailn, lane);
     };
+    // HEAD mode, two full batches of queued words: the two words' head
+    // lookups are independent, so they run interleaved (every load issued
+    // before the compares; a word of more than 8 letters never hits), then
+    // each batch's misses are queued and flushed as process does.
+    auto push_tail = [&](bool tail, uint4 tk) {
+        const uint32_t tb = __ballot_sync(kFull, tail);
+        if (tail) tailq[tailn + __popc(tb & ((1u << lane) - 1u))] = tk;
+        tailn += __popc(tb);
+        __syncwarp();
+        while (tailn >= 32) tl.round(tailq, tailn, lane);
+    };
+    auto process2 = [&](uint32_t e0, uint32_t e1) {
+        const uint32_t n0 = e0 & 31u, n1 = e1 & 31u;
+        const uint4 k0 = window_key16(ring + (e0 >> 27) * kWinB, (e0 >> 5) & 0x3FFu, n0, kmask);
+        const uint4 k1 = window_key16(ring + (e1 >> 27) * kWinB, (e1 >> 5) & 0x3FFu, n1, kmask);
+        const unsigned long long y0 = key_lo(k0), y1 = key_lo(k1);
+        const unsigned long long h0 = l1_mix(y0), h1 = l1_mix(y1);
+        const uint32_t s0 = head_slot(h0, sdisp[head_bucket(h0)]), s1 = head_slot(h1, sdisp[head_bucket(h1)]);
+        const unsigned long long v0 = skey[s0], v1 = skey[s1];
+        const bool hit0 = n0 <= 8u && v0 == y0, hit1 = n1 <= 8u && v1 == y1;
+        if (hit0) atomicAdd(&scnt[s0], 1u);
+        if (hit1) atomicAdd(&scnt[s1], 1u);
+        push_tail(!hit0, k0);
+        push_tail(!hit1, k1);
+    };
 
     // Words of 17+ letters: (address << 16 | run length, or 0 when the window
     // did not show the run's end).  With a deferred queue they are appended to
@@ -557,6 +582,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_count3(Count2Args a) {
         __syncwarp();
         // ---- queued words, 32 at a time
         uint32_t bq = 0;
+        if (MODE == MODE_HEAD)
+            for (; bq + 64 <= tcount; bq += 64) process2(tok[bq + lane], tok[bq + 32 + lane]);
         for (; bq + 32 <= tcount; bq += 32) process(tok[bq + lane], true);
         uint32_t rem = tcount - bq;
         if (tprev > bq) {  // words of the previous strip still queued: finish them all now
