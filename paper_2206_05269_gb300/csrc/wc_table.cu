@@ -565,6 +565,9 @@ __global__ void __launch_bounds__(kSortThreads) k_pass_one(J job, int p, int e, 
     __shared__ uint32_t tile_sh;
     const unsigned long long n = meta[0];
     const unsigned long long ntiles = (n + kSortTile - 1) / kSortTile;
+    // the grid is sized by capacity: blocks past the entries leave at once
+    // (block 0 stays: it records this pass's order even for an empty table)
+    if (blockIdx.x >= ntiles && blockIdx.x != 0) return;
     const uint32_t par = (uint32_t)e & 1u;
     if (blockIdx.x < ntiles) s.look_buf(par ^ 1u)[(unsigned long long)blockIdx.x * 256 + threadIdx.x] = 0u;
     if (blockIdx.x == 0 && threadIdx.x == 0) s.tile_ctr[par ^ 1u] = 0u;
