@@ -154,7 +154,7 @@ def profiled_traffic(kind: str):
                 d[k.strip()] = v.strip()
     if d.get("kernel_source_hash") != kernel_source_hash():
         return None, (f"{TRAFFIC_FILE} was captured on kernel source {d.get('kernel_source_hash')}, "
-                      f"not the current {kernel_source_hash()}: traffic unmeasured for this build")
+                      f"not the current {kernel_source_hash()}: traffic unmeasured for the current kernel source")
     v = d.get(kind)
     return (float(v) if v else None), f"ncu capture in {TRAFFIC_FILE} (kernel source {kernel_source_hash()})"
 
@@ -717,6 +717,11 @@ def run_hybrid(args, local) -> dict:
     ctr.close()
     best["on_device_total_ms"] = min(tms[1:])
     best["workload"] = "classes: 1,000 documents, 29.6 MB (the paper ran 4n speeches, n <= 500)"
+    # the paper's own timings for 4n = 1,000 documents (Sec. 4.1, n = 250; a
+    # 32-thread CPU and a V100; speech texts, sizes not given): context only
+    best["paper_n250"] = {"map_cpu_ms": 49.808, "map_and_reduce_cpu_ms": 82.518,
+                          "reduce_gpu_incl_matrix_and_copy_ms": 7.256,
+                          "hardware": "32-thread CPU + V100", "docs": 1000}
     best["cpu_threads"] = os.cpu_count()
     return best
 
