@@ -201,6 +201,11 @@ __global__ void __launch_bounds__(BLOCK, (DocCfg<BLOCK, LOGC1>::MINB)) k_docs(Ba
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *tok = tokall + warp * C::TOKCAP;
     const uintptr_t tb = reinterpret_cast<uintptr_t>(a.text);
+    // The size classes' kernels work on separate item queues: a later one
+    // may start as soon as this one's blocks have all started (its blocks
+    // then fill the SMs this one's finished blocks leave), and waits for this
+    // one only at its end, so that its completion implies this one's.
+    grid_dependency_trigger();
 
     for (;;) {
         if (threadIdx.x == 0) sh.item = atomicAdd(a.next_item, 1u);
@@ -560,10 +565,11 @@ __global__ void __launch_bounds__(BLOCK, (DocCfg<BLOCK, LOGC1>::MINB)) k_docs(Ba
         }
         __syncthreads();
     }
+    grid_dependency_wait();  // the previous size class's kernel has completed (a no-op after an ordinary launch)
 }
 
 template <int BLOCK, int LOGC1>
-cudaError_t launch_docs_t(const BatchArgs &a, int grid, cudaStream_t s) {
+cudaError_t launch_docs_t(const BatchArgs &a, int grid, cudaStream_t s, bool dependent) {
     using C = DocCfg<BLOCK, LOGC1>;
     const cudaError_t ea = ensure_smem_limit((const void *)k_docs<BLOCK, LOGC1>, (int)C::SMEM);
     if (ea != cudaSuccess) return ea;
@@ -574,6 +580,7 @@ cudaError_t launch_docs_t(const BatchArgs &a, int grid, cudaStream_t s) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_docs<BLOCK, LOGC1>, BLOCK, C::SMEM);
         grid = sms * (per > 0 ? per : 1);
     }
+    if (dependent) return launch_dependent(k_docs<BLOCK, LOGC1>, dim3(grid), dim3(BLOCK), C::SMEM, s, a);
     k_docs<BLOCK, LOGC1><<<grid, BLOCK, C::SMEM, s>>>(a);
     return cudaGetLastError();
 }
@@ -583,16 +590,16 @@ const DocShape kDocShapes[] = {
 };
 const int kNumDocShapes = sizeof(kDocShapes) / sizeof(kDocShapes[0]);
 
-cudaError_t launch_docs(const BatchArgs &a, int shape, cudaStream_t s) {
+cudaError_t launch_docs(const BatchArgs &a, int shape, cudaStream_t s, bool dependent) {
     switch (shape) {
-    case 0: return launch_docs_t<128, 10>(a, 0, s);
-    case 1: return launch_docs_t<256, 11>(a, 0, s);
-    case 2: return launch_docs_t<256, 12>(a, 0, s);
-    case 3: return launch_docs_t<512, 12>(a, 0, s);
-    case 4: return launch_docs_t<512, 13>(a, 0, s);
-    case 5: return launch_docs_t<1024, 13>(a, 0, s);
-    case 6: return launch_docs_t<64, 10>(a, 0, s);
-    default: return launch_docs_t<32, 9>(a, 0, s);
+    case 0: return launch_docs_t<128, 10>(a, 0, s, dependent);
+    case 1: return launch_docs_t<256, 11>(a, 0, s, dependent);
+    case 2: return launch_docs_t<256, 12>(a, 0, s, dependent);
+    case 3: return launch_docs_t<512, 12>(a, 0, s, dependent);
+    case 4: return launch_docs_t<512, 13>(a, 0, s, dependent);
+    case 5: return launch_docs_t<1024, 13>(a, 0, s, dependent);
+    case 6: return launch_docs_t<64, 10>(a, 0, s, dependent);
+    default: return launch_docs_t<32, 9>(a, 0, s, dependent);
     }
 }
 

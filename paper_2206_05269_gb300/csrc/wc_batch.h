@@ -41,7 +41,10 @@ struct DocShape {
 extern const DocShape kDocShapes[];
 extern const int kNumDocShapes;
 
-cudaError_t launch_docs(const BatchArgs &a, int shape, cudaStream_t s);
+// dependent: launched as a programmatic dependent of the previous size
+// class's kernel in the stream (independent work; it waits for that kernel
+// only at its end).
+cudaError_t launch_docs(const BatchArgs &a, int shape, cudaStream_t s, bool dependent = false);
 cudaError_t launch_segmented_finish(const BatchArgs &a, const GTable &g, uint64_t cap8, uint64_t cap16,
                                     uint64_t caplong, SortScratch &ss, unsigned long long *smeta, cudaStream_t s,
                                     uint32_t skip = 0);

@@ -334,7 +334,7 @@ static cudaError_t batch_enqueue(wc_batch *b, const uint8_t *d_text, const uint6
         s2.items = b->scr.items + b->nsmall;
         s2.nitems = b->nmedium;
         s2.next_item = b->scr.next + 1;
-        e = launch_docs(s2, shape_medium, stream);
+        e = launch_docs(s2, shape_medium, stream, n > 0);
         n++;
     }
     const size_t nbig = b->items.size() - b->nsmall - b->nmedium;
@@ -343,7 +343,7 @@ static cudaError_t batch_enqueue(wc_batch *b, const uint8_t *d_text, const uint6
         s3.items = b->scr.items + b->nsmall + b->nmedium;
         s3.nitems = (uint32_t)nbig;
         s3.next_item = b->scr.next + 2;
-        e = launch_docs(s3, shape_large, stream);
+        e = launch_docs(s3, shape_large, stream, n > 0);
         n++;
     }
     if (e == cudaSuccess) {

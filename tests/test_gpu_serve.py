@@ -99,7 +99,7 @@ def test_admission_waits_under_a_tight_budget():
     """Request text is charged to the context's budget with the tables: with
     requests of about 12 MB arriving together (each a unit of its own, longer
     on the GPU than the loop takes to launch the next), six streams and a
-    budget of 1.6 units, units wait for admission instead of failing, the
+    budget of 1.2 units, units wait for admission instead of failing, the
     context never holds more than its budget, and every answer is still the
     oracle's."""
     torch = pytest.importorskip("torch")
@@ -116,13 +116,15 @@ def test_admission_waits_under_a_tight_budget():
     serve.serve_batched(solo, reqs, max_inflight=1, **kw)
     unit = solo.mem_usage()[1]
     solo.close()
-    budget = int(unit * 1.6)
+    # 1.2 units: a context's first unit (tables sized from an estimate) and
+    # any other never fit together, so the second waits for the first
+    budget = int(unit * 1.2)
     tight = wc.Counter(0, count_bits=32, budget=budget)
     answers, stats = serve.serve_batched(tight, reqs, max_inflight=6, **kw)
     used, peak = tight.mem_usage()
     tight.close()
     assert stats["large"] == len(reqs)
-    assert stats["budget_waits"] > 0, f"six streams under a budget of 1.6 units must wait: unit {unit}, {stats}"
+    assert stats["budget_waits"] > 0, f"six streams under a budget of 1.2 units must wait: unit {unit}, {stats}"
     assert peak <= budget, f"peak {peak} over the budget {budget}"
     for (a, s, e), ans in zip(trip, answers):
         assert ans.as_list() == oracle.count(pool[s:e]).glob().as_list()[:100], f"request {ans.rid}"
