@@ -128,10 +128,19 @@ class ClockSampler:
 
 
 def kernel_source_hash() -> str:
+    """Hash of the counting kernel's source code: the files it is built
+    from, with // comments and blank lines left out (a comment edit does not
+    change the kernel the traffic capture measured)."""
     h = hashlib.sha256()
     for f in ("wc_count.cu", "wc_device.cuh", "wc_internal.h"):
-        with open(os.path.join(ROOT, "paper_2206_05269_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2206_05269_gb300", "csrc", f), "r", encoding="utf-8") as fh:
+            lines = []
+            for ln in fh.read().splitlines():
+                i = ln.find("//")
+                ln = (ln[:i] if i >= 0 else ln).rstrip()
+                if ln:
+                    lines.append(ln)
+        h.update("\n".join(lines).encode())
     return h.hexdigest()[:16]
 
 

@@ -19,7 +19,8 @@
 // window's lead byte across strips); a word belongs to the strip holding its
 // first byte and is read through the window's lookahead.  Starts of words of
 // at most 16 letters go to a per-warp queue (window position and length) and
-// are processed 32 at a time, one per lane:
+// are processed 32 at a time, one per lane (with a HEAD table, two batches of
+// 32 at once, their lookups interleaved):
 //   * level 1 (shared memory): a word of at most 8 letters is looked up in
 //     the block's table of 8,192 keys and, if there, its shared count is
 //     incremented.  Two table kinds:
@@ -34,9 +35,12 @@
 //     queue of 16-byte keys, flushed 32 at a time into the global 8-byte-key
 //     or 16-byte-key open-addressing table (slot loads issued one flush
 //     ahead, fire-and-forget reductions, CAS only for a word's first claim).
-// Words of 17+ letters are queued by address and inserted 32 at a time into
-// the global long-word table (bytes compared, never only hashes).  At the end
-// each block adds its nonzero level-1 counts into the global table.
+// Words of 17+ letters are queued by address and, with head scratch (texts
+// of 16 MB or more), appended to a global queue that k_long_deferred drains
+// after this kernel; otherwise (or when that queue is full) they are inserted
+// 32 at a time here.  Either way into the global long-word table, bytes
+// compared, never only hashes.  At the end each block adds its nonzero
+// level-1 counts into the global table.
 #include <algorithm>
 #include <cstddef>
 #include <mutex>
