@@ -564,26 +564,33 @@ __global__ void __launch_bounds__(kSortThreads) k_pass_one(J job, int p, int e, 
     __shared__ uint32_t wtot[WARPS];
     __shared__ uint32_t tile_sh;
     const unsigned long long n = meta[0];
+    // loads that do not depend on n go out with it: digit d's count over all
+    // entries (thread d) and the order this pass reads
+    const int d = threadIdx.x;
+    const uint32_t own = s.hist_all[p * 256 + d];
+    const uint32_t cur = s.cur[e];
     const unsigned long long ntiles = (n + kSortTile - 1) / kSortTile;
     // the grid is sized by capacity: blocks past the entries leave at once
     // (block 0 stays: it records this pass's order even for an empty table)
     if (blockIdx.x >= ntiles && blockIdx.x != 0) return;
     const uint32_t par = (uint32_t)e & 1u;
+    // the tile is taken before the skip test is known (a skipped pass's count
+    // is zeroed by the next pass like any other)
+    if (blockIdx.x < ntiles && threadIdx.x == 0) tile_sh = atomicAdd(&s.tile_ctr[par], 1u);
     if (blockIdx.x < ntiles) s.look_buf(par ^ 1u)[(unsigned long long)blockIdx.x * 256 + threadIdx.x] = 0u;
     if (blockIdx.x == 0 && threadIdx.x == 0) s.tile_ctr[par ^ 1u] = 0u;
-    const bool skip = pass_skipped(s, p, n);
+    // a pass is skipped when one digit value holds every entry
+    const bool skip = __syncthreads_or(own == n) != 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const uint32_t c = skip ? s.cur[e] : 1u - s.cur[e];
+        const uint32_t c = skip ? cur : 1u - cur;
         s.cur[e + 1] = c;
         if (last) s.cur[kCurFinal] = c;
     }
     if (skip || blockIdx.x >= ntiles) return;
-    if (threadIdx.x == 0) tile_sh = atomicAdd(&s.tile_ctr[par], 1u);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < WARPS * 256; i += kSortThreads) (&wcount[0][0])[i] = 0;
     __syncthreads();
     const uint32_t tile = tile_sh;
-    const uint32_t cur = s.cur[e];
     const uint32_t *in = s.perm_buf(cur);
     uint32_t *out = s.perm_buf(1 - cur);
     const unsigned long long t0 = (unsigned long long)tile * kSortTile + (unsigned long long)warp * (kSortTile / WARPS);
@@ -614,7 +621,6 @@ __global__ void __launch_bounds__(kSortThreads) k_pass_one(J job, int p, int e, 
     }
     __syncthreads();
     // thread d: this tile's count of digit d, published, then the look-back
-    const int d = threadIdx.x;
     uint32_t cnt = 0;
 #pragma unroll
     for (int w = 0; w < WARPS; w++) cnt += wcount[w][d];
@@ -653,7 +659,6 @@ __global__ void __launch_bounds__(kSortThreads) k_pass_one(J job, int p, int e, 
     }
     // this tile's first position for digit d: the entries with a smaller
     // digit (the all-pass histogram) plus digit d's entries in earlier tiles
-    const uint32_t own = s.hist_all[p * 256 + d];
     uint32_t incl = own;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
