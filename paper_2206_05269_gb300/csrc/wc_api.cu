@@ -602,7 +602,7 @@ wc_status scratch_create(wc_ctx *ctx, const CapPlan &p, bool head, cudaStream_t 
     const size_t b8 = r(p.cap8 * sizeof(G8Slot)), b16 = r(p.cap16 * sizeof(GSlot)), bl = r(p.caplong * sizeof(LSlot));
     const size_t hb = b8 + b16 + bl;
     const size_t bh = head ? r(head_scratch_bytes()) : 0;
-    cs.bytes = hb + bh + sort_scratch_bytes(cs.entries()) + 512;
+    cs.bytes = hb + bh + sort_scratch_bytes(cs.entries(), true) + 512;
     wc_status st = ctx->alloc(&cs.mem, cs.bytes, s);
     if (st != WC_OK) return st;
     uint8_t *q = static_cast<uint8_t *>(cs.mem);
@@ -610,7 +610,7 @@ wc_status scratch_create(wc_ctx *ctx, const CapPlan &p, bool head, cudaStream_t 
     cs.slots = reinterpret_cast<GSlot *>(q + b8);
     cs.lslots = reinterpret_cast<LSlot *>(q + b8 + b16);
     cs.head = head ? q + hb : nullptr;
-    sort_scratch_carve(cs.ss, q + hb + bh, cs.entries());
+    sort_scratch_carve(cs.ss, q + hb + bh, cs.entries(), true);
     cudaMemsetAsync(cs.mem, 0, hb, s);
     return WC_OK;
 }
@@ -647,7 +647,7 @@ wc_status wc_count_ex(wc_ctx *ctx, const uint8_t *d_text, uint64_t nbytes, const
     const uint32_t skip = sort_skip_mask(nbytes / 2 + 1, 0);  // no count exceeds the token bound
     if (e == cudaSuccess) e = finish_table(g, cs.gcap8, cs.gcap, cs.glcap, cs.ss, t->dt, stream, skip);
     ctx->prof_mark(ctx->ev_finish, stream);
-    ctx->launches += finish_table_launches(cs.ss.cap, skip);
+    ctx->launches += finish_table_launches(cs.ss, skip);
     ctx->release(cs.mem, cs.bytes, stream);
     table_mark_done(t, stream);
     if (e != cudaSuccess) {
@@ -731,7 +731,7 @@ wc_status wc_count_host(wc_ctx *ctx, const uint8_t *h_text, uint64_t nbytes, uin
     }
     const uint32_t skip = sort_skip_mask(nbytes / 2 + 1, 0);  // no count exceeds the token bound
     if (e == cudaSuccess) e = finish_table(g, cs.gcap8, cs.gcap, cs.glcap, cs.ss, t->dt, stream, skip);
-    ctx->launches += finish_table_launches(cs.ss.cap, skip);
+    ctx->launches += finish_table_launches(cs.ss, skip);
     for (auto x : ev)
         if (x) cudaEventDestroy(x);  // released once their work completes
     ctx->release(cs.mem, cs.bytes, stream);
@@ -800,7 +800,7 @@ wc_status wc_merge(wc_ctx *ctx, const wc_table *const *in, uint32_t n, cudaStrea
     ctx->prof_mark(ctx->ev_finish, stream);
     if (e == cudaSuccess) e = finish_table(g, cs.gcap8, cs.gcap, cs.glcap, cs.ss, t->dt, stream);
     ctx->prof_mark(ctx->ev_finish, stream);
-    ctx->launches += finish_table_launches(cs.ss.cap);
+    ctx->launches += finish_table_launches(cs.ss);
     ctx->release(dsrc, sb, stream);
     ctx->release(cs.mem, cs.bytes, stream);
     table_mark_done(t, stream);

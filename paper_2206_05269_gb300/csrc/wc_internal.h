@@ -138,6 +138,10 @@ struct SortScratch {
     uint32_t group_stride;
     uint32_t *look[2];       // 256 x ntiles each: per-tile digit counts published for the look-back, by pass parity
     uint32_t *tile_ctr;      // [2]: tiles taken in launch order, by pass parity
+    // merge sort of a single table (null when the scratch was carved without
+    // it): 128-bit keys, the high and low words of buffer 0, then of buffer 1
+    // (the indices travel in perm[0] and perm[1])
+    unsigned long long *mk[4];
     // permutation buffer c (0 or 1), selected without indexing the parameter array
     __device__ __forceinline__ uint32_t *perm_buf(uint32_t c) const { return c ? perm[1] : perm[0]; }
     __device__ __forceinline__ uint32_t *group_buf(uint32_t c) const { return c ? group_hist[1] : group_hist[0]; }
@@ -146,8 +150,10 @@ struct SortScratch {
 // Slot of SortScratch::cur where a radix pass records a look-back that gave
 // up waiting (the finish then reports WC_ERR_TIMEOUT).
 constexpr int kCurSortError = 30;
-size_t sort_scratch_bytes(uint64_t cap);
-void sort_scratch_carve(SortScratch &s, void *base, uint64_t cap);
+// with_msort: also the merge sort's key buffers (32 bytes an entry), which a
+// single table's finish then uses (see finish_table).
+size_t sort_scratch_bytes(uint64_t cap, bool with_msort = false);
+void sort_scratch_carve(SortScratch &s, void *base, uint64_t cap, bool with_msort = false);
 // Zeroes what a sort accumulates into (digit histograms, pass cursors, group
 // counts, the first pass's look-back buffer and the tile counters): every
 // sort of a scratch starts with this (stream-ordered memsets).
@@ -174,9 +180,11 @@ cudaError_t sort_entries(SortScratch &ss, const unsigned long long *meta, const 
 int sort_entries_launches(int passes, uint64_t cap, uint32_t skip = 0);
 
 // Compacts the global hash tables into unsorted scratch arrays and copies
-// the long words into out.arena; then sorts and writes `out`.
-// finish_table_launches(ss.cap) kernels are launched.
-int finish_table_launches(uint64_t cap, uint32_t skip = 0);
+// the long words into out.arena; then sorts and writes `out`.  The sort is a
+// merge sort when ss has its key buffers and `skip` shows every count below
+// 2^32 (the radix sort's count digits 4..7 skipped), else the radix sort.
+// finish_table_launches(ss, skip) kernels are launched.
+int finish_table_launches(const SortScratch &ss, uint32_t skip = 0);
 cudaError_t finish_table(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_t glcap, SortScratch &ss,
                          DevTable &out, cudaStream_t s, uint32_t skip = 0);
 

@@ -35,14 +35,14 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-size_t sort_scratch_bytes(uint64_t cap) {
+size_t sort_scratch_bytes(uint64_t cap, bool with_msort) {
     uint64_t ntiles = (cap + kSortTile - 1) / kSortTile;
     return cap * (8 + 8 + 8 + 8 + 4 + 4 + 4 + 4 + 4) + 4 * kPassesSeg * 256 + 4 * 256 * ntiles + 4 * 32 +
            2 * 4 * 256 * (ntiles <= kSortFusedMaxTiles ? sort_group_stride(ntiles) : 1) + 4096 +
-           2 * (4 * 256 * ntiles + 256) + 256;
+           2 * (4 * 256 * ntiles + 256) + 256 + (with_msort ? 4 * (cap * 8 + 256) : 0);
 }
 
-void sort_scratch_carve(SortScratch &s, void *base, uint64_t cap) {
+void sort_scratch_carve(SortScratch &s, void *base, uint64_t cap, bool with_msort) {
     uint64_t ntiles = (cap + kSortTile - 1) / kSortTile;
     uint8_t *p = static_cast<uint8_t *>(base);
     auto take = [&](size_t n) { uint8_t *r = p; p += (n + 255) & ~(size_t)255; return r; };
@@ -65,6 +65,8 @@ void sort_scratch_carve(SortScratch &s, void *base, uint64_t cap) {
     s.look[0] = reinterpret_cast<uint32_t *>(take(4 * 256 * ntiles));
     s.look[1] = reinterpret_cast<uint32_t *>(take(4 * 256 * ntiles));
     s.tile_ctr = reinterpret_cast<uint32_t *>(take(4 * 2));
+    for (int i = 0; i < 4; i++)
+        s.mk[i] = with_msort ? reinterpret_cast<unsigned long long *>(take(cap * 8)) : nullptr;
 }
 
 // ---------------------------------------------------------------- compaction
@@ -89,20 +91,39 @@ __device__ __forceinline__ void sort_key_prep(const SortScratch &s, unsigned lon
     atomicAdd(&h[9 * 256 + ((hi >> 8) & 0xFF)], 1u);
 }
 
-// One entry of a compaction; with h (the fused compaction of a single
-// table's finish) also its sort key and digit counts.
+// The merge sort's 128-bit key of an entry (counts below 2^32): the count
+// inverted in the high 32 bits (count descending), then the 80-bit packed
+// prefix, then 16 zero bits.  A count of at least 1 keeps the high word below
+// all ones, the key of the sort's padding.
+__device__ __forceinline__ void ms_key_prep(const SortScratch &s, unsigned long long i, unsigned long long khi,
+                                            unsigned long long klo, unsigned long long cnt) {
+    const unsigned long long ph = pack5(khi), pl = pack5(klo);
+    const unsigned long long lo = (ph << 40) | pl, hi16 = ph >> 24;  // the 80-bit code: hi16:lo
+    s.mk[0][i] = ((unsigned long long)(~(uint32_t)cnt) << 32) | (hi16 << 16) | (lo >> 48);
+    s.mk[1][i] = lo << 16;
+}
+
+// How a compaction prepares the sort: nothing (the sort packs its own keys),
+// the radix sort's keys and digit counts (into the block histogram h), or the
+// merge sort's keys.
+enum KeyPrep : int { kPrepNone = 0, kPrepRadix = 1, kPrepMerge = 2 };
+
+// One entry of a compaction, with the sort keys `prep` asks for.
 __device__ __forceinline__ void emit_entry(const SortScratch &ss, unsigned long long pos, unsigned long long khi,
-                                           unsigned long long klo, unsigned long long cnt, uint32_t lref, uint32_t *h) {
+                                           unsigned long long klo, unsigned long long cnt, uint32_t lref, uint32_t *h,
+                                           int prep) {
     ss.khi[pos] = khi;
     ss.klo[pos] = klo;
     ss.cnt[pos] = cnt;
     ss.lref[pos] = lref;
-    if (h) sort_key_prep(ss, pos, khi, klo, cnt, h);
+    if (prep == kPrepRadix) sort_key_prep(ss, pos, khi, klo, cnt, h);
+    else if (prep == kPrepMerge) ms_key_prep(ss, pos, khi, klo, cnt);
 }
 
 // Occupied 16-byte-key slots -> entries (big-endian key halves); block bid of nb.
 __device__ __forceinline__ void compact_short_body(const GSlot *slots, unsigned long long cap, const SortScratch &ss,
-                                                   unsigned long long *meta, unsigned bid, unsigned nb, uint32_t *h) {
+                                                   unsigned long long *meta, unsigned bid, unsigned nb, uint32_t *h,
+                                                   int prep) {
     __shared__ BlockTake sh;
     const unsigned long long step = (unsigned long long)nb * blockDim.x * kScanUnroll;
     for (unsigned long long b = (unsigned long long)bid * blockDim.x * kScanUnroll; b < cap; b += step) {
@@ -127,7 +148,7 @@ __device__ __forceinline__ void compact_short_body(const GSlot *slots, unsigned 
 #pragma unroll
         for (int u = 0; u < kScanUnroll; u++) {
             if (key_zero(k[u])) continue;
-            emit_entry(ss, pos, be64(k[u].x, k[u].y), be64(k[u].z, k[u].w), c[u], 0u, h);
+            emit_entry(ss, pos, be64(k[u].x, k[u].y), be64(k[u].z, k[u].w), c[u], 0u, h, prep);
             pos++;
         }
     }
@@ -135,7 +156,8 @@ __device__ __forceinline__ void compact_short_body(const GSlot *slots, unsigned 
 
 // Occupied 8-byte-key slots -> entries; block bid of nb.
 __device__ __forceinline__ void compact8_body(const G8Slot *slots, unsigned long long cap, const SortScratch &ss,
-                                              unsigned long long *meta, unsigned bid, unsigned nb, uint32_t *h) {
+                                              unsigned long long *meta, unsigned bid, unsigned nb, uint32_t *h,
+                                              int prep) {
     __shared__ BlockTake sh;
     const unsigned long long step = (unsigned long long)nb * blockDim.x * kScanUnroll;
     for (unsigned long long b = (unsigned long long)bid * blockDim.x * kScanUnroll; b < cap; b += step) {
@@ -156,7 +178,7 @@ __device__ __forceinline__ void compact8_body(const G8Slot *slots, unsigned long
         for (int u = 0; u < kScanUnroll; u++) {
             const unsigned long long key = v[u].x;
             if (!key) continue;
-            emit_entry(ss, pos, be64((uint32_t)key, (uint32_t)(key >> 32)), 0ull, v[u].y, 0u, h);
+            emit_entry(ss, pos, be64((uint32_t)key, (uint32_t)(key >> 32)), 0ull, v[u].y, 0u, h, prep);
             pos++;
         }
     }
@@ -176,7 +198,8 @@ __device__ __forceinline__ uint32_t byte16(uint4 v, uint32_t i) {
 // letters whose slot holds its first and last 16 letters (kLongReady) is
 // written from the slot, without reading its occurrence in the text.
 __device__ __forceinline__ void compact_long_body(const LSlot *ls, unsigned long long lcap, const SortScratch &ss,
-                                                  const DevTable &out, unsigned bid, unsigned nb, uint32_t *hist) {
+                                                  const DevTable &out, unsigned bid, unsigned nb, uint32_t *hist,
+                                                  int prep) {
     const int lane = threadIdx.x & 31;
     const unsigned long long nw = ((unsigned long long)nb * blockDim.x) >> 5;
     unsigned long long *meta = out.d_meta;
@@ -253,7 +276,7 @@ __device__ __forceinline__ void compact_long_body(const LSlot *ls, unsigned long
                 for (int j = 0; j < 8; j++) hi = (hi << 8) | (unsigned long long)(src[j] | 0x20u);
                 for (int j = 8; j < 16; j++) lo = (lo << 8) | (unsigned long long)(src[j] | 0x20u);
             }
-            emit_entry(ss, pos, hi, lo, c, full ? 0u : (uint32_t)(lidx + 1), hist);
+            emit_entry(ss, pos, hi, lo, c, full ? 0u : (uint32_t)(lidx + 1), hist, prep);
         }
     }
 }
@@ -261,23 +284,25 @@ __device__ __forceinline__ void compact_long_body(const LSlot *ls, unsigned long
 // All three tables' occupied slots -> entries in one launch: blocks
 // [0, nb8) scan the 8-byte table, the next nb16 the 16-byte table and the
 // rest the long-word table.  The per-kind entry counts go to meta[5] (8-byte)
-// and meta[6] (16-byte).  With `hist` (a single table's finish) the entries'
-// sort keys and digit histograms are taken here as well, for the sort's passes.
+// and meta[6] (16-byte).  In a single table's finish the entries' sort keys
+// are prepared here as well (`prep`; for the radix sort with the digit
+// histograms of its passes).
 __global__ void __launch_bounds__(256) k_compact_all(GTable g, unsigned long long cap8, unsigned long long cap16,
                                                      unsigned long long lcap, SortScratch ss, DevTable out,
-                                                     unsigned nb8, unsigned nb16, int hist) {
+                                                     unsigned nb8, unsigned nb16, int prep) {
     __shared__ uint32_t h[kPasses * 256];
     grid_dependency_wait();
     grid_dependency_trigger();
+    const bool hist = prep == kPrepRadix;
     if (hist) {
         for (int i = threadIdx.x; i < kPasses * 256; i += blockDim.x) h[i] = 0u;
         __syncthreads();
     }
     uint32_t *hp = hist ? h : nullptr;
     const unsigned b = blockIdx.x;
-    if (b < nb8) compact8_body(g.slots8, cap8, ss, out.d_meta, b, nb8, hp);
-    else if (b < nb8 + nb16) compact_short_body(g.slots, cap16, ss, out.d_meta, b - nb8, nb16, hp);
-    else compact_long_body(g.lslots, lcap, ss, out, b - nb8 - nb16, gridDim.x - nb8 - nb16, hp);
+    if (b < nb8) compact8_body(g.slots8, cap8, ss, out.d_meta, b, nb8, hp, prep);
+    else if (b < nb8 + nb16) compact_short_body(g.slots, cap16, ss, out.d_meta, b - nb8, nb16, hp, prep);
+    else compact_long_body(g.lslots, lcap, ss, out, b - nb8 - nb16, gridDim.x - nb8 - nb16, hp, prep);
     if (hist) {
         __syncthreads();
         for (int i = threadIdx.x; i < kPasses * 256; i += blockDim.x)
@@ -682,6 +707,279 @@ __global__ void __launch_bounds__(kSortThreads) k_pass_one(J job, int p, int e, 
     }
 }
 
+// ---------------------------------------------------------------- merge sort
+// A single table's finish (counts below 2^32) sorts its entries by one
+// 128-bit key each (ms_key_prep: count descending, then the 16-letter
+// prefix); the entry index travels with the key.  Keys that tie belong to
+// long words sharing count and prefix, which the long-word fix-up orders
+// afterwards, so ties may come out in any order.  Blocks first sort runs of
+// kMsTile entries: each thread sorts kMsPer entries in registers (a bitonic
+// network), then the block merges pairs of sorted pieces in shared memory
+// until the run is whole.  Each round then merges pairs of runs into runs
+// twice as long, until one run holds every entry: ceil(log2(n / kMsTile))
+// rounds, each one launch in which no block waits for another.  A block of a
+// round writes kMsTile consecutive outputs of one merged pair: it finds how
+// many of them come from the first run at its first and last output (the
+// merge path split; each search step tests kMsThreads candidates at once, one
+// a thread, and keeps the interval between the last that goes first and the
+// first that does not), stages the two input pieces in shared memory, and
+// merges kMsPer outputs a thread.  Every merge takes the first run's entry on
+// a tie, and every search counts the same way.  Keys and indices alternate
+// between two buffers: the run sort writes buffer 1, round r reads buffer
+// r & 1.
+constexpr int kMsTile = 4096;
+constexpr int kMsThreads = 256;
+constexpr int kMsPer = kMsTile / kMsThreads;  // entries a thread sorts or merges
+static_assert(kMsPer == 16 && (kMsTile & (kMsTile - 1)) == 0, "16 entries a thread, power-of-two runs");
+// Shared memory: slot i at i + i / 16, so that the 16 consecutive entries of
+// each of a warp's threads fall in different banks.
+constexpr int kMsSlots = kMsTile + kMsTile / 16;
+constexpr size_t kMsSmem = (size_t)kMsSlots * (8 + 8 + 4);
+__host__ __device__ __forceinline__ int ms_rounds(unsigned long long n) {
+    int r = 0;
+    for (unsigned long long len = kMsTile; len < n; len <<= 1) r++;
+    return r;
+}
+struct MsKey {
+    unsigned long long h, l;
+    uint32_t x;  // entry index (not compared)
+};
+// A run sort's key: the index within the run in the 16 free low bits of l.
+struct MsKey2 {
+    unsigned long long h, l;
+};
+__device__ __forceinline__ bool ms_less(const MsKey &a, const MsKey &b) { return a.h != b.h ? a.h < b.h : a.l < b.l; }
+__device__ __forceinline__ bool ms_less(const MsKey2 &a, const MsKey2 &b) { return a.h != b.h ? a.h < b.h : a.l < b.l; }
+struct MsShared {
+    unsigned long long *h, *l;
+    uint32_t *x;
+    __device__ __forceinline__ explicit MsShared(unsigned long long *base)
+        : h(base), l(base + kMsSlots), x(reinterpret_cast<uint32_t *>(base + 2 * kMsSlots)) {}
+    __device__ __forceinline__ static uint32_t at(uint32_t i) { return i + (i >> 4); }
+    __device__ __forceinline__ void get(uint32_t i, MsKey &k) const {
+        const uint32_t j = at(i);
+        k = MsKey{h[j], l[j], x[j]};
+    }
+    __device__ __forceinline__ void get(uint32_t i, MsKey2 &k) const {
+        const uint32_t j = at(i);
+        k = MsKey2{h[j], l[j]};
+    }
+    __device__ __forceinline__ void put(uint32_t i, const MsKey &k) const {
+        const uint32_t j = at(i);
+        h[j] = k.h;
+        l[j] = k.l;
+        x[j] = k.x;
+    }
+    __device__ __forceinline__ void put(uint32_t i, const MsKey2 &k) const {
+        const uint32_t j = at(i);
+        h[j] = k.h;
+        l[j] = k.l;
+    }
+};
+// How many of sm[a0, a0 + na) lead the first d outputs of merging them with
+// sm[b0, b0 + nb) (the first piece first on ties), by bisection.
+template <class K>
+__device__ __forceinline__ uint32_t ms_split(const MsShared &sm, uint32_t a0, uint32_t na, uint32_t b0, uint32_t nb,
+                                             uint32_t d) {
+    uint32_t lo = d > nb ? d - nb : 0u, hi = d < na ? d : na;
+    while (lo < hi) {
+        const uint32_t m = (lo + hi) >> 1;
+        K ka, kb;
+        sm.get(a0 + m, ka);
+        sm.get(b0 + d - 1 - m, kb);
+        if (!ms_less(kb, ka)) lo = m + 1;
+        else hi = m;
+    }
+    return lo;
+}
+// cnt (<= kMsPer) outputs of merging sm[a0, a0 + na) with sm[b0, b0 + nb),
+// starting ia entries into the first and ib into the second, into v.
+template <class K>
+__device__ __forceinline__ void ms_merge_into(const MsShared &sm, uint32_t a0, uint32_t na, uint32_t b0, uint32_t nb,
+                                              uint32_t ia, uint32_t ib, uint32_t cnt, K (&v)[kMsPer]) {
+    K ka{}, kb{};
+    if (ia < na) sm.get(a0 + ia, ka);
+    if (ib < nb) sm.get(b0 + ib, kb);
+#pragma unroll
+    for (int k = 0; k < kMsPer; k++) {
+        if ((uint32_t)k < cnt) {  // ia + ib < na + nb: one of the pieces has an entry left
+            const bool fromA = ib >= nb || (ia < na && !ms_less(kb, ka));
+            v[k] = fromA ? ka : kb;
+            if (fromA) {
+                if (++ia < na) sm.get(a0 + ia, ka);
+            } else {
+                if (++ib < nb) sm.get(b0 + ib, kb);
+            }
+        }
+    }
+}
+
+// Sorts entries [kMsTile * b, kMsTile * (b + 1)) of buffer 0 into buffer 1;
+// block 0 records which buffer the last round leaves the order in.
+__global__ void __launch_bounds__(kMsThreads) k_ms_runs(SortScratch s, const unsigned long long *meta) {
+    extern __shared__ __align__(16) unsigned long long ms_smem[];
+    const MsShared sm(ms_smem);
+    grid_dependency_wait();
+    grid_dependency_trigger();
+    const unsigned long long n = meta[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0) s.cur[kCurFinal] = (ms_rounds(n) & 1) ? 0u : 1u;
+    const unsigned long long base = (unsigned long long)blockIdx.x * kMsTile;
+    if (base >= n) return;
+    const uint32_t m = (uint32_t)(n - base < (unsigned long long)kMsTile ? n - base : (unsigned long long)kMsTile);
+    const uint32_t t = threadIdx.x;
+    // coalesced loads into shared memory (padding past m sorts last), then
+    // each thread's kMsPer consecutive entries into registers
+    MsKey2 v[kMsPer];
+#pragma unroll
+    for (int k = 0; k < kMsPer; k++) {
+        const uint32_t i = t + (uint32_t)k * kMsThreads;
+        v[k] = i < m ? MsKey2{s.mk[0][base + i], s.mk[1][base + i] | i} : MsKey2{~0ull, ~0ull};
+    }
+#pragma unroll
+    for (int k = 0; k < kMsPer; k++) sm.put(t + (uint32_t)k * kMsThreads, v[k]);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kMsPer; k++) sm.get(kMsPer * t + k, v[k]);
+    // bitonic network over the thread's entries (ascending)
+#pragma unroll
+    for (int k = 2; k <= kMsPer; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+            for (int i = 0; i < kMsPer; i++) {
+                const int p = i ^ j;
+                if (p > i && ms_less(v[p], v[i]) == ((i & k) == 0)) {
+                    const MsKey2 w = v[i];
+                    v[i] = v[p];
+                    v[p] = w;
+                }
+            }
+    // merge sorted pieces of sz entries in pairs until the run is whole;
+    // thread t produces outputs [kMsPer * t, kMsPer * (t + 1)) of its pair
+    for (uint32_t sz = kMsPer; sz < (uint32_t)kMsTile; sz <<= 1) {
+        __syncthreads();  // every thread has read the previous level
+#pragma unroll
+        for (int k = 0; k < kMsPer; k++) sm.put(kMsPer * t + k, v[k]);
+        __syncthreads();
+        const uint32_t g0 = (kMsPer * t) & ~(2 * sz - 1), d = kMsPer * t - g0;
+        const uint32_t ia = ms_split<MsKey2>(sm, g0, sz, g0 + sz, sz, d);
+        ms_merge_into(sm, g0, sz, g0 + sz, sz, ia, d - ia, kMsPer, v);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kMsPer; k++) sm.put(kMsPer * t + k, v[k]);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kMsPer; k++) {
+        const uint32_t i = t + (uint32_t)k * kMsThreads;
+        if (i < m) {
+            MsKey2 w;
+            sm.get(i, w);
+            s.mk[2][base + i] = w.h;
+            s.mk[3][base + i] = w.l & ~0xFFFFull;
+            s.perm[1][base + i] = (uint32_t)(base + (w.l & 0xFFFFull));
+        }
+    }
+}
+
+// Round r: runs of kMsTile << (r - 1) entries merged in pairs.
+__global__ void __launch_bounds__(kMsThreads) k_ms_merge(SortScratch s, const unsigned long long *meta, int r) {
+    extern __shared__ __align__(16) unsigned long long ms_smem[];
+    const MsShared sm(ms_smem);
+    grid_dependency_wait();
+    grid_dependency_trigger();
+    const unsigned long long n = meta[0];
+    const unsigned long long R = (unsigned long long)kMsTile << (r - 1);
+    const unsigned long long out0 = (unsigned long long)blockIdx.x * kMsTile;
+    if (R >= n || out0 >= n) return;  // one run holds everything already / no tile
+    const uint32_t src = (uint32_t)r & 1u;
+    const unsigned long long *ih = s.mk[src ? 2 : 0], *il = s.mk[src ? 3 : 1];
+    const uint32_t *ix = s.perm_buf(src);
+    unsigned long long *oh = s.mk[src ? 0 : 2], *ol = s.mk[src ? 1 : 3];
+    uint32_t *ox = s.perm_buf(1u - src);
+    // this tile's pair: run A = [p0, ae), run B = [ae, be); outputs [out0, out1)
+    const unsigned long long out1 = out0 + kMsTile < n ? out0 + kMsTile : n;
+    const unsigned long long p0 = out0 / (2 * R) * (2 * R);
+    const unsigned long long ae = p0 + R < n ? p0 + R : n, be = p0 + 2 * R < n ? p0 + 2 * R : n;
+    const uint32_t la = (uint32_t)(ae - p0), lb = (uint32_t)(be - ae);
+    const uint32_t d0 = (uint32_t)(out0 - p0), d1 = (uint32_t)(out1 - p0);
+    // A[a] goes before B[d - 1 - a]: its key is not above (A first on ties)
+    auto first = [&](uint32_t d, uint32_t a) {
+        const unsigned long long bh = ih[ae + d - 1 - a], bl = il[ae + d - 1 - a];
+        const unsigned long long ah = ih[p0 + a], al = il[p0 + a];
+        return !(bh != ah ? bh < ah : bl < al);
+    };
+    // the splits of outputs d0 and d1, searched together: a in
+    // [max(0, d - lb), min(d, la)], every bound block-uniform
+    constexpr uint32_t P = kMsThreads;
+    auto cand = [](uint32_t lo, uint32_t w, uint32_t i) -> uint32_t {  // i-th of P candidates in [lo, lo + w)
+        return w <= P ? lo + i : lo + (uint32_t)(((unsigned long long)(i + 1) * w) / (P + 1));
+    };
+    uint32_t lo0 = d0 > lb ? d0 - lb : 0u, hi0 = d0 < la ? d0 : la;
+    uint32_t lo1 = d1 > lb ? d1 - lb : 0u, hi1 = d1 < la ? d1 : la;
+    const uint32_t t = threadIdx.x;
+    while (lo0 < hi0 || lo1 < hi1) {  // each step leaves at most w / (P + 1) + 1 of w > P candidates, 0 of fewer
+        const uint32_t w0 = hi0 - lo0, w1 = hi1 - lo1;
+        const bool b0 = t < (w0 < P ? w0 : P) && first(d0, cand(lo0, w0, t));
+        const bool b1 = t < (w1 < P ? w1 : P) && first(d1, cand(lo1, w1, t));
+        const uint32_t c0 = (uint32_t)__syncthreads_count(b0), c1 = (uint32_t)__syncthreads_count(b1);
+        if (w0 <= P) {
+            lo0 += c0;
+            hi0 = lo0;
+        } else {
+            const uint32_t nl = c0 ? cand(lo0, w0, c0 - 1) + 1 : lo0;
+            if (c0 < P) hi0 = cand(lo0, w0, c0);
+            lo0 = nl;
+        }
+        if (w1 <= P) {
+            lo1 += c1;
+            hi1 = lo1;
+        } else {
+            const uint32_t nl = c1 ? cand(lo1, w1, c1 - 1) + 1 : lo1;
+            if (c1 < P) hi1 = cand(lo1, w1, c1);
+            lo1 = nl;
+        }
+    }
+    // the tile's inputs, A[lo0, lo1) then B[d0 - lo0, d1 - lo1): na + nb = L
+    const uint32_t L = d1 - d0, na = lo1 - lo0, nb = L - na;
+    const unsigned long long ga = p0 + lo0, gb = ae + (d0 - lo0);
+    MsKey v[kMsPer];
+#pragma unroll
+    for (int k = 0; k < kMsPer; k++) {
+        const uint32_t i = t + (uint32_t)k * kMsThreads;
+        if (i < L) {
+            const unsigned long long g = i < na ? ga + i : gb + (i - na);
+            v[k] = MsKey{ih[g], il[g], ix[g]};
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kMsPer; k++) {
+        const uint32_t i = t + (uint32_t)k * kMsThreads;
+        if (i < L) sm.put(i, v[k]);
+    }
+    __syncthreads();
+    // thread t: outputs [kMsPer * t, ...) of the tile, from its own split
+    const uint32_t dt = kMsPer * t < L ? kMsPer * t : L, cnt = L - dt < (uint32_t)kMsPer ? L - dt : (uint32_t)kMsPer;
+    const uint32_t ia = ms_split<MsKey>(sm, 0, na, na, nb, dt);
+    ms_merge_into(sm, 0, na, na, nb, ia, dt - ia, cnt, v);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kMsPer; k++)
+        if ((uint32_t)k < cnt) sm.put(dt + k, v[k]);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kMsPer; k++) {
+        const uint32_t i = t + (uint32_t)k * kMsThreads;
+        if (i < L) {
+            MsKey w;
+            sm.get(i, w);
+            oh[out0 + i] = w.h;
+            ol[out0 + i] = w.l;
+            ox[out0 + i] = w.x;
+        }
+    }
+}
+
 // Compares two entries whose 16-byte prefixes are equal by the bytes after
 // the prefix (a word that fits the prefix is a proper prefix of a longer one).
 __device__ __forceinline__ bool tail_less(const LongView &v, uint32_t a, uint32_t b) {
@@ -804,8 +1102,18 @@ static int grid_for(unsigned long long n, int threads, int max_blocks) {
     return (int)g;
 }
 
-// reset + fused compaction + the sort without its key pass + gather
-int finish_table_launches(uint64_t cap, uint32_t skip) { return 2 + sort_entries_launches(kPasses, cap, skip) - 1 + 1; }
+// A single table's finish merge-sorts when the scratch has the key buffers
+// and every count is below 2^32 (the radix sort's count digits 4..7 skipped).
+static bool use_msort(const SortScratch &ss, uint32_t skip) {
+    return ss.mk[0] && ((skip >> (kSortKeyPasses + 4)) & 0xFu) == 0xFu;
+}
+
+// reset + fused compaction + (run sort + merge rounds + long-word fix-up, or
+// the sort without its key pass) + gather
+int finish_table_launches(const SortScratch &ss, uint32_t skip) {
+    if (use_msort(ss, skip)) return 2 + 1 + ms_rounds(ss.cap) + 1 + 1;
+    return 2 + sort_entries_launches(kPasses, ss.cap, skip) - 1 + 1;
+}
 
 // The passes of one sort, for one table (J = OneJob) or a list of them;
 // keyed: the compaction has prepared the sort keys and histograms already.
@@ -836,6 +1144,19 @@ static void launch_sort(const J &job, uint64_t cap, int ntab, int passes, uint32
         e++;
     }
     launch_dependent(k_fix_long<J>, dim3(grid_for(cap, 256, sms * 4), ntab), dim3(256), 0, st, job, passes);
+}
+
+// Merge sort of a single table's entries (keys from the compaction): the
+// runs, every round the capacity may need (rounds beyond the entries' own
+// return at once), then the long-word fix-up.
+static void launch_msort(const OneJob &job, uint64_t cap, cudaStream_t st) {
+    const int grid = (int)std::max<uint64_t>(1, (cap + kMsTile - 1) / kMsTile);
+    ensure_smem_limit((const void *)k_ms_runs, (int)kMsSmem);
+    ensure_smem_limit((const void *)k_ms_merge, (int)kMsSmem);
+    launch_dependent(k_ms_runs, dim3(grid), dim3(kMsThreads), kMsSmem, st, job.j.s, job.j.meta);
+    for (int r = 1; r <= ms_rounds(cap); r++)
+        launch_dependent(k_ms_merge, dim3(grid), dim3(kMsThreads), kMsSmem, st, job.j.s, job.j.meta, r);
+    launch_dependent(k_fix_long<OneJob>, dim3(grid_for(cap, 256, sm_count() * 4)), dim3(256), 0, st, job, kPasses);
 }
 
 // LSD radix sort of the entries in ss (count n = meta[0]) into ss.perm_buf(ss.cur[passes]).
@@ -889,21 +1210,22 @@ void sort_state_reset(SortScratch &ss, cudaStream_t st) {
 // Resets the sort state and compacts the three tables in one launch (with
 // `keyed`, also preparing the sort keys and histograms).
 static void launch_compaction(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_t glcap, SortScratch &ss,
-                              DevTable &out, cudaStream_t st, bool keyed) {
+                              DevTable &out, cudaStream_t st, int prep) {
     const int sms = sm_count();
     sort_state_reset(ss, st);
     const int nb8 = grid_for(gcap8, 256 * kScanUnroll, sms * 8), nb16 = grid_for(gcap, 256 * kScanUnroll, sms * 8),
               nbl = grid_for(glcap, 256, sms * 8);
     launch_dependent(k_compact_all, dim3(nb8 + nb16 + nbl), dim3(256), 0, st, g, (unsigned long long)gcap8,
-                     (unsigned long long)gcap, (unsigned long long)glcap, ss, out, (unsigned)nb8, (unsigned)nb16,
-                     keyed ? 1 : 0);
+                     (unsigned long long)gcap, (unsigned long long)glcap, ss, out, (unsigned)nb8, (unsigned)nb16, prep);
 }
 
 cudaError_t finish_table(const GTable &g, uint64_t gcap8, uint64_t gcap, uint64_t glcap, SortScratch &ss,
                          DevTable &out, cudaStream_t st, uint32_t skip) {
-    launch_compaction(g, gcap8, gcap, glcap, ss, out, st, true);
+    const bool ms = use_msort(ss, skip);
+    launch_compaction(g, gcap8, gcap, glcap, ss, out, st, ms ? kPrepMerge : kPrepRadix);
     OneJob job{SortJob{ss, out.d_meta, LongView{ss.lref, out.loff, out.llen, out.arena}, out}};
-    launch_sort(job, ss.cap, 1, kPasses, skip, st, true);
+    if (ms) launch_msort(job, ss.cap, st);
+    else launch_sort(job, ss.cap, 1, kPasses, skip, st, true);
     launch_dependent(k_gather_final<OneJob>, dim3(grid_for(ss.cap, 256 * kScanUnroll, sm_count() * 8)), dim3(256), 0,
                      st, job);
     return cudaGetLastError();
@@ -920,7 +1242,7 @@ cudaError_t finish_tables(const FinishSpec *spec, int n, void *d_jobs, cudaStrea
     uint64_t cap = 0;
     for (int t = 0; t < n; t++) {
         const FinishSpec &f = spec[t];
-        launch_compaction(f.g, f.gcap8, f.gcap, f.glcap, *f.ss, *f.out, st, false);
+        launch_compaction(f.g, f.gcap8, f.gcap, f.glcap, *f.ss, *f.out, st, kPrepNone);
         jobs[t] = SortJob{*f.ss, f.out->d_meta, LongView{f.ss->lref, f.out->loff, f.out->llen, f.out->arena}, *f.out};
         cap = std::max<uint64_t>(cap, f.ss->cap);
     }

@@ -314,3 +314,34 @@ def test_counts_across_digit_boundaries(ctr):
     text = b"".join((w + b" ") * n for w, n in parts)
     t = ctr.count_checked(to_dev(text))
     assert t.as_list() == [(w, n) for w, n in parts]
+
+
+def distinct_words(rng, n: int) -> list[bytes]:
+    """n distinct lowercase words of 1-14 letters, in random order."""
+    letters = np.frombuffer(b"abcdefghijklmnopqrstuvwxyz", np.uint8)
+    seen = set()
+    out = []
+    while len(out) < n:
+        w = letters[rng.integers(0, 26, int(rng.integers(1, 15)))].tobytes()
+        if w not in seen:
+            seen.add(w)
+            out.append(w)
+    return out
+
+
+@pytest.mark.parametrize("ndistinct", [4095, 4096, 4097, 8192, 8193, 12289, 40000, 65537])
+def test_distinct_counts_around_sort_tiles(ctr, ndistinct):
+    """Tables of exactly 4096 * k - 1 ... 4096 * k + 1 distinct words and
+    larger: the sort's runs of 4096 entries and every merge of them.  Most
+    counts are 1-3, so runs of equal counts span tiles and are ordered by the
+    word; a few words of 17+ letters share their first 16 letters and count."""
+    rng = np.random.default_rng(ndistinct)
+    words = distinct_words(rng, ndistinct - 6)
+    words += [b"sharedprefixabcd" + s for s in (b"zz", b"a", b"mmm", b"b", b"zzz", b"")]
+    counts = rng.choice([1, 1, 1, 2, 2, 3, 7, 40], size=len(words))
+    counts[-6:] = 2
+    tokens = np.repeat(np.arange(len(words)), counts)
+    rng.shuffle(tokens)
+    data = b" ".join(words[i] for i in tokens)
+    exp = check(ctr, data, what=f"{ndistinct} distinct words")
+    assert exp[2].size == ndistinct
