@@ -805,10 +805,16 @@ __device__ __forceinline__ void ms_merge_into(const MsShared &sm, uint32_t a0, u
         if ((uint32_t)k < cnt) {  // ia + ib < na + nb: one of the pieces has an entry left
             const bool fromA = ib >= nb || (ia < na && !ms_less(kb, ka));
             v[k] = fromA ? ka : kb;
-            if (fromA) {
-                if (++ia < na) sm.get(a0 + ia, ka);
-            } else {
-                if (++ib < nb) sm.get(b0 + ib, kb);
+            // one load path for either piece (lanes taking from different
+            // pieces do not diverge): the taken piece's next entry
+            ia += fromA ? 1u : 0u;
+            ib += fromA ? 0u : 1u;
+            const uint32_t nx = fromA ? ia : ib;
+            if (nx < (fromA ? na : nb)) {
+                K nk;
+                sm.get((fromA ? a0 : b0) + nx, nk);
+                if (fromA) ka = nk;
+                else kb = nk;
             }
         }
     }
@@ -910,20 +916,23 @@ __global__ void __launch_bounds__(kMsThreads) k_ms_merge(SortScratch s, const un
         return !(bh != ah ? bh < ah : bl < al);
     };
     // the splits of outputs d0 and d1, searched together: a in
-    // [max(0, d - lb), min(d, la)], every bound block-uniform
-    constexpr uint32_t P = kMsThreads;
-    auto cand = [](uint32_t lo, uint32_t w, uint32_t i) -> uint32_t {  // i-th of P candidates in [lo, lo + w)
-        return w <= P ? lo + i : lo + (uint32_t)(((unsigned long long)(i + 1) * w) / (P + 1));
+    // [max(0, d - lb), min(d, la)], every bound block-uniform.  An interval
+    // of w <= E candidates is tested whole (thread i tests lo + i); a wider
+    // one at the P = E - 1 points lo + (i + 1) w / E (no division: E = 256)
+    constexpr uint32_t E = kMsThreads, P = E - 1;
+    static_assert(kMsThreads == 256, "candidates placed by a shift of 8");
+    auto cand = [](uint32_t lo, uint32_t w, uint32_t i) -> uint32_t {
+        return w <= E ? lo + i : lo + (uint32_t)(((unsigned long long)(i + 1) * w) >> 8);
     };
     uint32_t lo0 = d0 > lb ? d0 - lb : 0u, hi0 = d0 < la ? d0 : la;
     uint32_t lo1 = d1 > lb ? d1 - lb : 0u, hi1 = d1 < la ? d1 : la;
     const uint32_t t = threadIdx.x;
-    while (lo0 < hi0 || lo1 < hi1) {  // each step leaves at most w / (P + 1) + 1 of w > P candidates, 0 of fewer
+    while (lo0 < hi0 || lo1 < hi1) {  // each step leaves at most w / E + 1 of w > E candidates, 0 of fewer
         const uint32_t w0 = hi0 - lo0, w1 = hi1 - lo1;
-        const bool b0 = t < (w0 < P ? w0 : P) && first(d0, cand(lo0, w0, t));
-        const bool b1 = t < (w1 < P ? w1 : P) && first(d1, cand(lo1, w1, t));
+        const bool b0 = t < (w0 <= E ? w0 : P) && first(d0, cand(lo0, w0, t));
+        const bool b1 = t < (w1 <= E ? w1 : P) && first(d1, cand(lo1, w1, t));
         const uint32_t c0 = (uint32_t)__syncthreads_count(b0), c1 = (uint32_t)__syncthreads_count(b1);
-        if (w0 <= P) {
+        if (w0 <= E) {
             lo0 += c0;
             hi0 = lo0;
         } else {
@@ -931,7 +940,7 @@ __global__ void __launch_bounds__(kMsThreads) k_ms_merge(SortScratch s, const un
             if (c0 < P) hi0 = cand(lo0, w0, c0);
             lo0 = nl;
         }
-        if (w1 <= P) {
+        if (w1 <= E) {
             lo1 += c1;
             hi1 = lo1;
         } else {
