@@ -3,13 +3,16 @@
 // After the counting kernel the global hash tables hold each distinct word
 // once with its exact count (Sec. 3.3's reduced dictionary).  This file turns
 // them into the sorted output: compact the occupied slots, copy long words
-// into the table's own byte arena, then an LSD radix sort over a permutation:
-// 10 byte-digits of the 16-letter prefix packed 5 bits a letter (0 for
+// into the table's own byte arena, then sort.  A single table whose counts
+// are below 2^32 is merge-sorted by one 128-bit key per entry (the
+// complemented count, then the 16-letter prefix packed 5 bits a letter: 0 for
 // padding, 1..26 for a..z, so integer order is lexicographic order and a
-// proper prefix sorts first) and up to 8 digits of the complemented count
-// (count descending), then a fix-up that orders long words sharing count and
-// 16-letter prefix by their remaining bytes.  Every pass is stable, so the
-// final order is (count desc, word asc).  Digits that are equal for every
+// proper prefix sorts first).  Other sorts (batched, merged and allocation-
+// free tables) are an LSD radix sort over a permutation: 10 byte-digits of
+// the packed prefix and up to 8 digits of the complemented count (count
+// descending).  Either is followed by a fix-up that orders long words sharing
+// count and 16-letter prefix by their remaining bytes; every radix pass is
+// stable, so the final order is (count desc, word asc).  Digits that are equal for every
 // element are skipped, detected on the device from one histogram pass; those
 // the host's bounds already show constant (count bytes above the token bound,
 // document bytes above the document count) are not launched at all.
